@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput of the structured-matrix-approximation hot path on one GB300.
+
+Workload: the space-time covariance matrix (Section 6.2 class; 64 time lags x
+256 random points in the unit square, non-separable Gneiting covariance),
+16384 x 16384, dense in HBM, block Toeplitz in time with p = 127 distinct
+256 x 256 blocks.  One step = the whole path: struct_E gather -> X x3 M
+(DCT-II) -> Jacobi SVD of the 127 frontal slices -> global truncation at
+relative tolerance 1e-6 -> Kronecker-sum factors -> report (ranks, error,
+orthogonality) -> Kronecker-sum matvec on 256 right-hand sides.
+
+Prints ONE JSON line (rank 0).  `value` = steps per second (t-SVDM
+compressions/s, each including its 256-RHS matvec); the matvec GFLOP/s and
+the fp64 GPU form are reported beside it.  With --impl reference the FP64 CPU
+oracle is timed on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+NSM = 152
+FP32_LANES_PER_SM = 128
+NRHS = 256
+REL_TOL = 1e-6
+WORKLOAD = "spacetime_covariance_T64_N256 (16384^2 block Toeplitz, tensor 256x256x127)"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        d["source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["source"] = "fallback"
+    return d
+
+
+def svd_flops(m, n):
+    """Golub-Van Loan operation count of a full SVD (U, S, V) of an m x n
+    matrix, m >= n: 4 m^2 n + 8 m n^2 + 9 n^3."""
+    m, n = max(m, n), min(m, n)
+    return 4 * m * m * n + 8 * m * n * n + 9 * n ** 3
+
+
+def kron_matvec_flops(m, n, ell, q, nterms, nrhs):
+    """Algorithmic flops of Y = sum_j D_j X C_j^T with dense m x n D_j and
+    ell x q C_j, per batch of nrhs right-hand sides."""
+    return nrhs * nterms * (2 * n * q * ell + 2 * m * n * ell)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# the GPU arm
+# ----------------------------------------------------------------------------
+
+def build_device_inputs(torch, pr, dtype, device):
+    """Dense column-major A (ell m x q n) assembled on the device from the
+    distinct blocks, and NRHS right-hand sides."""
+    from sma_inputs import generators as G
+    blocks = torch.from_numpy(pr.blocks).to(device=device, dtype=dtype)      # p, m, n
+    bm = torch.from_numpy(pr.block_map.astype(np.int64)).to(device)          # ell, q
+    A4 = blocks[bm]                                                          # ell, q, m, n
+    At = A4.permute(1, 3, 0, 2).reshape(pr.q * pr.n, pr.ell * pr.m).contiguous()
+    del A4
+    A = At.t()                                                               # column-major view
+    x = G.random_rhs(pr.q * pr.n, NRHS, 1)
+    X = torch.from_numpy(np.ascontiguousarray(x.T)).to(device=device, dtype=dtype).t()
+    Y = torch.empty(NRHS, pr.ell * pr.m, dtype=dtype, device=device).t()
+    return A, X, Y
+
+
+def run_gpu_form(torch, S, pr, prec, steps, warmup, device, stream, flush):
+    dtype = torch.float32 if prec == S.SMA_MIXED else torch.float64
+    A, X, Y = build_device_inputs(torch, pr, dtype, device)
+    h = S.Handle([pr], prec=prec, decomp=S.SMA_TSVDM, rel_tol=REL_TOL,
+                 stream=stream.cuda_stream, profile=True)
+    evs = []
+    with torch.cuda.stream(stream):
+        for it in range(warmup + steps):
+            flush.fill_(float(it))                      # evict L2 between steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            if it == warmup:
+                h.profile(reset=True)
+            e0.record(stream)
+            h.compress([A], want_result=False)
+            e1.record(stream)
+            h.apply(0, X, Y)
+            e2.record(stream)
+            stream.synchronize()
+            if it >= warmup:
+                evs.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+    res = h.result(0)
+    prof = h.profile(reset=True)
+    ranks = h.ranks(0)
+    h.close()
+    del A, X, Y
+    torch.cuda.empty_cache()
+    comp = np.array([a for a, _ in evs])
+    app = np.array([b for _, b in evs])
+    return {"compress_ms": comp, "apply_ms": app, "result": res, "profile": prof,
+            "ranks": ranks}
+
+
+def run_e2e(torch, S, pr, steps, warmup, device, stream):
+    """The same step through the C ABI with HOST buffers: the library copies
+    what it needs (the p representative blocks) host->device, the right-hand
+    sides go up and the result comes back inside the timed region."""
+    Ah = np.asfortranarray(pr.dense().astype(np.float32))
+    pinned = torch.from_numpy(np.ascontiguousarray(Ah.T)).pin_memory()
+    A_host = pinned.numpy().T                                 # Fortran view of pinned memory
+    from sma_inputs import generators as G
+    x = G.random_rhs(pr.q * pr.n, NRHS, 1).astype(np.float32)
+    Xp = torch.from_numpy(np.ascontiguousarray(x.T)).pin_memory()
+    Yp = torch.empty(NRHS, pr.ell * pr.m, dtype=torch.float32).pin_memory()
+    X_host, Y_host = Xp.numpy().T, Yp.numpy().T
+    h = S.Handle([pr], prec=S.SMA_MIXED, decomp=S.SMA_TSVDM, rel_tol=REL_TOL,
+                 stream=stream.cuda_stream)
+    times = []
+    with torch.cuda.stream(stream):
+        for it in range(warmup + steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.compress([A_host], want_result=True)        # report read back to the host
+            h.apply(0, X_host, Y_host)                     # waits for Y on the host
+            t1 = time.perf_counter()
+            if it >= warmup:
+                times.append(t1 - t0)
+    h.close()
+    h2d = pr.p * pr.m * pr.n * 4 + x.nbytes
+    d2h = Y_host.nbytes + 64                               # Y and the report
+    del pinned, Xp, Yp
+    return float(np.mean(times)), h2d, d2h
+
+
+def cpu_oracle_sample(pr, nslices=16, nrhs=4):
+    """The FP64 oracle as it stands on a bounded sample of one step: the full
+    gather and transform, `nslices` of the p slice SVDs and the Kronecker-sum
+    matvec for `nrhs` of the NRHS right-hand sides; scaled to a full step."""
+    from oracle import sma_oracle as O
+    A = pr.dense()
+    t0 = time.perf_counter()
+    X = O.T_E(A, pr.block_map, pr.p, pr.m, pr.n)
+    M = O.dct2_matrix(pr.p)
+    Xh = O.mode3(X, M)
+    t1 = time.perf_counter()
+    for i in range(nslices):
+        np.linalg.svd(Xh[:, :, i], full_matrices=False)
+    t2 = time.perf_counter()
+    # the matvec on the full-rank factors (every slice kept at this tolerance)
+    terms = [(O.struct_E(list(M[i, :]), pr.block_map, pr.p), Xh[:, :, i]) for i in range(pr.p)]
+    x = np.random.default_rng(0).standard_normal((pr.q * pr.n, nrhs))
+    t3 = time.perf_counter()
+    O.apply_kron(terms, x)
+    t4 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * pr.p / nslices + (t4 - t3) * NRHS / nrhs
+    return full, {"gather_transform_s": t1 - t0, "svd_s_per_slice": (t2 - t1) / nslices,
+                  "apply_s_per_rhs": (t4 - t3) / nrhs}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    from sma_inputs import generators as G
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pr = G.spacetime_covariance()          # 256 points, 64 lags, p = 127
+    cfg = {"workload": WORKLOAD, "ell": pr.ell, "m": pr.m, "n": pr.n, "p": pr.p,
+           "rel_tol": REL_TOL, "nrhs": NRHS, "transform": "orthonormal DCT-II",
+           "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        for _ in range(args.warmup + args.steps):
+            t, _ = cpu_oracle_sample(pr)
+            steps.append(t)
+        t = float(np.mean(steps[args.warmup:]))
+        v = 1.0 / t
+        line = {"impl": "reference", "metric": "t-SVDM compressions/s (incl. 256-RHS Kron-sum matvec)",
+                "value": v, "unit": "compressions/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": cfg,
+                "cpu_baseline": {"value": v, "unit": "compressions/s", "cores": os.cpu_count(),
+                                 "kind": "oracle",
+                                 "sample": "full gather+transform, 16 of 127 slice SVDs, "
+                                           "4 of 256 RHS of the matvec; scaled to a full step"},
+                "e2e": {"value": v, "unit": "compressions/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    import paper_2105_01170_gb300 as S
+    from paper_2105_01170_gb300 import _build
+    _build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    stream = torch.cuda.Stream(device=device)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    clocks.start()
+    mixed = run_gpu_form(torch, S, pr, S.SMA_MIXED, args.steps, args.warmup, device, stream, flush)
+    clk = clocks.stop()
+    step_ms = float(np.mean(mixed["compress_ms"] + mixed["apply_ms"]))
+    t_total = float(np.sum(mixed["compress_ms"] + mixed["apply_ms"])) / 1e3
+    if dist:
+        tt = torch.tensor([t_total], device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = world * args.steps / t_total
+
+    res = mixed["result"]
+    prof = mixed["profile"]
+    nterms = pr.p
+    mv_flops = kron_matvec_flops(pr.m, pr.n, pr.ell, pr.q, nterms, NRHS)
+    app_ms = float(np.mean(mixed["apply_ms"]))
+    svd_ms = prof["ms"]["svd"] / max(prof["calls"]["svd"], 1)
+    svd_alg = pr.p * svd_flops(pr.m, pr.n)
+    pk = peaks()
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = NSM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s fp32 FMA
+    achieved = svd_alg / (svd_ms * 1e-3) / 1e12
+    roof = {"kernel": "jacobi_kernel<float> (per-slice SVD, one CTA per slice)",
+            "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": achieved / alu_peak, "traffic": None,
+            "peak_note": f"fp32 FMA: {NSM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
+                         "(unit counts x max clock; no measured ALU peak)",
+            "algorithmic": f"{pr.p} x GVL SVD count 4m^2n+8mn^2+9n^3 = {svd_alg:.3e} flop/launch",
+            "launch_ms": svd_ms}
+
+    line = {"metric": "t-SVDM compressions/s (incl. 256-RHS Kron-sum matvec), mixed vs FP64 GPU",
+            "value": value, "unit": "compressions/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (bf16x3 tensor-core contractions, fp64 angles and energy sums)",
+            "data": "synthetic", "config": cfg,
+            "compress_ms": float(np.mean(mixed["compress_ms"])),
+            "matvec": {"gflops": mv_flops / (app_ms * 1e-3) / 1e9, "ms": app_ms,
+                       "flop_per_apply": mv_flops, "terms": nterms},
+            "stage_ms": {k: v / max(prof["calls"][k], 1) for k, v in prof["ms"].items()},
+            "result": {"total_rank": res["total_rank"], "rel_err": res["rel_err"],
+                       "orth_defect": res["orth_defect"], "sweeps_max": res["sweeps_max"],
+                       "device_status": res["device_status"]},
+            "roofline": roof, "clocks": clk,
+            "gpu_launches": int(prof["launches"])}
+
+    if args.fp64_steps > 0:
+        f64 = run_gpu_form(torch, S, pr, S.SMA_FP64, args.fp64_steps, 1, device, stream, flush)
+        f_ms = float(np.mean(f64["compress_ms"] + f64["apply_ms"]))
+        line["fp64_gpu"] = {"value": 1e3 / f_ms, "unit": "compressions/s", "ms_per_step": f_ms,
+                            "compress_ms": float(np.mean(f64["compress_ms"])),
+                            "matvec_gflops": mv_flops / (np.mean(f64["apply_ms"]) * 1e-3) / 1e9,
+                            "total_rank": f64["result"]["total_rank"],
+                            "rel_err": f64["result"]["rel_err"],
+                            "stage_ms": {k: v / max(f64["profile"]["calls"][k], 1)
+                                         for k, v in f64["profile"]["ms"].items()}}
+        line["mixed_vs_fp64_speedup"] = f_ms / step_ms
+        line["ranks_equal_to_fp64"] = bool(np.array_equal(f64["ranks"], mixed["ranks"]))
+
+    e2e_t, h2d, d2h = run_e2e(torch, S, pr, max(2, args.steps // 2), 1, device, stream)
+    line["e2e"] = {"value": 1.0 / e2e_t, "unit": "compressions/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h}
+
+    if rank == 0 and not args.no_cpu:
+        t_cpu, parts = cpu_oracle_sample(pr)
+        line["cpu_baseline"] = {"value": 1.0 / t_cpu, "unit": "compressions/s",
+                                "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "full gather+transform, 16 of 127 slice SVDs (numpy "
+                                          "LAPACK), 4 of 256 RHS of the matvec; scaled to a "
+                                          "full step", "parts": parts}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * sma.h -- C ABI of the GB300 structured-matrix-approximation library.
+ *
+ * Kilmer & Saibaba, "Structured Matrix Approximations via Tensor
+ * Decompositions" (arXiv 2105.01170), Algorithm 1 (Section 3.1):
+ *   (1) determine the tuples (A_k) and (E_k)            -> sma_create
+ *   (2) X := T_E[A]  (Section 3, matrix-to-tensor map)    -> sma_compress
+ *   (3) compress X (t-SVDM, or the Tucker/HOSVD variants
+ *       of Sections 2.4, 5.1, 6.2, 6.3, 7.4)              -> sma_compress
+ *   (4) A_hat := M_E[T]  (Section 3, tensor-to-matrix map)
+ *       kept in factored form: sum of Kronecker products
+ *       (Theorem 'tuckerkron', eq. structTucker) or block
+ *       low rank (eq. blockTuck)                           -> sma_compress
+ *       applied as a matvec                                 -> sma_apply
+ *       or expanded densely for validation                  -> sma_reconstruct
+ *   (5) rank and error; the Frobenius error of A_hat equals
+ *       the tensor truncation error (Lemma 1, Lemma 2)     -> sma_result
+ *
+ * Conventions shared by every call
+ *   - Every matrix is column-major.  Block (a, b) of an (ell*m) x (q*n) block
+ *     matrix starts at row a*m, column b*n.
+ *   - block_map is a host int32 array of ell*q entries, column-major (entry
+ *     (a, b) at a + b*ell); each entry is the distinct-block index k in
+ *     [0, p) or -1 for a zero block.  Every k in [0, p) must occur.
+ *   - The mapped tensor is stored frontal-slice: X is m x n x p with
+ *     X[:, :, k] = sqrt(eta_k) A_k (the paper's m x p x n tensor with modes 2
+ *     and 3 swapped).
+ *   - Precision SMA_FP64 takes and returns double; SMA_MIXED takes and returns
+ *     float (transform, Gram and matvec contractions as 3-piece bf16 products
+ *     on tensor cores with fp32 accumulation; Jacobi SVD in fp32 with fp64
+ *     rotation angles; fp64 energy sums).
+ *   - Pointers to A, X and Y may be device memory or host memory; host
+ *     buffers are copied on the handle's stream (only the bytes the call
+ *     needs).  Device memory owned by the handle is allocated in sma_create
+ *     and released in sma_destroy; no other call allocates, except sma_apply,
+ *     which grows a per-handle workspace the first time it sees a larger nrhs.
+ *   - All work is ordered on the stream given in sma_options (NULL = legacy
+ *     default stream).  Calls on one handle are not thread-safe.
+ *   - Errors are returned as sma_status; nothing is thrown across the ABI.
+ *     Kernels report failures through a device status word that is read by
+ *     sma_get_result.
+ */
+#ifndef SMA_H_
+#define SMA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sma_ctx* sma_handle;
+
+typedef enum {
+  SMA_OK = 0,
+  SMA_ERR_ARG = 1,          /* a size, pointer or option is invalid          */
+  SMA_ERR_STRUCT = 2,       /* block_map does not cover 0..p-1 / out of range */
+  SMA_ERR_CUDA = 3,         /* a CUDA runtime call failed                     */
+  SMA_ERR_ALLOC = 4,        /* device allocation failed                       */
+  SMA_ERR_NOCONVERGE = 5,   /* Jacobi hit max_sweeps before convergence       */
+  SMA_ERR_TIMEOUT = 6,      /* a bounded device wait gave up                  */
+  SMA_ERR_NONFINITE = 7,    /* NaN/Inf met in the input or a result           */
+  SMA_ERR_STATE = 8,        /* call out of order (e.g. apply before compress) */
+  SMA_ERR_UNSUPPORTED = 9   /* option combination not implemented             */
+} sma_status;
+
+typedef enum { SMA_FP64 = 0, SMA_MIXED = 1 } sma_precision;
+
+typedef enum {
+  /* t-SVDM: Xhat = X x3 M, SVD of every frontal slice, truncation, x3 M^T.
+   * Factored result: A_hat = sum_i struct_E(M[i,:]) (x) L_i R_i.           */
+  SMA_TSVDM = 0,
+  /* Tucker-1 along the block index (Section 6.3): T = G x V, V the leading
+   * left singular vectors of the block-index unfolding; the Kronecker rank.
+   * Factored result: A_hat = sum_j struct_E(V[:,j]) (x) G_j.               */
+  SMA_TUCKER_BLOCKMODE = 1,
+  /* Two-sided compression with one shared U (Sections 5.1 and 6.2): SPSD
+   * preserving block low rank (I (x) U) struct_E(U^T A_k U) (I (x) U^T).    */
+  SMA_TUCKER_SHARED_U = 2,
+  /* Tucker-2 on block rows and block columns (eq. blockTuck with V = I):
+   * (I (x) U) struct_E(U^T A_k W) (I (x) W^T).                            */
+  SMA_TUCKER_ROWCOL = 3,
+  /* Multilevel (Section 7): truncated HOSVD of the weighted coefficient
+   * tensor of a three-level structured matrix with m = n = 1; result
+   * sum_j G_j struct1(U1_j) (x) struct2(U2_j) (x) struct3(U3_j).           */
+  SMA_HOSVD_MULTILEVEL = 4
+} sma_decomp;
+
+typedef enum { SMA_M_DCT2 = 0, SMA_M_IDENTITY = 1, SMA_M_USER = 2 } sma_transform;
+
+typedef enum {
+  SMA_INPUT_DENSE = 0,   /* A is the full (ell*m) x (q*n) matrix, leading dim lda    */
+  SMA_INPUT_BLOCKS = 1   /* A is the p distinct blocks A_k, each m x n with leading
+                            dim lda, block k starting at A + k*lda*n (BSR-like)      */
+} sma_input_layout;
+
+/* One structured block matrix (Section 3: ell x q blocks of m x n, p distinct).
+ * Multilevel (Section 7.2, levels = 3, m = n = 1): level t has an
+ * level_ell[t] x level_q[t] map level_maps[t] with level_p[t] distinct
+ * indices; the distinct scalars are passed in SMA_INPUT_BLOCKS layout in the
+ * order i1 + p1*(i2 + p2*i3); ell, q, p and block_map are then ignored.     */
+typedef struct {
+  int32_t ell, q, m, n, p;
+  const int32_t* block_map;           /* host, ell*q, column-major          */
+  int32_t levels;                     /* 1 (default) or 3                   */
+  const int32_t* level_ell;           /* [levels]                           */
+  const int32_t* level_q;             /* [levels]                           */
+  const int32_t* level_p;             /* [levels]                           */
+  const int32_t* const* level_maps;   /* [levels] host column-major maps    */
+} sma_problem;
+
+typedef struct {
+  sma_precision prec;
+  sma_decomp decomp;
+  sma_transform mkind;
+  sma_input_layout layout;
+  const double* M_user;   /* host p x p column-major orthogonal, for SMA_M_USER */
+  int32_t fixed_rank;     /* > 0: rank per slice (t-SVDM) / per mode (Tucker)   */
+  double rel_tol;         /* used when fixed_rank == 0: ||A - A_hat||_F <=
+                             rel_tol ||A||_F (global over slices for t-SVDM)   */
+  int32_t max_sweeps;     /* Jacobi sweep limit (0 = 30)                        */
+  void* stream;           /* cudaStream_t                                       */
+  int32_t profile;        /* != 0: record per-stage CUDA events (sma_profile)   */
+} sma_options;
+
+typedef struct {
+  int32_t total_rank;     /* t-SVDM: sum_i rho_i; Tucker: product of ranks      */
+  int32_t n_kron_terms;   /* Kronecker terms (t-SVDM: slices with rho_i > 0)    */
+  int32_t ranks[3];       /* Tucker mode ranks (unused entries 0)               */
+  int32_t sweeps_max;     /* largest Jacobi sweep count used                    */
+  int32_t device_status;  /* bit set of sma_status values raised by kernels     */
+  double norm;            /* ||A||_F = ||X||_F                                   */
+  double tensor_err;      /* ||X - T||_F = ||A - A_hat||_F (Lemma 1)             */
+  double rel_err;         /* tensor_err / norm                                   */
+  double orth_defect;     /* max |U^T U - I| over the orthonormal factors       */
+} sma_result;
+
+/* Validate the problems, derive eta_k and the weights 1/sqrt(eta_k), build M
+ * (DCT-II computed in fp64 on the host), allocate every device buffer the
+ * compression needs.  No kernel runs.  nprob >= 1 problems share the options;
+ * they are compressed together by one sma_compress call (batched launches).
+ * Errors: SMA_ERR_ARG (sizes <= 0, nprob < 1, bad enum, M_user NULL),
+ * SMA_ERR_STRUCT (map entry outside [-1, p) or a k that never occurs),
+ * SMA_ERR_UNSUPPORTED, SMA_ERR_ALLOC, SMA_ERR_CUDA.  On error *h is NULL.  */
+sma_status sma_create(sma_handle* h, const sma_problem* probs, int32_t nprob,
+                      const sma_options* opt);
+
+/* Steps (2)-(5) for every problem: A[i] points to problem i's input (layout
+ * per options, element type per precision), lda[i] its leading dimension.
+ * Enqueued on the handle's stream.  If res is non-NULL the call waits for the
+ * stream and fills res[0..nprob-1]; with res == NULL it returns at once and
+ * results are read later with sma_get_result.
+ * Errors: SMA_ERR_ARG (NULL A, lda too small), SMA_ERR_CUDA; device-side
+ * problems (non-convergence, non-finite data) are reported in
+ * res->device_status and as the return value when res is non-NULL.        */
+sma_status sma_compress(sma_handle h, const void* const* A, const int64_t* lda,
+                        sma_result* res);
+
+/* Wait for the handle's stream and copy problem i's report to *res.        */
+sma_status sma_get_result(sma_handle h, int32_t i, sma_result* res);
+
+/* Copy the retained per-slice ranks (t-SVDM: p entries) or the Tucker mode
+ * ranks (up to 3 entries) of problem i to host array ranks; *count receives
+ * the number written.  Waits for the stream.                                */
+sma_status sma_get_ranks(sma_handle h, int32_t i, int32_t* ranks, int32_t* count);
+
+/* Dense A_hat = M_E[T] of problem i ((ell*m) x (q*n), leading dim ld) written
+ * to Ahat (device or host).  Validation only: O(ell q m n) memory.          */
+sma_status sma_reconstruct(sma_handle h, int32_t i, void* Ahat, int64_t ld);
+
+/* Y = A_hat X for nrhs right-hand sides (step 4, the factored matvec):
+ * X is (q*n) x nrhs with leading dim ldx, Y is (ell*m) x nrhs with leading
+ * dim ldy; each column of X is vec of an n x q matrix (Section 2.2,
+ * vec(D X C^T) = (C (x) D) vec(X)).  Errors: SMA_ERR_STATE before a
+ * successful sma_compress, SMA_ERR_ARG, SMA_ERR_ALLOC, SMA_ERR_CUDA.       */
+sma_status sma_apply(sma_handle h, int32_t i, const void* X, int64_t ldx,
+                     void* Y, int64_t ldy, int32_t nrhs);
+
+/* Inspection of intermediate device buffers for step-by-step validation.
+ * Copies `count` elements (element type per precision, except sigma: double)
+ * of buffer `which` of problem i to dst (device or host); *avail receives the
+ * number of elements the buffer holds (call with count = 0 to query).
+ *   0 = X (m*n*p, the gathered tensor, step 2)
+ *   1 = Xhat (m*n*p, X x3 M)
+ *   2 = sigma (p * min(m,n) doubles, per slice descending)
+ *   3 = T (m*n*p, the approximation tensor, after sma_reconstruct)
+ *   4 = Tucker factor of the compressed mode (rows x rank, column-major)   */
+sma_status sma_export(sma_handle h, int32_t i, int32_t which, void* dst,
+                      int64_t count, int64_t* avail);
+
+/* Stages of the path timed when sma_options.profile != 0.                   */
+typedef enum {
+  SMA_STAGE_GATHER = 0,     /* step 1: struct_E gather and ||X||_F              */
+  SMA_STAGE_TRANSFORM = 1,  /* X x3 M (t-SVDM) or the unfolding Gram (Tucker)   */
+  SMA_STAGE_SVD = 2,        /* Jacobi SVD of the slices / Gram eigen-solve      */
+  SMA_STAGE_TRUNCATE = 3,   /* rank selection and error                         */
+  SMA_STAGE_FACTORS = 4,    /* truncated slices / core, struct_E terms          */
+  SMA_STAGE_REPORT = 5,     /* orthogonality check                              */
+  SMA_STAGE_APPLY = 6,      /* the factored matvec                              */
+  SMA_STAGE_COUNT = 7
+} sma_stage;
+
+/* Device time of each stage in ms, summed over the calls since the last
+ * reset, measured with CUDA events recorded on the handle's stream around
+ * the stage's kernels (ms[SMA_STAGE_COUNT]); calls[s] receives how many times
+ * stage s ran (may be NULL); *launches the number of kernels the library
+ * launched (may be NULL).  Waits for the stream.  reset != 0 clears the sums
+ * after reading.  Errors: SMA_ERR_STATE when profiling is off.              */
+sma_status sma_profile(sma_handle h, double* ms, int64_t* calls, int64_t* launches,
+                       int32_t reset);
+
+sma_status sma_destroy(sma_handle h);
+
+const char* sma_status_string(sma_status s);
+
+/* Library version string and build target ("sm_103a").                     */
+const char* sma_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMA_H_ */

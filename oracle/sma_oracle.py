@@ -140,7 +140,7 @@ def dct2_matrix(p: int) -> np.ndarray:
 
 def mode3(X: np.ndarray, M: np.ndarray) -> np.ndarray:
     """X x3 M: out[:, :, i] = sum_k M[i, k] X[:, :, k] (Section 2.1 mode product)."""
-    return np.einsum("abk,ik->abi", X, M)
+    return np.einsum("abk,ik->abi", X, M, optimize=True)
 
 
 def unfold(X: np.ndarray, mode: int) -> np.ndarray:
@@ -415,7 +415,7 @@ class SharedU:
     rel_err: float
 
     def tensor_approx(self) -> np.ndarray:
-        return np.einsum("ai,ijk,bj->abk", self.U, self.G, self.U)
+        return np.einsum("ai,ijk,bj->abk", self.U, self.G, self.U, optimize=True)
 
 
 def shared_u(X: np.ndarray, rel_tol: float | None = None, rank: int | None = None) -> SharedU:
@@ -423,8 +423,8 @@ def shared_u(X: np.ndarray, rel_tol: float | None = None, rank: int | None = Non
     mode-1 unfolding (the two truncated modes share the budget, reading R5)."""
     normX2 = float(np.sum(X * X))
     U, s, r = leading_left_singular(unfold(X, 1), rank, (rel_tol or 0.0) ** 2 * normX2 / 2.0)
-    G = np.einsum("ai,abk,bj->ijk", U, X, U)
-    T = np.einsum("ai,ijk,bj->abk", U, G, U)
+    G = np.einsum("ai,abk,bj->ijk", U, X, U, optimize=True)
+    T = np.einsum("ai,ijk,bj->abk", U, G, U, optimize=True)
     err = float(np.linalg.norm((X - T).ravel()))
     return SharedU(U, G, s, r, err, err / math.sqrt(normX2))
 
@@ -438,7 +438,7 @@ class Tucker2:
     rel_err: float
 
     def tensor_approx(self) -> np.ndarray:
-        return np.einsum("ai,ijk,bj->abk", self.U, self.F, self.W)
+        return np.einsum("ai,ijk,bj->abk", self.U, self.F, self.W, optimize=True)
 
 
 def tucker2_rows_cols(X: np.ndarray, r1: int, r3: int) -> Tucker2:
@@ -446,8 +446,8 @@ def tucker2_rows_cols(X: np.ndarray, r1: int, r3: int) -> Tucker2:
     normX2 = float(np.sum(X * X))
     U, _, _ = leading_left_singular(unfold(X, 1), r1)
     W, _, _ = leading_left_singular(unfold(X, 2), r3)
-    F = np.einsum("ai,abk,bj->ijk", U, X, W)
-    T = np.einsum("ai,ijk,bj->abk", U, F, W)
+    F = np.einsum("ai,abk,bj->ijk", U, X, W, optimize=True)
+    T = np.einsum("ai,ijk,bj->abk", U, F, W, optimize=True)
     err = float(np.linalg.norm((X - T).ravel()))
     return Tucker2(U, W, F, err, err / math.sqrt(normX2))
 
@@ -463,7 +463,7 @@ class HOSVD3:
 
     def tensor_approx(self) -> np.ndarray:
         U1, U2, U3 = self.factors
-        return np.einsum("ijk,ai,bj,ck->abc", self.G, U1, U2, U3)
+        return np.einsum("ijk,ai,bj,ck->abc", self.G, U1, U2, U3, optimize=True)
 
 
 def hosvd3(X: np.ndarray, rel_tol: float | None = None, ranks=None) -> HOSVD3:
@@ -481,8 +481,8 @@ def hosvd3(X: np.ndarray, rel_tol: float | None = None, ranks=None) -> HOSVD3:
         facs.append(U)
         sig.append(s)
         rk.append(r)
-    G = np.einsum("abc,ai,bj,ck->ijk", X, *facs)
-    T = np.einsum("ijk,ai,bj,ck->abc", G, *facs)
+    G = np.einsum("abc,ai,bj,ck->ijk", X, *facs, optimize=True)
+    T = np.einsum("ijk,ai,bj,ck->abc", G, *facs, optimize=True)
     err = float(np.linalg.norm((X - T).ravel()))
     return HOSVD3(facs, G, sig, tuple(rk), err, err / math.sqrt(normX2))
 
@@ -510,7 +510,7 @@ def psf_tensor(P: np.ndarray, K: int) -> np.ndarray:
     half = s // 2
     eta = multiplicities(banded_toeplitz_map(K, half), s).astype(np.float64)
     w = np.sqrt(eta)
-    return np.einsum("i,j,k,kji->ijk", w, w, w, P)
+    return np.einsum("i,j,k,kji->ijk", w, w, w, P, optimize=True)
 
 
 def blur_matrix(P: np.ndarray, K: int) -> np.ndarray:
@@ -555,7 +555,7 @@ def multilevel_apply(G, C1, C2, C3, vols: np.ndarray) -> np.ndarray:
         for j2 in range(len(C2)):
             for j3 in range(len(C3)):
                 g = G[j1, j2, j3]
-                out += g * np.einsum("zc,yb,xa,nabc->nxyz", C1[j1], C2[j2], C3[j3], vols)
+                out += g * np.einsum("zc,yb,xa,nabc->nxyz", C1[j1], C2[j2], C3[j3], vols, optimize=True)
     return out
 
 

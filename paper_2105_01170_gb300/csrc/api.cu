@@ -1,0 +1,1126 @@
+// C ABI of the structured-matrix-approximation path (include/sma.h).
+//
+// Host side only: validation of the structure description, derivation of
+// eta_k and the weights (Section 3), the transform M, device buffers, and the
+// enqueueing of the kernels of gemm.cu, jacobi.cu, steps.cu and tc_gemm.cu.
+// Every arithmetic step of the path runs in those kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_gemm.cuh"
+
+using namespace sma;
+
+namespace {
+
+#define SMA_CK(...)                                 \
+  do {                                              \
+    cudaError_t e_ = (__VA_ARGS__);                           \
+    if (e_ != cudaSuccess) {                        \
+      last_cuda_error() = e_;                       \
+      return SMA_ERR_CUDA;                          \
+    }                                               \
+  } while (0)
+
+#define SMA_TRY(...)                  \
+  do {                                \
+    sma_status s_ = (__VA_ARGS__);              \
+    if (s_ != SMA_OK) return s_;      \
+  } while (0)
+
+cudaError_t& last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Orthonormal DCT-II in fp64 (the transform M of the t-SVDM):
+// M[k, j] = a_k cos(pi (2j+1) k / (2p)), a_0 = sqrt(1/p), a_k = sqrt(2/p).
+std::vector<double> dct2(int p) {
+  std::vector<double> M((size_t)p * p);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < p; ++k) {
+    const double a = std::sqrt((k == 0 ? 1.0 : 2.0) / p);
+    for (int j = 0; j < p; ++j) M[k + (size_t)j * p] = a * std::cos(pi * (2 * j + 1) * k / (2.0 * p));
+  }
+  return M;
+}
+
+struct DevBuf {
+  std::vector<void*> ptrs;
+  ~DevBuf() {
+    for (void* q : ptrs) cudaFree(q);
+  }
+  template <typename U>
+  sma_status alloc(U** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(U)) != cudaSuccess) {
+      cudaGetLastError();
+      return SMA_ERR_ALLOC;
+    }
+    ptrs.push_back(q);
+    *out = static_cast<U*>(q);
+    return SMA_OK;
+  }
+  void release(void* q) {
+    for (auto& x : ptrs)
+      if (x == q) {
+        cudaFree(x);
+        x = nullptr;
+      }
+  }
+};
+
+// Per-problem state, one element type T (double: SMA_FP64, float: SMA_MIXED).
+template <typename T>
+struct Prob {
+  // host description
+  int ell = 0, q = 0, m = 0, n = 0, p = 0;
+  std::vector<int32_t> map;                 // column-major
+  std::vector<int64_t> eta;
+  std::vector<int> rep_a, rep_b;            // representative block (Section 3)
+  // plan
+  JacobiPlan jp{};
+  int rc = 0, mm = 0;
+  // common device buffers
+  int* d_map = nullptr;
+  double* d_w = nullptr;                    // sqrt(eta_k)
+  double* d_isq = nullptr;                  // 1/sqrt(eta_k)
+  int64_t* d_rep = nullptr;
+  int64_t rep_lda = -1;
+  int rep_layout = -1;
+  T* X = nullptr;
+  double* partial = nullptr;
+  int nparts = 0;
+  double* stats = nullptr;                  // [0] ||X||^2, [1] discarded energy
+  int* iscal = nullptr;                     // [0] total rank [1] terms [2..4] mode ranks
+  int* status = nullptr;
+  int* sweeps = nullptr;
+  double* orth = nullptr;                   // per slice / factor
+  int n_orth = 0;
+  // staging for host inputs
+  T* stage = nullptr;
+  // t-SVDM
+  T* Mt = nullptr;                          // M, p x p column-major
+  T* Xh = nullptr;
+  T* Wj = nullptr;
+  T* U = nullptr;                           // W = U Sigma (sorted), mm x rc per slice
+  T* V = nullptr;                           // right singular vectors, rc x rc per slice
+  double* sigma = nullptr;
+  double* suf = nullptr;
+  int* ranks = nullptr;
+  int* off = nullptr;
+  T* Gorth = nullptr;
+  // Kronecker-sum terms: D (m x n x nterms_max) and C (ell x q x nterms_max)
+  T* D = nullptr;
+  T* C = nullptr;
+  int nterms_max = 0;
+  // Tucker
+  double* X64 = nullptr;                    // fp64 copy of X (Gram accumulation)
+  double* gram = nullptr;
+  double* gvec = nullptr;                   // Jacobi output of the Gram (vectors)
+  double* gsig = nullptr;                   // Gram eigenvalues
+  double* Wg = nullptr;                     // block-mode Jacobi workspace for the Gram
+  double* gW = nullptr;                     // Jacobi W output for the Gram (unused values)
+  size_t gstride = 0;                       // elements between the two Gram slots
+  int gdim = 0;
+  T* F1 = nullptr;                          // leading factor (rows), T
+  T* F2 = nullptr;                          // second factor (cols), T
+  T* core = nullptr;                        // r1 x r3 x p core slices
+  T* tmp = nullptr;
+  T* mid = nullptr;                         // struct_E(core) dense (ell r1 x q r3)
+  int r1max = 0, r3max = 0;
+  // reconstruction
+  T* Tt = nullptr;
+  // apply workspace
+  T* Z = nullptr;
+  size_t Z_elems = 0;
+  T* Z2 = nullptr;
+  size_t Z2_elems = 0;
+  T* Xs = nullptr;
+  size_t Xs_elems = 0;
+  T* Ys = nullptr;
+  size_t Ys_elems = 0;
+  bool compressed = false;
+  // host copies of results
+  int h_iscal[8] = {0};
+};
+
+}  // namespace
+
+struct sma_ctx {
+  sma_options opt{};
+  cudaStream_t st = nullptr;
+  int nprob = 0;
+  int max_smem = 0;
+  int tc_ok = 0;
+  DevBuf mem;
+  std::vector<Prob<double>> p64;
+  std::vector<Prob<float>> p32;
+  // profiling: CUDA events around each stage on the handle's stream
+  bool prof = false;
+  struct Pend {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_free, ev_all;
+  std::vector<Pend> pend;
+  cudaEvent_t cur_a = nullptr;
+  int cur_stage = -1;
+  double acc_ms[SMA_STAGE_COUNT] = {0};
+  int64_t acc_calls[SMA_STAGE_COUNT] = {0};
+  int64_t launches = 0;
+  ~sma_ctx() {
+    for (cudaEvent_t e : ev_all) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+cudaEvent_t ev_get(sma_ctx* h) {
+  if (!h->ev_free.empty()) {
+    cudaEvent_t e = h->ev_free.back();
+    h->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  h->ev_all.push_back(e);
+  return e;
+}
+
+void stage_begin(sma_ctx* h, int s) {
+  if (!h->prof) return;
+  h->cur_a = ev_get(h);
+  if (h->cur_a) cudaEventRecord(h->cur_a, h->st);
+  h->cur_stage = h->cur_a ? s : -1;
+}
+
+void stage_end(sma_ctx* h) {
+  if (!h->prof || h->cur_stage < 0) return;
+  cudaEvent_t b = ev_get(h);
+  if (b) {
+    cudaEventRecord(b, h->st);
+    h->pend.push_back({h->cur_stage, h->cur_a, b});
+  }
+  h->cur_stage = -1;
+}
+
+// every kernel launch of the library goes through SMA_K (counted)
+#define SMA_K(...)          \
+  do {                      \
+    ++h->launches;          \
+    SMA_CK(__VA_ARGS__);    \
+  } while (0)
+
+template <typename T>
+std::vector<Prob<T>>& probs(sma_ctx* h);
+template <>
+std::vector<Prob<double>>& probs<double>(sma_ctx* h) { return h->p64; }
+template <>
+std::vector<Prob<float>>& probs<float>(sma_ctx* h) { return h->p32; }
+
+sma_status validate_problem(const sma_problem& pr, std::vector<int64_t>& eta,
+                            std::vector<int>& ra, std::vector<int>& rb) {
+  if (pr.levels != 0 && pr.levels != 1) return SMA_ERR_UNSUPPORTED;
+  if (pr.ell <= 0 || pr.q <= 0 || pr.m <= 0 || pr.n <= 0 || pr.p <= 0) return SMA_ERR_ARG;
+  if (!pr.block_map) return SMA_ERR_ARG;
+  if ((int64_t)pr.p > (int64_t)pr.ell * pr.q) return SMA_ERR_STRUCT;
+  eta.assign(pr.p, 0);
+  ra.assign(pr.p, -1);
+  rb.assign(pr.p, -1);
+  for (int b = 0; b < pr.q; ++b)
+    for (int a = 0; a < pr.ell; ++a) {
+      const int k = pr.block_map[a + (size_t)b * pr.ell];
+      if (k < -1 || k >= pr.p) return SMA_ERR_STRUCT;
+      if (k < 0) continue;
+      if (eta[k]++ == 0) {
+        ra[k] = a;
+        rb[k] = b;
+      }
+    }
+  for (int k = 0; k < pr.p; ++k)
+    if (eta[k] == 0) return SMA_ERR_STRUCT;
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
+  auto& mem = h->mem;
+  const sma_options& o = h->opt;
+  SMA_TRY(validate_problem(pr, P.eta, P.rep_a, P.rep_b));
+  P.ell = pr.ell; P.q = pr.q; P.m = pr.m; P.n = pr.n; P.p = pr.p;
+  P.map.assign(pr.block_map, pr.block_map + (size_t)pr.ell * pr.q);
+  const int m = P.m, n = P.n, p = P.p;
+  const size_t mnp = (size_t)m * n * p;
+  std::vector<double> w(p), isq(p);
+  for (int k = 0; k < p; ++k) {
+    w[k] = std::sqrt((double)P.eta[k]);
+    isq[k] = 1.0 / w[k];
+  }
+  SMA_TRY(mem.alloc(&P.d_map, P.map.size()));
+  SMA_TRY(mem.alloc(&P.d_w, p));
+  SMA_TRY(mem.alloc(&P.d_isq, p));
+  SMA_TRY(mem.alloc(&P.d_rep, p));
+  SMA_CK(cudaMemcpy(P.d_map, P.map.data(), P.map.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  SMA_CK(cudaMemcpy(P.d_w, w.data(), p * sizeof(double), cudaMemcpyHostToDevice));
+  SMA_CK(cudaMemcpy(P.d_isq, isq.data(), p * sizeof(double), cudaMemcpyHostToDevice));
+  SMA_TRY(mem.alloc(&P.X, mnp));
+  P.nparts = gather_parts(m, n, p);
+  SMA_TRY(mem.alloc(&P.partial, P.nparts));
+  SMA_TRY(mem.alloc(&P.stats, 8));
+  SMA_TRY(mem.alloc(&P.iscal, 8));
+  SMA_TRY(mem.alloc(&P.status, 1));
+  SMA_TRY(mem.alloc(&P.Tt, mnp));
+  SMA_CK(cudaMemset(P.stats, 0, 8 * sizeof(double)));
+  SMA_CK(cudaMemset(P.iscal, 0, 8 * sizeof(int)));
+  SMA_CK(cudaMemset(P.status, 0, sizeof(int)));
+
+  if (o.decomp == SMA_TSVDM) {
+    std::vector<double> M;
+    if (o.mkind == SMA_M_DCT2) {
+      M = dct2(p);
+    } else if (o.mkind == SMA_M_IDENTITY) {
+      M.assign((size_t)p * p, 0.0);
+      for (int k = 0; k < p; ++k) M[k + (size_t)k * p] = 1.0;
+    } else {
+      if (!o.M_user) return SMA_ERR_ARG;
+      M.assign(o.M_user, o.M_user + (size_t)p * p);
+    }
+    std::vector<T> Mt(M.begin(), M.end());
+    SMA_TRY(mem.alloc(&P.Mt, (size_t)p * p));
+    SMA_CK(cudaMemcpy(P.Mt, Mt.data(), Mt.size() * sizeof(T), cudaMemcpyHostToDevice));
+    P.jp = jacobi_plan<T>(m, n, h->max_smem);
+    P.rc = P.jp.rc;
+    P.mm = P.jp.mm;
+    const size_t urc = (size_t)P.mm * P.rc * p;
+    SMA_TRY(mem.alloc(&P.Xh, mnp));
+    if (P.jp.block_mode) SMA_TRY(mem.alloc(&P.Wj, (size_t)(P.mm + P.rc) * P.rc * p));
+    SMA_TRY(mem.alloc(&P.U, urc));
+    SMA_TRY(mem.alloc(&P.V, (size_t)P.rc * P.rc * p));
+    SMA_TRY(mem.alloc(&P.sigma, (size_t)P.rc * p));
+    SMA_TRY(mem.alloc(&P.suf, (size_t)(P.rc + 1) * p));
+    SMA_TRY(mem.alloc(&P.sweeps, p));
+    SMA_TRY(mem.alloc(&P.ranks, p));
+    SMA_TRY(mem.alloc(&P.off, p + 1));
+    SMA_TRY(mem.alloc(&P.Gorth, (size_t)P.rc * P.rc * p));
+    SMA_TRY(mem.alloc(&P.orth, p));
+    P.n_orth = p;
+    P.nterms_max = p;
+    SMA_TRY(mem.alloc(&P.D, mnp));
+    SMA_TRY(mem.alloc(&P.C, (size_t)P.ell * P.q * p));
+  } else {
+    // Tucker family: fp64 Gram and its Jacobi eigen-solve
+    int gdim = 0;
+    if (o.decomp == SMA_TUCKER_BLOCKMODE) gdim = p;
+    else if (o.decomp == SMA_TUCKER_SHARED_U) gdim = m;
+    else if (o.decomp == SMA_TUCKER_ROWCOL) gdim = (m > n ? m : n);
+    else return SMA_ERR_UNSUPPORTED;
+    if (o.decomp == SMA_TUCKER_SHARED_U && m != n) return SMA_ERR_ARG;
+    P.gdim = gdim;
+    P.gstride = (size_t)gdim * gdim;
+    SMA_TRY(mem.alloc(&P.X64, mnp));
+    SMA_TRY(mem.alloc(&P.Wg, (size_t)gdim * gdim * 2));
+    SMA_TRY(mem.alloc(&P.gW, (size_t)gdim * gdim));
+    SMA_TRY(mem.alloc(&P.gram, (size_t)gdim * gdim * 2));
+    SMA_TRY(mem.alloc(&P.gvec, (size_t)gdim * gdim * 2));
+    SMA_TRY(mem.alloc(&P.gsig, (size_t)gdim * 2));
+    SMA_TRY(mem.alloc(&P.suf, (size_t)(gdim + 1) * 2));
+    SMA_TRY(mem.alloc(&P.sweeps, 2));
+    SMA_TRY(mem.alloc(&P.ranks, 2));
+    SMA_TRY(mem.alloc(&P.off, 3));
+    SMA_TRY(mem.alloc(&P.orth, 2));
+    P.n_orth = (o.decomp == SMA_TUCKER_ROWCOL) ? 2 : 1;
+    if (o.decomp == SMA_TUCKER_BLOCKMODE) {
+      SMA_TRY(mem.alloc(&P.F1, (size_t)p * p));        // V (p x r)
+      SMA_TRY(mem.alloc(&P.D, mnp));                   // G_j slices (m x n x r)
+      SMA_TRY(mem.alloc(&P.C, (size_t)P.ell * P.q * p));
+      SMA_TRY(mem.alloc(&P.Gorth, (size_t)p * p));
+      P.nterms_max = p;
+    } else {
+      P.r1max = m;
+      P.r3max = (o.decomp == SMA_TUCKER_SHARED_U) ? m : n;
+      SMA_TRY(mem.alloc(&P.F1, (size_t)m * m));
+      SMA_TRY(mem.alloc(&P.F2, (size_t)n * n));
+      SMA_TRY(mem.alloc(&P.core, (size_t)P.r1max * P.r3max * p));
+      SMA_TRY(mem.alloc(&P.tmp, (size_t)(m > n ? m : n) * (m > n ? m : n) * p));
+      SMA_TRY(mem.alloc(&P.mid, (size_t)P.ell * P.r1max * P.q * P.r3max));
+      SMA_TRY(mem.alloc(&P.Gorth, (size_t)(m > n ? m : n) * (m > n ? m : n)));
+    }
+  }
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status make_T(sma_ctx* h, Prob<T>& P);
+
+// ---------------------------------------------------------------------------
+// step 1 (gather) shared by all decompositions
+// ---------------------------------------------------------------------------
+template <typename T>
+sma_status do_gather(sma_ctx* h, Prob<T>& P, const void* Ain, int64_t lda) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p;
+  const bool dense = h->opt.layout == SMA_INPUT_DENSE;
+  const int64_t need_rows = dense ? (int64_t)P.ell * m : m;
+  if (!Ain || lda < need_rows) return SMA_ERR_ARG;
+  const T* A = static_cast<const T*>(Ain);
+  stage_begin(h, SMA_STAGE_GATHER);
+  int64_t use_lda = lda;
+  int layout = dense ? 0 : 1;
+  if (!is_device_ptr(Ain)) {
+    // host input: copy only the p representative blocks to a staging buffer
+    if (!P.stage) SMA_TRY(h->mem.alloc(&P.stage, (size_t)m * n * p));
+    if (dense) {
+      for (int k = 0; k < p; ++k) {
+        const T* src = A + (int64_t)P.rep_a[k] * m + (int64_t)P.rep_b[k] * n * lda;
+        SMA_CK(cudaMemcpy2DAsync(P.stage + (size_t)k * m * n, m * sizeof(T), src, lda * sizeof(T),
+                                 m * sizeof(T), n, cudaMemcpyHostToDevice, st));
+      }
+    } else {
+      SMA_CK(cudaMemcpy2DAsync(P.stage, m * sizeof(T), A, lda * sizeof(T), m * sizeof(T),
+                               (size_t)n * p, cudaMemcpyHostToDevice, st));
+    }
+    A = P.stage;
+    use_lda = m;
+    layout = 1;
+  }
+  if (P.rep_lda != use_lda || P.rep_layout != layout) {
+    std::vector<int64_t> off(p);
+    for (int k = 0; k < p; ++k)
+      off[k] = layout == 0 ? (int64_t)P.rep_a[k] * m + (int64_t)P.rep_b[k] * n * use_lda
+                           : (int64_t)k * n * use_lda;
+    SMA_CK(cudaMemcpyAsync(P.d_rep, off.data(), p * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    SMA_CK(cudaStreamSynchronize(st));  // off[] is a stack buffer
+    P.rep_lda = use_lda;
+    P.rep_layout = layout;
+  }
+  SMA_K(gather<T, T>(A, use_lda, P.d_rep, P.d_w, m, n, p, P.X, P.partial, st));
+  SMA_K(finish_norm(P.partial, P.nparts, P.stats, st));
+  stage_end(h);
+  return SMA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// contraction dispatch: the mixed path sends large fp32 GEMMs to tcgen05
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t contract(sma_ctx* h, const GemmParams<T>& g) {
+  return gemm<T>(g, h->st);
+}
+template <>
+cudaError_t contract<float>(sma_ctx* h, const GemmParams<float>& g) {
+  if (h->tc_ok && tc_gemm_eligible(g)) return tc_gemm_bf16x3(g, h->st);
+  return gemm<float>(g, h->st);
+}
+
+// ---------------------------------------------------------------------------
+// t-SVDM (steps 2-5)
+// ---------------------------------------------------------------------------
+template <typename T>
+sma_status compress_tsvdm(sma_ctx* h, Prob<T>& P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p, mm = P.mm, rc = P.rc;
+  const int64_t mn = (int64_t)m * n;
+  // Xhat = X x3 M:  Xhat_mat (mn x p) = X_mat (mn x p) * M^T
+  stage_begin(h, SMA_STAGE_TRANSFORM);
+  {
+    GemmParams<T> g;
+    g.M = (int)mn; g.N = p; g.K = p;
+    g.A = P.X; g.a_rs = 1; g.a_cs = mn;
+    g.B = P.Mt; g.b_rs = p; g.b_cs = 1;
+    g.C = P.Xh; g.c_rs = 1; g.c_cs = mn;
+    SMA_K(contract<T>(h, g));
+  }
+  stage_end(h);
+  // per-slice SVD
+  stage_begin(h, SMA_STAGE_SVD);
+  {
+    JacobiParams<T> J;
+    J.src = P.Xh; J.src_bs = mn; J.m = m; J.n = n;
+    J.mm = mm; J.rc = rc; J.trans = P.jp.trans; J.ldS = P.jp.ldS; J.bcols = P.jp.bcols;
+    J.g = P.jp.g; J.sort_n = P.jp.sort_n;
+    J.max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
+    J.tol = 4.0 * std::sqrt((double)mm) * Eps<T>::v;
+    J.W = P.Wj; J.W_bs = (int64_t)(mm + rc) * rc;
+    J.U = P.U; J.U_bs = (int64_t)mm * rc;
+    J.V = P.V; J.V_bs = (int64_t)rc * rc;
+    J.sigma = P.sigma; J.sweeps = P.sweeps; J.status = P.status;
+    SMA_K(jacobi_svd<T>(J, p, P.jp.threads, P.jp.smem, st));
+  }
+  stage_end(h);
+  // truncation
+  stage_begin(h, SMA_STAGE_TRUNCATE);
+  SMA_K(truncate_ranks(P.sigma, rc, p, P.stats, h->opt.rel_tol, h->opt.fixed_rank, P.ranks, P.off,
+                        P.stats + 1, P.iscal, P.suf, st, 0));
+  stage_end(h);
+  stage_begin(h, SMA_STAGE_FACTORS);
+  // truncated slices: D_i = W_r V_r^T (W = U Sigma), or V_r W_r^T when the
+  // slice was processed transposed
+  const int64_t urc = (int64_t)mm * rc, vrc = (int64_t)rc * rc;
+  {
+    GemmParams<T> g;
+    g.M = m; g.N = n; g.K = rc; g.dK = P.ranks;
+    if (!P.jp.trans) {
+      g.A = P.U; g.a_rs = 1; g.a_cs = mm; g.a_b1 = urc;
+      g.B = P.V; g.b_rs = rc; g.b_cs = 1; g.b_b1 = vrc;
+    } else {
+      g.A = P.V; g.a_rs = 1; g.a_cs = rc; g.a_b1 = vrc;
+      g.B = P.U; g.b_rs = mm; g.b_cs = 1; g.b_b1 = urc;
+    }
+    g.C = P.D; g.c_rs = 1; g.c_cs = m; g.c_b1 = mn;
+    g.nb1 = p;
+    SMA_K(contract<T>(h, g));
+  }
+  // structured Kronecker factors C_i = struct_E(M[i, :])
+  SMA_K(build_struct_terms<T>(P.d_map, P.d_isq, P.ell, P.q, P.Mt, 1, p, p, nullptr, P.C, st));
+  stage_end(h);
+  // orthogonality of the retained left (or right) singular vectors
+  stage_begin(h, SMA_STAGE_REPORT);
+  {
+    GemmParams<T> g;
+    g.M = rc; g.N = rc; g.K = mm; g.dM = P.ranks; g.dN = P.ranks;
+    g.A = P.U; g.a_rs = mm; g.a_cs = 1; g.a_b1 = urc;
+    g.B = P.U; g.b_rs = 1; g.b_cs = mm; g.b_b1 = urc;
+    g.C = P.Gorth; g.c_rs = 1; g.c_cs = rc; g.c_b1 = (int64_t)rc * rc;
+    g.nb1 = p;
+    SMA_K(gemm<T>(g, st));
+    SMA_K(orth_defect<T>(P.Gorth, rc, p, P.ranks, P.sigma, P.orth, st));
+  }
+  stage_end(h);
+  return SMA_OK;
+}
+
+// Gram of an unfolding in fp64 followed by its Jacobi eigen-solve.
+// Y (rows x K) given by strides; result: gvec (rows x rows, sorted), gsig
+// (eigenvalues), rank written to ranks[slot] by the truncation kernel.
+template <typename T>
+sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_t y_rs,
+                       int64_t y_cs, int nb1, int64_t y_b1, double tol_share) {
+  cudaStream_t st = h->st;
+  double* G = P.gram + (size_t)slot * P.gstride;
+  stage_begin(h, SMA_STAGE_TRANSFORM);
+  {
+    GemmParams<double> g;
+    g.M = rows; g.N = rows; g.K = K;
+    g.A = P.X64; g.a_rs = y_rs; g.a_cs = y_cs; g.a_b1 = y_b1;
+    g.B = P.X64; g.b_rs = y_cs; g.b_cs = y_rs; g.b_b1 = y_b1;
+    g.C = G; g.c_rs = 1; g.c_cs = rows;
+    g.nb1 = 1;
+    if (nb1 > 1) {
+      // sum over batch entries (mode-1 / mode-2 unfoldings: sum_k X_k X_k^T)
+      for (int k = 0; k < nb1; ++k) {
+        GemmParams<double> gk = g;
+        gk.A = P.X64 + (int64_t)k * y_b1;
+        gk.B = P.X64 + (int64_t)k * y_b1;
+        gk.beta = (k == 0) ? 0.0 : 1.0;
+        SMA_K(gemm<double>(gk, st));
+      }
+    } else {
+      SMA_K(gemm<double>(g, st));
+    }
+  }
+  stage_end(h);
+  stage_begin(h, SMA_STAGE_SVD);
+  JacobiPlan jp = jacobi_plan<double>(rows, rows, h->max_smem);
+  double* W = jp.block_mode ? P.Wg : nullptr;
+  JacobiParams<double> J;
+  J.src = G; J.src_bs = 0; J.m = rows; J.n = rows;
+  J.mm = jp.mm; J.rc = jp.rc; J.trans = 0; J.ldS = jp.ldS; J.bcols = jp.bcols; J.g = jp.g;
+  J.sort_n = jp.sort_n;
+  J.max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
+  J.tol = 4.0 * std::sqrt((double)rows) * Eps<double>::v;
+  J.W = W; J.W_bs = 0;
+  J.U = P.gW; J.U_bs = 0;                                   // G V (not needed)
+  J.V = P.gvec + (size_t)slot * P.gstride; J.V_bs = 0;     // eigenvectors of G
+  J.sigma = P.gsig + (size_t)slot * P.gdim;
+  J.sweeps = P.sweeps + slot; J.status = P.status;
+  SMA_K(jacobi_svd<double>(J, 1, jp.threads, jp.smem, st));
+  stage_end(h);
+  stage_begin(h, SMA_STAGE_TRUNCATE);
+  // the Gram's singular values are the energies sigma^2 of the unfolding
+  SMA_K(truncate_ranks(P.gsig + (size_t)slot * P.gdim, rows, 1, P.stats, h->opt.rel_tol * tol_share,
+                        h->opt.fixed_rank, P.ranks + slot, P.off, P.stats + 2 + slot,
+                        P.iscal + 2 + slot, P.suf + (size_t)slot * (P.gdim + 1), st, 1));
+  stage_end(h);
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status compress_tucker(sma_ctx* h, Prob<T>& P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p;
+  const int64_t mn = (int64_t)m * n;
+  const sma_decomp d = h->opt.decomp;
+  SMA_K(convert<double, T>(P.X, P.X64, mn * p, st));
+  if (d == SMA_TUCKER_BLOCKMODE) {
+    // block-index unfolding: rows k, K = mn; Y(k, e) = X[e + mn k]
+    SMA_TRY(gram_factor(h, P, 0, p, (int)mn, mn, 1, 1, 0, 1.0));
+    stage_begin(h, SMA_STAGE_FACTORS);
+    SMA_K(convert<T, double>(P.gvec, P.F1, (int64_t)p * p, st));  // V = leading columns
+    // G = X x3 V^T: G_mat (mn x r) = X_mat (mn x p) V (p x r)
+    GemmParams<T> g;
+    g.M = (int)mn; g.N = p; g.K = p; g.dN = P.iscal + 2; g.dstride = 0;
+    g.A = P.X; g.a_rs = 1; g.a_cs = mn;
+    g.B = P.F1; g.b_rs = 1; g.b_cs = p;
+    g.C = P.D; g.c_rs = 1; g.c_cs = mn;
+    SMA_K(contract<T>(h, g));
+    // C_j = struct_E(V[:, j])
+    SMA_K(build_struct_terms<T>(P.d_map, P.d_isq, P.ell, P.q, P.F1, p, 1, p, P.iscal + 2, P.C, st));
+    // error ||X - T||_F measured directly (Lemma 1: equal to ||A - A_hat||_F)
+    SMA_TRY(make_T(h, P));
+    SMA_K(residual_norm2<T>(P.X, P.Tt, mn * p, P.partial, P.nparts, P.stats + 1, st));
+    stage_end(h);
+    // orthogonality of V_r
+    stage_begin(h, SMA_STAGE_REPORT);
+    GemmParams<T> go;
+    go.M = p; go.N = p; go.K = p; go.dM = P.iscal + 2; go.dN = P.iscal + 2; go.dstride = 0;
+    go.A = P.F1; go.a_rs = p; go.a_cs = 1;
+    go.B = P.F1; go.b_rs = 1; go.b_cs = p;
+    go.C = P.Gorth; go.c_rs = 1; go.c_cs = p;
+    SMA_K(gemm<T>(go, st));
+    SMA_K(orth_defect<T>(P.Gorth, p, 1, P.iscal + 2, nullptr, P.orth, st));
+    stage_end(h);
+    return SMA_OK;
+  }
+  // mode-1 unfolding [X_1 ... X_p] (m x np): Gram = sum_k X_k X_k^T
+  const int ntr = 2;  // two truncated modes share the budget
+  SMA_TRY(gram_factor(h, P, 0, m, (int)(mn * p / m), 1, m, 1, 0, 1.0 / std::sqrt((double)ntr)));
+  SMA_K(convert<T, double>(P.gvec, P.F1, (int64_t)m * m, st));
+  const int* r1 = P.iscal + 2;
+  const int* r3 = r1;
+  const T* Wf = P.F1;
+  int ldw = m;
+  if (d == SMA_TUCKER_ROWCOL) {
+    // mode-2 unfolding [X_1^T ... X_p^T] (n x mp): Gram = sum_k X_k^T X_k
+    SMA_TRY(gram_factor(h, P, 1, n, m, m, 1, p, mn, 1.0 / std::sqrt((double)ntr)));
+    SMA_K(convert<T, double>(P.gvec + P.gstride, P.F2, (int64_t)n * n, st));
+    r3 = P.iscal + 3;
+    Wf = P.F2;
+    ldw = n;
+  }
+  const int r1max = P.r1max, r3max = P.r3max;
+  stage_begin(h, SMA_STAGE_FACTORS);
+  SMA_CK(cudaMemsetAsync(P.core, 0, sizeof(T) * (size_t)r1max * r3max * p, st));
+  // tmp_k = U^T X_k (r1 x n)
+  GemmParams<T> g;
+  g.M = m; g.N = n; g.K = m; g.dM = r1; g.dstride = 0;
+  g.A = P.F1; g.a_rs = m; g.a_cs = 1;
+  g.B = P.X; g.b_rs = 1; g.b_cs = m; g.b_b1 = mn;
+  g.C = P.tmp; g.c_rs = 1; g.c_cs = m; g.c_b1 = (int64_t)m * n;
+  g.nb1 = p;
+  SMA_K(contract<T>(h, g));
+  // core_k = tmp_k W (r1 x r3), stored r1max x r3max per k
+  GemmParams<T> g2;
+  g2.M = m; g2.N = ldw; g2.K = n; g2.dM = r1; g2.dN = r3; g2.dstride = 0;
+  g2.A = P.tmp; g2.a_rs = 1; g2.a_cs = m; g2.a_b1 = (int64_t)m * n;
+  g2.B = Wf; g2.b_rs = 1; g2.b_cs = ldw;
+  g2.C = P.core; g2.c_rs = 1; g2.c_cs = r1max; g2.c_b1 = (int64_t)r1max * r3max;
+  g2.nb1 = p;
+  SMA_K(contract<T>(h, g2));
+  // middle factor struct_E(core_k), dense (ell r1max) x (q r3max)
+  SMA_K(scatter_ME<T>(P.d_map, P.d_isq, P.ell, P.q, r1max, r3max, P.core, P.mid,
+                       (int64_t)P.ell * r1max, st));
+  // error ||X - T||_F measured directly
+  SMA_TRY(make_T(h, P));
+  SMA_K(residual_norm2<T>(P.X, P.Tt, mn * p, P.partial, P.nparts, P.stats + 1, st));
+  stage_end(h);
+  // orthogonality of U (and W)
+  stage_begin(h, SMA_STAGE_REPORT);
+  for (int f = 0; f < P.n_orth; ++f) {
+    const T* F = f == 0 ? P.F1 : P.F2;
+    const int rows = f == 0 ? m : n;
+    GemmParams<T> go;
+    go.M = rows; go.N = rows; go.K = rows; go.dM = P.iscal + 2 + f; go.dN = P.iscal + 2 + f;
+    go.dstride = 0;
+    go.A = F; go.a_rs = rows; go.a_cs = 1;
+    go.B = F; go.b_rs = 1; go.b_cs = rows;
+    go.C = P.Gorth; go.c_rs = 1; go.c_cs = rows;
+    SMA_K(gemm<T>(go, st));
+    SMA_K(orth_defect<T>(P.Gorth, rows, 1, P.iscal + 2 + f, nullptr, P.orth + f, st));
+  }
+  stage_end(h);
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
+  SMA_CK(cudaMemsetAsync(P.status, 0, sizeof(int), h->st));
+  SMA_TRY(do_gather(h, P, A, lda));
+  if (h->opt.decomp == SMA_TSVDM) SMA_TRY(compress_tsvdm(h, P));
+  else SMA_TRY(compress_tucker(h, P));
+  P.compressed = true;
+  P.h_iscal[0] = -1;
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status read_result(sma_ctx* h, Prob<T>& P, sma_result* r) {
+  SMA_CK(cudaStreamSynchronize(h->st));
+  double stats[8];
+  int iscal[8];
+  int status = 0;
+  SMA_CK(cudaMemcpy(stats, P.stats, sizeof(stats), cudaMemcpyDeviceToHost));
+  SMA_CK(cudaMemcpy(iscal, P.iscal, sizeof(iscal), cudaMemcpyDeviceToHost));
+  SMA_CK(cudaMemcpy(&status, P.status, sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<double> orth(P.n_orth);
+  SMA_CK(cudaMemcpy(orth.data(), P.orth, P.n_orth * sizeof(double), cudaMemcpyDeviceToHost));
+  const int nsw = h->opt.decomp == SMA_TSVDM ? P.p : P.n_orth;
+  std::vector<int> sw(nsw);
+  SMA_CK(cudaMemcpy(sw.data(), P.sweeps, nsw * sizeof(int), cudaMemcpyDeviceToHost));
+  memcpy(P.h_iscal, iscal, sizeof(iscal));
+  std::memset(r, 0, sizeof(*r));
+  r->norm = std::sqrt(stats[0]);
+  r->device_status = status;
+  r->orth_defect = 0.0;
+  for (double v : orth) r->orth_defect = std::fmax(r->orth_defect, v);
+  r->sweeps_max = 0;
+  for (int v : sw) r->sweeps_max = v > r->sweeps_max ? v : r->sweeps_max;
+  const sma_decomp d = h->opt.decomp;
+  double err2 = 0.0;
+  if (d == SMA_TSVDM) {
+    err2 = stats[1];
+    r->total_rank = iscal[0];
+    r->n_kron_terms = iscal[1];
+  } else if (d == SMA_TUCKER_BLOCKMODE) {
+    err2 = stats[1];
+    r->ranks[0] = iscal[2];
+    r->total_rank = iscal[2];
+    r->n_kron_terms = iscal[2];
+  } else {
+    r->ranks[0] = iscal[2];
+    r->ranks[1] = d == SMA_TUCKER_ROWCOL ? iscal[3] : iscal[2];
+    r->total_rank = r->ranks[0] * r->ranks[1];
+    r->n_kron_terms = 0;
+    err2 = stats[1];
+  }
+  r->tensor_err = std::sqrt(std::fmax(err2, 0.0));
+  r->rel_err = stats[0] > 0 ? r->tensor_err / r->norm : 0.0;
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status compress_all(sma_ctx* h, const void* const* A, const int64_t* lda, sma_result* res) {
+  auto& ps = probs<T>(h);
+  for (int i = 0; i < h->nprob; ++i) SMA_TRY(compress_one(h, ps[i], A[i], lda[i]));
+  if (res) {
+    sma_status worst = SMA_OK;
+    for (int i = 0; i < h->nprob; ++i) {
+      SMA_TRY(read_result(h, ps[i], &res[i]));
+      const int ds = res[i].device_status;
+      if (ds & SMA_STATUS_BIT(SMA_ERR_NONFINITE)) worst = SMA_ERR_NONFINITE;
+      else if ((ds & SMA_STATUS_BIT(SMA_ERR_NOCONVERGE)) && worst == SMA_OK) worst = SMA_ERR_NOCONVERGE;
+    }
+    return worst;
+  }
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status grow(sma_ctx* h, T** buf, size_t* have, size_t need) {
+  if (*have >= need) return SMA_OK;
+  if (*buf) h->mem.release(*buf);
+  *buf = nullptr;
+  *have = 0;
+  SMA_TRY(h->mem.alloc(buf, need));
+  *have = need;
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status apply_one(sma_ctx* h, Prob<T>& P, const void* Xin, int64_t ldx, void* Yout,
+                     int64_t ldy, int nrhs) {
+  if (!P.compressed) return SMA_ERR_STATE;
+  if (nrhs <= 0 || !Xin || !Yout) return SMA_ERR_ARG;
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, ell = P.ell, q = P.q;
+  const int64_t xrows = (int64_t)q * n, yrows = (int64_t)ell * m;
+  if (ldx < xrows || ldy < yrows) return SMA_ERR_ARG;
+  const T* X = static_cast<const T*>(Xin);
+  T* Y = static_cast<T*>(Yout);
+  const bool xhost = !is_device_ptr(Xin), yhost = !is_device_ptr(Yout);
+  if (xhost) {
+    SMA_TRY(grow(h, &P.Xs, &P.Xs_elems, (size_t)xrows * nrhs));
+    SMA_CK(cudaMemcpy2DAsync(P.Xs, xrows * sizeof(T), X, ldx * sizeof(T), xrows * sizeof(T), nrhs,
+                             cudaMemcpyHostToDevice, st));
+    X = P.Xs;
+    ldx = xrows;
+  }
+  T* Yd = Y;
+  int64_t ldyd = ldy;
+  if (yhost) {
+    SMA_TRY(grow(h, &P.Ys, &P.Ys_elems, (size_t)yrows * nrhs));
+    Yd = P.Ys;
+    ldyd = yrows;
+  }
+  const sma_decomp d = h->opt.decomp;
+  stage_begin(h, SMA_STAGE_APPLY);
+  if (d == SMA_TSVDM || d == SMA_TUCKER_BLOCKMODE) {
+    // Kronecker sum Y = sum_j D_j X C_j^T (Section 2.2 vec identity).
+    if (P.h_iscal[0] < 0) {
+      SMA_CK(cudaStreamSynchronize(st));
+      SMA_CK(cudaMemcpy(P.h_iscal, P.iscal, sizeof(P.h_iscal), cudaMemcpyDeviceToHost));
+    }
+    // t-SVDM: one term per slice (rank-0 slices have D_i = 0);
+    // Tucker-1: the r2 retained block-mode columns.
+    const int nt = d == SMA_TSVDM ? P.nterms_max : P.h_iscal[2];
+    if (nt <= 0) {
+      if (ldyd == yrows) SMA_CK(cudaMemsetAsync(Yd, 0, sizeof(T) * (size_t)yrows * nrhs, st));
+      else SMA_CK(cudaMemset2DAsync(Yd, ldyd * sizeof(T), 0, yrows * sizeof(T), nrhs, st));
+      goto done;
+    }
+    const int64_t ldZ = (int64_t)n * nt;
+    SMA_TRY(grow(h, &P.Z, &P.Z_elems, (size_t)ldZ * ell * nrhs));
+    // Z[c + n j, a + ell s] = sum_b X_s[c, b] C_j[a, b]
+    GemmParams<T> g;
+    g.M = n; g.N = ell; g.K = q;
+    g.A = X; g.a_rs = 1; g.a_cs = n; g.a_b2 = ldx;
+    g.B = P.C; g.b_rs = ell; g.b_cs = 1; g.b_b1 = (int64_t)ell * q;
+    g.C = P.Z; g.c_rs = 1; g.c_cs = ldZ; g.c_b1 = n; g.c_b2 = ldZ * ell;
+    g.nb1 = nt; g.nb2 = nrhs;
+    SMA_K(gemm<T>(g, st));
+    // Y = [D_1 | ... | D_nt] Z   (m x (ell nrhs), K = n nt)
+    GemmParams<T> g2;
+    g2.M = m; g2.K = (int)ldZ;
+    g2.A = P.D; g2.a_rs = 1; g2.a_cs = m;
+    g2.B = P.Z; g2.b_rs = 1; g2.b_cs = ldZ;
+    if (ldyd == yrows) {
+      g2.N = ell * nrhs;
+      g2.C = Yd; g2.c_rs = 1; g2.c_cs = m;
+    } else {
+      g2.N = ell; g2.nb2 = nrhs; g2.b_b2 = ldZ * ell;
+      g2.C = Yd; g2.c_rs = 1; g2.c_cs = m; g2.c_b2 = ldyd;
+    }
+    SMA_K(contract<T>(h, g2));
+  } else {
+    // block low rank Y = (I (x) U) struct_E(F_k) (I (x) W^T) X
+    const int r1max = P.r1max, r3max = P.r3max;
+    const T* Wf = d == SMA_TUCKER_ROWCOL ? P.F2 : P.F1;
+    SMA_TRY(grow(h, &P.Z, &P.Z_elems, (size_t)q * r3max * nrhs));
+    SMA_TRY(grow(h, &P.Z2, &P.Z2_elems, (size_t)ell * r1max * nrhs));
+    // Z[:, b + q s] = W^T X_s[:, b]   (r3max x q nrhs, zero rows beyond r3)
+    GemmParams<T> g;
+    g.M = r3max; g.N = q; g.K = n;
+    g.A = Wf; g.a_rs = n; g.a_cs = 1;
+    g.B = X; g.b_rs = 1; g.b_cs = n; g.b_b2 = ldx;
+    g.C = P.Z; g.c_rs = 1; g.c_cs = r3max; g.c_b2 = (int64_t)r3max * q;
+    g.nb2 = nrhs;
+    SMA_K(contract<T>(h, g));
+    // Z2 = mid Z   ((ell r1max) x nrhs)
+    GemmParams<T> g2;
+    g2.M = ell * r1max; g2.N = nrhs; g2.K = q * r3max;
+    g2.A = P.mid; g2.a_rs = 1; g2.a_cs = (int64_t)ell * r1max;
+    g2.B = P.Z; g2.b_rs = 1; g2.b_cs = (int64_t)q * r3max;
+    g2.C = P.Z2; g2.c_rs = 1; g2.c_cs = (int64_t)ell * r1max;
+    SMA_K(contract<T>(h, g2));
+    // Y_s[:, a] = U Z2_s[:, a]
+    GemmParams<T> g3;
+    g3.M = m; g3.N = ell; g3.K = r1max;
+    g3.A = P.F1; g3.a_rs = 1; g3.a_cs = m;
+    g3.B = P.Z2; g3.b_rs = 1; g3.b_cs = r1max; g3.b_b2 = (int64_t)ell * r1max;
+    g3.C = Yd; g3.c_rs = 1; g3.c_cs = m; g3.c_b2 = ldyd;
+    g3.nb2 = nrhs;
+    SMA_K(contract<T>(h, g3));
+  }
+done:
+  stage_end(h);
+  if (yhost) {
+    SMA_CK(cudaMemcpy2DAsync(Y, ldy * sizeof(T), Yd, yrows * sizeof(T), yrows * sizeof(T), nrhs,
+                             cudaMemcpyDeviceToHost, st));
+    SMA_CK(cudaStreamSynchronize(st));
+  }
+  return SMA_OK;
+}
+
+// The approximation tensor T (m x n x p) in P.Tt from the factors.
+template <typename T>
+sma_status make_T(sma_ctx* h, Prob<T>& P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p;
+  const int64_t mn = (int64_t)m * n;
+  const sma_decomp d = h->opt.decomp;
+  if (d == SMA_TSVDM) {
+    // T = Dtrunc x3 M^T: T_mat = D_mat M
+    GemmParams<T> g;
+    g.M = (int)mn; g.N = p; g.K = p;
+    g.A = P.D; g.a_rs = 1; g.a_cs = mn;
+    g.B = P.Mt; g.b_rs = 1; g.b_cs = p;
+    g.C = P.Tt; g.c_rs = 1; g.c_cs = mn;
+    SMA_K(gemm<T>(g, st));
+  } else if (d == SMA_TUCKER_BLOCKMODE) {
+    // T = G x3 V: T_mat = G_mat V^T
+    GemmParams<T> g;
+    g.M = (int)mn; g.N = p; g.K = p; g.dK = P.iscal + 2; g.dstride = 0;
+    g.A = P.D; g.a_rs = 1; g.a_cs = mn;
+    g.B = P.F1; g.b_rs = p; g.b_cs = 1;
+    g.C = P.Tt; g.c_rs = 1; g.c_cs = mn;
+    SMA_K(gemm<T>(g, st));
+  } else {
+    const T* Wf = d == SMA_TUCKER_ROWCOL ? P.F2 : P.F1;
+    const int* r1 = P.iscal + 2;
+    const int* r3 = d == SMA_TUCKER_ROWCOL ? P.iscal + 3 : P.iscal + 2;
+    // tmp_k = U core_k  (m x r3), T_k = tmp_k W^T
+    GemmParams<T> g;
+    g.M = m; g.N = P.r3max; g.K = P.r1max; g.dN = r3; g.dK = r1; g.dstride = 0;
+    g.A = P.F1; g.a_rs = 1; g.a_cs = m;
+    g.B = P.core; g.b_rs = 1; g.b_cs = P.r1max; g.b_b1 = (int64_t)P.r1max * P.r3max;
+    g.C = P.tmp; g.c_rs = 1; g.c_cs = m; g.c_b1 = (int64_t)m * P.r3max;
+    g.nb1 = p;
+    SMA_K(gemm<T>(g, st));
+    GemmParams<T> g2;
+    g2.M = m; g2.N = n; g2.K = P.r3max; g2.dK = r3; g2.dstride = 0;
+    g2.A = P.tmp; g2.a_rs = 1; g2.a_cs = m; g2.a_b1 = (int64_t)m * P.r3max;
+    g2.B = Wf; g2.b_rs = n; g2.b_cs = 1;
+    g2.C = P.Tt; g2.c_rs = 1; g2.c_cs = m; g2.c_b1 = mn;
+    g2.nb1 = p;
+    SMA_K(gemm<T>(g2, st));
+  }
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status reconstruct_one(sma_ctx* h, Prob<T>& P, void* Ahat, int64_t ld) {
+  if (!P.compressed) return SMA_ERR_STATE;
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p;
+  const int64_t mn = (int64_t)m * n;
+  const sma_decomp d = h->opt.decomp;
+  if (!Ahat || ld < (int64_t)P.ell * m) return SMA_ERR_ARG;
+  SMA_TRY(make_T(h, P));
+  T* dst = static_cast<T*>(Ahat);
+  const bool host = !is_device_ptr(Ahat);
+  const int64_t rows = (int64_t)P.ell * m, cols = (int64_t)P.q * n;
+  T* tmpA = nullptr;
+  if (host) {
+    if (cudaMalloc(&tmpA, rows * cols * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return SMA_ERR_ALLOC;
+    }
+  }
+  ++h->launches;
+  cudaError_t e = scatter_ME<T>(P.d_map, P.d_isq, P.ell, P.q, m, n, P.Tt, host ? tmpA : dst,
+                                host ? rows : ld, st);
+  if (e == cudaSuccess && host) {
+    e = cudaMemcpy2DAsync(dst, ld * sizeof(T), tmpA, rows * sizeof(T), rows * sizeof(T), cols,
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (tmpA) cudaFree(tmpA);
+  SMA_CK(e);
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status export_one(sma_ctx* h, Prob<T>& P, int which, void* dst, int64_t count,
+                      int64_t* avail) {
+  const void* src = nullptr;
+  int64_t n = 0;
+  size_t es = sizeof(T);
+  const int64_t mnp = (int64_t)P.m * P.n * P.p;
+  switch (which) {
+    case 0: src = P.X; n = mnp; break;
+    case 1: src = P.Xh; n = P.Xh ? mnp : 0; break;
+    case 2:
+      if (h->opt.decomp == SMA_TSVDM) { src = P.sigma; n = (int64_t)P.rc * P.p; }
+      else { src = P.gsig; n = h->opt.decomp == SMA_TUCKER_BLOCKMODE ? P.p : P.m; }
+      es = sizeof(double);
+      break;
+    case 3: src = P.Tt; n = mnp; break;
+    case 4:
+      if (h->opt.decomp == SMA_TUCKER_BLOCKMODE) { src = P.F1; n = (int64_t)P.p * P.p; }
+      else if (h->opt.decomp != SMA_TSVDM) { src = P.F1; n = (int64_t)P.m * P.m; }
+      break;
+    default: return SMA_ERR_ARG;
+  }
+  if (avail) *avail = n;
+  if (count <= 0) return SMA_OK;
+  if (!src || !dst || count > n) return SMA_ERR_ARG;
+  SMA_CK(cudaStreamSynchronize(h->st));
+  SMA_CK(cudaMemcpy(dst, src, count * es, cudaMemcpyDefault));
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status ranks_one(sma_ctx* h, Prob<T>& P, int32_t* out, int32_t* count) {
+  SMA_CK(cudaStreamSynchronize(h->st));
+  if (h->opt.decomp == SMA_TSVDM) {
+    SMA_CK(cudaMemcpy(out, P.ranks, P.p * sizeof(int), cudaMemcpyDeviceToHost));
+    *count = P.p;
+  } else {
+    int isc[8];
+    SMA_CK(cudaMemcpy(isc, P.iscal, sizeof(isc), cudaMemcpyDeviceToHost));
+    const sma_decomp d = h->opt.decomp;
+    const int c = d == SMA_TUCKER_BLOCKMODE ? 1 : 2;
+    for (int i = 0; i < c; ++i) out[i] = (d == SMA_TUCKER_SHARED_U) ? isc[2] : isc[2 + i];
+    *count = c;
+  }
+  return SMA_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported C ABI
+// ===========================================================================
+extern "C" {
+
+const char* sma_version(void) { return "sma 0.1 (sm_103a)"; }
+
+const char* sma_status_string(sma_status s) {
+  switch (s) {
+    case SMA_OK: return "ok";
+    case SMA_ERR_ARG: return "invalid argument";
+    case SMA_ERR_STRUCT: return "invalid structure map";
+    case SMA_ERR_CUDA: return "CUDA error";
+    case SMA_ERR_ALLOC: return "device allocation failed";
+    case SMA_ERR_NOCONVERGE: return "Jacobi sweep limit reached";
+    case SMA_ERR_TIMEOUT: return "device wait timed out";
+    case SMA_ERR_NONFINITE: return "non-finite value";
+    case SMA_ERR_STATE: return "call out of order";
+    case SMA_ERR_UNSUPPORTED: return "unsupported option";
+  }
+  return "unknown status";
+}
+
+sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
+                      const sma_options* opt) {
+  if (!out) return SMA_ERR_ARG;
+  *out = nullptr;
+  if (!prob || !opt || nprob < 1) return SMA_ERR_ARG;
+  if (opt->prec != SMA_FP64 && opt->prec != SMA_MIXED) return SMA_ERR_ARG;
+  if ((int)opt->decomp < 0 || opt->decomp > SMA_HOSVD_MULTILEVEL) return SMA_ERR_ARG;
+  if ((int)opt->mkind < 0 || opt->mkind > SMA_M_USER) return SMA_ERR_ARG;
+  if (opt->layout != SMA_INPUT_DENSE && opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
+  if (opt->fixed_rank < 0 || !(opt->rel_tol >= 0.0)) return SMA_ERR_ARG;
+  if (opt->decomp == SMA_HOSVD_MULTILEVEL) return SMA_ERR_UNSUPPORTED;
+  // host-side validation of every problem before any CUDA call
+  for (int i = 0; i < nprob; ++i) {
+    std::vector<int64_t> eta;
+    std::vector<int> ra, rb;
+    SMA_TRY(validate_problem(prob[i], eta, ra, rb));
+    if (opt->decomp == SMA_TUCKER_SHARED_U && prob[i].m != prob[i].n) return SMA_ERR_ARG;
+    if (opt->decomp == SMA_TSVDM && opt->mkind == SMA_M_USER && !opt->M_user) return SMA_ERR_ARG;
+  }
+  std::unique_ptr<sma_ctx> h(new (std::nothrow) sma_ctx());
+  if (!h) return SMA_ERR_ALLOC;
+  h->opt = *opt;
+  h->st = static_cast<cudaStream_t>(opt->stream);
+  h->prof = opt->profile != 0;
+  h->nprob = nprob;
+  int dev = 0;
+  SMA_CK(cudaGetDevice(&dev));
+  SMA_CK(cudaDeviceGetAttribute(&h->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int major = 0, minor = 0;
+  SMA_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  SMA_CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+  h->tc_ok = (opt->prec == SMA_MIXED) && tc_gemm_available(major, minor);
+  if (opt->prec == SMA_FP64) {
+    h->p64.resize(nprob);
+    for (int i = 0; i < nprob; ++i) SMA_TRY(setup_problem(h.get(), h->p64[i], prob[i]));
+  } else {
+    h->p32.resize(nprob);
+    for (int i = 0; i < nprob; ++i) SMA_TRY(setup_problem(h.get(), h->p32[i], prob[i]));
+  }
+  *out = h.release();
+  return SMA_OK;
+}
+
+sma_status sma_compress(sma_handle h, const void* const* A, const int64_t* lda, sma_result* res) {
+  if (!h || !A || !lda) return SMA_ERR_ARG;
+  if (h->opt.prec == SMA_FP64) return compress_all<double>(h, A, lda, res);
+  return compress_all<float>(h, A, lda, res);
+}
+
+sma_status sma_get_result(sma_handle h, int32_t i, sma_result* res) {
+  if (!h || !res || i < 0 || i >= h->nprob) return SMA_ERR_ARG;
+  if (h->opt.prec == SMA_FP64) {
+    if (!h->p64[i].compressed) return SMA_ERR_STATE;
+    return read_result(h, h->p64[i], res);
+  }
+  if (!h->p32[i].compressed) return SMA_ERR_STATE;
+  return read_result(h, h->p32[i], res);
+}
+
+sma_status sma_get_ranks(sma_handle h, int32_t i, int32_t* ranks, int32_t* count) {
+  if (!h || !ranks || !count || i < 0 || i >= h->nprob) return SMA_ERR_ARG;
+  if (h->opt.prec == SMA_FP64) return ranks_one(h, h->p64[i], ranks, count);
+  return ranks_one(h, h->p32[i], ranks, count);
+}
+
+sma_status sma_reconstruct(sma_handle h, int32_t i, void* Ahat, int64_t ld) {
+  if (!h || i < 0 || i >= h->nprob) return SMA_ERR_ARG;
+  if (h->opt.prec == SMA_FP64) return reconstruct_one(h, h->p64[i], Ahat, ld);
+  return reconstruct_one(h, h->p32[i], Ahat, ld);
+}
+
+sma_status sma_apply(sma_handle h, int32_t i, const void* X, int64_t ldx, void* Y, int64_t ldy,
+                     int32_t nrhs) {
+  if (!h || i < 0 || i >= h->nprob) return SMA_ERR_ARG;
+  if (h->opt.prec == SMA_FP64) return apply_one(h, h->p64[i], X, ldx, Y, ldy, nrhs);
+  return apply_one(h, h->p32[i], X, ldx, Y, ldy, nrhs);
+}
+
+sma_status sma_export(sma_handle h, int32_t i, int32_t which, void* dst, int64_t count,
+                      int64_t* avail) {
+  if (!h || i < 0 || i >= h->nprob) return SMA_ERR_ARG;
+  if (h->opt.prec == SMA_FP64) return export_one(h, h->p64[i], which, dst, count, avail);
+  return export_one(h, h->p32[i], which, dst, count, avail);
+}
+
+sma_status sma_profile(sma_handle h, double* ms, int64_t* calls, int64_t* launches,
+                       int32_t reset) {
+  if (!h) return SMA_ERR_ARG;
+  if (!h->prof) return SMA_ERR_STATE;
+  SMA_CK(cudaStreamSynchronize(h->st));
+  for (auto& pe : h->pend) {
+    float t = 0.f;
+    SMA_CK(cudaEventElapsedTime(&t, pe.a, pe.b));
+    h->acc_ms[pe.stage] += t;
+    h->acc_calls[pe.stage] += 1;
+    h->ev_free.push_back(pe.a);
+    h->ev_free.push_back(pe.b);
+  }
+  h->pend.clear();
+  for (int s = 0; s < SMA_STAGE_COUNT; ++s) {
+    if (ms) ms[s] = h->acc_ms[s];
+    if (calls) calls[s] = h->acc_calls[s];
+  }
+  if (launches) *launches = h->launches;
+  if (reset) {
+    for (int s = 0; s < SMA_STAGE_COUNT; ++s) {
+      h->acc_ms[s] = 0.0;
+      h->acc_calls[s] = 0;
+    }
+    h->launches = 0;
+  }
+  return SMA_OK;
+}
+
+sma_status sma_destroy(sma_handle h) {
+  if (!h) return SMA_ERR_ARG;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  delete h;
+  return SMA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Kernel parameter blocks and launchers of the sma path (host side).
+#pragma once
+#include "common.cuh"
+
+namespace sma {
+
+// ---- step 1: struct_E gather --------------------------------------------
+// X[:, :, k] = w[k] * A_rep(k); rep_row/rep_col give the element offset of
+// the representative block (dense layout: row a*m, col b*n; blocks layout:
+// row 0, col k*n).  Source may be fp64 or fp32 (TS), output T.
+template <typename TS, typename T>
+cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off /*device, p*/,
+                   const double* w /*device, p*/, int m, int n, int p, T* X,
+                   double* partial /*device, >= 1024*/, cudaStream_t st);
+// ||X||_F^2 from the per-CTA partial sums written by gather.
+cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStream_t st);
+int gather_parts(int m, int n, int p);
+// ||X - T||_F^2 over `count` elements (fp64 accumulation; nparts partial sums
+// as for gather); two launches.
+template <typename T>
+cudaError_t residual_norm2(const T* X, const T* Tt, int64_t count, double* partial, int nparts,
+                           double* out, cudaStream_t st);
+
+// ---- step 3: Jacobi SVD ---------------------------------------------------
+template <typename T>
+struct JacobiParams {
+  const T* src = nullptr; int64_t src_bs = 0;   // slices m x n, ld m
+  int m = 0, n = 0;
+  int mm = 0, rc = 0, trans = 0, ldS = 0, bcols = 0, g = 1, sort_n = 1;
+  int max_sweeps = 30;
+  double tol = 0.0;
+  T* W = nullptr; int64_t W_bs = 0;             // block-mode workspace ((mm+rc) x rc per slice)
+  T* U = nullptr; int64_t U_bs = 0;             // out: W = U Sigma, mm x rc per slice (sorted)
+  T* V = nullptr; int64_t V_bs = 0;             // out: V, rc x rc per slice (sorted)
+  double* sigma = nullptr;                      // out: rc per slice, descending
+  int* sweeps = nullptr;                        // out: per slice
+  int* status = nullptr;                        // status bits (atomicOr)
+};
+struct JacobiPlan {
+  int trans, mm, rc, ldS, bcols, sort_n, threads, g, block_mode;
+  size_t smem;
+};
+template <typename T> JacobiPlan jacobi_plan(int m, int n, int max_smem);
+template <typename T>
+cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_t smem,
+                       cudaStream_t st);
+
+// ---- step 4: truncation ---------------------------------------------------
+// sigma: rc x p (descending per slice).  Tolerance rule when fixed_rank <= 0.
+// energies != 0: sigma holds energies (Gram eigenvalues) instead.
+// Writes ranks[p], off[p+1] (exclusive prefix), stats[1] = discarded energy,
+// iscal[0] = total rank, iscal[1] = #slices with rank > 0.
+cudaError_t truncate_ranks(const double* sigma, int rc, int p, const double* normX2,
+                           double rel_tol, int fixed_rank, int* ranks, int* off,
+                           double* err2, int* iscal, double* scratch /*(rc+1)*p*/,
+                           cudaStream_t st, int energies = 0);
+
+// ---- helpers of steps 3-5 ------------------------------------------------
+// C_i = struct_E(coef[i, :]) for i < nterms: C[a + ell*b + ell*q*i] =
+// coef[i*cs_i + k*cs_k] / sqrt(eta_k) with k = map(a, b) (0 if k < 0).
+template <typename T>
+cudaError_t build_struct_terms(const int* map, const double* inv_sqrt_eta, int ell, int q,
+                               const T* coef, int64_t cs_i, int64_t cs_k, int nterms,
+                               const int* nterms_dev, T* C, cudaStream_t st);
+// Ahat (ell*m x q*n, ld) = M_E[T]: block (a,b) = T[:,:,k] / sqrt(eta_k).
+template <typename T>
+cudaError_t scatter_ME(const int* map, const double* inv_sqrt_eta, int ell, int q, int m,
+                       int n, const T* Tt, T* Ahat, int64_t ld, cudaStream_t st);
+// max |G_i[a,b] / (s_a s_b) - delta_ab| over the leading r_i x r_i block of
+// each of p Gram matrices (s = per-slice scales, rc per slice; NULL = 1).
+template <typename T>
+cudaError_t orth_defect(const T* Gm, int rc, int p, const int* ranks, const double* scale,
+                        double* out, cudaStream_t st);
+// copy and precision conversion helpers
+template <typename TD, typename TS>
+cudaError_t convert(const TS* src, TD* dst, int64_t count, cudaStream_t st);
+
+}  // namespace sma

@@ -1,0 +1,388 @@
+// Bandwidth-bound steps of the path: the struct_E gather (Section 3,
+// matrix-to-tensor map), the global truncation rule, the construction of the
+// structured Kronecker factors C_j = struct_E(v_j) (Theorem 'tuckerkron'),
+// the tensor-to-matrix scatter M_E used for validation, and reports.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sma {
+namespace {
+
+constexpr int GATHER_THREADS = 256;
+constexpr int GATHER_MAX_CTAS = 152 * 8;
+
+// X[r, c, k] = w[k] * A[rep_off[k] + r + c*lda]; per-CTA fp64 sum of X^2.
+template <typename TS, typename T>
+__global__ void __launch_bounds__(GATHER_THREADS)
+gather_kernel(const TS* __restrict__ A, int64_t lda, const int64_t* __restrict__ rep_off,
+              const double* __restrict__ w, int m, int n, int p, T* __restrict__ X,
+              double* __restrict__ partial) {
+  __shared__ double red[32];
+  const int64_t slice = (int64_t)m * n;
+  const int64_t total = slice * p;
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / slice);
+    const int64_t rem = e - (int64_t)k * slice;
+    const int c = (int)(rem / m);
+    const int r = (int)(rem - (int64_t)c * m);
+    const double v = (double)A[rep_off[k] + r + (int64_t)c * lda] * w[k];
+    const T tv = (T)v;
+    X[e] = tv;
+    acc = fma((double)tv, (double)tv, acc);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// per-CTA fp64 sums of (X - T)^2
+template <typename T>
+__global__ void __launch_bounds__(GATHER_THREADS)
+residual_kernel(const T* __restrict__ X, const T* __restrict__ Tt, int64_t count,
+                double* __restrict__ partial) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double d = (double)X[e] - (double)Tt[e];
+    acc = fma(d, d, acc);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void finish_norm_kernel(const double* partial, int nparts, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += partial[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Global truncation (one CTA).  sigma is rc x p, descending per slice.
+// Tolerance rule: discard the longest prefix of all values taken in
+// ascending order (ties: higher slice first, then higher index) whose energy
+// sum stays <= budget.  F(v) = energy of all values <= v is monotone; the
+// largest attained value v* with F(v*) <= budget is found by bisection over
+// the bit patterns of non-negative doubles, then ties at the next value are
+// split in the order above.
+// ---------------------------------------------------------------------------
+constexpr int TR_THREADS = 1024;
+
+__device__ __forceinline__ int count_greater(const double* s, int rc, double v) {
+  // number of leading entries (descending array) strictly greater than v
+  int lo = 0, hi = rc;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (s[mid] > v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(TR_THREADS)
+truncate_kernel(const double* __restrict__ sigma, int rc, int p, const double* normX2,
+                double rel_tol, int fixed_rank, int* ranks, int* off, double* err2,
+                int* iscal, double* suf, int energies) {
+  __shared__ double red[32];
+  __shared__ unsigned long long s_lo, s_hi;
+  const int tid = threadIdx.x;
+  // suffix energies E_i[j] = sum_{j' >= j} sigma_ij'^2, E_i[rc] = 0
+  for (int i = tid; i < p; i += blockDim.x) {
+    const double* s = sigma + (int64_t)i * rc;
+    double* E = suf + (int64_t)i * (rc + 1);
+    double acc = 0.0;
+    E[rc] = 0.0;
+    for (int j = rc - 1; j >= 0; --j) {
+      acc += energies ? fmax(s[j], 0.0) : s[j] * s[j];
+      E[j] = acc;
+    }
+  }
+  __syncthreads();
+  if (fixed_rank > 0) {
+    double disc = 0.0;
+    for (int i = tid; i < p; i += blockDim.x) {
+      const int r = min(fixed_rank, rc);
+      ranks[i] = r;
+      disc += suf[(int64_t)i * (rc + 1) + r];
+    }
+    disc = block_sum(disc, red);
+    if (tid == 0) *err2 = disc;
+  } else {
+    const double budget = rel_tol * rel_tol * (*normX2);
+    // largest sigma overall (bisection upper bound)
+    double mx = 0.0;
+    for (int i = tid; i < p; i += blockDim.x) mx = fmax(mx, sigma[(int64_t)i * rc]);
+    __shared__ double smax[32];
+    {
+      double v = warp_max(mx);
+      if ((tid & 31) == 0) smax[tid >> 5] = v;
+      __syncthreads();
+      if (tid < 32) {
+        double t = (tid < (int)(blockDim.x >> 5)) ? smax[tid] : 0.0;
+        t = warp_max(t);
+        if (tid == 0) smax[0] = t;
+      }
+      __syncthreads();
+      mx = smax[0];
+      __syncthreads();
+    }
+    if (tid == 0) {
+      s_lo = 0ull;  // F(0) = 0 <= budget (all sigma >= 0)
+      s_hi = (unsigned long long)__double_as_longlong(mx);
+    }
+    __syncthreads();
+    // invariant: F(lo) <= budget; find the largest bits in [lo, hi] with F <= budget
+    for (int it = 0; it < 70; ++it) {
+      const unsigned long long lo = s_lo, hi = s_hi;
+      if (lo >= hi) break;
+      const unsigned long long mid = lo + (hi - lo + 1) / 2;
+      const double v = __longlong_as_double((long long)mid);
+      double F = 0.0;
+      for (int i = tid; i < p; i += blockDim.x) {
+        const double* s = sigma + (int64_t)i * rc;
+        F += suf[(int64_t)i * (rc + 1) + count_greater(s, rc, v)];
+      }
+      F = block_sum(F, red);
+      if (tid == 0) {
+        if (F <= budget) s_lo = mid; else s_hi = mid - 1;
+      }
+      __syncthreads();
+    }
+    const double vstar = __longlong_as_double((long long)s_lo);
+    // ranks before tie handling, F(v*), next larger value
+    double F = 0.0, vnext = INFINITY;
+    for (int i = tid; i < p; i += blockDim.x) {
+      const double* s = sigma + (int64_t)i * rc;
+      const int cg = count_greater(s, rc, vstar);
+      ranks[i] = cg;
+      F += suf[(int64_t)i * (rc + 1) + cg];
+      if (cg > 0) vnext = fmin(vnext, s[cg - 1]);
+    }
+    F = block_sum(F, red);
+    {
+      double v = -warp_max(-vnext);
+      if ((tid & 31) == 0) smax[tid >> 5] = v;
+      __syncthreads();
+      if (tid < 32) {
+        double t = (tid < (int)(blockDim.x >> 5)) ? smax[tid] : INFINITY;
+        t = -warp_max(-t);
+        if (tid == 0) smax[0] = t;
+      }
+      __syncthreads();
+      vnext = smax[0];
+      __syncthreads();
+    }
+    if (tid == 0) {
+      double disc = F;
+      if (isfinite(vnext) && vnext > 0.0) {
+        // tied values at vnext, split from the highest slice down
+        const double e = energies ? vnext : vnext * vnext;
+        for (int i = p - 1; i >= 0; --i) {
+          const double* s = sigma + (int64_t)i * rc;
+          int r = ranks[i];
+          while (r > 0 && s[r - 1] == vnext && disc + e <= budget) {
+            disc += e;
+            --r;
+          }
+          ranks[i] = r;
+          if (!(disc + e <= budget)) break;
+        }
+      }
+      *err2 = disc;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0, nz = 0;
+    for (int i = 0; i < p; ++i) {
+      off[i] = acc;
+      acc += ranks[i];
+      nz += ranks[i] > 0;
+    }
+    off[p] = acc;
+    iscal[0] = acc;
+    iscal[1] = nz;
+  }
+}
+
+template <typename T>
+__global__ void struct_terms_kernel(const int* __restrict__ map, const double* __restrict__ isq,
+                                    int ell, int q, const T* __restrict__ coef, int64_t cs_i,
+                                    int64_t cs_k, int nterms, const int* nterms_dev,
+                                    T* __restrict__ C) {
+  const int nt = nterms_dev ? min(nterms, *nterms_dev) : nterms;
+  const int64_t per = (int64_t)ell * q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * nterms;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / per);
+    const int pos = (int)(e - (int64_t)i * per);
+    const int k = map[pos];
+    T v = T(0);
+    if (i < nt && k >= 0) v = (T)((double)coef[i * cs_i + k * cs_k] * isq[k]);
+    C[e] = v;
+  }
+}
+
+template <typename T>
+__global__ void scatter_kernel(const int* __restrict__ map, const double* __restrict__ isq,
+                               int ell, int q, int m, int n, const T* __restrict__ Tt,
+                               T* __restrict__ Ahat, int64_t ld) {
+  const int64_t rows = (int64_t)ell * m, cols = (int64_t)q * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = e / rows, row = e - col * rows;
+    const int a = (int)(row / m), r = (int)(row - (int64_t)a * m);
+    const int b = (int)(col / n), c = (int)(col - (int64_t)b * n);
+    const int k = map[a + ell * b];
+    T v = T(0);
+    if (k >= 0) v = (T)((double)Tt[r + (int64_t)m * c + (int64_t)m * n * k] * isq[k]);
+    Ahat[row + col * ld] = v;
+  }
+}
+
+template <typename T>
+__global__ void orth_kernel(const T* __restrict__ Gm, int rc, const int* __restrict__ ranks,
+                            const double* __restrict__ scale, double* out) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  const int r = ranks ? ranks[i] : rc;
+  const T* G = Gm + (int64_t)i * rc * rc;
+  const double* sc = scale ? scale + (int64_t)i * rc : nullptr;
+  double mx = 0.0;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int a = e % r, b = e / r;
+    double g = (double)G[a + (int64_t)b * rc];
+    if (sc) g = (sc[a] > 0 && sc[b] > 0) ? g / (sc[a] * sc[b]) : (a == b ? 1.0 : 0.0);
+    const double v = g - (a == b ? 1.0 : 0.0);
+    mx = fmax(mx, fabs(v));
+  }
+  // block max via shared memory
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    t = warp_max(t);
+    if (threadIdx.x == 0) out[i] = t;
+  }
+}
+
+template <typename TD, typename TS>
+__global__ void convert_kernel(const TS* __restrict__ s, TD* __restrict__ d, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    d[e] = (TD)s[e];
+}
+
+inline unsigned grid_for(int64_t work, int threads, int64_t cap = 152 * 32) {
+  int64_t g = (work + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+int gather_parts(int m, int n, int p) {
+  const int64_t total = (int64_t)m * n * p;
+  int64_t g = (total + GATHER_THREADS * 4 - 1) / (GATHER_THREADS * 4);
+  if (g < 1) g = 1;
+  if (g > GATHER_MAX_CTAS) g = GATHER_MAX_CTAS;
+  return (int)g;
+}
+
+template <typename TS, typename T>
+cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off, const double* w, int m,
+                   int n, int p, T* X, double* partial, cudaStream_t st) {
+  const int g = gather_parts(m, n, p);
+  gather_kernel<TS, T><<<g, GATHER_THREADS, 0, st>>>(A, lda, rep_off, w, m, n, p, X, partial);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t residual_norm2(const T* X, const T* Tt, int64_t count, double* partial, int nparts,
+                           double* out, cudaStream_t st) {
+  residual_kernel<T><<<nparts, GATHER_THREADS, 0, st>>>(X, Tt, count, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  finish_norm_kernel<<<1, 1024, 0, st>>>(partial, nparts, out);
+  return cudaGetLastError();
+}
+template cudaError_t residual_norm2<float>(const float*, const float*, int64_t, double*, int,
+                                           double*, cudaStream_t);
+template cudaError_t residual_norm2<double>(const double*, const double*, int64_t, double*, int,
+                                            double*, cudaStream_t);
+
+cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStream_t st) {
+  finish_norm_kernel<<<1, 1024, 0, st>>>(partial, nparts, out);
+  return cudaGetLastError();
+}
+
+cudaError_t truncate_ranks(const double* sigma, int rc, int p, const double* normX2,
+                           double rel_tol, int fixed_rank, int* ranks, int* off, double* err2,
+                           int* iscal, double* scratch, cudaStream_t st, int energies) {
+  truncate_kernel<<<1, TR_THREADS, 0, st>>>(sigma, rc, p, normX2, rel_tol, fixed_rank, ranks,
+                                            off, err2, iscal, scratch, energies);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t build_struct_terms(const int* map, const double* isq, int ell, int q, const T* coef,
+                               int64_t cs_i, int64_t cs_k, int nterms, const int* nterms_dev,
+                               T* C, cudaStream_t st) {
+  const int64_t work = (int64_t)ell * q * nterms;
+  if (work <= 0) return cudaSuccess;
+  struct_terms_kernel<T><<<grid_for(work, 256), 256, 0, st>>>(map, isq, ell, q, coef, cs_i,
+                                                                cs_k, nterms, nterms_dev, C);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t scatter_ME(const int* map, const double* isq, int ell, int q, int m, int n,
+                       const T* Tt, T* Ahat, int64_t ld, cudaStream_t st) {
+  const int64_t work = (int64_t)ell * m * q * n;
+  scatter_kernel<T><<<grid_for(work, 256), 256, 0, st>>>(map, isq, ell, q, m, n, Tt, Ahat, ld);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t orth_defect(const T* Gm, int rc, int p, const int* ranks, const double* scale,
+                        double* out, cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  orth_kernel<T><<<p, 256, 0, st>>>(Gm, rc, ranks, scale, out);
+  return cudaGetLastError();
+}
+
+template <typename TD, typename TS>
+cudaError_t convert(const TS* src, TD* dst, int64_t count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  convert_kernel<TD, TS><<<grid_for(count, 256), 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+template cudaError_t gather<double, double>(const double*, int64_t, const int64_t*, const double*,
+                                            int, int, int, double*, double*, cudaStream_t);
+template cudaError_t gather<float, float>(const float*, int64_t, const int64_t*, const double*,
+                                          int, int, int, float*, double*, cudaStream_t);
+template cudaError_t build_struct_terms<float>(const int*, const double*, int, int, const float*,
+                                               int64_t, int64_t, int, const int*, float*,
+                                               cudaStream_t);
+template cudaError_t build_struct_terms<double>(const int*, const double*, int, int,
+                                                const double*, int64_t, int64_t, int, const int*,
+                                                double*, cudaStream_t);
+template cudaError_t scatter_ME<float>(const int*, const double*, int, int, int, int,
+                                       const float*, float*, int64_t, cudaStream_t);
+template cudaError_t scatter_ME<double>(const int*, const double*, int, int, int, int,
+                                        const double*, double*, int64_t, cudaStream_t);
+template cudaError_t orth_defect<float>(const float*, int, int, const int*, const double*,
+                                        double*, cudaStream_t);
+template cudaError_t orth_defect<double>(const double*, int, int, const int*, const double*,
+                                         double*, cudaStream_t);
+template cudaError_t convert<float, double>(const double*, float*, int64_t, cudaStream_t);
+template cudaError_t convert<double, float>(const float*, double*, int64_t, cudaStream_t);
+template cudaError_t convert<float, float>(const float*, float*, int64_t, cudaStream_t);
+template cudaError_t convert<double, double>(const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace sma
