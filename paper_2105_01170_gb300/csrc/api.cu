@@ -901,9 +901,7 @@ template <typename T>
 sma_status reconstruct_one(sma_ctx* h, Prob<T>& P, void* Ahat, int64_t ld) {
   if (!P.compressed) return SMA_ERR_STATE;
   cudaStream_t st = h->st;
-  const int m = P.m, n = P.n, p = P.p;
-  const int64_t mn = (int64_t)m * n;
-  const sma_decomp d = h->opt.decomp;
+  const int m = P.m, n = P.n;
   if (!Ahat || ld < (int64_t)P.ell * m) return SMA_ERR_ARG;
   SMA_TRY(make_T(h, P));
   T* dst = static_cast<T*>(Ahat);
