@@ -209,6 +209,39 @@ typedef enum {
 sma_status sma_profile(sma_handle h, double* ms, int64_t* calls, int64_t* launches,
                        int32_t reset);
 
+/* Batched one-sided Jacobi SVD of p fp32 slices that allocates no device
+ * memory.  The paper has no counterpart: this is a deployment variant of the
+ * per-slice SVD of the t-SVDM step for callers that cannot call cudaMalloc
+ * where they need the work done (the execution callback of an inference-
+ * engine plugin, which must not allocate; a loop whose device memory is
+ * budgeted once by another allocator) and therefore cannot create a handle.
+ * Its scratch -- the working copy of slices too large for shared memory and
+ * the status word -- is a fixed 8 MiB __device__ array that every GPU loading
+ * the library holds until the process exits.
+ *   X      device, m x n x p fp32, slice k at X + k*m*n (column-major, ld m)
+ *   W      device out, max(m,n) x min(m,n) x p: U Sigma of each slice (of its
+ *          transpose when m < n), columns by decreasing singular value
+ *   V      device out, min(m,n) x min(m,n) x p: the matching right vectors,
+ *          so that slice = W V^T (m >= n) or slice = V W^T (m < n)
+ *   sigma  device out, min(m,n) x p doubles, descending per slice
+ *   sweeps device out, p int32 (may be NULL): sweeps used per slice
+ *   status device out, one int32 (may be NULL): bit set of the sma_status
+ *          values the kernel raised (NOCONVERGE, NONFINITE)
+ *   max_sweeps (0 = 30); stream: cudaStream_t (NULL = legacy default stream)
+ * Limit: a slice that does not fit in shared memory needs
+ * (max(m,n) + min(m,n)) * min(m,n) floats of scratch; a slice needing more
+ * than the 8 MiB array is rejected with SMA_ERR_ARG (so is a NULL pointer or
+ * a size <= 0).  Larger p is processed in stream-ordered chunks that reuse
+ * the array.  SMA_ERR_CUDA if a CUDA call fails.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress and caches it; make that first call before any
+ * stream capture.  Every call shares the one array and clears its status word
+ * on entry, so calls whose work overlaps on the GPU (several streams or host
+ * threads) race on it and must be serialised by the caller.                */
+sma_status sma_slice_svd_noalloc(const float* X, int32_t m, int32_t n, int32_t p, float* W,
+                                 float* V, double* sigma, int32_t* sweeps, int32_t* status,
+                                 int32_t max_sweeps, void* stream);
+
 sma_status sma_destroy(sma_handle h);
 
 const char* sma_status_string(sma_status s);

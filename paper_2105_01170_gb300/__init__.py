@@ -33,8 +33,8 @@ SMA_INPUT_DENSE, SMA_INPUT_BLOCKS = 0, 1
 EXPORT_X, EXPORT_XHAT, EXPORT_SIGMA, EXPORT_T, EXPORT_FACTOR = 0, 1, 2, 3, 4
 
 EXPORTED = ("sma_create", "sma_compress", "sma_get_result", "sma_get_ranks", "sma_reconstruct",
-            "sma_apply", "sma_export", "sma_profile", "sma_destroy", "sma_status_string",
-            "sma_version")
+            "sma_apply", "sma_export", "sma_profile", "sma_slice_svd_noalloc", "sma_destroy",
+            "sma_status_string", "sma_version")
 STAGES = ("gather", "transform", "svd", "truncate", "factors", "report", "apply")
 
 
@@ -98,12 +98,14 @@ def lib() -> ctypes.CDLL:
         L.sma_export.argtypes = [vp, i32, i32, vp, i64, ctypes.POINTER(i64)]
         L.sma_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64), i32]
+        L.sma_slice_svd_noalloc.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, i32, vp]
         L.sma_destroy.argtypes = [vp]
         L.sma_status_string.argtypes = [ctypes.c_int]
         L.sma_status_string.restype = ctypes.c_char_p
         L.sma_version.restype = ctypes.c_char_p
         for name in ("sma_create", "sma_compress", "sma_get_result", "sma_get_ranks",
-                     "sma_reconstruct", "sma_apply", "sma_export", "sma_profile", "sma_destroy"):
+                     "sma_reconstruct", "sma_apply", "sma_export", "sma_profile",
+                     "sma_slice_svd_noalloc", "sma_destroy"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -163,6 +165,16 @@ def sma_export(h, i, which, ptr, count, avail):
 
 def sma_profile(h, ms, calls, launches, reset):
     return lib().sma_profile(h, ms, calls, ctypes.byref(launches), int(reset))
+
+
+def sma_slice_svd_noalloc(x_ptr, m, n, p, w_ptr, v_ptr, sigma_ptr, sweeps_ptr, status_ptr,
+                          max_sweeps=0, stream=None):
+    """Allocation-free batched slice SVD (device pointers; see include/sma.h)."""
+    c = ctypes.c_void_p
+    return lib().sma_slice_svd_noalloc(c(int(x_ptr)), int(m), int(n), int(p), c(int(w_ptr)),
+                                       c(int(v_ptr)), c(int(sigma_ptr)), c(int(sweeps_ptr or 0)),
+                                       c(int(status_ptr or 0)), int(max_sweeps),
+                                       c(int(stream or 0)))
 
 
 def sma_destroy(h):
