@@ -474,12 +474,15 @@ sma_status compress_tsvdm(sma_ctx* h, Prob<T>& P) {
                         P.stats + 1, P.iscal, P.suf, st, 0));
   stage_end(h);
   stage_begin(h, SMA_STAGE_FACTORS);
-  // truncated slices: D_i = W_r V_r^T (W = U Sigma), or V_r W_r^T when the
-  // slice was processed transposed
+  // truncated slices: D_i = Xhat_i - W_d V_d^T (W = U Sigma, d = the
+  // discarded columns rho_i..rc-1), or Xhat_i - V_d W_d^T when the slice was
+  // processed transposed.  Subtracting the discarded part keeps the error of
+  // the rebuilt slice proportional to the discarded energy, not to ||Xhat_i||.
   const int64_t urc = (int64_t)mm * rc, vrc = (int64_t)rc * rc;
+  SMA_CK(cudaMemcpyAsync(P.D, P.Xh, sizeof(T) * (size_t)mn * p, cudaMemcpyDeviceToDevice, st));
   {
     GemmParams<T> g;
-    g.M = m; g.N = n; g.K = rc; g.dK = P.ranks;
+    g.M = m; g.N = n; g.K = rc; g.dKoff = P.ranks;
     if (!P.jp.trans) {
       g.A = P.U; g.a_rs = 1; g.a_cs = mm; g.a_b1 = urc;
       g.B = P.V; g.b_rs = rc; g.b_cs = 1; g.b_b1 = vrc;
@@ -488,6 +491,7 @@ sma_status compress_tsvdm(sma_ctx* h, Prob<T>& P) {
       g.B = P.U; g.b_rs = mm; g.b_cs = 1; g.b_b1 = urc;
     }
     g.C = P.D; g.c_rs = 1; g.c_cs = m; g.c_b1 = mn;
+    g.alpha = T(-1); g.beta = T(1);
     g.nb1 = p;
     SMA_K(contract<T>(h, g));
   }

@@ -67,7 +67,8 @@ struct GemmParams {
   const int* dM = nullptr;
   const int* dN = nullptr;
   const int* dK = nullptr;
-  int dstride = 1;   // dM/dN/dK are read at [dstride * b1] (0 = one shared value)
+  const int* dKoff = nullptr;  // optional: K range starts at dKoff[dstride * b1]
+  int dstride = 1;   // dM/dN/dK/dKoff are read at [dstride * b1] (0 = one shared value)
   const T* A = nullptr; int64_t a_rs = 0, a_cs = 0, a_b1 = 0, a_b2 = 0;
   const T* B = nullptr; int64_t b_rs = 0, b_cs = 0, b_b1 = 0, b_b2 = 0;
   T* C = nullptr; int64_t c_rs = 0, c_cs = 0, c_b1 = 0, c_b2 = 0;

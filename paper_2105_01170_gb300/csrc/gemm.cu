@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
 
   const bool a_col = (p.a_rs == 1);
   const bool b_col = (p.b_rs == 1);
-  for (int k0 = 0; k0 < K; k0 += BK) {
+  const int kbeg = p.dKoff ? p.dKoff[di] : 0;
+  for (int k0 = kbeg; k0 < K; k0 += BK) {
 #pragma unroll
     for (int t = 0; t < (BM * BK) / NT; ++t) {
       const int e = tid + t * NT;

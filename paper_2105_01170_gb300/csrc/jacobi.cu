@@ -21,10 +21,10 @@
 // the sweep and the I x J cross pairs on every visit, so one sweep rotates
 // each column pair exactly once.
 //
-// Precision.  Dot products and rotations run in T (fp32 on the mixed path,
-// fp64 on the fp64 path); the rotation angle and the convergence test are
-// evaluated in fp64 on both paths; the final column norms are accumulated in
-// fp64.  Rotation (Rutishauser form):
+// Precision.  Dot products, rotation angles and rotations run in T (fp32 on
+// the mixed path, fp64 on the fp64 path); on the mixed path the angle and the
+// convergence test of nearly parallel columns (|cos| > 0.99) are evaluated in
+// fp64; the final column norms are accumulated in fp64.  Rotation (Rutishauser form):
 //   zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 //   c = 1/sqrt(1+t^2), s = c t, w_a' = c w_a - s w_b, w_b' = s w_a + c w_b,
 // applied when |gamma| > tol sqrt(alpha beta); the caller sets tol (4 sqrt(mm) eps(T)).
@@ -45,16 +45,92 @@ __device__ __forceinline__ Pair rr_pair(int k, int t, int c) {
   return pr;
 }
 
-// Rotate the columns at shared-memory slots a and b (group of g lanes, all
-// lanes of the warp must call this together).  Returns true if rotated.
+// Rotation angle for the pair with squared norms al, be and inner product
+// ga; false when the pair is already orthogonal to tolerance.
+__device__ __forceinline__ bool angle_fp64(double al, double be, double ga, double tol,
+                                           double& c, double& s) {
+  if (!(fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
+  const double zeta = (be - al) / (2.0 * ga);
+  const double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                                        : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = c * t;
+  return true;
+}
+
+template <typename T> struct Angle;
+template <> struct Angle<double> {
+  static __device__ __forceinline__ bool get(double al, double be, double ga, double tol,
+                                             double& c, double& s) {
+    return angle_fp64(al, be, ga, tol, c, s);
+  }
+};
+template <> struct Angle<float> {
+  // fp32 angle; fp64 for nearly parallel columns (|cos| > 0.99), where the
+  // difference of the squared norms loses most of its fp32 digits
+  static __device__ __forceinline__ bool get(float al, float be, float ga, double tol,
+                                             float& c, float& s) {
+    const float nrm = sqrtf(al) * sqrtf(be);
+    if (!(fabsf(ga) > (float)tol * nrm)) return false;
+    if (fabsf(ga) > 0.99f * nrm) {
+      double cd = 1.0, sd = 0.0;
+      angle_fp64(al, be, ga, 0.0, cd, sd);
+      c = (float)cd;
+      s = (float)sd;
+      return true;
+    }
+    const float zeta = (be - al) / (2.0f * ga);
+    const float az = fabsf(zeta);
+    const float t = (az > 1e18f) ? 0.5f / zeta : copysignf(1.0f, zeta) / (az + sqrtf(fmaf(zeta, zeta, 1.0f)));
+    // c = 1/sqrt(1 + t^2) to about half an ulp: q = 1 + t^2 as an unevaluated
+    // sum (q_hi + q_lo), one Newton step on rsqrt with the residual formed by
+    // fused multiply-adds; s = t c.  (The angle t itself may carry fp32
+    // rounding -- any exact rotation is valid -- but (c, s) must be as close
+    // to orthogonal as fp32 allows, since each column sees thousands of them.)
+    const float u_hi = t * t;
+    const float u_lo = fmaf(t, t, -u_hi);
+    const float q_hi = 1.0f + u_hi;
+    const float q_lo = ((u_hi <= 1.0f) ? ((1.0f - q_hi) + u_hi) : ((u_hi - q_hi) + 1.0f)) + u_lo;
+    const float r0 = rsqrtf(q_hi);
+    const float a_hi = r0 * r0;
+    const float a_lo = fmaf(r0, r0, -a_hi);
+    const float e = fmaf(-q_hi, a_hi, 1.0f) - fmaf(q_hi, a_lo, q_lo * a_hi);
+    c = fmaf(0.5f * r0, e, r0);
+    s = c * t;
+    return true;
+  }
+};
+
+// Rows per lane kept in registers between the dot products and the rotation.
+template <typename T> struct CacheRows { static constexpr int v = 32; };
+template <> struct CacheRows<double> { static constexpr int v = 16; };
+
+// Rotate the stacked columns at shared-memory slots a and b (group of g
+// lanes; every lane of the warp must call this together).  Dot products over
+// rows [0, mm), rotation over rows [0, len).  Returns true if rotated.
 template <typename T>
 __device__ __forceinline__ bool rotate_pair(T* S, int ldS, int a, int b, bool active,
                                             int mm, int len, int lane, int g, double tol) {
+  constexpr int NR = CacheRows<T>::v;
+  T xr[NR], yr[NR];
   T al = T(0), be = T(0), ga = T(0);
   T* x = S + (int64_t)(active ? a : 0) * ldS;
   T* y = S + (int64_t)(active ? b : 0) * ldS;
   if (active) {
-    for (int r = lane; r < mm; r += g) {
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int r = lane + i * g;
+      xr[i] = T(0);
+      yr[i] = T(0);
+      if (r < mm) {
+        xr[i] = x[r];
+        yr[i] = y[r];
+      }
+      al = fma(xr[i], xr[i], al);
+      be = fma(yr[i], yr[i], be);
+      ga = fma(xr[i], yr[i], ga);
+    }
+    for (int r = lane + NR * g; r < mm; r += g) {
       const T xv = x[r], yv = y[r];
       al = fma(xv, xv, al);
       be = fma(yv, yv, be);
@@ -67,14 +143,22 @@ __device__ __forceinline__ bool rotate_pair(T* S, int ldS, int a, int b, bool ac
     ga += __shfl_xor_sync(0xffffffffu, ga, o);
   }
   if (!active) return false;
-  const double dal = (double)al, dbe = (double)be, dga = (double)ga;
-  if (!(fabs(dga) > tol * sqrt(dal * dbe))) return false;
-  const double zeta = (dbe - dal) / (2.0 * dga);
-  const double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
-                                        : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double cs = 1.0 / sqrt(1.0 + t * t);
-  const T c = (T)cs, s = (T)(cs * t);
-  for (int r = lane; r < len; r += g) {
+  T c, s;
+  if (!Angle<T>::get(al, be, ga, tol, c, s)) return false;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const int r = lane + i * g;
+    if (r < mm) {
+      x[r] = c * xr[i] - s * yr[i];
+      y[r] = s * xr[i] + c * yr[i];
+    }
+  }
+  for (int r = lane + NR * g; r < mm; r += g) {
+    const T xv = x[r], yv = y[r];
+    x[r] = c * xv - s * yv;
+    y[r] = s * xv + c * yv;
+  }
+  for (int r = mm + lane; r < len; r += g) {
     const T xv = x[r], yv = y[r];
     x[r] = c * xv - s * yv;
     y[r] = s * xv + c * yv;
@@ -90,14 +174,63 @@ __device__ __forceinline__ T load_work(const T* src, int m, int trans, int mm, i
   return trans ? src[c + (int64_t)r * m] : src[r + (int64_t)c * m];
 }
 
+// Pair k of round t of one phase (the work between two stagings).
+//   kind 0: round robin over the bI columns in shared memory (cI = bI even-up);
+//   kind 1: first nri rounds: round robin inside block I (slots [0, bI), cI
+//           players, 0 = skip) and independently inside block J (slots
+//           [bc, bc + bJ), cJ players, 0 = skip); then bc rounds of cross
+//           pairs I x J: slot k with slot bc + (k + t') % bc.
+struct Phase {
+  int kind, bI, bJ, bc, cI, cJ, nri, npairs, nrounds;
+};
+
+__device__ __forceinline__ bool phase_pair(const Phase& ph, int t, int k, int& a, int& b) {
+  if (ph.kind == 0) {
+    if (k >= ph.cI / 2) return false;
+    const Pair pr = rr_pair(k, t, ph.cI);
+    a = pr.a;
+    b = pr.b;
+    return pr.a < ph.bI && pr.b < ph.bI;
+  }
+  if (t < ph.nri) {
+    const int pI = ph.cI / 2;
+    if (k < pI) {
+      if (t >= ph.cI - 1) return false;
+      const Pair pr = rr_pair(k, t, ph.cI);
+      a = pr.a;
+      b = pr.b;
+      return pr.a < ph.bI && pr.b < ph.bI;
+    }
+    if (k >= pI + ph.cJ / 2 || t >= ph.cJ - 1) return false;
+    const Pair pr = rr_pair(k - pI, t, ph.cJ);
+    a = ph.bc + pr.a;
+    b = ph.bc + pr.b;
+    return pr.a < ph.bJ && pr.b < ph.bJ;
+  }
+  if (k >= ph.bc) return false;
+  const int j = (k + t - ph.nri) % ph.bc;
+  a = k;
+  b = ph.bc + j;
+  return k < ph.bI && j < ph.bJ;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiParams<T> P) {
+__global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = blockIdx.x;
   const int tid = threadIdx.x, NTh = blockDim.x;
   const int mm = P.mm, rc = P.rc, ldS = P.ldS, g = P.g;
   const int len = mm + rc;  // stacked column [w; v]
   const int lane = tid % g, gid = tid / g, ngroups = NTh / g;
+  // Pair slot of this group.  Consecutive pair slots hold consecutive
+  // columns, so the groups sharing a warp take slots g apart: their g-row
+  // windows then fall on disjoint shared-memory banks (column stride is 1
+  // word mod 32).
+  int kslot = gid;
+  {
+    const int gpw = 32 / g, nw = NTh / 32, w = tid / 32, j = (tid % 32) / g;
+    if (g < 32 && nw % g == 0) kslot = (w % g) + g * j + 32 * (w / g);
+  }
   const T* src = P.src + (int64_t)s * P.src_bs;
   const bool in_smem = rc <= 2 * P.bcols;
   const int ncols_smem = in_smem ? rc : 2 * P.bcols;
@@ -107,116 +240,85 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const JacobiParams<T> P) {
   double* sig = reinterpret_cast<double*>(smem_raw + sig_off);
   int* idx = reinterpret_cast<int*>(sig + p2);
   T* W = P.W ? P.W + (int64_t)s * P.W_bs : nullptr;
+  const int bc = P.bcols;
+  const int nb = in_smem ? 1 : (rc + bc - 1) / bc;
 
-  int sweeps_used = 0;
-  bool converged = false;
-  if (in_smem) {
+  // load the stacked columns [slice; I] into shared memory or the workspace
+  {
     const int tot = len * rc;
     for (int e = tid; e < tot; e += NTh) {
       int r, c;
       if (P.trans) { c = e % rc; r = e / rc; } else { r = e % len; c = e / len; }
-      S[(int64_t)c * ldS + r] = load_work(src, P.m, P.trans, mm, r, c);
+      const T v = load_work(src, P.m, P.trans, mm, r, c);
+      if (in_smem) S[(int64_t)c * ldS + r] = v;
+      else W[r + (int64_t)c * len] = v;
     }
     __syncthreads();
-    const int c_even = rc + (rc & 1);
-    const int npairs = c_even / 2;
-    for (int sw = 0; sw < P.max_sweeps && rc > 1; ++sw) {
-      bool rot = false;
-      for (int t = 0; t < c_even - 1; ++t) {
-        for (int base = 0; base < npairs; base += ngroups) {
-          const int k = base + gid;
-          Pair pr = rr_pair(k < npairs ? k : 0, t, c_even);
-          const bool act = (k < npairs) && pr.a < rc && pr.b < rc;
-          rot |= rotate_pair(S, ldS, pr.a, pr.b, act, mm, len, lane, g, P.tol);
+  }
+  int sweeps_used = 0;
+  bool converged = (rc <= 1);
+  const int npair_sets = in_smem ? 1 : nb * (nb - 1) / 2;
+  for (int sw = 0; sw < P.max_sweeps && !converged; ++sw) {
+    bool rot = false;
+    int I = 0, J = 1;
+    for (int ps = 0; ps < npair_sets; ++ps) {
+      Phase ph;
+      if (in_smem) {
+        ph.kind = 0;
+        ph.bI = rc;
+        ph.cI = rc + (rc & 1);
+        ph.bJ = ph.bc = ph.cJ = ph.nri = 0;
+        ph.nrounds = ph.cI - 1;
+        ph.npairs = ph.cI / 2;
+      } else {
+        const int bI = min(bc, rc - I * bc), bJ = min(bc, rc - J * bc);
+        for (int e = tid; e < len * bI; e += NTh) {
+          const int r = e % len, c = e / len;
+          S[(int64_t)c * ldS + r] = W[r + (int64_t)(I * bc + c) * len];
+        }
+        for (int e = tid; e < len * bJ; e += NTh) {
+          const int r = e % len, c = e / len;
+          S[(int64_t)(bc + c) * ldS + r] = W[r + (int64_t)(J * bc + c) * len];
+        }
+        __syncthreads();
+        // pairs inside a block on the block's first visit of this sweep
+        const bool doI = (I == 0 && J == 1), doJ = (I == 0);
+        ph.kind = 1;
+        ph.bI = bI;
+        ph.bJ = bJ;
+        ph.bc = bc;
+        ph.cI = doI ? bI + (bI & 1) : 0;
+        ph.cJ = doJ ? bJ + (bJ & 1) : 0;
+        ph.nri = (doI || doJ) ? max(ph.cI, ph.cJ) - 1 : 0;
+        ph.nrounds = ph.nri + bc;
+        ph.npairs = max(bc, ph.cI / 2 + ph.cJ / 2);
+      }
+      for (int t = 0; t < ph.nrounds; ++t) {
+        for (int base = 0; base < ph.npairs; base += ngroups) {
+          int a = 0, b = 0;
+          const bool act = phase_pair(ph, t, base + kslot, a, b);
+          rot |= rotate_pair(S, ldS, a, b, act, mm, len, lane, g, P.tol);
         }
         __syncthreads();
       }
-      sweeps_used = sw + 1;
-      if (!__syncthreads_or(rot)) { converged = true; break; }
-    }
-    if (rc <= 1) converged = true;
-  } else {
-    // block mode: stacked working copy in global memory (len x rc)
-    const int tot = len * rc;
-    for (int e = tid; e < tot; e += NTh) {
-      int r, c;
-      if (P.trans) { c = e % rc; r = e / rc; } else { r = e % len; c = e / len; }
-      W[r + (int64_t)c * len] = load_work(src, P.m, P.trans, mm, r, c);
-    }
-    __syncthreads();
-    const int bc = P.bcols;
-    const int nb = (rc + bc - 1) / bc;
-    for (int sw = 0; sw < P.max_sweeps; ++sw) {
-      bool rot = false;
-      for (int I = 0; I < nb; ++I) {
-        for (int J = I + 1; J < nb; ++J) {
-          const int bI = min(bc, rc - I * bc), bJ = min(bc, rc - J * bc);
-          // stage blocks I -> slots [0, bI), J -> slots [bc, bc + bJ)
-          for (int e = tid; e < len * bI; e += NTh) {
-            const int r = e % len, c = e / len;
-            S[(int64_t)c * ldS + r] = W[r + (int64_t)(I * bc + c) * len];
-          }
-          for (int e = tid; e < len * bJ; e += NTh) {
-            const int r = e % len, c = e / len;
-            S[(int64_t)(bc + c) * ldS + r] = W[r + (int64_t)(J * bc + c) * len];
-          }
-          __syncthreads();
-          // pairs inside a block on the block's first visit of this sweep
-          const bool doI = (I == 0 && J == 1);
-          const bool doJ = (I == 0);
-          if (doI || doJ) {
-            const int cI = doI ? bI + (bI & 1) : 0;
-            const int cJ = doJ ? bJ + (bJ & 1) : 0;
-            const int pI = cI / 2, pJ = cJ / 2;
-            const int rounds = max(cI, cJ) - 1;
-            for (int t = 0; t < rounds; ++t) {
-              const int np = pI + pJ;
-              for (int base = 0; base < np; base += ngroups) {
-                const int k = base + gid;
-                bool act = false;
-                int a = 0, b = 0;
-                if (k < pI) {
-                  if (t < cI - 1) {
-                    Pair pr = rr_pair(k, t, cI);
-                    act = pr.a < bI && pr.b < bI;
-                    a = pr.a; b = pr.b;
-                  }
-                } else if (k < np) {
-                  if (t < cJ - 1) {
-                    Pair pr = rr_pair(k - pI, t, cJ);
-                    act = pr.a < bJ && pr.b < bJ;
-                    a = bc + pr.a; b = bc + pr.b;
-                  }
-                }
-                rot |= rotate_pair(S, ldS, a, b, act, mm, len, lane, g, P.tol);
-              }
-              __syncthreads();
-            }
-          }
-          // cross pairs I x J
-          for (int t = 0; t < bc; ++t) {
-            for (int base = 0; base < bc; base += ngroups) {
-              const int k = base + gid;
-              const int j = (k + t) % bc;
-              const bool act = (k < bc) && k < bI && j < bJ;
-              rot |= rotate_pair(S, ldS, k, bc + j, act, mm, len, lane, g, P.tol);
-            }
-            __syncthreads();
-          }
-          for (int e = tid; e < len * bI; e += NTh) {
-            const int r = e % len, c = e / len;
-            W[r + (int64_t)(I * bc + c) * len] = S[(int64_t)c * ldS + r];
-          }
-          for (int e = tid; e < len * bJ; e += NTh) {
-            const int r = e % len, c = e / len;
-            W[r + (int64_t)(J * bc + c) * len] = S[(int64_t)(bc + c) * ldS + r];
-          }
-          __syncthreads();
+      if (!in_smem) {
+        for (int e = tid; e < len * ph.bI; e += NTh) {
+          const int r = e % len, c = e / len;
+          W[r + (int64_t)(I * bc + c) * len] = S[(int64_t)c * ldS + r];
+        }
+        for (int e = tid; e < len * ph.bJ; e += NTh) {
+          const int r = e % len, c = e / len;
+          W[r + (int64_t)(J * bc + c) * len] = S[(int64_t)(bc + c) * ldS + r];
+        }
+        __syncthreads();
+        if (++J == nb) {
+          ++I;
+          J = I + 1;
         }
       }
-      sweeps_used = sw + 1;
-      if (!__syncthreads_or(rot)) { converged = true; break; }
     }
+    sweeps_used = sw + 1;
+    if (!__syncthreads_or(rot)) converged = true;
   }
 
   // column norms (fp64 accumulation)
@@ -307,7 +409,7 @@ JacobiPlan jacobi_plan(int m, int n, int max_smem) {
   int gd = 1;
   while (gd < 32 && gd * 16 < pl.mm + pl.rc) gd <<= 1;
   int nt = 32;
-  while (nt < 1024 && nt < maxpairs * gd) nt <<= 1;
+  while (nt < 512 && nt < maxpairs * gd) nt <<= 1;
   int gp = 1;
   while (gp * 2 <= 32 && gp * 2 * (maxpairs > 0 ? maxpairs : 1) <= nt) gp <<= 1;
   pl.threads = nt;
