@@ -157,6 +157,15 @@ struct Prob {
   size_t Xs_elems = 0;
   T* Ys = nullptr;
   size_t Ys_elems = 0;
+  // tcgen05 operands of the Kronecker-sum matvec (mixed path): Z^T and the
+  // concatenated terms D^T as three bf16 planes each, K-major
+  __nv_bfloat16* Zp = nullptr;
+  size_t Zp_elems = 0;
+  int64_t Zp_K = -1;
+  __nv_bfloat16* Dp = nullptr;
+  size_t Dp_elems = 0;
+  int64_t Dp_K = -1;
+  bool dp_valid = false;
   bool compressed = false;
   // host copies of results
   int h_iscal[8] = {0};
@@ -673,6 +682,7 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
   if (h->opt.decomp == SMA_TSVDM) SMA_TRY(compress_tsvdm(h, P));
   else SMA_TRY(compress_tucker(h, P));
   P.compressed = true;
+  P.dp_valid = false;
   P.h_iscal[0] = -1;
   return SMA_OK;
 }
@@ -750,6 +760,56 @@ sma_status grow(sma_ctx* h, T** buf, size_t* have, size_t need) {
   return SMA_OK;
 }
 
+// Mixed-path Kronecker-sum matvec on tensor cores: Y^T = Z^T D^T with
+// Z = [X_s C_j^T] (mid-index contraction on CUDA cores, written directly as
+// bf16 split planes) and D = [D_1 | ... | D_nt]; the long-K product runs in
+// the tcgen05 kernel.  Returns false when the shapes do not fit it (the
+// caller then runs the CUDA-core form); a CUDA error is reported through
+// tc_err so the caller can return it.
+template <typename T>
+bool tc_apply(sma_ctx*, Prob<T>&, const T*, int64_t, T*, int64_t, int64_t, int, int) {
+  return false;
+}
+template <>
+bool tc_apply<float>(sma_ctx* h, Prob<float>& P, const float* X, int64_t ldx, float* Yd,
+                     int64_t ldyd, int64_t yrows, int nrhs, int nt) {
+  if (!h->tc_ok || ldyd != yrows || P.m > 256 || nt <= 0) return false;
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, ell = P.ell, q = P.q;
+  const int64_t K = (int64_t)n * nt, Kp = tc_pad_k(K);
+  const int64_t rowsZ = (int64_t)ell * nrhs;
+  if (rowsZ > 0x7fffffff) return false;
+  const size_t zneed = (size_t)3 * rowsZ * Kp, dneed = (size_t)3 * m * Kp;
+  if (grow(h, &P.Zp, &P.Zp_elems, zneed) != SMA_OK) return false;
+  if (grow(h, &P.Dp, &P.Dp_elems, dneed) != SMA_OK) return false;
+  if (P.Zp_K != K) {  // zero the K padding once per shape
+    if (cudaMemsetAsync(P.Zp, 0, P.Zp_elems * sizeof(__nv_bfloat16), st) != cudaSuccess) return false;
+    P.Zp_K = K;
+  }
+  if (!P.dp_valid || P.Dp_K != K) {
+    if (P.Dp_K != K &&
+        cudaMemsetAsync(P.Dp, 0, P.Dp_elems * sizeof(__nv_bfloat16), st) != cudaSuccess)
+      return false;
+    ++h->launches;
+    if (tc_split_transpose(P.D, 1, m, m, (int)K, Kp, P.Dp, st) != cudaSuccess) return false;
+    P.Dp_K = K;
+    P.dp_valid = true;
+  }
+  // Z^T planes: element (c, a) of batch (j, s) at (a + ell s) Kp + c + n j
+  GemmParams<float> g;
+  g.M = n; g.N = ell; g.K = q;
+  g.A = X; g.a_rs = 1; g.a_cs = n; g.a_b2 = ldx;
+  g.B = P.C; g.b_rs = ell; g.b_cs = 1; g.b_b1 = (int64_t)ell * q;
+  g.C = nullptr; g.c_rs = 1; g.c_cs = Kp; g.c_b1 = n; g.c_b2 = (int64_t)ell * Kp;
+  g.Cs = P.Zp; g.cs_plane = rowsZ * Kp;
+  g.nb1 = nt; g.nb2 = nrhs;
+  ++h->launches;
+  if (gemm<float>(g, st) != cudaSuccess) return false;
+  ++h->launches;
+  if (tc_gemm_planes(P.Zp, P.Dp, (int)rowsZ, m, Kp, Yd, m, P.status, st) != cudaSuccess) return false;
+  return true;
+}
+
 template <typename T>
 sma_status apply_one(sma_ctx* h, Prob<T>& P, const void* Xin, int64_t ldx, void* Yout,
                      int64_t ldy, int nrhs) {
@@ -793,6 +853,7 @@ sma_status apply_one(sma_ctx* h, Prob<T>& P, const void* Xin, int64_t ldx, void*
       goto done;
     }
     const int64_t ldZ = (int64_t)n * nt;
+    if (tc_apply(h, P, X, ldx, Yd, ldyd, yrows, nrhs, nt)) goto done;
     SMA_TRY(grow(h, &P.Z, &P.Z_elems, (size_t)ldZ * ell * nrhs));
     // Z[c + n j, a + ell s] = sum_b X_s[c, b] C_j[a, b]
     GemmParams<T> g;

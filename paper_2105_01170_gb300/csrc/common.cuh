@@ -73,6 +73,9 @@ struct GemmParams {
   const T* B = nullptr; int64_t b_rs = 0, b_cs = 0, b_b1 = 0, b_b2 = 0;
   T* C = nullptr; int64_t c_rs = 0, c_cs = 0, c_b1 = 0, c_b2 = 0;
   const int* c_off = nullptr; int64_t c_off_mul = 0;
+  // optional (fp32 only): write C as three bf16 planes (hi, mid, lo) at the
+  // same offsets, plane p at Cs + p*cs_plane, instead of writing C
+  void* Cs = nullptr; int64_t cs_plane = 0;
   int nb1 = 1, nb2 = 1;
   T alpha = T(1), beta = T(0);
 };

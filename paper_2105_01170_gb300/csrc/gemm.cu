@@ -4,12 +4,28 @@
 // projections with run-time ranks, the Kronecker-sum middle contraction) and
 // as the fp64 form of every contraction.  The large fp32 contractions of the
 // mixed path go to the tcgen05 kernel in tc_gemm.cu instead.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace sma {
 namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+// three-plane bf16 split of an fp32 result (hi = bf16(v), mid = bf16(v - hi),
+// lo = bf16(v - hi - mid)); base_off is the batch offset applied to C
+__device__ __forceinline__ void store_split(const GemmParams<float>& p, int64_t base_off,
+                                            int64_t off, float v) {
+  __nv_bfloat16* d = static_cast<__nv_bfloat16*>(p.Cs) + base_off + off;
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(hi);
+  const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+  d[0] = hi;
+  d[p.cs_plane] = mid;
+  d[2 * p.cs_plane] = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+__device__ __forceinline__ void store_split(const GemmParams<double>&, int64_t, int64_t, double) {}
 
 template <typename T>
 __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
@@ -26,7 +42,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
   if (m0 >= M || n0 >= N) return;
   const T* A = p.A + b1 * p.a_b1 + b2 * p.a_b2;
   const T* B = p.B + b1 * p.b_b1 + b2 * p.b_b2;
-  T* C = p.C + (p.c_off ? (int64_t)p.c_off[b1] * p.c_off_mul : b1 * p.c_b1) + b2 * p.c_b2;
+  const int64_t cbo = (p.c_off ? (int64_t)p.c_off[b1] * p.c_off_mul : b1 * p.c_b1) + b2 * p.c_b2;
+  T* C = p.C + cbo;
 
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
@@ -79,8 +96,13 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
     for (int j = 0; j < 4; ++j) {
       const int gj = n0 + tx + 16 * j;
       if (gj >= N) continue;
-      T* c = C + (int64_t)gi * p.c_rs + (int64_t)gj * p.c_cs;
+      const int64_t off = (int64_t)gi * p.c_rs + (int64_t)gj * p.c_cs;
       T v = p.alpha * acc[i][j];
+      if (p.Cs) {
+        store_split(p, cbo, off, v);
+        continue;
+      }
+      T* c = C + off;
       if (p.beta != T(0)) v += p.beta * *c;
       *c = v;
     }

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
   // word mod 32).
   int kslot = gid;
   {
-    const int gpw = 32 / g, nw = NTh / 32, w = tid / 32, j = (tid % 32) / g;
+    const int nw = NTh / 32, w = tid / 32, j = (tid % 32) / g;
     if (g < 32 && nw % g == 0) kslot = (w % g) + g * j + 32 * (w / g);
   }
   const T* src = P.src + (int64_t)s * P.src_bs;

@@ -1,7 +1,357 @@
+// tcgen05 GEMM with 3-piece bf16 split operands (mixed path).
+//
+//   C[i * ldc + j] = sum_k A(i, k) B(j, k),   i < M, j < N <= 256,
+//
+// where A and B are fp32 matrices given as three bf16 planes each
+// (x = hi + mid + lo, hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid)),
+// stored K-major ([row][Kp], Kp a multiple of 64, zero padded).  The six
+// products with i + j <= 2 (hi hi, hi mid, mid hi, hi lo, lo hi, mid mid)
+// are accumulated in fp32 in tensor memory, which carries the operands'
+// fp32 accuracy.
+//
+// One CTA per 128-row tile of C, all N columns: an elected thread of warp 0
+// streams (A plane, B plane) tile pairs with TMA (3-D tensor maps, 128B
+// swizzle) through a 4-stage mbarrier ring; an elected thread of warp 1
+// issues tcgen05.mma (M128 x N256 x K16, accumulator in TMEM); warps 2-5
+// read the accumulator with tcgen05.ld and store fp32 rows.  Every wait is
+// bounded: on timeout the kernel sets an error bit, drains what it issued,
+// frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "tc_gemm.cuh"
 
 namespace sma {
-bool tc_gemm_available(int major, int minor) { return false && major == 10 && minor == 3; }
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;        // 16 KB
+constexpr int B_BYTES = BN * BK * 2;        // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int THREADS = 192;
+constexpr int TMEM_COLS = 256;
+constexpr uint64_t WAIT_NS = 4000000000ull;  // 4 s per wait
+constexpr uint32_t WAIT_ITERS = 1u << 30;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+
+__constant__ int kProdA[6] = {0, 0, 1, 0, 2, 1};
+__constant__ int kProdB[6] = {0, 1, 0, 2, 0, 1};
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  for (uint32_t i = 0; i < WAIT_ITERS; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (gtimer() - t0 > WAIT_NS) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(saddr(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms of
+// 1024 B (stride byte offset), descriptor version 1, layout type 2.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused here), 16 B
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+// kind::f16 instruction descriptor: fp32 accumulator, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t dtm, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtm),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          saddr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+  int M, N, Kp;
+  float* C;
+  int64_t ldc;
+  int* err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               const TcArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* tiles = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accum = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM;
+  const int total = (args.Kp / BK) * 6;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: (A plane, B plane) tiles for iteration it = 6 kb + product
+    int issued = 0;
+    for (int it = 0; it < total; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const int kb = it / 6, pr = it % 6;
+      uint8_t* st = tiles + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_3d(st, &mapA, &full[s], kb * BK, m0, kProdA[pr]);
+      tma_load_3d(st + A_BYTES, &mapB, &full[s], kb * BK, 0, kProdB[pr]);
+      issued = it + 1;
+    }
+    // drain: the copies of the last stages must land before the CTA exits
+    for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
+      if (!mbar_wait(&full[it % STAGES], (uint32_t)(it / STAGES) & 1u)) *abort_flag = 1;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t id = idesc_bf16(BM, BN);
+    for (int it = 0; it < total; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+      if (!mbar_wait(&full[s], ph)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      fence_after();
+      const uint32_t a0 = saddr(tiles + s * STAGE_BYTES);
+      const uint32_t b0 = a0 + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        mma(tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), id, (it > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accum);  // arrives once every MMA issued above has completed
+  }
+  if (warp >= 2) {
+    const bool ok = mbar_wait(accum, 0);
+    fence_after();
+    if (!ok) *abort_flag = 1;
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int grow = m0 + row;
+    __syncwarp();
+    if (!*abort_flag) {
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+        if (grow < args.M) {
+          float* dst = args.C + (int64_t)grow * args.ldc + c0;
+          const int nv = args.N - c0;
+          if (nv >= 32 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(dst + j) =
+                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                              __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nv) dst[j] = __uint_as_float(r[j]);
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(args.err, SMA_STATUS_BIT(SMA_ERR_TIMEOUT));
+}
+
+// fp32 -> three bf16 planes, with transposition: plane[p][j * Kp + k] from
+// src[j * s_rs + k * s_cs] for j < R, k < K (32 x 32 tiles through shared
+// memory so both sides are coalesced when s_rs == 1).
+__global__ void split_transpose_kernel(const float* __restrict__ src, int64_t s_rs, int64_t s_cs,
+                                       int R, int K, int64_t Kp, __nv_bfloat16* __restrict__ dst,
+                                       int64_t plane) {
+  __shared__ float tile[32][33];
+  const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int k = k0 + i, j = j0 + threadIdx.x;
+    tile[i][threadIdx.x] = (j < R && k < K) ? src[(int64_t)j * s_rs + (int64_t)k * s_cs] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int j = j0 + i, k = k0 + threadIdx.x;
+    if (j < R && k < K) {
+      const float x = tile[threadIdx.x][i];
+      const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+      const float r1 = x - __bfloat162float(hi);
+      const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+      const int64_t o = (int64_t)j * Kp + k;
+      dst[o] = hi;
+      dst[o + plane] = mid;
+      dst[o + 2 * plane] = lo;
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const __nv_bfloat16* planes, int rows, int64_t Kp, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 3};
+  const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
+  const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(planes), dims,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_gemm_available(int major, int minor) {
+  return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+int64_t tc_pad_k(int64_t K) { return (K + BK - 1) / BK * BK; }
+
+cudaError_t tc_split_transpose(const float* src, int64_t s_rs, int64_t s_cs, int R, int K,
+                               int64_t Kp, __nv_bfloat16* dst, cudaStream_t st) {
+  if (R <= 0 || K <= 0) return cudaSuccess;
+  dim3 grid((R + 31) / 32, (K + 31) / 32);
+  split_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(src, s_rs, s_cs, R, K, Kp, dst,
+                                                      (int64_t)R * Kp);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_planes(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N,
+                           int64_t Kp, float* C, int64_t ldc, int* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (N > BN || Kp % BK != 0 || Kp <= 0) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, Kp, BM) || !make_map(&mb, B, N, Kp, BN)) return cudaErrorInvalidValue;
+  const cudaError_t attr = cudaFuncSetAttribute(
+      tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  TcArgs a{M, N, (int)Kp, C, ldc, err};
+  tc_gemm_kernel<<<(M + BM - 1) / BM, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
 bool tc_gemm_eligible(const GemmParams<float>&) { return false; }
 cudaError_t tc_gemm_bf16x3(const GemmParams<float>& g, cudaStream_t st) { return gemm<float>(g, st); }
+
 }  // namespace sma
