@@ -77,10 +77,12 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       T a[4], b[4];
+      // rows follow tx so that consecutive threads write consecutive rows of
+      // the (column-major) output
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+      for (int i = 0; i < 4; ++i) a[i] = As[k][tx + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][ty + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -90,11 +92,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int gi = m0 + ty + 16 * i;
+    const int gi = m0 + tx + 16 * i;
     if (gi >= M) continue;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int gj = n0 + tx + 16 * j;
+      const int gj = n0 + ty + 16 * j;
       if (gj >= N) continue;
       const int64_t off = (int64_t)gi * p.c_rs + (int64_t)gj * p.c_cs;
       T v = p.alpha * acc[i][j];
