@@ -205,6 +205,14 @@ def _ptr_ld(a):
 
 
 @dataclass
+class MultilevelProblem:
+    """Three-level structured matrix with scalar blocks (Section 7.2): level t
+    has an ell_t x q_t map with p_t distinct indices."""
+    level_maps: list       # three (ell_t, q_t) int arrays
+    level_p: list          # three ints
+
+
+@dataclass
 class Problem:
     ell: int
     q: int
@@ -223,6 +231,9 @@ class Handle:
         self._keep = []
         structs = []
         for pr in problems:
+            if hasattr(pr, "level_maps"):
+                structs.append(self._multilevel_struct(pr))
+                continue
             bm = np.ascontiguousarray(np.asarray(pr.block_map, dtype=np.int32).ravel(order="F"))
             self._keep.append(bm)
             s = sma_problem(int(pr.ell), int(pr.q), int(pr.m), int(pr.n), int(pr.p),
@@ -243,6 +254,17 @@ class Handle:
         self.prec = prec
         st, self.h = sma_create(structs, self.opt)
         _check(st, "sma_create")
+
+    def _multilevel_struct(self, pr):
+        I32 = ctypes.c_int32
+        maps = [np.ascontiguousarray(np.asarray(m, dtype=np.int32).ravel(order="F"))
+                for m in pr.level_maps]
+        ells = (I32 * 3)(*[np.asarray(m).shape[0] for m in pr.level_maps])
+        qs = (I32 * 3)(*[np.asarray(m).shape[1] for m in pr.level_maps])
+        ps = (I32 * 3)(*[int(p) for p in pr.level_p])
+        mptrs = (ctypes.POINTER(I32) * 3)(*[m.ctypes.data_as(ctypes.POINTER(I32)) for m in maps])
+        self._keep += [maps, ells, qs, ps, mptrs]
+        return sma_problem(1, 1, 1, 1, 1, None, 3, ells, qs, ps, mptrs)
 
     def compress(self, As, want_result=True, check=True):
         ptrs, ldas = zip(*[_ptr_ld(a) for a in As])

@@ -146,6 +146,28 @@ struct Prob {
   T* tmp = nullptr;
   T* mid = nullptr;                         // struct_E(core) dense (ell r1 x q r3)
   int r1max = 0, r3max = 0;
+  // multilevel (three levels, m = n = 1; Section 7)
+  int L = 1;
+  int lell[3] = {0, 0, 0}, lq[3] = {0, 0, 0}, lp[3] = {0, 0, 0};
+  std::vector<int32_t> lmap[3];
+  int* d_lmap[3] = {nullptr, nullptr, nullptr};
+  double* d_lw[3] = {nullptr, nullptr, nullptr};
+  double* d_lisq[3] = {nullptr, nullptr, nullptr};
+  T* Uml[3] = {nullptr, nullptr, nullptr};  // factors (p_t x p_t, leading k_t used)
+  T* T1 = nullptr;
+  T* T2 = nullptr;
+  T* Gc = nullptr;                          // core, p1 x p2 x p3 (leading k's used)
+  T* Gcmp = nullptr;                        // compact core k1 k2 x k3
+  T* C1i = nullptr;                         // struct_1 terms, l1 x (k1 q1) interleaved
+  T* C2i = nullptr;                         // struct_2 terms, l2 x (k2 q2) interleaved
+  T* C3st = nullptr;                        // struct_3 terms, (l3 k3) x q3 stacked
+  T* U3x = nullptr;
+  size_t U3x_elems = 0;
+  T* Vml = nullptr;
+  size_t Vml_elems = 0;
+  T* Wml = nullptr;
+  size_t Wml_elems = 0;
+  bool ml_valid = false;
   // reconstruction
   T* Tt = nullptr;
   // apply workspace
@@ -248,6 +270,28 @@ std::vector<Prob<double>>& probs<double>(sma_ctx* h) { return h->p64; }
 template <>
 std::vector<Prob<float>>& probs<float>(sma_ctx* h) { return h->p32; }
 
+// Section 7.2: one map per level; every index of level t occurs.
+sma_status validate_levels(const sma_problem& pr, std::vector<int64_t> eta[3]) {
+  if (pr.levels != 3) return SMA_ERR_UNSUPPORTED;
+  if (pr.m != 1 || pr.n != 1) return SMA_ERR_ARG;
+  if (!pr.level_ell || !pr.level_q || !pr.level_p || !pr.level_maps) return SMA_ERR_ARG;
+  for (int t = 0; t < 3; ++t) {
+    const int ell = pr.level_ell[t], q = pr.level_q[t], p = pr.level_p[t];
+    const int32_t* map = pr.level_maps[t];
+    if (ell <= 0 || q <= 0 || p <= 0 || !map) return SMA_ERR_ARG;
+    if ((int64_t)p > (int64_t)ell * q) return SMA_ERR_STRUCT;
+    eta[t].assign(p, 0);
+    for (int64_t e = 0; e < (int64_t)ell * q; ++e) {
+      const int k = map[e];
+      if (k < -1 || k >= p) return SMA_ERR_STRUCT;
+      if (k >= 0) ++eta[t][k];
+    }
+    for (int k = 0; k < p; ++k)
+      if (eta[t][k] == 0) return SMA_ERR_STRUCT;
+  }
+  return SMA_OK;
+}
+
 sma_status validate_problem(const sma_problem& pr, std::vector<int64_t>& eta,
                             std::vector<int>& ra, std::vector<int>& rb) {
   if (pr.levels != 0 && pr.levels != 1) return SMA_ERR_UNSUPPORTED;
@@ -273,9 +317,75 @@ sma_status validate_problem(const sma_problem& pr, std::vector<int64_t>& eta,
 }
 
 template <typename T>
+sma_status setup_multilevel(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
+  auto& mem = h->mem;
+  std::vector<int64_t> eta[3];
+  SMA_TRY(validate_levels(pr, eta));
+  P.L = 3;
+  P.m = P.n = 1;
+  P.ell = P.q = 1;
+  int gdim = 1;
+  for (int t = 0; t < 3; ++t) {
+    P.lell[t] = pr.level_ell[t];
+    P.lq[t] = pr.level_q[t];
+    P.lp[t] = pr.level_p[t];
+    P.ell *= P.lell[t];
+    P.q *= P.lq[t];
+    gdim = P.lp[t] > gdim ? P.lp[t] : gdim;
+    P.lmap[t].assign(pr.level_maps[t], pr.level_maps[t] + (size_t)P.lell[t] * P.lq[t]);
+    std::vector<double> w(P.lp[t]), isq(P.lp[t]);
+    for (int k = 0; k < P.lp[t]; ++k) {
+      w[k] = std::sqrt((double)eta[t][k]);
+      isq[k] = 1.0 / w[k];
+    }
+    SMA_TRY(mem.alloc(&P.d_lmap[t], P.lmap[t].size()));
+    SMA_TRY(mem.alloc(&P.d_lw[t], P.lp[t]));
+    SMA_TRY(mem.alloc(&P.d_lisq[t], P.lp[t]));
+    SMA_TRY(mem.alloc(&P.Uml[t], (size_t)P.lp[t] * P.lp[t]));
+    SMA_CK(cudaMemcpy(P.d_lmap[t], P.lmap[t].data(), P.lmap[t].size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice));
+    SMA_CK(cudaMemcpy(P.d_lw[t], w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+    SMA_CK(cudaMemcpy(P.d_lisq[t], isq.data(), isq.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  P.p = P.lp[0] * P.lp[1] * P.lp[2];
+  const size_t np = (size_t)P.p;
+  P.gdim = gdim;
+  P.gstride = (size_t)gdim * gdim;
+  SMA_TRY(mem.alloc(&P.X, np));
+  SMA_TRY(mem.alloc(&P.X64, np));
+  SMA_TRY(mem.alloc(&P.Tt, np));
+  SMA_TRY(mem.alloc(&P.T1, np));
+  SMA_TRY(mem.alloc(&P.T2, np));
+  SMA_TRY(mem.alloc(&P.Gc, np));
+  SMA_TRY(mem.alloc(&P.Gcmp, np));
+  P.nparts = gather_parts(1, 1, P.p);
+  SMA_TRY(mem.alloc(&P.partial, P.nparts));
+  SMA_TRY(mem.alloc(&P.stats, 8));
+  SMA_TRY(mem.alloc(&P.iscal, 8));
+  SMA_TRY(mem.alloc(&P.status, 1));
+  SMA_TRY(mem.alloc(&P.gram, P.gstride * 3));
+  SMA_TRY(mem.alloc(&P.gvec, P.gstride * 3));
+  SMA_TRY(mem.alloc(&P.gsig, (size_t)gdim * 3));
+  SMA_TRY(mem.alloc(&P.suf, (size_t)(gdim + 1) * 3));
+  SMA_TRY(mem.alloc(&P.Wg, P.gstride * 2));
+  SMA_TRY(mem.alloc(&P.gW, P.gstride));
+  SMA_TRY(mem.alloc(&P.sweeps, 3));
+  SMA_TRY(mem.alloc(&P.ranks, 3));
+  SMA_TRY(mem.alloc(&P.off, 3));
+  SMA_TRY(mem.alloc(&P.orth, 3));
+  SMA_TRY(mem.alloc(&P.Gorth, P.gstride));
+  P.n_orth = 3;
+  SMA_CK(cudaMemset(P.stats, 0, 8 * sizeof(double)));
+  SMA_CK(cudaMemset(P.iscal, 0, 8 * sizeof(int)));
+  SMA_CK(cudaMemset(P.status, 0, sizeof(int)));
+  return SMA_OK;
+}
+
+template <typename T>
 sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   auto& mem = h->mem;
   const sma_options& o = h->opt;
+  if (o.decomp == SMA_HOSVD_MULTILEVEL) return setup_multilevel(h, P, pr);
   SMA_TRY(validate_problem(pr, P.eta, P.rep_a, P.rep_b));
   P.ell = pr.ell; P.q = pr.q; P.m = pr.m; P.n = pr.n; P.p = pr.p;
   P.map.assign(pr.block_map, pr.block_map + (size_t)pr.ell * pr.q);
@@ -675,9 +785,92 @@ sma_status compress_tucker(sma_ctx* h, Prob<T>& P) {
   return SMA_OK;
 }
 
+// Section 7: HOSVD of the weighted coefficient tensor of a three-level
+// structured matrix (m = n = 1), each mode with the budget tol^2 ||X||^2 / 3.
+template <typename T>
+sma_status compress_multilevel(sma_ctx* h, Prob<T>& P, const void* Ain) {
+  cudaStream_t st = h->st;
+  const int p1 = P.lp[0], p2 = P.lp[1], p3 = P.lp[2];
+  const int64_t np = P.p;
+  if (!Ain) return SMA_ERR_ARG;
+  const T* a = static_cast<const T*>(Ain);
+  stage_begin(h, SMA_STAGE_GATHER);
+  if (!is_device_ptr(Ain)) {
+    if (!P.stage) SMA_TRY(h->mem.alloc(&P.stage, (size_t)np));
+    SMA_CK(cudaMemcpyAsync(P.stage, a, np * sizeof(T), cudaMemcpyHostToDevice, st));
+    a = P.stage;
+  }
+  SMA_K(ml_gather<T>(a, P.d_lw[0], P.d_lw[1], P.d_lw[2], p1, p2, p3, P.X, P.partial, P.nparts, st));
+  SMA_K(finish_norm(P.partial, P.nparts, P.stats, st));
+  SMA_K(convert<double, T>(P.X, P.X64, np, st));
+  stage_end(h);
+  const double share = 1.0 / std::sqrt(3.0);
+  SMA_TRY(gram_factor(h, P, 0, p1, p2 * p3, 1, p1, 1, 0, share));                 // mode 1
+  SMA_TRY(gram_factor(h, P, 1, p2, p1, p1, 1, p3, (int64_t)p1 * p2, share));       // mode 2
+  SMA_TRY(gram_factor(h, P, 2, p3, p1 * p2, (int64_t)p1 * p2, 1, 1, 0, share));    // mode 3
+  stage_begin(h, SMA_STAGE_FACTORS);
+  for (int t = 0; t < 3; ++t)
+    SMA_K(convert<T, double>(P.gvec + P.gstride * t, P.Uml[t], (int64_t)P.lp[t] * P.lp[t], st));
+  const int* k1 = P.iscal + 2;
+  const int* k2 = P.iscal + 3;
+  const int* k3 = P.iscal + 4;
+  SMA_CK(cudaMemsetAsync(P.T1, 0, np * sizeof(T), st));
+  SMA_CK(cudaMemsetAsync(P.T2, 0, np * sizeof(T), st));
+  SMA_CK(cudaMemsetAsync(P.Gc, 0, np * sizeof(T), st));
+  {  // T1 = U1^T X_(1)  (p1 x p2 p3, leading k1 rows)
+    GemmParams<T> g;
+    g.M = p1; g.N = p2 * p3; g.K = p1; g.dM = k1; g.dstride = 0;
+    g.A = P.Uml[0]; g.a_rs = p1; g.a_cs = 1;
+    g.B = P.X; g.b_rs = 1; g.b_cs = p1;
+    g.C = P.T1; g.c_rs = 1; g.c_cs = p1;
+    SMA_K(contract<T>(h, g));
+  }
+  {  // T2[:, :, i3] = T1[:, :, i3] U2
+    GemmParams<T> g;
+    g.M = p1; g.N = p2; g.K = p2; g.dM = k1; g.dN = k2; g.dstride = 0;
+    g.A = P.T1; g.a_rs = 1; g.a_cs = p1; g.a_b1 = (int64_t)p1 * p2;
+    g.B = P.Uml[1]; g.b_rs = 1; g.b_cs = p2;
+    g.C = P.T2; g.c_rs = 1; g.c_cs = p1; g.c_b1 = (int64_t)p1 * p2;
+    g.nb1 = p3;
+    SMA_K(contract<T>(h, g));
+  }
+  {  // G = T2_(3)^T ... as (p1 p2) x p3 times U3
+    GemmParams<T> g;
+    g.M = p1 * p2; g.N = p3; g.K = p3; g.dN = k3; g.dstride = 0;
+    g.A = P.T2; g.a_rs = 1; g.a_cs = (int64_t)p1 * p2;
+    g.B = P.Uml[2]; g.b_rs = 1; g.b_cs = p3;
+    g.C = P.Gc; g.c_rs = 1; g.c_cs = (int64_t)p1 * p2;
+    SMA_K(contract<T>(h, g));
+  }
+  SMA_TRY(make_T(h, P));
+  SMA_K(residual_norm2<T>(P.X, P.Tt, np, P.partial, P.nparts, P.stats + 1, st));
+  stage_end(h);
+  stage_begin(h, SMA_STAGE_REPORT);
+  for (int t = 0; t < 3; ++t) {
+    const int rows = P.lp[t];
+    GemmParams<T> go;
+    go.M = rows; go.N = rows; go.K = rows; go.dM = P.iscal + 2 + t; go.dN = P.iscal + 2 + t;
+    go.dstride = 0;
+    go.A = P.Uml[t]; go.a_rs = rows; go.a_cs = 1;
+    go.B = P.Uml[t]; go.b_rs = 1; go.b_cs = rows;
+    go.C = P.Gorth; go.c_rs = 1; go.c_cs = rows;
+    SMA_K(gemm<T>(go, st));
+    SMA_K(orth_defect<T>(P.Gorth, rows, 1, P.iscal + 2 + t, nullptr, P.orth + t, st));
+  }
+  stage_end(h);
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
   SMA_CK(cudaMemsetAsync(P.status, 0, sizeof(int), h->st));
+  if (P.L == 3) {
+    SMA_TRY(compress_multilevel(h, P, A));
+    P.compressed = true;
+    P.ml_valid = false;
+    P.h_iscal[0] = -1;
+    return SMA_OK;
+  }
   SMA_TRY(do_gather(h, P, A, lda));
   if (h->opt.decomp == SMA_TSVDM) SMA_TRY(compress_tsvdm(h, P));
   else SMA_TRY(compress_tucker(h, P));
@@ -715,6 +908,11 @@ sma_status read_result(sma_ctx* h, Prob<T>& P, sma_result* r) {
     err2 = stats[1];
     r->total_rank = iscal[0];
     r->n_kron_terms = iscal[1];
+  } else if (d == SMA_HOSVD_MULTILEVEL) {
+    err2 = stats[1];
+    for (int t = 0; t < 3; ++t) r->ranks[t] = iscal[2 + t];
+    r->total_rank = iscal[2] * iscal[3] * iscal[4];
+    r->n_kron_terms = r->total_rank;
   } else if (d == SMA_TUCKER_BLOCKMODE) {
     err2 = stats[1];
     r->ranks[0] = iscal[2];
@@ -810,6 +1008,94 @@ bool tc_apply<float>(sma_ctx* h, Prob<float>& P, const float* X, int64_t ldx, fl
   return true;
 }
 
+// Section 7.4 matvec y = sum_j G_j (C1_j1 (x) C2_j2 (x) C3_j3) x for volumes
+// x (level-3 index fastest), as four strided batched GEMMs:
+//   S1  U3x[(a3 + l3 j3), (b2, b1)]         = sum_b3 C3_j3[a3, b3] x[b3, b2, b1]
+//   S2  V[a3 + l3 (j1 + k1 j2), (b2, b1)]   = sum_j3 G[j1, j2, j3] U3x[(a3 + l3 j3), (b2, b1)]
+//   S3  W[(a3 + l3 j1), b1, a2]             = sum_{j2, b2} C2_j2[a2, b2] V[...]
+//   S4  y[a3, a2, a1]                       = sum_{j1, b1} C1_j1[a1, b1] W[...]
+// with C3 stacked ((l3 k3) x q3) and C1, C2 interleaved (l_t x (k_t q_t),
+// column j + k_t b) so that every contraction runs over one stride.
+template <typename T>
+sma_status apply_multilevel(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Y, int64_t ldy,
+                            int nv) {
+  cudaStream_t st = h->st;
+  if (P.h_iscal[0] < 0) {
+    SMA_CK(cudaStreamSynchronize(st));
+    SMA_CK(cudaMemcpy(P.h_iscal, P.iscal, sizeof(P.h_iscal), cudaMemcpyDeviceToHost));
+  }
+  const int k1 = P.h_iscal[2], k2 = P.h_iscal[3], k3 = P.h_iscal[4];
+  const int l1 = P.lell[0], l2 = P.lell[1], l3 = P.lell[2];
+  const int q1 = P.lq[0], q2 = P.lq[1], q3 = P.lq[2];
+  const int p1 = P.lp[0], p2 = P.lp[1], p3 = P.lp[2];
+  if (k1 <= 0 || k2 <= 0 || k3 <= 0) {
+    SMA_CK(cudaMemset2DAsync(Y, ldy * sizeof(T), 0, (size_t)l1 * l2 * l3 * sizeof(T), nv, st));
+    return SMA_OK;
+  }
+  if (!P.ml_valid) {
+    if (!P.C1i) {
+      SMA_TRY(h->mem.alloc(&P.C1i, (size_t)l1 * q1 * p1));
+      SMA_TRY(h->mem.alloc(&P.C2i, (size_t)l2 * q2 * p2));
+      SMA_TRY(h->mem.alloc(&P.C3st, (size_t)l3 * q3 * p3));
+    }
+    SMA_K(struct_strided<T>(P.d_lmap[2], P.d_lisq[2], l3, q3, P.Uml[2], p3, k3, 1,
+                            (int64_t)l3 * k3, l3, P.C3st, st));
+    SMA_K(struct_strided<T>(P.d_lmap[1], P.d_lisq[1], l2, q2, P.Uml[1], p2, k2, 1,
+                            (int64_t)l2 * k2, l2, P.C2i, st));
+    SMA_K(struct_strided<T>(P.d_lmap[0], P.d_lisq[0], l1, q1, P.Uml[0], p1, k1, 1,
+                            (int64_t)l1 * k1, l1, P.C1i, st));
+    for (int j3 = 0; j3 < k3; ++j3)
+      SMA_CK(cudaMemcpy2DAsync(P.Gcmp + (size_t)k1 * k2 * j3, k1 * sizeof(T),
+                               P.Gc + (size_t)p1 * p2 * j3, p1 * sizeof(T), k1 * sizeof(T), k2,
+                               cudaMemcpyDeviceToDevice, st));
+    P.ml_valid = true;
+  }
+  const int64_t n21 = (int64_t)q2 * q1;
+  SMA_TRY(grow(h, &P.U3x, &P.U3x_elems, (size_t)l3 * k3 * n21 * nv));
+  SMA_TRY(grow(h, &P.Vml, &P.Vml_elems, (size_t)l3 * k1 * k2 * n21 * nv));
+  SMA_TRY(grow(h, &P.Wml, &P.Wml_elems, (size_t)l3 * k1 * q1 * l2 * nv));
+  {  // S1
+    GemmParams<T> g;
+    g.M = l3 * k3; g.N = (int)n21; g.K = q3;
+    g.A = P.C3st; g.a_rs = 1; g.a_cs = (int64_t)l3 * k3;
+    g.B = X; g.b_rs = 1; g.b_cs = q3; g.b_b2 = ldx;
+    g.C = P.U3x; g.c_rs = 1; g.c_cs = (int64_t)l3 * k3; g.c_b2 = (int64_t)l3 * k3 * n21;
+    g.nb2 = nv;
+    SMA_K(contract<T>(h, g));
+  }
+  {  // S2 (batched over a3)
+    GemmParams<T> g;
+    g.M = k1 * k2; g.N = (int)(n21 * nv); g.K = k3;
+    g.A = P.Gcmp; g.a_rs = 1; g.a_cs = (int64_t)k1 * k2;
+    g.B = P.U3x; g.b_rs = l3; g.b_cs = (int64_t)l3 * k3; g.b_b1 = 1;
+    g.C = P.Vml; g.c_rs = l3; g.c_cs = (int64_t)l3 * k1 * k2; g.c_b1 = 1;
+    g.nb1 = l3;
+    SMA_K(contract<T>(h, g));
+  }
+  {  // S3 (batched over b1, volume)
+    GemmParams<T> g;
+    g.M = l3 * k1; g.N = l2; g.K = k2 * q2;
+    g.A = P.Vml; g.a_rs = 1; g.a_cs = (int64_t)l3 * k1;
+    g.a_b1 = (int64_t)l3 * k1 * k2 * q2; g.a_b2 = (int64_t)l3 * k1 * k2 * n21;
+    g.B = P.C2i; g.b_rs = l2; g.b_cs = 1;
+    g.C = P.Wml; g.c_rs = 1; g.c_cs = (int64_t)l3 * k1 * q1;
+    g.c_b1 = (int64_t)l3 * k1; g.c_b2 = (int64_t)l3 * k1 * q1 * l2;
+    g.nb1 = q1; g.nb2 = nv;
+    SMA_K(contract<T>(h, g));
+  }
+  {  // S4 (batched over a2, volume)
+    GemmParams<T> g;
+    g.M = l3; g.N = l1; g.K = k1 * q1;
+    g.A = P.Wml; g.a_rs = 1; g.a_cs = l3;
+    g.a_b1 = (int64_t)l3 * k1 * q1; g.a_b2 = (int64_t)l3 * k1 * q1 * l2;
+    g.B = P.C1i; g.b_rs = l1; g.b_cs = 1;
+    g.C = Y; g.c_rs = 1; g.c_cs = (int64_t)l3 * l2; g.c_b1 = l3; g.c_b2 = ldy;
+    g.nb1 = l2; g.nb2 = nv;
+    SMA_K(contract<T>(h, g));
+  }
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status apply_one(sma_ctx* h, Prob<T>& P, const void* Xin, int64_t ldx, void* Yout,
                      int64_t ldy, int nrhs) {
@@ -838,7 +1124,9 @@ sma_status apply_one(sma_ctx* h, Prob<T>& P, const void* Xin, int64_t ldx, void*
   }
   const sma_decomp d = h->opt.decomp;
   stage_begin(h, SMA_STAGE_APPLY);
-  if (d == SMA_TSVDM || d == SMA_TUCKER_BLOCKMODE) {
+  if (d == SMA_HOSVD_MULTILEVEL) {
+    SMA_TRY(apply_multilevel(h, P, X, ldx, Yd, ldyd, nrhs));
+  } else if (d == SMA_TSVDM || d == SMA_TUCKER_BLOCKMODE) {
     // Kronecker sum Y = sum_j D_j X C_j^T (Section 2.2 vec identity).
     if (P.h_iscal[0] < 0) {
       SMA_CK(cudaStreamSynchronize(st));
@@ -923,6 +1211,35 @@ sma_status make_T(sma_ctx* h, Prob<T>& P) {
   const int m = P.m, n = P.n, p = P.p;
   const int64_t mn = (int64_t)m * n;
   const sma_decomp d = h->opt.decomp;
+  if (d == SMA_HOSVD_MULTILEVEL) {
+    const int p1 = P.lp[0], p2 = P.lp[1], p3 = P.lp[2];
+    {  // T1 = G_(3) U3^T as (p1 p2) x p3, K = k3
+      GemmParams<T> g;
+      g.M = p1 * p2; g.N = p3; g.K = p3; g.dK = P.iscal + 4; g.dstride = 0;
+      g.A = P.Gc; g.a_rs = 1; g.a_cs = (int64_t)p1 * p2;
+      g.B = P.Uml[2]; g.b_rs = p3; g.b_cs = 1;
+      g.C = P.T1; g.c_rs = 1; g.c_cs = (int64_t)p1 * p2;
+      SMA_K(gemm<T>(g, st));
+    }
+    {  // T2[:, :, i3] = T1[:, :, i3] U2^T, K = k2
+      GemmParams<T> g;
+      g.M = p1; g.N = p2; g.K = p2; g.dK = P.iscal + 3; g.dstride = 0;
+      g.A = P.T1; g.a_rs = 1; g.a_cs = p1; g.a_b1 = (int64_t)p1 * p2;
+      g.B = P.Uml[1]; g.b_rs = p2; g.b_cs = 1;
+      g.C = P.T2; g.c_rs = 1; g.c_cs = p1; g.c_b1 = (int64_t)p1 * p2;
+      g.nb1 = p3;
+      SMA_K(gemm<T>(g, st));
+    }
+    {  // T = U1 T2_(1), K = k1
+      GemmParams<T> g;
+      g.M = p1; g.N = p2 * p3; g.K = p1; g.dK = P.iscal + 2; g.dstride = 0;
+      g.A = P.Uml[0]; g.a_rs = 1; g.a_cs = p1;
+      g.B = P.T2; g.b_rs = 1; g.b_cs = p1;
+      g.C = P.Tt; g.c_rs = 1; g.c_cs = p1;
+      SMA_K(gemm<T>(g, st));
+    }
+    return SMA_OK;
+  }
   if (d == SMA_TSVDM) {
     // T = Dtrunc x3 M^T: T_mat = D_mat M
     GemmParams<T> g;
@@ -980,8 +1297,21 @@ sma_status reconstruct_one(sma_ctx* h, Prob<T>& P, void* Ahat, int64_t ld) {
     }
   }
   ++h->launches;
-  cudaError_t e = scatter_ME<T>(P.d_map, P.d_isq, P.ell, P.q, m, n, P.Tt, host ? tmpA : dst,
-                                host ? rows : ld, st);
+  cudaError_t e;
+  if (P.L == 3) {
+    MlMaps mp;
+    for (int t = 0; t < 3; ++t) {
+      mp.map[t] = P.d_lmap[t];
+      mp.isq[t] = P.d_lisq[t];
+      mp.ell[t] = P.lell[t];
+      mp.q[t] = P.lq[t];
+      mp.p[t] = P.lp[t];
+    }
+    e = ml_scatter<T>(mp, P.Tt, host ? tmpA : dst, host ? rows : ld, st);
+  } else {
+    e = scatter_ME<T>(P.d_map, P.d_isq, P.ell, P.q, m, n, P.Tt, host ? tmpA : dst,
+                      host ? rows : ld, st);
+  }
   if (e == cudaSuccess && host) {
     e = cudaMemcpy2DAsync(dst, ld * sizeof(T), tmpA, rows * sizeof(T), rows * sizeof(T), cols,
                           cudaMemcpyDeviceToHost, st);
@@ -1003,13 +1333,15 @@ sma_status export_one(sma_ctx* h, Prob<T>& P, int which, void* dst, int64_t coun
     case 0: src = P.X; n = mnp; break;
     case 1: src = P.Xh; n = P.Xh ? mnp : 0; break;
     case 2:
-      if (h->opt.decomp == SMA_TSVDM) { src = P.sigma; n = (int64_t)P.rc * P.p; }
+      if (h->opt.decomp == SMA_HOSVD_MULTILEVEL) { src = P.gsig; n = (int64_t)P.gdim * 3; }
+      else if (h->opt.decomp == SMA_TSVDM) { src = P.sigma; n = (int64_t)P.rc * P.p; }
       else { src = P.gsig; n = h->opt.decomp == SMA_TUCKER_BLOCKMODE ? P.p : P.m; }
       es = sizeof(double);
       break;
     case 3: src = P.Tt; n = mnp; break;
     case 4:
-      if (h->opt.decomp == SMA_TUCKER_BLOCKMODE) { src = P.F1; n = (int64_t)P.p * P.p; }
+      if (h->opt.decomp == SMA_HOSVD_MULTILEVEL) { src = P.Uml[0]; n = (int64_t)P.lp[0] * P.lp[0]; }
+      else if (h->opt.decomp == SMA_TUCKER_BLOCKMODE) { src = P.F1; n = (int64_t)P.p * P.p; }
       else if (h->opt.decomp != SMA_TSVDM) { src = P.F1; n = (int64_t)P.m * P.m; }
       break;
     default: return SMA_ERR_ARG;
@@ -1032,7 +1364,7 @@ sma_status ranks_one(sma_ctx* h, Prob<T>& P, int32_t* out, int32_t* count) {
     int isc[8];
     SMA_CK(cudaMemcpy(isc, P.iscal, sizeof(isc), cudaMemcpyDeviceToHost));
     const sma_decomp d = h->opt.decomp;
-    const int c = d == SMA_TUCKER_BLOCKMODE ? 1 : 2;
+    const int c = d == SMA_TUCKER_BLOCKMODE ? 1 : (d == SMA_HOSVD_MULTILEVEL ? 3 : 2);
     for (int i = 0; i < c; ++i) out[i] = (d == SMA_TUCKER_SHARED_U) ? isc[2] : isc[2 + i];
     *count = c;
   }
@@ -1074,11 +1406,16 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   if ((int)opt->mkind < 0 || opt->mkind > SMA_M_USER) return SMA_ERR_ARG;
   if (opt->layout != SMA_INPUT_DENSE && opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
   if (opt->fixed_rank < 0 || !(opt->rel_tol >= 0.0)) return SMA_ERR_ARG;
-  if (opt->decomp == SMA_HOSVD_MULTILEVEL) return SMA_ERR_UNSUPPORTED;
   // host-side validation of every problem before any CUDA call
   for (int i = 0; i < nprob; ++i) {
     std::vector<int64_t> eta;
     std::vector<int> ra, rb;
+    if (opt->decomp == SMA_HOSVD_MULTILEVEL) {
+      std::vector<int64_t> leta[3];
+      SMA_TRY(validate_levels(prob[i], leta));
+      if (opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
+      continue;
+    }
     SMA_TRY(validate_problem(prob[i], eta, ra, rb));
     if (opt->decomp == SMA_TUCKER_SHARED_U && prob[i].m != prob[i].n) return SMA_ERR_ARG;
     if (opt->decomp == SMA_TSVDM && opt->mkind == SMA_M_USER && !opt->M_user) return SMA_ERR_ARG;

@@ -48,8 +48,8 @@ __device__ __forceinline__ Pair rr_pair(int k, int t, int c) {
 // Rotation angle for the pair with squared norms al, be and inner product
 // ga; false when the pair is already orthogonal to tolerance.
 __device__ __forceinline__ bool angle_fp64(double al, double be, double ga, double tol,
-                                           double& c, double& s) {
-  if (!(fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
+                                           double floor_, double& c, double& s) {
+  if (!(fabs(ga) > tol * sqrt(al) * sqrt(be)) || !(fabs(ga) > floor_)) return false;
   const double zeta = (be - al) / (2.0 * ga);
   const double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
                                         : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -61,20 +61,20 @@ __device__ __forceinline__ bool angle_fp64(double al, double be, double ga, doub
 template <typename T> struct Angle;
 template <> struct Angle<double> {
   static __device__ __forceinline__ bool get(double al, double be, double ga, double tol,
-                                             double& c, double& s) {
-    return angle_fp64(al, be, ga, tol, c, s);
+                                             double floor_, double& c, double& s) {
+    return angle_fp64(al, be, ga, tol, floor_, c, s);
   }
 };
 template <> struct Angle<float> {
   // fp32 angle; fp64 for nearly parallel columns (|cos| > 0.99), where the
   // difference of the squared norms loses most of its fp32 digits
   static __device__ __forceinline__ bool get(float al, float be, float ga, double tol,
-                                             float& c, float& s) {
+                                             double floor_, float& c, float& s) {
     const float nrm = sqrtf(al) * sqrtf(be);
-    if (!(fabsf(ga) > (float)tol * nrm)) return false;
+    if (!(fabsf(ga) > (float)tol * nrm) || !((double)fabsf(ga) > floor_)) return false;
     if (fabsf(ga) > 0.99f * nrm) {
       double cd = 1.0, sd = 0.0;
-      angle_fp64(al, be, ga, 0.0, cd, sd);
+      angle_fp64(al, be, ga, 0.0, 0.0, cd, sd);
       c = (float)cd;
       s = (float)sd;
       return true;
@@ -108,9 +108,13 @@ template <> struct CacheRows<double> { static constexpr int v = 16; };
 // Rotate the stacked columns at shared-memory slots a and b (group of g
 // lanes; every lane of the warp must call this together).  Dot products over
 // rows [0, mm), rotation over rows [0, len).  Returns true if rotated.
+// A pair is left alone when it is orthogonal to the relative tolerance tol or
+// when its inner product is below floor_ = eps^2 ||W||_F^2, the rounding
+// level of the whole slice (columns that are numerically zero).
 template <typename T>
 __device__ __forceinline__ bool rotate_pair(T* S, int ldS, int a, int b, bool active,
-                                            int mm, int len, int lane, int g, double tol) {
+                                            int mm, int len, int lane, int g, double tol,
+                                            double floor_) {
   constexpr int NR = CacheRows<T>::v;
   T xr[NR], yr[NR];
   T al = T(0), be = T(0), ga = T(0);
@@ -144,7 +148,7 @@ __device__ __forceinline__ bool rotate_pair(T* S, int ldS, int a, int b, bool ac
   }
   if (!active) return false;
   T c, s;
-  if (!Angle<T>::get(al, be, ga, tol, c, s)) return false;
+  if (!Angle<T>::get(al, be, ga, tol, floor_, c, s)) return false;
 #pragma unroll
   for (int i = 0; i < NR; ++i) {
     const int r = lane + i * g;
@@ -244,16 +248,21 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
   const int nb = in_smem ? 1 : (rc + bc - 1) / bc;
 
   // load the stacked columns [slice; I] into shared memory or the workspace
+  __shared__ double red[32];
+  double floor_ = 0.0;
   {
     const int tot = len * rc;
+    double nrm2 = 0.0;
     for (int e = tid; e < tot; e += NTh) {
       int r, c;
       if (P.trans) { c = e % rc; r = e / rc; } else { r = e % len; c = e / len; }
       const T v = load_work(src, P.m, P.trans, mm, r, c);
+      if (r < mm) nrm2 = fma((double)v, (double)v, nrm2);
       if (in_smem) S[(int64_t)c * ldS + r] = v;
       else W[r + (int64_t)c * len] = v;
     }
-    __syncthreads();
+    nrm2 = block_sum(nrm2, red);
+    floor_ = Eps<T>::v * Eps<T>::v * nrm2;
   }
   int sweeps_used = 0;
   bool converged = (rc <= 1);
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
         for (int base = 0; base < ph.npairs; base += ngroups) {
           int a = 0, b = 0;
           const bool act = phase_pair(ph, t, base + kslot, a, b);
-          rot |= rotate_pair(S, ldS, a, b, act, mm, len, lane, g, P.tol);
+          rot |= rotate_pair(S, ldS, a, b, act, mm, len, lane, g, P.tol, floor_);
         }
         __syncthreads();
       }

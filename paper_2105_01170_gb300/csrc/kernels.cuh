@@ -71,6 +71,25 @@ cudaError_t scatter_ME(const int* map, const double* inv_sqrt_eta, int ell, int 
 template <typename T>
 cudaError_t orth_defect(const T* Gm, int rc, int p, const int* ranks, const double* scale,
                         double* out, cudaStream_t st);
+// ---- multilevel (three levels, m = n = 1) ---------------------------------
+struct MlMaps {
+  const int* map[3];
+  const double* isq[3];
+  int ell[3], q[3], p[3];
+};
+// X[i1 + p1 (i2 + p2 i3)] = w1[i1] w2[i2] w3[i3] a[...] and per-CTA ||X||^2
+// partial sums (nparts CTAs, as for gather).
+template <typename T>
+cudaError_t ml_gather(const T* a, const double* w1, const double* w2, const double* w3, int p1,
+                      int p2, int p3, T* X, double* partial, int nparts, cudaStream_t st);
+// out[a s_a + b s_b + j s_j] = coef[map(a,b) + p j] / sqrt(eta), j < nterms.
+template <typename T>
+cudaError_t struct_strided(const int* map, const double* isq, int ell, int q, const T* coef, int p,
+                           int nterms, int64_t s_a, int64_t s_b, int64_t s_j, T* out,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t ml_scatter(const MlMaps& mp, const T* Tt, T* Ahat, int64_t ld, cudaStream_t st);
+
 // copy and precision conversion helpers
 template <typename TD, typename TS>
 cudaError_t convert(const TS* src, TD* dst, int64_t count, cudaStream_t st);

@@ -276,6 +276,73 @@ __global__ void convert_kernel(const TS* __restrict__ s, TD* __restrict__ d, int
     d[e] = (TD)s[e];
 }
 
+// ---- multilevel (Section 7.2): X[i1 + p1 (i2 + p2 i3)] = w1 w2 w3 a[...] ----
+template <typename T>
+__global__ void ml_gather_kernel(const T* __restrict__ a, const double* __restrict__ w1,
+                                 const double* __restrict__ w2, const double* __restrict__ w3,
+                                 int p1, int p2, int p3, T* __restrict__ X,
+                                 double* __restrict__ partial) {
+  __shared__ double red[32];
+  const int64_t total = (int64_t)p1 * p2 * p3;
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i1 = (int)(e % p1);
+    const int i2 = (int)((e / p1) % p2);
+    const int i3 = (int)(e / ((int64_t)p1 * p2));
+    const T v = (T)((double)a[e] * (w1[i1] * w2[i2] * w3[i3]));
+    X[e] = v;
+    acc = fma((double)v, (double)v, acc);
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// out[a s_a + b s_b + j s_j] = coef[k + p j] / sqrt(eta_k), k = map(a, b)
+// (0 where map(a, b) < 0), for j < nterms: struct_E of coefficient columns in
+// an arbitrary (stacked / interleaved) layout.
+template <typename T>
+__global__ void struct_strided_kernel(const int* __restrict__ map, const double* __restrict__ isq,
+                                      int ell, int q, const T* __restrict__ coef, int p,
+                                      int nterms, int64_t s_a, int64_t s_b, int64_t s_j,
+                                      T* __restrict__ out) {
+  const int64_t per = (int64_t)ell * q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < per * nterms;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / per);
+    const int pos = (int)(e - (int64_t)j * per);
+    const int a = pos % ell, b = pos / ell;
+    const int k = map[pos];
+    out[a * s_a + b * s_b + j * s_j] = (k >= 0) ? (T)((double)coef[k + (int64_t)p * j] * isq[k]) : T(0);
+  }
+}
+
+// dense A_hat of a three-level structured matrix (m = n = 1) from the
+// approximation tensor T (p1 x p2 x p3): entry ((a1,a2,a3), (b1,b2,b3)),
+// row index a3 + l3 (a2 + l2 a1), column b3 + q3 (b2 + q2 b1).
+template <typename T>
+__global__ void ml_scatter_kernel(MlMaps mp, const T* __restrict__ Tt, T* __restrict__ Ahat,
+                                  int64_t ld) {
+  const int64_t rows = (int64_t)mp.ell[0] * mp.ell[1] * mp.ell[2];
+  const int64_t cols = (int64_t)mp.q[0] * mp.q[1] * mp.q[2];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = e / rows, row = e - col * rows;
+    const int a3 = (int)(row % mp.ell[2]), a2 = (int)((row / mp.ell[2]) % mp.ell[1]),
+              a1 = (int)(row / ((int64_t)mp.ell[2] * mp.ell[1]));
+    const int b3 = (int)(col % mp.q[2]), b2 = (int)((col / mp.q[2]) % mp.q[1]),
+              b1 = (int)(col / ((int64_t)mp.q[2] * mp.q[1]));
+    const int k1 = mp.map[0][a1 + mp.ell[0] * b1];
+    const int k2 = mp.map[1][a2 + mp.ell[1] * b2];
+    const int k3 = mp.map[2][a3 + mp.ell[2] * b3];
+    T v = T(0);
+    if (k1 >= 0 && k2 >= 0 && k3 >= 0)
+      v = (T)((double)Tt[k1 + (int64_t)mp.p[0] * (k2 + (int64_t)mp.p[1] * k3)] * mp.isq[0][k1] *
+              mp.isq[1][k2] * mp.isq[2][k3]);
+    Ahat[row + col * ld] = v;
+  }
+}
+
 inline unsigned grid_for(int64_t work, int threads, int64_t cap = 152 * 32) {
   int64_t g = (work + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -361,6 +428,41 @@ cudaError_t convert(const TS* src, TD* dst, int64_t count, cudaStream_t st) {
   convert_kernel<TD, TS><<<grid_for(count, 256), 256, 0, st>>>(src, dst, count);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t ml_gather(const T* a, const double* w1, const double* w2, const double* w3, int p1,
+                      int p2, int p3, T* X, double* partial, int nparts, cudaStream_t st) {
+  ml_gather_kernel<T><<<nparts, GATHER_THREADS, 0, st>>>(a, w1, w2, w3, p1, p2, p3, X, partial);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t struct_strided(const int* map, const double* isq, int ell, int q, const T* coef, int p,
+                           int nterms, int64_t s_a, int64_t s_b, int64_t s_j, T* out,
+                           cudaStream_t st) {
+  const int64_t work = (int64_t)ell * q * nterms;
+  if (work <= 0) return cudaSuccess;
+  struct_strided_kernel<T><<<grid_for(work, 256), 256, 0, st>>>(map, isq, ell, q, coef, p, nterms,
+                                                                  s_a, s_b, s_j, out);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t ml_scatter(const MlMaps& mp, const T* Tt, T* Ahat, int64_t ld, cudaStream_t st) {
+  const int64_t work = (int64_t)mp.ell[0] * mp.ell[1] * mp.ell[2] * mp.q[0] * mp.q[1] * mp.q[2];
+  ml_scatter_kernel<T><<<grid_for(work, 256), 256, 0, st>>>(mp, Tt, Ahat, ld);
+  return cudaGetLastError();
+}
+template cudaError_t ml_gather<float>(const float*, const double*, const double*, const double*, int,
+                                      int, int, float*, double*, int, cudaStream_t);
+template cudaError_t ml_gather<double>(const double*, const double*, const double*, const double*,
+                                       int, int, int, double*, double*, int, cudaStream_t);
+template cudaError_t struct_strided<float>(const int*, const double*, int, int, const float*, int,
+                                           int, int64_t, int64_t, int64_t, float*, cudaStream_t);
+template cudaError_t struct_strided<double>(const int*, const double*, int, int, const double*,
+                                            int, int, int64_t, int64_t, int64_t, double*,
+                                            cudaStream_t);
+template cudaError_t ml_scatter<float>(const MlMaps&, const float*, float*, int64_t, cudaStream_t);
+template cudaError_t ml_scatter<double>(const MlMaps&, const double*, double*, int64_t,
+                                        cudaStream_t);
 
 template cudaError_t gather<double, double>(const double*, int64_t, const int64_t*, const double*,
                                             int, int, int, double*, double*, cudaStream_t);
