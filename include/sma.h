@@ -121,6 +121,11 @@ typedef struct {
   int32_t max_sweeps;     /* Jacobi sweep limit (0 = 30)                        */
   void* stream;           /* cudaStream_t                                       */
   int32_t profile;        /* != 0: record per-stage CUDA events (sma_profile)   */
+  int32_t graph;          /* != 0: capture sma_compress into a CUDA graph on the
+                             second call with the same A pointers and leading
+                             dimensions, and replay it while they are unchanged
+                             (needs a non-NULL stream; stage timing is then
+                             reported for the whole compression only)          */
 } sma_options;
 
 typedef struct {
@@ -147,7 +152,8 @@ sma_status sma_create(sma_handle* h, const sma_problem* probs, int32_t nprob,
 
 /* Steps (2)-(5) for every problem: A[i] points to problem i's input (layout
  * per options, element type per precision), lda[i] its leading dimension.
- * Enqueued on the handle's stream.  If res is non-NULL the call waits for the
+ * Enqueued on the handle's stream.  With several t-SVDM problems the slice
+ * SVDs of all problems run in one launch per distinct slice size.  If res is non-NULL the call waits for the
  * stream and fills res[0..nprob-1]; with res == NULL it returns at once and
  * results are read later with sma_get_result.
  * Errors: SMA_ERR_ARG (NULL A, lda too small), SMA_ERR_CUDA; device-side

@@ -193,6 +193,15 @@ struct Prob {
   int h_iscal[8] = {0};
 };
 
+// Slices of one size across all problems: one batched Jacobi launch.
+template <typename T>
+struct SvdBin {
+  int m = 0, n = 0, count = 0;
+  JacobiPlan jp{};
+  SliceDesc<T>* desc = nullptr;   // device
+  T* W = nullptr;                 // block-mode workspace
+};
+
 }  // namespace
 
 struct sma_ctx {
@@ -204,6 +213,14 @@ struct sma_ctx {
   DevBuf mem;
   std::vector<Prob<double>> p64;
   std::vector<Prob<float>> p32;
+  std::vector<SvdBin<double>> bins64;
+  std::vector<SvdBin<float>> bins32;
+  // CUDA graph of sma_compress (options.graph)
+  std::vector<const void*> warm_ptrs, graph_ptrs;
+  std::vector<int64_t> warm_lda, graph_lda;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_launches = 0;
+  bool capturing = false;
   // profiling: CUDA events around each stage on the handle's stream
   bool prof = false;
   struct Pend {
@@ -219,6 +236,7 @@ struct sma_ctx {
   int64_t launches = 0;
   ~sma_ctx() {
     for (cudaEvent_t e : ev_all) cudaEventDestroy(e);
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
   }
 };
 
@@ -240,14 +258,14 @@ cudaEvent_t ev_get(sma_ctx* h) {
 }
 
 void stage_begin(sma_ctx* h, int s) {
-  if (!h->prof) return;
+  if (!h->prof || h->capturing) return;
   h->cur_a = ev_get(h);
   if (h->cur_a) cudaEventRecord(h->cur_a, h->st);
   h->cur_stage = h->cur_a ? s : -1;
 }
 
 void stage_end(sma_ctx* h) {
-  if (!h->prof || h->cur_stage < 0) return;
+  if (!h->prof || h->capturing || h->cur_stage < 0) return;
   cudaEvent_t b = ev_get(h);
   if (b) {
     cudaEventRecord(b, h->st);
@@ -269,6 +287,12 @@ template <>
 std::vector<Prob<double>>& probs<double>(sma_ctx* h) { return h->p64; }
 template <>
 std::vector<Prob<float>>& probs<float>(sma_ctx* h) { return h->p32; }
+template <typename T>
+std::vector<SvdBin<T>>& bins(sma_ctx* h);
+template <>
+std::vector<SvdBin<double>>& bins<double>(sma_ctx* h) { return h->bins64; }
+template <>
+std::vector<SvdBin<float>>& bins<float>(sma_ctx* h) { return h->bins32; }
 
 // Section 7.2: one map per level; every index of level t occurs.
 sma_status validate_levels(const sma_problem& pr, std::vector<int64_t> eta[3]) {
@@ -556,10 +580,9 @@ cudaError_t contract<float>(sma_ctx* h, const GemmParams<float>& g) {
 // t-SVDM (steps 2-5)
 // ---------------------------------------------------------------------------
 template <typename T>
-sma_status compress_tsvdm(sma_ctx* h, Prob<T>& P) {
-  cudaStream_t st = h->st;
-  const int m = P.m, n = P.n, p = P.p, mm = P.mm, rc = P.rc;
-  const int64_t mn = (int64_t)m * n;
+sma_status tsvdm_pre(sma_ctx* h, Prob<T>& P) {
+  const int p = P.p;
+  const int64_t mn = (int64_t)P.m * P.n;
   // Xhat = X x3 M:  Xhat_mat (mn x p) = X_mat (mn x p) * M^T
   stage_begin(h, SMA_STAGE_TRANSFORM);
   {
@@ -571,15 +594,28 @@ sma_status compress_tsvdm(sma_ctx* h, Prob<T>& P) {
     SMA_K(contract<T>(h, g));
   }
   stage_end(h);
-  // per-slice SVD
+  return SMA_OK;
+}
+
+template <typename T>
+JacobiParams<T> jacobi_params(sma_ctx* h, const JacobiPlan& jp) {
+  JacobiParams<T> J;
+  J.mm = jp.mm; J.rc = jp.rc; J.trans = jp.trans; J.ldS = jp.ldS; J.bcols = jp.bcols;
+  J.g = jp.g; J.sort_n = jp.sort_n;
+  J.max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
+  J.tol = 4.0 * std::sqrt((double)jp.mm) * Eps<T>::v;
+  return J;
+}
+
+template <typename T>
+sma_status tsvdm_svd(sma_ctx* h, Prob<T>& P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p, mm = P.mm, rc = P.rc;
+  const int64_t mn = (int64_t)m * n;
   stage_begin(h, SMA_STAGE_SVD);
   {
-    JacobiParams<T> J;
+    JacobiParams<T> J = jacobi_params<T>(h, P.jp);
     J.src = P.Xh; J.src_bs = mn; J.m = m; J.n = n;
-    J.mm = mm; J.rc = rc; J.trans = P.jp.trans; J.ldS = P.jp.ldS; J.bcols = P.jp.bcols;
-    J.g = P.jp.g; J.sort_n = P.jp.sort_n;
-    J.max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
-    J.tol = 4.0 * std::sqrt((double)mm) * Eps<T>::v;
     J.W = P.Wj; J.W_bs = (int64_t)(mm + rc) * rc;
     J.U = P.U; J.U_bs = (int64_t)mm * rc;
     J.V = P.V; J.V_bs = (int64_t)rc * rc;
@@ -587,6 +623,31 @@ sma_status compress_tsvdm(sma_ctx* h, Prob<T>& P) {
     SMA_K(jacobi_svd<T>(J, p, P.jp.threads, P.jp.smem, st));
   }
   stage_end(h);
+  return SMA_OK;
+}
+
+// all slices of all t-SVDM problems, one launch per slice size
+template <typename T>
+sma_status tsvdm_svd_batched(sma_ctx* h) {
+  stage_begin(h, SMA_STAGE_SVD);
+  for (auto& b : bins<T>(h)) {
+    JacobiParams<T> J = jacobi_params<T>(h, b.jp);
+    J.desc = b.desc;
+    J.m = b.m;
+    J.n = b.n;
+    J.W = b.W;
+    J.W_bs = (int64_t)(b.jp.mm + b.jp.rc) * b.jp.rc;
+    SMA_K(jacobi_svd<T>(J, b.count, b.jp.threads, b.jp.smem, h->st));
+  }
+  stage_end(h);
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status tsvdm_post(sma_ctx* h, Prob<T>& P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p, mm = P.mm, rc = P.rc;
+  const int64_t mn = (int64_t)m * n;
   // truncation
   stage_begin(h, SMA_STAGE_TRUNCATE);
   SMA_K(truncate_ranks(P.sigma, rc, p, P.stats, h->opt.rel_tol, h->opt.fixed_rank, P.ranks, P.off,
@@ -872,7 +933,7 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
     return SMA_OK;
   }
   SMA_TRY(do_gather(h, P, A, lda));
-  if (h->opt.decomp == SMA_TSVDM) SMA_TRY(compress_tsvdm(h, P));
+  if (h->opt.decomp == SMA_TSVDM) SMA_TRY(tsvdm_pre(h, P));
   else SMA_TRY(compress_tucker(h, P));
   P.compressed = true;
   P.dp_valid = false;
@@ -931,9 +992,85 @@ sma_status read_result(sma_ctx* h, Prob<T>& P, sma_result* r) {
 }
 
 template <typename T>
-sma_status compress_all(sma_ctx* h, const void* const* A, const int64_t* lda, sma_result* res) {
+sma_status enqueue_compress(sma_ctx* h, const void* const* A, const int64_t* lda) {
   auto& ps = probs<T>(h);
   for (int i = 0; i < h->nprob; ++i) SMA_TRY(compress_one(h, ps[i], A[i], lda[i]));
+  if (h->opt.decomp == SMA_TSVDM) {
+    if (h->nprob > 1) {
+      SMA_TRY(tsvdm_svd_batched<T>(h));
+    } else {
+      SMA_TRY(tsvdm_svd(h, ps[0]));
+    }
+    for (int i = 0; i < h->nprob; ++i) SMA_TRY(tsvdm_post(h, ps[i]));
+  }
+  return SMA_OK;
+}
+
+template <typename T>
+void mark_compressed(sma_ctx* h) {
+  for (auto& P : probs<T>(h)) {
+    P.compressed = true;
+    P.dp_valid = false;
+    P.ml_valid = false;
+    P.h_iscal[0] = -1;
+  }
+}
+
+// Graph mode: run normally the first time a set of inputs is seen (this also
+// uploads the representative-block offsets), capture the launches into a
+// CUDA graph the second time, replay the graph while inputs are unchanged.
+template <typename T>
+sma_status run_compress(sma_ctx* h, const void* const* A, const int64_t* lda) {
+  std::vector<const void*> ptrs(A, A + h->nprob);
+  std::vector<int64_t> ld(lda, lda + h->nprob);
+  const bool graph_ok = h->opt.graph && h->st != nullptr;
+  if (graph_ok && h->graph_exec && ptrs == h->graph_ptrs && ld == h->graph_lda) {
+    SMA_CK(cudaGraphLaunch(h->graph_exec, h->st));
+    h->launches += h->graph_launches;
+    mark_compressed<T>(h);
+    return SMA_OK;
+  }
+  if (graph_ok && ptrs == h->warm_ptrs && ld == h->warm_lda) {
+    bool host_input = false;
+    for (const void* q : ptrs) host_input |= !is_device_ptr(q);
+    if (!host_input) {
+      if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+      }
+      SMA_CK(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+      h->capturing = true;
+      const int64_t l0 = h->launches;
+      sma_status s = enqueue_compress<T>(h, A, lda);
+      h->capturing = false;
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(h->st, &g);
+      if (s != SMA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      SMA_CK(ec);
+      const cudaError_t ei = cudaGraphInstantiate(&h->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      SMA_CK(ei);
+      h->graph_launches = h->launches - l0;
+      h->graph_ptrs = ptrs;
+      h->graph_lda = ld;
+      SMA_CK(cudaGraphLaunch(h->graph_exec, h->st));
+      mark_compressed<T>(h);
+      return SMA_OK;
+    }
+  }
+  SMA_TRY(enqueue_compress<T>(h, A, lda));
+  h->warm_ptrs = ptrs;
+  h->warm_lda = ld;
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status compress_all(sma_ctx* h, const void* const* A, const int64_t* lda, sma_result* res) {
+  SMA_TRY(run_compress<T>(h, A, lda));
+  auto& ps = probs<T>(h);
   if (res) {
     sma_status worst = SMA_OK;
     for (int i = 0; i < h->nprob; ++i) {
@@ -1373,6 +1510,42 @@ sma_status ranks_one(sma_ctx* h, Prob<T>& P, int32_t* out, int32_t* count) {
 
 }  // namespace
 
+// Group the slices of all t-SVDM problems by slice size; upload one
+// descriptor array per size and allocate its block-mode workspace.
+template <typename T>
+sma_status build_bins(sma_ctx* h) {
+  auto& ps = probs<T>(h);
+  auto& bs = bins<T>(h);
+  std::vector<std::vector<SliceDesc<T>>> host;
+  for (auto& P : ps) {
+    size_t bi = 0;
+    for (; bi < bs.size(); ++bi)
+      if (bs[bi].m == P.m && bs[bi].n == P.n) break;
+    if (bi == bs.size()) {
+      SvdBin<T> b;
+      b.m = P.m;
+      b.n = P.n;
+      b.jp = P.jp;
+      bs.push_back(b);
+      host.emplace_back();
+    }
+    const int64_t mn = (int64_t)P.m * P.n, urc = (int64_t)P.mm * P.rc, vrc = (int64_t)P.rc * P.rc;
+    for (int k = 0; k < P.p; ++k)
+      host[bi].push_back(SliceDesc<T>{P.Xh + k * mn, P.U + k * urc, P.V + k * vrc,
+                                      P.sigma + (int64_t)k * P.rc, P.sweeps + k, P.status});
+  }
+  for (size_t bi = 0; bi < bs.size(); ++bi) {
+    auto& b = bs[bi];
+    b.count = (int)host[bi].size();
+    SMA_TRY(h->mem.alloc(&b.desc, host[bi].size()));
+    SMA_CK(cudaMemcpy(b.desc, host[bi].data(), host[bi].size() * sizeof(SliceDesc<T>),
+                      cudaMemcpyHostToDevice));
+    if (b.jp.block_mode)
+      SMA_TRY(h->mem.alloc(&b.W, (size_t)(b.jp.mm + b.jp.rc) * b.jp.rc * b.count));
+  }
+  return SMA_OK;
+}
+
 // ===========================================================================
 // exported C ABI
 // ===========================================================================
@@ -1436,9 +1609,11 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   if (opt->prec == SMA_FP64) {
     h->p64.resize(nprob);
     for (int i = 0; i < nprob; ++i) SMA_TRY(setup_problem(h.get(), h->p64[i], prob[i]));
+    if (opt->decomp == SMA_TSVDM && nprob > 1) SMA_TRY(build_bins<double>(h.get()));
   } else {
     h->p32.resize(nprob);
     for (int i = 0; i < nprob; ++i) SMA_TRY(setup_problem(h.get(), h->p32[i], prob[i]));
+    if (opt->decomp == SMA_TSVDM && nprob > 1) SMA_TRY(build_bins<float>(h.get()));
   }
   *out = h.release();
   return SMA_OK;

@@ -68,10 +68,10 @@ template <> struct Angle<double> {
 template <> struct Angle<float> {
   // fp32 angle; fp64 for nearly parallel columns (|cos| > 0.99), where the
   // difference of the squared norms loses most of its fp32 digits
-  static __device__ __forceinline__ bool get(float al, float be, float ga, double tol,
-                                             double floor_, float& c, float& s) {
+  static __device__ __forceinline__ bool get(float al, float be, float ga, float tol,
+                                             float floor_, float& c, float& s) {
     const float nrm = sqrtf(al) * sqrtf(be);
-    if (!(fabsf(ga) > (float)tol * nrm) || !((double)fabsf(ga) > floor_)) return false;
+    if (!(fabsf(ga) > tol * nrm) || !(fabsf(ga) > floor_)) return false;
     if (fabsf(ga) > 0.99f * nrm) {
       double cd = 1.0, sd = 0.0;
       angle_fp64(al, be, ga, 0.0, 0.0, cd, sd);
@@ -113,8 +113,7 @@ template <> struct CacheRows<double> { static constexpr int v = 16; };
 // level of the whole slice (columns that are numerically zero).
 template <typename T>
 __device__ __forceinline__ bool rotate_pair(T* S, int ldS, int a, int b, bool active,
-                                            int mm, int len, int lane, int g, double tol,
-                                            double floor_) {
+                                            int mm, int len, int lane, int g, T tol, T floor_) {
   constexpr int NR = CacheRows<T>::v;
   T xr[NR], yr[NR];
   T al = T(0), be = T(0), ga = T(0);
@@ -235,7 +234,8 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
     const int nw = NTh / 32, w = tid / 32, j = (tid % 32) / g;
     if (g < 32 && nw % g == 0) kslot = (w % g) + g * j + 32 * (w / g);
   }
-  const T* src = P.src + (int64_t)s * P.src_bs;
+  // output pointers are looked up after the sweeps (not kept live in them)
+  const T* src = P.desc ? P.desc[s].src : P.src + (int64_t)s * P.src_bs;
   const bool in_smem = rc <= 2 * P.bcols;
   const int ncols_smem = in_smem ? rc : 2 * P.bcols;
   T* S = reinterpret_cast<T*>(smem_raw);
@@ -264,6 +264,9 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
     nrm2 = block_sum(nrm2, red);
     floor_ = Eps<T>::v * Eps<T>::v * nrm2;
   }
+  // convergence thresholds in the working precision (no fp64 in the round)
+  const T tol_t = (T)P.tol;
+  const T floor_t = (T)floor_;
   int sweeps_used = 0;
   bool converged = (rc <= 1);
   const int npair_sets = in_smem ? 1 : nb * (nb - 1) / 2;
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
         for (int base = 0; base < ph.npairs; base += ngroups) {
           int a = 0, b = 0;
           const bool act = phase_pair(ph, t, base + kslot, a, b);
-          rot |= rotate_pair(S, ldS, a, b, act, mm, len, lane, g, P.tol, floor_);
+          rot |= rotate_pair(S, ldS, a, b, act, mm, len, lane, g, tol_t, floor_t);
         }
         __syncthreads();
       }
@@ -368,13 +371,32 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
     }
   }
   // outputs: sorted sigma, the sorted columns W (= U Sigma) and V
-  double* so = P.sigma + (int64_t)s * rc;
+  T* Wout;
+  T* Vout;
+  double* sig_out;
+  int* sweeps_out;
+  int* status_out;
+  if (P.desc) {
+    const SliceDesc<T> d = P.desc[s];
+    Wout = d.U;
+    Vout = d.V;
+    sig_out = d.sigma;
+    sweeps_out = d.sweeps;
+    status_out = d.status;
+  } else {
+    Wout = P.U + (int64_t)s * P.U_bs;
+    Vout = P.V + (int64_t)s * P.V_bs;
+    sig_out = P.sigma + (int64_t)s * rc;
+    sweeps_out = P.sweeps ? P.sweeps + s : nullptr;
+    status_out = P.status;
+  }
+  double* so = sig_out;
   for (int j = tid; j < rc; j += NTh) {
     so[j] = sig[j];
-    if (!isfinite(sig[j])) atomicOr(P.status, SMA_STATUS_BIT(SMA_ERR_NONFINITE));
+    if (!isfinite(sig[j])) atomicOr(status_out, SMA_STATUS_BIT(SMA_ERR_NONFINITE));
   }
-  T* Wo = P.U + (int64_t)s * P.U_bs;
-  T* Vo = P.V + (int64_t)s * P.V_bs;
+  T* Wo = Wout;
+  T* Vo = Vout;
   for (int e = tid; e < len * rc; e += NTh) {
     const int r = e % len, j = e / len;
     const int c = idx[j];
@@ -383,8 +405,8 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
     else Vo[(r - mm) + (int64_t)j * rc] = v;
   }
   if (tid == 0) {
-    if (P.sweeps) P.sweeps[s] = sweeps_used;
-    if (!converged) atomicOr(P.status, SMA_STATUS_BIT(SMA_ERR_NOCONVERGE));
+    if (sweeps_out) *sweeps_out = sweeps_used;
+    if (!converged) atomicOr(status_out, SMA_STATUS_BIT(SMA_ERR_NOCONVERGE));
   }
 }
 

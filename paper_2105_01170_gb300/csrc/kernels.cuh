@@ -22,8 +22,19 @@ cudaError_t residual_norm2(const T* X, const T* Tt, int64_t count, double* parti
                            double* out, cudaStream_t st);
 
 // ---- step 3: Jacobi SVD ---------------------------------------------------
+// Per-slice pointers for batched launches over slices of several problems.
+template <typename T>
+struct SliceDesc {
+  const T* src;      // m x n slice, ld m
+  T* U;              // mm x rc out
+  T* V;              // rc x rc out
+  double* sigma;     // rc out
+  int* sweeps;       // 1 out (may be null)
+  int* status;       // status word of the slice's problem
+};
 template <typename T>
 struct JacobiParams {
+  const SliceDesc<T>* desc = nullptr;           // if set: slice s uses desc[s]
   const T* src = nullptr; int64_t src_bs = 0;   // slices m x n, ld m
   int m = 0, n = 0;
   int mm = 0, rc = 0, trans = 0, ldS = 0, bcols = 0, g = 1, sort_n = 1;

@@ -12,8 +12,15 @@
 // One CTA per 128-row tile of C, all N columns: an elected thread of warp 0
 // streams (A plane, B plane) tile pairs with TMA (3-D tensor maps, 128B
 // swizzle) through a 4-stage mbarrier ring; an elected thread of warp 1
-// issues tcgen05.mma (M128 x N256 x K16, accumulator in TMEM); warps 2-5
-// read the accumulator with tcgen05.ld and store fp32 rows.  Every wait is
+// issues tcgen05.mma (M128 x N256 x K16) into tensor memory.
+//
+// Accumulation is chunked: the tensor core adds each step into the fp32
+// accumulator with about half an ulp of error, which over the long K of the
+// Kronecker-sum matvec (tens of thousands of steps) would cost most of the
+// fp32 accuracy.  So every CHUNK k-blocks start a fresh accumulator (two TMEM
+// buffers, ping-pong), and eight epilogue warps (warps 2-9) drain finished
+// chunks with tcgen05.ld into fp32 register sums (IEEE round-to-nearest),
+// 128 columns per thread, while the other buffer fills.  Every wait is
 // bounded: on timeout the kernel sets an error bit, drains what it issued,
 // frees its TMEM and returns.
 #include <cuda.h>
@@ -27,15 +34,17 @@
 namespace sma {
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4, CHUNK = 2;
 constexpr int A_BYTES = BM * BK * 2;        // 16 KB
 constexpr int B_BYTES = BN * BK * 2;        // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int THREADS = 192;
-constexpr int TMEM_COLS = 256;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int TMEM_COLS = 512;  // two 256-column accumulators
 constexpr uint64_t WAIT_NS = 4000000000ull;  // 4 s per wait
 constexpr uint32_t WAIT_ITERS = 1u << 30;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+static_assert(THREADS == 320, "two control warps and eight epilogue warps");
 
 __constant__ int kProdA[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int kProdB[6] = {0, 1, 0, 2, 0, 1};
@@ -151,20 +160,26 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(tiles + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* accf = empty + STAGES;   // chunk in buffer b complete (MMA commit)
+  uint64_t* acce = accf + 2;         // buffer b drained (one arrive per epilogue warp)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM;
-  const int total = (args.Kp / BK) * 6;
+  const int nkb = args.Kp / BK;
+  const int total = nkb * 6;
+  const int nch = (nkb + CHUNK - 1) / CHUNK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], EPI_WARPS);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
@@ -203,53 +218,78 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
       if (!mbar_wait(&full[it % STAGES], (uint32_t)(it / STAGES) & 1u)) *abort_flag = 1;
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
+    // MMA issuer: chunk c (CHUNK k-blocks) accumulates into buffer c & 1
     const uint32_t id = idesc_bf16(BM, BN);
-    for (int it = 0; it < total; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-      if (!mbar_wait(&full[s], ph)) {
+    int it = 0;
+    for (int c = 0; c < nch && !*abort_flag; ++c) {
+      const int b = c & 1;
+      if (c >= 2 && !mbar_wait(&acce[b], (uint32_t)((c >> 1) - 1) & 1u)) {
         *abort_flag = 1;
         break;
       }
-      if (*abort_flag) break;
       fence_after();
-      const uint32_t a0 = saddr(tiles + s * STAGE_BYTES);
-      const uint32_t b0 = a0 + A_BYTES;
+      const uint32_t dt = tmem + (uint32_t)(b * BN);
+      const int it_end = min(total, (c + 1) * CHUNK * 6);
+      bool first = true;
+      for (; it < it_end; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(&full[s], ph)) {
+          *abort_flag = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t a0 = saddr(tiles + s * STAGE_BYTES);
+        const uint32_t b0 = a0 + A_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
-        mma(tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), id, (it > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          mma(dt, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), id, first ? 0u : 1u);
+          first = false;
+        }
+        mma_commit(&empty[s]);
+      }
+      mma_commit(&accf[b]);  // arrives when this chunk's MMAs have completed
     }
-    mma_commit(accum);  // arrives once every MMA issued above has completed
-  }
-  if (warp >= 2) {
-    const bool ok = mbar_wait(accum, 0);
-    fence_after();
-    if (!ok) *abort_flag = 1;
-    const int q = warp & 3;
+  } else if (warp >= 2) {
+    // epilogue: warp e drains rows of quadrant (warp & 3), columns half h
+    const int e = warp - 2;
+    const int q = warp & 3, hc = e >> 2;
     const int row = q * 32 + lane;
     const int grow = m0 + row;
-    __syncwarp();
-    if (!*abort_flag) {
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+    float acc[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+    for (int c = 0; c < nch; ++c) {
+      const int b = c & 1;
+      const bool ok = mbar_wait(&accf[b], (uint32_t)(c >> 1) & 1u);
+      fence_after();
+      if (!ok) *abort_flag = 1;
+      __syncwarp();
+      if (*abort_flag) break;
+#pragma unroll
+      for (int part = 0; part < 4; ++part) {
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-        if (grow < args.M) {
-          float* dst = args.C + (int64_t)grow * args.ldc + c0;
-          const int nv = args.N - c0;
-          if (nv >= 32 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + hc * 128 + part * 32), r);
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4*>(dst + j) =
-                  make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                              __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-          } else {
+        for (int j = 0; j < 32; ++j) acc[part * 32 + j] += __uint_as_float(r[j]);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&acce[b])) : "memory");
+    }
+    if (!*abort_flag && grow < args.M) {
+      const int c0 = hc * 128;
+      float* dst = args.C + (int64_t)grow * args.ldc + c0;
+      const int nv = args.N - c0;
+      if (nv >= 128 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < nv) dst[j] = __uint_as_float(r[j]);
-          }
-        }
+        for (int j = 0; j < 128; j += 4)
+          *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 128; ++j)
+          if (j < nv) dst[j] = acc[j];
       }
     }
   }

@@ -43,7 +43,7 @@ def test_version_and_status_strings(lib):
 def _create(problems, **kw):
     opt = S.sma_options(kw.get("prec", S.SMA_FP64), kw.get("decomp", S.SMA_TSVDM),
                         kw.get("mkind", S.SMA_M_DCT2), kw.get("layout", S.SMA_INPUT_DENSE),
-                        None, kw.get("fixed_rank", 0), kw.get("rel_tol", 1e-6), 0, None, 0)
+                        None, kw.get("fixed_rank", 0), kw.get("rel_tol", 1e-6), 0, None, 0, 0)
     structs, keep = [], []
     for ell, q, m, n, p, bm in problems:
         b = np.ascontiguousarray(np.asarray(bm, dtype=np.int32).ravel(order="F"))

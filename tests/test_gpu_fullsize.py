@@ -1,0 +1,75 @@
+"""Parity at the benchmark's full size (space-time covariance, 16384^2,
+tensor 256 x 256 x 127, tolerance 1e-6), in the launch configuration the
+benchmark times: every singular value and rank, the error report, and the
+Kronecker-sum matvec on sampled right-hand sides, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import sma_oracle as O
+from sma_inputs import generators as G
+
+from _util import gpu_tensor, rank_window_ok, rel, to_dev, tol_for
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+S = pytest.importorskip("paper_2105_01170_gb300")
+PRECS = [S.SMA_FP64, S.SMA_MIXED]
+PNAME = {S.SMA_FP64: "fp64", S.SMA_MIXED: "mixed"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_01170_gb300 import _build
+    _build.build()
+
+
+@pytest.fixture(scope="module")
+def workload():
+    pr = G.spacetime_covariance()
+    Ad = pr.dense()
+    return pr, Ad
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_spacetime_full_size(prec, workload):
+    pr, Ad = workload
+    A = Ad if prec == S.SMA_FP64 else Ad.astype(np.float32)
+    dA = to_dev(A)
+    st = torch.cuda.Stream()
+    h = S.Handle([pr], prec=prec, rel_tol=1e-6, stream=st.cuda_stream)
+    with torch.cuda.stream(st):
+        res = h.compress([dA])[0]
+    del dA
+    X = O.T_E(np.asarray(A, dtype=np.float64), pr.block_map, pr.p, pr.m, pr.n)
+    ora = O.tsvdm(X, O.dct2_matrix(pr.p), rel_tol=1e-6)
+    assert res["device_status"] == 0
+    sig = gpu_tensor(h, S.EXPORT_SIGMA, (pr.m, pr.p), prec)
+    smax = max(float(np.max(s)) for s in ora.sigma)
+    diff = max(float(np.max(np.abs(sig[:, k] - ora.sigma[k]))) for k in range(pr.p))
+    assert diff <= (1e-12 if prec == S.SMA_FP64 else 2e-5) * smax
+    ranks = h.ranks(0)
+    if prec == S.SMA_FP64:
+        assert np.array_equal(ranks, ora.ranks)
+        assert abs(res["tensor_err"] - ora.err) <= 1e-9 * ora.err
+    else:
+        ok, margin = rank_window_ok(ranks, ora, 1e-6, ora.normX ** 2, perturb=0.2)
+        assert ok, (int(ranks.sum()), int(ora.ranks.sum()), margin)
+    assert res["rel_err"] <= 1e-6
+    # sampled matvec: two of the benchmark's right-hand sides
+    x = G.random_rhs(pr.q * pr.n, 2, 1)
+    xin = x if prec == S.SMA_FP64 else x.astype(np.float32)
+    X_d = to_dev(xin)
+    dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+    Y_d = torch.empty(2, pr.ell * pr.m, dtype=dt, device="cuda").t()
+    with torch.cuda.stream(st):
+        h.apply(0, X_d, Y_d)
+    st.synchronize()
+    y = Y_d.cpu().numpy().astype(np.float64)
+    if np.array_equal(ranks, ora.ranks):
+        yo = O.apply_kron(O.tsvdm_kron_terms(ora, pr.block_map), np.asarray(xin, dtype=np.float64))
+        assert rel(y, yo) < tol_for(prec), rel(y, yo)
+    # the operator itself reproduces A x to the truncation tolerance
+    ya = np.asarray(A, dtype=np.float64) @ np.asarray(xin, dtype=np.float64)
+    assert rel(y, ya) < 2e-6
