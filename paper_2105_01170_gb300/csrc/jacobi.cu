@@ -169,6 +169,90 @@ __device__ __forceinline__ bool rotate_pair(T* S, int ldS, int a, int b, bool ac
   return true;
 }
 
+// float4 form of rotate_pair: lane l handles rows 4q..4q+3 for q = l + i g;
+// columns start on 16-byte boundaries (ldS % 4 == 0, mm % 4 == len % 4 == 0).
+template <int VEC>
+__device__ __forceinline__ bool rotate_pair4(float* S, int ldS, int a, int b, bool active,
+                                             int mm, int len, int lane, int g, float tol,
+                                             float floor_) {
+  constexpr int NQ = CacheRows<float>::v / 4;
+  float4 xr[NQ], yr[NQ];
+  float al = 0.f, be = 0.f, ga = 0.f;
+  float4* x = reinterpret_cast<float4*>(S + (int64_t)(active ? a : 0) * ldS);
+  float4* y = reinterpret_cast<float4*>(S + (int64_t)(active ? b : 0) * ldS);
+  const int mq = mm >> 2, lq = len >> 2;
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+      const int q = lane + i * g;
+      xr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      yr[i] = xr[i];
+      if (q < mq) {
+        xr[i] = x[q];
+        yr[i] = y[q];
+      }
+      al = fmaf(xr[i].x, xr[i].x, fmaf(xr[i].y, xr[i].y, fmaf(xr[i].z, xr[i].z, fmaf(xr[i].w, xr[i].w, al))));
+      be = fmaf(yr[i].x, yr[i].x, fmaf(yr[i].y, yr[i].y, fmaf(yr[i].z, yr[i].z, fmaf(yr[i].w, yr[i].w, be))));
+      ga = fmaf(xr[i].x, yr[i].x, fmaf(xr[i].y, yr[i].y, fmaf(xr[i].z, yr[i].z, fmaf(xr[i].w, yr[i].w, ga))));
+    }
+    for (int q = lane + NQ * g; q < mq; q += g) {
+      const float4 xv = x[q], yv = y[q];
+      al = fmaf(xv.x, xv.x, fmaf(xv.y, xv.y, fmaf(xv.z, xv.z, fmaf(xv.w, xv.w, al))));
+      be = fmaf(yv.x, yv.x, fmaf(yv.y, yv.y, fmaf(yv.z, yv.z, fmaf(yv.w, yv.w, be))));
+      ga = fmaf(xv.x, yv.x, fmaf(xv.y, yv.y, fmaf(xv.z, yv.z, fmaf(xv.w, yv.w, ga))));
+    }
+  }
+  for (int o = g >> 1; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  if (!active) return false;
+  float c, sn;
+  if (!Angle<float>::get(al, be, ga, tol, floor_, c, sn)) return false;
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int q = lane + i * g;
+    if (q < mq) {
+      x[q] = make_float4(c * xr[i].x - sn * yr[i].x, c * xr[i].y - sn * yr[i].y,
+                         c * xr[i].z - sn * yr[i].z, c * xr[i].w - sn * yr[i].w);
+      y[q] = make_float4(sn * xr[i].x + c * yr[i].x, sn * xr[i].y + c * yr[i].y,
+                         sn * xr[i].z + c * yr[i].z, sn * xr[i].w + c * yr[i].w);
+    }
+  }
+  for (int q = lane + NQ * g; q < mq; q += g) {
+    const float4 xv = x[q], yv = y[q];
+    x[q] = make_float4(c * xv.x - sn * yv.x, c * xv.y - sn * yv.y, c * xv.z - sn * yv.z,
+                       c * xv.w - sn * yv.w);
+    y[q] = make_float4(sn * xv.x + c * yv.x, sn * xv.y + c * yv.y, sn * xv.z + c * yv.z,
+                       sn * xv.w + c * yv.w);
+  }
+  for (int q = mq + lane; q < lq; q += g) {
+    const float4 xv = x[q], yv = y[q];
+    x[q] = make_float4(c * xv.x - sn * yv.x, c * xv.y - sn * yv.y, c * xv.z - sn * yv.z,
+                       c * xv.w - sn * yv.w);
+    y[q] = make_float4(sn * xv.x + c * yv.x, sn * xv.y + c * yv.y, sn * xv.z + c * yv.z,
+                       sn * xv.w + c * yv.w);
+  }
+  return true;
+}
+
+// One call site for both forms: the float4 form when the layout allows it.
+template <typename T, int VEC>
+struct Rotator {
+  static __device__ __forceinline__ bool run(T* S, int ldS, int a, int b, bool act, int mm,
+                                             int len, int lane, int g, T tol, T fl) {
+    return rotate_pair(S, ldS, a, b, act, mm, len, lane, g, tol, fl);
+  }
+};
+template <>
+struct Rotator<float, 4> {
+  static __device__ __forceinline__ bool run(float* S, int ldS, int a, int b, bool act, int mm,
+                                             int len, int lane, int g, float tol, float fl) {
+    return rotate_pair4<4>(S, ldS, a, b, act, mm, len, lane, g, tol, fl);
+  }
+};
+
 template <typename T>
 __device__ __forceinline__ T load_work(const T* src, int m, int trans, int mm, int r, int c) {
   // stacked column c: rows [0, mm) the working matrix (the slice, m x n with
@@ -217,7 +301,30 @@ __device__ __forceinline__ bool phase_pair(const Phase& ph, int t, int k, int& a
   return k < ph.bI && j < ph.bJ;
 }
 
-template <typename T>
+// Copy ncols columns of `rows` elements between shared memory (stride ldS)
+// and the global workspace (stride ldg); float4 when VEC == 4.
+template <typename T, int VEC>
+__device__ __forceinline__ void copy_cols(T* S, int ldS, T* G, int ldg, int rows, int ncols,
+                                          int tid, int nth, bool to_smem) {
+  if (VEC == 4) {
+    const int rq = rows >> 2;
+    for (int e = tid; e < rq * ncols; e += nth) {
+      const int r = e % rq, c = e / rq;
+      float4* s4 = reinterpret_cast<float4*>(S + (int64_t)c * ldS) + r;
+      float4* g4 = reinterpret_cast<float4*>(G + (int64_t)c * ldg) + r;
+      if (to_smem) *s4 = *g4;
+      else *g4 = *s4;
+    }
+  } else {
+    for (int e = tid; e < rows * ncols; e += nth) {
+      const int r = e % rows, c = e / rows;
+      if (to_smem) S[(int64_t)c * ldS + r] = G[(int64_t)c * ldg + r];
+      else G[(int64_t)c * ldg + r] = S[(int64_t)c * ldS + r];
+    }
+  }
+}
+
+template <typename T, int VEC>
 __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = blockIdx.x;
@@ -284,14 +391,9 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
         ph.npairs = ph.cI / 2;
       } else {
         const int bI = min(bc, rc - I * bc), bJ = min(bc, rc - J * bc);
-        for (int e = tid; e < len * bI; e += NTh) {
-          const int r = e % len, c = e / len;
-          S[(int64_t)c * ldS + r] = W[r + (int64_t)(I * bc + c) * len];
-        }
-        for (int e = tid; e < len * bJ; e += NTh) {
-          const int r = e % len, c = e / len;
-          S[(int64_t)(bc + c) * ldS + r] = W[r + (int64_t)(J * bc + c) * len];
-        }
+        copy_cols<T, VEC>(S, ldS, W + (int64_t)(I * bc) * len, len, len, bI, tid, NTh, true);
+        copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len, bJ,
+                          tid, NTh, true);
         __syncthreads();
         // pairs inside a block on the block's first visit of this sweep
         const bool doI = (I == 0 && J == 1), doJ = (I == 0);
@@ -309,19 +411,14 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
         for (int base = 0; base < ph.npairs; base += ngroups) {
           int a = 0, b = 0;
           const bool act = phase_pair(ph, t, base + kslot, a, b);
-          rot |= rotate_pair(S, ldS, a, b, act, mm, len, lane, g, tol_t, floor_t);
+          rot |= Rotator<T, VEC>::run(S, ldS, a, b, act, mm, len, lane, g, tol_t, floor_t);
         }
         __syncthreads();
       }
       if (!in_smem) {
-        for (int e = tid; e < len * ph.bI; e += NTh) {
-          const int r = e % len, c = e / len;
-          W[r + (int64_t)(I * bc + c) * len] = S[(int64_t)c * ldS + r];
-        }
-        for (int e = tid; e < len * ph.bJ; e += NTh) {
-          const int r = e % len, c = e / len;
-          W[r + (int64_t)(J * bc + c) * len] = S[(int64_t)(bc + c) * ldS + r];
-        }
+        copy_cols<T, VEC>(S, ldS, W + (int64_t)(I * bc) * len, len, len, ph.bI, tid, NTh, false);
+        copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len,
+                          ph.bJ, tid, NTh, false);
         __syncthreads();
         if (++J == nb) {
           ++I;
@@ -418,7 +515,8 @@ JacobiPlan jacobi_plan(int m, int n, int max_smem) {
   pl.trans = (m < n) ? 1 : 0;
   pl.mm = pl.trans ? n : m;
   pl.rc = pl.trans ? m : n;
-  pl.ldS = pl.mm + pl.rc + 1;
+  pl.vec = (sizeof(T) == 4 && pl.mm % 4 == 0 && pl.rc % 4 == 0) ? 4 : 1;
+  pl.ldS = pl.mm + pl.rc + (pl.vec == 4 ? 4 : 1);
   int p2 = 1;
   while (p2 < pl.rc) p2 <<= 1;
   pl.sort_n = p2;
@@ -453,10 +551,13 @@ template <typename T>
 cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_t smem,
                        cudaStream_t st) {
   if (nslices <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  void (*kern)(const JacobiParams<T>) = jacobi_kernel<T, 1>;
+  if constexpr (sizeof(T) == 4) {
+    if (P.ldS % 4 == 0 && P.mm % 4 == 0 && P.rc % 4 == 0) kern = jacobi_kernel<T, 4>;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  jacobi_kernel<T><<<nslices, threads, smem, st>>>(P);
+  kern<<<nslices, threads, smem, st>>>(P);
   return cudaGetLastError();
 }
 

@@ -48,7 +48,7 @@ struct JacobiParams {
   int* status = nullptr;                        // status bits (atomicOr)
 };
 struct JacobiPlan {
-  int trans, mm, rc, ldS, bcols, sort_n, threads, g, block_mode;
+  int trans, mm, rc, ldS, bcols, sort_n, threads, g, block_mode, vec;
   size_t smem;
 };
 template <typename T> JacobiPlan jacobi_plan(int m, int n, int max_smem);
