@@ -186,6 +186,10 @@ struct Prob {
   int64_t Zp_K = -1;
   __nv_bfloat16* Dp = nullptr;
   size_t Dp_elems = 0;
+  // tcgen05 operands of the transform X x3 M (mixed t-SVDM, p <= 256)
+  __nv_bfloat16* Xp = nullptr;             // X as [mn][Kp] planes
+  __nv_bfloat16* Mp = nullptr;             // M as [p][Kp] planes
+  int64_t Mkp = 0;
   int64_t Dp_K = -1;
   bool dp_valid = false;
   bool compressed = false;
@@ -340,6 +344,28 @@ sma_status validate_problem(const sma_problem& pr, std::vector<int64_t>& eta,
   return SMA_OK;
 }
 
+// Mixed path: the transform runs on tcgen05 (M' = m n rows, N' = p <= 256,
+// K = p); M's split planes are built once here.
+template <typename T>
+sma_status setup_tc_transform(sma_ctx*, Prob<T>&) {
+  return SMA_OK;
+}
+template <>
+sma_status setup_tc_transform<float>(sma_ctx* h, Prob<float>& P) {
+  if (!h->tc_ok || P.p > 256) return SMA_OK;
+  const int64_t Kp = tc_pad_k(P.p), mn = (int64_t)P.m * P.n;
+  SMA_TRY(h->mem.alloc(&P.Xp, (size_t)3 * mn * Kp));
+  SMA_TRY(h->mem.alloc(&P.Mp, (size_t)3 * P.p * Kp));
+  SMA_CK(cudaMemset(P.Xp, 0, sizeof(__nv_bfloat16) * (size_t)3 * mn * Kp));
+  SMA_CK(cudaMemset(P.Mp, 0, sizeof(__nv_bfloat16) * (size_t)3 * P.p * Kp));
+  // plane element (i, k) = M[i, k] (M column-major, ld p)
+  ++h->launches;
+  SMA_CK(tc_split_transpose(P.Mt, 1, P.p, P.p, P.p, Kp, P.Mp, nullptr));
+  SMA_CK(cudaDeviceSynchronize());
+  P.Mkp = Kp;
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status setup_multilevel(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   auto& mem = h->mem;
@@ -452,6 +478,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     std::vector<T> Mt(M.begin(), M.end());
     SMA_TRY(mem.alloc(&P.Mt, (size_t)p * p));
     SMA_CK(cudaMemcpy(P.Mt, Mt.data(), Mt.size() * sizeof(T), cudaMemcpyHostToDevice));
+    SMA_TRY(setup_tc_transform(h, P));
     P.jp = jacobi_plan<T>(m, n, h->max_smem);
     P.rc = P.jp.rc;
     P.mm = P.jp.mm;
@@ -579,12 +606,35 @@ cudaError_t contract<float>(sma_ctx* h, const GemmParams<float>& g) {
 // ---------------------------------------------------------------------------
 // t-SVDM (steps 2-5)
 // ---------------------------------------------------------------------------
+// Xhat = X x3 M on tcgen05: A = X as K-major planes (element (e, k) =
+// X[e + mn k]), B = M planes (element (i, k) = M[i, k]); Xhat written
+// column-major (ld mn).  False when not set up for it.
+template <typename T>
+bool tc_transform(sma_ctx*, Prob<T>&) {
+  return false;
+}
+template <>
+bool tc_transform<float>(sma_ctx* h, Prob<float>& P) {
+  if (!P.Xp || !P.Mp) return false;
+  const int64_t mn = (int64_t)P.m * P.n;
+  if (mn > 0x7fffffff) return false;
+  ++h->launches;
+  if (tc_split_transpose(P.X, 1, mn, (int)mn, P.p, P.Mkp, P.Xp, h->st) != cudaSuccess) return false;
+  ++h->launches;
+  return tc_gemm_planes(P.Xp, P.Mp, (int)mn, P.p, P.Mkp, P.Xh, mn, P.status, h->st, true) ==
+         cudaSuccess;
+}
+
 template <typename T>
 sma_status tsvdm_pre(sma_ctx* h, Prob<T>& P) {
   const int p = P.p;
   const int64_t mn = (int64_t)P.m * P.n;
   // Xhat = X x3 M:  Xhat_mat (mn x p) = X_mat (mn x p) * M^T
   stage_begin(h, SMA_STAGE_TRANSFORM);
+  if (tc_transform(h, P)) {
+    stage_end(h);
+    return SMA_OK;
+  }
   {
     GemmParams<T> g;
     g.M = (int)mn; g.N = p; g.K = p;

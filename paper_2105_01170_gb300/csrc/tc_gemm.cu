@@ -149,6 +149,7 @@ struct TcArgs {
   int M, N, Kp;
   float* C;
   int64_t ldc;
+  int col_major;  // 0: C[i * ldc + j]; 1: C[i + j * ldc]
   int* err;
 };
 
@@ -278,7 +279,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&acce[b])) : "memory");
     }
-    if (!*abort_flag && grow < args.M) {
+    if (!*abort_flag && grow < args.M && args.col_major) {
+      // lanes hold consecutive rows: each store instruction is coalesced
+      const int c0 = hc * 128;
+      const int nv = args.N - c0;
+      float* dst = args.C + grow + (int64_t)c0 * args.ldc;
+#pragma unroll
+      for (int j = 0; j < 128; ++j)
+        if (j < nv) dst[(int64_t)j * args.ldc] = acc[j];
+    } else if (!*abort_flag && grow < args.M) {
       const int c0 = hc * 128;
       float* dst = args.C + (int64_t)grow * args.ldc + c0;
       const int nv = args.N - c0;
@@ -378,7 +387,8 @@ cudaError_t tc_split_transpose(const float* src, int64_t s_rs, int64_t s_cs, int
 }
 
 cudaError_t tc_gemm_planes(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N,
-                           int64_t Kp, float* C, int64_t ldc, int* err, cudaStream_t st) {
+                           int64_t Kp, float* C, int64_t ldc, int* err, cudaStream_t st,
+                           bool col_major) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (N > BN || Kp % BK != 0 || Kp <= 0) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
@@ -386,7 +396,7 @@ cudaError_t tc_gemm_planes(const __nv_bfloat16* A, const __nv_bfloat16* B, int M
   const cudaError_t attr = cudaFuncSetAttribute(
       tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
-  TcArgs a{M, N, (int)Kp, C, ldc, err};
+  TcArgs a{M, N, (int)Kp, C, ldc, col_major ? 1 : 0, err};
   tc_gemm_kernel<<<(M + BM - 1) / BM, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
   return cudaGetLastError();
 }
