@@ -109,6 +109,17 @@ typedef struct {
   const int32_t* const* level_maps;   /* [levels] host column-major maps    */
 } sma_problem;
 
+/* Preconditioning of the t-SVDM slice SVDs (an implementation choice; the
+ * paper only needs the SVD).  SMA_PRECOND_QRCP factors each slice (or its
+ * transpose) as B P = Q1 R1 by a column-pivoted Householder QR and runs the
+ * one-sided Jacobi SVD on R1^T, which converges in fewer sweeps (Drmac and
+ * Veselic 2008); SMA_PRECOND_AUTO does so when min(m, n) >= 64.            */
+typedef enum {
+  SMA_PRECOND_AUTO = 0,
+  SMA_PRECOND_NONE = 1,
+  SMA_PRECOND_QRCP = 2
+} sma_precondition;
+
 typedef struct {
   sma_precision prec;
   sma_decomp decomp;
@@ -126,6 +137,7 @@ typedef struct {
                              dimensions, and replay it while they are unchanged
                              (needs a non-NULL stream; stage timing is then
                              reported for the whole compression only)          */
+  sma_precondition precondition;  /* t-SVDM slice SVD preconditioning          */
 } sma_options;
 
 typedef struct {

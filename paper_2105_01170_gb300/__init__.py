@@ -30,6 +30,7 @@ SMA_FP64, SMA_MIXED = 0, 1
 SMA_TSVDM, SMA_TUCKER_BLOCKMODE, SMA_TUCKER_SHARED_U, SMA_TUCKER_ROWCOL, SMA_HOSVD_MULTILEVEL = 0, 1, 2, 3, 4
 SMA_M_DCT2, SMA_M_IDENTITY, SMA_M_USER = 0, 1, 2
 SMA_INPUT_DENSE, SMA_INPUT_BLOCKS = 0, 1
+SMA_PRECOND_AUTO, SMA_PRECOND_NONE, SMA_PRECOND_QRCP = 0, 1, 2
 EXPORT_X, EXPORT_XHAT, EXPORT_SIGMA, EXPORT_T, EXPORT_FACTOR = 0, 1, 2, 3, 4
 
 EXPORTED = ("sma_create", "sma_compress", "sma_get_result", "sma_get_ranks", "sma_reconstruct",
@@ -54,7 +55,8 @@ class sma_options(ctypes.Structure):
                 ("layout", ctypes.c_int), ("M_user", ctypes.POINTER(ctypes.c_double)),
                 ("fixed_rank", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("profile", ctypes.c_int32), ("graph", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("precondition", ctypes.c_int)]
 
 
 class sma_result(ctypes.Structure):
@@ -227,7 +229,8 @@ class Handle:
 
     def __init__(self, problems, prec=SMA_MIXED, decomp=SMA_TSVDM, mkind=SMA_M_DCT2,
                  layout=SMA_INPUT_DENSE, M_user=None, fixed_rank=0, rel_tol=0.0,
-                 max_sweeps=0, stream=None, profile=False, graph=False):
+                 max_sweeps=0, stream=None, profile=False, graph=False,
+                 precondition=None):
         self._keep = []
         structs = []
         for pr in problems:
@@ -249,7 +252,8 @@ class Handle:
         if stream is not None:
             sptr = ctypes.c_void_p(int(stream))
         self.opt = sma_options(prec, decomp, mkind, layout, mu, int(fixed_rank), float(rel_tol),
-                               int(max_sweeps), sptr, 1 if profile else 0, 1 if graph else 0)
+                               int(max_sweeps), sptr, 1 if profile else 0, 1 if graph else 0,
+                               SMA_PRECOND_AUTO if precondition is None else int(precondition))
         self.nprob = len(structs)
         self.prec = prec
         st, self.h = sma_create(structs, self.opt)

@@ -19,6 +19,10 @@ using namespace sma;
 
 namespace {
 
+// SMA_PRECOND_AUTO preconditions the slice SVD by a column-pivoted QR from
+// this min(m, n) on (below it a slice's Jacobi takes few sweeps anyway)
+constexpr int kQrAutoMin = 64;
+
 #define SMA_CK(...)                                 \
   do {                                              \
     cudaError_t e_ = (__VA_ARGS__);                           \
@@ -120,8 +124,21 @@ struct Prob {
   T* Mt = nullptr;                          // M, p x p column-major
   T* Xh = nullptr;
   T* Wj = nullptr;
-  T* U = nullptr;                           // W = U Sigma (sorted), mm x rc per slice
-  T* V = nullptr;                           // right singular vectors, rc x rc per slice
+  T* U = nullptr;                           // Jacobi W = U Sigma (sorted), jp.mm x rc per slice
+  T* V = nullptr;                           // Jacobi V, rc x rc per slice
+  // column-pivoted QR preconditioning (qr.cu): the Jacobi then runs on the
+  // rc x rc factor R1^T, and the rebuild uses L = Q1 V (discarded columns)
+  // and Rt = P W in place of the slice's own W and V
+  bool qr = false;
+  int trans = 0;                            // slices processed transposed (m < n)
+  QrPlan qplan{};
+  T* qF = nullptr;
+  T* qG = nullptr;
+  T* qtau = nullptr;
+  int* qperm = nullptr;
+  T* qJ = nullptr;
+  T* qRt = nullptr;
+  T* qL = nullptr;
   double* sigma = nullptr;
   double* suf = nullptr;
   int* ranks = nullptr;
@@ -479,13 +496,29 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     SMA_TRY(mem.alloc(&P.Mt, (size_t)p * p));
     SMA_CK(cudaMemcpy(P.Mt, Mt.data(), Mt.size() * sizeof(T), cudaMemcpyHostToDevice));
     SMA_TRY(setup_tc_transform(h, P));
-    P.jp = jacobi_plan<T>(m, n, h->max_smem);
-    P.rc = P.jp.rc;
-    P.mm = P.jp.mm;
-    const size_t urc = (size_t)P.mm * P.rc * p;
+    P.trans = m < n ? 1 : 0;
+    P.mm = m < n ? n : m;
+    P.rc = m < n ? m : n;
+    P.qplan = qr_plan<T>(P.mm, P.rc, h->max_smem);
+    const bool qr_fits = P.qplan.smem_qr <= (size_t)h->max_smem &&
+                         P.qplan.smem_fin <= (size_t)h->max_smem && P.qplan.fslot >= 0;
+    P.qr = qr_fits && (o.precondition == SMA_PRECOND_QRCP ||
+                       (o.precondition == SMA_PRECOND_AUTO && P.rc >= kQrAutoMin));
+    P.jp = P.qr ? jacobi_plan<T>(P.rc, P.rc, h->max_smem) : jacobi_plan<T>(m, n, h->max_smem);
     SMA_TRY(mem.alloc(&P.Xh, mnp));
-    if (P.jp.block_mode) SMA_TRY(mem.alloc(&P.Wj, (size_t)(P.mm + P.rc) * P.rc * p));
-    SMA_TRY(mem.alloc(&P.U, urc));
+    if (P.jp.block_mode)
+      SMA_TRY(mem.alloc(&P.Wj, (size_t)(P.jp.mm + P.jp.rc) * P.jp.rc * p));
+    SMA_TRY(mem.alloc(&P.U, (size_t)P.jp.mm * P.rc * p));
+    if (P.qr) {
+      const size_t frc = (size_t)P.mm * P.rc * p, rr = (size_t)P.rc * P.rc * p;
+      SMA_TRY(mem.alloc(&P.qF, frc));
+      if (P.qplan.novf > 0) SMA_TRY(mem.alloc(&P.qG, (size_t)P.mm * P.qplan.novf * p));
+      SMA_TRY(mem.alloc(&P.qtau, (size_t)P.rc * p));
+      SMA_TRY(mem.alloc(&P.qperm, (size_t)P.rc * p));
+      SMA_TRY(mem.alloc(&P.qJ, rr));
+      SMA_TRY(mem.alloc(&P.qRt, rr));
+      SMA_TRY(mem.alloc(&P.qL, frc));
+    }
     SMA_TRY(mem.alloc(&P.V, (size_t)P.rc * P.rc * p));
     SMA_TRY(mem.alloc(&P.sigma, (size_t)P.rc * p));
     SMA_TRY(mem.alloc(&P.suf, (size_t)(P.rc + 1) * p));
@@ -658,16 +691,38 @@ JacobiParams<T> jacobi_params(sma_ctx* h, const JacobiPlan& jp) {
 }
 
 template <typename T>
+QrParams<T> qr_params(const Prob<T>& P) {
+  QrParams<T> q;
+  q.src = P.Xh; q.src_bs = (int64_t)P.m * P.n;
+  q.m = P.m; q.mm = P.mm; q.rc = P.rc; q.trans = P.trans;
+  q.plan = P.qplan;
+  q.F = P.qF; q.F_bs = (int64_t)P.mm * P.rc;
+  q.G = P.qG; q.G_bs = (int64_t)P.mm * P.qplan.novf;
+  q.tau = P.qtau; q.perm = P.qperm;
+  q.Jin = P.qJ; q.J_bs = (int64_t)P.rc * P.rc;
+  q.W = P.U; q.W_bs = (int64_t)P.rc * P.rc;
+  q.V = P.V; q.V_bs = (int64_t)P.rc * P.rc;
+  q.Rt = P.qRt; q.Rt_bs = (int64_t)P.rc * P.rc;
+  q.L = P.qL; q.L_bs = (int64_t)P.mm * P.rc;
+  return q;
+}
+
+template <typename T>
 sma_status tsvdm_svd(sma_ctx* h, Prob<T>& P) {
   cudaStream_t st = h->st;
-  const int m = P.m, n = P.n, p = P.p, mm = P.mm, rc = P.rc;
+  const int m = P.m, n = P.n, p = P.p, rc = P.rc;
   const int64_t mn = (int64_t)m * n;
   stage_begin(h, SMA_STAGE_SVD);
+  if (P.qr) SMA_K(qrcp<T>(qr_params(P), p, st));
   {
     JacobiParams<T> J = jacobi_params<T>(h, P.jp);
-    J.src = P.Xh; J.src_bs = mn; J.m = m; J.n = n;
-    J.W = P.Wj; J.W_bs = (int64_t)(mm + rc) * rc;
-    J.U = P.U; J.U_bs = (int64_t)mm * rc;
+    if (P.qr) {
+      J.src = P.qJ; J.src_bs = (int64_t)rc * rc; J.m = rc; J.n = rc;
+    } else {
+      J.src = P.Xh; J.src_bs = mn; J.m = m; J.n = n;
+    }
+    J.W = P.Wj; J.W_bs = (int64_t)(P.jp.mm + P.jp.rc) * P.jp.rc;
+    J.U = P.U; J.U_bs = (int64_t)P.jp.mm * rc;
     J.V = P.V; J.V_bs = (int64_t)rc * rc;
     J.sigma = P.sigma; J.sweeps = P.sweeps; J.status = P.status;
     SMA_K(jacobi_svd<T>(J, p, P.jp.threads, P.jp.smem, st));
@@ -680,6 +735,8 @@ sma_status tsvdm_svd(sma_ctx* h, Prob<T>& P) {
 template <typename T>
 sma_status tsvdm_svd_batched(sma_ctx* h) {
   stage_begin(h, SMA_STAGE_SVD);
+  for (auto& P : probs<T>(h))
+    if (P.qr) SMA_K(qrcp<T>(qr_params(P), P.p, h->st));
   for (auto& b : bins<T>(h)) {
     JacobiParams<T> J = jacobi_params<T>(h, b.jp);
     J.desc = b.desc;
@@ -708,17 +765,22 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P) {
   // discarded columns rho_i..rc-1), or Xhat_i - V_d W_d^T when the slice was
   // processed transposed.  Subtracting the discarded part keeps the error of
   // the rebuilt slice proportional to the discarded energy, not to ||Xhat_i||.
+  // With the QR preconditioning the slice is (Q1 V)(P W)^T: L = Q1 [V_d; 0]
+  // and Rt = P W take the places of W and V.
   const int64_t urc = (int64_t)mm * rc, vrc = (int64_t)rc * rc;
+  if (P.qr) SMA_K(qr_finish<T>(qr_params(P), P.ranks, p, st));
+  T* const Lf = P.qr ? P.qL : P.U;
+  T* const Rf = P.qr ? P.qRt : P.V;
   SMA_CK(cudaMemcpyAsync(P.D, P.Xh, sizeof(T) * (size_t)mn * p, cudaMemcpyDeviceToDevice, st));
   {
     GemmParams<T> g;
     g.M = m; g.N = n; g.K = rc; g.dKoff = P.ranks;
-    if (!P.jp.trans) {
-      g.A = P.U; g.a_rs = 1; g.a_cs = mm; g.a_b1 = urc;
-      g.B = P.V; g.b_rs = rc; g.b_cs = 1; g.b_b1 = vrc;
+    if (!P.trans) {
+      g.A = Lf; g.a_rs = 1; g.a_cs = mm; g.a_b1 = urc;
+      g.B = Rf; g.b_rs = rc; g.b_cs = 1; g.b_b1 = vrc;
     } else {
-      g.A = P.V; g.a_rs = 1; g.a_cs = rc; g.a_b1 = vrc;
-      g.B = P.U; g.b_rs = mm; g.b_cs = 1; g.b_b1 = urc;
+      g.A = Rf; g.a_rs = 1; g.a_cs = rc; g.a_b1 = vrc;
+      g.B = Lf; g.b_rs = mm; g.b_cs = 1; g.b_b1 = urc;
     }
     g.C = P.D; g.c_rs = 1; g.c_cs = m; g.c_b1 = mn;
     g.alpha = T(-1); g.beta = T(1);
@@ -728,13 +790,16 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P) {
   // structured Kronecker factors C_i = struct_E(M[i, :])
   SMA_K(build_struct_terms<T>(P.d_map, P.d_isq, P.ell, P.q, P.Mt, 1, p, p, nullptr, P.C, st));
   stage_end(h);
-  // orthogonality of the retained left (or right) singular vectors
+  // orthogonality of the retained columns of the Jacobi W (the slice's left
+  // singular vectors, or with the QR preconditioning its right ones)
   stage_begin(h, SMA_STAGE_REPORT);
   {
+    const int jmm = P.jp.mm;
+    const int64_t ubs = (int64_t)jmm * rc;
     GemmParams<T> g;
-    g.M = rc; g.N = rc; g.K = mm; g.dM = P.ranks; g.dN = P.ranks;
-    g.A = P.U; g.a_rs = mm; g.a_cs = 1; g.a_b1 = urc;
-    g.B = P.U; g.b_rs = 1; g.b_cs = mm; g.b_b1 = urc;
+    g.M = rc; g.N = rc; g.K = jmm; g.dM = P.ranks; g.dN = P.ranks;
+    g.A = P.U; g.a_rs = jmm; g.a_cs = 1; g.a_b1 = ubs;
+    g.B = P.U; g.b_rs = 1; g.b_cs = jmm; g.b_b1 = ubs;
     g.C = P.Gorth; g.c_rs = 1; g.c_cs = rc; g.c_b1 = (int64_t)rc * rc;
     g.nb1 = p;
     SMA_K(gemm<T>(g, st));
@@ -1569,19 +1634,23 @@ sma_status build_bins(sma_ctx* h) {
   std::vector<std::vector<SliceDesc<T>>> host;
   for (auto& P : ps) {
     size_t bi = 0;
+    // the Jacobi input: the slice, or R1^T (rc x rc) with the QR preconditioning
+    const int jm = P.qr ? P.rc : P.m, jn = P.qr ? P.rc : P.n;
     for (; bi < bs.size(); ++bi)
-      if (bs[bi].m == P.m && bs[bi].n == P.n) break;
+      if (bs[bi].m == jm && bs[bi].n == jn) break;
     if (bi == bs.size()) {
       SvdBin<T> b;
-      b.m = P.m;
-      b.n = P.n;
+      b.m = jm;
+      b.n = jn;
       b.jp = P.jp;
       bs.push_back(b);
       host.emplace_back();
     }
-    const int64_t mn = (int64_t)P.m * P.n, urc = (int64_t)P.mm * P.rc, vrc = (int64_t)P.rc * P.rc;
+    const int64_t jmn = (int64_t)jm * jn, urc = (int64_t)P.jp.mm * P.rc,
+                  vrc = (int64_t)P.rc * P.rc;
+    const T* jsrc = P.qr ? P.qJ : P.Xh;
     for (int k = 0; k < P.p; ++k)
-      host[bi].push_back(SliceDesc<T>{P.Xh + k * mn, P.U + k * urc, P.V + k * vrc,
+      host[bi].push_back(SliceDesc<T>{jsrc + k * jmn, P.U + k * urc, P.V + k * vrc,
                                       P.sigma + (int64_t)k * P.rc, P.sweeps + k, P.status});
   }
   for (size_t bi = 0; bi < bs.size(); ++bi) {
@@ -1629,6 +1698,7 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   if ((int)opt->mkind < 0 || opt->mkind > SMA_M_USER) return SMA_ERR_ARG;
   if (opt->layout != SMA_INPUT_DENSE && opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
   if (opt->fixed_rank < 0 || !(opt->rel_tol >= 0.0)) return SMA_ERR_ARG;
+  if ((int)opt->precondition < 0 || opt->precondition > SMA_PRECOND_QRCP) return SMA_ERR_ARG;
   // host-side validation of every problem before any CUDA call
   for (int i = 0; i < nprob; ++i) {
     std::vector<int64_t> eta;

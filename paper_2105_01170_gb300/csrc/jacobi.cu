@@ -512,6 +512,8 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
 template <typename T>
 JacobiPlan jacobi_plan(int m, int n, int max_smem) {
   JacobiPlan pl;
+  // leave room for the kernel's static shared memory
+  max_smem = max_smem > 1024 ? max_smem - 1024 : 0;
   pl.trans = (m < n) ? 1 : 0;
   pl.mm = pl.trans ? n : m;
   pl.rc = pl.trans ? m : n;

@@ -56,6 +56,36 @@ template <typename T>
 cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_t smem,
                        cudaStream_t st);
 
+// ---- QR preconditioning of the slice SVD (qr.cu) ---------------------------
+// Shared-memory plan: the factorisation keeps nslot columns of a slice in
+// shared memory and novf = rc - nslot in the global overflow G; the finish
+// kernel keeps up to fslot of the columns it builds in shared memory.
+struct QrPlan {
+  int nslot = 0, novf = 0, fslot = 0;
+  size_t smem_qr = 0, smem_fin = 0;
+};
+template <typename T> QrPlan qr_plan(int mm, int rc, int max_smem);
+template <typename T>
+struct QrParams {
+  const T* src = nullptr; int64_t src_bs = 0;   // slices m x n, ld m
+  int m = 0, mm = 0, rc = 0, trans = 0;         // B = slice (trans = 0) or its transpose
+  QrPlan plan{};
+  T* F = nullptr; int64_t F_bs = 0;             // out: reflectors and R1, mm x rc per slice
+  T* G = nullptr; int64_t G_bs = 0;             // overflow columns, mm x novf per slice
+  T* tau = nullptr;                             // out: rc per slice
+  int* perm = nullptr;                          // out: rc per slice
+  T* Jin = nullptr; int64_t J_bs = 0;           // out: R1^T, rc x rc per slice
+  const T* W = nullptr; int64_t W_bs = 0;       // Jacobi W of R1^T (rc x rc)
+  const T* V = nullptr; int64_t V_bs = 0;       // Jacobi V of R1^T (rc x rc)
+  T* Rt = nullptr; int64_t Rt_bs = 0;           // out: P W, rc x rc
+  T* L = nullptr; int64_t L_bs = 0;             // out: Q1 [V_d; 0], mm x rc
+};
+// B P = Q1 R1 for every slice's working matrix B (mm x rc); writes R1^T.
+template <typename T> cudaError_t qrcp(const QrParams<T>& P, int nslices, cudaStream_t st);
+// Rt = P W and L_d = Q1 [V_d; 0] for columns ranks[s]..rc-1.
+template <typename T>
+cudaError_t qr_finish(const QrParams<T>& P, const int* ranks, int nslices, cudaStream_t st);
+
 // ---- step 4: truncation ---------------------------------------------------
 // sigma: rc x p (descending per slice).  Tolerance rule when fixed_rank <= 0.
 // energies != 0: sigma holds energies (Gram eigenvalues) instead.

@@ -1,0 +1,381 @@
+// QR preconditioning of the per-slice one-sided Jacobi SVD.
+//
+// One-sided Jacobi converges in markedly fewer sweeps on the transposed
+// triangular factor of a column-pivoted QR than on the slice itself (the
+// preconditioning of Drmac and Veselic, "New fast and accurate Jacobi SVD
+// algorithm", 2008): with  B P = Q1 R1  (B the mm x rc working matrix),
+// Jacobi on R1^T gives R1^T = W V^T, hence
+//     B = (Q1 V) (P W)^T,
+// with the singular values the column norms of W.  qrcp_kernel factors every
+// slice (Householder reflectors, LAPACK-style storage: R on and above the
+// diagonal, the reflector tails below, tau separately) and writes R1^T as the
+// Jacobi input; qr_finish_kernel forms P W (a row scatter) and Q1 [V_d; 0]
+// for the columns d = rho_i..rc-1 that the truncation discards, which is all
+// the truncated rebuild  Xhat_i - (Q1 V_d)(P W_d)^T  needs.
+//
+// One CTA per slice.  The active columns live in shared memory as far as it
+// holds them; pivoting swaps column pointers, never data.  Columns that do not
+// fit go to a global overflow; the columns with the largest norms are placed
+// there, since the pivoting retires them first.  The partial column norms are
+// recomputed exactly after every step from the updated column (it is in
+// registers anyway), so no downdating formula is involved.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sma {
+namespace {
+
+constexpr int QR_THREADS = 512;
+constexpr int QR_RPL = 8;   // rows per lane held in registers by the column update
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+template <typename T>
+__device__ __forceinline__ T load_slice(const T* src, int m, int trans, int r, int c) {
+  return trans ? src[c + (int64_t)r * m] : src[r + (int64_t)c * m];
+}
+
+// block-wide argmax over nrm[k..rc) (ties: smallest index); all threads get it
+__device__ __forceinline__ int block_argmax(const double* nrm, int k, int rc, double* rv,
+                                            int* ri) {
+  double best = -1.0;
+  int bi = k;
+  for (int j = k + threadIdx.x; j < rc; j += blockDim.x)
+    if (nrm[j] > best) {
+      best = nrm[j];
+      bi = j;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    rv[w] = best;
+    ri[w] = bi;
+  }
+  __syncthreads();
+  if (w == 0) {
+    best = threadIdx.x < (unsigned)nw ? rv[threadIdx.x] : -1.0;
+    bi = threadIdx.x < (unsigned)nw ? ri[threadIdx.x] : k;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (threadIdx.x == 0) ri[32] = bi;
+  }
+  __syncthreads();
+  return ri[32];
+}
+
+// x <- (I - tau v v^T) x on rows k..mm-1 of one column, by one warp (v[k] = 1,
+// v zero above k).  With NORM, returns to every lane ||x[k+1..mm)||^2 of the
+// updated column.
+template <typename T, bool NORM>
+__device__ __forceinline__ double reflect_col(T* x, const T* v, T tau, int k, int mm, int lane) {
+  double a = 0.0;
+  if (mm - k <= 32 * QR_RPL) {
+    T xr[QR_RPL];
+    T w = T(0);
+#pragma unroll
+    for (int i = 0; i < QR_RPL; ++i) {
+      const int r = k + lane + 32 * i;
+      xr[i] = r < mm ? x[r] : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < QR_RPL; ++i) {
+      const int r = k + lane + 32 * i;
+      if (r < mm) w = fma(v[r], xr[i], w);
+    }
+    w = warp_sum(w);
+    const T tw = tau * w;
+#pragma unroll
+    for (int i = 0; i < QR_RPL; ++i) {
+      const int r = k + lane + 32 * i;
+      if (r < mm) {
+        const T y = fma(-tw, v[r], xr[i]);
+        x[r] = y;
+        if (NORM && r > k) a = fma((double)y, (double)y, a);
+      }
+    }
+  } else {
+    T w = T(0);
+    for (int r = k + lane; r < mm; r += 32) w = fma(v[r], x[r], w);
+    w = warp_sum(w);
+    const T tw = tau * w;
+    for (int r = k + lane; r < mm; r += 32) {
+      const T y = fma(-tw, v[r], x[r]);
+      x[r] = y;
+      if (NORM && r > k) a = fma((double)y, (double)y, a);
+    }
+  }
+  if (NORM) a = warp_sum(a);
+  return a;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = blockIdx.x;
+  const int mm = P.mm, rc = P.rc;
+  const int novf = P.plan.novf;
+  const size_t colb = align16((size_t)mm * sizeof(T));
+  double* nrm = reinterpret_cast<double*>(smem_raw);                  // [rc]
+  T** colp = reinterpret_cast<T**>(nrm + rc);                         // [rc]
+  int* perm = reinterpret_cast<int*>(colp + rc);                      // [rc]
+  int* ipos = perm + rc;                                              // [rc]
+  unsigned char* p1 = smem_raw + align16((size_t)rc * 24);
+  T* v = reinterpret_cast<T*>(p1);                                    // [mm]
+  unsigned char* slots = p1 + colb;                                   // [nslot][mm]
+  __shared__ double rv[32];
+  __shared__ int ri[33];
+  __shared__ double red[32];
+  __shared__ T sh_tau, sh_beta, sh_scale;
+  const T* src = P.src + (int64_t)s * P.src_bs;
+  T* F = P.F + (int64_t)s * P.F_bs;
+  T* G = P.G + (int64_t)s * P.G_bs;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+
+  // column norms of B, then the order by descending norm (ties by index)
+  for (int c = warp; c < rc; c += nw) {
+    double a = 0.0;
+    for (int r = lane; r < mm; r += 32) {
+      const double x = (double)load_slice(src, P.m, P.trans, r, c);
+      a = fma(x, x, a);
+    }
+    a = warp_sum(a);
+    if (lane == 0) nrm[c] = a;
+  }
+  __syncthreads();
+  // (a NaN norm counts as -1 so that the order stays total and the ranks a
+  // permutation)
+  for (int c = tid; c < rc; c += nth) {
+    const double nc = nrm[c] == nrm[c] ? nrm[c] : -1.0;
+    int rk = 0;
+    for (int i = 0; i < rc; ++i) {
+      const double ni = nrm[i] == nrm[i] ? nrm[i] : -1.0;
+      rk += (ni > nc || (ni == nc && i < c)) ? 1 : 0;
+    }
+    perm[rk] = c;
+    ipos[c] = rk;
+  }
+  // position j starts with the column of rank j; the first novf positions
+  // (largest norms) are stored in the overflow
+  for (int j = tid; j < rc; j += nth)
+    colp[j] = j < novf ? G + (int64_t)j * mm
+                       : reinterpret_cast<T*>(slots + (size_t)(j - novf) * colb);
+  __syncthreads();
+  for (int e = tid; e < mm * rc; e += nth) {
+    int r, c;
+    if (P.trans) { c = e % rc; r = e / rc; } else { r = e % mm; c = e / mm; }
+    colp[ipos[c]][r] = load_slice(src, P.m, P.trans, r, c);
+  }
+  __syncthreads();
+  for (int j = warp; j < rc; j += nw) {
+    const T* cj = colp[j];
+    double a = 0.0;
+    for (int r = lane; r < mm; r += 32) {
+      const double x = (double)cj[r];
+      a = fma(x, x, a);
+    }
+    a = warp_sum(a);
+    if (lane == 0) nrm[j] = a;
+  }
+  __syncthreads();
+
+  for (int k = 0; k < rc; ++k) {
+    // pivot: the remaining column with the largest norm (pointer swap)
+    const int jp = block_argmax(nrm, k, rc, rv, ri);
+    if (jp != k && tid == 0) {
+      const double t = nrm[k]; nrm[k] = nrm[jp]; nrm[jp] = t;
+      T* tp = colp[k]; colp[k] = colp[jp]; colp[jp] = tp;
+      const int pi = perm[k]; perm[k] = perm[jp]; perm[jp] = pi;
+    }
+    __syncthreads();
+    // Householder reflector of B[k:, k]: copy to v, norm of the tail
+    const T* ck = colp[k];
+    double s2 = 0.0;
+    for (int r = k + tid; r < mm; r += nth) {
+      const T x = ck[r];
+      v[r] = x;
+      if (r > k) s2 = fma((double)x, (double)x, s2);
+    }
+    s2 = block_sum(s2, red);
+    if (tid == 0) {
+      const double alpha = (double)v[k];
+      if (s2 == 0.0) {
+        sh_tau = T(0);
+        sh_beta = (T)alpha;
+        sh_scale = T(1);
+      } else {
+        const double beta = -copysign(sqrt(alpha * alpha + s2), alpha);
+        sh_tau = (T)((beta - alpha) / beta);
+        sh_beta = (T)beta;
+        sh_scale = (T)(1.0 / (alpha - beta));
+      }
+    }
+    __syncthreads();
+    const T tau = sh_tau;
+    // retire column k into F: R[0..k, k] and the reflector tail
+    T* Fk = F + (int64_t)k * mm;
+    for (int r = tid; r < mm; r += nth) {
+      T out;
+      if (r < k) {
+        out = ck[r];
+      } else if (r == k) {
+        out = sh_beta;
+      } else {
+        out = v[r] * sh_scale;
+        v[r] = out;
+      }
+      Fk[r] = out;
+    }
+    if (tid == 0) {
+      v[k] = T(1);
+      P.tau[(int64_t)s * rc + k] = tau;
+    }
+    __syncthreads();
+    // apply the reflector to the remaining columns; exact partial norms
+    for (int j = k + 1 + warp; j < rc; j += nw) {
+      const double a = reflect_col<T, true>(colp[j], v, tau, k, mm, lane);
+      if (lane == 0) nrm[j] = a;
+    }
+    __syncthreads();
+  }
+  // Jacobi input R1^T (rc x rc, lower triangular); the permutation
+  T* J = P.Jin + (int64_t)s * P.J_bs;
+  for (int e = tid; e < rc * rc; e += nth) {
+    const int r = e % rc, c = e / rc;
+    J[r + (int64_t)c * rc] = (c <= r) ? F[c + (int64_t)r * mm] : T(0);
+  }
+  for (int j = tid; j < rc; j += nth) P.perm[(int64_t)s * rc + j] = perm[j];
+}
+
+// Rt = P W (row j of W to row perm[j]) for all columns; L_d = Q1 [V_d; 0]
+// for the discarded columns d = ranks[s]..rc-1, the reflectors applied last
+// to first with the next reflector fetched while the current one is applied.
+// The first fslot of those columns are built in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS) qr_finish_kernel(const QrParams<T> P,
+                                                                const int* __restrict__ ranks) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = blockIdx.x;
+  const int mm = P.mm, rc = P.rc;
+  const size_t colb = align16((size_t)mm * sizeof(T));
+  unsigned char* slots = smem_raw + 2 * colb;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+  const int* perm = P.perm + (int64_t)s * rc;
+  const T* W = P.W + (int64_t)s * P.W_bs;        // rc x rc (Jacobi W of R1^T)
+  const T* V = P.V + (int64_t)s * P.V_bs;        // rc x rc
+  T* Rt = P.Rt + (int64_t)s * P.Rt_bs;           // rc x rc
+  T* L = P.L + (int64_t)s * P.L_bs;              // mm x rc
+  const T* F = P.F + (int64_t)s * P.F_bs;
+  const T* tau = P.tau + (int64_t)s * rc;
+  for (int e = tid; e < rc * rc; e += nth) {
+    const int j = e % rc, c = e / rc;
+    const int pj = perm[j];
+    if ((unsigned)pj < (unsigned)rc) Rt[pj + (int64_t)c * rc] = W[j + (int64_t)c * rc];
+  }
+  const int d0 = ranks ? min(max(ranks[s], 0), rc) : 0;
+  const int nd = rc - d0;
+  if (nd == 0) return;
+  const int fslot = P.plan.fslot;
+  auto col = [&](int t) -> T* {
+    return t < fslot ? reinterpret_cast<T*>(slots + (size_t)t * colb)
+                     : L + (int64_t)(d0 + t) * mm;
+  };
+  for (int e = tid; e < mm * nd; e += nth) {
+    const int r = e % mm, t = e / mm;
+    col(t)[r] = (r < rc) ? V[r + (int64_t)(d0 + t) * rc] : T(0);
+  }
+  {
+    const int k = rc - 1;
+    T* v0 = reinterpret_cast<T*>(smem_raw);
+    for (int r = k + tid; r < mm; r += nth) v0[r] = (r == k) ? T(1) : F[r + (int64_t)k * mm];
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int k = rc - 1; k >= 0; --k) {
+    const T* vk = reinterpret_cast<const T*>(smem_raw + (size_t)cur * colb);
+    if (k > 0) {
+      T* nx = reinterpret_cast<T*>(smem_raw + (size_t)(cur ^ 1) * colb);
+      const int k1 = k - 1;
+      for (int r = k1 + tid; r < mm; r += nth) nx[r] = (r == k1) ? T(1) : F[r + (int64_t)k1 * mm];
+    }
+    const T tk = tau[k];
+    if (tk != T(0))
+      for (int t = warp; t < nd; t += nw) reflect_col<T, false>(col(t), vk, tk, k, mm, lane);
+    __syncthreads();
+    cur ^= 1;
+  }
+  const int ns = min(nd, fslot);
+  for (int e = tid; e < mm * ns; e += nth) {
+    const int r = e % mm, t = e / mm;
+    L[r + (int64_t)(d0 + t) * mm] = col(t)[r];
+  }
+}
+
+}  // namespace
+
+template <typename T>
+QrPlan qr_plan(int mm, int rc, int max_smem) {
+  QrPlan q;
+  // leave room for the kernels' static shared memory
+  max_smem = max_smem > 1024 ? max_smem - 1024 : 0;
+  const size_t colb = align16((size_t)mm * sizeof(T));
+  const size_t head = align16((size_t)rc * 24) + colb;
+  const size_t avail = (size_t)max_smem > head ? (size_t)max_smem - head : 0;
+  q.nslot = (int)std::min<size_t>((size_t)rc, avail / colb);
+  q.novf = rc - q.nslot;
+  q.smem_qr = head + (size_t)q.nslot * colb;
+  const size_t fhead = 2 * colb;
+  const size_t favail = (size_t)max_smem > fhead ? (size_t)max_smem - fhead : 0;
+  q.fslot = (int)std::min<size_t>((size_t)rc, favail / colb);
+  q.smem_fin = fhead + (size_t)q.fslot * colb;
+  return q;
+}
+
+template <typename T>
+cudaError_t qrcp(const QrParams<T>& P, int nslices, cudaStream_t st) {
+  if (nslices <= 0) return cudaSuccess;
+  if (P.plan.novf > 0 && !P.G) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(qrcp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)P.plan.smem_qr);
+  if (e != cudaSuccess) return e;
+  qrcp_kernel<T><<<nslices, QR_THREADS, P.plan.smem_qr, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t qr_finish(const QrParams<T>& P, const int* ranks, int nslices, cudaStream_t st) {
+  if (nslices <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(qr_finish_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)P.plan.smem_fin);
+  if (e != cudaSuccess) return e;
+  qr_finish_kernel<T><<<nslices, QR_THREADS, P.plan.smem_fin, st>>>(P, ranks);
+  return cudaGetLastError();
+}
+
+template QrPlan qr_plan<float>(int, int, int);
+template QrPlan qr_plan<double>(int, int, int);
+template cudaError_t qrcp<float>(const QrParams<float>&, int, cudaStream_t);
+template cudaError_t qrcp<double>(const QrParams<double>&, int, cudaStream_t);
+template cudaError_t qr_finish<float>(const QrParams<float>&, const int*, int, cudaStream_t);
+template cudaError_t qr_finish<double>(const QrParams<double>&, const int*, int, cudaStream_t);
+
+}  // namespace sma

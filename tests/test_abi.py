@@ -43,7 +43,8 @@ def test_version_and_status_strings(lib):
 def _create(problems, **kw):
     opt = S.sma_options(kw.get("prec", S.SMA_FP64), kw.get("decomp", S.SMA_TSVDM),
                         kw.get("mkind", S.SMA_M_DCT2), kw.get("layout", S.SMA_INPUT_DENSE),
-                        None, kw.get("fixed_rank", 0), kw.get("rel_tol", 1e-6), 0, None, 0, 0)
+                        None, kw.get("fixed_rank", 0), kw.get("rel_tol", 1e-6), 0, None, 0, 0,
+                        kw.get("precondition", S.SMA_PRECOND_AUTO))
     structs, keep = [], []
     for ell, q, m, n, p, bm in problems:
         b = np.ascontiguousarray(np.asarray(bm, dtype=np.int32).ravel(order="F"))
@@ -75,6 +76,8 @@ def test_rejects_bad_sizes_and_options(lib):
     assert _create([(3, 3, 2, 3, 5, bm)], decomp=S.SMA_TUCKER_SHARED_U)[0] == S.SMA_ERR_ARG
     assert _create([(3, 3, 2, 2, 5, bm)], mkind=S.SMA_M_USER)[0] == S.SMA_ERR_ARG
     assert _create([(3, 3, 2, 2, 5, bm)], prec=7)[0] == S.SMA_ERR_ARG
+    assert _create([(3, 3, 2, 2, 5, bm)], precondition=3)[0] == S.SMA_ERR_ARG
+    assert _create([(3, 3, 2, 2, 5, bm)], precondition=-1)[0] == S.SMA_ERR_ARG
     assert S.sma_create([], S.sma_options())[0] == S.SMA_ERR_ARG
 
 

@@ -54,6 +54,9 @@ def problem(kind):
     if kind == "block_mode_fp32":          # 256 x 256 fp32 exceeds shared memory
         bm = G.toeplitz_map(2)
         return G.Problem(kind, g.standard_normal((3, 256, 256)), bm)
+    if kind == "tall_300x40":              # QR reflectors longer than 256 rows
+        bm = G.toeplitz_map(2)
+        return G.Problem(kind, g.standard_normal((3, 300, 40)), bm)
     raise KeyError(kind)
 
 
@@ -86,14 +89,19 @@ def test_transform_matches(prec, kind):
     assert rel(Xh, Xho) < (1e-14 if prec == S.SMA_FP64 else 2e-6)
 
 
+PRECONDS = [S.SMA_PRECOND_NONE, S.SMA_PRECOND_QRCP]
+QNAME = {S.SMA_PRECOND_NONE: "plain", S.SMA_PRECOND_QRCP: "qrcp"}
+
+
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 @pytest.mark.parametrize("kind", ["toeplitz_ragged", "wide_trans", "tridiag_zero_blocks",
                                   "planted_cfg1", "single_block", "block_mode_fp64",
-                                  "block_mode_fp32"])
+                                  "block_mode_fp32", "tall_300x40"])
 @pytest.mark.parametrize("tol", [1e-2, 1e-6])
-def test_tsvdm_end_to_end(prec, kind, tol):
+@pytest.mark.parametrize("pre", PRECONDS, ids=QNAME.get)
+def test_tsvdm_end_to_end(prec, kind, tol, pre):
     pr = problem(kind)
-    h, A, res = run(pr, prec, rel_tol=tol)
+    h, A, res = run(pr, prec, rel_tol=tol, precondition=pre)
     X = oracle_tensor(A, pr)
     M = O.dct2_matrix(pr.p)
     ora = O.tsvdm(X, M, rel_tol=tol)
@@ -129,9 +137,10 @@ def test_tsvdm_end_to_end(prec, kind, tol):
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 @pytest.mark.parametrize("kind", ["toeplitz_ragged", "wide_trans", "tridiag_zero_blocks"])
-def test_kron_sum_apply(prec, kind):
+@pytest.mark.parametrize("pre", PRECONDS, ids=QNAME.get)
+def test_kron_sum_apply(prec, kind, pre):
     pr = problem(kind)
-    h, A, res = run(pr, prec, rel_tol=1e-2)
+    h, A, res = run(pr, prec, rel_tol=1e-2, precondition=pre)
     ora = O.tsvdm(oracle_tensor(A, pr), O.dct2_matrix(pr.p), rel_tol=1e-2)
     assert np.array_equal(h.ranks(0), ora.ranks) or prec == S.SMA_MIXED
     x = G.random_rhs(pr.q * pr.n, 5, 0).astype(np_dtype(prec)).astype(np.float64)
@@ -154,7 +163,8 @@ def test_planted_rank_ranks_equal_with_margin():
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
-def test_planted_slice_ranks_and_zero_rank_slices(prec):
+@pytest.mark.parametrize("pre", PRECONDS, ids=QNAME.get)
+def test_planted_slice_ranks_and_zero_rank_slices(prec, pre):
     m, n, p = 12, 9, 6
     ranks = [3, 0, 1, 5, 2, 0]
     L, R = G.planted_tsvdm_tensor(m, n, p, ranks)
@@ -164,7 +174,7 @@ def test_planted_slice_ranks_and_zero_rank_slices(prec):
     # a block-diagonal matrix whose distinct blocks are the slices of X
     blocks = np.transpose(X, (2, 0, 1)).copy()
     pr = G.Problem("planted_tsvdm", blocks, G.block_diagonal_map(p))
-    h, A, res = run(pr, prec, rel_tol=1e-4)
+    h, A, res = run(pr, prec, rel_tol=1e-4, precondition=pre)
     ora = O.tsvdm(oracle_tensor(A, pr), M, rel_tol=1e-4)
     assert list(ora.ranks) == ranks
     assert list(h.ranks(0)) == ranks
@@ -176,10 +186,11 @@ def test_planted_slice_ranks_and_zero_rank_slices(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
-def test_fixed_rank_and_user_transform(prec):
+@pytest.mark.parametrize("pre", PRECONDS, ids=QNAME.get)
+def test_fixed_rank_and_user_transform(prec, pre):
     pr = problem("toeplitz_ragged")
     Mu = G.random_orthogonal(pr.p, 5)
-    h, A, res = run(pr, prec, fixed_rank=2, mkind=S.SMA_M_USER, M_user=Mu)
+    h, A, res = run(pr, prec, fixed_rank=2, mkind=S.SMA_M_USER, M_user=Mu, precondition=pre)
     ora = O.tsvdm(oracle_tensor(A, pr), Mu, fixed_rank=2)
     assert list(h.ranks(0)) == [2] * pr.p
     Ah = reconstruct(h, pr, prec)
