@@ -215,7 +215,9 @@ typedef enum {
   SMA_STAGE_FACTORS = 4,    /* truncated slices / core, struct_E terms          */
   SMA_STAGE_REPORT = 5,     /* orthogonality check                              */
   SMA_STAGE_APPLY = 6,      /* the factored matvec                              */
-  SMA_STAGE_COUNT = 7
+  SMA_STAGE_PRECOND = 7,    /* QR preconditioning of the slice SVDs and its
+                               rebuild of the discarded columns               */
+  SMA_STAGE_COUNT = 8
 } sma_stage;
 
 /* Device time of each stage in ms, summed over the calls since the last

@@ -36,7 +36,7 @@ EXPORT_X, EXPORT_XHAT, EXPORT_SIGMA, EXPORT_T, EXPORT_FACTOR = 0, 1, 2, 3, 4
 EXPORTED = ("sma_create", "sma_compress", "sma_get_result", "sma_get_ranks", "sma_reconstruct",
             "sma_apply", "sma_export", "sma_profile", "sma_slice_svd_noalloc", "sma_destroy",
             "sma_status_string", "sma_version")
-STAGES = ("gather", "transform", "svd", "truncate", "factors", "report", "apply")
+STAGES = ("gather", "transform", "svd", "truncate", "factors", "report", "apply", "precond")
 
 
 class sma_problem(ctypes.Structure):

@@ -712,8 +712,12 @@ sma_status tsvdm_svd(sma_ctx* h, Prob<T>& P) {
   cudaStream_t st = h->st;
   const int m = P.m, n = P.n, p = P.p, rc = P.rc;
   const int64_t mn = (int64_t)m * n;
+  if (P.qr) {
+    stage_begin(h, SMA_STAGE_PRECOND);
+    SMA_K(qrcp<T>(qr_params(P), p, st));
+    stage_end(h);
+  }
   stage_begin(h, SMA_STAGE_SVD);
-  if (P.qr) SMA_K(qrcp<T>(qr_params(P), p, st));
   {
     JacobiParams<T> J = jacobi_params<T>(h, P.jp);
     if (P.qr) {
@@ -734,9 +738,11 @@ sma_status tsvdm_svd(sma_ctx* h, Prob<T>& P) {
 // all slices of all t-SVDM problems, one launch per slice size
 template <typename T>
 sma_status tsvdm_svd_batched(sma_ctx* h) {
-  stage_begin(h, SMA_STAGE_SVD);
+  stage_begin(h, SMA_STAGE_PRECOND);
   for (auto& P : probs<T>(h))
     if (P.qr) SMA_K(qrcp<T>(qr_params(P), P.p, h->st));
+  stage_end(h);
+  stage_begin(h, SMA_STAGE_SVD);
   for (auto& b : bins<T>(h)) {
     JacobiParams<T> J = jacobi_params<T>(h, b.jp);
     J.desc = b.desc;
@@ -760,6 +766,11 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P) {
   SMA_K(truncate_ranks(P.sigma, rc, p, P.stats, h->opt.rel_tol, h->opt.fixed_rank, P.ranks, P.off,
                         P.stats + 1, P.iscal, P.suf, st, 0));
   stage_end(h);
+  if (P.qr) {
+    stage_begin(h, SMA_STAGE_PRECOND);
+    SMA_K(qr_finish<T>(qr_params(P), P.ranks, p, st));
+    stage_end(h);
+  }
   stage_begin(h, SMA_STAGE_FACTORS);
   // truncated slices: D_i = Xhat_i - W_d V_d^T (W = U Sigma, d = the
   // discarded columns rho_i..rc-1), or Xhat_i - V_d W_d^T when the slice was
@@ -768,7 +779,6 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P) {
   // With the QR preconditioning the slice is (Q1 V)(P W)^T: L = Q1 [V_d; 0]
   // and Rt = P W take the places of W and V.
   const int64_t urc = (int64_t)mm * rc, vrc = (int64_t)rc * rc;
-  if (P.qr) SMA_K(qr_finish<T>(qr_params(P), P.ranks, p, st));
   T* const Lf = P.qr ? P.qL : P.U;
   T* const Rf = P.qr ? P.qRt : P.V;
   SMA_CK(cudaMemcpyAsync(P.D, P.Xh, sizeof(T) * (size_t)mn * p, cudaMemcpyDeviceToDevice, st));

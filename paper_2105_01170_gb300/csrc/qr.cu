@@ -37,10 +37,31 @@ __device__ __forceinline__ T load_slice(const T* src, int m, int trans, int r, i
   return trans ? src[c + (int64_t)r * m] : src[r + (int64_t)c * m];
 }
 
+// block-wide max of v (NaN ignored); every thread gets it; red holds >= 32
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < nw ? red[lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[0] = v;
+  }
+  __syncthreads();
+  v = red[0];
+  __syncthreads();
+  return v;
+}
+
 // block-wide argmax over nrm[k..rc) (ties: smallest index); all threads get it
-__device__ __forceinline__ int block_argmax(const double* nrm, int k, int rc, double* rv,
-                                            int* ri) {
-  double best = -1.0;
+template <typename T>
+__device__ __forceinline__ int block_argmax(const T* nrm, int k, int rc, T* rv, int* ri) {
+  T best = T(-1);
   int bi = k;
   for (int j = k + threadIdx.x; j < rc; j += blockDim.x)
     if (nrm[j] > best) {
@@ -49,7 +70,7 @@ __device__ __forceinline__ int block_argmax(const double* nrm, int k, int rc, do
     }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const T ob = __shfl_xor_sync(0xffffffffu, best, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
     if (ob > best || (ob == best && oi < bi)) {
       best = ob;
@@ -63,11 +84,11 @@ __device__ __forceinline__ int block_argmax(const double* nrm, int k, int rc, do
   }
   __syncthreads();
   if (w == 0) {
-    best = threadIdx.x < (unsigned)nw ? rv[threadIdx.x] : -1.0;
+    best = threadIdx.x < (unsigned)nw ? rv[threadIdx.x] : T(-1);
     bi = threadIdx.x < (unsigned)nw ? ri[threadIdx.x] : k;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) {
         best = ob;
@@ -81,11 +102,12 @@ __device__ __forceinline__ int block_argmax(const double* nrm, int k, int rc, do
 }
 
 // x <- (I - tau v v^T) x on rows k..mm-1 of one column, by one warp (v[k] = 1,
-// v zero above k).  With NORM, returns to every lane ||x[k+1..mm)||^2 of the
-// updated column.
+// v zero above k).  With NORM, returns to every lane ||nsc x[k+1..mm)||^2 of
+// the updated column (nsc a power of two that keeps the squares in range).
 template <typename T, bool NORM>
-__device__ __forceinline__ double reflect_col(T* x, const T* v, T tau, int k, int mm, int lane) {
-  double a = 0.0;
+__device__ __forceinline__ T reflect_col(T* x, const T* v, T tau, int k, int mm, int lane,
+                                         T nsc) {
+  T a = T(0);
   if (mm - k <= 32 * QR_RPL) {
     T xr[QR_RPL];
     T w = T(0);
@@ -107,7 +129,10 @@ __device__ __forceinline__ double reflect_col(T* x, const T* v, T tau, int k, in
       if (r < mm) {
         const T y = fma(-tw, v[r], xr[i]);
         x[r] = y;
-        if (NORM && r > k) a = fma((double)y, (double)y, a);
+        if (NORM && r > k) {
+          const T ys = y * nsc;
+          a = fma(ys, ys, a);
+        }
       }
     }
   } else {
@@ -118,7 +143,10 @@ __device__ __forceinline__ double reflect_col(T* x, const T* v, T tau, int k, in
     for (int r = k + lane; r < mm; r += 32) {
       const T y = fma(-tw, v[r], x[r]);
       x[r] = y;
-      if (NORM && r > k) a = fma((double)y, (double)y, a);
+      if (NORM && r > k) {
+        const T ys = y * nsc;
+        a = fma(ys, ys, a);
+      }
     }
   }
   if (NORM) a = warp_sum(a);
@@ -132,28 +160,45 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   const int mm = P.mm, rc = P.rc;
   const int novf = P.plan.novf;
   const size_t colb = align16((size_t)mm * sizeof(T));
-  double* nrm = reinterpret_cast<double*>(smem_raw);                  // [rc]
-  T** colp = reinterpret_cast<T**>(nrm + rc);                         // [rc]
+  T* nrm = reinterpret_cast<T*>(smem_raw);                            // [rc] (8-byte slots)
+  T** colp = reinterpret_cast<T**>(smem_raw + (size_t)rc * 8);        // [rc]
   int* perm = reinterpret_cast<int*>(colp + rc);                      // [rc]
   int* ipos = perm + rc;                                              // [rc]
   unsigned char* p1 = smem_raw + align16((size_t)rc * 24);
   T* v = reinterpret_cast<T*>(p1);                                    // [mm]
   unsigned char* slots = p1 + colb;                                   // [nslot][mm]
-  __shared__ double rv[32];
+  __shared__ T rv[32];
   __shared__ int ri[33];
   __shared__ double red[32];
-  __shared__ T sh_tau, sh_beta, sh_scale;
+  __shared__ T sh_tau, sh_beta, sh_scale, sh_nsc;
   const T* src = P.src + (int64_t)s * P.src_bs;
   T* F = P.F + (int64_t)s * P.F_bs;
   T* G = P.G + (int64_t)s * P.G_bs;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
 
+  // The norms that steer the pivoting are kept in T (fp64 arithmetic is far
+  // slower than fp32 on this part) for the entries scaled by nsc = 2^-e,
+  // 2^(e-1) <= max |B| < 2^e: an orthogonal update keeps every scaled entry
+  // below sqrt(mm), so no square overflows.
+  T amax = T(0);
+  for (int e = tid; e < mm * rc; e += nth) {
+    int r, c;
+    if (P.trans) { c = e % rc; r = e / rc; } else { r = e % mm; c = e / mm; }
+    amax = fmax(amax, fabs(load_slice(src, P.m, P.trans, r, c)));
+  }
+  amax = block_max(amax, rv);
+  if (tid == 0) {
+    const int ex = (amax > T(0) && isfinite(amax)) ? min(max(ilogb(amax), -100), 100) : -1;
+    sh_nsc = ldexp(T(1), -ex - 1);
+  }
+  __syncthreads();
+  const T nsc = sh_nsc;
   // column norms of B, then the order by descending norm (ties by index)
   for (int c = warp; c < rc; c += nw) {
-    double a = 0.0;
+    T a = T(0);
     for (int r = lane; r < mm; r += 32) {
-      const double x = (double)load_slice(src, P.m, P.trans, r, c);
+      const T x = load_slice(src, P.m, P.trans, r, c) * nsc;
       a = fma(x, x, a);
     }
     a = warp_sum(a);
@@ -163,10 +208,10 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   // (a NaN norm counts as -1 so that the order stays total and the ranks a
   // permutation)
   for (int c = tid; c < rc; c += nth) {
-    const double nc = nrm[c] == nrm[c] ? nrm[c] : -1.0;
+    const T nc = nrm[c] == nrm[c] ? nrm[c] : T(-1);
     int rk = 0;
     for (int i = 0; i < rc; ++i) {
-      const double ni = nrm[i] == nrm[i] ? nrm[i] : -1.0;
+      const T ni = nrm[i] == nrm[i] ? nrm[i] : T(-1);
       rk += (ni > nc || (ni == nc && i < c)) ? 1 : 0;
     }
     perm[rk] = c;
@@ -186,9 +231,9 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   __syncthreads();
   for (int j = warp; j < rc; j += nw) {
     const T* cj = colp[j];
-    double a = 0.0;
+    T a = T(0);
     for (int r = lane; r < mm; r += 32) {
-      const double x = (double)cj[r];
+      const T x = cj[r] * nsc;
       a = fma(x, x, a);
     }
     a = warp_sum(a);
@@ -200,7 +245,7 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
     // pivot: the remaining column with the largest norm (pointer swap)
     const int jp = block_argmax(nrm, k, rc, rv, ri);
     if (jp != k && tid == 0) {
-      const double t = nrm[k]; nrm[k] = nrm[jp]; nrm[jp] = t;
+      const T t = nrm[k]; nrm[k] = nrm[jp]; nrm[jp] = t;
       T* tp = colp[k]; colp[k] = colp[jp]; colp[jp] = tp;
       const int pi = perm[k]; perm[k] = perm[jp]; perm[jp] = pi;
     }
@@ -250,7 +295,7 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
     __syncthreads();
     // apply the reflector to the remaining columns; exact partial norms
     for (int j = k + 1 + warp; j < rc; j += nw) {
-      const double a = reflect_col<T, true>(colp[j], v, tau, k, mm, lane);
+      const T a = reflect_col<T, true>(colp[j], v, tau, k, mm, lane, nsc);
       if (lane == 0) nrm[j] = a;
     }
     __syncthreads();
@@ -318,7 +363,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_finish_kernel(const QrParams<T>
     }
     const T tk = tau[k];
     if (tk != T(0))
-      for (int t = warp; t < nd; t += nw) reflect_col<T, false>(col(t), vk, tk, k, mm, lane);
+      for (int t = warp; t < nd; t += nw) reflect_col<T, false>(col(t), vk, tk, k, mm, lane, T(1));
     __syncthreads();
     cur ^= 1;
   }
