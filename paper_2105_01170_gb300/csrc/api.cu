@@ -684,7 +684,7 @@ template <typename T>
 JacobiParams<T> jacobi_params(sma_ctx* h, const JacobiPlan& jp) {
   JacobiParams<T> J;
   J.mm = jp.mm; J.rc = jp.rc; J.trans = jp.trans; J.ldS = jp.ldS; J.bcols = jp.bcols;
-  J.g = jp.g; J.sort_n = jp.sort_n;
+  J.g = jp.g; J.sort_n = jp.sort_n; J.tile = jp.tile;
   J.max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
   J.tol = 4.0 * std::sqrt((double)jp.mm) * Eps<T>::v;
   return J;
@@ -855,7 +855,7 @@ sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_
   JacobiParams<double> J;
   J.src = G; J.src_bs = 0; J.m = rows; J.n = rows;
   J.mm = jp.mm; J.rc = jp.rc; J.trans = 0; J.ldS = jp.ldS; J.bcols = jp.bcols; J.g = jp.g;
-  J.sort_n = jp.sort_n;
+  J.sort_n = jp.sort_n; J.tile = jp.tile;
   J.max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
   J.tol = 4.0 * std::sqrt((double)rows) * Eps<double>::v;
   J.W = W; J.W_bs = 0;

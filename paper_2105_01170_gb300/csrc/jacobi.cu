@@ -253,6 +253,207 @@ struct Rotator<float, 4> {
   }
 };
 
+// ---- register-tiled sweeps (fp32, float4 rows) -----------------------------
+// The pair-per-group rotations above move both stacked columns through shared
+// memory for every rotation, which makes the sweep bound by shared-memory
+// bandwidth.  In the tiled form a warp holds 8 columns in registers (c = 0..3
+// tile A, 4..7 tile B; lane l keeps the float4 rows q = l + 32 i of the
+// dot-product part, rows < mm) and rotates a group of pairs among them before
+// writing them back: INNER = the pairs inside each tile (3 sub-rounds),
+// CROSS = all A x B pairs (4 sub-rounds).  A sub-round's 4 pairs are disjoint;
+// their 12 dot products are reduced across the warp together (a butterfly
+// reduce-scatter), lanes 0..3 each compute one angle, and the rotations are
+// applied to the registers and recorded.  The recorded rotations are then
+// applied in the same order to the V rows of the 8 columns in one streamed
+// pass: the rows of a stacked column are rotated independently and the angles
+// depend on the W rows only, so the result is the same sequence of rotations
+// as in the untiled form.
+
+// Pair q (0..3) of sub-round r of a group, as register columns (a, b).
+template <bool INNER>
+__device__ __forceinline__ void tile_pair(int r, int q, int& a, int& b) {
+  if (INNER) {
+    const int o = (q >> 1) * 4, i = q & 1;
+    if (r == 0) {
+      a = o + 2 * i;
+      b = o + 2 * i + 1;
+    } else if (r == 1) {
+      a = o + i;
+      b = o + i + 2;
+    } else {
+      a = o + i;
+      b = o + 3 - i;
+    }
+  } else {
+    a = q;
+    b = 4 + ((q + r) & 3);
+  }
+}
+
+// Warp sum of 16 values at once: after the four halving exchanges and a final
+// one, lane l holds the full sum of value (l >> 1) & 15.
+__device__ __forceinline__ float reduce16(const float (&v)[16], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+  float u8[8], u4[4], u2[2];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float send = h4 ? v[i] : v[i + 8];
+    const float keep = h4 ? v[i + 8] : v[i];
+    u8[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float send = h3 ? u8[i] : u8[i + 4];
+    const float keep = h3 ? u8[i + 4] : u8[i];
+    u4[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h2 ? u4[i] : u4[i + 2];
+    const float keep = h2 ? u4[i + 2] : u4[i];
+    u2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  const float send = h1 ? u2[0] : u2[1];
+  const float keep = h1 ? u2[1] : u2[0];
+  float u1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  u1 += __shfl_xor_sync(0xffffffffu, u1, 1);
+  return u1;
+}
+
+__device__ __forceinline__ float dot4(const float4& a, const float4& b, float acc) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+}
+
+__device__ __forceinline__ void rot4(float4& x, float4& y, float c, float s) {
+  const float4 a = x, b = y;
+  x = make_float4(c * a.x - s * b.x, c * a.y - s * b.y, c * a.z - s * b.z, c * a.w - s * b.w);
+  y = make_float4(s * a.x + c * b.x, s * a.y + c * b.y, s * a.z + c * b.z, s * a.w + c * b.w);
+}
+
+// One group of rotations on tiles A (slots sa.., na columns) and B (slots
+// sb.., nb columns) by one warp; columns past na / nb are absent (zero, never
+// rotated).  INNER pairs of A (B) only when doA (doB).  mq = mm / 4 float4
+// rows of dot-product part, rq = rc / 4 float4 rows of V part.  Returns true
+// if any pair was rotated.
+template <int NQW, bool INNER>
+__device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, int sb, int nb,
+                                           bool doA, bool doB, int mq, int rq, int lane,
+                                           float tol, float floor_) {
+  constexpr int NR = INNER ? 3 : 4;
+  float4 x[8][NQW];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const bool valid = c < 4 ? c < na : (c - 4) < nb;
+    const int slot = c < 4 ? sa + c : sb + c - 4;
+    const float4* col = reinterpret_cast<const float4*>(S + (int64_t)(valid ? slot : 0) * ldS);
+#pragma unroll
+    for (int i = 0; i < NQW; ++i) {
+      const int qq = lane + 32 * i;
+      x[c][i] = (valid && qq < mq) ? col[qq] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  float cr[NR][4], sr[NR][4];
+  unsigned mk[NR];
+  unsigned any = 0;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    float v[16];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int a, b;
+      tile_pair<INNER>(r, q, a, b);
+      float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+      for (int i = 0; i < NQW; ++i) {
+        al = dot4(x[a][i], x[a][i], al);
+        be = dot4(x[b][i], x[b][i], be);
+        ga = dot4(x[a][i], x[b][i], ga);
+      }
+      v[q] = al;
+      v[4 + q] = be;
+      v[8 + q] = ga;
+      v[12 + q] = 0.f;
+    }
+    const float red = reduce16(v, lane);
+    const int q = lane & 3;
+    const float al = __shfl_sync(0xffffffffu, red, 2 * q);
+    const float be = __shfl_sync(0xffffffffu, red, 2 * (4 + q));
+    const float ga = __shfl_sync(0xffffffffu, red, 2 * (8 + q));
+    const bool allowed = INNER ? (q < 2 ? doA : doB) : true;
+    float c = 1.f, s = 0.f;
+    const bool ok = allowed && Angle<float>::get(al, be, ga, tol, floor_, c, s);
+    if (!ok) {
+      c = 1.f;
+      s = 0.f;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ok) & 0xfu;
+    mk[r] = m;
+    any |= m;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      cr[r][qq] = __shfl_sync(0xffffffffu, c, qq);
+      sr[r][qq] = __shfl_sync(0xffffffffu, s, qq);
+    }
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      if ((m >> qq) & 1u) {
+        int a, b;
+        tile_pair<INNER>(r, qq, a, b);
+#pragma unroll
+        for (int i = 0; i < NQW; ++i) rot4(x[a][i], x[b][i], cr[r][qq], sr[r][qq]);
+      }
+    }
+  }
+  if (!any) return false;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const bool valid = c < 4 ? c < na : (c - 4) < nb;
+    if (!valid) continue;
+    float4* col = reinterpret_cast<float4*>(S + (int64_t)(c < 4 ? sa + c : sb + c - 4) * ldS);
+#pragma unroll
+    for (int i = 0; i < NQW; ++i) {
+      const int qq = lane + 32 * i;
+      if (qq < mq) col[qq] = x[c][i];
+    }
+  }
+  // V rows: float4 rows [mq, mq + rq) of the stacked columns
+  for (int qq = lane; qq < rq; qq += 32) {
+    float4 y[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const bool valid = c < 4 ? c < na : (c - 4) < nb;
+      const float4* col =
+          reinterpret_cast<const float4*>(S + (int64_t)(c < 4 ? sa + c : sb + c - 4) * ldS);
+      y[c] = valid ? col[mq + qq] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if ((mk[r] >> q) & 1u) {
+          int a, b;
+          tile_pair<INNER>(r, q, a, b);
+          rot4(y[a], y[b], cr[r][q], sr[r][q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const bool valid = c < 4 ? c < na : (c - 4) < nb;
+      if (!valid) continue;
+      float4* col = reinterpret_cast<float4*>(S + (int64_t)(c < 4 ? sa + c : sb + c - 4) * ldS);
+      col[mq + qq] = y[c];
+    }
+  }
+  return true;
+}
+
+// columns of tile t of a block of ncols columns (0 when t is past the end)
+__device__ __forceinline__ int tile_cols(int t, int ncols) {
+  const int r = ncols - 4 * t;
+  return r <= 0 ? 0 : (r < 4 ? r : 4);
+}
+
 template <typename T>
 __device__ __forceinline__ T load_work(const T* src, int m, int trans, int mm, int r, int c) {
   // stacked column c: rows [0, mm) the working matrix (the slice, m x n with
@@ -324,8 +525,10 @@ __device__ __forceinline__ void copy_cols(T* S, int ldS, T* G, int ldg, int rows
   }
 }
 
-template <typename T, int VEC>
-__global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
+// TILE = 0: pair-per-group rotations; TILE = NQW > 0 (fp32, VEC = 4, mm <= 128
+// NQW): the register-tiled form with 12 warps.
+template <typename T, int VEC, int TILE>
+__global__ void __launch_bounds__(TILE ? 384 : 512) jacobi_kernel(const JacobiParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = blockIdx.x;
   const int tid = threadIdx.x, NTh = blockDim.x;
@@ -380,6 +583,77 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const JacobiParams<T> P) {
   for (int sw = 0; sw < P.max_sweeps && !converged; ++sw) {
     bool rot = false;
     int I = 0, J = 1;
+    if constexpr (TILE > 0) {
+      const int wp = tid >> 5, ln = tid & 31, nwp = NTh >> 5;
+      const int mq = mm >> 2, rq = rc >> 2;
+      for (int ps = 0; ps < npair_sets; ++ps) {
+        if (in_smem) {
+          // round robin over the tiles; the pairs inside each tile in round 0
+          const int nt = (rc + 3) >> 2, ntp = nt + (nt & 1);
+          for (int t = 0; t < ntp - 1; ++t) {
+            for (int k = wp; k < ntp / 2; k += nwp) {
+              const Pair pr = rr_pair(k, t, ntp);
+              const int na = tile_cols(pr.a, rc), nb2 = tile_cols(pr.b, rc);
+              if (t == 0)
+                rot |= tile_group<TILE, true>(S, ldS, 4 * pr.a, na, 4 * pr.b, nb2, na > 0, nb2 > 0,
+                                              mq, rq, ln, tol_t, floor_t);
+              if (na > 0 && nb2 > 0)
+                rot |= tile_group<TILE, false>(S, ldS, 4 * pr.a, na, 4 * pr.b, nb2, false, false,
+                                               mq, rq, ln, tol_t, floor_t);
+            }
+            __syncthreads();
+          }
+        } else {
+          const int bI = min(bc, rc - I * bc), bJ = min(bc, rc - J * bc);
+          copy_cols<T, VEC>(S, ldS, W + (int64_t)(I * bc) * len, len, len, bI, tid, NTh, true);
+          copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len, bJ,
+                            tid, NTh, true);
+          __syncthreads();
+          const int btI = (bI + 3) >> 2, btJ = (bJ + 3) >> 2;
+          // pairs inside a block on the block's first visit of this sweep
+          const bool doI = (I == 0 && J == 1), doJ = (I == 0);
+          const int cI = doI ? btI + (btI & 1) : 0, cJ = doJ ? btJ + (btJ & 1) : 0;
+          const int nri = (doI || doJ) ? max(cI, cJ) - 1 : 0;
+          for (int t = 0; t < nri; ++t) {
+            for (int k = wp; k < cI / 2 + cJ / 2; k += nwp) {
+              int base, nc, cc, kk;
+              if (k < cI / 2) { base = 0; nc = bI; cc = cI; kk = k; }
+              else { base = bc; nc = bJ; cc = cJ; kk = k - cI / 2; }
+              if (t >= cc - 1) continue;
+              const Pair pr = rr_pair(kk, t, cc);
+              const int na = tile_cols(pr.a, nc), nb2 = tile_cols(pr.b, nc);
+              if (t == 0)
+                rot |= tile_group<TILE, true>(S, ldS, base + 4 * pr.a, na, base + 4 * pr.b, nb2,
+                                              na > 0, nb2 > 0, mq, rq, ln, tol_t, floor_t);
+              if (na > 0 && nb2 > 0)
+                rot |= tile_group<TILE, false>(S, ldS, base + 4 * pr.a, na, base + 4 * pr.b, nb2,
+                                               false, false, mq, rq, ln, tol_t, floor_t);
+            }
+            __syncthreads();
+          }
+          // cross pairs I x J: tile k of I with tile (k + t) mod btc of J
+          const int btc = max(btI, btJ);
+          for (int t = 0; t < btc; ++t) {
+            for (int k = wp; k < btI; k += nwp) {
+              const int jt = (k + t) % btc;
+              if (jt >= btJ) continue;
+              rot |= tile_group<TILE, false>(S, ldS, 4 * k, tile_cols(k, bI), bc + 4 * jt,
+                                             tile_cols(jt, bJ), false, false, mq, rq, ln, tol_t,
+                                             floor_t);
+            }
+            __syncthreads();
+          }
+          copy_cols<T, VEC>(S, ldS, W + (int64_t)(I * bc) * len, len, len, bI, tid, NTh, false);
+          copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len, bJ,
+                            tid, NTh, false);
+          __syncthreads();
+          if (++J == nb) {
+            ++I;
+            J = I + 1;
+          }
+        }
+      }
+    } else
     for (int ps = 0; ps < npair_sets; ++ps) {
       Phase ph;
       if (in_smem) {
@@ -534,6 +808,36 @@ JacobiPlan jacobi_plan(int m, int n, int max_smem) {
     pl.bcols = (pl.rc + nb - 1) / nb;
     pl.smem = 2 * (size_t)pl.bcols * col_bytes + sort_bytes;
   }
+  // register-tiled sweeps: fp32 float4 rows, dot-product part <= 256 rows,
+  // enough tiles of 4 columns to keep 12 warps busy
+  pl.tile = (sizeof(T) == 4 && pl.vec == 4 && pl.mm <= 256 && pl.rc >= 32) ? (pl.mm <= 128 ? 1 : 2)
+                                                                           : 0;
+  if (pl.tile) {
+    pl.threads = 384;
+    pl.g = 32;
+    if (full > (size_t)max_smem) {
+      // blocks of a multiple of 4 columns, at most 4 per warp (one tile pair
+      // per warp and cross round)
+      int bmax = (int)(((size_t)max_smem - sort_bytes) / (2 * col_bytes)) & ~3;
+      if (bmax > 4 * (pl.threads / 32)) bmax = 4 * (pl.threads / 32);
+      if (bmax >= 4) {
+        int nb = (pl.rc + bmax - 1) / bmax;
+        if (nb < 3) nb = 3;
+        pl.bcols = (((pl.rc + nb - 1) / nb) + 3) & ~3;
+        pl.smem = 2 * (size_t)pl.bcols * col_bytes + sort_bytes;
+        pl.block_mode = pl.rc <= 2 * pl.bcols ? 0 : 1;
+        if (pl.block_mode) return pl;
+      }
+      pl.tile = 0;   // fall back to the pair-per-group plan below
+      const int bm2 = (int)(((size_t)max_smem - sort_bytes) / (2 * col_bytes));
+      const int nb2 = (pl.rc + bm2 - 1) / bm2 < 3 ? 3 : (pl.rc + bm2 - 1) / bm2;
+      pl.bcols = (pl.rc + nb2 - 1) / nb2;
+      pl.smem = 2 * (size_t)pl.bcols * col_bytes + sort_bytes;
+    } else {
+      pl.block_mode = 0;
+      return pl;
+    }
+  }
   const bool in_smem = pl.rc <= 2 * pl.bcols;
   const int maxpairs = in_smem ? (pl.rc + 1) / 2 : pl.bcols;
   // threads: one group of g lanes per pair of a round, about 16 rows per lane
@@ -553,9 +857,13 @@ template <typename T>
 cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_t smem,
                        cudaStream_t st) {
   if (nslices <= 0) return cudaSuccess;
-  void (*kern)(const JacobiParams<T>) = jacobi_kernel<T, 1>;
+  void (*kern)(const JacobiParams<T>) = jacobi_kernel<T, 1, 0>;
   if constexpr (sizeof(T) == 4) {
-    if (P.ldS % 4 == 0 && P.mm % 4 == 0 && P.rc % 4 == 0) kern = jacobi_kernel<T, 4>;
+    if (P.ldS % 4 == 0 && P.mm % 4 == 0 && P.rc % 4 == 0) {
+      kern = jacobi_kernel<T, 4, 0>;
+      if (P.tile == 1 && P.mm <= 128) kern = jacobi_kernel<T, 4, 1>;
+      if (P.tile == 2 && P.mm <= 256) kern = jacobi_kernel<T, 4, 2>;
+    }
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

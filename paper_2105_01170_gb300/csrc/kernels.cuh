@@ -46,9 +46,11 @@ struct JacobiParams {
   double* sigma = nullptr;                      // out: rc per slice, descending
   int* sweeps = nullptr;                        // out: per slice
   int* status = nullptr;                        // status bits (atomicOr)
+  int tile = 0;                                 // register-tiled sweeps (JacobiPlan::tile)
 };
 struct JacobiPlan {
   int trans, mm, rc, ldS, bcols, sort_n, threads, g, block_mode, vec;
+  int tile;   // 0: one pair per group of g lanes; 1, 2: register tiles (mm <= 128 tile)
   size_t smem;
 };
 template <typename T> JacobiPlan jacobi_plan(int m, int n, int max_smem);

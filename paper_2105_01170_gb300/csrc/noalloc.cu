@@ -88,7 +88,7 @@ sma_status sma_slice_svd_noalloc(const float* X, int32_t m, int32_t n, int32_t p
     sma::JacobiParams<float> J;
     J.src = X + c0 * mn; J.src_bs = mn; J.m = m; J.n = n;
     J.mm = pl.mm; J.rc = pl.rc; J.trans = pl.trans; J.ldS = pl.ldS; J.bcols = pl.bcols;
-    J.g = pl.g; J.sort_n = pl.sort_n;
+    J.g = pl.g; J.sort_n = pl.sort_n; J.tile = pl.tile;
     J.max_sweeps = max_sweeps > 0 ? max_sweeps : 30;
     J.tol = 4.0 * std::sqrt((double)pl.mm) * sma::Eps<float>::v;
     J.W = pl.block_mode ? d_work : nullptr; J.W_bs = per_slice;
