@@ -79,9 +79,12 @@ template <> struct Angle<float> {
       s = (float)sd;
       return true;
     }
-    const float zeta = (be - al) / (2.0f * ga);
+    // t only has to be close to the optimal tangent (any exact rotation is
+    // valid), so the divisions are the fast approximate ones
+    const float zeta = __fdividef(be - al, 2.0f * ga);
     const float az = fabsf(zeta);
-    const float t = (az > 1e18f) ? 0.5f / zeta : copysignf(1.0f, zeta) / (az + sqrtf(fmaf(zeta, zeta, 1.0f)));
+    const float t = (az > 1e18f) ? __fdividef(0.5f, zeta)
+                                 : copysignf(__fdividef(1.0f, az + sqrtf(fmaf(zeta, zeta, 1.0f))), zeta);
     // c = 1/sqrt(1 + t^2) to about half an ulp: q = 1 + t^2 as an unevaluated
     // sum (q_hi + q_lo), one Newton step on rsqrt with the residual formed by
     // fused multiply-adds; s = t c.  (The angle t itself may carry fp32
@@ -333,12 +336,13 @@ __device__ __forceinline__ void rot4(float4& x, float4& y, float c, float s) {
 // One group of rotations on tiles A (slots sa.., na columns) and B (slots
 // sb.., nb columns) by one warp; columns past na / nb are absent (zero, never
 // rotated).  INNER pairs of A (B) only when doA (doB).  mq = mm / 4 float4
-// rows of dot-product part, rq = rc / 4 float4 rows of V part.  Returns true
-// if any pair was rotated.
+// rows of dot-product part, rq = rc / 4 float4 rows of V part.  csw: the
+// warp's shared-memory record of the rotations (2 float4 per sub-round).
+// Returns true if any pair was rotated.
 template <int NQW, bool INNER>
 __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, int sb, int nb,
                                            bool doA, bool doB, int mq, int rq, int lane,
-                                           float tol, float floor_) {
+                                           float tol, float floor_, float4* csw) {
   constexpr int NR = INNER ? 3 : 4;
   float4 x[8][NQW];
 #pragma unroll
@@ -352,7 +356,6 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
       x[c][i] = (valid && qq < mq) ? col[qq] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
-  float cr[NR][4], sr[NR][4];
   unsigned mk[NR];
   unsigned any = 0;
 #pragma unroll
@@ -389,22 +392,26 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
     const unsigned m = __ballot_sync(0xffffffffu, ok) & 0xfu;
     mk[r] = m;
     any |= m;
-#pragma unroll
-    for (int qq = 0; qq < 4; ++qq) {
-      cr[r][qq] = __shfl_sync(0xffffffffu, c, qq);
-      sr[r][qq] = __shfl_sync(0xffffffffu, s, qq);
+    // record (c_q, s_q) of the sub-round: lanes 0 and 2 write one float4 each
+    {
+      const float c1 = __shfl_down_sync(0xffffffffu, c, 1);
+      const float s1 = __shfl_down_sync(0xffffffffu, s, 1);
+      if (lane == 0 || lane == 2) csw[2 * r + (lane >> 1)] = make_float4(c, s, c1, s1);
     }
 #pragma unroll
     for (int qq = 0; qq < 4; ++qq) {
       if ((m >> qq) & 1u) {
         int a, b;
         tile_pair<INNER>(r, qq, a, b);
+        const float cq = __shfl_sync(0xffffffffu, c, qq);
+        const float sq = __shfl_sync(0xffffffffu, s, qq);
 #pragma unroll
-        for (int i = 0; i < NQW; ++i) rot4(x[a][i], x[b][i], cr[r][qq], sr[r][qq]);
+        for (int i = 0; i < NQW; ++i) rot4(x[a][i], x[b][i], cq, sq);
       }
     }
   }
   if (!any) return false;
+  __syncwarp();
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const bool valid = c < 4 ? c < na : (c - 4) < nb;
@@ -428,12 +435,16 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
     }
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
+      if (mk[r] == 0u) continue;
+      const float4 cs01 = csw[2 * r], cs23 = csw[2 * r + 1];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         if ((mk[r] >> q) & 1u) {
           int a, b;
           tile_pair<INNER>(r, q, a, b);
-          rot4(y[a], y[b], cr[r][q], sr[r][q]);
+          const float cq = q == 0 ? cs01.x : q == 1 ? cs01.z : q == 2 ? cs23.x : cs23.z;
+          const float sq = q == 0 ? cs01.y : q == 1 ? cs01.w : q == 2 ? cs23.y : cs23.w;
+          rot4(y[a], y[b], cq, sq);
         }
       }
     }
@@ -445,6 +456,7 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
       col[mq + qq] = y[c];
     }
   }
+  __syncwarp();   // the record is rewritten by the warp's next group
   return true;
 }
 
@@ -503,7 +515,9 @@ __device__ __forceinline__ bool phase_pair(const Phase& ph, int t, int k, int& a
 }
 
 // Copy ncols columns of `rows` elements between shared memory (stride ldS)
-// and the global workspace (stride ldg); float4 when VEC == 4.
+// and the global workspace (stride ldg); float4 when VEC == 4.  Element e
+// always goes to the same thread, so a copy out of a slot region followed by
+// a copy into it needs no barrier in between.
 template <typename T, int VEC>
 __device__ __forceinline__ void copy_cols(T* S, int ldS, T* G, int ldg, int rows, int ncols,
                                           int tid, int nth, bool to_smem) {
@@ -525,10 +539,108 @@ __device__ __forceinline__ void copy_cols(T* S, int ldS, T* G, int ldg, int rows
   }
 }
 
+// Rounds of the tiled sweep.  kind 0 (all rc columns in shared memory): a
+// round robin over the ntp tile players, ntp - 1 rounds of ntp / 2 tasks, the
+// pairs inside each tile in round 0.  kind 1 (blocks I, J staged in slots
+// [0, bc) and [bc, 2 bc)): on a block's first visit of the sweep nri rounds of
+// round robin inside the block(s) (cI / 2 + cJ / 2 tasks), then btc rounds of
+// the cross pairs, tile k of I with tile (k + t) mod btc of J (btI tasks).
+struct TPhase {
+  int kind, ntp, bI, bJ, bc, btI, btJ, cI, cJ, nri, btc;
+};
+struct TTask {
+  int sa, na, sb, nb;
+  bool inner;
+};
+__device__ __forceinline__ TPhase tphase_smem(int rc) {
+  TPhase p{};
+  const int nt = (rc + 3) >> 2;
+  p.kind = 0;
+  p.ntp = nt + (nt & 1);
+  p.bI = rc;
+  return p;
+}
+__device__ __forceinline__ TPhase tphase_blocks(int bI, int bJ, int bc, bool doI, bool doJ) {
+  TPhase p{};
+  p.kind = 1;
+  p.bI = bI;
+  p.bJ = bJ;
+  p.bc = bc;
+  p.btI = (bI + 3) >> 2;
+  p.btJ = (bJ + 3) >> 2;
+  p.cI = doI ? p.btI + (p.btI & 1) : 0;
+  p.cJ = doJ ? p.btJ + (p.btJ & 1) : 0;
+  p.nri = (doI || doJ) ? max(p.cI, p.cJ) - 1 : 0;
+  p.btc = max(p.btI, p.btJ);
+  return p;
+}
+__device__ __forceinline__ int tphase_rounds(const TPhase& p) {
+  return p.kind == 0 ? p.ntp - 1 : p.nri + p.btc;
+}
+__device__ __forceinline__ int tphase_tasks(const TPhase& p, int t) {
+  if (p.kind == 0) return p.ntp / 2;
+  return t < p.nri ? p.cI / 2 + p.cJ / 2 : p.btI;
+}
+__device__ __forceinline__ bool tphase_task(const TPhase& p, int t, int k, TTask& d) {
+  if (p.kind == 0) {
+    const Pair pr = rr_pair(k, t, p.ntp);
+    d.sa = 4 * pr.a;
+    d.sb = 4 * pr.b;
+    d.na = tile_cols(pr.a, p.bI);
+    d.nb = tile_cols(pr.b, p.bI);
+    d.inner = (t == 0);
+    return true;
+  }
+  if (t < p.nri) {
+    int base, nc, cc, kk;
+    if (k < p.cI / 2) {
+      base = 0; nc = p.bI; cc = p.cI; kk = k;
+    } else {
+      base = p.bc; nc = p.bJ; cc = p.cJ; kk = k - p.cI / 2;
+    }
+    if (t >= cc - 1) return false;
+    const Pair pr = rr_pair(kk, t, cc);
+    d.sa = base + 4 * pr.a;
+    d.sb = base + 4 * pr.b;
+    d.na = tile_cols(pr.a, nc);
+    d.nb = tile_cols(pr.b, nc);
+    d.inner = (t == 0);
+    return true;
+  }
+  const int jt = (k + t - p.nri) % p.btc;
+  if (jt >= p.btJ) return false;
+  d.sa = 4 * k;
+  d.na = tile_cols(k, p.bI);
+  d.sb = p.bc + 4 * jt;
+  d.nb = tile_cols(jt, p.bJ);
+  d.inner = false;
+  return true;
+}
+
+// Block staging of a phase (I, J): block I stays in slots [0, bc) while
+// consecutive phases share it (resI), block J goes to slots [bc, 2 bc).
+template <typename T, int VEC>
+__device__ __forceinline__ void stage_in(T* S, int ldS, T* W, int len, int bc, int rc, int I,
+                                         int J, int& resI, int tid, int nth) {
+  if (I != resI) {
+    if (resI >= 0)
+      copy_cols<T, VEC>(S, ldS, W + (int64_t)(resI * bc) * len, len, len, min(bc, rc - resI * bc),
+                        tid, nth, false);
+    copy_cols<T, VEC>(S, ldS, W + (int64_t)(I * bc) * len, len, len, min(bc, rc - I * bc), tid,
+                      nth, true);
+    resI = I;
+  }
+  copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len,
+                    min(bc, rc - J * bc), tid, nth, true);
+  __syncthreads();
+}
+
 // TILE = 0: pair-per-group rotations; TILE = NQW > 0 (fp32, VEC = 4, mm <= 128
-// NQW): the register-tiled form with 12 warps.
+// NQW): the register-tiled form with at most 11 warps.
+constexpr int kMaxTileWarps = 12;
+
 template <typename T, int VEC, int TILE>
-__global__ void __launch_bounds__(TILE ? 384 : 512) jacobi_kernel(const JacobiParams<T> P) {
+__global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel(const JacobiParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = blockIdx.x;
   const int tid = threadIdx.x, NTh = blockDim.x;
@@ -583,70 +695,39 @@ __global__ void __launch_bounds__(TILE ? 384 : 512) jacobi_kernel(const JacobiPa
   for (int sw = 0; sw < P.max_sweeps && !converged; ++sw) {
     bool rot = false;
     int I = 0, J = 1;
+    int resI = -1;   // block held in slots [0, bc) (block mode)
     if constexpr (TILE > 0) {
       const int wp = tid >> 5, ln = tid & 31, nwp = NTh >> 5;
       const int mq = mm >> 2, rq = rc >> 2;
+      __shared__ float4 cs_rec[kMaxTileWarps][8];   // rotation record of each warp
+      float4* csw = cs_rec[wp];
       for (int ps = 0; ps < npair_sets; ++ps) {
+        TPhase ph;
         if (in_smem) {
-          // round robin over the tiles; the pairs inside each tile in round 0
-          const int nt = (rc + 3) >> 2, ntp = nt + (nt & 1);
-          for (int t = 0; t < ntp - 1; ++t) {
-            for (int k = wp; k < ntp / 2; k += nwp) {
-              const Pair pr = rr_pair(k, t, ntp);
-              const int na = tile_cols(pr.a, rc), nb2 = tile_cols(pr.b, rc);
-              if (t == 0)
-                rot |= tile_group<TILE, true>(S, ldS, 4 * pr.a, na, 4 * pr.b, nb2, na > 0, nb2 > 0,
-                                              mq, rq, ln, tol_t, floor_t);
-              if (na > 0 && nb2 > 0)
-                rot |= tile_group<TILE, false>(S, ldS, 4 * pr.a, na, 4 * pr.b, nb2, false, false,
-                                               mq, rq, ln, tol_t, floor_t);
-            }
-            __syncthreads();
-          }
+          ph = tphase_smem(rc);
         } else {
-          const int bI = min(bc, rc - I * bc), bJ = min(bc, rc - J * bc);
-          copy_cols<T, VEC>(S, ldS, W + (int64_t)(I * bc) * len, len, len, bI, tid, NTh, true);
-          copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len, bJ,
-                            tid, NTh, true);
-          __syncthreads();
-          const int btI = (bI + 3) >> 2, btJ = (bJ + 3) >> 2;
-          // pairs inside a block on the block's first visit of this sweep
-          const bool doI = (I == 0 && J == 1), doJ = (I == 0);
-          const int cI = doI ? btI + (btI & 1) : 0, cJ = doJ ? btJ + (btJ & 1) : 0;
-          const int nri = (doI || doJ) ? max(cI, cJ) - 1 : 0;
-          for (int t = 0; t < nri; ++t) {
-            for (int k = wp; k < cI / 2 + cJ / 2; k += nwp) {
-              int base, nc, cc, kk;
-              if (k < cI / 2) { base = 0; nc = bI; cc = cI; kk = k; }
-              else { base = bc; nc = bJ; cc = cJ; kk = k - cI / 2; }
-              if (t >= cc - 1) continue;
-              const Pair pr = rr_pair(kk, t, cc);
-              const int na = tile_cols(pr.a, nc), nb2 = tile_cols(pr.b, nc);
-              if (t == 0)
-                rot |= tile_group<TILE, true>(S, ldS, base + 4 * pr.a, na, base + 4 * pr.b, nb2,
-                                              na > 0, nb2 > 0, mq, rq, ln, tol_t, floor_t);
-              if (na > 0 && nb2 > 0)
-                rot |= tile_group<TILE, false>(S, ldS, base + 4 * pr.a, na, base + 4 * pr.b, nb2,
-                                               false, false, mq, rq, ln, tol_t, floor_t);
-            }
-            __syncthreads();
+          stage_in<T, VEC>(S, ldS, W, len, bc, rc, I, J, resI, tid, NTh);
+          ph = tphase_blocks(min(bc, rc - I * bc), min(bc, rc - J * bc), bc, I == 0 && J == 1,
+                             I == 0);
+        }
+        const int nrounds = tphase_rounds(ph);
+        for (int t = 0; t < nrounds; ++t) {
+          const int ntasks = tphase_tasks(ph, t);
+          for (int k = wp; k < ntasks; k += nwp) {
+            TTask d;
+            if (!tphase_task(ph, t, k, d)) continue;
+            if (d.inner)
+              rot |= tile_group<TILE, true>(S, ldS, d.sa, d.na, d.sb, d.nb, d.na > 0, d.nb > 0, mq,
+                                            rq, ln, tol_t, floor_t, csw);
+            if (d.na > 0 && d.nb > 0)
+              rot |= tile_group<TILE, false>(S, ldS, d.sa, d.na, d.sb, d.nb, false, false, mq, rq,
+                                             ln, tol_t, floor_t, csw);
           }
-          // cross pairs I x J: tile k of I with tile (k + t) mod btc of J
-          const int btc = max(btI, btJ);
-          for (int t = 0; t < btc; ++t) {
-            for (int k = wp; k < btI; k += nwp) {
-              const int jt = (k + t) % btc;
-              if (jt >= btJ) continue;
-              rot |= tile_group<TILE, false>(S, ldS, 4 * k, tile_cols(k, bI), bc + 4 * jt,
-                                             tile_cols(jt, bJ), false, false, mq, rq, ln, tol_t,
-                                             floor_t);
-            }
-            __syncthreads();
-          }
-          copy_cols<T, VEC>(S, ldS, W + (int64_t)(I * bc) * len, len, len, bI, tid, NTh, false);
-          copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len, bJ,
-                            tid, NTh, false);
           __syncthreads();
+        }
+        if (!in_smem) {
+          copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len,
+                            ph.bJ, tid, NTh, false);
           if (++J == nb) {
             ++I;
             J = I + 1;
@@ -665,10 +746,7 @@ __global__ void __launch_bounds__(TILE ? 384 : 512) jacobi_kernel(const JacobiPa
         ph.npairs = ph.cI / 2;
       } else {
         const int bI = min(bc, rc - I * bc), bJ = min(bc, rc - J * bc);
-        copy_cols<T, VEC>(S, ldS, W + (int64_t)(I * bc) * len, len, len, bI, tid, NTh, true);
-        copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len, bJ,
-                          tid, NTh, true);
-        __syncthreads();
+        stage_in<T, VEC>(S, ldS, W, len, bc, rc, I, J, resI, tid, NTh);
         // pairs inside a block on the block's first visit of this sweep
         const bool doI = (I == 0 && J == 1), doJ = (I == 0);
         ph.kind = 1;
@@ -690,16 +768,17 @@ __global__ void __launch_bounds__(TILE ? 384 : 512) jacobi_kernel(const JacobiPa
         __syncthreads();
       }
       if (!in_smem) {
-        copy_cols<T, VEC>(S, ldS, W + (int64_t)(I * bc) * len, len, len, ph.bI, tid, NTh, false);
         copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len,
                           ph.bJ, tid, NTh, false);
-        __syncthreads();
         if (++J == nb) {
           ++I;
           J = I + 1;
         }
       }
     }
+    if (resI >= 0)
+      copy_cols<T, VEC>(S, ldS, W + (int64_t)(resI * bc) * len, len, len, min(bc, rc - resI * bc),
+                        tid, NTh, false);
     sweeps_used = sw + 1;
     if (!__syncthreads_or(rot)) converged = true;
   }
@@ -787,7 +866,7 @@ template <typename T>
 JacobiPlan jacobi_plan(int m, int n, int max_smem) {
   JacobiPlan pl;
   // leave room for the kernel's static shared memory
-  max_smem = max_smem > 1024 ? max_smem - 1024 : 0;
+  max_smem = max_smem > 2048 ? max_smem - 2048 : 0;
   pl.trans = (m < n) ? 1 : 0;
   pl.mm = pl.trans ? n : m;
   pl.rc = pl.trans ? m : n;
@@ -813,19 +892,21 @@ JacobiPlan jacobi_plan(int m, int n, int max_smem) {
   pl.tile = (sizeof(T) == 4 && pl.vec == 4 && pl.mm <= 256 && pl.rc >= 32) ? (pl.mm <= 128 ? 1 : 2)
                                                                            : 0;
   if (pl.tile) {
-    pl.threads = 384;
+    // one warp per tile-pair task of a round, at most kTileWarps
+    constexpr int kTileWarps = kMaxTileWarps;
     pl.g = 32;
     if (full > (size_t)max_smem) {
       // blocks of a multiple of 4 columns, at most 4 per warp (one tile pair
       // per warp and cross round)
       int bmax = (int)(((size_t)max_smem - sort_bytes) / (2 * col_bytes)) & ~3;
-      if (bmax > 4 * (pl.threads / 32)) bmax = 4 * (pl.threads / 32);
+      if (bmax > 4 * kTileWarps) bmax = 4 * kTileWarps;
       if (bmax >= 4) {
         int nb = (pl.rc + bmax - 1) / bmax;
         if (nb < 3) nb = 3;
         pl.bcols = (((pl.rc + nb - 1) / nb) + 3) & ~3;
         pl.smem = 2 * (size_t)pl.bcols * col_bytes + sort_bytes;
         pl.block_mode = pl.rc <= 2 * pl.bcols ? 0 : 1;
+        pl.threads = 32 * kTileWarps;   // the spare warps shorten the first-visit rounds
         if (pl.block_mode) return pl;
       }
       pl.tile = 0;   // fall back to the pair-per-group plan below
@@ -834,6 +915,8 @@ JacobiPlan jacobi_plan(int m, int n, int max_smem) {
       pl.bcols = (pl.rc + nb2 - 1) / nb2;
       pl.smem = 2 * (size_t)pl.bcols * col_bytes + sort_bytes;
     } else {
+      const int nt = (pl.rc + 3) / 4, tasks = (nt + (nt & 1)) / 2;
+      pl.threads = 32 * (tasks < 4 ? 4 : (tasks > kTileWarps ? kTileWarps : tasks));
       pl.block_mode = 0;
       return pl;
     }
