@@ -209,6 +209,14 @@ struct Prob {
   int64_t Mkp = 0;
   int64_t Dp_K = -1;
   bool dp_valid = false;
+  // tcgen05 operands of the mid-index contraction: the right-hand sides as
+  // [(c + n s)][Kq] planes and the terms C_j as [(a + ell j)][Kq] planes
+  __nv_bfloat16* Xq = nullptr;
+  size_t Xq_elems = 0;
+  int64_t Xq_shape = -1;
+  __nv_bfloat16* Cq = nullptr;
+  size_t Cq_elems = 0;
+  bool cq_valid = false;
   bool compressed = false;
   // host copies of results
   int h_iscal[8] = {0};
@@ -1062,6 +1070,7 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
   else SMA_TRY(compress_tucker(h, P));
   P.compressed = true;
   P.dp_valid = false;
+  P.cq_valid = false;
   P.h_iscal[0] = -1;
   return SMA_OK;
 }
@@ -1136,6 +1145,7 @@ void mark_compressed(sma_ctx* h) {
   for (auto& P : probs<T>(h)) {
     P.compressed = true;
     P.dp_valid = false;
+    P.cq_valid = false;
     P.ml_valid = false;
     P.h_iscal[0] = -1;
   }
@@ -1221,11 +1231,10 @@ sma_status grow(sma_ctx* h, T** buf, size_t* have, size_t need) {
 }
 
 // Mixed-path Kronecker-sum matvec on tensor cores: Y^T = Z^T D^T with
-// Z = [X_s C_j^T] (mid-index contraction on CUDA cores, written directly as
-// bf16 split planes) and D = [D_1 | ... | D_nt]; the long-K product runs in
-// the tcgen05 kernel.  Returns false when the shapes do not fit it (the
-// caller then runs the CUDA-core form); a CUDA error is reported through
-// tc_err so the caller can return it.
+// Z = [X_s C_j^T] and D = [D_1 | ... | D_nt].  Both products run in tcgen05
+// kernels: the mid-index contraction (K = q) writes Z directly as the bf16
+// split planes of the long-K product's operand.  Returns false when the
+// shapes do not fit them (the caller then runs the CUDA-core form).
 template <typename T>
 bool tc_apply(sma_ctx*, Prob<T>&, const T*, int64_t, T*, int64_t, int64_t, int, int) {
   return false;
@@ -1240,7 +1249,9 @@ bool tc_apply<float>(sma_ctx* h, Prob<float>& P, const float* X, int64_t ldx, fl
   const int64_t rowsZ = (int64_t)ell * nrhs;
   if (rowsZ > 0x7fffffff) return false;
   const size_t zneed = (size_t)3 * rowsZ * Kp, dneed = (size_t)3 * m * Kp;
+  const __nv_bfloat16* zold = P.Zp;
   if (grow(h, &P.Zp, &P.Zp_elems, zneed) != SMA_OK) return false;
+  if (P.Zp != zold) P.Zp_K = -1;   // a new buffer: its K padding is not zero yet
   if (grow(h, &P.Dp, &P.Dp_elems, dneed) != SMA_OK) return false;
   if (P.Zp_K != K) {  // zero the K padding once per shape
     if (cudaMemsetAsync(P.Zp, 0, P.Zp_elems * sizeof(__nv_bfloat16), st) != cudaSuccess) return false;
@@ -1255,16 +1266,36 @@ bool tc_apply<float>(sma_ctx* h, Prob<float>& P, const float* X, int64_t ldx, fl
     P.Dp_K = K;
     P.dp_valid = true;
   }
-  // Z^T planes: element (c, a) of batch (j, s) at (a + ell s) Kp + c + n j
-  GemmParams<float> g;
-  g.M = n; g.N = ell; g.K = q;
-  g.A = X; g.a_rs = 1; g.a_cs = n; g.a_b2 = ldx;
-  g.B = P.C; g.b_rs = ell; g.b_cs = 1; g.b_b1 = (int64_t)ell * q;
-  g.C = nullptr; g.c_rs = 1; g.c_cs = Kp; g.c_b1 = n; g.c_b2 = (int64_t)ell * Kp;
-  g.Cs = P.Zp; g.cs_plane = rowsZ * Kp;
-  g.nb1 = nt; g.nb2 = nrhs;
+  // Z^T planes: element (c, a) of batch (j, s) at (a + ell s) Kp + c + n j,
+  // from X_s[c, b] (c + n b + ldx s) and C_j[a, b] (a + ell b + ell q j)
+  const int64_t Kq = tc_pad_k(q);
+  const int64_t rowsX = (int64_t)n * nrhs, rowsC = (int64_t)ell * nt;
+  if (rowsX > 0x7fffffff || rowsC > 0x7fffffff || nrhs > 65535 || nt > 65535) return false;
+  const int64_t xshape = rowsX * Kq;
+  if (P.Xq_shape != xshape) {  // zero the K padding (b >= q) once per shape
+    if (grow(h, &P.Xq, &P.Xq_elems, (size_t)3 * rowsX * Kq) != SMA_OK) return false;
+    if (cudaMemsetAsync(P.Xq, 0, (size_t)3 * rowsX * Kq * sizeof(__nv_bfloat16), st) != cudaSuccess)
+      return false;
+    P.Xq_shape = xshape;
+  }
+  if (!P.cq_valid) {
+    if (grow(h, &P.Cq, &P.Cq_elems, (size_t)3 * rowsC * Kq) != SMA_OK) return false;
+    if (cudaMemsetAsync(P.Cq, 0, (size_t)3 * rowsC * Kq * sizeof(__nv_bfloat16), st) != cudaSuccess)
+      return false;
+    ++h->launches;
+    if (tc_split_transpose_batched(P.C, 1, ell, ell, q, Kq, nt, (int64_t)ell * q, (int64_t)ell * Kq,
+                                   rowsC * Kq, P.Cq, st) != cudaSuccess)
+      return false;
+    P.cq_valid = true;
+  }
   ++h->launches;
-  if (gemm<float>(g, st) != cudaSuccess) return false;
+  if (tc_split_transpose_batched(X, 1, n, n, q, Kq, nrhs, ldx, (int64_t)n * Kq, rowsX * Kq, P.Xq,
+                                 st) != cudaSuccess)
+    return false;
+  ++h->launches;
+  if (tc_mid_planes(P.Xq, (int)rowsX, P.Cq, (int)rowsC, Kq, P.Zp, Kp, rowsZ * Kp, n, ell, P.status,
+                    st) != cudaSuccess)
+    return false;
   ++h->launches;
   if (tc_gemm_planes(P.Zp, P.Dp, (int)rowsZ, m, Kp, Yd, m, P.status, st) != cudaSuccess) return false;
   return true;

@@ -312,14 +312,165 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   if (threadIdx.x == 0 && *abort_flag) atomicOr(args.err, SMA_STATUS_BIT(SMA_ERR_TIMEOUT));
 }
 
+// ---- mid-index contraction of the Kronecker-sum matvec ----------------------
+// Z(i, j) = sum_k A(i, k) B(j, k) over the six split products for a short K
+// (Kq = a few k-blocks), written as three bf16 planes straight into the
+// operand layout of the long-K product: row i = c + n s, column j = a + ell t
+// go to Z[p * plane + (a + ell s) * Kp + c + n t].  One CTA per 128 x 256
+// tile, two stages (two CTAs per SM, so one CTA's epilogue overlaps the other
+// CTA's loads and MMAs), four epilogue warps, 256 TMEM columns.
+constexpr int MID_STAGES = 2;
+constexpr int MID_EPI_WARPS = 4;
+constexpr int MID_THREADS = 64 + 32 * MID_EPI_WARPS;
+constexpr int MID_TMEM = 256;
+constexpr int MID_SMEM = MID_STAGES * STAGE_BYTES + 1024 + 256;
+
+struct MidArgs {
+  int M, N, Kq, n, ell;
+  int64_t Kp, plane;
+  __nv_bfloat16* Z;
+  int* err;
+};
+
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& hi, __nv_bfloat16& mid,
+                                       __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(hi);
+  mid = __float2bfloat16_rn(r1);
+  lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+
+__global__ void __launch_bounds__(MID_THREADS)
+tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              const MidArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* tiles = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(tiles + MID_STAGES * STAGE_BYTES);
+  uint64_t* empty = full + MID_STAGES;
+  uint64_t* accf = empty + MID_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int total = (args.Kq / BK) * 6;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MID_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     saddr(tmem_slot)),
+                 "r"(MID_TMEM));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int it = 0; it < total; ++it) {
+      const int s = it % MID_STAGES;
+      const uint32_t ph = (uint32_t)(it / MID_STAGES) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const int kb = it / 6, pr = it % 6;
+      uint8_t* st = tiles + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_3d(st, &mapA, &full[s], kb * BK, m0, kProdA[pr]);
+      tma_load_3d(st + A_BYTES, &mapB, &full[s], kb * BK, n0, kProdB[pr]);
+      issued = it + 1;
+    }
+    for (int it = (issued > MID_STAGES ? issued - MID_STAGES : 0); it < issued; ++it)
+      if (!mbar_wait(&full[it % MID_STAGES], (uint32_t)(it / MID_STAGES) & 1u)) *abort_flag = 1;
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t id = idesc_bf16(BM, BN);
+    for (int it = 0; it < total; ++it) {
+      const int s = it % MID_STAGES;
+      const uint32_t ph = (uint32_t)(it / MID_STAGES) & 1u;
+      if (*abort_flag || !mbar_wait(&full[s], ph)) {
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      const uint32_t a0 = saddr(tiles + s * STAGE_BYTES);
+      const uint32_t b0 = a0 + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        mma(tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), id, (it > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    mma_commit(accf);  // arrives when every MMA issued above has completed
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    const int grow = m0 + q * 32 + lane;
+    const bool ok = mbar_wait(accf, 0u);
+    fence_after();
+    if (!ok) *abort_flag = 1;
+    __syncwarp();
+    if (!*abort_flag) {
+      const int c = grow % args.n, s = grow / args.n;
+      const int64_t rbase = (int64_t)args.ell * s * args.Kp + c;
+#pragma unroll 1
+      for (int part = 0; part < BN / 32; ++part) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(part * 32), r);
+        const int g0 = n0 + part * 32;
+        int t = g0 / args.ell, a = g0 - t * args.ell;
+        if (grow < args.M) {
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            if (g0 + jj < args.N) {
+              __nv_bfloat16 hi, mi, lo;
+              split3(__uint_as_float(r[jj]), hi, mi, lo);
+              __nv_bfloat16* d = args.Z + rbase + (int64_t)a * args.Kp + (int64_t)args.n * t;
+              d[0] = hi;
+              d[args.plane] = mi;
+              d[2 * args.plane] = lo;
+            }
+            if (++a == args.ell) {
+              a = 0;
+              ++t;
+            }
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(MID_TMEM));
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(args.err, SMA_STATUS_BIT(SMA_ERR_TIMEOUT));
+}
+
 // fp32 -> three bf16 planes, with transposition: plane[p][j * Kp + k] from
 // src[j * s_rs + k * s_cs] for j < R, k < K (32 x 32 tiles through shared
 // memory so both sides are coalesced when s_rs == 1).
 __global__ void split_transpose_kernel(const float* __restrict__ src, int64_t s_rs, int64_t s_cs,
                                        int R, int K, int64_t Kp, __nv_bfloat16* __restrict__ dst,
-                                       int64_t plane) {
+                                       int64_t plane, int64_t src_bs, int64_t dst_bs) {
   __shared__ float tile[32][33];
   const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  src += (int64_t)blockIdx.z * src_bs;
+  dst += (int64_t)blockIdx.z * dst_bs;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int k = k0 + i, j = j0 + threadIdx.x;
     tile[i][threadIdx.x] = (j < R && k < K) ? src[(int64_t)j * s_rs + (int64_t)k * s_cs] : 0.f;
@@ -382,7 +533,18 @@ cudaError_t tc_split_transpose(const float* src, int64_t s_rs, int64_t s_cs, int
   if (R <= 0 || K <= 0) return cudaSuccess;
   dim3 grid((R + 31) / 32, (K + 31) / 32);
   split_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(src, s_rs, s_cs, R, K, Kp, dst,
-                                                      (int64_t)R * Kp);
+                                                      (int64_t)R * Kp, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_split_transpose_batched(const float* src, int64_t s_rs, int64_t s_cs, int R, int K,
+                                       int64_t Kp, int nbatch, int64_t src_bs, int64_t dst_bs,
+                                       int64_t plane, __nv_bfloat16* dst, cudaStream_t st) {
+  if (R <= 0 || K <= 0 || nbatch <= 0) return cudaSuccess;
+  if (nbatch > 65535) return cudaErrorInvalidValue;
+  dim3 grid((R + 31) / 32, (K + 31) / 32, nbatch);
+  split_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(src, s_rs, s_cs, R, K, Kp, dst, plane,
+                                                      src_bs, dst_bs);
   return cudaGetLastError();
 }
 
@@ -398,6 +560,23 @@ cudaError_t tc_gemm_planes(const __nv_bfloat16* A, const __nv_bfloat16* B, int M
   if (attr != cudaSuccess) return attr;
   TcArgs a{M, N, (int)Kp, C, ldc, col_major ? 1 : 0, err};
   tc_gemm_kernel<<<(M + BM - 1) / BM, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_mid_planes(const __nv_bfloat16* A, int M, const __nv_bfloat16* B, int N, int64_t Kq,
+                          __nv_bfloat16* Z, int64_t Kp, int64_t zplane, int n, int ell, int* err,
+                          cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (Kq % BK != 0 || Kq <= 0 || n <= 0 || ell <= 0) return cudaErrorInvalidValue;
+  if ((M + BM - 1) / BM > 0x7fffffff || (N + BN - 1) / BN > 65535) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, Kq, BM) || !make_map(&mb, B, N, Kq, BN)) return cudaErrorInvalidValue;
+  const cudaError_t attr = cudaFuncSetAttribute(
+      tc_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MID_SMEM);
+  if (attr != cudaSuccess) return attr;
+  MidArgs a{M, N, (int)Kq, n, ell, Kp, zplane, Z, err};
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  tc_mid_kernel<<<grid, MID_THREADS, MID_SMEM, st>>>(ma, mb, a);
   return cudaGetLastError();
 }
 
