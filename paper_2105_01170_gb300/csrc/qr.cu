@@ -153,6 +153,85 @@ __device__ __forceinline__ T reflect_col(T* x, const T* v, T tau, int k, int mm,
   return a;
 }
 
+// block-wide sum of v in T; every thread gets it; red holds >= 32
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v, T* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < nw ? red[lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[32] = v;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// x_c <- (I - tau v v^T) x_c on rows k..mm-1 for the NC columns with act[c]
+// (one warp, interleaved for latency); lane 0 gets the updated row-k entry
+// of each column in yk[c].
+template <typename T, int NC>
+__device__ __forceinline__ void reflect_n(T* const (&x)[NC], const bool (&act)[NC], const T* v,
+                                          T tau, int k, int mm, int lane, T (&yk)[NC]) {
+  if (mm - k <= 32 * QR_RPL) {
+    T xr[NC][QR_RPL];
+    T w[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      w[c] = T(0);
+#pragma unroll
+      for (int i = 0; i < QR_RPL; ++i) {
+        const int r = k + lane + 32 * i;
+        xr[c][i] = (act[c] && r < mm) ? x[c][r] : T(0);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < QR_RPL; ++i) {
+      const int r = k + lane + 32 * i;
+      if (r < mm) {
+        const T vr = v[r];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) w[c] = fma(vr, xr[c][i], w[c]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T tw = tau * w[c];
+#pragma unroll
+      for (int i = 0; i < QR_RPL; ++i) {
+        const int r = k + lane + 32 * i;
+        if (act[c] && r < mm) {
+          const T y = fma(-tw, v[r], xr[c][i]);
+          x[c][r] = y;
+          if (i == 0) yk[c] = y;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (!act[c]) continue;
+      T w = T(0);
+      for (int r = k + lane; r < mm; r += 32) w = fma(v[r], x[c][r], w);
+      w = warp_sum(w);
+      const T tw = tau * w;
+      for (int r = k + lane; r < mm; r += 32) {
+        const T y = fma(-tw, v[r], x[c][r]);
+        x[c][r] = y;
+        if (r == k) yk[c] = y;
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -161,16 +240,17 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   const int novf = P.plan.novf;
   const size_t colb = align16((size_t)mm * sizeof(T));
   T* nrm = reinterpret_cast<T*>(smem_raw);                            // [rc] (8-byte slots)
-  T** colp = reinterpret_cast<T**>(smem_raw + (size_t)rc * 8);        // [rc]
+  T* nrm0 = reinterpret_cast<T*>(smem_raw + (size_t)rc * 8);          // [rc] (8-byte slots)
+  T** colp = reinterpret_cast<T**>(smem_raw + (size_t)rc * 16);       // [rc]
   int* perm = reinterpret_cast<int*>(colp + rc);                      // [rc]
   int* ipos = perm + rc;                                              // [rc]
-  unsigned char* p1 = smem_raw + align16((size_t)rc * 24);
+  unsigned char* p1 = smem_raw + align16((size_t)rc * 32);
   T* v = reinterpret_cast<T*>(p1);                                    // [mm]
   unsigned char* slots = p1 + colb;                                   // [nslot][mm]
   __shared__ T rv[32];
   __shared__ int ri[33];
-  __shared__ double red[32];
-  __shared__ T sh_tau, sh_beta, sh_scale, sh_nsc;
+  __shared__ T redt[33];
+  __shared__ T sh_nsc;
   const T* src = P.src + (int64_t)s * P.src_bs;
   T* F = P.F + (int64_t)s * P.F_bs;
   T* G = P.G + (int64_t)s * P.G_bs;
@@ -237,53 +317,50 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
       a = fma(x, x, a);
     }
     a = warp_sum(a);
-    if (lane == 0) nrm[j] = a;
+    if (lane == 0) {
+      nrm[j] = a;
+      nrm0[j] = a;
+    }
   }
   __syncthreads();
 
   for (int k = 0; k < rc; ++k) {
-    // pivot: the remaining column with the largest norm (pointer swap)
+    // pivot: the remaining column with the largest norm
     const int jp = block_argmax(nrm, k, rc, rv, ri);
-    if (jp != k && tid == 0) {
-      const T t = nrm[k]; nrm[k] = nrm[jp]; nrm[jp] = t;
-      T* tp = colp[k]; colp[k] = colp[jp]; colp[jp] = tp;
-      const int pi = perm[k]; perm[k] = perm[jp]; perm[jp] = pi;
-    }
-    __syncthreads();
-    // Householder reflector of B[k:, k]: copy to v, norm of the tail
-    const T* ck = colp[k];
-    double s2 = 0.0;
+    const T* cp = colp[jp];
+    // Householder reflector of the pivot column's rows k..mm-1: copy to v,
+    // squared norm of its tail on the scaled entries
+    T s2 = T(0);
     for (int r = k + tid; r < mm; r += nth) {
-      const T x = ck[r];
+      const T x = cp[r];
       v[r] = x;
-      if (r > k) s2 = fma((double)x, (double)x, s2);
-    }
-    s2 = block_sum(s2, red);
-    if (tid == 0) {
-      const double alpha = (double)v[k];
-      if (s2 == 0.0) {
-        sh_tau = T(0);
-        sh_beta = (T)alpha;
-        sh_scale = T(1);
-      } else {
-        const double beta = -copysign(sqrt(alpha * alpha + s2), alpha);
-        sh_tau = (T)((beta - alpha) / beta);
-        sh_beta = (T)beta;
-        sh_scale = (T)(1.0 / (alpha - beta));
+      if (r > k) {
+        const T xs = x * nsc;
+        s2 = fma(xs, xs, s2);
       }
     }
-    __syncthreads();
-    const T tau = sh_tau;
-    // retire column k into F: R[0..k, k] and the reflector tail
+    s2 = block_sum_t(s2, redt);
+    // every thread forms the same scalars (alpha from the column, which this
+    // step does not modify): beta = -sign(alpha) ||x[k:]||, tau = (beta -
+    // alpha) / beta, tail scale 1 / (alpha - beta)
+    const T alpha_s = cp[k] * nsc;
+    T tau = T(0), beta = cp[k], scale = T(1);
+    if (s2 != T(0)) {
+      const T beta_s = -copysign(sqrt(fma(alpha_s, alpha_s, s2)), alpha_s);
+      tau = (beta_s - alpha_s) / beta_s;
+      beta = beta_s / nsc;
+      scale = nsc / (alpha_s - beta_s);
+    }
+    // retire the pivot column into F column k: R[0..k, k] and the reflector
     T* Fk = F + (int64_t)k * mm;
     for (int r = tid; r < mm; r += nth) {
       T out;
       if (r < k) {
-        out = ck[r];
+        out = cp[r];
       } else if (r == k) {
-        out = sh_beta;
+        out = beta;
       } else {
-        out = v[r] * sh_scale;
+        out = v[r] * scale;
         v[r] = out;
       }
       Fk[r] = out;
@@ -291,12 +368,51 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
     if (tid == 0) {
       v[k] = T(1);
       P.tau[(int64_t)s * rc + k] = tau;
+      if (jp != k) {   // the column at position k moves to position jp
+        T t = nrm[k]; nrm[k] = nrm[jp]; nrm[jp] = t;
+        t = nrm0[k]; nrm0[k] = nrm0[jp]; nrm0[jp] = t;
+        T* tp = colp[k]; colp[k] = colp[jp]; colp[jp] = tp;
+        const int pi = perm[k]; perm[k] = perm[jp]; perm[jp] = pi;
+      }
     }
     __syncthreads();
-    // apply the reflector to the remaining columns; exact partial norms
-    for (int j = k + 1 + warp; j < rc; j += nw) {
-      const T a = reflect_col<T, true>(colp[j], v, tau, k, mm, lane, nsc);
-      if (lane == 0) nrm[j] = a;
+    // apply the reflector to the remaining columns, two per warp at a time;
+    // downdate their partial norms (n - y_k^2), recomputed exactly when the
+    // downdate has lost most of its digits
+    for (int j0 = k + 1 + warp; j0 < rc; j0 += 2 * nw) {
+      const int j1 = j0 + nw;
+      T* const xs[2] = {colp[j0], colp[j1 < rc ? j1 : j0]};
+      const bool act[2] = {true, j1 < rc};
+      T yk[2] = {T(0), T(0)};
+      reflect_n<T, 2>(xs, act, v, tau, k, mm, lane, yk);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (!act[c]) continue;
+        const int j = c ? j1 : j0;
+        T nn = T(0);
+        int rec = 0;
+        if (lane == 0) {
+          const T y = yk[c] * nsc;
+          nn = nrm[j] - y * y;
+          rec = (nn > T(1e-3) * nrm0[j]) ? 0 : 1;
+        }
+        rec = __shfl_sync(0xffffffffu, rec, 0);
+        if (rec) {
+          __syncwarp();
+          T a = T(0);
+          for (int r = k + 1 + lane; r < mm; r += 32) {
+            const T z = xs[c][r] * nsc;
+            a = fma(z, z, a);
+          }
+          a = warp_sum(a);
+          if (lane == 0) {
+            nrm[j] = a;
+            nrm0[j] = a;
+          }
+        } else if (lane == 0) {
+          nrm[j] = nn;
+        }
+      }
     }
     __syncthreads();
   }
@@ -382,7 +498,7 @@ QrPlan qr_plan(int mm, int rc, int max_smem) {
   // leave room for the kernels' static shared memory
   max_smem = max_smem > 1024 ? max_smem - 1024 : 0;
   const size_t colb = align16((size_t)mm * sizeof(T));
-  const size_t head = align16((size_t)rc * 24) + colb;
+  const size_t head = align16((size_t)rc * 32) + colb;
   const size_t avail = (size_t)max_smem > head ? (size_t)max_smem - head : 0;
   q.nslot = (int)std::min<size_t>((size_t)rc, avail / colb);
   q.novf = rc - q.nslot;
