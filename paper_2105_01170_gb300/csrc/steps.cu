@@ -244,17 +244,29 @@ __global__ void scatter_kernel(const int* __restrict__ map, const double* __rest
 
 template <typename T>
 __global__ void orth_kernel(const T* __restrict__ Gm, int rc, const int* __restrict__ ranks,
-                            const double* __restrict__ scale, double* out) {
+                            const double* __restrict__ scale, double* out, int use_inv) {
+  // G[a, b] / (s_a s_b) - delta_ab with the reciprocals 1 / s_a staged once
+  // per slice (fp64 division is slow on this part); 0 where s_a = 0
+  extern __shared__ double inv[];
   __shared__ double red[32];
   const int i = blockIdx.x;
   const int r = ranks ? ranks[i] : rc;
   const T* G = Gm + (int64_t)i * rc * rc;
   const double* sc = scale ? scale + (int64_t)i * rc : nullptr;
+  if (sc && use_inv) {
+    for (int a = threadIdx.x; a < r; a += blockDim.x) inv[a] = sc[a] > 0 ? 1.0 / sc[a] : 0.0;
+    __syncthreads();
+  }
   double mx = 0.0;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int a = e % r, b = e / r;
     double g = (double)G[a + (int64_t)b * rc];
-    if (sc) g = (sc[a] > 0 && sc[b] > 0) ? g / (sc[a] * sc[b]) : (a == b ? 1.0 : 0.0);
+    if (sc && use_inv) {
+      const double ia = inv[a], ib = inv[b];
+      g = (ia > 0 && ib > 0) ? g * ia * ib : (a == b ? 1.0 : 0.0);
+    } else if (sc) {
+      g = (sc[a] > 0 && sc[b] > 0) ? g / (sc[a] * sc[b]) : (a == b ? 1.0 : 0.0);
+    }
     const double v = g - (a == b ? 1.0 : 0.0);
     mx = fmax(mx, fabs(v));
   }
@@ -418,7 +430,9 @@ template <typename T>
 cudaError_t orth_defect(const T* Gm, int rc, int p, const int* ranks, const double* scale,
                         double* out, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
-  orth_kernel<T><<<p, 256, 0, st>>>(Gm, rc, ranks, scale, out);
+  const int use_inv = (scale && rc <= 6144) ? 1 : 0;   // reciprocals fit in 48 KB
+  orth_kernel<T><<<p, 256, use_inv ? (size_t)rc * sizeof(double) : 0, st>>>(Gm, rc, ranks, scale,
+                                                                             out, use_inv);
   return cudaGetLastError();
 }
 
