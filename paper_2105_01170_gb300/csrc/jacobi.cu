@@ -102,6 +102,42 @@ template <> struct Angle<float> {
     s = c * t;
     return true;
   }
+  // The same rotation as (c, t = s / c), for the scaled-rotation form.
+  static __device__ __forceinline__ bool get_ct(float al, float be, float ga, float tol,
+                                                float floor_, float& c, float& t) {
+    // square roots and reciprocals through the approximate hardware
+    // functions: the threshold needs no more, and any tangent is a valid
+    // rotation as long as c is computed from it accurately (below)
+    al = fmaxf(al, 0.f);
+    be = fmaxf(be, 0.f);
+    const float nrm = (al * rsqrtf(al)) * (be * rsqrtf(be));   // NaN when a norm is 0
+    if (!(fabsf(ga) > tol * nrm) || !(fabsf(ga) > floor_)) return false;
+    if (fabsf(ga) > 0.99f * nrm) {
+      double cd = 1.0, sd = 0.0;
+      angle_fp64(al, be, ga, 0.0, 0.0, cd, sd);
+      c = (float)cd;
+      t = (float)(sd / cd);
+      return true;
+    }
+    const float zeta = __fdividef(be - al, 2.0f * ga);
+    const float az = fabsf(zeta);
+    if (az > 1e18f) {
+      t = __fdividef(0.5f, zeta);
+    } else {
+      const float q = fmaf(zeta, zeta, 1.0f);
+      t = copysignf(__fdividef(1.0f, az + q * rsqrtf(q)), zeta);
+    }
+    const float u_hi = t * t;
+    const float u_lo = fmaf(t, t, -u_hi);
+    const float q_hi = 1.0f + u_hi;
+    const float q_lo = ((u_hi <= 1.0f) ? ((1.0f - q_hi) + u_hi) : ((u_hi - q_hi) + 1.0f)) + u_lo;
+    const float r0 = rsqrtf(q_hi);
+    const float a_hi = r0 * r0;
+    const float a_lo = fmaf(r0, r0, -a_hi);
+    const float e = fmaf(-q_hi, a_hi, 1.0f) - fmaf(q_hi, a_lo, q_lo * a_hi);
+    c = fmaf(0.5f * r0, e, r0);
+    return true;
+  }
 };
 
 // Rows per lane kept in registers between the dot products and the rotation.
@@ -327,18 +363,43 @@ __device__ __forceinline__ float dot4(const float4& a, const float4& b, float ac
   return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
 }
 
-__device__ __forceinline__ void rot4(float4& x, float4& y, float c, float s) {
-  const float4 a = x, b = y;
-  x = make_float4(c * a.x - s * b.x, c * a.y - s * b.y, c * a.z - s * b.z, c * a.w - s * b.w);
-  y = make_float4(s * a.x + c * b.x, s * a.y + c * b.y, s * a.z + c * b.z, s * a.w + c * b.w);
+// Warp sum of 4 values at once: lane l ends with the full sum of value
+// 2 ((l >> 4) & 1) + ((l >> 3) & 1), so value q sits in lane 8 q.
+__device__ __forceinline__ float reduce4(const float (&v)[4], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8;
+  float u2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h4 ? v[i] : v[i + 2];
+    const float keep = h4 ? v[i + 2] : v[i];
+    u2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  const float send = h3 ? u2[0] : u2[1];
+  const float keep = h3 ? u2[1] : u2[0];
+  float u = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  u += __shfl_xor_sync(0xffffffffu, u, 4);
+  u += __shfl_xor_sync(0xffffffffu, u, 2);
+  u += __shfl_xor_sync(0xffffffffu, u, 1);
+  return u;
 }
 
 // One group of rotations on tiles A (slots sa.., na columns) and B (slots
 // sb.., nb columns) by one warp; columns past na / nb are absent (zero, never
 // rotated).  INNER pairs of A (B) only when doA (doB).  mq = mm / 4 float4
 // rows of dot-product part, rq = rc / 4 float4 rows of V part.  csw: the
-// warp's shared-memory record of the rotations (2 float4 per sub-round).
-// Returns true if any pair was rotated.
+// warp's shared-memory record of the group (per sub-round four (t1, t2)
+// pairs, then the eight column scales).  Returns true if any pair was
+// rotated.
+//
+// The squared column norms are reduced once per group and then updated with
+// each rotation (alpha' = alpha - t gamma, beta' = beta + t gamma), so a
+// sub-round reduces only its four inner products.  The rotations use the
+// scaled form: a column is d times its register copy, and the rotation
+// (c, t) of the true columns becomes x_a <- x_a - (t d_b / d_a) x_b,
+// x_b <- x_b + (t d_a / d_b) x_a on the copies with d_a, d_b <- c d_a, c d_b
+// (two FMAs per row instead of four); the scales are folded back when the
+// group ends.  Within a group a column takes at most four rotations with
+// |t| <= 1, so d stays in [1/4, 1].
 template <int NQW, bool INNER>
 __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, int sb, int nb,
                                            bool doA, bool doB, int mq, int rq, int lane,
@@ -356,74 +417,121 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
       x[c][i] = (valid && qq < mq) ? col[qq] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
+  // squared norms of the 8 columns, in every lane
+  float nrm8[8];
+  {
+    float v[16];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      float a = 0.f;
+#pragma unroll
+      for (int i = 0; i < NQW; ++i) a = dot4(x[c][i], x[c][i], a);
+      v[c] = a;
+      v[8 + c] = 0.f;
+    }
+    const float red = reduce16(v, lane);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) nrm8[c] = __shfl_sync(0xffffffffu, red, 2 * c);
+  }
+  float d[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) d[c] = 1.f;
   unsigned mk[NR];
   unsigned any = 0;
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
-    float v[16];
+    float g4[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int a, b;
       tile_pair<INNER>(r, q, a, b);
-      float al = 0.f, be = 0.f, ga = 0.f;
+      float g = 0.f;
 #pragma unroll
-      for (int i = 0; i < NQW; ++i) {
-        al = dot4(x[a][i], x[a][i], al);
-        be = dot4(x[b][i], x[b][i], be);
-        ga = dot4(x[a][i], x[b][i], ga);
-      }
-      v[q] = al;
-      v[4 + q] = be;
-      v[8 + q] = ga;
-      v[12 + q] = 0.f;
+      for (int i = 0; i < NQW; ++i) g = dot4(x[a][i], x[b][i], g);
+      g4[q] = g;
     }
-    const float red = reduce16(v, lane);
+    const float gr = reduce4(g4, lane);
+    // lanes 0..3: the angle of pair q = lane (lanes 4..31 repeat them)
     const int q = lane & 3;
-    const float al = __shfl_sync(0xffffffffu, red, 2 * q);
-    const float be = __shfl_sync(0xffffffffu, red, 2 * (4 + q));
-    const float ga = __shfl_sync(0xffffffffu, red, 2 * (8 + q));
+    const float gq = __shfl_sync(0xffffffffu, gr, 8 * q);
+    float al = 0.f, be = 0.f, dd = 1.f;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      int a, b;
+      tile_pair<INNER>(r, qq, a, b);
+      if (q == qq) {
+        al = nrm8[a];
+        be = nrm8[b];
+        dd = d[a] * d[b];
+      }
+    }
+    const float ga = gq * dd;
     const bool allowed = INNER ? (q < 2 ? doA : doB) : true;
-    float c = 1.f, s = 0.f;
-    const bool ok = allowed && Angle<float>::get(al, be, ga, tol, floor_, c, s);
-    if (!ok) {
+    float c = 1.f, t = 0.f;
+    const bool ok = allowed && Angle<float>::get_ct(al, be, ga, tol, floor_, c, t);
+    if (!ok) {   // an exact identity: t = 0, c = 1
       c = 1.f;
-      s = 0.f;
+      t = 0.f;
     }
     const unsigned m = __ballot_sync(0xffffffffu, ok) & 0xfu;
     mk[r] = m;
     any |= m;
-    // record (c_q, s_q) of the sub-round: lanes 0 and 2 write one float4 each
-    {
-      const float c1 = __shfl_down_sync(0xffffffffu, c, 1);
-      const float s1 = __shfl_down_sync(0xffffffffu, s, 1);
-      if (lane == 0 || lane == 2) csw[2 * r + (lane >> 1)] = make_float4(c, s, c1, s1);
+    if (m == 0u) continue;
+    // all four pairs unconditionally (the ones not rotated are identities),
+    // so their independent chains interleave
+    float cq[4], tq[4], gt[4], t1[4], t2[4];
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      cq[qq] = __shfl_sync(0xffffffffu, c, qq);
+      tq[qq] = __shfl_sync(0xffffffffu, t, qq);
+      gt[qq] = __shfl_sync(0xffffffffu, ga, qq);
     }
 #pragma unroll
     for (int qq = 0; qq < 4; ++qq) {
-      if ((m >> qq) & 1u) {
-        int a, b;
-        tile_pair<INNER>(r, qq, a, b);
-        const float cq = __shfl_sync(0xffffffffu, c, qq);
-        const float sq = __shfl_sync(0xffffffffu, s, qq);
+      int a, b;
+      tile_pair<INNER>(r, qq, a, b);
+      t1[qq] = __fdividef(tq[qq] * d[b], d[a]);
+      t2[qq] = __fdividef(tq[qq] * d[a], d[b]);
 #pragma unroll
-        for (int i = 0; i < NQW; ++i) rot4(x[a][i], x[b][i], cq, sq);
+      for (int i = 0; i < NQW; ++i) {
+        const float4 xa = x[a][i], xb = x[b][i];
+        x[a][i] = make_float4(fmaf(-t1[qq], xb.x, xa.x), fmaf(-t1[qq], xb.y, xa.y),
+                              fmaf(-t1[qq], xb.z, xa.z), fmaf(-t1[qq], xb.w, xa.w));
+        x[b][i] = make_float4(fmaf(t2[qq], xa.x, xb.x), fmaf(t2[qq], xa.y, xb.y),
+                              fmaf(t2[qq], xa.z, xb.z), fmaf(t2[qq], xa.w, xb.w));
       }
+      d[a] *= cq[qq];
+      d[b] *= cq[qq];
+      nrm8[a] = fmaf(-tq[qq], gt[qq], nrm8[a]);
+      nrm8[b] = fmaf(tq[qq], gt[qq], nrm8[b]);
+    }
+    if (lane == 0) {
+      csw[2 * r] = make_float4(t1[0], t2[0], t1[1], t2[1]);
+      csw[2 * r + 1] = make_float4(t1[2], t2[2], t1[3], t2[3]);
     }
   }
   if (!any) return false;
-  __syncwarp();
+  // fold the scales back and store
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const bool valid = c < 4 ? c < na : (c - 4) < nb;
     if (!valid) continue;
     float4* col = reinterpret_cast<float4*>(S + (int64_t)(c < 4 ? sa + c : sb + c - 4) * ldS);
+    const float dc = d[c];
 #pragma unroll
     for (int i = 0; i < NQW; ++i) {
       const int qq = lane + 32 * i;
-      if (qq < mq) col[qq] = x[c][i];
+      const float4 v = x[c][i];
+      if (qq < mq) col[qq] = make_float4(dc * v.x, dc * v.y, dc * v.z, dc * v.w);
     }
   }
-  // V rows: float4 rows [mq, mq + rq) of the stacked columns
+  if (lane == 0) {
+    csw[2 * NR] = make_float4(d[0], d[1], d[2], d[3]);
+    csw[2 * NR + 1] = make_float4(d[4], d[5], d[6], d[7]);
+  }
+  __syncwarp();
+  // V rows: the same scaled rotations, then the scales
+  const float4 d03 = csw[2 * NR], d47 = csw[2 * NR + 1];
   for (int qq = lane; qq < rq; qq += 32) {
     float4 y[8];
 #pragma unroll
@@ -436,16 +544,18 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
       if (mk[r] == 0u) continue;
-      const float4 cs01 = csw[2 * r], cs23 = csw[2 * r + 1];
+      const float4 r01 = csw[2 * r], r23 = csw[2 * r + 1];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if ((mk[r] >> q) & 1u) {
-          int a, b;
-          tile_pair<INNER>(r, q, a, b);
-          const float cq = q == 0 ? cs01.x : q == 1 ? cs01.z : q == 2 ? cs23.x : cs23.z;
-          const float sq = q == 0 ? cs01.y : q == 1 ? cs01.w : q == 2 ? cs23.y : cs23.w;
-          rot4(y[a], y[b], cq, sq);
-        }
+        int a, b;
+        tile_pair<INNER>(r, q, a, b);
+        const float ta = q == 0 ? r01.x : q == 1 ? r01.z : q == 2 ? r23.x : r23.z;
+        const float tb = q == 0 ? r01.y : q == 1 ? r01.w : q == 2 ? r23.y : r23.w;
+        const float4 ya = y[a], yb = y[b];
+        y[a] = make_float4(fmaf(-ta, yb.x, ya.x), fmaf(-ta, yb.y, ya.y), fmaf(-ta, yb.z, ya.z),
+                           fmaf(-ta, yb.w, ya.w));
+        y[b] = make_float4(fmaf(tb, ya.x, yb.x), fmaf(tb, ya.y, yb.y), fmaf(tb, ya.z, yb.z),
+                           fmaf(tb, ya.w, yb.w));
       }
     }
 #pragma unroll
@@ -453,7 +563,10 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
       const bool valid = c < 4 ? c < na : (c - 4) < nb;
       if (!valid) continue;
       float4* col = reinterpret_cast<float4*>(S + (int64_t)(c < 4 ? sa + c : sb + c - 4) * ldS);
-      col[mq + qq] = y[c];
+      const float dc = c == 0 ? d03.x : c == 1 ? d03.y : c == 2 ? d03.z : c == 3 ? d03.w
+                     : c == 4 ? d47.x : c == 5 ? d47.y : c == 6 ? d47.z : d47.w;
+      const float4 v = y[c];
+      col[mq + qq] = make_float4(dc * v.x, dc * v.y, dc * v.z, dc * v.w);
     }
   }
   __syncwarp();   // the record is rewritten by the warp's next group
@@ -699,7 +812,7 @@ __global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel
     if constexpr (TILE > 0) {
       const int wp = tid >> 5, ln = tid & 31, nwp = NTh >> 5;
       const int mq = mm >> 2, rq = rc >> 2;
-      __shared__ float4 cs_rec[kMaxTileWarps][8];   // rotation record of each warp
+      __shared__ float4 cs_rec[kMaxTileWarps][10];   // rotation record of each warp
       float4* csw = cs_rec[wp];
       for (int ps = 0; ps < npair_sets; ++ps) {
         TPhase ph;
@@ -866,7 +979,7 @@ template <typename T>
 JacobiPlan jacobi_plan(int m, int n, int max_smem) {
   JacobiPlan pl;
   // leave room for the kernel's static shared memory
-  max_smem = max_smem > 2048 ? max_smem - 2048 : 0;
+  max_smem = max_smem > 3072 ? max_smem - 3072 : 0;
   pl.trans = (m < n) ? 1 : 0;
   pl.mm = pl.trans ? n : m;
   pl.rc = pl.trans ? m : n;
