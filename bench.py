@@ -39,6 +39,11 @@ REL_TOL = 1e-6
 # the headline metric, as the benchmark configuration names it; value = whole
 # steps (compression + 256-RHS matvec) per second, the matvec GFLOP/s beside it
 METRIC = "t-SVDM compressions/s + Kron-sum matvec GFLOP/s, mixed vs FP64 GPU, equal err"
+# DRAM bytes (read + write) of one slice of the register-tiled Jacobi SVD at
+# 256 x 256, from an ncu capture of the 15-slice case (4,164,096 B read, 0
+# written; profiles/jacobi_kernel_spacetime_T8_256x256x15.md); every slice
+# moves the same bytes, so a launch moves p times this
+JACOBI_DRAM_BYTES_PER_SLICE = 4164096 / 15
 
 
 def log(*a):
@@ -324,7 +329,10 @@ def main():
     achieved = svd_alg / (svd_ms * 1e-3) / 1e12
     roof = {"kernel": "jacobi_kernel<float> (per-slice SVD, one CTA per slice)",
             "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": achieved / alu_peak, "traffic": None,
+            "frac": achieved / alu_peak,
+            "traffic": (JACOBI_DRAM_BYTES_PER_SLICE * pr.p
+                        if (pr.m, pr.n) == (256, 256) else None),
+            "traffic_note": "dram read+write bytes per launch, ncu capture of 15 slices scaled by slices",
             "peak_note": f"fp32 FMA: {NSM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                          "(unit counts x max clock; no measured ALU peak)",
             "algorithmic": f"{pr.p} x GVL SVD count 4m^2n+8mn^2+9n^3 = {svd_alg:.3e} flop/launch",

@@ -54,6 +54,9 @@ def problem(kind):
     if kind == "block_mode_fp32":          # 256 x 256 fp32 exceeds shared memory
         bm = G.toeplitz_map(2)
         return G.Problem(kind, g.standard_normal((3, 256, 256)), bm)
+    if kind == "wide_128":                 # n = 128 blocks: the matvec's staged epilogue
+        bm = G.toeplitz_map(3)
+        return G.Problem(kind, g.standard_normal((5, 24, 128)), bm)
     if kind == "tall_300x40":              # QR reflectors longer than 256 rows
         bm = G.toeplitz_map(2)
         return G.Problem(kind, g.standard_normal((3, 300, 40)), bm)
@@ -136,7 +139,8 @@ def test_tsvdm_end_to_end(prec, kind, tol, pre):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
-@pytest.mark.parametrize("kind", ["toeplitz_ragged", "wide_trans", "tridiag_zero_blocks"])
+@pytest.mark.parametrize("kind", ["toeplitz_ragged", "wide_trans", "tridiag_zero_blocks",
+                                  "block_mode_fp32", "wide_128"])
 @pytest.mark.parametrize("pre", PRECONDS, ids=QNAME.get)
 def test_kron_sum_apply(prec, kind, pre):
     pr = problem(kind)
