@@ -730,6 +730,37 @@ __device__ __forceinline__ bool tphase_task(const TPhase& p, int t, int k, TTask
   return true;
 }
 
+// Block pair of phase ps of a tiled sweep over nb blocks.  The sweep opens
+// with the matching (0,1), (2,3), ... in which both blocks also rotate their
+// inner pairs (all tasks of those rounds busy), then visits the remaining
+// pairs in lexicographic order with cross pairs only; for odd nb the last
+// block's inner pairs go with its first visit, (0, nb - 1).
+__device__ __forceinline__ void tile_phase_ij(int ps, int nb, int& I, int& J, bool& doI,
+                                              bool& doJ) {
+  const int nm = nb / 2;
+  if (ps < nm) {
+    I = 2 * ps;
+    J = I + 1;
+    doI = doJ = true;
+    return;
+  }
+  int idx = ps - nm;
+  for (int a = 0; a < nb; ++a)
+    for (int b = a + 1; b < nb; ++b) {
+      if ((a & 1) == 0 && b == a + 1) continue;   // a matching pair
+      if (idx-- == 0) {
+        I = a;
+        J = b;
+        doI = false;
+        doJ = (nb & 1) && a == 0 && b == nb - 1;
+        return;
+      }
+    }
+  I = 0;
+  J = 1;
+  doI = doJ = false;
+}
+
 // Block staging of a phase (I, J): block I stays in slots [0, bc) while
 // consecutive phases share it (resI), block J goes to slots [bc, 2 bc).
 template <typename T, int VEC>
@@ -819,9 +850,10 @@ __global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel
         if (in_smem) {
           ph = tphase_smem(rc);
         } else {
+          bool doI, doJ;
+          tile_phase_ij(ps, nb, I, J, doI, doJ);
           stage_in<T, VEC>(S, ldS, W, len, bc, rc, I, J, resI, tid, NTh);
-          ph = tphase_blocks(min(bc, rc - I * bc), min(bc, rc - J * bc), bc, I == 0 && J == 1,
-                             I == 0);
+          ph = tphase_blocks(min(bc, rc - I * bc), min(bc, rc - J * bc), bc, doI, doJ);
         }
         const int nrounds = tphase_rounds(ph);
         for (int t = 0; t < nrounds; ++t) {
@@ -838,14 +870,9 @@ __global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel
           }
           __syncthreads();
         }
-        if (!in_smem) {
+        if (!in_smem)
           copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len,
                             ph.bJ, tid, NTh, false);
-          if (++J == nb) {
-            ++I;
-            J = I + 1;
-          }
-        }
       }
     } else
     for (int ps = 0; ps < npair_sets; ++ps) {
