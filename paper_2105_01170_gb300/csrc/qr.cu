@@ -244,13 +244,15 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   T** colp = reinterpret_cast<T**>(smem_raw + (size_t)rc * 16);       // [rc]
   int* perm = reinterpret_cast<int*>(colp + rc);                      // [rc]
   int* ipos = perm + rc;                                              // [rc]
-  unsigned char* p1 = smem_raw + align16((size_t)rc * 32);
+  int* gpos = ipos + rc;                                              // [novf]
+  unsigned char* p1 = smem_raw + align16((size_t)rc * 36);
   T* v = reinterpret_cast<T*>(p1);                                    // [mm]
   unsigned char* slots = p1 + colb;                                   // [nslot][mm]
   __shared__ T rv[32];
   __shared__ int ri[33];
   __shared__ T redt[33];
   __shared__ T sh_nsc;
+  __shared__ int sh_nglob, sh_mig_src, sh_mig_pos;
   const T* src = P.src + (int64_t)s * P.src_bs;
   T* F = P.F + (int64_t)s * P.F_bs;
   T* G = P.G + (int64_t)s * P.G_bs;
@@ -299,9 +301,12 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   }
   // position j starts with the column of rank j; the first novf positions
   // (largest norms) are stored in the overflow
-  for (int j = tid; j < rc; j += nth)
+  for (int j = tid; j < rc; j += nth) {
     colp[j] = j < novf ? G + (int64_t)j * mm
                        : reinterpret_cast<T*>(slots + (size_t)(j - novf) * colb);
+    if (j < novf) gpos[j] = j;   // overflow column j sits at position j
+  }
+  if (tid == 0) sh_nglob = novf;
   __syncthreads();
   for (int e = tid; e < mm * rc; e += nth) {
     int r, c;
@@ -373,9 +378,40 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
         t = nrm0[k]; nrm0[k] = nrm0[jp]; nrm0[jp] = t;
         T* tp = colp[k]; colp[k] = colp[jp]; colp[jp] = tp;
         const int pi = perm[k]; perm[k] = perm[jp]; perm[jp] = pi;
+        if (sh_nglob > 0 && tp >= G && tp < G + (int64_t)novf * mm)
+          gpos[(tp - G) / mm] = jp;
+      }
+      // Overflow columns move into shared memory as slots free up: the
+      // retired pivot's slot takes one remaining overflow column (copied
+      // below), or a retired overflow pivot leaves the overflow itself.
+      sh_mig_src = -1;
+      if (sh_nglob > 0) {
+        T* pk = colp[k];
+        if (pk >= G && pk < G + (int64_t)novf * mm) {
+          gpos[(pk - G) / mm] = -1;
+          --sh_nglob;
+        } else {
+          for (int g = 0; g < novf; ++g)
+            if (gpos[g] > k) {
+              sh_mig_src = g;
+              sh_mig_pos = gpos[g];
+              gpos[g] = -1;
+              --sh_nglob;
+              break;
+            }
+        }
       }
     }
     __syncthreads();
+    if (sh_mig_src >= 0) {   // (block-uniform) copy the column into the freed slot
+      const int g = sh_mig_src, pos = sh_mig_pos;
+      T* dst = colp[k];
+      const T* srcg = G + (int64_t)g * mm;
+      for (int r = tid; r < mm; r += nth) dst[r] = srcg[r];
+      __syncthreads();
+      if (tid == 0) colp[pos] = dst;
+      __syncthreads();
+    }
     // apply the reflector to the remaining columns, two per warp at a time;
     // downdate their partial norms (n - y_k^2), recomputed exactly when the
     // downdate has lost most of its digits
@@ -498,7 +534,7 @@ QrPlan qr_plan(int mm, int rc, int max_smem) {
   // leave room for the kernels' static shared memory
   max_smem = max_smem > 1024 ? max_smem - 1024 : 0;
   const size_t colb = align16((size_t)mm * sizeof(T));
-  const size_t head = align16((size_t)rc * 32) + colb;
+  const size_t head = align16((size_t)rc * 36) + colb;
   const size_t avail = (size_t)max_smem > head ? (size_t)max_smem - head : 0;
   q.nslot = (int)std::min<size_t>((size_t)rc, avail / colb);
   q.novf = rc - q.nslot;
