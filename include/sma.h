@@ -138,6 +138,12 @@ typedef struct {
                              (needs a non-NULL stream; stage timing is then
                              reported for the whole compression only)          */
   sma_precondition precondition;  /* t-SVDM slice SVD preconditioning          */
+  int32_t autotune;       /* 1: on the first compression of each slice shape,
+                             time the candidate slice-SVD plans on the actual
+                             slices (twice each) and keep the fastest; the
+                             choice is cached for the process.  0: default
+                             plan.  Trial runs are not part of sma_profile's
+                             stage times.                                     */
 } sma_options;
 
 typedef struct {

@@ -56,7 +56,7 @@ class sma_options(ctypes.Structure):
                 ("fixed_rank", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("profile", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("precondition", ctypes.c_int)]
+                ("precondition", ctypes.c_int), ("autotune", ctypes.c_int32)]
 
 
 class sma_result(ctypes.Structure):
@@ -230,7 +230,7 @@ class Handle:
     def __init__(self, problems, prec=SMA_MIXED, decomp=SMA_TSVDM, mkind=SMA_M_DCT2,
                  layout=SMA_INPUT_DENSE, M_user=None, fixed_rank=0, rel_tol=0.0,
                  max_sweeps=0, stream=None, profile=False, graph=False,
-                 precondition=None):
+                 precondition=None, autotune=False):
         self._keep = []
         structs = []
         for pr in problems:
@@ -253,7 +253,8 @@ class Handle:
             sptr = ctypes.c_void_p(int(stream))
         self.opt = sma_options(prec, decomp, mkind, layout, mu, int(fixed_rank), float(rel_tol),
                                int(max_sweeps), sptr, 1 if profile else 0, 1 if graph else 0,
-                               SMA_PRECOND_AUTO if precondition is None else int(precondition))
+                               SMA_PRECOND_AUTO if precondition is None else int(precondition),
+                               1 if autotune else 0)
         self.nprob = len(structs)
         self.prec = prec
         st, self.h = sma_create(structs, self.opt)

@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -130,6 +132,7 @@ struct Prob {
   // rc x rc factor R1^T, and the rebuild uses L = Q1 V (discarded columns)
   // and Rt = P W in place of the slice's own W and V
   bool qr = false;
+  bool tuned = false;                       // Jacobi plan chosen by the autotuner
   int trans = 0;                            // slices processed transposed (m < n)
   QrPlan qplan{};
   T* qF = nullptr;
@@ -226,6 +229,7 @@ struct Prob {
 template <typename T>
 struct SvdBin {
   int m = 0, n = 0, count = 0;
+  bool tuned = false;
   JacobiPlan jp{};
   SliceDesc<T>* desc = nullptr;   // device
   T* W = nullptr;                 // block-mode workspace
@@ -715,6 +719,78 @@ QrParams<T> qr_params(const Prob<T>& P) {
   return q;
 }
 
+// ---- autotuner of the slice-SVD plan ---------------------------------------
+// On the first compression of a slice shape (options.autotune), every
+// candidate plan (jacobi_plan_candidates) runs twice on the actual slices and
+// the fastest second run wins; the choice is cached for the process, keyed by
+// the Jacobi input shape and the element type.  The problems' device status
+// words are saved and restored around the trial runs, which write only the
+// outputs the real run overwrites.
+std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+std::map<uint64_t, JacobiPlan>& tune_cache() {
+  static std::map<uint64_t, JacobiPlan> c;
+  return c;
+}
+
+template <typename T>
+sma_status tune_plan(sma_ctx* h, JacobiParams<T> J, int count, int jm, int jn, JacobiPlan& plan,
+                     const std::vector<int*>& status_words) {
+  const uint64_t key = ((uint64_t)(uint32_t)jm << 32) | ((uint64_t)(uint32_t)jn << 4) | sizeof(T);
+  {
+    std::lock_guard<std::mutex> g(tune_mutex());
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) {
+      plan = it->second;
+      return SMA_OK;
+    }
+  }
+  cudaStream_t st = h->st;
+  int* saved = nullptr;
+  SMA_TRY(h->mem.alloc(&saved, status_words.size()));
+  for (size_t i = 0; i < status_words.size(); ++i)
+    SMA_CK(cudaMemcpyAsync(saved + i, status_words[i], sizeof(int), cudaMemcpyDeviceToDevice, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SMA_CK(cudaEventCreate(&e0));
+  SMA_CK(cudaEventCreate(&e1));
+  JacobiPlan best = plan;
+  float best_ms = 3.0e38f;
+  cudaError_t err = cudaSuccess;
+  for (const JacobiPlan& c : jacobi_plan_candidates<T>(jm, jn, h->max_smem)) {
+    if (c.block_mode != plan.block_mode) continue;
+    JacobiParams<T> Jc = J;
+    Jc.mm = c.mm; Jc.rc = c.rc; Jc.trans = c.trans; Jc.ldS = c.ldS; Jc.bcols = c.bcols;
+    Jc.g = c.g; Jc.sort_n = c.sort_n; Jc.tile = c.tile;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
+      err = cudaEventRecord(e0, st);
+      if (err == cudaSuccess) err = jacobi_svd<T>(Jc, count, c.threads, c.smem, st);
+      ++h->launches;
+      if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (err != cudaSuccess) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SMA_CK(err);
+  for (size_t i = 0; i < status_words.size(); ++i)
+    SMA_CK(cudaMemcpyAsync(status_words[i], saved + i, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  SMA_CK(cudaStreamSynchronize(st));
+  h->mem.release(saved);
+  plan = best;
+  std::lock_guard<std::mutex> g(tune_mutex());
+  tune_cache()[key] = best;
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status tsvdm_svd(sma_ctx* h, Prob<T>& P) {
   cudaStream_t st = h->st;
@@ -725,20 +801,25 @@ sma_status tsvdm_svd(sma_ctx* h, Prob<T>& P) {
     SMA_K(qrcp<T>(qr_params(P), p, st));
     stage_end(h);
   }
-  stage_begin(h, SMA_STAGE_SVD);
-  {
-    JacobiParams<T> J = jacobi_params<T>(h, P.jp);
+  auto params = [&](const JacobiPlan& jp) {
+    JacobiParams<T> J = jacobi_params<T>(h, jp);
     if (P.qr) {
       J.src = P.qJ; J.src_bs = (int64_t)rc * rc; J.m = rc; J.n = rc;
     } else {
       J.src = P.Xh; J.src_bs = mn; J.m = m; J.n = n;
     }
-    J.W = P.Wj; J.W_bs = (int64_t)(P.jp.mm + P.jp.rc) * P.jp.rc;
-    J.U = P.U; J.U_bs = (int64_t)P.jp.mm * rc;
+    J.W = P.Wj; J.W_bs = (int64_t)(jp.mm + jp.rc) * jp.rc;
+    J.U = P.U; J.U_bs = (int64_t)jp.mm * rc;
     J.V = P.V; J.V_bs = (int64_t)rc * rc;
     J.sigma = P.sigma; J.sweeps = P.sweeps; J.status = P.status;
-    SMA_K(jacobi_svd<T>(J, p, P.jp.threads, P.jp.smem, st));
+    return J;
+  };
+  if (h->opt.autotune && !h->capturing && !P.tuned) {
+    SMA_TRY(tune_plan<T>(h, params(P.jp), p, P.qr ? rc : m, P.qr ? rc : n, P.jp, {P.status}));
+    P.tuned = true;
   }
+  stage_begin(h, SMA_STAGE_SVD);
+  SMA_K(jacobi_svd<T>(params(P.jp), p, P.jp.threads, P.jp.smem, st));
   stage_end(h);
   return SMA_OK;
 }
@@ -750,16 +831,26 @@ sma_status tsvdm_svd_batched(sma_ctx* h) {
   for (auto& P : probs<T>(h))
     if (P.qr) SMA_K(qrcp<T>(qr_params(P), P.p, h->st));
   stage_end(h);
-  stage_begin(h, SMA_STAGE_SVD);
-  for (auto& b : bins<T>(h)) {
-    JacobiParams<T> J = jacobi_params<T>(h, b.jp);
+  auto params = [&](const SvdBin<T>& b, const JacobiPlan& jp) {
+    JacobiParams<T> J = jacobi_params<T>(h, jp);
     J.desc = b.desc;
     J.m = b.m;
     J.n = b.n;
     J.W = b.W;
-    J.W_bs = (int64_t)(b.jp.mm + b.jp.rc) * b.jp.rc;
-    SMA_K(jacobi_svd<T>(J, b.count, b.jp.threads, b.jp.smem, h->st));
+    J.W_bs = (int64_t)(jp.mm + jp.rc) * jp.rc;
+    return J;
+  };
+  if (h->opt.autotune && !h->capturing) {
+    std::vector<int*> sw;
+    for (auto& P : probs<T>(h)) sw.push_back(P.status);
+    for (auto& b : bins<T>(h))
+      if (!b.tuned) {
+        SMA_TRY(tune_plan<T>(h, params(b, b.jp), b.count, b.m, b.n, b.jp, sw));
+        b.tuned = true;
+      }
   }
+  stage_begin(h, SMA_STAGE_SVD);
+  for (auto& b : bins<T>(h)) SMA_K(jacobi_svd<T>(params(b, b.jp), b.count, b.jp.threads, b.jp.smem, h->st));
   stage_end(h);
   return SMA_OK;
 }
@@ -1740,6 +1831,7 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   if (opt->layout != SMA_INPUT_DENSE && opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
   if (opt->fixed_rank < 0 || !(opt->rel_tol >= 0.0)) return SMA_ERR_ARG;
   if ((int)opt->precondition < 0 || opt->precondition > SMA_PRECOND_QRCP) return SMA_ERR_ARG;
+  if (opt->autotune < 0 || opt->autotune > 1) return SMA_ERR_ARG;
   // host-side validation of every problem before any CUDA call
   for (int i = 0; i < nprob; ++i) {
     std::vector<int64_t> eta;

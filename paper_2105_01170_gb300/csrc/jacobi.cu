@@ -28,6 +28,8 @@
 //   zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 //   c = 1/sqrt(1+t^2), s = c t, w_a' = c w_a - s w_b, w_b' = s w_a + c w_b,
 // applied when |gamma| > tol sqrt(alpha beta); the caller sets tol (4 sqrt(mm) eps(T)).
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -1003,7 +1005,7 @@ __global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel
 }  // namespace
 
 template <typename T>
-JacobiPlan jacobi_plan(int m, int n, int max_smem) {
+JacobiPlan jacobi_plan_impl(int m, int n, int max_smem, bool allow_tile) {
   JacobiPlan pl;
   // leave room for the kernel's static shared memory
   max_smem = max_smem > 3072 ? max_smem - 3072 : 0;
@@ -1029,8 +1031,9 @@ JacobiPlan jacobi_plan(int m, int n, int max_smem) {
   }
   // register-tiled sweeps: fp32 float4 rows, dot-product part <= 256 rows,
   // enough tiles of 4 columns to keep 12 warps busy
-  pl.tile = (sizeof(T) == 4 && pl.vec == 4 && pl.mm <= 256 && pl.rc >= 32) ? (pl.mm <= 128 ? 1 : 2)
-                                                                           : 0;
+  pl.tile = (allow_tile && sizeof(T) == 4 && pl.vec == 4 && pl.mm <= 256 && pl.rc >= 32)
+                ? (pl.mm <= 128 ? 1 : 2)
+                : 0;
   if (pl.tile) {
     // one warp per tile-pair task of a round, at most kTileWarps
     constexpr int kTileWarps = kMaxTileWarps;
@@ -1077,6 +1080,43 @@ JacobiPlan jacobi_plan(int m, int n, int max_smem) {
 }
 
 template <typename T>
+JacobiPlan jacobi_plan(int m, int n, int max_smem) {
+  return jacobi_plan_impl<T>(m, n, max_smem, true);
+}
+
+// Alternatives to the default plan for the autotuner, all with the default's
+// storage mode (whole slice in shared memory or block mode), so one
+// workspace serves them: the untiled form where the default is tiled, and
+// for tiled block mode 4 columns more or fewer per block and 11 or 12 warps.
+template <typename T>
+std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem) {
+  std::vector<JacobiPlan> out;
+  const JacobiPlan base = jacobi_plan<T>(m, n, max_smem);
+  out.push_back(base);
+  if (base.tile) {
+    const JacobiPlan u = jacobi_plan_impl<T>(m, n, max_smem, false);
+    if (u.block_mode == base.block_mode) out.push_back(u);
+  }
+  if (base.tile && base.block_mode) {
+    const int cap = (max_smem > 3072 ? max_smem - 3072 : 0);
+    const size_t sort_bytes = (size_t)base.sort_n * (sizeof(double) + sizeof(int)) + 16;
+    const size_t col_bytes = (size_t)base.ldS * sizeof(T);
+    for (int d : {-4, 4}) {
+      JacobiPlan v = base;
+      v.bcols = base.bcols + d;
+      v.smem = 2 * (size_t)v.bcols * col_bytes + sort_bytes;
+      if (v.bcols >= 8 && v.bcols <= 48 && v.smem <= (size_t)cap && base.rc > 2 * v.bcols &&
+          (base.rc + v.bcols - 1) / v.bcols >= 3)
+        out.push_back(v);
+    }
+    JacobiPlan w = base;
+    w.threads = base.threads == 384 ? 352 : 384;
+    out.push_back(w);
+  }
+  return out;
+}
+
+template <typename T>
 cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_t smem,
                        cudaStream_t st) {
   if (nslices <= 0) return cudaSuccess;
@@ -1096,6 +1136,8 @@ cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_
 
 template JacobiPlan jacobi_plan<float>(int, int, int);
 template JacobiPlan jacobi_plan<double>(int, int, int);
+template std::vector<JacobiPlan> jacobi_plan_candidates<float>(int, int, int);
+template std::vector<JacobiPlan> jacobi_plan_candidates<double>(int, int, int);
 template cudaError_t jacobi_svd<float>(const JacobiParams<float>&, int, int, size_t, cudaStream_t);
 template cudaError_t jacobi_svd<double>(const JacobiParams<double>&, int, int, size_t, cudaStream_t);
 

@@ -1,5 +1,7 @@
 // Kernel parameter blocks and launchers of the sma path (host side).
 #pragma once
+#include <vector>
+
 #include "common.cuh"
 
 namespace sma {
@@ -54,6 +56,8 @@ struct JacobiPlan {
   size_t smem;
 };
 template <typename T> JacobiPlan jacobi_plan(int m, int n, int max_smem);
+// The default plan and the autotuner's alternatives to it (same storage mode).
+template <typename T> std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem);
 template <typename T>
 cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_t smem,
                        cudaStream_t st);

@@ -44,7 +44,7 @@ def _create(problems, **kw):
     opt = S.sma_options(kw.get("prec", S.SMA_FP64), kw.get("decomp", S.SMA_TSVDM),
                         kw.get("mkind", S.SMA_M_DCT2), kw.get("layout", S.SMA_INPUT_DENSE),
                         None, kw.get("fixed_rank", 0), kw.get("rel_tol", 1e-6), 0, None, 0, 0,
-                        kw.get("precondition", S.SMA_PRECOND_AUTO))
+                        kw.get("precondition", S.SMA_PRECOND_AUTO), kw.get("autotune", 0))
     structs, keep = [], []
     for ell, q, m, n, p, bm in problems:
         b = np.ascontiguousarray(np.asarray(bm, dtype=np.int32).ravel(order="F"))
@@ -78,6 +78,7 @@ def test_rejects_bad_sizes_and_options(lib):
     assert _create([(3, 3, 2, 2, 5, bm)], prec=7)[0] == S.SMA_ERR_ARG
     assert _create([(3, 3, 2, 2, 5, bm)], precondition=3)[0] == S.SMA_ERR_ARG
     assert _create([(3, 3, 2, 2, 5, bm)], precondition=-1)[0] == S.SMA_ERR_ARG
+    assert _create([(3, 3, 2, 2, 5, bm)], autotune=2)[0] == S.SMA_ERR_ARG
     assert S.sma_create([], S.sma_options())[0] == S.SMA_ERR_ARG
 
 

@@ -30,12 +30,13 @@ def batch(count=8):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
-def test_batched_tsvdm_matches_oracle(prec):
+@pytest.mark.parametrize("tune", [False, True], ids=["default_plan", "autotuned"])
+def test_batched_tsvdm_matches_oracle(prec, tune):
     prs = batch()
     assert len({pr.m for pr in prs}) >= 3
     tol = 1e-3
     As = [input_matrix(pr, prec) for pr in prs]
-    h = S.Handle(prs, prec=prec, rel_tol=tol)
+    h = S.Handle(prs, prec=prec, rel_tol=tol, autotune=tune)
     res = h.compress([to_dev(A) for A in As])
     for i, (pr, A) in enumerate(zip(prs, As)):
         X = O.T_E(np.asarray(A, dtype=np.float64), pr.block_map, pr.p, pr.m, pr.n)

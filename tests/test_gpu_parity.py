@@ -292,3 +292,25 @@ def test_rowcol_tucker_blr(prec):
     assert rel(apply(h, pr, x, prec), Ao @ x) < tol_for(prec) * 10
     floor = (1e-13 if prec == S.SMA_FP64 else TOL_MIXED) * np.linalg.norm(X)
     assert abs(res["tensor_err"] - t.err) <= 1e-6 * t.err + floor
+
+
+@pytest.mark.parametrize("kind", ["block_mode_fp32", "toeplitz_ragged", "wide_128"])
+def test_autotuned_plan_gives_the_same_compression(kind):
+    """The autotuner only changes the Jacobi plan (tile, block width, warps):
+    the retained ranks, singular values and rebuilt tensor stay those of the
+    default plan to fp32 accuracy, and a second handle reuses the choice."""
+    pr = problem(kind)
+    prec = S.SMA_MIXED
+    h0, A, r0 = run(pr, prec, rel_tol=1e-6)
+    h1, _, r1 = run(pr, prec, rel_tol=1e-6, autotune=True)
+    h2, _, r2 = run(pr, prec, rel_tol=1e-6, autotune=True)
+    rc = min(pr.m, pr.n)
+    s0, s1 = (gpu_tensor(h, S.EXPORT_SIGMA, (rc, pr.p), prec) for h in (h0, h1))
+    assert np.max(np.abs(s0 - s1)) <= 2e-5 * np.max(s0)
+    assert np.array_equal(h1.ranks(0), h2.ranks(0))
+    assert abs(r1["tensor_err"] - r0["tensor_err"]) <= 1e-4 * r0["norm"]
+    for r in (r1, r2):
+        assert r["device_status"] == 0
+    T0, T1 = (reconstruct(h, pr, prec) for h in (h0, h1))
+    assert rel(T1, T0) < TOL_MIXED
+
