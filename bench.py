@@ -190,13 +190,15 @@ def run_batch(torch, S, steps, warmup, device, stream, flush):
         np.concatenate(list(pr.blocks), axis=1).astype(np.float32))).to(device) for pr in prs]
     blocks = [b.t().contiguous().t() for b in blocks]
     h = S.Handle(prs, prec=S.SMA_MIXED, rel_tol=1e-3, layout=S.SMA_INPUT_BLOCKS,
-                 stream=stream.cuda_stream, autotune=True)
+                 stream=stream.cuda_stream, autotune=True, profile=True)
     ts = []
     with torch.cuda.stream(stream):
         for it in range(warmup + steps):
             flush.fill_(float(it))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            if it == warmup:
+                h.profile(reset=True)
             e0.record(stream)
             h.compress(blocks, want_result=False)
             e1.record(stream)
@@ -204,6 +206,7 @@ def run_batch(torch, S, steps, warmup, device, stream, flush):
             if it >= warmup:
                 ts.append(e0.elapsed_time(e1))
     res = [h.result(i) for i in range(len(prs))]
+    prof = h.profile(reset=True)
     h.close()
     del blocks
     torch.cuda.empty_cache()
@@ -214,6 +217,8 @@ def run_batch(torch, S, steps, warmup, device, stream, flush):
             "matrices": len(prs), "slices": nslices, "ms_per_compression": ms,
             "matrices_per_s": len(prs) / (ms * 1e-3), "slices_per_s": nslices / (ms * 1e-3),
             "max_rel_err": max(r["rel_err"] for r in res),
+            "stage_ms": {k: v / max(steps, 1) for k, v in prof["ms"].items()},
+            "launches_per_compression": int(prof["launches"]) // max(steps, 1),
             "device_status": int(np.bitwise_or.reduce([r["device_status"] for r in res]))}
 
 

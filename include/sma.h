@@ -113,7 +113,7 @@ typedef struct {
  * paper only needs the SVD).  SMA_PRECOND_QRCP factors each slice (or its
  * transpose) as B P = Q1 R1 by a column-pivoted Householder QR and runs the
  * one-sided Jacobi SVD on R1^T, which converges in fewer sweeps (Drmac and
- * Veselic 2008); SMA_PRECOND_AUTO does so when min(m, n) >= 64.            */
+ * Veselic 2008); SMA_PRECOND_AUTO does so when min(m, n) >= 128.           */
 typedef enum {
   SMA_PRECOND_AUTO = 0,
   SMA_PRECOND_NONE = 1,

@@ -22,8 +22,9 @@ using namespace sma;
 namespace {
 
 // SMA_PRECOND_AUTO preconditions the slice SVD by a column-pivoted QR from
-// this min(m, n) on (below it a slice's Jacobi takes few sweeps anyway)
-constexpr int kQrAutoMin = 64;
+// this min(m, n) on (below it the factorisation costs more than the sweeps
+// it saves)
+constexpr int kQrAutoMin = 128;
 
 #define SMA_CK(...)                                 \
   do {                                              \
@@ -248,6 +249,7 @@ struct sma_ctx {
   std::vector<Prob<float>> p32;
   std::vector<SvdBin<double>> bins64;
   std::vector<SvdBin<float>> bins32;
+  TruncDesc* tdesc = nullptr;   // device, one per t-SVDM problem (batched truncation)
   // CUDA graph of sma_compress (options.graph)
   std::vector<const void*> warm_ptrs, graph_ptrs;
   std::vector<int64_t> warm_lda, graph_lda;
@@ -855,16 +857,27 @@ sma_status tsvdm_svd_batched(sma_ctx* h) {
   return SMA_OK;
 }
 
+// Truncation of every problem of the handle in one launch (several problems).
 template <typename T>
-sma_status tsvdm_post(sma_ctx* h, Prob<T>& P) {
+sma_status truncate_all(sma_ctx* h) {
+  stage_begin(h, SMA_STAGE_TRUNCATE);
+  SMA_K(truncate_ranks_batched(h->tdesc, h->nprob, h->opt.rel_tol, h->opt.fixed_rank, h->st));
+  stage_end(h);
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status tsvdm_post(sma_ctx* h, Prob<T>& P, bool truncated) {
   cudaStream_t st = h->st;
   const int m = P.m, n = P.n, p = P.p, mm = P.mm, rc = P.rc;
   const int64_t mn = (int64_t)m * n;
   // truncation
-  stage_begin(h, SMA_STAGE_TRUNCATE);
-  SMA_K(truncate_ranks(P.sigma, rc, p, P.stats, h->opt.rel_tol, h->opt.fixed_rank, P.ranks, P.off,
-                        P.stats + 1, P.iscal, P.suf, st, 0));
-  stage_end(h);
+  if (!truncated) {
+    stage_begin(h, SMA_STAGE_TRUNCATE);
+    SMA_K(truncate_ranks(P.sigma, rc, p, P.stats, h->opt.rel_tol, h->opt.fixed_rank, P.ranks,
+                         P.off, P.stats + 1, P.iscal, P.suf, st, 0));
+    stage_end(h);
+  }
   if (P.qr) {
     stage_begin(h, SMA_STAGE_PRECOND);
     SMA_K(qr_finish<T>(qr_params(P), P.ranks, p, st));
@@ -1226,7 +1239,9 @@ sma_status enqueue_compress(sma_ctx* h, const void* const* A, const int64_t* lda
     } else {
       SMA_TRY(tsvdm_svd(h, ps[0]));
     }
-    for (int i = 0; i < h->nprob; ++i) SMA_TRY(tsvdm_post(h, ps[i]));
+    const bool batched = h->nprob > 1 && h->tdesc;
+    if (batched) SMA_TRY(truncate_all<T>(h));
+    for (int i = 0; i < h->nprob; ++i) SMA_TRY(tsvdm_post(h, ps[i], batched));
   }
   return SMA_OK;
 }
@@ -1794,6 +1809,12 @@ sma_status build_bins(sma_ctx* h) {
     if (b.jp.block_mode)
       SMA_TRY(h->mem.alloc(&b.W, (size_t)(b.jp.mm + b.jp.rc) * b.jp.rc * b.count));
   }
+  std::vector<TruncDesc> td;
+  for (auto& P : ps)
+    td.push_back(TruncDesc{P.sigma, P.rc, P.p, P.stats, P.ranks, P.off, P.stats + 1, P.iscal,
+                           P.suf});
+  SMA_TRY(h->mem.alloc(&h->tdesc, td.size()));
+  SMA_CK(cudaMemcpy(h->tdesc, td.data(), td.size() * sizeof(TruncDesc), cudaMemcpyHostToDevice));
   return SMA_OK;
 }
 

@@ -97,6 +97,19 @@ cudaError_t qr_finish(const QrParams<T>& P, const int* ranks, int nslices, cudaS
 // energies != 0: sigma holds energies (Gram eigenvalues) instead.
 // Writes ranks[p], off[p+1] (exclusive prefix), stats[1] = discarded energy,
 // iscal[0] = total rank, iscal[1] = #slices with rank > 0.
+// The truncation of several t-SVDM problems in one launch (one CTA each).
+struct TruncDesc {
+  const double* sigma;
+  int rc, p;
+  const double* normX2;
+  int* ranks;
+  int* off;
+  double* err2;
+  int* iscal;
+  double* suf;
+};
+cudaError_t truncate_ranks_batched(const TruncDesc* d, int nprob, double rel_tol, int fixed_rank,
+                                   cudaStream_t st);
 cudaError_t truncate_ranks(const double* sigma, int rc, int p, const double* normX2,
                            double rel_tol, int fixed_rank, int* ranks, int* off,
                            double* err2, int* iscal, double* scratch /*(rc+1)*p*/,

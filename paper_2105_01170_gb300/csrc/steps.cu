@@ -81,10 +81,10 @@ __device__ __forceinline__ int count_greater(const double* s, int rc, double v) 
   return lo;
 }
 
-__global__ void __launch_bounds__(TR_THREADS)
-truncate_kernel(const double* __restrict__ sigma, int rc, int p, const double* normX2,
-                double rel_tol, int fixed_rank, int* ranks, int* off, double* err2,
-                int* iscal, double* suf, int energies) {
+__device__ __forceinline__ void truncate_block(const double* __restrict__ sigma, int rc, int p,
+                                               const double* normX2, double rel_tol,
+                                               int fixed_rank, int* ranks, int* off, double* err2,
+                                               int* iscal, double* suf, int energies) {
   __shared__ double red[32];
   __shared__ unsigned long long s_lo, s_hi;
   const int tid = threadIdx.x;
@@ -205,6 +205,22 @@ truncate_kernel(const double* __restrict__ sigma, int rc, int p, const double* n
     iscal[0] = acc;
     iscal[1] = nz;
   }
+}
+
+__global__ void __launch_bounds__(TR_THREADS)
+truncate_kernel(const double* __restrict__ sigma, int rc, int p, const double* normX2,
+                double rel_tol, int fixed_rank, int* ranks, int* off, double* err2,
+                int* iscal, double* suf, int energies) {
+  truncate_block(sigma, rc, p, normX2, rel_tol, fixed_rank, ranks, off, err2, iscal, suf,
+                 energies);
+}
+
+// one CTA per problem
+__global__ void __launch_bounds__(TR_THREADS)
+truncate_batched_kernel(const TruncDesc* __restrict__ d, double rel_tol, int fixed_rank) {
+  const TruncDesc t = d[blockIdx.x];
+  truncate_block(t.sigma, t.rc, t.p, t.normX2, rel_tol, fixed_rank, t.ranks, t.off, t.err2,
+                 t.iscal, t.suf, 0);
 }
 
 template <typename T>
@@ -396,6 +412,13 @@ template cudaError_t residual_norm2<double>(const double*, const double*, int64_
 
 cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStream_t st) {
   finish_norm_kernel<<<1, 1024, 0, st>>>(partial, nparts, out);
+  return cudaGetLastError();
+}
+
+cudaError_t truncate_ranks_batched(const TruncDesc* d, int nprob, double rel_tol, int fixed_rank,
+                                   cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  truncate_batched_kernel<<<nprob, TR_THREADS, 0, st>>>(d, rel_tol, fixed_rank);
   return cudaGetLastError();
 }
 
