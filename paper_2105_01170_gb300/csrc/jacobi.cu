@@ -1113,6 +1113,37 @@ std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem) {
     w.threads = base.threads == 384 ? 352 : 384;
     out.push_back(w);
   }
+  // whole slice in shared memory: smaller CTAs put more slices on an SM (the
+  // round robin then takes several passes of the warps per round)
+  if (!base.block_mode) {
+    if (base.tile) {
+      for (int t : {64, 128})
+        if (t < base.threads) {
+          JacobiPlan v = base;
+          v.threads = t;
+          out.push_back(v);
+        }
+      JacobiPlan u = jacobi_plan_impl<T>(m, n, max_smem, false);
+      if (!u.block_mode && u.threads >= 64) {
+        const int nt = u.threads / 2;
+        int gp = 1;
+        const int mp = (u.rc + 1) / 2;
+        while (gp * 2 <= 32 && gp * 2 * (mp > 0 ? mp : 1) <= nt) gp <<= 1;
+        u.threads = nt;
+        u.g = gp;
+        out.push_back(u);
+      }
+    } else if (base.threads >= 64) {
+      JacobiPlan u = base;
+      const int nt = u.threads / 2;
+      int gp = 1;
+      const int mp = (u.rc + 1) / 2;
+      while (gp * 2 <= 32 && gp * 2 * (mp > 0 ? mp : 1) <= nt) gp <<= 1;
+      u.threads = nt;
+      u.g = gp;
+      out.push_back(u);
+    }
+  }
   return out;
 }
 
