@@ -107,6 +107,9 @@ struct Prob {
   int rc = 0, mm = 0;
   // common device buffers
   int* d_map = nullptr;
+  int* d_nzpos = nullptr;                   // map positions with a block (column-major)
+  int* d_nzk = nullptr;                     // their block index k
+  int nnz = 0;
   double* d_w = nullptr;                    // sqrt(eta_k)
   double* d_isq = nullptr;                  // 1/sqrt(eta_k)
   int64_t* d_rep = nullptr;
@@ -482,6 +485,21 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   SMA_TRY(mem.alloc(&P.d_isq, p));
   SMA_TRY(mem.alloc(&P.d_rep, p));
   SMA_CK(cudaMemcpy(P.d_map, P.map.data(), P.map.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  {  // the structure's nonzero positions: the Kronecker factors are written there only
+    std::vector<int> nzpos, nzk;
+    for (size_t pos = 0; pos < P.map.size(); ++pos)
+      if (P.map[pos] >= 0) {
+        nzpos.push_back((int)pos);
+        nzk.push_back(P.map[pos]);
+      }
+    P.nnz = (int)nzpos.size();
+    SMA_TRY(mem.alloc(&P.d_nzpos, nzpos.size()));
+    SMA_TRY(mem.alloc(&P.d_nzk, nzk.size()));
+    if (P.nnz > 0) {
+      SMA_CK(cudaMemcpy(P.d_nzpos, nzpos.data(), nzpos.size() * sizeof(int), cudaMemcpyHostToDevice));
+      SMA_CK(cudaMemcpy(P.d_nzk, nzk.data(), nzk.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+  }
   SMA_CK(cudaMemcpy(P.d_w, w.data(), p * sizeof(double), cudaMemcpyHostToDevice));
   SMA_CK(cudaMemcpy(P.d_isq, isq.data(), p * sizeof(double), cudaMemcpyHostToDevice));
   SMA_TRY(mem.alloc(&P.X, mnp));
@@ -545,6 +563,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     P.nterms_max = p;
     SMA_TRY(mem.alloc(&P.D, mnp));
     SMA_TRY(mem.alloc(&P.C, (size_t)P.ell * P.q * p));
+    SMA_CK(cudaMemset(P.C, 0, sizeof(T) * (size_t)P.ell * P.q * p));   // zero off the structure
   } else {
     // Tucker family: fp64 Gram and its Jacobi eigen-solve
     int gdim = 0;
@@ -571,6 +590,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
       SMA_TRY(mem.alloc(&P.F1, (size_t)p * p));        // V (p x r)
       SMA_TRY(mem.alloc(&P.D, mnp));                   // G_j slices (m x n x r)
       SMA_TRY(mem.alloc(&P.C, (size_t)P.ell * P.q * p));
+      SMA_CK(cudaMemset(P.C, 0, sizeof(T) * (size_t)P.ell * P.q * p));
       SMA_TRY(mem.alloc(&P.Gorth, (size_t)p * p));
       P.nterms_max = p;
     } else {
@@ -910,7 +930,8 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P, bool truncated) {
     SMA_K(contract<T>(h, g));
   }
   // structured Kronecker factors C_i = struct_E(M[i, :])
-  SMA_K(build_struct_terms<T>(P.d_map, P.d_isq, P.ell, P.q, P.Mt, 1, p, p, nullptr, P.C, st));
+  SMA_K(build_struct_terms_nz<T>(P.d_nzpos, P.d_nzk, P.nnz, P.d_isq, P.ell, P.q, P.Mt, 1, p, p,
+                                  nullptr, P.C, st));
   stage_end(h);
   // orthogonality of the retained columns of the Jacobi W (the slice's left
   // singular vectors, or with the QR preconditioning its right ones)
@@ -1006,7 +1027,8 @@ sma_status compress_tucker(sma_ctx* h, Prob<T>& P) {
     g.C = P.D; g.c_rs = 1; g.c_cs = mn;
     SMA_K(contract<T>(h, g));
     // C_j = struct_E(V[:, j])
-    SMA_K(build_struct_terms<T>(P.d_map, P.d_isq, P.ell, P.q, P.F1, p, 1, p, P.iscal + 2, P.C, st));
+    SMA_K(build_struct_terms_nz<T>(P.d_nzpos, P.d_nzk, P.nnz, P.d_isq, P.ell, P.q, P.F1, p, 1, p,
+                                    P.iscal + 2, P.C, st));
     // error ||X - T||_F measured directly (Lemma 1: equal to ||A - A_hat||_F)
     SMA_TRY(make_T(h, P));
     SMA_K(residual_norm2<T>(P.X, P.Tt, mn * p, P.partial, P.nparts, P.stats + 1, st));

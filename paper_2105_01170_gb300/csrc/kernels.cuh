@@ -118,6 +118,12 @@ cudaError_t truncate_ranks(const double* sigma, int rc, int p, const double* nor
 // ---- helpers of steps 3-5 ------------------------------------------------
 // C_i = struct_E(coef[i, :]) for i < nterms: C[a + ell*b + ell*q*i] =
 // coef[i*cs_i + k*cs_k] / sqrt(eta_k) with k = map(a, b) (0 if k < 0).
+// As build_struct_terms, writing only the nnz positions nzpos[] (block
+// indices nzk[]) of every term; C's other positions must already be zero.
+template <typename T>
+cudaError_t build_struct_terms_nz(const int* nzpos, const int* nzk, int nnz, const double* isq,
+                                  int ell, int q, const T* coef, int64_t cs_i, int64_t cs_k,
+                                  int nterms, const int* nterms_dev, T* C, cudaStream_t st);
 template <typename T>
 cudaError_t build_struct_terms(const int* map, const double* inv_sqrt_eta, int ell, int q,
                                const T* coef, int64_t cs_i, int64_t cs_k, int nterms,

@@ -241,6 +241,25 @@ __global__ void struct_terms_kernel(const int* __restrict__ map, const double* _
   }
 }
 
+// The same terms written only at the map's nonzero positions nzpos[e] (block
+// index k = nzk[e]); the other positions of C stay as the caller zeroed them.
+template <typename T>
+__global__ void struct_terms_nz_kernel(const int* __restrict__ nzpos, const int* __restrict__ nzk,
+                                       int nnz, const double* __restrict__ isq, int ell, int q,
+                                       const T* __restrict__ coef, int64_t cs_i, int64_t cs_k,
+                                       int nterms, const int* nterms_dev, T* __restrict__ C) {
+  const int nt = nterms_dev ? min(nterms, *nterms_dev) : nterms;
+  const int64_t per = (int64_t)ell * q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)nnz * nterms;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / nnz);
+    const int z = (int)(e - (int64_t)i * nnz);
+    const int k = nzk[z];
+    const T v = (i < nt) ? (T)((double)coef[i * cs_i + k * cs_k] * isq[k]) : T(0);
+    C[(int64_t)i * per + nzpos[z]] = v;
+  }
+}
+
 template <typename T>
 __global__ void scatter_kernel(const int* __restrict__ map, const double* __restrict__ isq,
                                int ell, int q, int m, int n, const T* __restrict__ Tt,
@@ -429,6 +448,24 @@ cudaError_t truncate_ranks(const double* sigma, int rc, int p, const double* nor
                                             off, err2, iscal, scratch, energies);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t build_struct_terms_nz(const int* nzpos, const int* nzk, int nnz, const double* isq,
+                                  int ell, int q, const T* coef, int64_t cs_i, int64_t cs_k,
+                                  int nterms, const int* nterms_dev, T* C, cudaStream_t st) {
+  const int64_t work = (int64_t)nnz * nterms;
+  if (work <= 0) return cudaSuccess;
+  struct_terms_nz_kernel<T><<<grid_for(work, 256), 256, 0, st>>>(nzpos, nzk, nnz, isq, ell, q,
+                                                                   coef, cs_i, cs_k, nterms,
+                                                                   nterms_dev, C);
+  return cudaGetLastError();
+}
+template cudaError_t build_struct_terms_nz<float>(const int*, const int*, int, const double*, int,
+                                                  int, const float*, int64_t, int64_t, int,
+                                                  const int*, float*, cudaStream_t);
+template cudaError_t build_struct_terms_nz<double>(const int*, const int*, int, const double*, int,
+                                                   int, const double*, int64_t, int64_t, int,
+                                                   const int*, double*, cudaStream_t);
 
 template <typename T>
 cudaError_t build_struct_terms(const int* map, const double* isq, int ell, int q, const T* coef,
