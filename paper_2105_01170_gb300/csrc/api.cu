@@ -210,7 +210,7 @@ struct Prob {
   int64_t Zp_K = -1;
   __nv_bfloat16* Dp = nullptr;
   size_t Dp_elems = 0;
-  // tcgen05 operands of the transform X x3 M (mixed t-SVDM, p <= 256)
+  // tcgen05 operands of the transform X x3 M (mixed t-SVDM)
   __nv_bfloat16* Xp = nullptr;             // X as [mn][Kp] planes
   __nv_bfloat16* Mp = nullptr;             // M as [p][Kp] planes
   int64_t Mkp = 0;
@@ -378,7 +378,7 @@ sma_status validate_problem(const sma_problem& pr, std::vector<int64_t>& eta,
   return SMA_OK;
 }
 
-// Mixed path: the transform runs on tcgen05 (M' = m n rows, N' = p <= 256,
+// Mixed path: the transform runs on tcgen05 (M' = m n rows, N' = p in tiles of 256,
 // K = p); M's split planes are built once here.
 template <typename T>
 sma_status setup_tc_transform(sma_ctx*, Prob<T>&) {
@@ -386,7 +386,7 @@ sma_status setup_tc_transform(sma_ctx*, Prob<T>&) {
 }
 template <>
 sma_status setup_tc_transform<float>(sma_ctx* h, Prob<float>& P) {
-  if (!h->tc_ok || P.p > 256) return SMA_OK;
+  if (!h->tc_ok || P.p > 65535) return SMA_OK;
   const int64_t Kp = tc_pad_k(P.p), mn = (int64_t)P.m * P.n;
   SMA_TRY(h->mem.alloc(&P.Xp, (size_t)3 * mn * Kp));
   SMA_TRY(h->mem.alloc(&P.Mp, (size_t)3 * P.p * Kp));

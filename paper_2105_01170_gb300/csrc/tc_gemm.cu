@@ -1,6 +1,6 @@
 // tcgen05 GEMM with 3-piece bf16 split operands (mixed path).
 //
-//   C[i * ldc + j] = sum_k A(i, k) B(j, k),   i < M, j < N <= 256,
+//   C[i * ldc + j] = sum_k A(i, k) B(j, k),   i < M, j < N,
 //
 // where A and B are fp32 matrices given as three bf16 planes each
 // (x = hi + mid + lo, hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid)),
@@ -9,7 +9,7 @@
 // are accumulated in fp32 in tensor memory, which carries the operands'
 // fp32 accuracy.
 //
-// One CTA per 128-row tile of C, all N columns: an elected thread of warp 0
+// One CTA per 128 x 256 tile of C: an elected thread of warp 0
 // streams (A plane, B plane) tile pairs with TMA (3-D tensor maps, 128B
 // swizzle) through a 4-stage mbarrier ring; an elected thread of warp 1
 // issues tcgen05.mma (M128 x N256 x K16) into tensor memory.
@@ -167,7 +167,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int nkb = args.Kp / BK;
   const int total = nkb * 6;
   const int nch = (nkb + CHUNK - 1) / CHUNK;
@@ -212,7 +212,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       uint8_t* st = tiles + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
       tma_load_3d(st, &mapA, &full[s], kb * BK, m0, kProdA[pr]);
-      tma_load_3d(st + A_BYTES, &mapB, &full[s], kb * BK, 0, kProdB[pr]);
+      tma_load_3d(st + A_BYTES, &mapB, &full[s], kb * BK, n0, kProdB[pr]);
       issued = it + 1;
     }
     // drain: the copies of the last stages must land before the CTA exits
@@ -281,14 +281,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     }
     if (!*abort_flag && grow < args.M && args.col_major) {
       // lanes hold consecutive rows: each store instruction is coalesced
-      const int c0 = hc * 128;
+      const int c0 = n0 + hc * 128;
       const int nv = args.N - c0;
       float* dst = args.C + grow + (int64_t)c0 * args.ldc;
 #pragma unroll
       for (int j = 0; j < 128; ++j)
         if (j < nv) dst[(int64_t)j * args.ldc] = acc[j];
     } else if (!*abort_flag && grow < args.M) {
-      const int c0 = hc * 128;
+      const int c0 = n0 + hc * 128;
       float* dst = args.C + (int64_t)grow * args.ldc + c0;
       const int nv = args.N - c0;
       if (nv >= 128 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
@@ -552,14 +552,15 @@ cudaError_t tc_gemm_planes(const __nv_bfloat16* A, const __nv_bfloat16* B, int M
                            int64_t Kp, float* C, int64_t ldc, int* err, cudaStream_t st,
                            bool col_major) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if (N > BN || Kp % BK != 0 || Kp <= 0) return cudaErrorInvalidValue;
+  if (Kp % BK != 0 || Kp <= 0 || (N + BN - 1) / BN > 65535) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, Kp, BM) || !make_map(&mb, B, N, Kp, BN)) return cudaErrorInvalidValue;
   const cudaError_t attr = cudaFuncSetAttribute(
       tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
   TcArgs a{M, N, (int)Kp, C, ldc, col_major ? 1 : 0, err};
-  tc_gemm_kernel<<<(M + BM - 1) / BM, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
   return cudaGetLastError();
 }
 

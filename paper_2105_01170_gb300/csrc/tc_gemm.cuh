@@ -17,7 +17,7 @@ int64_t tc_pad_k(int64_t K);
 cudaError_t tc_split_transpose(const float* src, int64_t s_rs, int64_t s_cs, int R, int K,
                                int64_t Kp, __nv_bfloat16* dst, cudaStream_t st);
 // C(i, j) = sum_k A(i,k) B(j,k) over the six split products, A given as
-// three planes [M][Kp], B as three planes [N][Kp] (N <= 256, Kp % 64 == 0,
+// three planes [M][Kp], B as three planes [N][Kp] (Kp % 64 == 0,
 // padding columns zero); C(i, j) at C[i*ldc + j], or C[i + j*ldc] when
 // col_major.  Timeouts set SMA_ERR_TIMEOUT in *err.
 cudaError_t tc_gemm_planes(const __nv_bfloat16* A, const __nv_bfloat16* B, int M, int N,

@@ -54,6 +54,9 @@ def problem(kind):
     if kind == "block_mode_fp32":          # 256 x 256 fp32 exceeds shared memory
         bm = G.toeplitz_map(2)
         return G.Problem(kind, g.standard_normal((3, 256, 256)), bm)
+    if kind == "p300":                     # more than 256 distinct blocks: N-tiled transform
+        bm = G.block_diagonal_map(300)
+        return G.Problem(kind, g.standard_normal((300, 8, 6)), bm)
     if kind == "wide_128":                 # n = 128 blocks: the matvec's staged epilogue
         bm = G.toeplitz_map(3)
         return G.Problem(kind, g.standard_normal((5, 24, 128)), bm)
@@ -83,7 +86,7 @@ def test_gather_is_exact(prec, kind):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
-@pytest.mark.parametrize("kind", ["toeplitz_ragged", "wide_trans", "planted_cfg1"])
+@pytest.mark.parametrize("kind", ["toeplitz_ragged", "wide_trans", "planted_cfg1", "p300"])
 def test_transform_matches(prec, kind):
     pr = problem(kind)
     h, A, _ = run(pr, prec, rel_tol=1e-3)
@@ -99,7 +102,7 @@ QNAME = {S.SMA_PRECOND_NONE: "plain", S.SMA_PRECOND_QRCP: "qrcp"}
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 @pytest.mark.parametrize("kind", ["toeplitz_ragged", "wide_trans", "tridiag_zero_blocks",
                                   "planted_cfg1", "single_block", "block_mode_fp64",
-                                  "block_mode_fp32", "tall_300x40"])
+                                  "block_mode_fp32", "tall_300x40", "p300"])
 @pytest.mark.parametrize("tol", [1e-2, 1e-6])
 @pytest.mark.parametrize("pre", PRECONDS, ids=QNAME.get)
 def test_tsvdm_end_to_end(prec, kind, tol, pre):
