@@ -157,6 +157,7 @@ struct Prob {
   int nterms_max = 0;
   // Tucker
   double* X64 = nullptr;                    // fp64 copy of X (Gram accumulation)
+  double* Xu = nullptr;                     // an unfolding of X64 laid out contiguously
   double* gram = nullptr;
   double* gvec = nullptr;                   // Jacobi output of the Gram (vectors)
   double* gsig = nullptr;                   // Gram eigenvalues
@@ -437,6 +438,7 @@ sma_status setup_multilevel(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   P.gstride = (size_t)gdim * gdim;
   SMA_TRY(mem.alloc(&P.X, np));
   SMA_TRY(mem.alloc(&P.X64, np));
+  SMA_TRY(mem.alloc(&P.Xu, np));
   SMA_TRY(mem.alloc(&P.Tt, np));
   SMA_TRY(mem.alloc(&P.T1, np));
   SMA_TRY(mem.alloc(&P.T2, np));
@@ -575,6 +577,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     P.gdim = gdim;
     P.gstride = (size_t)gdim * gdim;
     SMA_TRY(mem.alloc(&P.X64, mnp));
+    SMA_TRY(mem.alloc(&P.Xu, mnp));
     SMA_TRY(mem.alloc(&P.Wg, (size_t)gdim * gdim * 2));
     SMA_TRY(mem.alloc(&P.gW, (size_t)gdim * gdim));
     SMA_TRY(mem.alloc(&P.gram, (size_t)gdim * gdim * 2));
@@ -969,14 +972,14 @@ sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_
     g.C = G; g.c_rs = 1; g.c_cs = rows;
     g.nb1 = 1;
     if (nb1 > 1) {
-      // sum over batch entries (mode-1 / mode-2 unfoldings: sum_k X_k X_k^T)
-      for (int k = 0; k < nb1; ++k) {
-        GemmParams<double> gk = g;
-        gk.A = P.X64 + (int64_t)k * y_b1;
-        gk.B = P.X64 + (int64_t)k * y_b1;
-        gk.beta = (k == 0) ? 0.0 : 1.0;
-        SMA_K(gemm<double>(gk, st));
-      }
+      // sum over batch entries: lay the unfolding out contiguously (rows x
+      // K nb1) and form its Gram in one product
+      SMA_K(permute3(P.X64, y_rs, y_cs, y_b1, rows, K, nb1, P.Xu, st));
+      GemmParams<double> gu = g;
+      gu.K = K * nb1;
+      gu.A = P.Xu; gu.a_rs = 1; gu.a_cs = rows;
+      gu.B = P.Xu; gu.b_rs = rows; gu.b_cs = 1;
+      SMA_K(gemm<double>(gu, st));
     } else {
       SMA_K(gemm<double>(g, st));
     }

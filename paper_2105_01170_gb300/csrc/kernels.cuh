@@ -157,6 +157,9 @@ template <typename T>
 cudaError_t ml_scatter(const MlMaps& mp, const T* Tt, T* Ahat, int64_t ld, cudaStream_t st);
 
 // copy and precision conversion helpers
+// dst[i0 + n0 (i1 + n1 i2)] = src[i0 s0 + i1 s1 + i2 s2] (fp64)
+cudaError_t permute3(const double* src, int64_t s0, int64_t s1, int64_t s2, int n0, int n1, int n2,
+                     double* dst, cudaStream_t st);
 template <typename TD, typename TS>
 cudaError_t convert(const TS* src, TD* dst, int64_t count, cudaStream_t st);
 

@@ -316,6 +316,20 @@ __global__ void orth_kernel(const T* __restrict__ Gm, int rc, const int* __restr
   }
 }
 
+// dst[i0 + n0 (i1 + n1 i2)] = src[i0 s0 + i1 s1 + i2 s2]: an unfolding laid
+// out contiguously (one GEMM then forms its Gram instead of one per slice)
+__global__ void permute3_kernel(const double* __restrict__ src, int64_t s0, int64_t s1, int64_t s2,
+                                int n0, int n1, int n2, double* __restrict__ dst) {
+  const int64_t total = (int64_t)n0 * n1 * n2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = (int)(e % n0);
+    const int64_t r = e / n0;
+    const int i1 = (int)(r % n1), i2 = (int)(r / n1);
+    dst[e] = src[i0 * s0 + i1 * s1 + i2 * s2];
+  }
+}
+
 template <typename TD, typename TS>
 __global__ void convert_kernel(const TS* __restrict__ s, TD* __restrict__ d, int64_t count) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
@@ -493,6 +507,14 @@ cudaError_t orth_defect(const T* Gm, int rc, int p, const int* ranks, const doub
   const int use_inv = (scale && rc <= 6144) ? 1 : 0;   // reciprocals fit in 48 KB
   orth_kernel<T><<<p, 256, use_inv ? (size_t)rc * sizeof(double) : 0, st>>>(Gm, rc, ranks, scale,
                                                                              out, use_inv);
+  return cudaGetLastError();
+}
+
+cudaError_t permute3(const double* src, int64_t s0, int64_t s1, int64_t s2, int n0, int n1, int n2,
+                     double* dst, cudaStream_t st) {
+  const int64_t work = (int64_t)n0 * n1 * n2;
+  if (work <= 0) return cudaSuccess;
+  permute3_kernel<<<grid_for(work, 256), 256, 0, st>>>(src, s0, s1, s2, n0, n1, n2, dst);
   return cudaGetLastError();
 }
 
