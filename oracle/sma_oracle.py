@@ -28,7 +28,12 @@ Readings of points the paper leaves open (each also listed in the design notes):
   R5  HOSVD with t truncated modes gives each mode the budget tol^2||X||^2/t;
   R6  eq. (blockTuck) sums j = 1..r2 (the printed upper limit ell is a typo);
   R7  orthonormal DCT-II: M[k, j] = a_k cos(pi (2j+1) k / (2p)),
-      a_0 = sqrt(1/p), a_k = sqrt(2/p).
+      a_0 = sqrt(1/p), a_k = sqrt(2/p);
+  R15 Section 5.2: T_0 is the one distinct block on the whole diagonal; the
+      tolerance of the SPD-preserving form applies to the tensor of
+      A = sum_k E_k (x) L^-1 T_k L^-T; in the rearranged form printed after
+      the theorem the right factor is (I (x) L^-T P L^T), the transpose of the
+      left one (as printed, L^T P L^-T, the result would not be symmetric).
 """
 from __future__ import annotations
 
@@ -427,6 +432,67 @@ def shared_u(X: np.ndarray, rel_tol: float | None = None, rank: int | None = Non
     T = np.einsum("ai,ijk,bj->abk", U, G, U, optimize=True)
     err = float(np.linalg.norm((X - T).ravel()))
     return SharedU(U, G, s, r, err, err / math.sqrt(normX2))
+
+
+# ---------------------------------------------------------------------------
+# Section 5.2: preserving positive definiteness
+# ---------------------------------------------------------------------------
+
+@dataclass
+class SPDApprox:
+    k0: int                  # block index of the diagonal block T_0
+    L: np.ndarray            # T_0 = L L^T (lower triangular, m x m)
+    inner_map: np.ndarray    # map of A = sum_k E_k (x) A_k: T_0's positions empty, 0..p-2
+    X: np.ndarray            # tensor of A: X[:, :, k'] = sqrt(eta_k') L^-1 T_k L^-T
+    su: SharedU              # shared-U compression of X (Section 5.1)
+
+    def inner_approx(self) -> np.ndarray:
+        """M_E of the compressed tensor: the approximation of A."""
+        return M_E(self.su.tensor_approx(), self.inner_map)
+
+    def dense(self) -> np.ndarray:
+        """T_hat = (I (x) L) (I + M_E[T]) (I (x) L^T)."""
+        ell = self.inner_map.shape[0]
+        B = np.kron(np.eye(ell), self.L)
+        return B @ (np.eye(B.shape[0]) + self.inner_approx()) @ B.T
+
+
+def spd_split(block_map: np.ndarray) -> tuple[int, np.ndarray]:
+    """Section 5.2 writes T = I (x) T_0 + sum_k E_k (x) T_k: the block index k0
+    that fills the whole diagonal (and nothing else), and the map of the
+    remaining blocks renumbered 0..p-2 with T_0's positions empty."""
+    ell = block_map.shape[0]
+    diag = {int(block_map[a, a]) for a in range(ell)}
+    if len(diag) != 1 or min(diag) < 0:
+        raise ValueError("the diagonal blocks are not one distinct block")
+    k0 = diag.pop()
+    off = [(a, b) for a in range(ell) for b in range(block_map.shape[1])
+           if a != b and block_map[a, b] == k0]
+    if off:
+        raise ValueError("the diagonal block also occurs off the diagonal")
+    inner = np.where(block_map == k0, -1, np.where(block_map > k0, block_map - 1, block_map))
+    return k0, inner.astype(block_map.dtype)
+
+
+def spd_preserving(A: np.ndarray, block_map: np.ndarray, p: int, m: int,
+                   rel_tol: float | None = None, rank: int | None = None) -> SPDApprox:
+    """Section 5.2: Cholesky T_0 = L L^T of the diagonal block, A_k = L^-1 T_k
+    L^-T for the other distinct blocks, the shared-U compression of the tensor
+    of A = sum_k E_k (x) A_k (the tolerance applies to that tensor), and
+    T_hat = (I (x) L)(I + M_E[T])(I (x) L^T), which is SPD when T is."""
+    k0, inner = spd_split(block_map)
+    reps = representatives(block_map, p)
+    L = np.linalg.cholesky(block(A, *reps[k0], m, m))
+    Linv = np.linalg.solve(L, np.eye(m))
+    pin = p - 1
+    eta = multiplicities(inner, pin)
+    X = np.empty((m, m, pin))
+    for k in range(p):
+        if k == k0:
+            continue
+        kk = k - 1 if k > k0 else k
+        X[:, :, kk] = math.sqrt(eta[kk]) * (Linv @ block(A, *reps[k], m, m) @ Linv.T)
+    return SPDApprox(k0, L, inner, X, shared_u(X, rel_tol, rank))
 
 
 @dataclass

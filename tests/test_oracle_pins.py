@@ -435,3 +435,68 @@ def test_psf_weighting_and_lemma2():
     y = O.multilevel_apply(Gc, C1, C2, C3, vols)
     yd = np.stack([(Ah @ v.ravel(order="F")).reshape((K, K, K), order="F") for v in vols])
     assert rel(y, yd) < 1e-13
+
+
+# ---------------------------------------------------------------- Section 5.2 (SPD)
+
+def _spd_case():
+    pr = G.spacetime_covariance(npts=12, T=6)
+    T = pr.dense()
+    assert np.linalg.eigvalsh(T)[0] > 0          # a covariance: SPD
+    return pr, T
+
+
+def test_spd_split_of_block_toeplitz():
+    pr, _ = _spd_case()
+    k0, inner = O.spd_split(pr.block_map)
+    assert k0 == 0 and inner.max() == pr.p - 2
+    assert np.all(np.diag(inner) == -1)
+    with pytest.raises(ValueError):
+        O.spd_split(G.block_diagonal_map(3))      # distinct diagonal blocks
+
+
+def test_spd_full_rank_reproduces_T():
+    pr, T = _spd_case()
+    s = O.spd_preserving(T, pr.block_map, pr.p, pr.m, rank=pr.m)
+    assert np.linalg.norm(s.dense() - T) <= 1e-12 * np.linalg.norm(T)
+
+
+def test_spd_every_rank_positive_definite_where_spsd_form_is_singular():
+    """The theorem of Section 5.2, against Section 5.1's SPSD construction
+    (I (x) P) T (I (x) P) on T itself, which is only semidefinite for r < m."""
+    pr, T = _spd_case()
+    X = O.T_E(T, pr.block_map, pr.p, pr.m, pr.n)
+    for r in range(1, pr.m):
+        s = O.spd_preserving(T, pr.block_map, pr.p, pr.m, rank=r)
+        ev = np.linalg.eigvalsh(s.dense())
+        assert ev[0] > 1e-6 * ev[-1], (r, ev[0])
+        su = O.shared_u(X, rank=r)
+        ev2 = np.linalg.eigvalsh(O.M_E(su.tensor_approx(), pr.block_map))
+        assert abs(ev2[0]) < 1e-10 * ev2[-1], (r, ev2[0])
+
+
+def test_spd_equals_the_rearranged_form():
+    """T_hat = I (x) T_0 + (I (x) L P L^-1)(T - I (x) T_0)(I (x) L^-T P L^T),
+    P = U U^T: the identity stated after the theorem of Section 5.2, whose
+    right factor is the transpose of the left one (reading R15)."""
+    pr, T = _spd_case()
+    s = O.spd_preserving(T, pr.block_map, pr.p, pr.m, rank=3)
+    L, P = s.L, s.su.U @ s.su.U.T
+    Li = np.linalg.inv(L)
+    I = np.eye(pr.ell)
+    T0 = np.kron(I, L @ L.T)
+    alt = T0 + np.kron(I, L @ P @ Li) @ (T - T0) @ np.kron(I, Li.T @ P @ L.T)
+    assert np.linalg.norm(s.dense() - alt) <= 1e-12 * np.linalg.norm(T)
+    # the factor as printed (L^T P L^-T) does not give the construction
+    printed = T0 + np.kron(I, L @ P @ Li) @ (T - T0) @ np.kron(I, L.T @ P @ Li.T)
+    assert np.linalg.norm(s.dense() - printed) > 1e-6 * np.linalg.norm(T)
+
+
+def test_spd_inner_error_is_lemma_1():
+    pr, T = _spd_case()
+    s = O.spd_preserving(T, pr.block_map, pr.p, pr.m, rel_tol=1e-3)
+    A = O.M_E(s.X, s.inner_map)
+    e = np.linalg.norm(A - s.inner_approx())
+    assert abs(e - s.su.err) <= 1e-12 * np.linalg.norm(A)
+    assert s.su.err <= 1e-3 * np.linalg.norm(s.X) * (1 + 1e-12)
+
