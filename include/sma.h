@@ -6,7 +6,7 @@
  *   (1) determine the tuples (A_k) and (E_k)            -> sma_create
  *   (2) X := T_E[A]  (Section 3, matrix-to-tensor map)    -> sma_compress
  *   (3) compress X (t-SVDM, or the Tucker/HOSVD variants
- *       of Sections 2.4, 5.1, 6.2, 6.3, 7.4)              -> sma_compress
+ *       of Sections 2.4, 5.1, 5.2, 6.2, 6.3, 7.4)         -> sma_compress
  *   (4) A_hat := M_E[T]  (Section 3, tensor-to-matrix map)
  *       kept in factored form: sum of Kronecker products
  *       (Theorem 'tuckerkron', eq. structTucker) or block
@@ -61,7 +61,9 @@ typedef enum {
   SMA_ERR_TIMEOUT = 6,      /* a bounded device wait gave up                  */
   SMA_ERR_NONFINITE = 7,    /* NaN/Inf met in the input or a result           */
   SMA_ERR_STATE = 8,        /* call out of order (e.g. apply before compress) */
-  SMA_ERR_UNSUPPORTED = 9   /* option combination not implemented             */
+  SMA_ERR_UNSUPPORTED = 9,  /* option combination not implemented             */
+  SMA_ERR_NOT_SPD = 10      /* SMA_TUCKER_SPD: the diagonal block T_0 has a
+                               Cholesky pivot that is not positive and finite */
 } sma_status;
 
 typedef enum { SMA_FP64 = 0, SMA_MIXED = 1 } sma_precision;
@@ -83,7 +85,20 @@ typedef enum {
   /* Multilevel (Section 7): truncated HOSVD of the weighted coefficient
    * tensor of a three-level structured matrix with m = n = 1; result
    * sum_j G_j struct1(U1_j) (x) struct2(U2_j) (x) struct3(U3_j).           */
-  SMA_HOSVD_MULTILEVEL = 4
+  SMA_HOSVD_MULTILEVEL = 4,
+  /* Positive-definiteness preserving block low rank (Section 5.2) for an SPD
+   * T = I (x) T_0 + sum_k E_k (x) T_k: square blocks (m = n) and a square
+   * block map (ell = q) whose diagonal holds one distinct block T_0 that
+   * occurs nowhere else, and p >= 2.  T_0 = L L^T (Cholesky on the device,
+   * in the element type); the other blocks become A_k = L^-1 T_k L^-T with
+   * the map renumbered 0..p-2 (T_0's positions empty), and their tensor is
+   * compressed as in SMA_TUCKER_SHARED_U.  Factored result:
+   *   T_hat = (I (x) L)(I + (I (x) U) struct_E(U^T A_k U) (I (x) U^T))(I (x) L^T),
+   * symmetric positive definite at every rank.  The tolerance, norm,
+   * tensor_err and ranks in sma_result refer to the tensor of the A_k
+   * (||A - A_hat||_F by Lemma 1, A = sum_k E_k (x) A_k).  A T_0 that is
+   * not numerically SPD sets SMA_ERR_NOT_SPD in device_status (L = 0).   */
+  SMA_TUCKER_SPD = 5
 } sma_decomp;
 
 typedef enum { SMA_M_DCT2 = 0, SMA_M_IDENTITY = 1, SMA_M_USER = 2 } sma_transform;
@@ -163,7 +178,10 @@ typedef struct {
  * compression needs.  No kernel runs.  nprob >= 1 problems share the options;
  * they are compressed together by one sma_compress call (batched launches).
  * Errors: SMA_ERR_ARG (sizes <= 0, nprob < 1, bad enum, M_user NULL),
- * SMA_ERR_STRUCT (map entry outside [-1, p) or a k that never occurs),
+ * SMA_ERR_STRUCT (map entry outside [-1, p) or a k that never occurs; for
+ * SMA_TUCKER_SPD also a diagonal that is not one distinct block, a block
+ * that is on the diagonal and off it, or p < 2), SMA_ERR_ARG also for
+ * SMA_TUCKER_SPD with m != n or ell != q,
  * SMA_ERR_UNSUPPORTED, SMA_ERR_ALLOC, SMA_ERR_CUDA.  On error *h is NULL.  */
 sma_status sma_create(sma_handle* h, const sma_problem* probs, int32_t nprob,
                       const sma_options* opt);
@@ -189,13 +207,16 @@ sma_status sma_get_result(sma_handle h, int32_t i, sma_result* res);
 sma_status sma_get_ranks(sma_handle h, int32_t i, int32_t* ranks, int32_t* count);
 
 /* Dense A_hat = M_E[T] of problem i ((ell*m) x (q*n), leading dim ld) written
- * to Ahat (device or host).  Validation only: O(ell q m n) memory.          */
+ * to Ahat (device or host).  Validation only: O(ell q m n) memory.  For
+ * SMA_TUCKER_SPD this is T_hat = (I (x) L)(I + M_E[T])(I (x) L^T), built in
+ * two temporary (ell m)^2 device buffers allocated by this call.           */
 sma_status sma_reconstruct(sma_handle h, int32_t i, void* Ahat, int64_t ld);
 
 /* Y = A_hat X for nrhs right-hand sides (step 4, the factored matvec):
  * X is (q*n) x nrhs with leading dim ldx, Y is (ell*m) x nrhs with leading
  * dim ldy; each column of X is vec of an n x q matrix (Section 2.2,
- * vec(D X C^T) = (C (x) D) vec(X)).  Errors: SMA_ERR_STATE before a
+ * vec(D X C^T) = (C (x) D) vec(X)).  SMA_TUCKER_SPD applies T_hat as
+ * (I (x) L)(X' + A_hat X') with X' = (I (x) L^T) X.  Errors: SMA_ERR_STATE before a
  * successful sma_compress, SMA_ERR_ARG, SMA_ERR_ALLOC, SMA_ERR_CUDA.       */
 sma_status sma_apply(sma_handle h, int32_t i, const void* X, int64_t ldx,
                      void* Y, int64_t ldy, int32_t nrhs);
@@ -208,7 +229,9 @@ sma_status sma_apply(sma_handle h, int32_t i, const void* X, int64_t ldx,
  *   1 = Xhat (m*n*p, X x3 M)
  *   2 = sigma (p * min(m,n) doubles, per slice descending)
  *   3 = T (m*n*p, the approximation tensor, after sma_reconstruct)
- *   4 = Tucker factor of the compressed mode (rows x rank, column-major)   */
+ *   4 = Tucker factor of the compressed mode (rows x rank, column-major)
+ *   5 = SMA_TUCKER_SPD: the Cholesky factor L of T_0 (m x m, column-major,
+ *       zero above the diagonal)                                          */
 sma_status sma_export(sma_handle h, int32_t i, int32_t which, void* dst,
                       int64_t count, int64_t* avail);
 

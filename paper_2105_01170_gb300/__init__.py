@@ -26,12 +26,14 @@ LIB_PATH = os.path.join(_HERE, "libsma.so")
 # enums (include/sma.h)
 SMA_OK, SMA_ERR_ARG, SMA_ERR_STRUCT, SMA_ERR_CUDA, SMA_ERR_ALLOC = 0, 1, 2, 3, 4
 SMA_ERR_NOCONVERGE, SMA_ERR_TIMEOUT, SMA_ERR_NONFINITE, SMA_ERR_STATE, SMA_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
+SMA_ERR_NOT_SPD = 10
 SMA_FP64, SMA_MIXED = 0, 1
 SMA_TSVDM, SMA_TUCKER_BLOCKMODE, SMA_TUCKER_SHARED_U, SMA_TUCKER_ROWCOL, SMA_HOSVD_MULTILEVEL = 0, 1, 2, 3, 4
+SMA_TUCKER_SPD = 5
 SMA_M_DCT2, SMA_M_IDENTITY, SMA_M_USER = 0, 1, 2
 SMA_INPUT_DENSE, SMA_INPUT_BLOCKS = 0, 1
 SMA_PRECOND_AUTO, SMA_PRECOND_NONE, SMA_PRECOND_QRCP = 0, 1, 2
-EXPORT_X, EXPORT_XHAT, EXPORT_SIGMA, EXPORT_T, EXPORT_FACTOR = 0, 1, 2, 3, 4
+EXPORT_X, EXPORT_XHAT, EXPORT_SIGMA, EXPORT_T, EXPORT_FACTOR, EXPORT_CHOL = 0, 1, 2, 3, 4, 5
 
 EXPORTED = ("sma_create", "sma_compress", "sma_get_result", "sma_get_ranks", "sma_reconstruct",
             "sma_apply", "sma_export", "sma_profile", "sma_slice_svd_noalloc", "sma_destroy",

@@ -225,6 +225,18 @@ struct Prob {
   __nv_bfloat16* Cq = nullptr;
   size_t Cq_elems = 0;
   bool cq_valid = false;
+  // Section 5.2 (SMA_TUCKER_SPD): T_0 = L L^T is split off the diagonal and
+  // every field above describes the inner problem of the A_k = L^-1 T_k L^-T
+  bool spd = false;
+  int k0 = -1;                              // T_0's block index in the caller's numbering
+  int psrc = 0;                             // distinct blocks in the caller's input
+  T* T0 = nullptr;                          // m x m
+  T* Lc = nullptr;                          // L, m x m lower triangular
+  T* Linv = nullptr;                        // L^-1, m x m
+  T* Sx = nullptr;                          // apply workspace (I (x) L^T) X
+  size_t Sx_elems = 0;
+  T* Sy = nullptr;                          // apply workspace, inner product plus X'
+  size_t Sy_elems = 0;
   bool compressed = false;
   // host copies of results
   int h_iscal[8] = {0};
@@ -381,6 +393,28 @@ sma_status validate_problem(const sma_problem& pr, std::vector<int64_t>& eta,
 
 // Mixed path: the transform runs on tcgen05 (M' = m n rows, N' = p in tiles of 256,
 // K = p); M's split planes are built once here.
+// Section 5.2 writes an SPD block matrix as T = I (x) T_0 + sum_k E_k (x) T_k:
+// k0 is the block index that fills the diagonal (and occurs nowhere else),
+// inner the map of the remaining blocks renumbered 0..p-2 with T_0's
+// positions empty.  The map must already have passed validate_problem.
+sma_status spd_split(const sma_problem& pr, int* k0, std::vector<int32_t>& inner) {
+  if (pr.m != pr.n || pr.ell != pr.q) return SMA_ERR_ARG;
+  if (pr.p < 2) return SMA_ERR_STRUCT;
+  const int ell = pr.ell;
+  const int32_t* map = pr.block_map;
+  const int32_t d = map[0];
+  if (d < 0) return SMA_ERR_STRUCT;
+  inner.assign((size_t)ell * ell, -1);
+  for (int b = 0; b < ell; ++b)
+    for (int a = 0; a < ell; ++a) {
+      const int32_t v = map[a + (size_t)b * ell];
+      if ((a == b) != (v == d)) return SMA_ERR_STRUCT;
+      inner[a + (size_t)b * ell] = v == d ? -1 : (v > d ? v - 1 : v);
+    }
+  *k0 = d;
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status setup_tc_transform(sma_ctx*, Prob<T>&) {
   return SMA_OK;
@@ -472,9 +506,19 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   auto& mem = h->mem;
   const sma_options& o = h->opt;
   if (o.decomp == SMA_HOSVD_MULTILEVEL) return setup_multilevel(h, P, pr);
-  SMA_TRY(validate_problem(pr, P.eta, P.rep_a, P.rep_b));
-  P.ell = pr.ell; P.q = pr.q; P.m = pr.m; P.n = pr.n; P.p = pr.p;
-  P.map.assign(pr.block_map, pr.block_map + (size_t)pr.ell * pr.q);
+  sma_problem pin = pr;
+  std::vector<int32_t> inner;
+  if (o.decomp == SMA_TUCKER_SPD) {
+    SMA_TRY(validate_problem(pr, P.eta, P.rep_a, P.rep_b));
+    SMA_TRY(spd_split(pr, &P.k0, inner));
+    pin.block_map = inner.data();
+    pin.p = pr.p - 1;
+    P.spd = true;
+  }
+  P.psrc = pr.p;
+  SMA_TRY(validate_problem(pin, P.eta, P.rep_a, P.rep_b));
+  P.ell = pin.ell; P.q = pin.q; P.m = pin.m; P.n = pin.n; P.p = pin.p;
+  P.map.assign(pin.block_map, pin.block_map + (size_t)pin.ell * pin.q);
   const int m = P.m, n = P.n, p = P.p;
   const size_t mnp = (size_t)m * n * p;
   std::vector<double> w(p), isq(p);
@@ -570,10 +614,11 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     // Tucker family: fp64 Gram and its Jacobi eigen-solve
     int gdim = 0;
     if (o.decomp == SMA_TUCKER_BLOCKMODE) gdim = p;
-    else if (o.decomp == SMA_TUCKER_SHARED_U) gdim = m;
+    else if (o.decomp == SMA_TUCKER_SHARED_U || o.decomp == SMA_TUCKER_SPD) gdim = m;
     else if (o.decomp == SMA_TUCKER_ROWCOL) gdim = (m > n ? m : n);
     else return SMA_ERR_UNSUPPORTED;
-    if (o.decomp == SMA_TUCKER_SHARED_U && m != n) return SMA_ERR_ARG;
+    if ((o.decomp == SMA_TUCKER_SHARED_U || o.decomp == SMA_TUCKER_SPD) && m != n)
+      return SMA_ERR_ARG;
     P.gdim = gdim;
     P.gstride = (size_t)gdim * gdim;
     SMA_TRY(mem.alloc(&P.X64, mnp));
@@ -598,13 +643,18 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
       P.nterms_max = p;
     } else {
       P.r1max = m;
-      P.r3max = (o.decomp == SMA_TUCKER_SHARED_U) ? m : n;
+      P.r3max = (o.decomp == SMA_TUCKER_SHARED_U || o.decomp == SMA_TUCKER_SPD) ? m : n;
       SMA_TRY(mem.alloc(&P.F1, (size_t)m * m));
       SMA_TRY(mem.alloc(&P.F2, (size_t)n * n));
       SMA_TRY(mem.alloc(&P.core, (size_t)P.r1max * P.r3max * p));
       SMA_TRY(mem.alloc(&P.tmp, (size_t)(m > n ? m : n) * (m > n ? m : n) * p));
       SMA_TRY(mem.alloc(&P.mid, (size_t)P.ell * P.r1max * P.q * P.r3max));
       SMA_TRY(mem.alloc(&P.Gorth, (size_t)(m > n ? m : n) * (m > n ? m : n)));
+    }
+    if (P.spd) {
+      SMA_TRY(mem.alloc(&P.T0, (size_t)m * m));
+      SMA_TRY(mem.alloc(&P.Lc, (size_t)m * m));
+      SMA_TRY(mem.alloc(&P.Linv, (size_t)m * m));
     }
   }
   return SMA_OK;
@@ -627,9 +677,17 @@ sma_status do_gather(sma_ctx* h, Prob<T>& P, const void* Ain, int64_t lda) {
   stage_begin(h, SMA_STAGE_GATHER);
   int64_t use_lda = lda;
   int layout = dense ? 0 : 1;
+  if (P.spd) {
+    // the diagonal block T_0: block (0, 0) of the matrix, or block k0 of the list
+    const T* src = A + (dense ? 0 : (int64_t)P.k0 * n * lda);
+    SMA_CK(cudaMemcpy2DAsync(P.T0, m * sizeof(T), src, lda * sizeof(T), m * sizeof(T), n,
+                             is_device_ptr(Ain) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             st));
+  }
   if (!is_device_ptr(Ain)) {
-    // host input: copy only the p representative blocks to a staging buffer
-    if (!P.stage) SMA_TRY(h->mem.alloc(&P.stage, (size_t)m * n * p));
+    // host input: copy only the representative blocks to a staging buffer
+    // (the block list keeps the caller's numbering, T_0 included)
+    if (!P.stage) SMA_TRY(h->mem.alloc(&P.stage, (size_t)m * n * (dense ? p : P.psrc)));
     if (dense) {
       for (int k = 0; k < p; ++k) {
         const T* src = A + (int64_t)P.rep_a[k] * m + (int64_t)P.rep_b[k] * n * lda;
@@ -638,7 +696,7 @@ sma_status do_gather(sma_ctx* h, Prob<T>& P, const void* Ain, int64_t lda) {
       }
     } else {
       SMA_CK(cudaMemcpy2DAsync(P.stage, m * sizeof(T), A, lda * sizeof(T), m * sizeof(T),
-                               (size_t)n * p, cudaMemcpyHostToDevice, st));
+                               (size_t)n * P.psrc, cudaMemcpyHostToDevice, st));
     }
     A = P.stage;
     use_lda = m;
@@ -646,9 +704,12 @@ sma_status do_gather(sma_ctx* h, Prob<T>& P, const void* Ain, int64_t lda) {
   }
   if (P.rep_lda != use_lda || P.rep_layout != layout) {
     std::vector<int64_t> off(p);
-    for (int k = 0; k < p; ++k)
+    for (int k = 0; k < p; ++k) {
+      // a caller's block list (not a staged copy of a dense input) also holds T_0
+      const int ks = k + (P.spd && !dense && k >= P.k0 ? 1 : 0);
       off[k] = layout == 0 ? (int64_t)P.rep_a[k] * m + (int64_t)P.rep_b[k] * n * use_lda
-                           : (int64_t)k * n * use_lda;
+                           : (int64_t)ks * n * use_lda;
+    }
     SMA_CK(cudaMemcpyAsync(P.d_rep, off.data(), p * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     SMA_CK(cudaStreamSynchronize(st));  // off[] is a stack buffer
     P.rep_lda = use_lda;
@@ -1184,6 +1245,37 @@ sma_status compress_multilevel(sma_ctx* h, Prob<T>& P, const void* Ain) {
   return SMA_OK;
 }
 
+// Section 5.2: T_0 = L L^T and L^-1 on the device, then the gathered tensor
+// (X_k = sqrt(eta_k) T_k) becomes X_k = sqrt(eta_k) L^-1 T_k L^-T by two
+// batched products, and ||X||_F is taken again.
+template <typename T>
+sma_status spd_congruence(sma_ctx* h, Prob<T>& P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, p = P.p;
+  const int64_t mm = (int64_t)m * m;
+  stage_begin(h, SMA_STAGE_TRANSFORM);
+  SMA_K(chol_inv<T>(P.T0, m, m, P.Lc, P.Linv, P.status, st));
+  // tmp_k = L^-1 X_k
+  GemmParams<T> g;
+  g.M = m; g.N = m; g.K = m;
+  g.A = P.Linv; g.a_rs = 1; g.a_cs = m;
+  g.B = P.X; g.b_rs = 1; g.b_cs = m; g.b_b1 = mm;
+  g.C = P.tmp; g.c_rs = 1; g.c_cs = m; g.c_b1 = mm;
+  g.nb1 = p;
+  SMA_K(contract<T>(h, g));
+  // X_k = tmp_k L^-T
+  GemmParams<T> g2;
+  g2.M = m; g2.N = m; g2.K = m;
+  g2.A = P.tmp; g2.a_rs = 1; g2.a_cs = m; g2.a_b1 = mm;
+  g2.B = P.Linv; g2.b_rs = m; g2.b_cs = 1;
+  g2.C = P.X; g2.c_rs = 1; g2.c_cs = m; g2.c_b1 = mm;
+  g2.nb1 = p;
+  SMA_K(contract<T>(h, g2));
+  SMA_K(residual_norm2<T>(P.X, nullptr, mm * p, P.partial, P.nparts, P.stats, st));
+  stage_end(h);
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
   SMA_CK(cudaMemsetAsync(P.status, 0, sizeof(int), h->st));
@@ -1195,6 +1287,7 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
     return SMA_OK;
   }
   SMA_TRY(do_gather(h, P, A, lda));
+  if (P.spd) SMA_TRY(spd_congruence(h, P));
   if (h->opt.decomp == SMA_TSVDM) SMA_TRY(tsvdm_pre(h, P));
   else SMA_TRY(compress_tucker(h, P));
   P.compressed = true;
@@ -1342,7 +1435,9 @@ sma_status compress_all(sma_ctx* h, const void* const* A, const int64_t* lda, sm
     for (int i = 0; i < h->nprob; ++i) {
       SMA_TRY(read_result(h, ps[i], &res[i]));
       const int ds = res[i].device_status;
-      if (ds & SMA_STATUS_BIT(SMA_ERR_NONFINITE)) worst = SMA_ERR_NONFINITE;
+      if (ds & SMA_STATUS_BIT(SMA_ERR_NOT_SPD)) worst = SMA_ERR_NOT_SPD;
+      else if ((ds & SMA_STATUS_BIT(SMA_ERR_NONFINITE)) && worst != SMA_ERR_NOT_SPD)
+        worst = SMA_ERR_NONFINITE;
       else if ((ds & SMA_STATUS_BIT(SMA_ERR_NOCONVERGE)) && worst == SMA_OK) worst = SMA_ERR_NOCONVERGE;
     }
     return worst;
@@ -1521,6 +1616,13 @@ sma_status apply_multilevel(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* 
 }
 
 template <typename T>
+sma_status apply_core(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, int64_t ldyd,
+                      int nrhs);
+template <typename T>
+sma_status spd_apply(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, int64_t ldyd,
+                     int nrhs);
+
+template <typename T>
 sma_status apply_one(sma_ctx* h, Prob<T>& P, const void* Xin, int64_t ldx, void* Yout,
                      int64_t ldy, int nrhs) {
   if (!P.compressed) return SMA_ERR_STATE;
@@ -1546,8 +1648,27 @@ sma_status apply_one(sma_ctx* h, Prob<T>& P, const void* Xin, int64_t ldx, void*
     Yd = P.Ys;
     ldyd = yrows;
   }
-  const sma_decomp d = h->opt.decomp;
   stage_begin(h, SMA_STAGE_APPLY);
+  if (P.spd) SMA_TRY(spd_apply(h, P, X, ldx, Yd, ldyd, nrhs));
+  else SMA_TRY(apply_core(h, P, X, ldx, Yd, ldyd, nrhs));
+  stage_end(h);
+  if (yhost) {
+    SMA_CK(cudaMemcpy2DAsync(Y, ldy * sizeof(T), Yd, yrows * sizeof(T), yrows * sizeof(T), nrhs,
+                             cudaMemcpyDeviceToHost, st));
+    SMA_CK(cudaStreamSynchronize(st));
+  }
+  return SMA_OK;
+}
+
+// Step 4 on device buffers: Y (ell m x nrhs, ld ldyd) = A_hat X (q n x nrhs,
+// ld ldx) in the problem's factored form.
+template <typename T>
+sma_status apply_core(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, int64_t ldyd,
+                      int nrhs) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, ell = P.ell, q = P.q;
+  const int64_t yrows = (int64_t)ell * m;
+  const sma_decomp d = h->opt.decomp;
   if (d == SMA_HOSVD_MULTILEVEL) {
     SMA_TRY(apply_multilevel(h, P, X, ldx, Yd, ldyd, nrhs));
   } else if (d == SMA_TSVDM || d == SMA_TUCKER_BLOCKMODE) {
@@ -1562,10 +1683,10 @@ sma_status apply_one(sma_ctx* h, Prob<T>& P, const void* Xin, int64_t ldx, void*
     if (nt <= 0) {
       if (ldyd == yrows) SMA_CK(cudaMemsetAsync(Yd, 0, sizeof(T) * (size_t)yrows * nrhs, st));
       else SMA_CK(cudaMemset2DAsync(Yd, ldyd * sizeof(T), 0, yrows * sizeof(T), nrhs, st));
-      goto done;
+      return SMA_OK;
     }
     const int64_t ldZ = (int64_t)n * nt;
-    if (tc_apply(h, P, X, ldx, Yd, ldyd, yrows, nrhs, nt)) goto done;
+    if (tc_apply(h, P, X, ldx, Yd, ldyd, yrows, nrhs, nt)) return SMA_OK;
     SMA_TRY(grow(h, &P.Z, &P.Z_elems, (size_t)ldZ * ell * nrhs));
     // Z[c + n j, a + ell s] = sum_b X_s[c, b] C_j[a, b]
     GemmParams<T> g;
@@ -1618,13 +1739,44 @@ sma_status apply_one(sma_ctx* h, Prob<T>& P, const void* Xin, int64_t ldx, void*
     g3.nb2 = nrhs;
     SMA_K(contract<T>(h, g3));
   }
-done:
-  stage_end(h);
-  if (yhost) {
-    SMA_CK(cudaMemcpy2DAsync(Y, ldy * sizeof(T), Yd, yrows * sizeof(T), yrows * sizeof(T), nrhs,
-                             cudaMemcpyDeviceToHost, st));
-    SMA_CK(cudaStreamSynchronize(st));
+  return SMA_OK;
+}
+
+// Section 5.2: T_hat X = (I (x) L)(X' + A_hat X') with X' = (I (x) L^T) X.
+template <typename T>
+sma_status spd_apply(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, int64_t ldyd,
+                     int nrhs) {
+  cudaStream_t st = h->st;
+  const int m = P.m, ell = P.ell;
+  const int64_t rows = (int64_t)ell * m;
+  SMA_TRY(grow(h, &P.Sx, &P.Sx_elems, (size_t)rows * nrhs));
+  SMA_TRY(grow(h, &P.Sy, &P.Sy_elems, (size_t)rows * nrhs));
+  // X'[:, b + ell s] = L^T X_s[:, b]  (one product over all columns when X is contiguous)
+  GemmParams<T> g;
+  g.M = m; g.K = m;
+  g.A = P.Lc; g.a_rs = m; g.a_cs = 1;
+  g.B = X; g.b_rs = 1; g.b_cs = m;
+  g.C = P.Sx; g.c_rs = 1; g.c_cs = m;
+  if (ldx == rows) {
+    g.N = (int)(ell * (int64_t)nrhs);
+  } else {
+    g.N = ell; g.b_b2 = ldx; g.c_b2 = rows; g.nb2 = nrhs;
   }
+  SMA_K(contract<T>(h, g));
+  SMA_TRY(apply_core(h, P, P.Sx, rows, P.Sy, rows, nrhs));
+  SMA_K(add_into<T>(P.Sx, rows, P.Sy, rows, rows, nrhs, st));
+  // Y_s[:, a] = L Y'_s[:, a]
+  GemmParams<T> g2;
+  g2.M = m; g2.K = m;
+  g2.A = P.Lc; g2.a_rs = 1; g2.a_cs = m;
+  g2.B = P.Sy; g2.b_rs = 1; g2.b_cs = m;
+  g2.C = Yd; g2.c_rs = 1; g2.c_cs = m;
+  if (ldyd == rows) {
+    g2.N = (int)(ell * (int64_t)nrhs);
+  } else {
+    g2.N = ell; g2.b_b2 = rows; g2.c_b2 = ldyd; g2.nb2 = nrhs;
+  }
+  SMA_K(contract<T>(h, g2));
   return SMA_OK;
 }
 
@@ -1703,9 +1855,70 @@ sma_status make_T(sma_ctx* h, Prob<T>& P) {
   return SMA_OK;
 }
 
+// Section 5.2: T_hat = (I (x) L)(I + M_E[T])(I (x) L^T), densely, through
+// two temporary (ell m)^2 buffers.
+template <typename T>
+sma_status spd_reconstruct(sma_ctx* h, Prob<T>& P, void* Ahat, int64_t ld) {
+  cudaStream_t st = h->st;
+  const int m = P.m, ell = P.ell;
+  const int64_t rows = (int64_t)ell * m;
+  SMA_TRY(make_T(h, P));
+  T* dst = static_cast<T*>(Ahat);
+  const bool host = !is_device_ptr(Ahat);
+  T* W = nullptr;
+  if (cudaMalloc(&W, 2 * (size_t)rows * rows * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return SMA_ERR_ALLOC;
+  }
+  T* W1 = W;
+  T* W2 = W + (size_t)rows * rows;
+  T* out = host ? W1 : dst;
+  const int64_t ldo = host ? rows : ld;
+  auto run = [&]() -> cudaError_t {
+    cudaError_t e;
+    ++h->launches;
+    if ((e = scatter_ME<T>(P.d_map, P.d_isq, ell, ell, m, m, P.Tt, W1, rows, st)) != cudaSuccess)
+      return e;
+    ++h->launches;
+    if ((e = add_identity<T>(W1, rows, rows, st)) != cudaSuccess) return e;
+    // W2 = (I (x) L) W1: block row a of W1 times L
+    GemmParams<T> g;
+    g.M = m; g.N = (int)rows; g.K = m;
+    g.A = P.Lc; g.a_rs = 1; g.a_cs = m;
+    g.B = W1; g.b_rs = 1; g.b_cs = rows; g.b_b1 = m;
+    g.C = W2; g.c_rs = 1; g.c_cs = rows; g.c_b1 = m;
+    g.nb1 = ell;
+    ++h->launches;
+    if ((e = gemm<T>(g, st)) != cudaSuccess) return e;
+    // out = W2 (I (x) L^T): block column b of W2 times L^T
+    GemmParams<T> g2;
+    g2.M = (int)rows; g2.N = m; g2.K = m;
+    g2.A = W2; g2.a_rs = 1; g2.a_cs = rows; g2.a_b1 = (int64_t)m * rows;
+    g2.B = P.Lc; g2.b_rs = m; g2.b_cs = 1;
+    g2.C = out; g2.c_rs = 1; g2.c_cs = ldo; g2.c_b1 = (int64_t)m * ldo;
+    g2.nb1 = ell;
+    ++h->launches;
+    if ((e = gemm<T>(g2, st)) != cudaSuccess) return e;
+    if (host)
+      e = cudaMemcpy2DAsync(dst, ld * sizeof(T), W1, rows * sizeof(T), rows * sizeof(T), rows,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+  };
+  const cudaError_t e = run();
+  if (e != cudaSuccess) cudaStreamSynchronize(st);
+  cudaFree(W);
+  SMA_CK(e);
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status reconstruct_one(sma_ctx* h, Prob<T>& P, void* Ahat, int64_t ld) {
   if (!P.compressed) return SMA_ERR_STATE;
+  if (P.spd) {
+    if (!Ahat || ld < (int64_t)P.ell * P.m) return SMA_ERR_ARG;
+    return spd_reconstruct(h, P, Ahat, ld);
+  }
   cudaStream_t st = h->st;
   const int m = P.m, n = P.n;
   if (!Ahat || ld < (int64_t)P.ell * m) return SMA_ERR_ARG;
@@ -1768,6 +1981,9 @@ sma_status export_one(sma_ctx* h, Prob<T>& P, int which, void* dst, int64_t coun
       else if (h->opt.decomp == SMA_TUCKER_BLOCKMODE) { src = P.F1; n = (int64_t)P.p * P.p; }
       else if (h->opt.decomp != SMA_TSVDM) { src = P.F1; n = (int64_t)P.m * P.m; }
       break;
+    case 5:
+      if (P.spd) { src = P.Lc; n = (int64_t)P.m * P.m; }
+      break;
     default: return SMA_ERR_ARG;
   }
   if (avail) *avail = n;
@@ -1789,7 +2005,8 @@ sma_status ranks_one(sma_ctx* h, Prob<T>& P, int32_t* out, int32_t* count) {
     SMA_CK(cudaMemcpy(isc, P.iscal, sizeof(isc), cudaMemcpyDeviceToHost));
     const sma_decomp d = h->opt.decomp;
     const int c = d == SMA_TUCKER_BLOCKMODE ? 1 : (d == SMA_HOSVD_MULTILEVEL ? 3 : 2);
-    for (int i = 0; i < c; ++i) out[i] = (d == SMA_TUCKER_SHARED_U) ? isc[2] : isc[2 + i];
+    const bool shared = d == SMA_TUCKER_SHARED_U || d == SMA_TUCKER_SPD;
+    for (int i = 0; i < c; ++i) out[i] = shared ? isc[2] : isc[2 + i];
     *count = c;
   }
   return SMA_OK;
@@ -1862,6 +2079,7 @@ const char* sma_status_string(sma_status s) {
     case SMA_ERR_NONFINITE: return "non-finite value";
     case SMA_ERR_STATE: return "call out of order";
     case SMA_ERR_UNSUPPORTED: return "unsupported option";
+    case SMA_ERR_NOT_SPD: return "diagonal block not positive definite";
   }
   return "unknown status";
 }
@@ -1872,7 +2090,7 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   *out = nullptr;
   if (!prob || !opt || nprob < 1) return SMA_ERR_ARG;
   if (opt->prec != SMA_FP64 && opt->prec != SMA_MIXED) return SMA_ERR_ARG;
-  if ((int)opt->decomp < 0 || opt->decomp > SMA_HOSVD_MULTILEVEL) return SMA_ERR_ARG;
+  if ((int)opt->decomp < 0 || opt->decomp > SMA_TUCKER_SPD) return SMA_ERR_ARG;
   if ((int)opt->mkind < 0 || opt->mkind > SMA_M_USER) return SMA_ERR_ARG;
   if (opt->layout != SMA_INPUT_DENSE && opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
   if (opt->fixed_rank < 0 || !(opt->rel_tol >= 0.0)) return SMA_ERR_ARG;
@@ -1890,6 +2108,11 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
     }
     SMA_TRY(validate_problem(prob[i], eta, ra, rb));
     if (opt->decomp == SMA_TUCKER_SHARED_U && prob[i].m != prob[i].n) return SMA_ERR_ARG;
+    if (opt->decomp == SMA_TUCKER_SPD) {
+      int k0 = -1;
+      std::vector<int32_t> inner;
+      SMA_TRY(spd_split(prob[i], &k0, inner));
+    }
     if (opt->decomp == SMA_TSVDM && opt->mkind == SMA_M_USER && !opt->M_user) return SMA_ERR_ARG;
   }
   std::unique_ptr<sma_ctx> h(new (std::nothrow) sma_ctx());

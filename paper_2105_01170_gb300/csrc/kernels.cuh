@@ -18,7 +18,7 @@ cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off /*device, p*
 cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStream_t st);
 int gather_parts(int m, int n, int p);
 // ||X - T||_F^2 over `count` elements (fp64 accumulation; nparts partial sums
-// as for gather); two launches.
+// as for gather); two launches.  Tt == nullptr gives ||X||_F^2.
 template <typename T>
 cudaError_t residual_norm2(const T* X, const T* Tt, int64_t count, double* partial, int nparts,
                            double* out, cudaStream_t st);
@@ -162,5 +162,20 @@ cudaError_t permute3(const double* src, int64_t s0, int64_t s1, int64_t s2, int 
                      double* dst, cudaStream_t st);
 template <typename TD, typename TS>
 cudaError_t convert(const TS* src, TD* dst, int64_t count, cudaStream_t st);
+
+// ---- Section 5.2 (SPD-preserving form) -------------------------------------
+// T_0 (m x m, ld ld0) = L L^T and L^-1, one CTA, both m x m column-major
+// (ld m); a pivot that is not positive and finite zeroes L and L^-1 and sets
+// SMA_ERR_NOT_SPD in *status.
+template <typename T>
+cudaError_t chol_inv(const T* T0, int64_t ld0, int m, T* L, T* Linv, int* status,
+                     cudaStream_t st);
+// A(i, i) += 1 for i < n.
+template <typename T>
+cudaError_t add_identity(T* A, int64_t ld, int64_t n, cudaStream_t st);
+// Y[:, s] += X[:, s], rows entries per column, s < cols.
+template <typename T>
+cudaError_t add_into(const T* X, int64_t ldx, T* Y, int64_t ldy, int64_t rows, int cols,
+                     cudaStream_t st);
 
 }  // namespace sma

@@ -45,7 +45,7 @@ residual_kernel(const T* __restrict__ X, const T* __restrict__ Tt, int64_t count
   double acc = 0.0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const double d = (double)X[e] - (double)Tt[e];
+    const double d = Tt ? (double)X[e] - (double)Tt[e] : (double)X[e];
     acc = fma(d, d, acc);
   }
   acc = block_sum(acc, red);

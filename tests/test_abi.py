@@ -82,6 +82,22 @@ def test_rejects_bad_sizes_and_options(lib):
     assert S.sma_create([], S.sma_options())[0] == S.SMA_ERR_ARG
 
 
+def test_spd_split_is_validated_before_any_device_call(lib):
+    """Section 5.2 needs T = I (x) T_0 + sum_k E_k (x) T_k: one distinct block
+    on the whole diagonal and nowhere else, square blocks, p >= 2."""
+    spd = dict(decomp=S.SMA_TUCKER_SPD)
+    bm = G.toeplitz_map(4)                                    # lag 0 on the diagonal only
+    assert S.sma_status_string(S.SMA_ERR_NOT_SPD) == "diagonal block not positive definite"
+    assert _create([(4, 4, 3, 2, 7, bm)], **spd)[0] == S.SMA_ERR_ARG      # m != n
+    assert _create([(4, 4, 3, 3, 4, G.block_diagonal_map(4))], **spd)[0] == S.SMA_ERR_STRUCT
+    off = bm.copy()
+    off[1, 0] = off[0, 0]              # T_0 also off the diagonal (lag 1 still occurs below)
+    assert _create([(4, 4, 3, 3, 7, off)], **spd)[0] == S.SMA_ERR_STRUCT
+    one = np.where(np.eye(3, dtype=bool), 0, -1).astype(np.int32)
+    assert _create([(3, 3, 2, 2, 1, one)], **spd)[0] == S.SMA_ERR_STRUCT  # p = 1
+    assert _create([(3, 3, 2, 2, 5, G.toeplitz_map(3))], decomp=6)[0] == S.SMA_ERR_ARG
+
+
 def test_null_handle_calls(lib):
     assert S.sma_destroy(None) == S.SMA_ERR_ARG
     assert S.sma_apply(None, 0, 0, 1, 0, 1, 1) == S.SMA_ERR_ARG

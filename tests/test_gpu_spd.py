@@ -1,0 +1,214 @@
+"""Section 5.2 on the GPU: the positive-definiteness preserving form
+T_hat = (I (x) L)(I + M_E[T])(I (x) L^T), compared with the FP64 oracle's
+spd_preserving on the same (rounded) input.  Checked: the Cholesky factor,
+the congruence-transformed tensor, the retained ranks, the reported error
+(Lemma 1 on the inner tensor), the dense T_hat, its positive definiteness
+at a rank where the plain SPSD form is singular, and the factored matvec."""
+import numpy as np
+import pytest
+
+from oracle import sma_oracle as O
+from sma_inputs import generators as G
+
+from _util import gpu_tensor, np_dtype, rel, to_dev, torch_dtype
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+S = pytest.importorskip("paper_2105_01170_gb300")
+
+PRECS = [S.SMA_FP64, S.SMA_MIXED]
+PNAME = {S.SMA_FP64: "fp64", S.SMA_MIXED: "mixed"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_01170_gb300 import _build
+    _build.build()
+
+
+def tol_x(prec, s):
+    """Relative Frobenius bound on the transformed tensor L^-1 T_k L^-T: the
+    path's bar (1e-10 FP64, 1e-5 mixed), or, where the arithmetic cannot
+    reach it, the rounding of the two products, 2 eps sqrt(m) times the
+    amplification c = || |L^-1| |T_k| |L^-T| || / ||A_k|| aggregated over
+    the blocks (the cancellation the congruence undergoes)."""
+    eps = 1.1e-16 if prec == S.SMA_FP64 else 6e-8
+    Li = np.abs(np.linalg.inv(s.L))
+    num = 0.0
+    for k in range(s.X.shape[2]):
+        Tw = np.abs(s.L @ s.X[:, :, k] @ s.L.T)
+        num += float(np.sum((Li @ Tw @ Li.T) ** 2))
+    c = np.sqrt(num) / np.linalg.norm(s.X)
+    bar = 1e-10 if prec == S.SMA_FP64 else 1e-5
+    return max(bar, 2 * eps * np.sqrt(s.L.shape[0]) * c)
+
+
+def blocks_input(pr, prec):
+    """The p distinct blocks side by side (m x n p), in the path's precision."""
+    return np.concatenate(list(pr.blocks), axis=1).astype(np_dtype(prec))
+
+
+def run(pr, prec, layout, host, **kw):
+    A = pr.dense() if layout == S.SMA_INPUT_DENSE else blocks_input(pr, prec)
+    A = np.asfortranarray(A.astype(np_dtype(prec)))
+    h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_SPD, layout=layout, **kw)
+    res = h.compress([A if host else to_dev(A)], check=False)[0]
+    Ad = pr.dense().astype(np_dtype(prec)).astype(np.float64)
+    return h, Ad, res
+
+
+def shared_rank_margin(sigma, r, rel_tol, normX2):
+    """Slack of the shared-U rank decision (budget tol^2 ||X||^2 / 2 on the
+    discarded mode-1 energies), relative to the budget."""
+    e = np.asarray(sigma, dtype=np.float64) ** 2
+    budget = rel_tol * rel_tol * normX2 / 2.0
+    tail = lambda k: float(np.sum(e[k:]))
+    up = budget - tail(r)
+    down = tail(r - 1) - budget if r > 0 else np.inf
+    return min(up, down) / budget
+
+
+def dense_that(h, pr, prec):
+    rows = pr.ell * pr.m
+    Ah = torch.empty(rows, rows, dtype=torch_dtype(prec), device="cuda").t()
+    h.reconstruct(0, Ah)
+    return Ah.cpu().numpy().astype(np.float64)
+
+
+CASES = {
+    # (points, time lags): m = points, ell = lags, p = 2 lags - 1
+    "small": (12, 6),
+    "mid": (48, 10),
+}
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("layout,host", [(S.SMA_INPUT_DENSE, False), (S.SMA_INPUT_BLOCKS, False),
+                                         (S.SMA_INPUT_BLOCKS, True), (S.SMA_INPUT_DENSE, True)],
+                         ids=["dense_dev", "blocks_dev", "blocks_host", "dense_host"])
+def test_spd_fixed_rank_matches_oracle(prec, case, layout, host):
+    npts, T = CASES[case]
+    pr = G.spacetime_covariance(npts=npts, T=T, seed_index=1)
+    r = 3
+    h, A, res = run(pr, prec, layout, host, fixed_rank=r)
+    assert res["device_status"] == 0
+    s = O.spd_preserving(A, pr.block_map, pr.p, pr.m, rank=r)
+    tx = tol_x(prec, s)
+    # the Cholesky factor and the transformed tensor
+    L = gpu_tensor(h, S.EXPORT_CHOL, (pr.m, pr.m), prec)
+    assert np.array_equal(np.triu(L, 1), np.zeros_like(L))
+    assert rel(L, s.L) < tx
+    X = gpu_tensor(h, S.EXPORT_X, s.X.shape, prec)
+    assert rel(X, s.X) < tx
+    assert list(h.ranks(0)) == [r, r]
+    assert abs(res["norm"] - np.linalg.norm(s.X)) <= tx * np.linalg.norm(s.X)
+    assert abs(res["tensor_err"] - s.su.err) <= 10 * tx * np.linalg.norm(s.X)
+    # T_hat, densely, and its positive definiteness
+    Th = dense_that(h, pr, prec)
+    To = s.dense()
+    assert rel(Th, To) < 10 * tx
+    ev = np.linalg.eigvalsh((Th + Th.T) / 2)
+    ev_o = np.linalg.eigvalsh(To)
+    assert ev.min() > 0.5 * ev_o.min() > 0
+    # the matvec against the dense oracle form, device and host buffers
+    x = G.random_rhs(pr.ell * pr.m, 5, 7).astype(np_dtype(prec))
+    Y = torch.empty(5, pr.ell * pr.m, dtype=torch_dtype(prec), device="cuda").t()
+    h.apply(0, to_dev(x), Y)
+    yo = To @ x.astype(np.float64)
+    assert rel(Y.cpu().numpy(), yo) < 10 * tx
+    Yh = np.zeros((pr.ell * pr.m, 5), dtype=np_dtype(prec), order="F")
+    h.apply(0, np.asfortranarray(x), Yh)
+    assert rel(Yh, yo) < 10 * tx
+    h.close()
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_spd_tolerance_rank_and_lemma_1(prec):
+    pr = G.spacetime_covariance(npts=48, T=10, seed_index=1)
+    tol = 1e-3
+    h, A, res = run(pr, prec, S.SMA_INPUT_DENSE, False, rel_tol=tol)
+    s = O.spd_preserving(A, pr.block_map, pr.p, pr.m, rel_tol=tol)
+    normX2 = float(np.sum(s.X ** 2))
+    margin = shared_rank_margin(s.su.sigma, s.su.rank, tol, normX2)
+    if margin > 1e-3:
+        assert list(h.ranks(0)) == [s.su.rank, s.su.rank]
+    # the reported error is the inner tensor's, within the budget
+    assert res["tensor_err"] <= tol * res["norm"] * (1 + 1e-6)
+    # Lemma 1 on the inner matrix: recover A_hat = B^-1 T_hat B^-T - I with
+    # the device's own L (B = I (x) L) and compare ||A - A_hat||_F with the
+    # reported tensor error
+    Lg = gpu_tensor(h, S.EXPORT_CHOL, (pr.m, pr.m), prec)
+    Bg = np.kron(np.eye(pr.ell), Lg)
+    Th = dense_that(h, pr, prec)
+    inner = np.linalg.solve(Bg, np.linalg.solve(Bg, Th).T).T - np.eye(Th.shape[0])
+    Ainner = O.M_E(s.X, s.inner_map)   # A = sum_k E_k (x) A_k
+    err = np.linalg.norm(Ainner - inner)
+    assert abs(err - res["tensor_err"]) <= 1e-3 * res["tensor_err"] + \
+        10 * tol_x(prec, s) * np.linalg.norm(Ainner)
+    h.close()
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_spd_not_positive_definite_is_reported(prec):
+    pr = G.spacetime_covariance(npts=12, T=4, seed_index=1)
+    blocks = pr.blocks.copy()
+    k0 = int(pr.block_map[0, 0])
+    blocks[k0] = -blocks[k0]          # T_0 negative definite
+    bad = G.Problem(pr.name, blocks, pr.block_map, pr.extra)
+    A = np.asfortranarray(bad.dense().astype(np_dtype(prec)))
+    h = S.Handle([bad], prec=prec, decomp=S.SMA_TUCKER_SPD, fixed_rank=2)
+    res = h.compress([to_dev(A)], check=False)[0]
+    assert h.last_status == S.SMA_ERR_NOT_SPD
+    assert res["device_status"] & (1 << S.SMA_ERR_NOT_SPD)
+    L = gpu_tensor(h, S.EXPORT_CHOL, (pr.m, pr.m), prec)
+    assert not np.any(L)
+    assert np.isfinite(res["norm"]) and np.isfinite(res["tensor_err"])
+    h.close()
+
+
+def test_spd_fullsize_covariance_fp64():
+    """256 points, 64 lags (T_0 256 x 256 with condition number about 1.6e4):
+    the transformed tensor, ranks at tolerance 1e-6, the error and a factored
+    matvec on sampled right-hand sides."""
+    pr = G.spacetime_covariance()
+    prec = S.SMA_FP64
+    tol = 1e-6
+    B = blocks_input(pr, prec)
+    h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_SPD, layout=S.SMA_INPUT_BLOCKS,
+                 rel_tol=tol)
+    res = h.compress([to_dev(B)])[0]
+    assert res["device_status"] == 0
+    # the oracle from the blocks: T_0 and the others, placed by the map
+    k0 = int(pr.block_map[0, 0])
+    m = pr.m
+    L = np.linalg.cholesky(pr.blocks[k0])
+    X_gpu = gpu_tensor(h, S.EXPORT_X, (m, m, pr.p - 1), prec)
+    s = O.spd_preserving(pr.dense(), pr.block_map, pr.p, m, rel_tol=tol)
+    assert rel(gpu_tensor(h, S.EXPORT_CHOL, (m, m), prec), L) < 1e-13
+    assert rel(X_gpu, s.X) < 1e-11
+    normX2 = float(np.sum(s.X ** 2))
+    margin = shared_rank_margin(s.su.sigma, s.su.rank, tol, normX2)
+    if margin > 1e-6:
+        assert list(h.ranks(0)) == [s.su.rank, s.su.rank]
+    assert abs(res["tensor_err"] - s.su.err) <= 1e-6 * s.su.err + 1e-12 * np.sqrt(normX2)
+    # T_hat x for 3 right-hand sides, the oracle side in factored form
+    nrhs = 3
+    x = G.random_rhs(pr.ell * m, nrhs, 11)
+    Y = torch.empty(nrhs, pr.ell * m, dtype=torch.float64, device="cuda").t()
+    h.apply(0, to_dev(x), Y)
+    eta = O.multiplicities(s.inner_map, pr.p - 1)
+    xs = x.reshape(m, pr.ell, nrhs, order="F")
+    xp = np.einsum("ji,jbs->ibs", s.L, xs)                      # (I (x) L^T) x
+    core = np.einsum("ai,ijk,bj->abk", s.su.U, s.su.G, s.su.U, optimize=True)
+    yp = xp.copy()
+    for a in range(pr.ell):
+        for b in range(pr.ell):
+            k = int(s.inner_map[a, b])
+            if k >= 0:
+                yp[:, a, :] += core[:, :, k] @ xp[:, b, :] / np.sqrt(eta[k])
+    yo = np.einsum("ij,jbs->ibs", s.L, yp).reshape(pr.ell * m, nrhs, order="F")
+    assert rel(Y.cpu().numpy(), yo) < 1e-11
+    h.close()
