@@ -24,6 +24,9 @@ namespace {
 // SMA_PRECOND_AUTO preconditions the slice SVD by a column-pivoted QR from
 // this min(m, n) on (below it the factorisation costs more than the sweeps
 // it saves)
+// Gram eigen-solves of this order and larger run over many CTAs
+// (jacobi_svd_coop); smaller ones in one CTA.
+constexpr int kCoopMinRows = 96;
 constexpr int kQrAutoMin = 128;
 
 #define SMA_CK(...)                                 \
@@ -266,6 +269,14 @@ struct sma_ctx {
   std::vector<SvdBin<double>> bins64;
   std::vector<SvdBin<float>> bins32;
   TruncDesc* tdesc = nullptr;   // device, one per t-SVDM problem (batched truncation)
+  int nsm = 0;                   // SMs of the device
+  // Tucker / HOSVD Grams: split-K partial products and the cooperative
+  // Jacobi's barrier state, shared by the problems (one stream)
+  double* gpart = nullptr;
+  size_t gpart_elems = 0;
+  unsigned* coop_bar = nullptr;
+  int* coop_rot = nullptr;
+  int* coop_abort = nullptr;
   // CUDA graph of sma_compress (options.graph)
   std::vector<const void*> warm_ptrs, graph_ptrs;
   std::vector<int64_t> warm_lda, graph_lda;
@@ -1026,21 +1037,37 @@ sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_
   double* G = P.gram + (size_t)slot * P.gstride;
   stage_begin(h, SMA_STAGE_TRANSFORM);
   {
+    // the unfolding Y (rows x Ktot): strided in X64, or laid out contiguously
+    // first when it sums over a batch index
     GemmParams<double> g;
-    g.M = rows; g.N = rows; g.K = K;
-    g.A = P.X64; g.a_rs = y_rs; g.a_cs = y_cs; g.a_b1 = y_b1;
-    g.B = P.X64; g.b_rs = y_cs; g.b_cs = y_rs; g.b_b1 = y_b1;
-    g.C = G; g.c_rs = 1; g.c_cs = rows;
-    g.nb1 = 1;
+    g.M = rows; g.N = rows;
     if (nb1 > 1) {
-      // sum over batch entries: lay the unfolding out contiguously (rows x
-      // K nb1) and form its Gram in one product
       SMA_K(permute3(P.X64, y_rs, y_cs, y_b1, rows, K, nb1, P.Xu, st));
-      GemmParams<double> gu = g;
-      gu.K = K * nb1;
-      gu.A = P.Xu; gu.a_rs = 1; gu.a_cs = rows;
-      gu.B = P.Xu; gu.b_rs = rows; gu.b_cs = 1;
-      SMA_K(gemm<double>(gu, st));
+      g.K = K * nb1;
+      g.A = P.Xu; g.a_rs = 1; g.a_cs = rows;
+      g.B = P.Xu; g.b_rs = rows; g.b_cs = 1;
+    } else {
+      g.K = K;
+      g.A = P.X64; g.a_rs = y_rs; g.a_cs = y_cs;
+      g.B = P.X64; g.b_rs = y_cs; g.b_cs = y_rs;
+    }
+    g.C = G; g.c_rs = 1; g.c_cs = rows;
+    // G = Y Y^T has few output tiles: split K so that about two CTAs per SM
+    // take part, each writing its partial product, then sum the partials in
+    // a fixed order (deterministic)
+    const int64_t tiles = (int64_t)((rows + 63) / 64) * ((rows + 63) / 64);
+    int64_t nsplit = (2 * (int64_t)h->nsm + tiles - 1) / tiles;
+    if (nsplit > g.K / 64) nsplit = g.K / 64;
+    if (nsplit > 1) {
+      const int kc = (int)(((g.K + nsplit - 1) / nsplit + 15) / 16 * 16);
+      nsplit = (g.K + kc - 1) / kc;
+    }
+    if (nsplit > 1 && (size_t)nsplit * rows * rows <= h->gpart_elems) {
+      g.kchunk = (int)(((g.K + nsplit - 1) / nsplit + 15) / 16 * 16);
+      g.nb1 = (int)nsplit;
+      g.C = h->gpart; g.c_b1 = (int64_t)rows * rows;
+      SMA_K(gemm<double>(g, st));
+      SMA_K(sum_slabs(h->gpart, (int)nsplit, (int64_t)rows * rows, G, st));
     } else {
       SMA_K(gemm<double>(g, st));
     }
@@ -1048,7 +1075,10 @@ sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_
   stage_end(h);
   stage_begin(h, SMA_STAGE_SVD);
   JacobiPlan jp = jacobi_plan<double>(rows, rows, h->max_smem);
-  double* W = jp.block_mode ? P.Wg : nullptr;
+  const JacobiPlan cp = jacobi_coop_plan<double>(rows, h->max_smem);
+  const bool coop = rows >= kCoopMinRows && cp.smem > 0 && h->coop_bar;
+  if (coop) jp = cp;
+  double* W = (jp.block_mode || coop) ? P.Wg : nullptr;
   JacobiParams<double> J;
   J.src = G; J.src_bs = 0; J.m = rows; J.n = rows;
   J.mm = jp.mm; J.rc = jp.rc; J.trans = 0; J.ldS = jp.ldS; J.bcols = jp.bcols; J.g = jp.g;
@@ -1060,7 +1090,11 @@ sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_
   J.V = P.gvec + (size_t)slot * P.gstride; J.V_bs = 0;     // eigenvectors of G
   J.sigma = P.gsig + (size_t)slot * P.gdim;
   J.sweeps = P.sweeps + slot; J.status = P.status;
-  SMA_K(jacobi_svd<double>(J, 1, jp.threads, jp.smem, st));
+  if (coop) {
+    SMA_K(jacobi_svd_coop<double>(J, cp, CoopSync{h->coop_bar, h->coop_rot, h->coop_abort}, st));
+  } else {
+    SMA_K(jacobi_svd<double>(J, 1, jp.threads, jp.smem, st));
+  }
   stage_end(h);
   stage_begin(h, SMA_STAGE_TRUNCATE);
   // the Gram's singular values are the energies sigma^2 of the unfolding
@@ -2060,6 +2094,22 @@ sma_status build_bins(sma_ctx* h) {
   return SMA_OK;
 }
 
+// Shared state of the Gram eigen-solves: the split-K partial products hold
+// nsplit * rows^2 doubles with nsplit <= 2 nsm / tiles + 1 and tiles >=
+// rows^2 / 4096, so 2 nsm 4096 + rows^2 bounds every Gram of the handle.
+static sma_status setup_gram_shared(sma_ctx* h) {
+  int gmax = 1;
+  for (auto& P : h->p64) gmax = P.gdim > gmax ? P.gdim : gmax;
+  for (auto& P : h->p32) gmax = P.gdim > gmax ? P.gdim : gmax;
+  h->gpart_elems = (size_t)2 * h->nsm * 4096 + (size_t)gmax * gmax;
+  SMA_TRY(h->mem.alloc(&h->gpart, h->gpart_elems));
+  const int sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
+  SMA_TRY(h->mem.alloc(&h->coop_bar, 1));
+  SMA_TRY(h->mem.alloc(&h->coop_rot, (size_t)sweeps));
+  SMA_TRY(h->mem.alloc(&h->coop_abort, 1));
+  return SMA_OK;
+}
+
 // ===========================================================================
 // exported C ABI
 // ===========================================================================
@@ -2128,6 +2178,7 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   SMA_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
   SMA_CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
   h->tc_ok = (opt->prec == SMA_MIXED) && tc_gemm_available(major, minor);
+  SMA_CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
   if (opt->prec == SMA_FP64) {
     h->p64.resize(nprob);
     for (int i = 0; i < nprob; ++i) SMA_TRY(setup_problem(h.get(), h->p64[i], prob[i]));
@@ -2137,6 +2188,7 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
     for (int i = 0; i < nprob; ++i) SMA_TRY(setup_problem(h.get(), h->p32[i], prob[i]));
     if (opt->decomp == SMA_TSVDM && nprob > 1) SMA_TRY(build_bins<float>(h.get()));
   }
+  if (opt->decomp != SMA_TSVDM) SMA_TRY(setup_gram_shared(h.get()));
   *out = h.release();
   return SMA_OK;
 }

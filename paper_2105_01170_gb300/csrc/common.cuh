@@ -78,6 +78,9 @@ struct GemmParams {
   void* Cs = nullptr; int64_t cs_plane = 0;
   int nb1 = 1, nb2 = 1;
   T alpha = T(1), beta = T(0);
+  // > 0: split K, batch index b1 takes the range [b1 kchunk, (b1 + 1) kchunk)
+  // (A and B then usually have no b1 offset; each b1 writes its own partial C)
+  int kchunk = 0;
 };
 
 template <typename T> cudaError_t gemm(const GemmParams<T>& p, cudaStream_t st);

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
   const int di = p.dstride * b1;
   const int M = p.dM ? min(p.M, p.dM[di]) : p.M;
   const int N = p.dN ? min(p.N, p.dN[di]) : p.N;
-  const int K = p.dK ? min(p.K, p.dK[di]) : p.K;
+  int K = p.dK ? min(p.K, p.dK[di]) : p.K;
   const int tiles_m = (p.M + BM - 1) / BM;
   const int m0 = (blockIdx.x % tiles_m) * BM;
   const int n0 = (blockIdx.x / tiles_m) * BN;
@@ -55,7 +55,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
 
   const bool a_col = (p.a_rs == 1);
   const bool b_col = (p.b_rs == 1);
-  const int kbeg = p.dKoff ? p.dKoff[di] : 0;
+  int kbeg = p.dKoff ? p.dKoff[di] : 0;
+  if (p.kchunk > 0) {
+    kbeg = b1 * p.kchunk;
+    K = min(K, kbeg + p.kchunk);
+  }
   for (int k0 = kbeg; k0 < K; k0 += BK) {
 #pragma unroll
     for (int t = 0; t < (BM * BK) / NT; ++t) {

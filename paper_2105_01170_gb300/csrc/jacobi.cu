@@ -1002,6 +1002,199 @@ __global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel
   }
 }
 
+// ---- one large matrix over many CTAs (cooperative launch) ------------------
+// The block mode above walks the block pairs of a sweep one after another in
+// one CTA, which leaves one SM to do all of the work for a single matrix (the
+// fp64 unfolding Gram of a Tucker variant).  The pairs of one round of a
+// block tournament are disjoint, so here CTA c takes pair c of every round:
+// nb = 2 gridDim.x blocks of bc columns, round t pairs the blocks by the
+// circle method, a block's inner pairs are rotated in round 0 (the first
+// round every block plays), and the cross pairs of the two blocks in bc
+// sub-rounds as in Phase kind 1.  The stacked columns live in the global
+// workspace between rounds (read and written at L2, .cg); rounds are
+// separated by a grid barrier on a counter in global memory whose wait is
+// bounded: a CTA that gives up sets the abort flag and SMA_ERR_TIMEOUT, and
+// every other waiting CTA returns when it sees the flag.
+
+constexpr unsigned long long kCoopWaitNs = 4000000000ull;   // 4 s per barrier
+
+__device__ __forceinline__ unsigned long long coop_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Barrier number k (1-based) of the launch: every CTA adds 1 to the counter
+// and waits until it reaches k * gridDim.x.  False when the launch aborted.
+__device__ bool coop_barrier(const CoopSync& cs, unsigned k, int* status) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(cs.bar, 1u);
+    const unsigned target = k * gridDim.x;
+    const unsigned long long t0 = coop_timer();
+    int ok = 1;
+    while (*(volatile unsigned*)cs.bar < target) {
+      if (*(volatile int*)cs.abort_flag) {
+        ok = 0;
+        break;
+      }
+      if (coop_timer() - t0 > kCoopWaitNs) {
+        atomicExch(cs.abort_flag, 1);
+        atomicOr(status, SMA_STATUS_BIT(SMA_ERR_TIMEOUT));
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ncols stacked columns between shared memory (stride ldS) and the workspace
+// (stride len), bypassing L1 so that columns written by other CTAs are seen.
+template <typename T>
+__device__ __forceinline__ void coop_cols(T* S, int ldS, T* G, int len, int ncols, bool to_smem) {
+  for (int e = threadIdx.x; e < len * ncols; e += blockDim.x) {
+    const int r = e % len, c = e / len;
+    if (to_smem) S[(int64_t)c * ldS + r] = __ldcg(G + (int64_t)c * len + r);
+    else __stcg(G + (int64_t)c * len + r, S[(int64_t)c * ldS + r]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) jacobi_coop_kernel(const JacobiParams<T> P,
+                                                          const CoopSync cs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, NTh = blockDim.x;
+  const int cta = blockIdx.x, ncta = gridDim.x;
+  const int mm = P.mm, rc = P.rc, ldS = P.ldS, g = P.g, bc = P.bcols;
+  const int len = mm + rc;
+  const int lane = tid % g, kslot = tid / g, ngroups = NTh / g;
+  const int nb = 2 * ncta;
+  T* S = reinterpret_cast<T*>(smem_raw);
+  T* W = P.W;
+  unsigned nbar = 0;
+  // stacked columns [A; I] into the workspace (the CTAs share the copy) and
+  // ||A||_F^2 (every CTA sums it whole, so no reduction across CTAs is needed)
+  __shared__ double red[32];
+  double nrm2 = 0.0;
+  {
+    const int64_t tot = (int64_t)len * rc;
+    for (int64_t e = (int64_t)cta * NTh + tid; e < tot; e += (int64_t)ncta * NTh) {
+      const int r = (int)(e % len), c = (int)(e / len);
+      __stcg(W + e, load_work(P.src, P.m, P.trans, mm, r, c));
+    }
+    for (int64_t e = tid; e < (int64_t)mm * rc; e += NTh) {
+      const int r = (int)(e % mm), c = (int)(e / mm);
+      const double v = (double)load_work(P.src, P.m, P.trans, mm, r, c);
+      nrm2 = fma(v, v, nrm2);
+    }
+    nrm2 = block_sum(nrm2, red);
+  }
+  const T tol_t = (T)P.tol;
+  const T floor_t = (T)(Eps<T>::v * Eps<T>::v * nrm2);
+  if (!coop_barrier(cs, ++nbar, P.status)) return;
+  int sweeps_used = 0;
+  bool converged = (rc <= 1);
+  for (int sw = 0; sw < P.max_sweeps && !converged; ++sw) {
+    bool rot = false;
+    for (int t = 0; t < nb - 1; ++t) {
+      const Pair pr = rr_pair(cta, t, nb);
+      const int bI = max(0, min(bc, rc - pr.a * bc)), bJ = max(0, min(bc, rc - pr.b * bc));
+      T* WI = W + (int64_t)pr.a * bc * len;
+      T* WJ = W + (int64_t)pr.b * bc * len;
+      coop_cols<T>(S, ldS, WI, len, bI, true);
+      coop_cols<T>(S + (int64_t)bc * ldS, ldS, WJ, len, bJ, true);
+      __syncthreads();
+      Phase ph;
+      ph.kind = 1;
+      ph.bI = bI;
+      ph.bJ = bJ;
+      ph.bc = bc;
+      ph.cI = (t == 0 && bI > 1) ? bI + (bI & 1) : 0;
+      ph.cJ = (t == 0 && bJ > 1) ? bJ + (bJ & 1) : 0;
+      ph.nri = (ph.cI || ph.cJ) ? max(ph.cI, ph.cJ) - 1 : 0;
+      ph.nrounds = ph.nri + ((bI > 0 && bJ > 0) ? bc : 0);
+      ph.npairs = max(bc, ph.cI / 2 + ph.cJ / 2);
+      for (int r = 0; r < ph.nrounds; ++r) {
+        for (int base = 0; base < ph.npairs; base += ngroups) {
+          int a = 0, b = 0;
+          const bool act = phase_pair(ph, r, base + kslot, a, b);
+          rot |= Rotator<T, 1>::run(S, ldS, a, b, act, mm, len, lane, g, tol_t, floor_t);
+        }
+        __syncthreads();
+      }
+      coop_cols<T>(S, ldS, WI, len, bI, false);
+      coop_cols<T>(S + (int64_t)bc * ldS, ldS, WJ, len, bJ, false);
+      if (!coop_barrier(cs, ++nbar, P.status)) return;
+    }
+    // sweep result: CTAs that rotated anything count themselves, then every
+    // CTA reads the count after one more barrier
+    if (__syncthreads_or(rot) && tid == 0) atomicAdd(cs.rot + sw, 1);
+    if (!coop_barrier(cs, ++nbar, P.status)) return;
+    sweeps_used = sw + 1;
+    converged = *(volatile int*)(cs.rot + sw) == 0;
+  }
+  if (cta != 0) return;
+  // CTA 0: column norms, descending sort, outputs (as in jacobi_kernel)
+  const int p2 = P.sort_n;
+  const size_t sig_off = ((size_t)2 * bc * ldS * sizeof(T) + 15) & ~(size_t)15;
+  double* sig = reinterpret_cast<double*>(smem_raw + sig_off);
+  int* idx = reinterpret_cast<int*>(sig + p2);
+  const int warp = tid >> 5, wl = tid & 31, nwarps = NTh >> 5;
+  for (int c = warp; c < p2; c += nwarps) {
+    double acc = 0.0;
+    if (c < rc)
+      for (int r = wl; r < mm; r += 32) {
+        const double v = (double)__ldcg(W + r + (int64_t)c * len);
+        acc = fma(v, v, acc);
+      }
+    acc = warp_sum(acc);
+    if (wl == 0) {
+      sig[c] = (c < rc) ? sqrt(acc) : -1.0;
+      idx[c] = c;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= p2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < p2; i += NTh) {
+        const int l = i ^ j;
+        if (l > i) {
+          const double si = sig[i], sl = sig[l];
+          const int ii = idx[i], il = idx[l];
+          const bool i_first = (si > sl) || (si == sl && ii < il);
+          const bool up = ((i & k) == 0);
+          if (up ? !i_first : i_first) {
+            sig[i] = sl; sig[l] = si;
+            idx[i] = il; idx[l] = ii;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = tid; j < rc; j += NTh) {
+    P.sigma[j] = sig[j];
+    if (!isfinite(sig[j])) atomicOr(P.status, SMA_STATUS_BIT(SMA_ERR_NONFINITE));
+  }
+  for (int64_t e = tid; e < (int64_t)len * rc; e += NTh) {
+    const int r = (int)(e % len), j = (int)(e / len);
+    const T v = __ldcg(W + r + (int64_t)idx[j] * len);
+    if (r < mm) P.U[r + (int64_t)j * mm] = v;
+    else P.V[(r - mm) + (int64_t)j * rc] = v;
+  }
+  if (tid == 0) {
+    if (P.sweeps) *P.sweeps = sweeps_used;
+    if (!converged) atomicOr(P.status, SMA_STATUS_BIT(SMA_ERR_NOCONVERGE));
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -1165,11 +1358,72 @@ cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_
   return cudaGetLastError();
 }
 
+template <typename T>
+JacobiPlan jacobi_coop_plan(int rows, int max_smem) {
+  JacobiPlan pl{};
+  pl.trans = 0;
+  pl.mm = pl.rc = rows;
+  pl.vec = 1;
+  pl.bcols = 4;
+  const int len = 2 * rows;
+  pl.ldS = len + 1;
+  int p2 = 1;
+  while (p2 < rows) p2 <<= 1;
+  pl.sort_n = p2;
+  pl.g = rows >= 64 ? 32 : 16;
+  pl.threads = pl.bcols * pl.g;
+  const int nblk = (rows + pl.bcols - 1) / pl.bcols;
+  pl.block_mode = (nblk + 1) / 2;   // CTAs of the launch
+  pl.tile = 0;
+  pl.smem = (((size_t)2 * pl.bcols * pl.ldS * sizeof(T) + 15) & ~(size_t)15) +
+            (size_t)p2 * (sizeof(double) + sizeof(int));
+  if (pl.smem > (size_t)max_smem) pl.smem = 0;
+  return pl;
+}
+
+template <typename T>
+cudaError_t jacobi_svd_coop(const JacobiParams<T>& P, const JacobiPlan& pl, const CoopSync& cs,
+                            cudaStream_t st) {
+  if (pl.smem == 0 || pl.block_mode < 1) return cudaErrorInvalidValue;
+  if (P.mm != P.rc || P.bcols != pl.bcols || P.g != pl.g || P.trans != 0)
+    return cudaErrorInvalidValue;
+  void (*kern)(const JacobiParams<T>, const CoopSync) = jacobi_coop_kernel<T>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, pl.threads, pl.smem)) !=
+      cudaSuccess)
+    return e;
+  if ((int64_t)per_sm * nsm < pl.block_mode) return cudaErrorCooperativeLaunchTooLarge;
+  JacobiParams<T> p = P;
+  CoopSync c = cs;
+  void* args[] = {&p, &c};
+  if ((e = cudaMemsetAsync(cs.bar, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(cs.abort_flag, 0, sizeof(int), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(cs.rot, 0, sizeof(int) * (size_t)P.max_sweeps, st)) != cudaSuccess)
+    return e;
+  e = cudaLaunchCooperativeKernel((const void*)kern, dim3(pl.block_mode), dim3(pl.threads), args,
+                                  pl.smem, st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 template JacobiPlan jacobi_plan<float>(int, int, int);
 template JacobiPlan jacobi_plan<double>(int, int, int);
 template std::vector<JacobiPlan> jacobi_plan_candidates<float>(int, int, int);
 template std::vector<JacobiPlan> jacobi_plan_candidates<double>(int, int, int);
 template cudaError_t jacobi_svd<float>(const JacobiParams<float>&, int, int, size_t, cudaStream_t);
 template cudaError_t jacobi_svd<double>(const JacobiParams<double>&, int, int, size_t, cudaStream_t);
+
+template JacobiPlan jacobi_coop_plan<double>(int, int);
+template JacobiPlan jacobi_coop_plan<float>(int, int);
+template cudaError_t jacobi_svd_coop<double>(const JacobiParams<double>&, const JacobiPlan&,
+                                             const CoopSync&, cudaStream_t);
+template cudaError_t jacobi_svd_coop<float>(const JacobiParams<float>&, const JacobiPlan&,
+                                            const CoopSync&, cudaStream_t);
 
 }  // namespace sma

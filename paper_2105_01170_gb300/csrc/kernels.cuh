@@ -16,6 +16,9 @@ cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off /*device, p*
                    double* partial /*device, >= 1024*/, cudaStream_t st);
 // ||X||_F^2 from the per-CTA partial sums written by gather.
 cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStream_t st);
+// out[e] = sum_s part[e + s count] for e < count, s < nslab (fixed order: the
+// split-K partial products of a Gram).
+cudaError_t sum_slabs(const double* part, int nslab, int64_t count, double* out, cudaStream_t st);
 int gather_parts(int m, int n, int p);
 // ||X - T||_F^2 over `count` elements (fp64 accumulation; nparts partial sums
 // as for gather); two launches.  Tt == nullptr gives ||X||_F^2.
@@ -61,6 +64,21 @@ template <typename T> std::vector<JacobiPlan> jacobi_plan_candidates(int m, int 
 template <typename T>
 cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_t smem,
                        cudaStream_t st);
+// One square matrix (P.mm == P.rc, not transposed) over many CTAs of a
+// cooperative launch: blocks of bcols columns, one block pair per CTA and
+// round of a block tournament, a bounded grid barrier between rounds.  The
+// plan's block_mode field holds the CTA count; smem == 0 when it does not
+// fit.  cs: barrier counter, per-sweep rotation counts (max_sweeps ints) and
+// an abort flag in device memory, cleared by the launcher on the stream.
+struct CoopSync {
+  unsigned* bar;
+  int* rot;
+  int* abort_flag;
+};
+template <typename T> JacobiPlan jacobi_coop_plan(int rows, int max_smem);
+template <typename T>
+cudaError_t jacobi_svd_coop(const JacobiParams<T>& P, const JacobiPlan& pl, const CoopSync& cs,
+                            cudaStream_t st);
 
 // ---- QR preconditioning of the slice SVD (qr.cu) ---------------------------
 // Shared-memory plan: the factorisation keeps nslot columns of a slice in

@@ -443,6 +443,24 @@ template cudaError_t residual_norm2<float>(const float*, const float*, int64_t, 
 template cudaError_t residual_norm2<double>(const double*, const double*, int64_t, double*, int,
                                             double*, cudaStream_t);
 
+__global__ void sum_slabs_kernel(const double* __restrict__ part, int nslab, int64_t count,
+                                 double* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < nslab; ++s) acc += part[e + s * count];
+    out[e] = acc;
+  }
+}
+
+cudaError_t sum_slabs(const double* part, int nslab, int64_t count, double* out, cudaStream_t st) {
+  int64_t grid = (count + 255) / 256;
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  sum_slabs_kernel<<<(int)grid, 256, 0, st>>>(part, nslab, count, out);
+  return cudaGetLastError();
+}
+
 cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStream_t st) {
   finish_norm_kernel<<<1, 1024, 0, st>>>(partial, nparts, out);
   return cudaGetLastError();

@@ -1,0 +1,131 @@
+"""The Tucker variants at Gram orders where the eigen-solve runs over many CTAs
+(a cooperative launch, one block pair per CTA and round) and the Gram itself
+is a split-K product: the block-index Gram of a 99-block Toeplitz matrix and
+the mode-1 Gram of a 128-point covariance, against the FP64 oracle, plus
+graph capture and replay of the cooperative launch."""
+import numpy as np
+import pytest
+
+from oracle import sma_oracle as O
+from sma_inputs import generators as G
+
+from _util import (TOL_MIXED, apply, gpu_tensor, input_matrix, np_dtype, oracle_tensor,
+                   reconstruct, rel, to_dev, tol_for)
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+S = pytest.importorskip("paper_2105_01170_gb300")
+
+PRECS = [S.SMA_FP64, S.SMA_MIXED]
+PNAME = {S.SMA_FP64: "fp64", S.SMA_MIXED: "mixed"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_01170_gb300 import _build
+    _build.build()
+
+
+def run(pr, prec, decomp, **kw):
+    A = input_matrix(pr, prec)
+    h = S.Handle([pr], prec=prec, decomp=decomp, **kw)
+    res = h.compress([to_dev(A)])[0]
+    return h, A, res
+
+
+def stored_tensor(A, pr, prec):
+    """The oracle's tensor as the path stores it: the mixed path keeps the
+    gathered tensor in fp32 (each entry the rounded fp64 product), and its
+    Gram is formed from that tensor in fp64."""
+    X = oracle_tensor(A, pr)
+    return X if prec == S.SMA_FP64 else X.astype(np.float32).astype(np.float64)
+
+
+def projector_gap(Ug, Uo):
+    """Spectral distance between the subspaces spanned by two orthonormal bases."""
+    return float(np.linalg.norm(Ug @ Ug.T - Uo @ Uo.T, 2))
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_blockmode_99_blocks(prec):
+    pr = G.planted_kron_toeplitz(ell=50, m=6, terms=4, seed_index=5)
+    assert pr.p == 99
+    tol = 1e-6 if prec == S.SMA_FP64 else 1e-4
+    h, A, res = run(pr, prec, S.SMA_TUCKER_BLOCKMODE, rel_tol=tol)
+    assert res["device_status"] == 0
+    X = stored_tensor(A, pr, prec)
+    t = O.tucker1_blockmode(X, rel_tol=tol)
+    assert t.rank == 4 and res["ranks"][0] == 4
+    # the Gram's eigenvalues are the squared singular values of the unfolding
+    ev = gpu_tensor(h, S.EXPORT_SIGMA, None, prec)[:pr.p]
+    assert np.allclose(np.sqrt(np.maximum(ev[:4], 0)), t.sigma[:4], rtol=1e-12, atol=0)
+    assert np.all(ev[4:] <= 1e-12 * ev[0])
+    V = gpu_tensor(h, S.EXPORT_FACTOR, (pr.p, pr.p), prec)[:, :4]
+    assert projector_gap(V, t.V[:, :4]) < (1e-12 if prec == S.SMA_FP64 else 1e-6)
+    Ah = reconstruct(h, pr, prec)
+    assert rel(Ah, O.M_E(t.tensor_approx(), pr.block_map)) < tol_for(prec)
+    floor = (1e-13 if prec == S.SMA_FP64 else TOL_MIXED) * np.linalg.norm(X)
+    assert abs(res["tensor_err"] - t.err) <= 1e-6 * t.err + floor
+    assert res["orth_defect"] < (1e-12 if prec == S.SMA_FP64 else 1e-6)
+    h.close()
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+@pytest.mark.parametrize("mode", ["tol", "rank"])
+def test_shared_u_128_points(prec, mode):
+    pr = G.spacetime_covariance(npts=128, T=8, seed_index=2)
+    tol = 1e-2                          # keeps about 100 of the 128 mode-1 directions
+    kw = dict(rel_tol=tol) if mode == "tol" else dict(fixed_rank=24)
+    h, A, res = run(pr, prec, S.SMA_TUCKER_SHARED_U, **kw)
+    assert res["device_status"] == 0
+    X = stored_tensor(A, pr, prec)
+    su = O.shared_u(X, rel_tol=kw.get("rel_tol"), rank=kw.get("fixed_rank"))
+    r = int(h.ranks(0)[0])
+    if mode == "rank":
+        assert r == 24
+    else:
+        # identical ranks where the oracle's decision has slack: the budget
+        # tol^2 ||X||^2 / 2 against the tail sums of the mode-1 energies
+        e = su.sigma ** 2
+        budget = tol * tol * float(np.sum(X * X)) / 2
+        slack = min(budget - np.sum(e[su.rank:]), np.sum(e[su.rank - 1:]) - budget) / budget
+        if slack > 1e-6:
+            assert r == su.rank
+    # both precisions form and solve the Gram in fp64 (from the same rounded
+    # input), so the eigenvalues agree to fp64 accuracy
+    ev = gpu_tensor(h, S.EXPORT_SIGMA, None, prec)[:pr.m]
+    assert np.max(np.abs(ev - su.sigma[:pr.m] ** 2)) <= 1e-11 * ev[0]
+    U = gpu_tensor(h, S.EXPORT_FACTOR, (pr.m, pr.m), prec)[:, :r]
+    gap_tol = 1e-9 if prec == S.SMA_FP64 else 1e-6
+    assert projector_gap(U, su.U[:, :r]) < gap_tol
+    Ah = reconstruct(h, pr, prec)
+    Ao = O.M_E(su.tensor_approx(), pr.block_map)
+    assert rel(Ah, Ao) < 10 * tol_for(prec)
+    x = G.random_rhs(pr.q * pr.n, 3, 5).astype(np_dtype(prec)).astype(np.float64)
+    assert rel(apply(h, pr, x, prec), Ao @ x) < 10 * tol_for(prec)
+    floor = (1e-12 if prec == S.SMA_FP64 else TOL_MIXED) * np.linalg.norm(X)
+    assert abs(res["tensor_err"] - su.err) <= 1e-6 * su.err + floor
+    h.close()
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_cooperative_gram_graph_replay_is_identical(prec):
+    pr = G.spacetime_covariance(npts=128, T=8, seed_index=3)
+    st = torch.cuda.Stream()
+    A = to_dev(input_matrix(pr, prec))
+    h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_SHARED_U, rel_tol=1e-2,
+                 stream=st.cuda_stream, graph=True)
+    with torch.cuda.stream(st):
+        outs = []
+        for _ in range(4):              # run, capture, replay, replay
+            res = h.compress([A])[0]
+            outs.append((res, gpu_tensor(h, S.EXPORT_SIGMA, None, prec),
+                         gpu_tensor(h, S.EXPORT_FACTOR, None, prec)))
+    for res, sig, U in outs[1:]:
+        assert res["ranks"] == outs[0][0]["ranks"]
+        assert res["tensor_err"] == outs[0][0]["tensor_err"]
+        assert np.array_equal(sig, outs[0][1])
+        assert np.array_equal(U, outs[0][2])
+    h.close()
