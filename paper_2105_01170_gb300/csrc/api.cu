@@ -26,7 +26,7 @@ namespace {
 // it saves)
 // Gram eigen-solves of this order and larger run over many CTAs
 // (jacobi_svd_coop); smaller ones in one CTA.
-constexpr int kCoopMinRows = 96;
+constexpr int kCoopMinRows = 40;
 constexpr int kQrAutoMin = 128;
 
 #define SMA_CK(...)                                 \

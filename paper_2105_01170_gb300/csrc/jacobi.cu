@@ -1018,6 +1018,115 @@ __global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel
 
 constexpr unsigned long long kCoopWaitNs = 4000000000ull;   // 4 s per barrier
 
+// fp64 rotation of the cooperative kernel with the tangent taken in fp32: any
+// tangent near the optimal one gives an exact (valid) rotation, which leaves
+// the pair orthogonal to about fp32 relative accuracy for the next sweep to
+// finish, while (c, s) themselves are orthonormal to fp64 accuracy: c =
+// 1/sqrt(1 + t^2) from the fp32 estimate refined by two Newton steps in fp64.
+// The threshold is tested without square roots; nearly parallel columns
+// (|cos| > 0.99) and values outside the fp32 range take the fp64 angle.
+__device__ __forceinline__ bool angle_fp64_fast(double al, double be, double ga, double tol,
+                                                double floor_, double& c, double& s) {
+  const double g2 = ga * ga, ab = al * be;
+  if (!(g2 > tol * tol * ab) || !(fabs(ga) > floor_)) return false;
+  const double d = be - al;
+  const double ad = fabs(d), ag = fabs(ga);
+  if (g2 > 0.9801 * ab || ag > 1e30 || ag < 1e-30 || ad > 1e30 || (ad < 1e-30 && ad != 0.0))
+    return angle_fp64(al, be, ga, 0.0, 0.0, c, s);
+  const float zeta = __fdividef((float)d, 2.0f * (float)ga);
+  const float az = fabsf(zeta);
+  float tf;
+  if (az > 1e18f) {
+    tf = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.0f);
+    tf = copysignf(__fdividef(1.0f, az + q * rsqrtf(q)), zeta);
+  }
+  const double t = (double)tf;
+  const double q = fma(t, t, 1.0);
+  double r = (double)rsqrtf((float)q);
+  r = r * fma(-0.5 * q, r * r, 1.5);
+  r = r * fma(-0.5 * q, r * r, 1.5);
+  c = r;
+  s = r * t;
+  return true;
+}
+
+// rotate_pair for fp64 with the angle above; NR rows per lane stay in
+// registers between the dot products and the rotation.
+template <int NR>
+__device__ __forceinline__ bool rotate_pair_f64(double* S, int ldS, int a, int b, bool active,
+                                                int mm, int len, int lane, int g, double tol,
+                                                double floor_) {
+  double xr[NR], yr[NR];
+  double al = 0.0, be = 0.0, ga = 0.0;
+  double* x = S + (int64_t)(active ? a : 0) * ldS;
+  double* y = S + (int64_t)(active ? b : 0) * ldS;
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+      const int r = lane + i * g;
+      xr[i] = 0.0;
+      yr[i] = 0.0;
+      if (r < mm) {
+        xr[i] = x[r];
+        yr[i] = y[r];
+        al = fma(xr[i], xr[i], al);
+        be = fma(yr[i], yr[i], be);
+        ga = fma(xr[i], yr[i], ga);
+      }
+    }
+    for (int r = lane + NR * g; r < mm; r += g) {
+      const double xv = x[r], yv = y[r];
+      al = fma(xv, xv, al);
+      be = fma(yv, yv, be);
+      ga = fma(xv, yv, ga);
+    }
+  }
+  for (int o = g >> 1; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  if (!active) return false;
+  double c, s;
+  if (!angle_fp64_fast(al, be, ga, tol, floor_, c, s)) return false;
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    const int r = lane + i * g;
+    if (r < mm) {
+      x[r] = c * xr[i] - s * yr[i];
+      y[r] = s * xr[i] + c * yr[i];
+    }
+  }
+  for (int r = lane + NR * g; r < mm; r += g) {
+    const double xv = x[r], yv = y[r];
+    x[r] = c * xv - s * yv;
+    y[r] = s * xv + c * yv;
+  }
+  for (int r = mm + lane; r < len; r += g) {
+    const double xv = x[r], yv = y[r];
+    x[r] = c * xv - s * yv;
+    y[r] = s * xv + c * yv;
+  }
+  return true;
+}
+
+template <typename T>
+struct CoopRotator {
+  static __device__ __forceinline__ bool run(T* S, int ldS, int a, int b, bool act, int mm,
+                                             int len, int lane, int g, T tol, T fl) {
+    return Rotator<T, 1>::run(S, ldS, a, b, act, mm, len, lane, g, tol, fl);
+  }
+};
+template <>
+struct CoopRotator<double> {
+  static __device__ __forceinline__ bool run(double* S, int ldS, int a, int b, bool act, int mm,
+                                             int len, int lane, int g, double tol, double fl) {
+    return rotate_pair_f64<8>(S, ldS, a, b, act, mm, len, lane, g, tol, fl);
+  }
+};
+
 __device__ __forceinline__ unsigned long long coop_timer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -1125,7 +1234,7 @@ __global__ void __launch_bounds__(512) jacobi_coop_kernel(const JacobiParams<T> 
         for (int base = 0; base < ph.npairs; base += ngroups) {
           int a = 0, b = 0;
           const bool act = phase_pair(ph, r, base + kslot, a, b);
-          rot |= Rotator<T, 1>::run(S, ldS, a, b, act, mm, len, lane, g, tol_t, floor_t);
+          rot |= CoopRotator<T>::run(S, ldS, a, b, act, mm, len, lane, g, tol_t, floor_t);
         }
         __syncthreads();
       }
