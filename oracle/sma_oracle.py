@@ -403,6 +403,23 @@ def tucker1_blockmode(X: np.ndarray, rel_tol: float | None = None,
     return Tucker1Block(V, G, s, r, err, err / math.sqrt(normX2))
 
 
+def tucker1_blockmode_sketch(X: np.ndarray, Omega: np.ndarray, Psi: np.ndarray,
+                             rank: int) -> Tucker1Block:
+    """Section 6.3, the randomized variant used for the largest matrix of the
+    Kronecker-sum experiment: V is taken from the block-index unfolding of the
+    sketch Y = X x1 Omega^T x2 Psi^T (our orientation: Y[:, :, k] =
+    Omega^T X[:, :, k] Psi, Omega m x s and Psi n x s Gaussian, passed in),
+    keeping `rank` leading left singular vectors; the rest is the Tucker-1
+    compression of X itself, G = X x3 V^T.  The error is ||X - G x3 V||_F,
+    measured directly (the sketch's singular values are not those of X)."""
+    normX2 = float(np.sum(X * X))
+    Ysk = np.einsum("ai,abk,bj->ijk", Omega, X, Psi, optimize=True)
+    V, s, r = leading_left_singular(unfold(Ysk, 3), rank)
+    G = mode3(X, V.T)
+    err = float(np.linalg.norm((X - mode3(G, V)).ravel()))
+    return Tucker1Block(V, G, s, r, err, err / math.sqrt(normX2))
+
+
 def tucker1_kron_terms(t: Tucker1Block, block_map: np.ndarray):
     """A_hat = sum_j struct_E(V[:, j]) (x) sq(G_:,j,:) (Section 6.3 / Theorem
     'tuckerkron' with U, W identities)."""

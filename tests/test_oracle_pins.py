@@ -500,3 +500,49 @@ def test_spd_inner_error_is_lemma_1():
     assert abs(e - s.su.err) <= 1e-12 * np.linalg.norm(A)
     assert s.su.err <= 1e-3 * np.linalg.norm(s.X) * (1 + 1e-12)
 
+
+
+# ------------------------------------------- Section 6.3, randomized block-index factor
+
+def test_sketch_with_identity_maps_is_the_deterministic_factor():
+    """Omega = I_m, Psi = I_n make the sketch the tensor itself: the same
+    subspace, core and error as the deterministic Tucker-1 at that rank."""
+    pr = G.planted_kron_toeplitz(ell=6, m=5, terms=3, noise=1e-3, seed_index=3)
+    X = O.T_E(pr.dense(), pr.block_map, pr.p, pr.m, pr.n)
+    r = 4
+    t = O.tucker1_blockmode(X, rank=r)
+    s = O.tucker1_blockmode_sketch(X, np.eye(pr.m), np.eye(pr.n), r)
+    assert np.allclose(s.V @ s.V.T, t.V @ t.V.T, atol=1e-12)
+    assert abs(s.err - t.err) <= 1e-12 * np.linalg.norm(X)
+    assert np.allclose(s.tensor_approx(), t.tensor_approx(), atol=1e-12 * np.abs(X).max())
+
+
+def test_sketch_recovers_a_planted_kronecker_sum_exactly():
+    """A noise-free sum of 3 Kronecker products has a rank-3 block-index
+    unfolding; Gaussian sketches with s^2 >= 3 keep its row space, so the
+    sketched factor spans it and the error vanishes."""
+    pr = G.planted_kron_toeplitz(ell=7, m=6, terms=3, noise=0.0, seed_index=4)
+    X = O.T_E(pr.dense(), pr.block_map, pr.p, pr.m, pr.n)
+    g = np.random.default_rng(11)
+    for sk in (2, 3, 5):
+        s = O.tucker1_blockmode_sketch(X, g.standard_normal((pr.m, sk)),
+                                       g.standard_normal((pr.n, sk)), 3)
+        assert s.err <= 1e-12 * np.linalg.norm(X)
+        t = O.tucker1_blockmode(X, rank=3)
+        assert np.allclose(s.V @ s.V.T, t.V @ t.V.T, atol=1e-10)
+
+
+def test_sketch_error_is_a_projection_residual_and_not_below_the_optimum():
+    """V has orthonormal columns, so the error is the Pythagorean remainder
+    sqrt(||X||^2 - ||X x3 V^T||^2); no rank-r factor beats the leading
+    singular vectors of the unfolding (Eckart-Young)."""
+    pr = G.planted_kron_toeplitz(ell=8, m=6, terms=5, noise=1e-2, seed_index=6)
+    X = O.T_E(pr.dense(), pr.block_map, pr.p, pr.m, pr.n)
+    g = np.random.default_rng(12)
+    for r, sk in ((2, 3), (4, 3), (5, 6)):
+        s = O.tucker1_blockmode_sketch(X, g.standard_normal((pr.m, sk)),
+                                       g.standard_normal((pr.n, sk)), r)
+        assert np.allclose(s.V.T @ s.V, np.eye(r), atol=1e-12)
+        pyth = np.sqrt(max(np.sum(X * X) - np.sum(s.G * s.G), 0.0))
+        assert abs(s.err - pyth) <= 1e-9 * np.linalg.norm(X)
+        assert s.err >= O.tucker1_blockmode(X, rank=r).err * (1 - 1e-12)
