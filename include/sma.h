@@ -159,6 +159,19 @@ typedef struct {
                              choice is cached for the process.  0: default
                              plan.  Trial runs are not part of sma_profile's
                              stage times.                                     */
+  /* Randomized block-index factor (Section 6.3, the variant used for the
+   * largest matrix of the Kronecker-sum experiment), SMA_TUCKER_BLOCKMODE
+   * only: with sketch_cols = s > 0, V is taken from the sketch
+   * Y[:, :, k] = Omega^T X[:, :, k] Psi (s x s x p) instead of from X: the
+   * s^2 x s^2 Gram of its block-index unfolding is eigen-solved, and the
+   * fixed_rank (required, 1 <= fixed_rank <= s^2) leading left singular
+   * vectors of the unfolding are recovered as Y_(3) W Sigma^-1.  The core,
+   * the Kronecker terms and the error (measured as ||X - T||_F) are those of
+   * X.  All problems must have the same m and n.  sma_export(2) then
+   * returns the s^2 eigenvalues of the sketch's Gram.                      */
+  int32_t sketch_cols;
+  const double* sketch_omega;   /* host, m x s column-major (e.g. N(0,1))  */
+  const double* sketch_psi;     /* host, n x s column-major                */
 } sma_options;
 
 typedef struct {

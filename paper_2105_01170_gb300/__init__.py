@@ -58,7 +58,10 @@ class sma_options(ctypes.Structure):
                 ("fixed_rank", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("max_sweeps", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("profile", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("precondition", ctypes.c_int), ("autotune", ctypes.c_int32)]
+                ("precondition", ctypes.c_int), ("autotune", ctypes.c_int32),
+                ("sketch_cols", ctypes.c_int32),
+                ("sketch_omega", ctypes.POINTER(ctypes.c_double)),
+                ("sketch_psi", ctypes.POINTER(ctypes.c_double))]
 
 
 class sma_result(ctypes.Structure):
@@ -232,7 +235,7 @@ class Handle:
     def __init__(self, problems, prec=SMA_MIXED, decomp=SMA_TSVDM, mkind=SMA_M_DCT2,
                  layout=SMA_INPUT_DENSE, M_user=None, fixed_rank=0, rel_tol=0.0,
                  max_sweeps=0, stream=None, profile=False, graph=False,
-                 precondition=None, autotune=False):
+                 precondition=None, autotune=False, sketch=None):
         self._keep = []
         structs = []
         for pr in problems:
@@ -253,10 +256,22 @@ class Handle:
         sptr = None
         if stream is not None:
             sptr = ctypes.c_void_p(int(stream))
+        # sketch = (Omega, Psi): the Gaussian maps of the randomized block-index
+        # factor, m x s and n x s
+        sk_cols, sk_om, sk_ps = 0, None, None
+        if sketch is not None:
+            Om = np.asfortranarray(np.asarray(sketch[0], dtype=np.float64))
+            Ps = np.asfortranarray(np.asarray(sketch[1], dtype=np.float64))
+            if Om.ndim != 2 or Ps.ndim != 2 or Om.shape[1] != Ps.shape[1]:
+                raise ValueError("sketch maps must be m x s and n x s")
+            self._keep += [Om, Ps]
+            sk_cols = Om.shape[1]
+            sk_om = Om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            sk_ps = Ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.opt = sma_options(prec, decomp, mkind, layout, mu, int(fixed_rank), float(rel_tol),
                                int(max_sweeps), sptr, 1 if profile else 0, 1 if graph else 0,
                                SMA_PRECOND_AUTO if precondition is None else int(precondition),
-                               1 if autotune else 0)
+                               1 if autotune else 0, sk_cols, sk_om, sk_ps)
         self.nprob = len(structs)
         self.prec = prec
         st, self.h = sma_create(structs, self.opt)

@@ -174,6 +174,14 @@ struct Prob {
   T* tmp = nullptr;
   T* mid = nullptr;                         // struct_E(core) dense (ell r1 x q r3)
   int r1max = 0, r3max = 0;
+  // randomized block-index factor (Section 6.3): Omega (m x sk), Psi (n x sk),
+  // the sketch Y (sk x sk x p, T and fp64) and Omega^T X_k (sk x n x p)
+  int sk = 0;
+  T* Om = nullptr;
+  T* Ps = nullptr;
+  T* Ysk = nullptr;
+  double* Y64 = nullptr;
+  T* Ytmp = nullptr;
   // multilevel (three levels, m = n = 1; Section 7)
   int L = 1;
   int lell[3] = {0, 0, 0}, lq[3] = {0, 0, 0}, lp[3] = {0, 0, 0};
@@ -624,16 +632,24 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   } else {
     // Tucker family: fp64 Gram and its Jacobi eigen-solve
     int gdim = 0;
-    if (o.decomp == SMA_TUCKER_BLOCKMODE) gdim = p;
+    if (o.decomp == SMA_TUCKER_BLOCKMODE) {
+      gdim = p;
+      P.sk = o.sketch_cols > 0 ? o.sketch_cols : 0;
+      if (P.sk * P.sk > gdim) gdim = P.sk * P.sk;
+    }
     else if (o.decomp == SMA_TUCKER_SHARED_U || o.decomp == SMA_TUCKER_SPD) gdim = m;
     else if (o.decomp == SMA_TUCKER_ROWCOL) gdim = (m > n ? m : n);
     else return SMA_ERR_UNSUPPORTED;
     if ((o.decomp == SMA_TUCKER_SHARED_U || o.decomp == SMA_TUCKER_SPD) && m != n)
       return SMA_ERR_ARG;
+    if (P.sk > 0 && o.fixed_rank > p) return SMA_ERR_ARG;
     P.gdim = gdim;
     P.gstride = (size_t)gdim * gdim;
-    SMA_TRY(mem.alloc(&P.X64, mnp));
-    SMA_TRY(mem.alloc(&P.Xu, mnp));
+    if (P.sk == 0) {
+      // the fp64 copy of X the Grams are formed from (the sketch forms its own)
+      SMA_TRY(mem.alloc(&P.X64, mnp));
+      SMA_TRY(mem.alloc(&P.Xu, mnp));
+    }
     SMA_TRY(mem.alloc(&P.Wg, (size_t)gdim * gdim * 2));
     SMA_TRY(mem.alloc(&P.gW, (size_t)gdim * gdim));
     SMA_TRY(mem.alloc(&P.gram, (size_t)gdim * gdim * 2));
@@ -645,6 +661,18 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     SMA_TRY(mem.alloc(&P.off, 3));
     SMA_TRY(mem.alloc(&P.orth, 2));
     P.n_orth = (o.decomp == SMA_TUCKER_ROWCOL) ? 2 : 1;
+    if (P.sk > 0) {
+      const int s2 = P.sk * P.sk;
+      SMA_TRY(mem.alloc(&P.Om, (size_t)m * P.sk));
+      SMA_TRY(mem.alloc(&P.Ps, (size_t)n * P.sk));
+      SMA_TRY(mem.alloc(&P.Ysk, (size_t)s2 * p));
+      SMA_TRY(mem.alloc(&P.Y64, (size_t)s2 * p));
+      SMA_TRY(mem.alloc(&P.Ytmp, (size_t)P.sk * n * p));
+      std::vector<T> om(o.sketch_omega, o.sketch_omega + (size_t)m * P.sk);
+      std::vector<T> ps(o.sketch_psi, o.sketch_psi + (size_t)n * P.sk);
+      SMA_CK(cudaMemcpy(P.Om, om.data(), om.size() * sizeof(T), cudaMemcpyHostToDevice));
+      SMA_CK(cudaMemcpy(P.Ps, ps.data(), ps.size() * sizeof(T), cudaMemcpyHostToDevice));
+    }
     if (o.decomp == SMA_TUCKER_BLOCKMODE) {
       SMA_TRY(mem.alloc(&P.F1, (size_t)p * p));        // V (p x r)
       SMA_TRY(mem.alloc(&P.D, mnp));                   // G_j slices (m x n x r)
@@ -1032,8 +1060,10 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P, bool truncated) {
 // (eigenvalues), rank written to ranks[slot] by the truncation kernel.
 template <typename T>
 sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_t y_rs,
-                       int64_t y_cs, int nb1, int64_t y_b1, double tol_share) {
+                       int64_t y_cs, int nb1, int64_t y_b1, double tol_share,
+                       const double* Ysrc = nullptr) {
   cudaStream_t st = h->st;
+  if (!Ysrc) Ysrc = P.X64;
   double* G = P.gram + (size_t)slot * P.gstride;
   stage_begin(h, SMA_STAGE_TRANSFORM);
   {
@@ -1042,14 +1072,14 @@ sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_
     GemmParams<double> g;
     g.M = rows; g.N = rows;
     if (nb1 > 1) {
-      SMA_K(permute3(P.X64, y_rs, y_cs, y_b1, rows, K, nb1, P.Xu, st));
+      SMA_K(permute3(Ysrc, y_rs, y_cs, y_b1, rows, K, nb1, P.Xu, st));
       g.K = K * nb1;
       g.A = P.Xu; g.a_rs = 1; g.a_cs = rows;
       g.B = P.Xu; g.b_rs = rows; g.b_cs = 1;
     } else {
       g.K = K;
-      g.A = P.X64; g.a_rs = y_rs; g.a_cs = y_cs;
-      g.B = P.X64; g.b_rs = y_cs; g.b_cs = y_rs;
+      g.A = Ysrc; g.a_rs = y_rs; g.a_cs = y_cs;
+      g.B = Ysrc; g.b_rs = y_cs; g.b_cs = y_rs;
     }
     g.C = G; g.c_rs = 1; g.c_cs = rows;
     // G = Y Y^T has few output tiles: split K so that about two CTAs per SM
@@ -1105,18 +1135,74 @@ sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_
   return SMA_OK;
 }
 
+// Section 6.3, randomized block-index factor: the sketch Y_k = Omega^T X_k Psi
+// (sk x sk per block), the sk^2 x sk^2 Gram H = Y_(3)^T Y_(3) of its
+// block-index unfolding (p x sk^2) and its eigenpairs (W, sigma^2), then the
+// r = fixed_rank leading left singular vectors of the unfolding as
+// V = Y_(3) W_r Sigma_r^-1 (fp64, p x r, ld p) in the second Gram slot of gvec.
+template <typename T>
+sma_status sketch_factor(sma_ctx* h, Prob<T>& P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p, sk = P.sk, s2 = sk * sk;
+  stage_begin(h, SMA_STAGE_TRANSFORM);
+  {
+    // Ytmp_k = Omega^T X_k  (sk x n)
+    GemmParams<T> g;
+    g.M = sk; g.N = n; g.K = m;
+    g.A = P.Om; g.a_rs = m; g.a_cs = 1;
+    g.B = P.X; g.b_rs = 1; g.b_cs = m; g.b_b1 = (int64_t)m * n;
+    g.C = P.Ytmp; g.c_rs = 1; g.c_cs = sk; g.c_b1 = (int64_t)sk * n;
+    g.nb1 = p;
+    SMA_K(contract<T>(h, g));
+    // Y_k = Ytmp_k Psi  (sk x sk)
+    GemmParams<T> g2;
+    g2.M = sk; g2.N = sk; g2.K = n;
+    g2.A = P.Ytmp; g2.a_rs = 1; g2.a_cs = sk; g2.a_b1 = (int64_t)sk * n;
+    g2.B = P.Ps; g2.b_rs = 1; g2.b_cs = n;
+    g2.C = P.Ysk; g2.c_rs = 1; g2.c_cs = sk; g2.c_b1 = s2;
+    g2.nb1 = p;
+    SMA_K(contract<T>(h, g2));
+    SMA_K(convert<double, T>(P.Ysk, P.Y64, (int64_t)s2 * p, st));
+  }
+  stage_end(h);
+  // H = Y_(3)^T Y_(3): rows e (stride 1), K = p (stride sk^2); its eigenpairs
+  // and the rank (fixed_rank, at most sk^2)
+  SMA_TRY(gram_factor(h, P, 0, s2, p, 1, s2, 1, 0, 1.0, P.Y64));
+  stage_begin(h, SMA_STAGE_FACTORS);
+  double* V = P.gvec + P.gstride;
+  SMA_CK(cudaMemsetAsync(V, 0, sizeof(double) * (size_t)p * p, st));
+  {
+    // V(k, j) = sum_e Y_(3)(k, e) W(e, j), j < r
+    GemmParams<double> g;
+    g.M = p; g.N = s2; g.K = s2; g.dN = P.iscal + 2; g.dstride = 0;
+    g.A = P.Y64; g.a_rs = s2; g.a_cs = 1;
+    g.B = P.gvec; g.b_rs = 1; g.b_cs = s2;
+    g.C = V; g.c_rs = 1; g.c_cs = p;
+    SMA_K(gemm<double>(g, st));
+  }
+  SMA_K(scale_cols_rsqrt(V, p, p, P.gsig, P.iscal + 2, st));
+  stage_end(h);
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status compress_tucker(sma_ctx* h, Prob<T>& P) {
   cudaStream_t st = h->st;
   const int m = P.m, n = P.n, p = P.p;
   const int64_t mn = (int64_t)m * n;
   const sma_decomp d = h->opt.decomp;
-  SMA_K(convert<double, T>(P.X, P.X64, mn * p, st));
+  if (P.X64) SMA_K(convert<double, T>(P.X, P.X64, mn * p, st));
   if (d == SMA_TUCKER_BLOCKMODE) {
-    // block-index unfolding: rows k, K = mn; Y(k, e) = X[e + mn k]
-    SMA_TRY(gram_factor(h, P, 0, p, (int)mn, mn, 1, 1, 0, 1.0));
-    stage_begin(h, SMA_STAGE_FACTORS);
-    SMA_K(convert<T, double>(P.gvec, P.F1, (int64_t)p * p, st));  // V = leading columns
+    if (P.sk > 0) {
+      SMA_TRY(sketch_factor(h, P));
+      stage_begin(h, SMA_STAGE_FACTORS);
+      SMA_K(convert<T, double>(P.gvec + P.gstride, P.F1, (int64_t)p * p, st));
+    } else {
+      // block-index unfolding: rows k, K = mn; Y(k, e) = X[e + mn k]
+      SMA_TRY(gram_factor(h, P, 0, p, (int)mn, mn, 1, 1, 0, 1.0));
+      stage_begin(h, SMA_STAGE_FACTORS);
+      SMA_K(convert<T, double>(P.gvec, P.F1, (int64_t)p * p, st));  // V = leading columns
+    }
     // G = X x3 V^T: G_mat (mn x r) = X_mat (mn x p) V (p x r)
     GemmParams<T> g;
     g.M = (int)mn; g.N = p; g.K = p; g.dN = P.iscal + 2; g.dstride = 0;
@@ -2006,7 +2092,10 @@ sma_status export_one(sma_ctx* h, Prob<T>& P, int which, void* dst, int64_t coun
     case 2:
       if (h->opt.decomp == SMA_HOSVD_MULTILEVEL) { src = P.gsig; n = (int64_t)P.gdim * 3; }
       else if (h->opt.decomp == SMA_TSVDM) { src = P.sigma; n = (int64_t)P.rc * P.p; }
-      else { src = P.gsig; n = h->opt.decomp == SMA_TUCKER_BLOCKMODE ? P.p : P.m; }
+      else {
+        src = P.gsig;
+        n = h->opt.decomp == SMA_TUCKER_BLOCKMODE ? (P.sk > 0 ? P.sk * P.sk : P.p) : P.m;
+      }
       es = sizeof(double);
       break;
     case 3: src = P.Tt; n = mnp; break;
@@ -2146,6 +2235,17 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   if (opt->fixed_rank < 0 || !(opt->rel_tol >= 0.0)) return SMA_ERR_ARG;
   if ((int)opt->precondition < 0 || opt->precondition > SMA_PRECOND_QRCP) return SMA_ERR_ARG;
   if (opt->autotune < 0 || opt->autotune > 1) return SMA_ERR_ARG;
+  if (opt->sketch_cols < 0) return SMA_ERR_ARG;
+  if (opt->sketch_cols > 0) {
+    // Section 6.3's randomized factor: block-index mode, a fixed rank the
+    // sketch can hold, both maps, one (m, n) for all problems
+    if (opt->decomp != SMA_TUCKER_BLOCKMODE || !opt->sketch_omega || !opt->sketch_psi)
+      return SMA_ERR_ARG;
+    if (opt->fixed_rank < 1 || (int64_t)opt->fixed_rank > (int64_t)opt->sketch_cols * opt->sketch_cols)
+      return SMA_ERR_ARG;
+    for (int i = 1; i < nprob; ++i)
+      if (prob[i].m != prob[0].m || prob[i].n != prob[0].n) return SMA_ERR_ARG;
+  }
   // host-side validation of every problem before any CUDA call
   for (int i = 0; i < nprob; ++i) {
     std::vector<int64_t> eta;

@@ -1487,6 +1487,23 @@ JacobiPlan jacobi_coop_plan(int rows, int max_smem) {
   pl.smem = (((size_t)2 * pl.bcols * pl.ldS * sizeof(T) + 15) & ~(size_t)15) +
             (size_t)p2 * (sizeof(double) + sizeof(int));
   if (pl.smem > (size_t)max_smem) pl.smem = 0;
+  // every CTA of the launch must be resident at once (the rounds wait on one
+  // another): otherwise the plan is unusable and the caller takes the
+  // single-CTA kernel
+  if (pl.smem > 0) {
+    void (*kern)(const JacobiParams<T>, const CoopSync) = jacobi_coop_kernel<T>;
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem) !=
+            cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, pl.threads, pl.smem) !=
+            cudaSuccess ||
+        (int64_t)per_sm * nsm < pl.block_mode) {
+      cudaGetLastError();
+      pl.smem = 0;
+    }
+  }
   return pl;
 }
 

@@ -19,6 +19,11 @@ cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStre
 // out[e] = sum_s part[e + s count] for e < count, s < nslab (fixed order: the
 // split-K partial products of a Gram).
 cudaError_t sum_slabs(const double* part, int nslab, int64_t count, double* out, cudaStream_t st);
+// V[:, j] *= 1 / sqrt(ev[j]) for j < *r (device count), V with leading
+// dimension ld (at most ld columns), rows entries per column; a column whose
+// ev[j] <= 0 is zeroed.
+cudaError_t scale_cols_rsqrt(double* V, int64_t ld, int rows, const double* ev, const int* r,
+                             cudaStream_t st);
 int gather_parts(int m, int n, int p);
 // ||X - T||_F^2 over `count` elements (fp64 accumulation; nparts partial sums
 // as for gather); two launches.  Tt == nullptr gives ||X||_F^2.

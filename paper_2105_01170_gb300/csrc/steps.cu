@@ -453,6 +453,24 @@ __global__ void sum_slabs_kernel(const double* __restrict__ part, int nslab, int
   }
 }
 
+// V[:, j] /= sqrt(ev[j]) for j < *r (zero column where ev[j] <= 0).
+__global__ void scale_cols_rsqrt_kernel(double* V, int64_t ld, int rows, const double* ev,
+                                        const int* r) {
+  const int j = blockIdx.x;
+  if (j >= *r) return;
+  const double e = ev[j];
+  const double f = e > 0.0 ? 1.0 / sqrt(e) : 0.0;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) V[i + j * ld] *= f;
+}
+
+cudaError_t scale_cols_rsqrt(double* V, int64_t ld, int rows, const double* ev, const int* r,
+                             cudaStream_t st) {
+  // one CTA per possible column; columns at or past *r return at once
+  const int cols = (int)(ld < 65535 ? ld : 65535);
+  scale_cols_rsqrt_kernel<<<cols, 256, 0, st>>>(V, ld, rows, ev, r);
+  return cudaGetLastError();
+}
+
 cudaError_t sum_slabs(const double* part, int nslab, int64_t count, double* out, cudaStream_t st) {
   int64_t grid = (count + 255) / 256;
   if (grid > 4096) grid = 4096;

@@ -242,15 +242,30 @@ def block_tridiag_batch(count: int = 512, ell_range=(16, 256),
         ell = int(g.integers(ell_range[0], ell_range[1] + 1))
         m = int(m_choices[int(g.integers(0, len(m_choices)))])
         K = int(g.integers(kmax_range[0], kmax_range[1] + 1))
-        bm = block_banded_map(ell, 1)
-        p = int(bm.max()) + 1
-        D = g.standard_normal((K, m, m))
-        c = g.standard_normal((p, K))
-        blocks = np.einsum("pk,kij->pij", c, D) + noise * g.standard_normal((p, m, m))
-        mask = (g.random((m, m)) >= drop).astype(np.float64)
-        blocks *= mask[None]
-        out.append(Problem(f"tridiag_{idx}", blocks, bm, {"K": K, "mask": mask}))
+        out.append(_tridiag_problem(g, f"tridiag_{idx}", ell, m, K, noise, drop))
     return out
+
+
+def _tridiag_problem(g: np.random.Generator, name: str, ell: int, m: int, K: int,
+                     noise: float, drop: float) -> Problem:
+    bm = block_banded_map(ell, 1)
+    p = int(bm.max()) + 1
+    D = g.standard_normal((K, m, m))
+    c = g.standard_normal((p, K))
+    blocks = np.einsum("pk,kij->pij", c, D) + noise * g.standard_normal((p, m, m))
+    mask = (g.random((m, m)) >= drop).astype(np.float64)
+    blocks *= mask[None]
+    return Problem(name, blocks, bm, {"K": K, "mask": mask})
+
+
+def block_tridiag_kron(ell: int, m: int, K: int = 5, noise: float = 1e-4, drop: float = 0.3,
+                       seed_index: int = 3, salt: int = 6) -> Problem:
+    """One block-tridiagonal matrix of the batched workload's kind with chosen
+    sizes (ell blocks of m x m, Kron rank K): the stand-in for the largest
+    SuiteSparse matrix of the Kronecker-sum table, compressed there with the
+    randomized block-index factor."""
+    return _tridiag_problem(rng_for(seed_index, salt=salt), f"tridiag_{ell}x{m}", ell, m, K,
+                            noise, drop)
 
 
 # ---------------------------------------------------------------------------
@@ -292,6 +307,14 @@ def random_orthogonal(p: int, seed_index: int, salt: int = 3) -> np.ndarray:
     g = rng_for(seed_index, salt=salt)
     Q, R = np.linalg.qr(g.standard_normal((p, p)))
     return Q * np.sign(np.diag(R))[None, :]
+
+
+def gaussian_sketch(m: int, n: int, s: int, seed_index: int = 7,
+                    salt: int = 5) -> tuple[np.ndarray, np.ndarray]:
+    """Independent N(0,1) maps Omega (m x s) and Psi (n x s) for the
+    randomized block-index factor (Section 6.3)."""
+    g = rng_for(seed_index, salt=salt)
+    return g.standard_normal((m, s)), g.standard_normal((n, s))
 
 
 def planted_tsvdm_tensor(m: int, n: int, p: int, ranks, seed_index: int = 9,

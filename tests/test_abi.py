@@ -98,6 +98,39 @@ def test_spd_split_is_validated_before_any_device_call(lib):
     assert _create([(3, 3, 2, 2, 5, G.toeplitz_map(3))], decomp=6)[0] == S.SMA_ERR_ARG
 
 
+def test_sketch_options_are_validated(lib):
+    """The randomized block-index factor needs block-index mode, both maps, a
+    fixed rank the sketch can hold (<= s^2 and <= p) and one (m, n)."""
+    bm = G.toeplitz_map(4)
+    om = np.zeros((3, 2))
+    keep = []
+
+    def create(probs, s=2, omega=True, psi=True, **kw):
+        opt = S.sma_options(kw.get("prec", S.SMA_FP64), kw.get("decomp", S.SMA_TUCKER_BLOCKMODE),
+                            S.SMA_M_DCT2, S.SMA_INPUT_DENSE, None, kw.get("fixed_rank", 2), 0.0, 0,
+                            None, 0, 0, S.SMA_PRECOND_AUTO, 0, s,
+                            om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if omega else None,
+                            om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if psi else None)
+        structs = []
+        for ell, m, n, p, b in probs:
+            b = np.ascontiguousarray(np.asarray(b, dtype=np.int32).ravel(order="F"))
+            keep.append(b)
+            structs.append(S.sma_problem(ell, ell, m, n, p,
+                                         b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                         1, None, None, None, None))
+        return S.sma_create(structs, opt)[0]
+
+    one = [(4, 3, 3, 7, bm)]
+    assert create(one, decomp=S.SMA_TSVDM) == S.SMA_ERR_ARG
+    assert create(one, decomp=S.SMA_TUCKER_SHARED_U) == S.SMA_ERR_ARG
+    assert create(one, fixed_rank=0) == S.SMA_ERR_ARG
+    assert create(one, fixed_rank=5) == S.SMA_ERR_ARG          # s^2 = 4 < 5
+    assert create(one, omega=False) == S.SMA_ERR_ARG
+    assert create(one, psi=False) == S.SMA_ERR_ARG
+    assert create(one, s=-1) == S.SMA_ERR_ARG
+    assert create(one + [(4, 2, 3, 7, bm)]) == S.SMA_ERR_ARG  # another m
+
+
 def test_null_handle_calls(lib):
     assert S.sma_destroy(None) == S.SMA_ERR_ARG
     assert S.sma_apply(None, 0, 0, 1, 0, 1, 1) == S.SMA_ERR_ARG
