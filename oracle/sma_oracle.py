@@ -427,6 +427,72 @@ def tucker1_kron_terms(t: Tucker1Block, block_map: np.ndarray):
     return [(struct_E(list(t.V[:, j]), block_map, p), t.G[:, :, j]) for j in range(t.rank)]
 
 
+# ---------------------------------------------------------------------------
+# CP (Kruskal) compressor: Sections 2.3, 4.1 (Theorem tildeA, Corollary
+# kronsumcp) and 5 (Theorem blockCP)
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class CPModel:
+    Xf: np.ndarray         # m x r
+    Yf: np.ndarray         # p x r (block index)
+    Zf: np.ndarray         # n x r
+    fit_err: list          # ||X - T||_F after each iteration
+    err: float
+    rel_err: float
+
+    def tensor_approx(self) -> np.ndarray:
+        """Frontal slice k of the Kruskal tensor: Xf diag(Yf[k, :]) Zf^T."""
+        return np.einsum("aj,kj,bj->abk", self.Xf, self.Yf, self.Zf, optimize=True)
+
+
+def cp_als(X: np.ndarray, Xf0: np.ndarray, Zf0: np.ndarray, iters: int) -> CPModel:
+    """CP by alternating least squares (the method the paper points to for
+    Section 2.3's decomposition): each factor in turn is the least-squares
+    solution with the other two fixed, through the normal equations whose
+    matrix is the Hadamard product of the other two factors' Gram matrices.
+    Our orientation: slice k of X (m x n x p) is approximated by
+    Xf diag(Yf[k, :]) Zf^T.  Order within an iteration: Yf (from the given
+    Xf, Zf), then Xf, then Zf; the initial Xf, Zf are inputs, there is no
+    column normalisation, and `iters` iterations are run."""
+    Xf, Zf = Xf0.astype(np.float64).copy(), Zf0.astype(np.float64).copy()
+    m, n, p = X.shape
+    fit = []
+    Yf = None
+    for _ in range(iters):
+        # Yf[k, j] = sum_ab X[a, b, k] Xf[a, j] Zf[b, j], then (Xf^T Xf * Zf^T Zf)^-1
+        M3 = np.einsum("abk,aj,bj->kj", X, Xf, Zf, optimize=True)
+        Yf = np.linalg.solve((Xf.T @ Xf) * (Zf.T @ Zf), M3.T).T
+        M1 = np.einsum("abk,bj,kj->aj", X, Zf, Yf, optimize=True)
+        Xf = np.linalg.solve((Zf.T @ Zf) * (Yf.T @ Yf), M1.T).T
+        M2 = np.einsum("abk,aj,kj->bj", X, Xf, Yf, optimize=True)
+        Zf = np.linalg.solve((Xf.T @ Xf) * (Yf.T @ Yf), M2.T).T
+        T = np.einsum("aj,kj,bj->abk", Xf, Yf, Zf, optimize=True)
+        fit.append(float(np.linalg.norm((X - T).ravel())))
+    normX = float(np.linalg.norm(X.ravel()))
+    return CPModel(Xf, Yf, Zf, fit, fit[-1], fit[-1] / normX)
+
+
+def cp_kron_terms(c: CPModel, block_map: np.ndarray):
+    """Corollary kronsumcp with F = Yf, G = I: A_hat = sum_j struct_E(Yf[:, j])
+    (x) Xf[:, j] Zf[:, j]^T."""
+    p = c.Yf.shape[0]
+    return [(struct_E(list(c.Yf[:, j]), block_map, p), np.outer(c.Xf[:, j], c.Zf[:, j]))
+            for j in range(c.Yf.shape[1])]
+
+
+def cp_blr(c: CPModel, block_map: np.ndarray) -> np.ndarray:
+    """Theorem blockCP: (I (x) Q_X) struct_E(F_k) (I (x) Q_Z^T), Xf = Q_X R_X,
+    Zf = Q_Z R_Z thin QR, F_k = R_X diag(Yf[k, :]) R_Z^T (dense, for checks)."""
+    QX, RX = np.linalg.qr(c.Xf)
+    QZ, RZ = np.linalg.qr(c.Zf)
+    p = c.Yf.shape[0]
+    F = [RX @ np.diag(c.Yf[k]) @ RZ.T for k in range(p)]
+    ell, q = block_map.shape
+    return np.kron(np.eye(ell), QX) @ struct_E(F, block_map, p) @ np.kron(np.eye(q), QZ).T
+
+
 @dataclass
 class SharedU:
     U: np.ndarray          # m x r

@@ -546,3 +546,58 @@ def test_sketch_error_is_a_projection_residual_and_not_below_the_optimum():
         pyth = np.sqrt(max(np.sum(X * X) - np.sum(s.G * s.G), 0.0))
         assert abs(s.err - pyth) <= 1e-9 * np.linalg.norm(X)
         assert s.err >= O.tucker1_blockmode(X, rank=r).err * (1 - 1e-12)
+
+
+# ------------------------------------------- Sections 2.3, 4.1, 5: CP by alternating least squares
+
+def _planted_cp(m, n, p, r, seed, noise=0.0):
+    g = np.random.default_rng(seed)
+    Xf, Yf, Zf = g.standard_normal((m, r)), g.standard_normal((p, r)), g.standard_normal((n, r))
+    X = np.einsum("aj,kj,bj->abk", Xf, Yf, Zf)
+    if noise:
+        X = X + noise * g.standard_normal(X.shape)
+    return X, Xf, Yf, Zf, g
+
+
+def test_cp_als_recovers_a_planted_kruskal_tensor():
+    """An exact rank-3 Kruskal tensor, started near its factors: the fit
+    reaches rounding level and the product tensor is the planted one."""
+    X, Xf, Yf, Zf, g = _planted_cp(7, 6, 9, 3, 21)
+    c = O.cp_als(X, Xf + 0.05 * g.standard_normal(Xf.shape), Zf + 0.05 * g.standard_normal(Zf.shape), 40)
+    assert c.err <= 1e-10 * np.linalg.norm(X)
+    assert np.allclose(c.tensor_approx(), X, atol=1e-10 * np.abs(X).max())
+
+
+def test_cp_als_rank_one_is_exact_in_one_iteration():
+    """For a rank-1 tensor each least-squares step is exact once the other two
+    factors are parallel to the true ones: from the true Xf, Zf one iteration
+    reproduces X."""
+    X, Xf, Yf, Zf, _ = _planted_cp(5, 4, 6, 1, 22)
+    c = O.cp_als(X, 2.0 * Xf, -0.5 * Zf, 1)
+    assert c.err <= 1e-12 * np.linalg.norm(X)
+
+
+def test_cp_als_fit_never_increases():
+    """Every ALS step solves its least-squares problem exactly, so the error
+    after each iteration is non-increasing."""
+    X, _, _, _, g = _planted_cp(8, 7, 10, 4, 23, noise=0.3)
+    c = O.cp_als(X, g.standard_normal((8, 3)), g.standard_normal((7, 3)), 25)
+    f = np.asarray(c.fit_err)
+    assert np.all(np.diff(f) <= 1e-12 * f[0])
+    assert c.err == f[-1]
+
+
+def test_cp_kronecker_sum_and_block_form_equal_M_E():
+    """Corollary kronsumcp and Theorem blockCP both reproduce M_E of the
+    Kruskal tensor (block Toeplitz map, so the C_j are Toeplitz)."""
+    ell, m, n = 5, 4, 3
+    bm = G.toeplitz_map(ell)
+    p = int(bm.max()) + 1
+    X, _, _, _, g = _planted_cp(m, n, p, 3, 24, noise=0.1)
+    c = O.cp_als(X, g.standard_normal((m, 2)), g.standard_normal((n, 2)), 5)
+    dense = O.M_E(c.tensor_approx(), bm)
+    terms = O.cp_kron_terms(c, bm)
+    assert np.allclose(O.kron_dense(terms), dense, atol=1e-12 * np.abs(dense).max())
+    assert np.allclose(O.cp_blr(c, bm), dense, atol=1e-12 * np.abs(dense).max())
+    for C, _ in terms:       # each C_j keeps the block-Toeplitz structure
+        assert np.allclose(C[1:, 1:], C[:-1, :-1])
