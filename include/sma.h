@@ -98,7 +98,19 @@ typedef enum {
    * tensor_err and ranks in sma_result refer to the tensor of the A_k
    * (||A - A_hat||_F by Lemma 1, A = sum_k E_k (x) A_k).  A T_0 that is
    * not numerically SPD sets SMA_ERR_NOT_SPD in device_status (L = 0).   */
-  SMA_TUCKER_SPD = 5
+  SMA_TUCKER_SPD = 5,
+  /* CP (Kruskal) form by alternating least squares (Section 2.3; Theorem
+   * tildeA and Corollary kronsumcp): slice k of X is approximated by
+   * Xf diag(Yf[k, :]) Zf^T with r = fixed_rank terms (1 <= r <= 64, r <= p),
+   * cp_iters iterations from the caller's initial Xf, Zf (each iteration
+   * updates Yf, then Xf, then Zf as least-squares solutions through the
+   * normal equations, whose r x r matrices are solved in fp64; no column
+   * normalisation).  Factored result: the Kronecker sum
+   *   A_hat = sum_j struct_E(Yf[:, j]) (x) Xf[:, j] Zf[:, j]^T,
+   * applied and reconstructed like SMA_TUCKER_BLOCKMODE; tensor_err is
+   * ||X - T||_F measured directly.  A singular normal-equations matrix sets
+   * SMA_ERR_NONFINITE.  All problems must have the same m and n.           */
+  SMA_CP_ALS = 6
 } sma_decomp;
 
 typedef enum { SMA_M_DCT2 = 0, SMA_M_IDENTITY = 1, SMA_M_USER = 2 } sma_transform;
@@ -172,6 +184,11 @@ typedef struct {
   int32_t sketch_cols;
   const double* sketch_omega;   /* host, m x s column-major (e.g. N(0,1))  */
   const double* sketch_psi;     /* host, n x s column-major                */
+  /* SMA_CP_ALS: iterations (>= 1) and the initial factors, host, column-
+   * major: cp_init_x m x fixed_rank, cp_init_z n x fixed_rank.             */
+  int32_t cp_iters;
+  const double* cp_init_x;
+  const double* cp_init_z;
 } sma_options;
 
 typedef struct {
@@ -244,7 +261,9 @@ sma_status sma_apply(sma_handle h, int32_t i, const void* X, int64_t ldx,
  *   3 = T (m*n*p, the approximation tensor, after sma_reconstruct)
  *   4 = Tucker factor of the compressed mode (rows x rank, column-major)
  *   5 = SMA_TUCKER_SPD: the Cholesky factor L of T_0 (m x m, column-major,
- *       zero above the diagonal)                                          */
+ *       zero above the diagonal)
+ *   6, 7 = SMA_CP_ALS: the factors Xf (m x r) and Zf (n x r); the block-
+ *       index factor Yf is buffer 4 (p x p storage, the first r columns)   */
 sma_status sma_export(sma_handle h, int32_t i, int32_t which, void* dst,
                       int64_t count, int64_t* avail);
 
@@ -252,7 +271,8 @@ sma_status sma_export(sma_handle h, int32_t i, int32_t which, void* dst,
 typedef enum {
   SMA_STAGE_GATHER = 0,     /* step 1: struct_E gather and ||X||_F              */
   SMA_STAGE_TRANSFORM = 1,  /* X x3 M (t-SVDM) or the unfolding Gram (Tucker)   */
-  SMA_STAGE_SVD = 2,        /* Jacobi SVD of the slices / Gram eigen-solve      */
+  SMA_STAGE_SVD = 2,        /* Jacobi SVD of the slices / Gram eigen-solve /
+                               the CP iterations                               */
   SMA_STAGE_TRUNCATE = 3,   /* rank selection and error                         */
   SMA_STAGE_FACTORS = 4,    /* truncated slices / core, struct_E terms          */
   SMA_STAGE_REPORT = 5,     /* orthogonality check                              */

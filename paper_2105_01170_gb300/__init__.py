@@ -30,10 +30,12 @@ SMA_ERR_NOT_SPD = 10
 SMA_FP64, SMA_MIXED = 0, 1
 SMA_TSVDM, SMA_TUCKER_BLOCKMODE, SMA_TUCKER_SHARED_U, SMA_TUCKER_ROWCOL, SMA_HOSVD_MULTILEVEL = 0, 1, 2, 3, 4
 SMA_TUCKER_SPD = 5
+SMA_CP_ALS = 6
 SMA_M_DCT2, SMA_M_IDENTITY, SMA_M_USER = 0, 1, 2
 SMA_INPUT_DENSE, SMA_INPUT_BLOCKS = 0, 1
 SMA_PRECOND_AUTO, SMA_PRECOND_NONE, SMA_PRECOND_QRCP = 0, 1, 2
 EXPORT_X, EXPORT_XHAT, EXPORT_SIGMA, EXPORT_T, EXPORT_FACTOR, EXPORT_CHOL = 0, 1, 2, 3, 4, 5
+EXPORT_CP_X, EXPORT_CP_Z = 6, 7
 
 EXPORTED = ("sma_create", "sma_compress", "sma_get_result", "sma_get_ranks", "sma_reconstruct",
             "sma_apply", "sma_export", "sma_profile", "sma_slice_svd_noalloc", "sma_destroy",
@@ -61,7 +63,10 @@ class sma_options(ctypes.Structure):
                 ("precondition", ctypes.c_int), ("autotune", ctypes.c_int32),
                 ("sketch_cols", ctypes.c_int32),
                 ("sketch_omega", ctypes.POINTER(ctypes.c_double)),
-                ("sketch_psi", ctypes.POINTER(ctypes.c_double))]
+                ("sketch_psi", ctypes.POINTER(ctypes.c_double)),
+                ("cp_iters", ctypes.c_int32),
+                ("cp_init_x", ctypes.POINTER(ctypes.c_double)),
+                ("cp_init_z", ctypes.POINTER(ctypes.c_double))]
 
 
 class sma_result(ctypes.Structure):
@@ -235,7 +240,7 @@ class Handle:
     def __init__(self, problems, prec=SMA_MIXED, decomp=SMA_TSVDM, mkind=SMA_M_DCT2,
                  layout=SMA_INPUT_DENSE, M_user=None, fixed_rank=0, rel_tol=0.0,
                  max_sweeps=0, stream=None, profile=False, graph=False,
-                 precondition=None, autotune=False, sketch=None):
+                 precondition=None, autotune=False, sketch=None, cp_init=None, cp_iters=0):
         self._keep = []
         structs = []
         for pr in problems:
@@ -268,10 +273,19 @@ class Handle:
             sk_cols = Om.shape[1]
             sk_om = Om.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             sk_ps = Ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        # cp_init = (Xf0, Zf0): the initial CP factors, m x r and n x r
+        cp_x = cp_z = None
+        if cp_init is not None:
+            X0 = np.asfortranarray(np.asarray(cp_init[0], dtype=np.float64))
+            Z0 = np.asfortranarray(np.asarray(cp_init[1], dtype=np.float64))
+            self._keep += [X0, Z0]
+            cp_x = X0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            cp_z = Z0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.opt = sma_options(prec, decomp, mkind, layout, mu, int(fixed_rank), float(rel_tol),
                                int(max_sweeps), sptr, 1 if profile else 0, 1 if graph else 0,
                                SMA_PRECOND_AUTO if precondition is None else int(precondition),
-                               1 if autotune else 0, sk_cols, sk_om, sk_ps)
+                               1 if autotune else 0, sk_cols, sk_om, sk_ps, int(cp_iters), cp_x,
+                               cp_z)
         self.nprob = len(structs)
         self.prec = prec
         st, self.h = sma_create(structs, self.opt)

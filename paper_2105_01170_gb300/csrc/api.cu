@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <initializer_list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -177,6 +179,17 @@ struct Prob {
   // randomized block-index factor (Section 6.3): Omega (m x sk), Psi (n x sk),
   // the sketch Y (sk x sk x p, T and fp64) and Omega^T X_k (sk x n x p)
   int sk = 0;
+  // CP by alternating least squares: the factors Xf (m x r), Zf (n x r), their
+  // initial values, and the Khatri-Rao / contraction / per-block workspaces
+  // (Yf, p x r, lives in F1)
+  int cp_r = 0;
+  T* cXf = nullptr;
+  T* cZf = nullptr;
+  T* cXf0 = nullptr;
+  T* cZf0 = nullptr;
+  T* cKR = nullptr;
+  T* cM = nullptr;
+  T* cSlab = nullptr;
   T* Om = nullptr;
   T* Ps = nullptr;
   T* Ysk = nullptr;
@@ -629,6 +642,30 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     SMA_TRY(mem.alloc(&P.D, mnp));
     SMA_TRY(mem.alloc(&P.C, (size_t)P.ell * P.q * p));
     SMA_CK(cudaMemset(P.C, 0, sizeof(T) * (size_t)P.ell * P.q * p));   // zero off the structure
+  } else if (o.decomp == SMA_CP_ALS) {
+    const int r = o.fixed_rank;
+    if (r > p) return SMA_ERR_ARG;
+    P.cp_r = r;
+    const size_t big = std::max({(size_t)m * n, (size_t)n * p, (size_t)m * p});
+    SMA_TRY(mem.alloc(&P.cXf, (size_t)m * r));
+    SMA_TRY(mem.alloc(&P.cZf, (size_t)n * r));
+    SMA_TRY(mem.alloc(&P.cXf0, (size_t)m * r));
+    SMA_TRY(mem.alloc(&P.cZf0, (size_t)n * r));
+    SMA_TRY(mem.alloc(&P.cKR, big * r));
+    SMA_TRY(mem.alloc(&P.cM, (size_t)std::max({m, n, p}) * r));
+    SMA_TRY(mem.alloc(&P.cSlab, (size_t)p * n * r));
+    std::vector<T> x0(o.cp_init_x, o.cp_init_x + (size_t)m * r);
+    std::vector<T> z0(o.cp_init_z, o.cp_init_z + (size_t)n * r);
+    SMA_CK(cudaMemcpy(P.cXf0, x0.data(), x0.size() * sizeof(T), cudaMemcpyHostToDevice));
+    SMA_CK(cudaMemcpy(P.cZf0, z0.data(), z0.size() * sizeof(T), cudaMemcpyHostToDevice));
+    SMA_TRY(mem.alloc(&P.F1, (size_t)p * p));        // Yf (p x r)
+    SMA_TRY(mem.alloc(&P.D, mnp));                   // Xf[:, j] Zf[:, j]^T (m x n x r)
+    SMA_TRY(mem.alloc(&P.C, (size_t)P.ell * P.q * p));
+    SMA_CK(cudaMemset(P.C, 0, sizeof(T) * (size_t)P.ell * P.q * p));
+    SMA_TRY(mem.alloc(&P.orth, 1));
+    SMA_TRY(mem.alloc(&P.sweeps, 1));
+    P.n_orth = 0;
+    P.nterms_max = p;
   } else {
     // Tucker family: fp64 Gram and its Jacobi eigen-solve
     int gdim = 0;
@@ -1396,6 +1433,70 @@ sma_status spd_congruence(sma_ctx* h, Prob<T>& P) {
   return SMA_OK;
 }
 
+// CP by alternating least squares from the given Xf, Zf: per iteration Yf,
+// then Xf, then Zf, each the least-squares solution with the other two fixed
+// (the contraction of X with the Khatri-Rao product of the other two factors,
+// solved against the Hadamard product of their Gram matrices); then the
+// Kronecker terms of Corollary kronsumcp, D_j = Xf[:, j] Zf[:, j]^T and
+// C_j = struct_E(Yf[:, j]), and the error measured on the tensor.
+template <typename T>
+sma_status compress_cp(sma_ctx* h, Prob<T>& P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p, r = P.cp_r;
+  const int64_t mn = (int64_t)m * n;
+  T* Yf = P.F1;   // p x r, ld p
+  stage_begin(h, SMA_STAGE_SVD);
+  SMA_CK(cudaMemcpyAsync(P.cXf, P.cXf0, sizeof(T) * (size_t)m * r, cudaMemcpyDeviceToDevice, st));
+  SMA_CK(cudaMemcpyAsync(P.cZf, P.cZf0, sizeof(T) * (size_t)n * r, cudaMemcpyDeviceToDevice, st));
+  for (int it = 0; it < h->opt.cp_iters; ++it) {
+    // Yf: M3 = X_(3) (Xf . Zf)  (p x r), X_(3)(k, a + m b) = X[a + m b + mn k]
+    SMA_K(khatri_rao<T>(P.cXf, m, P.cZf, n, r, P.cKR, st));
+    {
+      GemmParams<T> g;
+      g.M = p; g.N = r; g.K = (int)mn;
+      g.A = P.X; g.a_rs = mn; g.a_cs = 1;
+      g.B = P.cKR; g.b_rs = 1; g.b_cs = mn;
+      g.C = P.cM; g.c_rs = 1; g.c_cs = p;
+      SMA_K(contract<T>(h, g));
+    }
+    SMA_K(cp_solve<T>(P.cXf, m, P.cZf, n, r, P.cM, p, Yf, p, P.status, st));
+    // Xf: M1 = X_(1) (Zf . Yf)  (m x r), X_(1) = [X_1 ... X_p] (m x n p)
+    SMA_K(khatri_rao<T>(P.cZf, n, Yf, p, r, P.cKR, st));
+    {
+      GemmParams<T> g;
+      g.M = m; g.N = r; g.K = (int)((int64_t)n * p);
+      g.A = P.X; g.a_rs = 1; g.a_cs = m;
+      g.B = P.cKR; g.b_rs = 1; g.b_cs = (int64_t)n * p;
+      g.C = P.cM; g.c_rs = 1; g.c_cs = m;
+      SMA_K(contract<T>(h, g));
+    }
+    SMA_K(cp_solve<T>(P.cZf, n, Yf, p, r, P.cM, m, P.cXf, m, P.status, st));
+    // Zf: M2 = sum_k X_k^T Xf diag(Yf[k, :])  (n x r), one partial per block
+    SMA_K(khatri_rao<T>(P.cXf, m, Yf, p, r, P.cKR, st));
+    {
+      GemmParams<T> g;
+      g.M = n; g.N = r; g.K = m;
+      g.A = P.X; g.a_rs = m; g.a_cs = 1; g.a_b1 = mn;
+      g.B = P.cKR; g.b_rs = 1; g.b_cs = (int64_t)m * p; g.b_b1 = m;
+      g.C = P.cSlab; g.c_rs = 1; g.c_cs = n; g.c_b1 = (int64_t)n * r;
+      g.nb1 = p;
+      SMA_K(contract<T>(h, g));
+    }
+    SMA_K(sum_slabs_t<T>(P.cSlab, p, (int64_t)n * r, P.cM, st));
+    SMA_K(cp_solve<T>(P.cXf, m, Yf, p, r, P.cM, n, P.cZf, n, P.status, st));
+  }
+  stage_end(h);
+  stage_begin(h, SMA_STAGE_FACTORS);
+  SMA_K(khatri_rao<T>(P.cXf, m, P.cZf, n, r, P.D, st));   // D[(a + m b), j] = Xf[a, j] Zf[b, j]
+  SMA_K(set_int(P.iscal + 2, r, st));
+  SMA_K(build_struct_terms_nz<T>(P.d_nzpos, P.d_nzk, P.nnz, P.d_isq, P.ell, P.q, P.F1, p, 1, p,
+                                  P.iscal + 2, P.C, st));
+  SMA_TRY(make_T(h, P));
+  SMA_K(residual_norm2<T>(P.X, P.Tt, mn * p, P.partial, P.nparts, P.stats + 1, st));
+  stage_end(h);
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
   SMA_CK(cudaMemsetAsync(P.status, 0, sizeof(int), h->st));
@@ -1409,6 +1510,7 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
   SMA_TRY(do_gather(h, P, A, lda));
   if (P.spd) SMA_TRY(spd_congruence(h, P));
   if (h->opt.decomp == SMA_TSVDM) SMA_TRY(tsvdm_pre(h, P));
+  else if (h->opt.decomp == SMA_CP_ALS) SMA_TRY(compress_cp(h, P));
   else SMA_TRY(compress_tucker(h, P));
   P.compressed = true;
   P.dp_valid = false;
@@ -1450,7 +1552,7 @@ sma_status read_result(sma_ctx* h, Prob<T>& P, sma_result* r) {
     for (int t = 0; t < 3; ++t) r->ranks[t] = iscal[2 + t];
     r->total_rank = iscal[2] * iscal[3] * iscal[4];
     r->n_kron_terms = r->total_rank;
-  } else if (d == SMA_TUCKER_BLOCKMODE) {
+  } else if (d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS) {
     err2 = stats[1];
     r->ranks[0] = iscal[2];
     r->total_rank = iscal[2];
@@ -1791,7 +1893,7 @@ sma_status apply_core(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, in
   const sma_decomp d = h->opt.decomp;
   if (d == SMA_HOSVD_MULTILEVEL) {
     SMA_TRY(apply_multilevel(h, P, X, ldx, Yd, ldyd, nrhs));
-  } else if (d == SMA_TSVDM || d == SMA_TUCKER_BLOCKMODE) {
+  } else if (d == SMA_TSVDM || d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS) {
     // Kronecker sum Y = sum_j D_j X C_j^T (Section 2.2 vec identity).
     if (P.h_iscal[0] < 0) {
       SMA_CK(cudaStreamSynchronize(st));
@@ -1944,8 +2046,8 @@ sma_status make_T(sma_ctx* h, Prob<T>& P) {
     g.B = P.Mt; g.b_rs = 1; g.b_cs = p;
     g.C = P.Tt; g.c_rs = 1; g.c_cs = mn;
     SMA_K(gemm<T>(g, st));
-  } else if (d == SMA_TUCKER_BLOCKMODE) {
-    // T = G x3 V: T_mat = G_mat V^T
+  } else if (d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS) {
+    // T = G x3 V: T_mat = G_mat V^T (CP: G_mat = [vec(Xf_j Zf_j^T)], V = Yf)
     GemmParams<T> g;
     g.M = (int)mn; g.N = p; g.K = p; g.dK = P.iscal + 2; g.dstride = 0;
     g.A = P.D; g.a_rs = 1; g.a_cs = mn;
@@ -2092,6 +2194,7 @@ sma_status export_one(sma_ctx* h, Prob<T>& P, int which, void* dst, int64_t coun
     case 2:
       if (h->opt.decomp == SMA_HOSVD_MULTILEVEL) { src = P.gsig; n = (int64_t)P.gdim * 3; }
       else if (h->opt.decomp == SMA_TSVDM) { src = P.sigma; n = (int64_t)P.rc * P.p; }
+      else if (h->opt.decomp == SMA_CP_ALS) { src = nullptr; n = 0; }
       else {
         src = P.gsig;
         n = h->opt.decomp == SMA_TUCKER_BLOCKMODE ? (P.sk > 0 ? P.sk * P.sk : P.p) : P.m;
@@ -2101,11 +2204,20 @@ sma_status export_one(sma_ctx* h, Prob<T>& P, int which, void* dst, int64_t coun
     case 3: src = P.Tt; n = mnp; break;
     case 4:
       if (h->opt.decomp == SMA_HOSVD_MULTILEVEL) { src = P.Uml[0]; n = (int64_t)P.lp[0] * P.lp[0]; }
-      else if (h->opt.decomp == SMA_TUCKER_BLOCKMODE) { src = P.F1; n = (int64_t)P.p * P.p; }
+      else if (h->opt.decomp == SMA_TUCKER_BLOCKMODE || h->opt.decomp == SMA_CP_ALS) {
+        src = P.F1;
+        n = (int64_t)P.p * P.p;
+      }
       else if (h->opt.decomp != SMA_TSVDM) { src = P.F1; n = (int64_t)P.m * P.m; }
       break;
     case 5:
       if (P.spd) { src = P.Lc; n = (int64_t)P.m * P.m; }
+      break;
+    case 6:
+      if (P.cp_r > 0) { src = P.cXf; n = (int64_t)P.m * P.cp_r; }
+      break;
+    case 7:
+      if (P.cp_r > 0) { src = P.cZf; n = (int64_t)P.n * P.cp_r; }
       break;
     default: return SMA_ERR_ARG;
   }
@@ -2127,7 +2239,8 @@ sma_status ranks_one(sma_ctx* h, Prob<T>& P, int32_t* out, int32_t* count) {
     int isc[8];
     SMA_CK(cudaMemcpy(isc, P.iscal, sizeof(isc), cudaMemcpyDeviceToHost));
     const sma_decomp d = h->opt.decomp;
-    const int c = d == SMA_TUCKER_BLOCKMODE ? 1 : (d == SMA_HOSVD_MULTILEVEL ? 3 : 2);
+    const int c = (d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS) ? 1
+                                                                 : (d == SMA_HOSVD_MULTILEVEL ? 3 : 2);
     const bool shared = d == SMA_TUCKER_SHARED_U || d == SMA_TUCKER_SPD;
     for (int i = 0; i < c; ++i) out[i] = shared ? isc[2] : isc[2 + i];
     *count = c;
@@ -2229,7 +2342,15 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   *out = nullptr;
   if (!prob || !opt || nprob < 1) return SMA_ERR_ARG;
   if (opt->prec != SMA_FP64 && opt->prec != SMA_MIXED) return SMA_ERR_ARG;
-  if ((int)opt->decomp < 0 || opt->decomp > SMA_TUCKER_SPD) return SMA_ERR_ARG;
+  if ((int)opt->decomp < 0 || opt->decomp > SMA_CP_ALS) return SMA_ERR_ARG;
+  if (opt->decomp == SMA_CP_ALS) {
+    // CP: a rank the small solves take, iterations, both initial factors, one (m, n)
+    if (opt->fixed_rank < 1 || opt->fixed_rank > kCpMaxRank || opt->cp_iters < 1 ||
+        !opt->cp_init_x || !opt->cp_init_z)
+      return SMA_ERR_ARG;
+    for (int i = 1; i < nprob; ++i)
+      if (prob[i].m != prob[0].m || prob[i].n != prob[0].n) return SMA_ERR_ARG;
+  }
   if ((int)opt->mkind < 0 || opt->mkind > SMA_M_USER) return SMA_ERR_ARG;
   if (opt->layout != SMA_INPUT_DENSE && opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
   if (opt->fixed_rank < 0 || !(opt->rel_tol >= 0.0)) return SMA_ERR_ARG;
@@ -2288,7 +2409,7 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
     for (int i = 0; i < nprob; ++i) SMA_TRY(setup_problem(h.get(), h->p32[i], prob[i]));
     if (opt->decomp == SMA_TSVDM && nprob > 1) SMA_TRY(build_bins<float>(h.get()));
   }
-  if (opt->decomp != SMA_TSVDM) SMA_TRY(setup_gram_shared(h.get()));
+  if (opt->decomp != SMA_TSVDM && opt->decomp != SMA_CP_ALS) SMA_TRY(setup_gram_shared(h.get()));
   *out = h.release();
   return SMA_OK;
 }

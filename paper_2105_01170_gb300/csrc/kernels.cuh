@@ -186,6 +186,24 @@ cudaError_t permute3(const double* src, int64_t s0, int64_t s1, int64_t s2, int 
 template <typename TD, typename TS>
 cudaError_t convert(const TS* src, TD* dst, int64_t count, cudaStream_t st);
 
+// ---- CP by alternating least squares (cp.cu) --------------------------------
+constexpr int kCpMaxRank = 64;
+// out[(a + ra b), j] = A[a, j] B[b, j]: the Khatri-Rao (columnwise Kronecker)
+// product of A (ra x r) and B (rb x r), out (ra rb x r); all ld = rows.
+template <typename T>
+cudaError_t khatri_rao(const T* A, int ra, const T* B, int rb, int r, T* out, cudaStream_t st);
+// out (rows x r, ld ldo) = M (rows x r, ld rows) ((B1^T B1) .* (B2^T B2))^-1,
+// B1 n1 x r, B2 n2 x r, r <= kCpMaxRank; the r x r system in fp64 (one CTA);
+// a singular system sets SMA_ERR_NONFINITE in *status and writes zeros.
+template <typename T>
+cudaError_t cp_solve(const T* B1, int n1, const T* B2, int n2, int r, const T* M, int rows, T* out,
+                     int64_t ldo, int* status, cudaStream_t st);
+// out[e] = sum_s part[e + s count] in a fixed order (fp64 accumulation).
+template <typename T>
+cudaError_t sum_slabs_t(const T* part, int nslab, int64_t count, T* out, cudaStream_t st);
+// *dst = v on the stream.
+cudaError_t set_int(int* dst, int v, cudaStream_t st);
+
 // ---- Section 5.2 (SPD-preserving form) -------------------------------------
 // T_0 (m x m, ld ld0) = L L^T and L^-1, one CTA, both m x m column-major
 // (ld m); a pivot that is not positive and finite zeroes L and L^-1 and sets

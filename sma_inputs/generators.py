@@ -317,6 +317,34 @@ def gaussian_sketch(m: int, n: int, s: int, seed_index: int = 7,
     return g.standard_normal((m, s)), g.standard_normal((n, s))
 
 
+def planted_cp_toeplitz(ell: int = 8, m: int = 12, n: int = 10, r: int = 3,
+                        noise: float = 0.0, seed_index: int = 10,
+                        salt: int = 7) -> tuple[Problem, dict]:
+    """Block-Toeplitz matrix whose weighted block tensor is an exact rank-r
+    Kruskal tensor (plus optional noise): block k = Xf diag(Yf[k, :]) Zf^T /
+    sqrt(eta_k), so X[:, :, k] = sqrt(eta_k) A_k = Xf diag(Yf[k, :]) Zf^T.
+    Returns the problem and the planted factors."""
+    g = rng_for(seed_index, salt=salt)
+    bm = toeplitz_map(ell)
+    p = 2 * ell - 1
+    eta = np.zeros(p)
+    for k in bm.ravel():
+        eta[k] += 1
+    Xf, Yf, Zf = g.standard_normal((m, r)), g.standard_normal((p, r)), g.standard_normal((n, r))
+    X = np.einsum("aj,kj,bj->kab", Xf, Yf, Zf)
+    if noise:
+        X = X + noise * g.standard_normal(X.shape)
+    blocks = X / np.sqrt(eta)[:, None, None]
+    return Problem("planted_cp_toeplitz", blocks, bm, {"r": r}), {"Xf": Xf, "Yf": Yf, "Zf": Zf}
+
+
+def cp_initial_factors(m: int, n: int, r: int, seed_index: int = 11,
+                       salt: int = 8) -> tuple[np.ndarray, np.ndarray]:
+    """N(0,1) starting factors Xf (m x r) and Zf (n x r) for CP-ALS."""
+    g = rng_for(seed_index, salt=salt)
+    return g.standard_normal((m, r)), g.standard_normal((n, r))
+
+
 def planted_tsvdm_tensor(m: int, n: int, p: int, ranks, seed_index: int = 9,
                          salt: int = 4) -> tuple[np.ndarray, list]:
     """Random factors for a tensor whose transform-domain slices have given

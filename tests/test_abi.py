@@ -131,6 +131,37 @@ def test_sketch_options_are_validated(lib):
     assert create(one + [(4, 2, 3, 7, bm)]) == S.SMA_ERR_ARG  # another m
 
 
+def test_cp_options_are_validated(lib):
+    """CP-ALS needs a rank in 1..64 (and <= p), iterations and both initial
+    factors, and one (m, n) for all problems."""
+    bm = G.toeplitz_map(4)
+    x0 = np.zeros((3, 70))
+    keep = []
+
+    def create(probs, r=2, iters=3, ix=True, iz=True):
+        dp = ctypes.POINTER(ctypes.c_double)
+        opt = S.sma_options(S.SMA_FP64, S.SMA_CP_ALS, S.SMA_M_DCT2, S.SMA_INPUT_DENSE, None, r, 0.0,
+                            0, None, 0, 0, S.SMA_PRECOND_AUTO, 0, 0, None, None, iters,
+                            x0.ctypes.data_as(dp) if ix else None,
+                            x0.ctypes.data_as(dp) if iz else None)
+        structs = []
+        for ell, m, n, p, b in probs:
+            b = np.ascontiguousarray(np.asarray(b, dtype=np.int32).ravel(order="F"))
+            keep.append(b)
+            structs.append(S.sma_problem(ell, ell, m, n, p,
+                                         b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                         1, None, None, None, None))
+        return S.sma_create(structs, opt)[0]
+
+    one = [(4, 3, 3, 7, bm)]
+    assert create(one, r=0) == S.SMA_ERR_ARG
+    assert create(one, r=65) == S.SMA_ERR_ARG
+    assert create(one, iters=0) == S.SMA_ERR_ARG
+    assert create(one, ix=False) == S.SMA_ERR_ARG
+    assert create(one, iz=False) == S.SMA_ERR_ARG
+    assert create(one + [(4, 3, 2, 7, bm)]) == S.SMA_ERR_ARG
+
+
 def test_null_handle_calls(lib):
     assert S.sma_destroy(None) == S.SMA_ERR_ARG
     assert S.sma_apply(None, 0, 0, 1, 0, 1, 1) == S.SMA_ERR_ARG
