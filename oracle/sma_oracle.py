@@ -713,6 +713,104 @@ def multilevel_apply(G, C1, C2, C3, vols: np.ndarray) -> np.ndarray:
 # ---------------------------------------------------------------------------
 
 
+# ---------------------------------------------------------------------------
+# Section 7 with two levels and m x n blocks: the (L+2)-order tensor
+# ---------------------------------------------------------------------------
+
+
+def product_map(map1: np.ndarray, map2: np.ndarray) -> np.ndarray:
+    """The two-level structure sum_{i1,i2} E1_i1 (x) E2_i2 (x) A^(i1,i2) as a
+    one-level map: level 1 outermost, so block row a1 ell2 + a2 and block
+    column b1 q2 + b2 hold block index i1 + p1 i2 (-1 where either level is
+    empty).  The weights multiply: eta = eta1_i1 eta2_i2."""
+    l1, q1 = map1.shape
+    l2, q2 = map2.shape
+    p1 = int(map1.max()) + 1
+    out = -np.ones((l1 * l2, q1 * q2), dtype=np.int32)
+    for a1 in range(l1):
+        for b1 in range(q1):
+            i1 = int(map1[a1, b1])
+            if i1 < 0:
+                continue
+            for a2 in range(l2):
+                for b2 in range(q2):
+                    i2 = int(map2[a2, b2])
+                    if i2 >= 0:
+                        out[a1 * l2 + a2, b1 * q2 + b2] = i1 + p1 * i2
+    return out
+
+
+def two_level_tensor(A: np.ndarray, map1: np.ndarray, map2: np.ndarray, m: int,
+                     n: int) -> np.ndarray:
+    """Section 7.1: the (L+2)-order tensor of a two-level structured matrix,
+    X[:, :, i1, i2] = sqrt(eta1_i1 eta2_i2) A^(i1,i2) (m x n x p1 x p2; the
+    paper's m x p1 x p2 x n with the block kept as the first two modes)."""
+    p1, p2 = int(map1.max()) + 1, int(map2.max()) + 1
+    eta1, eta2 = multiplicities(map1, p1), multiplicities(map2, p2)
+    X = np.empty((m, n, p1, p2))
+    for i1 in range(p1):
+        a1, b1 = representatives(map1, p1)[i1]
+        for i2 in range(p2):
+            a2, b2 = representatives(map2, p2)[i2]
+            blk = block(A, a1 * map2.shape[0] + a2, b1 * map2.shape[1] + b2, m, n)
+            X[:, :, i1, i2] = math.sqrt(eta1[i1] * eta2[i2]) * blk
+    return X
+
+
+def two_level_matrix(X: np.ndarray, map1: np.ndarray, map2: np.ndarray) -> np.ndarray:
+    """M_E of Section 7.1: sum_{i1,i2} E1_i1 (x) E2_i2 (x) X[:, :, i1, i2]."""
+    p1, p2 = X.shape[2], X.shape[3]
+    E1, E2 = mapping_matrices(map1, p1), mapping_matrices(map2, p2)
+    return sum(np.kron(np.kron(E1[i1], E2[i2]), X[:, :, i1, i2])
+               for i1 in range(p1) for i2 in range(p2))
+
+
+@dataclass
+class HOSVD4:
+    factors: list          # [Xf (m x kx), Zf (n x kz), Y1 (p1 x k1), Y2 (p2 x k2)]
+    G: np.ndarray          # kx x kz x k1 x k2
+    ranks: tuple
+    err: float
+    rel_err: float
+
+    def tensor_approx(self) -> np.ndarray:
+        Xf, Zf, Y1, Y2 = self.factors
+        return np.einsum("xzij,ax,bz,ci,dj->abcd", self.G, Xf, Zf, Y1, Y2, optimize=True)
+
+
+def hosvd4(X: np.ndarray, rel_tol: float | None = None, ranks=None) -> HOSVD4:
+    """Truncated HOSVD of the fourth-order tensor (eq. multiTX with L = 2):
+    each factor holds leading left singular vectors of its unfolding; with a
+    tolerance every one of the four modes gets tol^2 ||X||^2 / 4 (reading R5)."""
+    normX2 = float(np.sum(X * X))
+    budget = (rel_tol or 0.0) ** 2 * normX2 / 4.0
+    facs, rk = [], []
+    for t in range(4):
+        Y = np.moveaxis(X, t, 0).reshape(X.shape[t], -1)
+        U, _, r = leading_left_singular(Y, None if ranks is None else ranks[t], budget)
+        facs.append(U)
+        rk.append(r)
+    G = np.einsum("abcd,ax,bz,ci,dj->xzij", X, *facs, optimize=True)
+    h = HOSVD4(facs, G, tuple(rk), 0.0, 0.0)
+    err = float(np.linalg.norm((X - h.tensor_approx()).ravel()))
+    h.err, h.rel_err = err, err / math.sqrt(normX2)
+    return h
+
+
+def two_level_kron_terms(h: HOSVD4, map1: np.ndarray, map2: np.ndarray):
+    """Section 7.3: sum_{j1,j2} struct1(Y1[:, j1]) (x) struct2(Y2[:, j2]) (x)
+    Xf G[:, :, j1, j2] Zf^T, as (C, D) pairs with C the Kronecker product of
+    the two level structures."""
+    Xf, Zf, Y1, Y2 = h.factors
+    p1, p2 = Y1.shape[0], Y2.shape[0]
+    terms = []
+    for j2 in range(Y2.shape[1]):
+        for j1 in range(Y1.shape[1]):
+            C = np.kron(struct_E(list(Y1[:, j1]), map1, p1), struct_E(list(Y2[:, j2]), map2, p2))
+            terms.append((C, Xf @ h.G[:, :, j1, j2] @ Zf.T))
+    return terms
+
+
 def fro(A: np.ndarray) -> float:
     return float(np.linalg.norm(np.asarray(A).ravel()))
 

@@ -98,6 +98,17 @@ def symmetric_tridiagonal_map(ell: int) -> np.ndarray:
     return bm
 
 
+def symmetric_banded_toeplitz_map(ell: int, half: int) -> np.ndarray:
+    """Block-symmetric banded Toeplitz map: index |a - b| for |a - b| <= half
+    (p = half + 1), the same block above and below the diagonal."""
+    bm = -np.ones((ell, ell), dtype=np.int32)
+    for a in range(ell):
+        for b in range(ell):
+            if abs(a - b) <= half:
+                bm[a, b] = abs(a - b)
+    return bm
+
+
 def place_blocks(blocks: np.ndarray, block_map: np.ndarray) -> np.ndarray:
     """Dense A with blocks[block_map[a, b]] at block position (a, b)."""
     p, m, n = blocks.shape
@@ -343,6 +354,44 @@ def cp_initial_factors(m: int, n: int, r: int, seed_index: int = 11,
     """N(0,1) starting factors Xf (m x r) and Zf (n x r) for CP-ALS."""
     g = rng_for(seed_index, salt=salt)
     return g.standard_normal((m, r)), g.standard_normal((n, r))
+
+
+def two_level_problem(map1: np.ndarray, map2: np.ndarray, m: int, n: int, ranks=None,
+                      noise: float = 0.0, seed_index: int = 12, salt: int = 9) -> Problem:
+    """A two-level structured matrix (Section 7.1): level 1 outermost, the
+    distinct m x n blocks A^(i1,i2) listed in the order i1 + p1 i2 over the
+    one-level product map (block row a1 ell2 + a2, column b1 q2 + b2).  With
+    ranks = (kx, kz, k1, k2) the weighted block tensor
+    X[:, :, i1, i2] = sqrt(eta1 eta2) A^(i1,i2) has that multilinear rank
+    (N(0,1) core and factors) plus optional noise; otherwise the blocks are
+    N(0,1)."""
+    g = rng_for(seed_index, salt=salt)
+    l1, q1 = map1.shape
+    l2, q2 = map2.shape
+    p1, p2 = int(map1.max()) + 1, int(map2.max()) + 1
+    eta1 = np.bincount(map1[map1 >= 0].ravel(), minlength=p1).astype(np.float64)
+    eta2 = np.bincount(map2[map2 >= 0].ravel(), minlength=p2).astype(np.float64)
+    if ranks is None:
+        X = g.standard_normal((m, n, p1, p2))
+    else:
+        kx, kz, k1, k2 = ranks
+        G = g.standard_normal((kx, kz, k1, k2))
+        fs = [g.standard_normal((d, k)) for d, k in ((m, kx), (n, kz), (p1, k1), (p2, k2))]
+        X = np.einsum("xzij,ax,bz,ci,dj->abcd", G, *fs)
+    if noise:
+        X = X + noise * g.standard_normal(X.shape)
+    w = np.sqrt(np.outer(eta1, eta2))                      # [i1, i2]
+    A = X / w[None, None, :, :]
+    blocks = np.stack([A[:, :, i1, i2] for i2 in range(p2) for i1 in range(p1)])
+    bm = -np.ones((l1 * l2, q1 * q2), dtype=np.int32)
+    for a1 in range(l1):
+        for b1 in range(q1):
+            for a2 in range(l2):
+                for b2 in range(q2):
+                    i1, i2 = map1[a1, b1], map2[a2, b2]
+                    if i1 >= 0 and i2 >= 0:
+                        bm[a1 * l2 + a2, b1 * q2 + b2] = i1 + p1 * i2
+    return Problem("two_level", blocks, bm, {"map1": map1, "map2": map2, "p1": p1, "p2": p2})
 
 
 def planted_tsvdm_tensor(m: int, n: int, p: int, ranks, seed_index: int = 9,

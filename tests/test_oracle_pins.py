@@ -601,3 +601,64 @@ def test_cp_kronecker_sum_and_block_form_equal_M_E():
     assert np.allclose(O.cp_blr(c, bm), dense, atol=1e-12 * np.abs(dense).max())
     for C, _ in terms:       # each C_j keeps the block-Toeplitz structure
         assert np.allclose(C[1:, 1:], C[:-1, :-1])
+
+
+# ------------------------------------------- Section 7 with two levels and m x n blocks
+
+def _two_level(ranks=None, noise=0.0, m=3, n=2):
+    map1 = G.symmetric_banded_toeplitz_map(4, 2)   # 4 x 4 block pentadiagonal, block symmetric
+    map2 = G.block_diagonal_map(5)                 # 5 x 5 block diagonal
+    pr = G.two_level_problem(map1, map2, m, n, ranks=ranks, noise=noise)
+    return map1, map2, pr
+
+
+def test_two_level_running_example_sizes():
+    """The example of Section 7.1: 4 x 4 block-pentadiagonal symmetric Toeplitz
+    of 5 x 5 block-diagonal blocks is stored as 3 x 5 = 15 distinct m x n
+    blocks, a fourth-order m x 3 x 5 x n tensor (ours: m x n x 3 x 5)."""
+    map1, map2, pr = _two_level()
+    assert (int(map1.max()) + 1, int(map2.max()) + 1) == (3, 5)
+    assert pr.p == 15
+    X = O.two_level_tensor(pr.dense(), map1, map2, pr.m, pr.n)
+    assert X.shape == (pr.m, pr.n, 3, 5)
+
+
+def test_two_level_map_round_trip_and_product_form():
+    """M_E(T_E(A)) = A for an exactly two-level structured A; the tensor is
+    the one-level tensor of the product map with the block index split as
+    i1 + p1 i2, so the weights multiply (eta = eta1 eta2)."""
+    map1, map2, pr = _two_level()
+    A = pr.dense()
+    X = O.two_level_tensor(A, map1, map2, pr.m, pr.n)
+    assert np.allclose(O.two_level_matrix(X, map1, map2), A, atol=1e-13)
+    bm = O.product_map(map1, map2)
+    assert np.array_equal(bm, pr.block_map)
+    X3 = O.T_E(A, bm, pr.p, pr.m, pr.n)
+    assert np.allclose(X3, X.reshape(pr.m, pr.n, -1, order="F"), atol=1e-13)
+    eta = O.multiplicities(bm, pr.p)
+    assert np.array_equal(eta, np.outer(O.multiplicities(map1, 3), O.multiplicities(map2, 5)).ravel(order="F"))
+
+
+def test_two_level_kron_sum_is_M_E_and_lemma_holds():
+    """Section 7.3: the sum over (j1, j2) of struct1 (x) struct2 (x)
+    Xf G_j1j2 Zf^T equals M_E of the Tucker tensor, and its Frobenius error
+    equals the tensor error (the multilevel Lemma)."""
+    map1, map2, pr = _two_level(m=4, n=3)
+    A = pr.dense()
+    X = O.two_level_tensor(A, map1, map2, pr.m, pr.n)
+    h = O.hosvd4(X, ranks=(3, 2, 2, 3))
+    dense = O.two_level_matrix(h.tensor_approx(), map1, map2)
+    assert np.allclose(O.kron_dense(O.two_level_kron_terms(h, map1, map2)), dense,
+                       atol=1e-12 * np.abs(dense).max())
+    assert abs(np.linalg.norm(A - dense) - h.err) <= 1e-12 * np.linalg.norm(A)
+    assert h.err > 0.1 * np.linalg.norm(X)        # a real truncation
+
+
+def test_two_level_planted_multilinear_rank_is_exact():
+    map1, map2, pr = _two_level(ranks=(2, 2, 2, 3), m=4, n=3)
+    X = O.two_level_tensor(pr.dense(), map1, map2, pr.m, pr.n)
+    h = O.hosvd4(X, rel_tol=1e-10)
+    assert h.ranks == (2, 2, 2, 3)
+    assert h.err <= 1e-12 * np.linalg.norm(X)
+    full = O.hosvd4(X, ranks=X.shape)
+    assert full.err <= 1e-12 * np.linalg.norm(X)
