@@ -122,14 +122,24 @@ typedef enum {
 } sma_input_layout;
 
 /* One structured block matrix (Section 3: ell x q blocks of m x n, p distinct).
- * Multilevel (Section 7.2, levels = 3, m = n = 1): level t has an
+ * Multilevel (Section 7), with SMA_HOSVD_MULTILEVEL: level t has an
  * level_ell[t] x level_q[t] map level_maps[t] with level_p[t] distinct
- * indices; the distinct scalars are passed in SMA_INPUT_BLOCKS layout in the
- * order i1 + p1*(i2 + p2*i3); ell, q, p and block_map are then ignored.     */
+ * indices, level 1 outermost; ell, q, p and block_map are then ignored.
+ *   levels = 3, m = n = 1 (Section 7.2): the distinct scalars are passed in
+ *     SMA_INPUT_BLOCKS layout in the order i1 + p1*(i2 + p2*i3).
+ *   levels = 2, any m x n blocks (Section 7.1): the matrix is
+ *     (ell1 ell2 m) x (q1 q2 n), block row a1*ell2 + a2 and block column
+ *     b1*q2 + b2 holding A^(i1,i2); in SMA_INPUT_BLOCKS layout the distinct
+ *     blocks come in the order i1 + p1*i2.  The fourth-order tensor
+ *     (m x n x p1 x p2) is compressed by a truncated HOSVD over its four
+ *     modes (tol^2 ||X||^2 / 4 each, or fixed_rank per mode), and the result
+ *     is the Kronecker sum over (j1, j2) of struct1(Y1[:, j1]) (x)
+ *     struct2(Y2[:, j2]) (x) Xf G[:, :, j1, j2] Zf^T; sma_result.ranks are
+ *     (kx, kz, k1, k2) and n_kron_terms = k1 k2.                          */
 typedef struct {
   int32_t ell, q, m, n, p;
   const int32_t* block_map;           /* host, ell*q, column-major          */
-  int32_t levels;                     /* 1 (default) or 3                   */
+  int32_t levels;                     /* 1 (default), 2 or 3                */
   const int32_t* level_ell;           /* [levels]                           */
   const int32_t* level_q;             /* [levels]                           */
   const int32_t* level_p;             /* [levels]                           */
@@ -194,7 +204,7 @@ typedef struct {
 typedef struct {
   int32_t total_rank;     /* t-SVDM: sum_i rho_i; Tucker: product of ranks      */
   int32_t n_kron_terms;   /* Kronecker terms (t-SVDM: slices with rho_i > 0)    */
-  int32_t ranks[3];       /* Tucker mode ranks (unused entries 0)               */
+  int32_t ranks[4];       /* Tucker mode ranks (unused entries 0)               */
   int32_t sweeps_max;     /* largest Jacobi sweep count used                    */
   int32_t device_status;  /* bit set of sma_status values raised by kernels     */
   double norm;            /* ||A||_F = ||X||_F                                   */

@@ -71,7 +71,7 @@ class sma_options(ctypes.Structure):
 
 class sma_result(ctypes.Structure):
     _fields_ = [("total_rank", ctypes.c_int32), ("n_kron_terms", ctypes.c_int32),
-                ("ranks", ctypes.c_int32 * 3), ("sweeps_max", ctypes.c_int32),
+                ("ranks", ctypes.c_int32 * 4), ("sweeps_max", ctypes.c_int32),
                 ("device_status", ctypes.c_int32), ("norm", ctypes.c_double),
                 ("tensor_err", ctypes.c_double), ("rel_err", ctypes.c_double),
                 ("orth_defect", ctypes.c_double)]
@@ -218,10 +218,13 @@ def _ptr_ld(a):
 
 @dataclass
 class MultilevelProblem:
-    """Three-level structured matrix with scalar blocks (Section 7.2): level t
-    has an ell_t x q_t map with p_t distinct indices."""
-    level_maps: list       # three (ell_t, q_t) int arrays
-    level_p: list          # three ints
+    """Multilevel structured matrix (Section 7): level t has an ell_t x q_t map
+    with p_t distinct indices, level 1 outermost.  Three levels with scalar
+    blocks (m = n = 1, Section 7.2) or two levels with m x n blocks."""
+    level_maps: list       # (ell_t, q_t) int arrays, one per level
+    level_p: list          # p_t per level
+    m: int = 1
+    n: int = 1
 
 
 @dataclass
@@ -295,12 +298,13 @@ class Handle:
         I32 = ctypes.c_int32
         maps = [np.ascontiguousarray(np.asarray(m, dtype=np.int32).ravel(order="F"))
                 for m in pr.level_maps]
-        ells = (I32 * 3)(*[np.asarray(m).shape[0] for m in pr.level_maps])
-        qs = (I32 * 3)(*[np.asarray(m).shape[1] for m in pr.level_maps])
-        ps = (I32 * 3)(*[int(p) for p in pr.level_p])
-        mptrs = (ctypes.POINTER(I32) * 3)(*[m.ctypes.data_as(ctypes.POINTER(I32)) for m in maps])
+        L = len(maps)
+        ells = (I32 * L)(*[np.asarray(m).shape[0] for m in pr.level_maps])
+        qs = (I32 * L)(*[np.asarray(m).shape[1] for m in pr.level_maps])
+        ps = (I32 * L)(*[int(p) for p in pr.level_p])
+        mptrs = (ctypes.POINTER(I32) * L)(*[m.ctypes.data_as(ctypes.POINTER(I32)) for m in maps])
         self._keep += [maps, ells, qs, ps, mptrs]
-        return sma_problem(1, 1, 1, 1, 1, None, 3, ells, qs, ps, mptrs)
+        return sma_problem(1, 1, int(pr.m), int(pr.n), 1, None, L, ells, qs, ps, mptrs)
 
     def compress(self, As, want_result=True, check=True):
         ptrs, ldas = zip(*[_ptr_ld(a) for a in As])

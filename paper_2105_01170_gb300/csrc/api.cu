@@ -217,6 +217,15 @@ struct Prob {
   T* Wml = nullptr;
   size_t Wml_elems = 0;
   bool ml_valid = false;
+  // two levels with m x n blocks (Section 7): the one-level problem of the
+  // product map; the factors of the four modes (m, n, p1, p2) and the core
+  // and term workspaces of the Kronecker sum over (j1, j2)
+  bool ml2 = false;
+  T* mlF[4] = {nullptr, nullptr, nullptr, nullptr};
+  T* mlT1 = nullptr;
+  T* mlT2 = nullptr;
+  T* mlG = nullptr;
+  T* mlGt = nullptr;
   // reconstruction
   T* Tt = nullptr;
   // apply workspace
@@ -379,10 +388,11 @@ std::vector<SvdBin<float>>& bins<float>(sma_ctx* h) { return h->bins32; }
 
 // Section 7.2: one map per level; every index of level t occurs.
 sma_status validate_levels(const sma_problem& pr, std::vector<int64_t> eta[3]) {
-  if (pr.levels != 3) return SMA_ERR_UNSUPPORTED;
-  if (pr.m != 1 || pr.n != 1) return SMA_ERR_ARG;
+  if (pr.levels != 2 && pr.levels != 3) return SMA_ERR_UNSUPPORTED;
+  if (pr.levels == 3 && (pr.m != 1 || pr.n != 1)) return SMA_ERR_ARG;
+  if (pr.m <= 0 || pr.n <= 0) return SMA_ERR_ARG;
   if (!pr.level_ell || !pr.level_q || !pr.level_p || !pr.level_maps) return SMA_ERR_ARG;
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < pr.levels; ++t) {
     const int ell = pr.level_ell[t], q = pr.level_q[t], p = pr.level_p[t];
     const int32_t* map = pr.level_maps[t];
     if (ell <= 0 || q <= 0 || p <= 0 || !map) return SMA_ERR_ARG;
@@ -537,9 +547,37 @@ template <typename T>
 sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   auto& mem = h->mem;
   const sma_options& o = h->opt;
-  if (o.decomp == SMA_HOSVD_MULTILEVEL) return setup_multilevel(h, P, pr);
   sma_problem pin = pr;
   std::vector<int32_t> inner;
+  if (o.decomp == SMA_HOSVD_MULTILEVEL) {
+    if (pr.levels != 2) return setup_multilevel(h, P, pr);
+    // two levels, m x n blocks: the one-level product map, level 1 outermost
+    // (block row a1 ell2 + a2, column b1 q2 + b2, block index i1 + p1 i2)
+    std::vector<int64_t> leta[3];
+    SMA_TRY(validate_levels(pr, leta));
+    const int l1 = pr.level_ell[0], q1 = pr.level_q[0], p1 = pr.level_p[0];
+    const int l2 = pr.level_ell[1], q2 = pr.level_q[1], p2 = pr.level_p[1];
+    inner.assign((size_t)l1 * l2 * q1 * q2, -1);
+    const int64_t L = (int64_t)l1 * l2;
+    for (int b1 = 0; b1 < q1; ++b1)
+      for (int a1 = 0; a1 < l1; ++a1) {
+        const int i1 = pr.level_maps[0][a1 + (size_t)b1 * l1];
+        if (i1 < 0) continue;
+        for (int b2 = 0; b2 < q2; ++b2)
+          for (int a2 = 0; a2 < l2; ++a2) {
+            const int i2 = pr.level_maps[1][a2 + (size_t)b2 * l2];
+            if (i2 >= 0) inner[(a1 * l2 + a2) + (size_t)(b1 * q2 + b2) * L] = i1 + p1 * i2;
+          }
+      }
+    pin.levels = 1;
+    pin.ell = l1 * l2;
+    pin.q = q1 * q2;
+    pin.p = p1 * p2;
+    pin.block_map = inner.data();
+    P.ml2 = true;
+    P.lell[0] = l1; P.lq[0] = q1; P.lp[0] = p1;
+    P.lell[1] = l2; P.lq[1] = q2; P.lp[1] = p2;
+  }
   if (o.decomp == SMA_TUCKER_SPD) {
     SMA_TRY(validate_problem(pr, P.eta, P.rep_a, P.rep_b));
     SMA_TRY(spd_split(pr, &P.k0, inner));
@@ -676,6 +714,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     }
     else if (o.decomp == SMA_TUCKER_SHARED_U || o.decomp == SMA_TUCKER_SPD) gdim = m;
     else if (o.decomp == SMA_TUCKER_ROWCOL) gdim = (m > n ? m : n);
+    else if (P.ml2) gdim = std::max({m, n, P.lp[0], P.lp[1]});
     else return SMA_ERR_UNSUPPORTED;
     if ((o.decomp == SMA_TUCKER_SHARED_U || o.decomp == SMA_TUCKER_SPD) && m != n)
       return SMA_ERR_ARG;
@@ -687,17 +726,18 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
       SMA_TRY(mem.alloc(&P.X64, mnp));
       SMA_TRY(mem.alloc(&P.Xu, mnp));
     }
+    const int nslot = P.ml2 ? 4 : 2;
     SMA_TRY(mem.alloc(&P.Wg, (size_t)gdim * gdim * 2));
     SMA_TRY(mem.alloc(&P.gW, (size_t)gdim * gdim));
-    SMA_TRY(mem.alloc(&P.gram, (size_t)gdim * gdim * 2));
-    SMA_TRY(mem.alloc(&P.gvec, (size_t)gdim * gdim * 2));
-    SMA_TRY(mem.alloc(&P.gsig, (size_t)gdim * 2));
-    SMA_TRY(mem.alloc(&P.suf, (size_t)(gdim + 1) * 2));
-    SMA_TRY(mem.alloc(&P.sweeps, 2));
-    SMA_TRY(mem.alloc(&P.ranks, 2));
-    SMA_TRY(mem.alloc(&P.off, 3));
-    SMA_TRY(mem.alloc(&P.orth, 2));
-    P.n_orth = (o.decomp == SMA_TUCKER_ROWCOL) ? 2 : 1;
+    SMA_TRY(mem.alloc(&P.gram, (size_t)gdim * gdim * nslot));
+    SMA_TRY(mem.alloc(&P.gvec, (size_t)gdim * gdim * nslot));
+    SMA_TRY(mem.alloc(&P.gsig, (size_t)gdim * nslot));
+    SMA_TRY(mem.alloc(&P.suf, (size_t)(gdim + 1) * nslot));
+    SMA_TRY(mem.alloc(&P.sweeps, nslot));
+    SMA_TRY(mem.alloc(&P.ranks, nslot));
+    SMA_TRY(mem.alloc(&P.off, nslot + 1));
+    SMA_TRY(mem.alloc(&P.orth, nslot));
+    P.n_orth = P.ml2 ? 4 : ((o.decomp == SMA_TUCKER_ROWCOL) ? 2 : 1);
     if (P.sk > 0) {
       const int s2 = P.sk * P.sk;
       SMA_TRY(mem.alloc(&P.Om, (size_t)m * P.sk));
@@ -710,7 +750,20 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
       SMA_CK(cudaMemcpy(P.Om, om.data(), om.size() * sizeof(T), cudaMemcpyHostToDevice));
       SMA_CK(cudaMemcpy(P.Ps, ps.data(), ps.size() * sizeof(T), cudaMemcpyHostToDevice));
     }
-    if (o.decomp == SMA_TUCKER_BLOCKMODE) {
+    if (P.ml2) {
+      const int dims[4] = {m, n, P.lp[0], P.lp[1]};
+      for (int t = 0; t < 4; ++t) SMA_TRY(mem.alloc(&P.mlF[t], (size_t)dims[t] * dims[t]));
+      SMA_TRY(mem.alloc(&P.mlT1, mnp));
+      SMA_TRY(mem.alloc(&P.mlT2, mnp));
+      SMA_TRY(mem.alloc(&P.mlG, mnp));
+      SMA_TRY(mem.alloc(&P.mlGt, mnp));
+      SMA_TRY(mem.alloc(&P.F1, (size_t)p * p));        // coefficient vectors (p x terms)
+      SMA_TRY(mem.alloc(&P.D, mnp));                   // D_t = Xf G_t Zf^T (m x n x terms)
+      SMA_TRY(mem.alloc(&P.C, (size_t)P.ell * P.q * p));
+      SMA_CK(cudaMemset(P.C, 0, sizeof(T) * (size_t)P.ell * P.q * p));
+      SMA_TRY(mem.alloc(&P.Gorth, (size_t)gdim * gdim));
+      P.nterms_max = p;
+    } else if (o.decomp == SMA_TUCKER_BLOCKMODE) {
       SMA_TRY(mem.alloc(&P.F1, (size_t)p * p));        // V (p x r)
       SMA_TRY(mem.alloc(&P.D, mnp));                   // G_j slices (m x n x r)
       SMA_TRY(mem.alloc(&P.C, (size_t)P.ell * P.q * p));
@@ -1326,6 +1379,114 @@ sma_status compress_tucker(sma_ctx* h, Prob<T>& P) {
   return SMA_OK;
 }
 
+// Section 7 with two levels and m x n blocks: truncated HOSVD of the fourth-
+// order tensor X[a, b, i1, i2] (stored as the one-level tensor of the
+// product map, block index i1 + p1 i2), each of the four modes with the
+// budget tol^2 ||X||^2 / 4; core G = X x Xf^T x Zf^T x Y1^T x Y2^T; the
+// Kronecker sum over (j1, j2) of struct1(Y1[:, j1]) (x) struct2(Y2[:, j2])
+// (x) Xf G[:, :, j1, j2] Zf^T kept as one-level terms: coefficient vectors
+// Y1[i1, j1] Y2[i2, j2] over the product map and D_t = Xf G_t Zf^T.
+template <typename T>
+sma_status compress_ml2(sma_ctx* h, Prob<T>& P) {
+  cudaStream_t st = h->st;
+  const int m = P.m, n = P.n, p = P.p, p1 = P.lp[0], p2 = P.lp[1];
+  const int64_t mn = (int64_t)m * n;
+  SMA_K(convert<double, T>(P.X, P.X64, mn * p, st));
+  const double share = 0.5;   // four truncated modes: tol^2 ||X||^2 / 4 each
+  SMA_TRY(gram_factor(h, P, 0, m, (int)(n * (int64_t)p), 1, m, 1, 0, share));          // a
+  SMA_TRY(gram_factor(h, P, 1, n, m, m, 1, p, mn, share));                              // b
+  SMA_TRY(gram_factor(h, P, 2, p1, (int)mn, mn, 1, p2, mn * p1, share));                // i1
+  SMA_TRY(gram_factor(h, P, 3, p2, (int)(mn * p1), mn * p1, 1, 1, 0, share));           // i2
+  stage_begin(h, SMA_STAGE_FACTORS);
+  const int dims[4] = {m, n, p1, p2};
+  for (int t = 0; t < 4; ++t)
+    SMA_K(convert<T, double>(P.gvec + P.gstride * t, P.mlF[t], (int64_t)dims[t] * dims[t], st));
+  const T* Xf = P.mlF[0];
+  const T* Zf = P.mlF[1];
+  const int* kx = P.iscal + 2;
+  const int* kz = P.iscal + 3;
+  const int* k1 = P.iscal + 4;
+  const int* k2 = P.iscal + 5;
+  SMA_CK(cudaMemsetAsync(P.mlT1, 0, sizeof(T) * (size_t)mn * p, st));
+  SMA_CK(cudaMemsetAsync(P.mlT2, 0, sizeof(T) * (size_t)mn * p, st));
+  SMA_CK(cudaMemsetAsync(P.mlG, 0, sizeof(T) * (size_t)mn * p, st));
+  {  // T1_k = Xf^T X_k (rows < kx)
+    GemmParams<T> g;
+    g.M = m; g.N = n; g.K = m; g.dM = kx; g.dstride = 0;
+    g.A = Xf; g.a_rs = m; g.a_cs = 1;
+    g.B = P.X; g.b_rs = 1; g.b_cs = m; g.b_b1 = mn;
+    g.C = P.mlT1; g.c_rs = 1; g.c_cs = m; g.c_b1 = mn;
+    g.nb1 = p;
+    SMA_K(contract<T>(h, g));
+  }
+  {  // T2_k = T1_k Zf (kx x kz in m x n storage)
+    GemmParams<T> g;
+    g.M = m; g.N = n; g.K = n; g.dM = kx; g.dN = kz; g.dstride = 0;
+    g.A = P.mlT1; g.a_rs = 1; g.a_cs = m; g.a_b1 = mn;
+    g.B = Zf; g.b_rs = 1; g.b_cs = n;
+    g.C = P.mlT2; g.c_rs = 1; g.c_cs = m; g.c_b1 = mn;
+    g.nb1 = p;
+    SMA_K(contract<T>(h, g));
+  }
+  SMA_CK(cudaMemsetAsync(P.mlT1, 0, sizeof(T) * (size_t)mn * p, st));
+  {  // T3[e, j1, i2] = sum_i1 T2[e, i1, i2] Y1[i1, j1]  (j1 < k1)
+    GemmParams<T> g;
+    g.M = (int)mn; g.N = p1; g.K = p1; g.dN = k1; g.dstride = 0;
+    g.A = P.mlT2; g.a_rs = 1; g.a_cs = mn; g.a_b1 = mn * p1;
+    g.B = P.mlF[2]; g.b_rs = 1; g.b_cs = p1;
+    g.C = P.mlT1; g.c_rs = 1; g.c_cs = mn; g.c_b1 = mn * p1;
+    g.nb1 = p2;
+    SMA_K(contract<T>(h, g));
+  }
+  {  // G[e, j1, j2] = sum_i2 T3[e, j1, i2] Y2[i2, j2]  (j2 < k2)
+    GemmParams<T> g;
+    g.M = (int)(mn * p1); g.N = p2; g.K = p2; g.dN = k2; g.dstride = 0;
+    g.A = P.mlT1; g.a_rs = 1; g.a_cs = mn * p1;
+    g.B = P.mlF[3]; g.b_rs = 1; g.b_cs = p2;
+    g.C = P.mlG; g.c_rs = 1; g.c_cs = mn * p1;
+    SMA_K(contract<T>(h, g));
+  }
+  // terms t = j1 + k1 j2 < k1 k2: core slices and coefficient vectors; the
+  // rest zero; the term count in iscal[1]
+  SMA_K(ml2_terms<T>(P.mlG, (int)mn, p1, p2, P.mlF[2], P.mlF[3], k1, k2, P.mlGt, P.F1, P.iscal + 1,
+                     st));
+  {  // D_t = Xf Gt_t Zf^T: Xf Gt_t (K = kx), then (.) Zf^T (K = kz)
+    GemmParams<T> g;
+    g.M = m; g.N = n; g.K = m; g.dK = kx; g.dstride = 0;
+    g.A = Xf; g.a_rs = 1; g.a_cs = m;
+    g.B = P.mlGt; g.b_rs = 1; g.b_cs = m; g.b_b1 = mn;
+    g.C = P.mlT2; g.c_rs = 1; g.c_cs = m; g.c_b1 = mn;
+    g.nb1 = p;
+    SMA_K(contract<T>(h, g));
+    GemmParams<T> g2;
+    g2.M = m; g2.N = n; g2.K = n; g2.dK = kz; g2.dstride = 0;
+    g2.A = P.mlT2; g2.a_rs = 1; g2.a_cs = m; g2.a_b1 = mn;
+    g2.B = Zf; g2.b_rs = n; g2.b_cs = 1;
+    g2.C = P.D; g2.c_rs = 1; g2.c_cs = m; g2.c_b1 = mn;
+    g2.nb1 = p;
+    SMA_K(contract<T>(h, g2));
+  }
+  SMA_K(build_struct_terms_nz<T>(P.d_nzpos, P.d_nzk, P.nnz, P.d_isq, P.ell, P.q, P.F1, p, 1, p,
+                                  P.iscal + 1, P.C, st));
+  SMA_TRY(make_T(h, P));
+  SMA_K(residual_norm2<T>(P.X, P.Tt, mn * p, P.partial, P.nparts, P.stats + 1, st));
+  stage_end(h);
+  stage_begin(h, SMA_STAGE_REPORT);
+  for (int t = 0; t < 4; ++t) {
+    const int rows = dims[t];
+    GemmParams<T> go;
+    go.M = rows; go.N = rows; go.K = rows; go.dM = P.iscal + 2 + t; go.dN = P.iscal + 2 + t;
+    go.dstride = 0;
+    go.A = P.mlF[t]; go.a_rs = rows; go.a_cs = 1;
+    go.B = P.mlF[t]; go.b_rs = 1; go.b_cs = rows;
+    go.C = P.Gorth; go.c_rs = 1; go.c_cs = rows;
+    SMA_K(gemm<T>(go, st));
+    SMA_K(orth_defect<T>(P.Gorth, rows, 1, P.iscal + 2 + t, nullptr, P.orth + t, st));
+  }
+  stage_end(h);
+  return SMA_OK;
+}
+
 // Section 7: HOSVD of the weighted coefficient tensor of a three-level
 // structured matrix (m = n = 1), each mode with the budget tol^2 ||X||^2 / 3.
 template <typename T>
@@ -1510,6 +1671,7 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
   SMA_TRY(do_gather(h, P, A, lda));
   if (P.spd) SMA_TRY(spd_congruence(h, P));
   if (h->opt.decomp == SMA_TSVDM) SMA_TRY(tsvdm_pre(h, P));
+  else if (P.ml2) SMA_TRY(compress_ml2(h, P));
   else if (h->opt.decomp == SMA_CP_ALS) SMA_TRY(compress_cp(h, P));
   else SMA_TRY(compress_tucker(h, P));
   P.compressed = true;
@@ -1546,6 +1708,11 @@ sma_status read_result(sma_ctx* h, Prob<T>& P, sma_result* r) {
   if (d == SMA_TSVDM) {
     err2 = stats[1];
     r->total_rank = iscal[0];
+    r->n_kron_terms = iscal[1];
+  } else if (P.ml2) {
+    err2 = stats[1];
+    for (int t = 0; t < 4; ++t) r->ranks[t] = iscal[2 + t];
+    r->total_rank = iscal[2] * iscal[3] * iscal[4] * iscal[5];
     r->n_kron_terms = iscal[1];
   } else if (d == SMA_HOSVD_MULTILEVEL) {
     err2 = stats[1];
@@ -1891,9 +2058,9 @@ sma_status apply_core(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, in
   const int m = P.m, n = P.n, ell = P.ell, q = P.q;
   const int64_t yrows = (int64_t)ell * m;
   const sma_decomp d = h->opt.decomp;
-  if (d == SMA_HOSVD_MULTILEVEL) {
+  if (d == SMA_HOSVD_MULTILEVEL && !P.ml2) {
     SMA_TRY(apply_multilevel(h, P, X, ldx, Yd, ldyd, nrhs));
-  } else if (d == SMA_TSVDM || d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS) {
+  } else if (d == SMA_TSVDM || d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS || P.ml2) {
     // Kronecker sum Y = sum_j D_j X C_j^T (Section 2.2 vec identity).
     if (P.h_iscal[0] < 0) {
       SMA_CK(cudaStreamSynchronize(st));
@@ -1901,7 +2068,7 @@ sma_status apply_core(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, in
     }
     // t-SVDM: one term per slice (rank-0 slices have D_i = 0);
     // Tucker-1: the r2 retained block-mode columns.
-    const int nt = d == SMA_TSVDM ? P.nterms_max : P.h_iscal[2];
+    const int nt = d == SMA_TSVDM ? P.nterms_max : (P.ml2 ? P.h_iscal[1] : P.h_iscal[2]);
     if (nt <= 0) {
       if (ldyd == yrows) SMA_CK(cudaMemsetAsync(Yd, 0, sizeof(T) * (size_t)yrows * nrhs, st));
       else SMA_CK(cudaMemset2DAsync(Yd, ldyd * sizeof(T), 0, yrows * sizeof(T), nrhs, st));
@@ -2009,7 +2176,7 @@ sma_status make_T(sma_ctx* h, Prob<T>& P) {
   const int m = P.m, n = P.n, p = P.p;
   const int64_t mn = (int64_t)m * n;
   const sma_decomp d = h->opt.decomp;
-  if (d == SMA_HOSVD_MULTILEVEL) {
+  if (d == SMA_HOSVD_MULTILEVEL && !P.ml2) {
     const int p1 = P.lp[0], p2 = P.lp[1], p3 = P.lp[2];
     {  // T1 = G_(3) U3^T as (p1 p2) x p3, K = k3
       GemmParams<T> g;
@@ -2046,10 +2213,11 @@ sma_status make_T(sma_ctx* h, Prob<T>& P) {
     g.B = P.Mt; g.b_rs = 1; g.b_cs = p;
     g.C = P.Tt; g.c_rs = 1; g.c_cs = mn;
     SMA_K(gemm<T>(g, st));
-  } else if (d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS) {
-    // T = G x3 V: T_mat = G_mat V^T (CP: G_mat = [vec(Xf_j Zf_j^T)], V = Yf)
+  } else if (d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS || P.ml2) {
+    // T = G x3 V: T_mat = G_mat V^T (CP: G_mat = [vec(Xf_j Zf_j^T)], V = Yf;
+    // two levels: the D_t and the coefficient vectors, iscal[1] terms)
     GemmParams<T> g;
-    g.M = (int)mn; g.N = p; g.K = p; g.dK = P.iscal + 2; g.dstride = 0;
+    g.M = (int)mn; g.N = p; g.K = p; g.dK = P.ml2 ? P.iscal + 1 : P.iscal + 2; g.dstride = 0;
     g.A = P.D; g.a_rs = 1; g.a_cs = mn;
     g.B = P.F1; g.b_rs = p; g.b_cs = 1;
     g.C = P.Tt; g.c_rs = 1; g.c_cs = mn;
@@ -2192,7 +2360,7 @@ sma_status export_one(sma_ctx* h, Prob<T>& P, int which, void* dst, int64_t coun
     case 0: src = P.X; n = mnp; break;
     case 1: src = P.Xh; n = P.Xh ? mnp : 0; break;
     case 2:
-      if (h->opt.decomp == SMA_HOSVD_MULTILEVEL) { src = P.gsig; n = (int64_t)P.gdim * 3; }
+      if (h->opt.decomp == SMA_HOSVD_MULTILEVEL) { src = P.gsig; n = (int64_t)P.gdim * (P.ml2 ? 4 : 3); }
       else if (h->opt.decomp == SMA_TSVDM) { src = P.sigma; n = (int64_t)P.rc * P.p; }
       else if (h->opt.decomp == SMA_CP_ALS) { src = nullptr; n = 0; }
       else {
@@ -2203,7 +2371,8 @@ sma_status export_one(sma_ctx* h, Prob<T>& P, int which, void* dst, int64_t coun
       break;
     case 3: src = P.Tt; n = mnp; break;
     case 4:
-      if (h->opt.decomp == SMA_HOSVD_MULTILEVEL) { src = P.Uml[0]; n = (int64_t)P.lp[0] * P.lp[0]; }
+      if (P.ml2) { src = P.F1; n = (int64_t)P.p * P.p; }
+      else if (h->opt.decomp == SMA_HOSVD_MULTILEVEL) { src = P.Uml[0]; n = (int64_t)P.lp[0] * P.lp[0]; }
       else if (h->opt.decomp == SMA_TUCKER_BLOCKMODE || h->opt.decomp == SMA_CP_ALS) {
         src = P.F1;
         n = (int64_t)P.p * P.p;
@@ -2239,8 +2408,10 @@ sma_status ranks_one(sma_ctx* h, Prob<T>& P, int32_t* out, int32_t* count) {
     int isc[8];
     SMA_CK(cudaMemcpy(isc, P.iscal, sizeof(isc), cudaMemcpyDeviceToHost));
     const sma_decomp d = h->opt.decomp;
-    const int c = (d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS) ? 1
-                                                                 : (d == SMA_HOSVD_MULTILEVEL ? 3 : 2);
+    const int c = P.ml2 ? 4
+                        : (d == SMA_TUCKER_BLOCKMODE || d == SMA_CP_ALS)
+                              ? 1
+                              : (d == SMA_HOSVD_MULTILEVEL ? 3 : 2);
     const bool shared = d == SMA_TUCKER_SHARED_U || d == SMA_TUCKER_SPD;
     for (int i = 0; i < c; ++i) out[i] = shared ? isc[2] : isc[2 + i];
     *count = c;
@@ -2374,7 +2545,7 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
     if (opt->decomp == SMA_HOSVD_MULTILEVEL) {
       std::vector<int64_t> leta[3];
       SMA_TRY(validate_levels(prob[i], leta));
-      if (opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
+      if (prob[i].levels == 3 && opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
       continue;
     }
     SMA_TRY(validate_problem(prob[i], eta, ra, rb));

@@ -19,6 +19,13 @@ cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStre
 // out[e] = sum_s part[e + s count] for e < count, s < nslab (fixed order: the
 // split-K partial products of a Gram).
 cudaError_t sum_slabs(const double* part, int nslab, int64_t count, double* out, cudaStream_t st);
+// Two-level Kronecker terms (Section 7): t = j1 + k1 j2 < k1 k2 (device k1,
+// k2): Gt[:, t] = G[:, j1, j2] (G mn x p1 x p2, Gt mn x p1 p2) and
+// V[i1 + p1 i2, t] = Y1[i1, j1] Y2[i2, j2] (V p1 p2 x p1 p2, Y1 p1 x p1,
+// Y2 p2 x p2); later terms zero; *nterms = k1 k2.
+template <typename T>
+cudaError_t ml2_terms(const T* G, int mn, int p1, int p2, const T* Y1, const T* Y2, const int* k1,
+                      const int* k2, T* Gt, T* V, int* nterms, cudaStream_t st);
 // V[:, j] *= 1 / sqrt(ev[j]) for j < *r (device count), V with leading
 // dimension ld (at most ld columns), rows entries per column; a column whose
 // ev[j] <= 0 is zeroed.

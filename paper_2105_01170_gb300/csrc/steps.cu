@@ -453,6 +453,28 @@ __global__ void sum_slabs_kernel(const double* __restrict__ part, int nslab, int
   }
 }
 
+// Terms of the two-level Kronecker sum: t = j1 + k1 j2 < k1 k2 copies the core
+// slice G[:, j1, j2] (mn entries; G is mn x p1 x p2) to Gt[:, t] and writes
+// the coefficient vector V[i1 + p1 i2, t] = Y1[i1, j1] Y2[i2, j2]; terms
+// t >= k1 k2 (up to p1 p2) are zero; *nterms = k1 k2.  One CTA per term.
+template <typename T>
+__global__ void ml2_terms_kernel(const T* __restrict__ G, int mn, int p1, int p2,
+                                 const T* __restrict__ Y1, const T* __restrict__ Y2,
+                                 const int* __restrict__ k1p, const int* __restrict__ k2p,
+                                 T* __restrict__ Gt, T* __restrict__ V, int* __restrict__ nterms) {
+  const int t = blockIdx.x, p = p1 * p2;
+  const int k1 = *k1p, k2 = *k2p;
+  const bool live = k1 > 0 && t < k1 * k2;
+  const int j1 = live ? t % k1 : 0, j2 = live ? t / k1 : 0;
+  const T* g = G + ((int64_t)j1 + (int64_t)p1 * j2) * mn;
+  for (int e = threadIdx.x; e < mn; e += blockDim.x) Gt[(int64_t)t * mn + e] = live ? g[e] : T(0);
+  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+    const int i1 = k % p1, i2 = k / p1;
+    V[k + (int64_t)t * p] = live ? Y1[i1 + (int64_t)j1 * p1] * Y2[i2 + (int64_t)j2 * p2] : T(0);
+  }
+  if (t == 0 && threadIdx.x == 0) *nterms = k1 * k2;
+}
+
 // V[:, j] /= sqrt(ev[j]) for j < *r (zero column where ev[j] <= 0).
 __global__ void scale_cols_rsqrt_kernel(double* V, int64_t ld, int rows, const double* ev,
                                         const int* r) {
@@ -462,6 +484,20 @@ __global__ void scale_cols_rsqrt_kernel(double* V, int64_t ld, int rows, const d
   const double f = e > 0.0 ? 1.0 / sqrt(e) : 0.0;
   for (int i = threadIdx.x; i < rows; i += blockDim.x) V[i + j * ld] *= f;
 }
+
+template <typename T>
+cudaError_t ml2_terms(const T* G, int mn, int p1, int p2, const T* Y1, const T* Y2, const int* k1,
+                      const int* k2, T* Gt, T* V, int* nterms, cudaStream_t st) {
+  const int p = p1 * p2;
+  if (p <= 0 || p > 65535 * 1024) return cudaErrorInvalidValue;
+  ml2_terms_kernel<T><<<p, 256, 0, st>>>(G, mn, p1, p2, Y1, Y2, k1, k2, Gt, V, nterms);
+  return cudaGetLastError();
+}
+template cudaError_t ml2_terms<float>(const float*, int, int, int, const float*, const float*,
+                                      const int*, const int*, float*, float*, int*, cudaStream_t);
+template cudaError_t ml2_terms<double>(const double*, int, int, int, const double*, const double*,
+                                       const int*, const int*, double*, double*, int*,
+                                       cudaStream_t);
 
 cudaError_t scale_cols_rsqrt(double* V, int64_t ld, int rows, const double* ev, const int* r,
                              cudaStream_t st) {

@@ -46,7 +46,7 @@ def test_multilevel_small_dense(prec):
     K, half, tol = 9, 2, 1e-3
     h, res, X, Pin, bm, s = setup(K, half, (1.0, 1.5, 2.0), prec, tol)
     ho = O.hosvd3(X, rel_tol=tol)
-    assert tuple(res["ranks"]) == ho.ranks
+    assert tuple(res["ranks"][:3]) == ho.ranks
     assert list(h.ranks(0)) == list(ho.ranks)
     floor = (1e-13 if prec == S.SMA_FP64 else TOL_MIXED) * np.linalg.norm(X)
     assert abs(res["tensor_err"] - ho.err) <= 1e-6 * ho.err + floor
@@ -81,7 +81,7 @@ def test_multilevel_full_psf(prec):
     K, half, tol = 64, 7, 1e-4
     h, res, X, Pin, bm, s = setup(K, half, (2.0, 3.0, 4.0), prec, tol)
     ho = O.hosvd3(X, rel_tol=tol)
-    assert tuple(res["ranks"]) == ho.ranks == (1, 6, 6)
+    assert tuple(res["ranks"][:3]) == ho.ranks == (1, 6, 6)
     floor = (1e-13 if prec == S.SMA_FP64 else TOL_MIXED) * np.linalg.norm(X)
     assert abs(res["tensor_err"] - ho.err) <= 1e-6 * ho.err + floor
     Gc, C1, C2, C3 = O.multilevel_kron_terms(ho, K, half)
