@@ -190,6 +190,7 @@ struct Prob {
   T* cKR = nullptr;
   T* cM = nullptr;
   T* cSlab = nullptr;
+  size_t cSlab_elems = 0;
   T* Om = nullptr;
   T* Ps = nullptr;
   T* Ysk = nullptr;
@@ -691,7 +692,11 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     SMA_TRY(mem.alloc(&P.cZf0, (size_t)n * r));
     SMA_TRY(mem.alloc(&P.cKR, big * r));
     SMA_TRY(mem.alloc(&P.cM, (size_t)std::max({m, n, p}) * r));
-    SMA_TRY(mem.alloc(&P.cSlab, (size_t)p * n * r));
+    // per-block partials of the mode-2 contraction, or split-K partials of
+    // the other two (at most 2 nsm / tiles + 1 chunks of M x r)
+    P.cSlab_elems = std::max((size_t)p * n * r,
+                             (size_t)(2 * h->nsm + 1) * std::max({m, n, p}) * r);
+    SMA_TRY(mem.alloc(&P.cSlab, P.cSlab_elems));
     std::vector<T> x0(o.cp_init_x, o.cp_init_x + (size_t)m * r);
     std::vector<T> z0(o.cp_init_z, o.cp_init_z + (size_t)n * r);
     SMA_CK(cudaMemcpy(P.cXf0, x0.data(), x0.size() * sizeof(T), cudaMemcpyHostToDevice));
@@ -1594,6 +1599,32 @@ sma_status spd_congruence(sma_ctx* h, Prob<T>& P) {
   return SMA_OK;
 }
 
+// C = A B for a product with few output tiles and a long K (the CP
+// contractions: r columns, K = m n or n p): K split so that about two CTAs
+// per SM take part, one partial product per chunk into `part`, then the
+// partials summed in chunk order into C (which must be dense, ld M).
+template <typename T>
+sma_status contract_split_k(sma_ctx* h, GemmParams<T> g, T* part, size_t part_elems) {
+  const int64_t tiles = (int64_t)((g.M + 63) / 64) * ((g.N + 63) / 64);
+  int64_t nsplit = (2 * (int64_t)h->nsm + tiles - 1) / tiles;
+  if (nsplit > g.K / 64) nsplit = g.K / 64;
+  const bool dense_c = g.c_rs == 1 && g.c_cs == g.M;
+  if (nsplit <= 1 || g.nb1 != 1 || g.nb2 != 1 || !dense_c || g.beta != T(0) || g.dK || g.dKoff ||
+      (size_t)nsplit * g.M * g.N > part_elems) {
+    SMA_K(contract<T>(h, g));
+    return SMA_OK;
+  }
+  const int kc = (int)(((g.K + nsplit - 1) / nsplit + 15) / 16 * 16);
+  nsplit = (g.K + kc - 1) / kc;
+  T* C = g.C;
+  g.kchunk = kc;
+  g.nb1 = (int)nsplit;
+  g.C = part; g.c_b1 = (int64_t)g.M * g.N;
+  SMA_K(gemm<T>(g, h->st));
+  SMA_K(sum_slabs_t<T>(part, (int)nsplit, (int64_t)g.M * g.N, C, h->st));
+  return SMA_OK;
+}
+
 // CP by alternating least squares from the given Xf, Zf: per iteration Yf,
 // then Xf, then Zf, each the least-squares solution with the other two fixed
 // (the contraction of X with the Khatri-Rao product of the other two factors,
@@ -1618,7 +1649,7 @@ sma_status compress_cp(sma_ctx* h, Prob<T>& P) {
       g.A = P.X; g.a_rs = mn; g.a_cs = 1;
       g.B = P.cKR; g.b_rs = 1; g.b_cs = mn;
       g.C = P.cM; g.c_rs = 1; g.c_cs = p;
-      SMA_K(contract<T>(h, g));
+      SMA_TRY(contract_split_k<T>(h, g, P.cSlab, P.cSlab_elems));
     }
     SMA_K(cp_solve<T>(P.cXf, m, P.cZf, n, r, P.cM, p, Yf, p, P.status, st));
     // Xf: M1 = X_(1) (Zf . Yf)  (m x r), X_(1) = [X_1 ... X_p] (m x n p)
@@ -1629,7 +1660,7 @@ sma_status compress_cp(sma_ctx* h, Prob<T>& P) {
       g.A = P.X; g.a_rs = 1; g.a_cs = m;
       g.B = P.cKR; g.b_rs = 1; g.b_cs = (int64_t)n * p;
       g.C = P.cM; g.c_rs = 1; g.c_cs = m;
-      SMA_K(contract<T>(h, g));
+      SMA_TRY(contract_split_k<T>(h, g, P.cSlab, P.cSlab_elems));
     }
     SMA_K(cp_solve<T>(P.cZf, n, Yf, p, r, P.cM, m, P.cXf, m, P.status, st));
     // Zf: M2 = sum_k X_k^T Xf diag(Yf[k, :])  (n x r), one partial per block
