@@ -60,11 +60,45 @@ __device__ __forceinline__ bool angle_fp64(double al, double be, double ga, doub
   return true;
 }
 
+// fp64 rotation with the tangent taken in fp32: any
+// tangent near the optimal one gives an exact (valid) rotation, which leaves
+// the pair orthogonal to about fp32 relative accuracy for the next sweep to
+// finish, while (c, s) themselves are orthonormal to fp64 accuracy: c =
+// 1/sqrt(1 + t^2) from the fp32 estimate refined by two Newton steps in fp64.
+// The threshold is tested without square roots; nearly parallel columns
+// (|cos| > 0.99) and values outside the fp32 range take the fp64 angle.
+__device__ __forceinline__ bool angle_fp64_fast(double al, double be, double ga, double tol,
+                                                double floor_, double& c, double& s) {
+  const double g2 = ga * ga, ab = al * be;
+  if (!(g2 > tol * tol * ab) || !(fabs(ga) > floor_)) return false;
+  const double d = be - al;
+  const double ad = fabs(d), ag = fabs(ga);
+  if (g2 > 0.9801 * ab || ag > 1e30 || ag < 1e-30 || ad > 1e30 || (ad < 1e-30 && ad != 0.0))
+    return angle_fp64(al, be, ga, 0.0, 0.0, c, s);
+  const float zeta = __fdividef((float)d, 2.0f * (float)ga);
+  const float az = fabsf(zeta);
+  float tf;
+  if (az > 1e18f) {
+    tf = __fdividef(0.5f, zeta);
+  } else {
+    const float q = fmaf(zeta, zeta, 1.0f);
+    tf = copysignf(__fdividef(1.0f, az + q * rsqrtf(q)), zeta);
+  }
+  const double t = (double)tf;
+  const double q = fma(t, t, 1.0);
+  double r = (double)rsqrtf((float)q);
+  r = r * fma(-0.5 * q, r * r, 1.5);
+  r = r * fma(-0.5 * q, r * r, 1.5);
+  c = r;
+  s = r * t;
+  return true;
+}
+
 template <typename T> struct Angle;
 template <> struct Angle<double> {
   static __device__ __forceinline__ bool get(double al, double be, double ga, double tol,
                                              double floor_, double& c, double& s) {
-    return angle_fp64(al, be, ga, tol, floor_, c, s);
+    return angle_fp64_fast(al, be, ga, tol, floor_, c, s);
   }
 };
 template <> struct Angle<float> {
@@ -1017,40 +1051,6 @@ __global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel
 // every other waiting CTA returns when it sees the flag.
 
 constexpr unsigned long long kCoopWaitNs = 4000000000ull;   // 4 s per barrier
-
-// fp64 rotation of the cooperative kernel with the tangent taken in fp32: any
-// tangent near the optimal one gives an exact (valid) rotation, which leaves
-// the pair orthogonal to about fp32 relative accuracy for the next sweep to
-// finish, while (c, s) themselves are orthonormal to fp64 accuracy: c =
-// 1/sqrt(1 + t^2) from the fp32 estimate refined by two Newton steps in fp64.
-// The threshold is tested without square roots; nearly parallel columns
-// (|cos| > 0.99) and values outside the fp32 range take the fp64 angle.
-__device__ __forceinline__ bool angle_fp64_fast(double al, double be, double ga, double tol,
-                                                double floor_, double& c, double& s) {
-  const double g2 = ga * ga, ab = al * be;
-  if (!(g2 > tol * tol * ab) || !(fabs(ga) > floor_)) return false;
-  const double d = be - al;
-  const double ad = fabs(d), ag = fabs(ga);
-  if (g2 > 0.9801 * ab || ag > 1e30 || ag < 1e-30 || ad > 1e30 || (ad < 1e-30 && ad != 0.0))
-    return angle_fp64(al, be, ga, 0.0, 0.0, c, s);
-  const float zeta = __fdividef((float)d, 2.0f * (float)ga);
-  const float az = fabsf(zeta);
-  float tf;
-  if (az > 1e18f) {
-    tf = __fdividef(0.5f, zeta);
-  } else {
-    const float q = fmaf(zeta, zeta, 1.0f);
-    tf = copysignf(__fdividef(1.0f, az + q * rsqrtf(q)), zeta);
-  }
-  const double t = (double)tf;
-  const double q = fma(t, t, 1.0);
-  double r = (double)rsqrtf((float)q);
-  r = r * fma(-0.5 * q, r * r, 1.5);
-  r = r * fma(-0.5 * q, r * r, 1.5);
-  c = r;
-  s = r * t;
-  return true;
-}
 
 // rotate_pair for fp64 with the angle above; NR rows per lane stay in
 // registers between the dot products and the rotation.
