@@ -168,6 +168,7 @@ struct Prob {
   double* gsig = nullptr;                   // Gram eigenvalues
   double* Wg = nullptr;                     // block-mode Jacobi workspace for the Gram
   double* gW = nullptr;                     // Jacobi W output for the Gram (unused values)
+  SliceDesc<double>* gdesc = nullptr;       // per Gram slot: the Jacobi's pointers
   size_t gstride = 0;                       // elements between the two Gram slots
   int gdim = 0;
   T* F1 = nullptr;                          // leading factor (rows), T
@@ -478,6 +479,21 @@ sma_status setup_tc_transform<float>(sma_ctx* h, Prob<float>& P) {
   return SMA_OK;
 }
 
+// Per-slot pointers of the Gram eigen-solves (Gram, unused W output,
+// eigenvectors, eigenvalues, sweep count), so that Grams of one order can be
+// solved by one launch.
+template <typename T>
+sma_status setup_gram_desc(sma_ctx* h, Prob<T>& P, int nslot) {
+  std::vector<SliceDesc<double>> d(nslot);
+  for (int sl = 0; sl < nslot; ++sl)
+    d[sl] = SliceDesc<double>{P.gram + (size_t)sl * P.gstride, P.gW + (size_t)sl * P.gstride,
+                              P.gvec + (size_t)sl * P.gstride, P.gsig + (size_t)sl * P.gdim,
+                              P.sweeps + sl, P.status};
+  SMA_TRY(h->mem.alloc(&P.gdesc, (size_t)nslot));
+  SMA_CK(cudaMemcpy(P.gdesc, d.data(), d.size() * sizeof(SliceDesc<double>), cudaMemcpyHostToDevice));
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status setup_multilevel(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   auto& mem = h->mem;
@@ -531,11 +547,12 @@ sma_status setup_multilevel(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   SMA_TRY(mem.alloc(&P.gsig, (size_t)gdim * 3));
   SMA_TRY(mem.alloc(&P.suf, (size_t)(gdim + 1) * 3));
   SMA_TRY(mem.alloc(&P.Wg, P.gstride * 2));
-  SMA_TRY(mem.alloc(&P.gW, P.gstride));
+  SMA_TRY(mem.alloc(&P.gW, P.gstride * 3));
   SMA_TRY(mem.alloc(&P.sweeps, 3));
   SMA_TRY(mem.alloc(&P.ranks, 3));
-  SMA_TRY(mem.alloc(&P.off, 3));
+  SMA_TRY(mem.alloc(&P.off, 4));
   SMA_TRY(mem.alloc(&P.orth, 3));
+  SMA_TRY(setup_gram_desc(h, P, 3));
   SMA_TRY(mem.alloc(&P.Gorth, P.gstride));
   P.n_orth = 3;
   SMA_CK(cudaMemset(P.stats, 0, 8 * sizeof(double)));
@@ -733,7 +750,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     }
     const int nslot = P.ml2 ? 4 : 2;
     SMA_TRY(mem.alloc(&P.Wg, (size_t)gdim * gdim * 2));
-    SMA_TRY(mem.alloc(&P.gW, (size_t)gdim * gdim));
+    SMA_TRY(mem.alloc(&P.gW, (size_t)gdim * gdim * nslot));
     SMA_TRY(mem.alloc(&P.gram, (size_t)gdim * gdim * nslot));
     SMA_TRY(mem.alloc(&P.gvec, (size_t)gdim * gdim * nslot));
     SMA_TRY(mem.alloc(&P.gsig, (size_t)gdim * nslot));
@@ -742,6 +759,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     SMA_TRY(mem.alloc(&P.ranks, nslot));
     SMA_TRY(mem.alloc(&P.off, nslot + 1));
     SMA_TRY(mem.alloc(&P.orth, nslot));
+    SMA_TRY(setup_gram_desc(h, P, nslot));
     P.n_orth = P.ml2 ? 4 : ((o.decomp == SMA_TUCKER_ROWCOL) ? 2 : 1);
     if (P.sk > 0) {
       const int s2 = P.sk * P.sk;
@@ -1153,14 +1171,27 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P, bool truncated) {
 // Gram of an unfolding in fp64 followed by its Jacobi eigen-solve.
 // Y (rows x K) given by strides; result: gvec (rows x rows, sorted), gsig
 // (eigenvalues), rank written to ranks[slot] by the truncation kernel.
+// One unfolding Gram of a Tucker variant: Y (rows x K, element (i, k) at
+// Ysrc[i y_rs + k y_cs], summed over nb1 batch entries y_b1 apart; Ysrc =
+// the fp64 copy of X unless given) and its share of the tolerance budget.
+struct GramSpec {
+  int rows, K;
+  int64_t y_rs, y_cs;
+  int nb1;
+  int64_t y_b1;
+  double share;
+  const double* src;
+};
+
+// G_slot = Y Y^T in fp64.
 template <typename T>
-sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_t y_rs,
-                       int64_t y_cs, int nb1, int64_t y_b1, double tol_share,
-                       const double* Ysrc = nullptr) {
+sma_status gram_form(sma_ctx* h, Prob<T>& P, int slot, const GramSpec& gs) {
   cudaStream_t st = h->st;
-  if (!Ysrc) Ysrc = P.X64;
-  double* G = P.gram + (size_t)slot * P.gstride;
+  const int rows = gs.rows, K = gs.K, nb1 = gs.nb1;
+  const int64_t y_rs = gs.y_rs, y_cs = gs.y_cs, y_b1 = gs.y_b1;
+  const double* Ysrc = gs.src ? gs.src : P.X64;
   stage_begin(h, SMA_STAGE_TRANSFORM);
+  double* G = P.gram + (size_t)slot * P.gstride;
   {
     // the unfolding Y (rows x Ktot): strided in X64, or laid out contiguously
     // first when it sums over a batch index
@@ -1198,36 +1229,89 @@ sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_
     }
   }
   stage_end(h);
+  return SMA_OK;
+}
+
+// Eigenpairs of the Grams in slots [slot, slot + count), all of order rows:
+// one cooperative launch per Gram from kCoopMinRows up, otherwise one
+// single-CTA launch for the whole group (one CTA per Gram, through the
+// per-slot descriptors).
+template <typename T>
+sma_status gram_solve(sma_ctx* h, Prob<T>& P, int slot, int count, int rows) {
+  cudaStream_t st = h->st;
   stage_begin(h, SMA_STAGE_SVD);
   JacobiPlan jp = jacobi_plan<double>(rows, rows, h->max_smem);
-  const JacobiPlan cp = jacobi_coop_plan<double>(rows, h->max_smem);
+  JacobiPlan cp{};
+  if (rows >= kCoopMinRows) cp = jacobi_coop_plan<double>(rows, h->max_smem);
   const bool coop = rows >= kCoopMinRows && cp.smem > 0 && h->coop_bar;
   if (coop) jp = cp;
-  double* W = (jp.block_mode || coop) ? P.Wg : nullptr;
   JacobiParams<double> J;
-  J.src = G; J.src_bs = 0; J.m = rows; J.n = rows;
+  J.m = rows; J.n = rows;
   J.mm = jp.mm; J.rc = jp.rc; J.trans = 0; J.ldS = jp.ldS; J.bcols = jp.bcols; J.g = jp.g;
   J.sort_n = jp.sort_n; J.tile = jp.tile;
   J.max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
   J.tol = 4.0 * std::sqrt((double)rows) * Eps<double>::v;
-  J.W = W; J.W_bs = 0;
-  J.U = P.gW; J.U_bs = 0;                                   // G V (not needed)
-  J.V = P.gvec + (size_t)slot * P.gstride; J.V_bs = 0;     // eigenvectors of G
-  J.sigma = P.gsig + (size_t)slot * P.gdim;
-  J.sweeps = P.sweeps + slot; J.status = P.status;
-  if (coop) {
-    SMA_K(jacobi_svd_coop<double>(J, cp, CoopSync{h->coop_bar, h->coop_rot, h->coop_abort}, st));
-  } else {
-    SMA_K(jacobi_svd<double>(J, 1, jp.threads, jp.smem, st));
+  J.status = P.status;
+  if (!coop && !jp.block_mode && count > 1 && P.gdesc) {
+    J.desc = P.gdesc + slot;
+    SMA_K(jacobi_svd<double>(J, count, jp.threads, jp.smem, st));
+    stage_end(h);
+    return SMA_OK;
+  }
+  for (int c = 0; c < count; ++c) {
+    const int sl = slot + c;
+    J.src = P.gram + (size_t)sl * P.gstride; J.src_bs = 0;
+    J.W = (jp.block_mode || coop) ? P.Wg : nullptr; J.W_bs = 0;
+    J.U = P.gW; J.U_bs = 0;                                   // G V (not needed)
+    J.V = P.gvec + (size_t)sl * P.gstride; J.V_bs = 0;       // eigenvectors of G
+    J.sigma = P.gsig + (size_t)sl * P.gdim;
+    J.sweeps = P.sweeps + sl;
+    if (coop) {
+      SMA_K(jacobi_svd_coop<double>(J, cp, CoopSync{h->coop_bar, h->coop_rot, h->coop_abort}, st));
+    } else {
+      SMA_K(jacobi_svd<double>(J, 1, jp.threads, jp.smem, st));
+    }
   }
   stage_end(h);
+  return SMA_OK;
+}
+
+// Rank of slot's mode: the Gram's eigenvalues are the energies sigma^2 of the
+// unfolding; the budget is (rel_tol share)^2 ||X||^2, or fixed_rank.
+template <typename T>
+sma_status gram_truncate(sma_ctx* h, Prob<T>& P, int slot, int rows, double share) {
   stage_begin(h, SMA_STAGE_TRUNCATE);
-  // the Gram's singular values are the energies sigma^2 of the unfolding
-  SMA_K(truncate_ranks(P.gsig + (size_t)slot * P.gdim, rows, 1, P.stats, h->opt.rel_tol * tol_share,
+  SMA_K(truncate_ranks(P.gsig + (size_t)slot * P.gdim, rows, 1, P.stats, h->opt.rel_tol * share,
                         h->opt.fixed_rank, P.ranks + slot, P.off, P.stats + 2 + slot,
-                        P.iscal + 2 + slot, P.suf + (size_t)slot * (P.gdim + 1), st, 1));
+                        P.iscal + 2 + slot, P.suf + (size_t)slot * (P.gdim + 1), h->st, 1));
   stage_end(h);
   return SMA_OK;
+}
+
+// Every Gram of a compression: form them all, solve consecutive slots of one
+// small order together, then the ranks.
+template <typename T>
+sma_status gram_all(sma_ctx* h, Prob<T>& P, const GramSpec* gs, int n) {
+  for (int i = 0; i < n; ++i) SMA_TRY(gram_form(h, P, i, gs[i]));
+  for (int i = 0; i < n;) {
+    int j = i + 1;
+    if (gs[i].rows < kCoopMinRows)
+      while (j < n && gs[j].rows == gs[i].rows) ++j;
+    SMA_TRY(gram_solve(h, P, i, j - i, gs[i].rows));
+    i = j;
+  }
+  for (int i = 0; i < n; ++i) SMA_TRY(gram_truncate(h, P, i, gs[i].rows, gs[i].share));
+  return SMA_OK;
+}
+
+template <typename T>
+sma_status gram_factor(sma_ctx* h, Prob<T>& P, int slot, int rows, int K, int64_t y_rs,
+                       int64_t y_cs, int nb1, int64_t y_b1, double tol_share,
+                       const double* Ysrc = nullptr) {
+  const GramSpec gs{rows, K, y_rs, y_cs, nb1, y_b1, tol_share, Ysrc};
+  SMA_TRY(gram_form(h, P, slot, gs));
+  SMA_TRY(gram_solve(h, P, slot, 1, rows));
+  return gram_truncate(h, P, slot, rows, tol_share);
 }
 
 // Section 6.3, randomized block-index factor: the sketch Y_k = Omega^T X_k Psi
@@ -1324,17 +1408,19 @@ sma_status compress_tucker(sma_ctx* h, Prob<T>& P) {
     stage_end(h);
     return SMA_OK;
   }
-  // mode-1 unfolding [X_1 ... X_p] (m x np): Gram = sum_k X_k X_k^T
+  // mode-1 unfolding [X_1 ... X_p] (m x np): Gram = sum_k X_k X_k^T;
+  // ROWCOL also the mode-2 unfolding [X_1^T ... X_p^T] (n x mp)
   const int ntr = 2;  // two truncated modes share the budget
-  SMA_TRY(gram_factor(h, P, 0, m, (int)(mn * p / m), 1, m, 1, 0, 1.0 / std::sqrt((double)ntr)));
+  const double share = 1.0 / std::sqrt((double)ntr);
+  const GramSpec gs[2] = {{m, (int)(mn * p / m), 1, m, 1, 0, share, nullptr},
+                          {n, m, m, 1, p, mn, share, nullptr}};
+  SMA_TRY(gram_all(h, P, gs, d == SMA_TUCKER_ROWCOL ? 2 : 1));
   SMA_K(convert<T, double>(P.gvec, P.F1, (int64_t)m * m, st));
   const int* r1 = P.iscal + 2;
   const int* r3 = r1;
   const T* Wf = P.F1;
   int ldw = m;
   if (d == SMA_TUCKER_ROWCOL) {
-    // mode-2 unfolding [X_1^T ... X_p^T] (n x mp): Gram = sum_k X_k^T X_k
-    SMA_TRY(gram_factor(h, P, 1, n, m, m, 1, p, mn, 1.0 / std::sqrt((double)ntr)));
     SMA_K(convert<T, double>(P.gvec + P.gstride, P.F2, (int64_t)n * n, st));
     r3 = P.iscal + 3;
     Wf = P.F2;
@@ -1398,10 +1484,12 @@ sma_status compress_ml2(sma_ctx* h, Prob<T>& P) {
   const int64_t mn = (int64_t)m * n;
   SMA_K(convert<double, T>(P.X, P.X64, mn * p, st));
   const double share = 0.5;   // four truncated modes: tol^2 ||X||^2 / 4 each
-  SMA_TRY(gram_factor(h, P, 0, m, (int)(n * (int64_t)p), 1, m, 1, 0, share));          // a
-  SMA_TRY(gram_factor(h, P, 1, n, m, m, 1, p, mn, share));                              // b
-  SMA_TRY(gram_factor(h, P, 2, p1, (int)mn, mn, 1, p2, mn * p1, share));                // i1
-  SMA_TRY(gram_factor(h, P, 3, p2, (int)(mn * p1), mn * p1, 1, 1, 0, share));           // i2
+  const GramSpec gs[4] = {
+      {m, (int)(n * (int64_t)p), 1, m, 1, 0, share, nullptr},        // a
+      {n, m, m, 1, p, mn, share, nullptr},                           // b
+      {p1, (int)mn, mn, 1, p2, mn * p1, share, nullptr},             // i1
+      {p2, (int)(mn * p1), mn * p1, 1, 1, 0, share, nullptr}};       // i2
+  SMA_TRY(gram_all(h, P, gs, 4));
   stage_begin(h, SMA_STAGE_FACTORS);
   const int dims[4] = {m, n, p1, p2};
   for (int t = 0; t < 4; ++t)
@@ -1512,9 +1600,10 @@ sma_status compress_multilevel(sma_ctx* h, Prob<T>& P, const void* Ain) {
   SMA_K(convert<double, T>(P.X, P.X64, np, st));
   stage_end(h);
   const double share = 1.0 / std::sqrt(3.0);
-  SMA_TRY(gram_factor(h, P, 0, p1, p2 * p3, 1, p1, 1, 0, share));                 // mode 1
-  SMA_TRY(gram_factor(h, P, 1, p2, p1, p1, 1, p3, (int64_t)p1 * p2, share));       // mode 2
-  SMA_TRY(gram_factor(h, P, 2, p3, p1 * p2, (int64_t)p1 * p2, 1, 1, 0, share));    // mode 3
+  const GramSpec gs[3] = {{p1, p2 * p3, 1, p1, 1, 0, share, nullptr},                   // mode 1
+                          {p2, p1, p1, 1, p3, (int64_t)p1 * p2, share, nullptr},       // mode 2
+                          {p3, p1 * p2, (int64_t)p1 * p2, 1, 1, 0, share, nullptr}};   // mode 3
+  SMA_TRY(gram_all(h, P, gs, 3));
   stage_begin(h, SMA_STAGE_FACTORS);
   for (int t = 0; t < 3; ++t)
     SMA_K(convert<T, double>(P.gvec + P.gstride * t, P.Uml[t], (int64_t)P.lp[t] * P.lp[t], st));
