@@ -2091,7 +2091,9 @@ sma_status apply_multilevel(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* 
     g.nb2 = nv;
     SMA_K(contract<T>(h, g));
   }
-  {  // S2 (batched over a3)
+  if (k3 <= 16) {  // S2: the core over j3 for every (a3, column), coalesced over a3
+    SMA_K(ml_core<T>(P.Gcmp, k1 * k2, k3, P.U3x, l3, n21 * nv, P.Vml, st));
+  } else {  // S2 (batched over a3)
     GemmParams<T> g;
     g.M = k1 * k2; g.N = (int)(n21 * nv); g.K = k3;
     g.A = P.Gcmp; g.a_rs = 1; g.a_cs = (int64_t)k1 * k2;

@@ -185,6 +185,12 @@ cudaError_t struct_strided(const int* map, const double* isq, int ell, int q, co
                            cudaStream_t st);
 template <typename T>
 cudaError_t ml_scatter(const MlMaps& mp, const T* Tt, T* Ahat, int64_t ld, cudaStream_t st);
+// V[a3 + l3 j12 + l3 k12 c] = sum_j3 G[j12 + k12 j3] U[a3 + l3 j3 + l3 k3 c]
+// for a3 < l3, c < ncol, j12 < k12, j3 < k3 (k3 <= 16): the core contraction of
+// the three-level matvec, memory-bound, coalesced over a3.
+template <typename T>
+cudaError_t ml_core(const T* G, int k12, int k3, const T* U, int l3, int64_t ncol, T* V,
+                    cudaStream_t st);
 
 // copy and precision conversion helpers
 // dst[i0 + n0 (i1 + n1 i2)] = src[i0 s0 + i1 s1 + i2 s2] (fp64)

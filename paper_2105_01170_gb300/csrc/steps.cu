@@ -475,6 +475,53 @@ __global__ void ml2_terms_kernel(const T* __restrict__ G, int mn, int p1, int p2
   if (t == 0 && threadIdx.x == 0) *nterms = k1 * k2;
 }
 
+// Core step of the three-level matvec: for every column c and a3,
+// V[a3 + l3 j12 + l3 k12 c] = sum_j3 G[j12 + k12 j3] U[a3 + l3 j3 + l3 k3 c]
+// (j12 < k12, j3 < k3 <= 16); threads run over a3 fastest, so both sides are
+// coalesced.  G (k12 x k3) is staged in shared memory.
+template <typename T>
+__global__ void ml_core_kernel(const T* __restrict__ G, int k12, int k3, const T* __restrict__ U,
+                               int l3, int64_t ncol, T* __restrict__ V) {
+  extern __shared__ unsigned char sm_raw[];
+  T* Gs = reinterpret_cast<T*>(sm_raw);
+  for (int e = threadIdx.x; e < k12 * k3; e += blockDim.x) Gs[e] = G[e];
+  __syncthreads();
+  const int64_t total = (int64_t)l3 * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a3 = (int)(e % l3);
+    const int64_t c = e / l3;
+    T u[16];
+#pragma unroll
+    for (int j3 = 0; j3 < 16; ++j3)
+      u[j3] = j3 < k3 ? U[a3 + (int64_t)l3 * j3 + (int64_t)l3 * k3 * c] : T(0);
+    T* v = V + a3 + (int64_t)l3 * k12 * c;
+    for (int j12 = 0; j12 < k12; ++j12) {
+      T acc = T(0);
+#pragma unroll
+      for (int j3 = 0; j3 < 16; ++j3)
+        if (j3 < k3) acc = fma(Gs[j12 + k12 * j3], u[j3], acc);
+      v[(int64_t)l3 * j12] = acc;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t ml_core(const T* G, int k12, int k3, const T* U, int l3, int64_t ncol, T* V,
+                    cudaStream_t st) {
+  if (k3 < 1 || k3 > 16 || k12 < 1 || l3 < 1) return cudaErrorInvalidValue;
+  const int64_t total = (int64_t)l3 * ncol;
+  int64_t grid = (total + 255) / 256;
+  if (grid > 152 * 32) grid = 152 * 32;
+  ml_core_kernel<T><<<(int)grid, 256, (size_t)k12 * k3 * sizeof(T), st>>>(G, k12, k3, U, l3, ncol,
+                                                                          V);
+  return cudaGetLastError();
+}
+template cudaError_t ml_core<float>(const float*, int, int, const float*, int, int64_t, float*,
+                                    cudaStream_t);
+template cudaError_t ml_core<double>(const double*, int, int, const double*, int, int64_t,
+                                     double*, cudaStream_t);
+
 // V[:, j] /= sqrt(ev[j]) for j < *r (zero column where ev[j] <= 0).
 __global__ void scale_cols_rsqrt_kernel(double* V, int64_t ld, int rows, const double* ev,
                                         const int* r) {
