@@ -318,9 +318,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 // operand layout of the long-K product: row i = c + n s, column j = a + ell t
 // go to Z[p * plane + (a + ell s) * Kp + c + n t].  One CTA per 128 x 256
 // tile, two stages (two CTAs per SM, so one CTA's epilogue overlaps the other
-// CTA's loads and MMAs), four epilogue warps, 256 TMEM columns.
+// CTA's loads and MMAs), 256 TMEM columns.  The kernel is bound by writing the
+// planes: sixteen epilogue warps (four per TMEM lane quadrant, a quarter of
+// the columns each) keep enough stores in flight, and the stores are
+// streaming (.cs), since the planes are read back only by the next kernel.
 constexpr int MID_STAGES = 2;
-constexpr int MID_EPI_WARPS = 4;
+constexpr int MID_EPI_WARPS = 16;
 constexpr int MID_THREADS = 64 + 32 * MID_EPI_WARPS;
 constexpr int MID_TMEM = 256;
 constexpr int MID_SMEM = MID_STAGES * STAGE_BYTES + 1024 + 256;
@@ -417,6 +420,7 @@ tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     mma_commit(accf);  // arrives when every MMA issued above has completed
   } else if (warp >= 2) {
     const int q = warp & 3;
+    const int hp = (warp - 2) >> 2;   // which quarter of the columns
     const int grow = m0 + q * 32 + lane;
     const bool ok = mbar_wait(accf, 0u);
     fence_after();
@@ -426,7 +430,7 @@ tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
       const int c = grow % args.n, s = grow / args.n;
       const int64_t rbase = (int64_t)args.ell * s * args.Kp + c;
 #pragma unroll 1
-      for (int part = 0; part < BN / 32; ++part) {
+      for (int part = hp * (BN / 128); part < (hp + 1) * (BN / 128); ++part) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(part * 32), r);
         const int g0 = n0 + part * 32;
@@ -438,9 +442,9 @@ tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
               __nv_bfloat16 hi, mi, lo;
               split3(__uint_as_float(r[jj]), hi, mi, lo);
               __nv_bfloat16* d = args.Z + rbase + (int64_t)a * args.Kp + (int64_t)args.n * t;
-              d[0] = hi;
-              d[args.plane] = mi;
-              d[2 * args.plane] = lo;
+              asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d), "h"(__bfloat16_as_ushort(hi)) : "memory");
+              asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d + args.plane), "h"(__bfloat16_as_ushort(mi)) : "memory");
+              asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d + 2 * args.plane), "h"(__bfloat16_as_ushort(lo)) : "memory");
             }
             if (++a == args.ell) {
               a = 0;
