@@ -330,6 +330,7 @@ constexpr int MID_SMEM = MID_STAGES * STAGE_BYTES + 1024 + 256;
 
 struct MidArgs {
   int M, N, Kq, n, ell;
+  int pairs;   // n even and Z, Kp, plane allow 32-bit stores of two rows
   int64_t Kp, plane;
   __nv_bfloat16* Z;
   int* err;
@@ -426,7 +427,55 @@ tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     fence_after();
     if (!ok) *abort_flag = 1;
     __syncwarp();
-    if (!*abort_flag) {
+    if (!*abort_flag && args.pairs) {
+      // rows c and c + 1 (an even and an odd lane) are adjacent in Z: the lane
+      // pair swaps one value per column pair so that each lane holds both rows
+      // of one column, splits them together and stores 32-bit words
+      const bool odd = lane & 1;
+      const int row0 = grow - (odd ? 1 : 0);                // the pair's first row
+      const int c0 = row0 % args.n, s0 = row0 / args.n;
+      const bool rows_ok = row0 + 1 < args.M;
+      const int64_t rbase = (int64_t)args.ell * s0 * args.Kp + c0;
+#pragma unroll 1
+      for (int part = hp * (BN / 128); part < (hp + 1) * (BN / 128); ++part) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(part * 32), r);
+        const int g0 = n0 + part * 32;
+        // (a, t) of the even column of each pair, advanced by two per pair
+        int t = g0 / args.ell, a = g0 - t * args.ell;
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          const float xe = __uint_as_float(r[2 * kk]), xo = __uint_as_float(r[2 * kk + 1]);
+          const float got = __shfl_xor_sync(0xffffffffu, odd ? xe : xo, 1);
+          const float v0 = odd ? got : xe;                  // row0 at this lane's column
+          const float v1 = odd ? xo : got;                  // row0 + 1
+          int aj = a + (odd ? 1 : 0), tj = t;
+          if (aj >= args.ell) {
+            aj -= args.ell;
+            ++tj;
+          }
+          const int gj = g0 + 2 * kk + (odd ? 1 : 0);
+          if (rows_ok && gj < args.N) {
+            __nv_bfloat16 h0, m0_, l0, h1, m1, l1;
+            split3(v0, h0, m0_, l0);
+            split3(v1, h1, m1, l1);
+            const uint32_t wh = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            const uint32_t wm = (uint32_t)__bfloat16_as_ushort(m0_) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
+            const uint32_t wl = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            __nv_bfloat16* d = args.Z + rbase + (int64_t)aj * args.Kp + (int64_t)args.n * tj;
+            asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d), "r"(wh) : "memory");
+            asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d + args.plane), "r"(wm) : "memory");
+            asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d + 2 * args.plane), "r"(wl) : "memory");
+          }
+          a += 2;
+          while (a >= args.ell) {
+            a -= args.ell;
+            ++t;
+          }
+        }
+      }
+    }
+    if (!*abort_flag && !args.pairs) {
       const int c = grow % args.n, s = grow / args.n;
       const int64_t rbase = (int64_t)args.ell * s * args.Kp + c;
 #pragma unroll 1
@@ -579,7 +628,11 @@ cudaError_t tc_mid_planes(const __nv_bfloat16* A, int M, const __nv_bfloat16* B,
   const cudaError_t attr = cudaFuncSetAttribute(
       tc_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MID_SMEM);
   if (attr != cudaSuccess) return attr;
-  MidArgs a{M, N, (int)Kq, n, ell, Kp, zplane, Z, err};
+  const int pairs = (n % 2 == 0 && M % 2 == 0 && Kp % 2 == 0 && zplane % 2 == 0 &&
+                     (reinterpret_cast<uintptr_t>(Z) & 3) == 0)
+                        ? 1
+                        : 0;
+  MidArgs a{M, N, (int)Kq, n, ell, pairs, Kp, zplane, Z, err};
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
   tc_mid_kernel<<<grid, MID_THREADS, MID_SMEM, st>>>(ma, mb, a);
   return cudaGetLastError();
