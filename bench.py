@@ -41,13 +41,26 @@ REL_TOL = 1e-6
 METRIC = "t-SVDM compressions/s + Kron-sum matvec GFLOP/s, mixed vs FP64 GPU, equal err"
 # DRAM bytes (read + write) of one slice of the register-tiled Jacobi SVD at
 # 256 x 256, from an ncu capture of the 15-slice case (4,164,096 B read, 0
-# written; profiles/jacobi_kernel_spacetime_T8_256x256x15.md); every slice
-# moves the same bytes, so a launch moves p times this
+# written); every slice moves the same bytes, so a launch moves p times this
 JACOBI_DRAM_BYTES_PER_SLICE = 4164096 / 15
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+def replica_throughput(t_local, steps, dist=None, device=None):
+    """Whole-job throughput of N independent replicas: every rank runs `steps`
+    steps; the job takes as long as its slowest rank (the max over ranks of
+    the local timed total), and the value counts the steps of all ranks."""
+    import torch
+    world = dist.get_world_size() if dist else 1
+    t = float(t_local)
+    if dist:
+        tt = torch.tensor([t], device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return world * steps / t, t
 
 
 def peaks():
@@ -354,11 +367,7 @@ def main():
     clk = clocks.stop()
     step_ms = float(np.mean(mixed["compress_ms"] + mixed["apply_ms"]))
     t_total = float(np.sum(mixed["compress_ms"] + mixed["apply_ms"])) / 1e3
-    if dist:
-        tt = torch.tensor([t_total], device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-    value = world * args.steps / t_total
+    value, t_total = replica_throughput(t_total, args.steps, dist, device)
 
     res = mixed["result"]
     prof = mixed["profile"]
