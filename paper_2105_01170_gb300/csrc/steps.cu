@@ -281,30 +281,38 @@ template <typename T>
 __global__ void orth_kernel(const T* __restrict__ Gm, int rc, const int* __restrict__ ranks,
                             const double* __restrict__ scale, double* out, int use_inv) {
   // G[a, b] / (s_a s_b) - delta_ab with the reciprocals 1 / s_a staged once
-  // per slice (fp64 division is slow on this part); 0 where s_a = 0
-  extern __shared__ double inv[];
+  // per slice; the per-element products run in the element type (fp32 on the
+  // mixed path, whose factors carry fp32 accuracy; fp64 arithmetic is slow on
+  // this part); 0 where s_a = 0 (or below the fp32 range)
+  extern __shared__ double inv_raw[];
+  T* inv = reinterpret_cast<T*>(inv_raw);
   __shared__ double red[32];
   const int i = blockIdx.x;
   const int r = ranks ? ranks[i] : rc;
   const T* G = Gm + (int64_t)i * rc * rc;
   const double* sc = scale ? scale + (int64_t)i * rc : nullptr;
+  const double smin = sizeof(T) == 4 ? 1e-30 : 0.0;
   if (sc && use_inv) {
-    for (int a = threadIdx.x; a < r; a += blockDim.x) inv[a] = sc[a] > 0 ? 1.0 / sc[a] : 0.0;
+    for (int a = threadIdx.x; a < r; a += blockDim.x)
+      inv[a] = sc[a] > smin ? (T)(1.0 / sc[a]) : T(0);
     __syncthreads();
   }
-  double mx = 0.0;
+  T mxt = T(0);
+  double mxd = 0.0;
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int a = e % r, b = e / r;
-    double g = (double)G[a + (int64_t)b * rc];
     if (sc && use_inv) {
-      const double ia = inv[a], ib = inv[b];
-      g = (ia > 0 && ib > 0) ? g * ia * ib : (a == b ? 1.0 : 0.0);
-    } else if (sc) {
-      g = (sc[a] > 0 && sc[b] > 0) ? g / (sc[a] * sc[b]) : (a == b ? 1.0 : 0.0);
+      const T ia = inv[a], ib = inv[b];
+      const T g = (ia > T(0) && ib > T(0)) ? G[a + (int64_t)b * rc] * ia * ib
+                                           : (a == b ? T(1) : T(0));
+      mxt = fmax(mxt, fabs(g - (a == b ? T(1) : T(0))));
+    } else {
+      double g = (double)G[a + (int64_t)b * rc];
+      if (sc) g = (sc[a] > 0 && sc[b] > 0) ? g / (sc[a] * sc[b]) : (a == b ? 1.0 : 0.0);
+      mxd = fmax(mxd, fabs(g - (a == b ? 1.0 : 0.0)));
     }
-    const double v = g - (a == b ? 1.0 : 0.0);
-    mx = fmax(mx, fabs(v));
   }
+  double mx = fmax(mxd, (double)mxt);
   // block max via shared memory
   mx = warp_max(mx);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
