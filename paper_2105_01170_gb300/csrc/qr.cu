@@ -27,7 +27,7 @@
 namespace sma {
 namespace {
 
-constexpr int QR_THREADS = 512;
+constexpr int QR_THREADS = 768;
 constexpr int QR_RPL = 8;   // rows per lane held in registers by the column update
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
