@@ -37,7 +37,7 @@ def _worker(rank, world, port, out):
 
 def test_replica_throughput_is_steps_of_all_ranks_over_the_slowest():
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
