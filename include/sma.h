@@ -150,11 +150,16 @@ typedef struct {
  * paper only needs the SVD).  SMA_PRECOND_QRCP factors each slice (or its
  * transpose) as B P = Q1 R1 by a column-pivoted Householder QR and runs the
  * one-sided Jacobi SVD on R1^T, which converges in fewer sweeps (Drmac and
- * Veselic 2008); SMA_PRECOND_AUTO does so when min(m, n) >= 128.           */
+ * Veselic 2008).  SMA_PRECOND_QRCP2 adds a second (unpivoted) QR,
+ * R1^T = Q2 R2, and runs the Jacobi on R2^T (fewer sweeps again; slices
+ * with max(m, n) <= 256, otherwise it acts as SMA_PRECOND_QRCP).
+ * SMA_PRECOND_AUTO takes both QRs when min(m, n) >= 128 (and
+ * max(m, n) <= 256), the first one alone when min(m, n) >= 128 otherwise. */
 typedef enum {
   SMA_PRECOND_AUTO = 0,
   SMA_PRECOND_NONE = 1,
-  SMA_PRECOND_QRCP = 2
+  SMA_PRECOND_QRCP = 2,
+  SMA_PRECOND_QRCP2 = 3
 } sma_precondition;
 
 typedef struct {

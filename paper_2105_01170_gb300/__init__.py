@@ -33,7 +33,7 @@ SMA_TUCKER_SPD = 5
 SMA_CP_ALS = 6
 SMA_M_DCT2, SMA_M_IDENTITY, SMA_M_USER = 0, 1, 2
 SMA_INPUT_DENSE, SMA_INPUT_BLOCKS = 0, 1
-SMA_PRECOND_AUTO, SMA_PRECOND_NONE, SMA_PRECOND_QRCP = 0, 1, 2
+SMA_PRECOND_AUTO, SMA_PRECOND_NONE, SMA_PRECOND_QRCP, SMA_PRECOND_QRCP2 = 0, 1, 2, 3
 EXPORT_X, EXPORT_XHAT, EXPORT_SIGMA, EXPORT_T, EXPORT_FACTOR, EXPORT_CHOL = 0, 1, 2, 3, 4, 5
 EXPORT_CP_X, EXPORT_CP_Z = 6, 7
 

@@ -23,13 +23,14 @@ using namespace sma;
 
 namespace {
 
-// SMA_PRECOND_AUTO preconditions the slice SVD by a column-pivoted QR from
-// this min(m, n) on (below it the factorisation costs more than the sweeps
-// it saves)
 // Gram eigen-solves of this order and larger run over many CTAs
 // (jacobi_svd_coop); smaller ones in one CTA.
 constexpr int kCoopMinRows = 40;
+// SMA_PRECOND_AUTO preconditions the slice SVD by a column-pivoted QR from
+// this min(m, n) on (below it the factorisation costs more than the sweeps
+// it saves), and by two from kQr2AutoMin on
 constexpr int kQrAutoMin = 128;
+constexpr int kQr2AutoMin = 128;
 
 #define SMA_CK(...)                                 \
   do {                                              \
@@ -151,6 +152,13 @@ struct Prob {
   T* qJ = nullptr;
   T* qRt = nullptr;
   T* qL = nullptr;
+  // second QR (unpivoted, blocked), of R1^T = Q2 R2: the Jacobi runs on
+  // R2^T, and the rebuild uses L = Q1 [W_d; 0] and Rt = P Q2 V_d
+  bool qr2 = false;
+  T* qF2 = nullptr;
+  T* qtau2 = nullptr;
+  int* qperm2 = nullptr;
+  T* qJ2 = nullptr;
   double* sigma = nullptr;
   double* suf = nullptr;
   int* ranks = nullptr;
@@ -668,8 +676,11 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     P.qplan = qr_plan<T>(P.mm, P.rc, h->max_smem);
     const bool qr_fits = P.qplan.smem_qr <= (size_t)h->max_smem &&
                          P.qplan.smem_fin <= (size_t)h->max_smem && P.qplan.fslot >= 0;
-    P.qr = qr_fits && (o.precondition == SMA_PRECOND_QRCP ||
+    P.qr = qr_fits && (o.precondition == SMA_PRECOND_QRCP || o.precondition == SMA_PRECOND_QRCP2 ||
                        (o.precondition == SMA_PRECOND_AUTO && P.rc >= kQrAutoMin));
+    P.qr2 = P.qr && P.mm <= kQrWarpRows &&
+            (o.precondition == SMA_PRECOND_QRCP2 ||
+             (o.precondition == SMA_PRECOND_AUTO && P.rc >= kQr2AutoMin));
     P.jp = P.qr ? jacobi_plan<T>(P.rc, P.rc, h->max_smem) : jacobi_plan<T>(m, n, h->max_smem);
     SMA_TRY(mem.alloc(&P.Xh, mnp));
     if (P.jp.block_mode)
@@ -684,6 +695,13 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
       SMA_TRY(mem.alloc(&P.qJ, rr));
       SMA_TRY(mem.alloc(&P.qRt, rr));
       SMA_TRY(mem.alloc(&P.qL, frc));
+    }
+    if (P.qr2) {
+      const size_t rr = (size_t)P.rc * P.rc * p;
+      SMA_TRY(mem.alloc(&P.qF2, rr));
+      SMA_TRY(mem.alloc(&P.qtau2, (size_t)P.rc * p));
+      SMA_TRY(mem.alloc(&P.qperm2, (size_t)P.rc * p));
+      SMA_TRY(mem.alloc(&P.qJ2, rr));
     }
     SMA_TRY(mem.alloc(&P.V, (size_t)P.rc * P.rc * p));
     SMA_TRY(mem.alloc(&P.sigma, (size_t)P.rc * p));
@@ -957,6 +975,33 @@ QrParams<T> qr_params(const Prob<T>& P) {
   return q;
 }
 
+// The second QR: R1^T (rc x rc, the first QR's Jacobi input) = Q2 R2
+// (perm2 = identity).
+template <typename T>
+QrParams<T> qr2_params(const Prob<T>& P) {
+  QrParams<T> q;
+  q.src = P.qJ; q.src_bs = (int64_t)P.rc * P.rc;
+  q.m = P.rc; q.mm = P.rc; q.rc = P.rc; q.trans = 0;
+  q.F = P.qF2; q.F_bs = (int64_t)P.rc * P.rc;
+  q.tau = P.qtau2; q.perm = P.qperm2;
+  q.Jin = P.qJ2; q.J_bs = (int64_t)P.rc * P.rc;
+  return q;
+}
+
+// The Jacobi input of a preconditioned problem: R2^T after two QRs, else R1^T.
+template <typename T>
+const T* qr_jacobi_input(const Prob<T>& P) {
+  return P.qr2 ? P.qJ2 : P.qJ;
+}
+
+// Both QRs of a preconditioned problem's slices.
+template <typename T>
+cudaError_t qr_precondition(const Prob<T>& P, cudaStream_t st) {
+  cudaError_t e = qrcp<T>(qr_params(P), P.p, st);
+  if (e == cudaSuccess && P.qr2) e = qr_blocked<T>(qr2_params(P), P.p, st);
+  return e;
+}
+
 // ---- autotuner of the slice-SVD plan ---------------------------------------
 // On the first compression of a slice shape (options.autotune), every
 // candidate plan (jacobi_plan_candidates) runs twice on the actual slices and
@@ -1036,13 +1081,13 @@ sma_status tsvdm_svd(sma_ctx* h, Prob<T>& P) {
   const int64_t mn = (int64_t)m * n;
   if (P.qr) {
     stage_begin(h, SMA_STAGE_PRECOND);
-    SMA_K(qrcp<T>(qr_params(P), p, st));
+    SMA_K(qr_precondition<T>(P, st));
     stage_end(h);
   }
   auto params = [&](const JacobiPlan& jp) {
     JacobiParams<T> J = jacobi_params<T>(h, jp);
     if (P.qr) {
-      J.src = P.qJ; J.src_bs = (int64_t)rc * rc; J.m = rc; J.n = rc;
+      J.src = qr_jacobi_input(P); J.src_bs = (int64_t)rc * rc; J.m = rc; J.n = rc;
     } else {
       J.src = P.Xh; J.src_bs = mn; J.m = m; J.n = n;
     }
@@ -1067,7 +1112,7 @@ template <typename T>
 sma_status tsvdm_svd_batched(sma_ctx* h) {
   stage_begin(h, SMA_STAGE_PRECOND);
   for (auto& P : probs<T>(h))
-    if (P.qr) SMA_K(qrcp<T>(qr_params(P), P.p, h->st));
+    if (P.qr) SMA_K(qr_precondition<T>(P, h->st));
   stage_end(h);
   auto params = [&](const SvdBin<T>& b, const JacobiPlan& jp) {
     JacobiParams<T> J = jacobi_params<T>(h, jp);
@@ -1116,7 +1161,8 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P, bool truncated) {
   }
   if (P.qr) {
     stage_begin(h, SMA_STAGE_PRECOND);
-    SMA_K(qr_finish<T>(qr_params(P), P.ranks, p, st));
+    const QrParams<T> q2 = qr2_params(P);
+    SMA_K(qr_finish<T>(qr_params(P), P.qr2 ? &q2 : nullptr, P.ranks, p, st));
     stage_end(h);
   }
   stage_begin(h, SMA_STAGE_FACTORS);
@@ -1125,7 +1171,8 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P, bool truncated) {
   // processed transposed.  Subtracting the discarded part keeps the error of
   // the rebuilt slice proportional to the discarded energy, not to ||Xhat_i||.
   // With the QR preconditioning the slice is (Q1 V)(P W)^T: L = Q1 [V_d; 0]
-  // and Rt = P W take the places of W and V.
+  // and Rt = P W take the places of W and V; after two QRs it is
+  // (Q1 W)(P Q2 V)^T, with L = Q1 [W_d; 0] and Rt = P Q2 V_d.
   const int64_t urc = (int64_t)mm * rc, vrc = (int64_t)rc * rc;
   T* const Lf = P.qr ? P.qL : P.U;
   T* const Rf = P.qr ? P.qRt : P.V;
@@ -2566,7 +2613,7 @@ sma_status build_bins(sma_ctx* h) {
     }
     const int64_t jmn = (int64_t)jm * jn, urc = (int64_t)P.jp.mm * P.rc,
                   vrc = (int64_t)P.rc * P.rc;
-    const T* jsrc = P.qr ? P.qJ : P.Xh;
+    const T* jsrc = P.qr ? qr_jacobi_input(P) : P.Xh;
     for (int k = 0; k < P.p; ++k)
       host[bi].push_back(SliceDesc<T>{jsrc + k * jmn, P.U + k * urc, P.V + k * vrc,
                                       P.sigma + (int64_t)k * P.rc, P.sweeps + k, P.status});
@@ -2647,7 +2694,7 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   if ((int)opt->mkind < 0 || opt->mkind > SMA_M_USER) return SMA_ERR_ARG;
   if (opt->layout != SMA_INPUT_DENSE && opt->layout != SMA_INPUT_BLOCKS) return SMA_ERR_ARG;
   if (opt->fixed_rank < 0 || !(opt->rel_tol >= 0.0)) return SMA_ERR_ARG;
-  if ((int)opt->precondition < 0 || opt->precondition > SMA_PRECOND_QRCP) return SMA_ERR_ARG;
+  if ((int)opt->precondition < 0 || opt->precondition > SMA_PRECOND_QRCP2) return SMA_ERR_ARG;
   if (opt->autotune < 0 || opt->autotune > 1) return SMA_ERR_ARG;
   if (opt->sketch_cols < 0) return SMA_ERR_ARG;
   if (opt->sketch_cols > 0) {

@@ -118,9 +118,19 @@ struct QrParams {
 };
 // B P = Q1 R1 for every slice's working matrix B (mm x rc); writes R1^T.
 template <typename T> cudaError_t qrcp(const QrParams<T>& P, int nslices, cudaStream_t st);
-// Rt = P W and L_d = Q1 [V_d; 0] for columns ranks[s]..rc-1.
+// Unpivoted blocked Householder QR of every slice's n x n matrix (mm == rc
+// == n <= kQrWarpRows, ld m), same outputs as qrcp with perm = identity.
+template <typename T> cudaError_t qr_blocked(const QrParams<T>& P, int nslices, cudaStream_t st);
+// Working matrices of at most this many rows rebuild their discarded columns
+// with the columns held in registers (and may take the second QR).
+constexpr int kQrWarpRows = 256;
+// The rebuild factors of the discarded columns d = ranks[s]..rc-1.  One QR
+// (P2 null): Rt_d = P W_d and L_d = Q1 [V_d; 0].  Two QRs (P2: the second
+// QR R1^T P2 = Q2 R2 whose R2^T the Jacobi factored; needs
+// mm <= kQrWarpRows): Rt_d = P (Q2 V_d) and L_d = Q1 [P2 W_d; 0].
 template <typename T>
-cudaError_t qr_finish(const QrParams<T>& P, const int* ranks, int nslices, cudaStream_t st);
+cudaError_t qr_finish(const QrParams<T>& P, const QrParams<T>* P2, const int* ranks, int nslices,
+                      cudaStream_t st);
 
 // ---- step 4: truncation ---------------------------------------------------
 // sigma: rc x p (descending per slice).  Tolerance rule when fixed_rank <= 0.

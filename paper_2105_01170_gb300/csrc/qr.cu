@@ -9,9 +9,16 @@
 // with the singular values the column norms of W.  qrcp_kernel factors every
 // slice (Householder reflectors, LAPACK-style storage: R on and above the
 // diagonal, the reflector tails below, tau separately) and writes R1^T as the
-// Jacobi input; qr_finish_kernel forms P W (a row scatter) and Q1 [V_d; 0]
-// for the columns d = rho_i..rc-1 that the truncation discards, which is all
-// the truncated rebuild  Xhat_i - (Q1 V_d)(P W_d)^T  needs.
+// Jacobi input; qr_finish forms P W_d (a row scatter) and Q1 [V_d; 0] for
+// the columns d = rho_i..rc-1 that the truncation discards, which is all the
+// truncated rebuild  Xhat_i - (Q1 V_d)(P W_d)^T  needs.
+//
+// A second QR, of R1^T (R1^T P2 = Q2 R2, the Jacobi then run on R2^T =
+// W V^T), brings the Jacobi input closer to diagonal again and saves further
+// sweeps (the second step of the same preconditioning): then
+//     B = (Q1 P2 W)(P Q2 V)^T,
+// and the rebuild takes L_d = Q1 [P2 W_d; 0] and Rt_d = P Q2 V_d.  The second
+// QR needs no pivoting (P2 = I): qr_blocked_kernel, by panels.
 //
 // One CTA per slice.  The active columns live in shared memory as far as it
 // holds them; pivoting swaps column pointers, never data.  Columns that do not
@@ -29,6 +36,7 @@ namespace {
 
 constexpr int QR_THREADS = 768;
 constexpr int QR_RPL = 8;   // rows per lane held in registers by the column update
+static_assert(32 * QR_RPL == kQrWarpRows, "register rebuild covers kQrWarpRows rows");
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
@@ -526,6 +534,347 @@ __global__ void __launch_bounds__(QR_THREADS) qr_finish_kernel(const QrParams<T>
   }
 }
 
+// ---- unpivoted blocked Householder QR of an n x n matrix (n <= 256) -------
+// The second QR of the two-step preconditioning needs no pivoting (its input
+// R1^T already carries the first QR's ordering), so it runs by panels of
+// QB_NB columns: warp 0 factors a panel with the panel's columns in
+// registers (lane l: rows l + 32 i) and leaves the reflectors in shared
+// memory; then every warp applies them to the trailing columns, QB_NC columns
+// at a time in registers.  Two block barriers per panel instead of several
+// per column.  Same output as qrcp_kernel: F = R on and above the diagonal
+// and the reflector tails below (ld n), tau, perm = identity, Jin = R^T.
+constexpr int QB_NB = 8;
+constexpr int QB_NC = 4;
+template <typename T> struct QbThreads { static constexpr int v = 512; };
+template <> struct QbThreads<double> { static constexpr int v = 256; };
+
+// entry `row` of a register column (lane row % 32, register row / 32),
+// broadcast to the warp
+template <typename T>
+__device__ __forceinline__ T reg_entry(const T (&x)[QR_RPL], int row) {
+  const int ir = row >> 5;
+  T a = T(0);
+#pragma unroll
+  for (int i = 0; i < QR_RPL; ++i)
+    if (i == ir) a = x[i];
+  return __shfl_sync(0xffffffffu, a, row & 31);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(QbThreads<T>::v) qr_blocked_kernel(const QrParams<T> P) {
+  __shared__ T Vs[QB_NB][kQrWarpRows];
+  __shared__ T ts[QB_NB];
+  __shared__ T rv[32];
+  __shared__ T sh_nsc;
+  const int s = blockIdx.x;
+  const int n = P.rc;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+  const T* src = P.src + (int64_t)s * P.src_bs;
+  T* F = P.F + (int64_t)s * P.F_bs;
+  T* tau = P.tau + (int64_t)s * n;
+  // F <- the input; power-of-two scale for the norms as in qrcp_kernel
+  T amax = T(0);
+  for (int e = tid; e < n * n; e += nth) {
+    const int r = e % n, c = e / n;
+    const T a = src[r + (int64_t)c * P.m];
+    F[e] = a;
+    amax = fmax(amax, fabs(a));
+  }
+  amax = block_max(amax, rv);
+  if (tid == 0) {
+    const int ex = (amax > T(0) && isfinite(amax)) ? min(max(ilogb(amax), -100), 100) : -1;
+    sh_nsc = ldexp(T(1), -ex - 1);
+  }
+  __syncthreads();
+  const T nsc = sh_nsc;
+  for (int j0 = 0; j0 < n; j0 += QB_NB) {
+    const int nb = min(QB_NB, n - j0);
+    const int i0 = j0 >> 5;   // register rows below i0 are above the panel: untouched
+    if (warp == 0) {
+      T x[QB_NB][QR_RPL];
+#pragma unroll
+      for (int c = 0; c < QB_NB; ++c)
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) {
+          const int r = lane + 32 * i;
+          x[c][i] = (c < nb && r < n) ? F[r + (int64_t)(j0 + c) * n] : T(0);
+        }
+#pragma unroll
+      for (int jj = 0; jj < QB_NB; ++jj) {
+        if (jj >= nb) break;
+        const int j = j0 + jj;
+        // reflector of column jj, rows j..n-1: beta = -sign(alpha) ||x[j:]||,
+        // tau = (beta - alpha) / beta, tail scale 1 / (alpha - beta)
+        T s2 = T(0);
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (i >= i0 && r > j && r < n) {
+            const T xs = x[jj][i] * nsc;
+            s2 = fma(xs, xs, s2);
+          }
+        }
+        s2 = warp_sum(s2);
+        const T alpha = reg_entry(x[jj], j);
+        const T alpha_s = alpha * nsc;
+        T tk = T(0), beta = alpha, scale = T(1);
+        if (s2 != T(0)) {
+          const T beta_s = -copysign(sqrt(fma(alpha_s, alpha_s, s2)), alpha_s);
+          tk = (beta_s - alpha_s) / beta_s;
+          beta = beta_s / nsc;
+          scale = nsc / (alpha_s - beta_s);
+        }
+        // column jj becomes [R(0..j, j); v tail]; v = e_j + tail
+        T v[QR_RPL];
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) {
+          const int r = lane + 32 * i;
+          T vi = T(0);
+          if (r == j) {
+            vi = T(1);
+            x[jj][i] = beta;
+          } else if (r > j && r < n) {
+            vi = x[jj][i] * scale;
+            x[jj][i] = vi;
+          }
+          v[i] = vi;
+          Vs[jj][r] = vi;
+        }
+        if (lane == 0) {
+          ts[jj] = tk;
+          tau[j] = tk;
+        }
+        // the panel's later columns
+        if (tk != T(0)) {
+#pragma unroll
+          for (int c = jj + 1; c < QB_NB; ++c) {
+            if (c >= nb) break;
+            T w = T(0);
+#pragma unroll
+            for (int i = 0; i < QR_RPL; ++i)
+              if (i >= i0) w = fma(v[i], x[c][i], w);
+            w = warp_sum(w);
+            const T tw = tk * w;
+#pragma unroll
+            for (int i = 0; i < QR_RPL; ++i)
+              if (i >= i0) x[c][i] = fma(-tw, v[i], x[c][i]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < QB_NB; ++c)
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (c < nb && i >= i0 && r < n) F[r + (int64_t)(j0 + c) * n] = x[c][i];
+        }
+    }
+    __syncthreads();
+    // trailing columns j0 + nb .. n-1: the panel's reflectors, first to last
+    for (int t0 = j0 + nb + warp * QB_NC; t0 < n; t0 += nw * QB_NC) {
+      const int nc = min(QB_NC, n - t0);
+      T x[QB_NC][QR_RPL];
+#pragma unroll
+      for (int c = 0; c < QB_NC; ++c)
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) {
+          const int r = lane + 32 * i;
+          x[c][i] = (c < nc && i >= i0 && r < n) ? F[r + (int64_t)(t0 + c) * n] : T(0);
+        }
+#pragma unroll
+      for (int jj = 0; jj < QB_NB; ++jj) {
+        if (jj >= nb) break;
+        const T tk = ts[jj];
+        if (tk == T(0)) continue;
+        T v[QR_RPL];
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) v[i] = (i >= i0) ? Vs[jj][lane + 32 * i] : T(0);
+        T w[QB_NC];
+#pragma unroll
+        for (int c = 0; c < QB_NC; ++c) {
+          T a = T(0);
+#pragma unroll
+          for (int i = 0; i < QR_RPL; ++i)
+            if (i >= i0) a = fma(v[i], x[c][i], a);
+          w[c] = a;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int c = 0; c < QB_NC; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+#pragma unroll
+        for (int c = 0; c < QB_NC; ++c) {
+          const T tw = tk * w[c];
+#pragma unroll
+          for (int i = 0; i < QR_RPL; ++i)
+            if (i >= i0) x[c][i] = fma(-tw, v[i], x[c][i]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < QB_NC; ++c)
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (c < nc && i >= i0 && r < n) F[r + (int64_t)(t0 + c) * n] = x[c][i];
+        }
+    }
+    __syncthreads();
+  }
+  // Jacobi input R^T (lower triangular) and the identity permutation
+  T* J = P.Jin + (int64_t)s * P.J_bs;
+  for (int e = tid; e < n * n; e += nth) {
+    const int r = e % n, c = e / n;
+    J[r + (int64_t)c * n] = (c <= r) ? F[c + (int64_t)r * n] : T(0);
+  }
+  for (int j = tid; j < n; j += nth) P.perm[(int64_t)s * n + j] = j;
+}
+
+// ---- rebuild with the columns held in registers (mm <= 32 QR_RPL) ---------
+// Each warp keeps NC columns in registers (lane l: rows l + 32 i) and applies
+// all rc reflectors to them, last to first, with no block barrier; the next
+// reflector's rows are loaded while the current one is applied.
+
+constexpr int QF_THREADS = 512;
+
+// x_c <- H_0 H_1 ... H_{rc-1} x_c for the NC register columns (length len;
+// reflector k: v = e_k + F[k+1..len, k], ld len, scalar tau[k]).
+template <typename T, int NC>
+__device__ __forceinline__ void apply_q_warp(T (&x)[NC][QR_RPL], const T* __restrict__ F,
+                                             const T* __restrict__ tau, int rc, int len, int lane) {
+  if (rc <= 0) return;
+  T vn[QR_RPL];
+  auto fetch = [&](int kk) {
+    const T* f = F + (int64_t)kk * len;
+#pragma unroll
+    for (int i = 0; i < QR_RPL; ++i) {
+      const int r = lane + 32 * i;
+      vn[i] = (r > kk && r < len) ? f[r] : (r == kk ? T(1) : T(0));
+    }
+  };
+  fetch(rc - 1);
+  T tn = tau[rc - 1];
+  for (int k = rc - 1; k >= 0; --k) {
+    T v[QR_RPL];
+#pragma unroll
+    for (int i = 0; i < QR_RPL; ++i) v[i] = vn[i];
+    const T tk = tn;
+    if (k > 0) {
+      fetch(k - 1);
+      tn = tau[k - 1];
+    }
+    if (tk == T(0)) continue;
+    T w[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T a = T(0);
+#pragma unroll
+      for (int i = 0; i < QR_RPL; ++i) a = fma(v[i], x[c][i], a);
+      w[c] = a;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T tw = tk * w[c];
+#pragma unroll
+      for (int i = 0; i < QR_RPL; ++i) x[c][i] = fma(-tw, v[i], x[c][i]);
+    }
+  }
+}
+
+// The discarded columns d = ranks[s]..rc-1 of the rebuild factors.
+//   One QR (TWO = false):  Rt_d = P1 W_d,  L_d = Q1 [V_d; 0].
+//   Two QRs (B P1 = Q1 R1, R1^T P2 = Q2 R2, the Jacobi on R2^T giving
+//   R2^T = W V^T, hence B = (Q1 P2 W)(P1 Q2 V)^T):
+//                          Rt_d = P1 (Q2 V_d),  L_d = Q1 [P2 W_d; 0].
+// P carries the first factorisation and the outputs, P2 the second.
+template <typename T, int NC, bool TWO>
+__global__ void __launch_bounds__(QF_THREADS)
+    qr_finish_warp_kernel(const QrParams<T> P, const QrParams<T> P2, const int* __restrict__ ranks) {
+  const int s = blockIdx.x;
+  const int mm = P.mm, rc = P.rc;
+  const int d0 = ranks ? min(max(ranks[s], 0), rc) : 0;
+  const int nd = rc - d0;
+  if (nd == 0) return;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+  const int* perm1 = P.perm + (int64_t)s * rc;
+  const T* W = P.W + (int64_t)s * P.W_bs + (int64_t)d0 * rc;   // rc x nd
+  const T* V = P.V + (int64_t)s * P.V_bs + (int64_t)d0 * rc;   // rc x nd
+  T* Rt = P.Rt + (int64_t)s * P.Rt_bs + (int64_t)d0 * rc;      // rc x nd
+  T* L = P.L + (int64_t)s * P.L_bs + (int64_t)d0 * mm;         // mm x nd
+  if (TWO) {
+    // L_d <- [P2 W_d; 0]: row j of W_d to row perm2[j]
+    const int* perm2 = P2.perm + (int64_t)s * rc;
+    for (int64_t e = tid; e < (int64_t)mm * nd; e += nth) {
+      const int r = (int)(e % mm), t = (int)(e / mm);
+      if (r < rc) {
+        const int pj = perm2[r];
+        if ((unsigned)pj < (unsigned)rc) L[pj + (int64_t)t * mm] = W[r + (int64_t)t * rc];
+      } else {
+        L[r + (int64_t)t * mm] = T(0);
+      }
+    }
+    __syncthreads();
+  } else {
+    // Rt_d <- P1 W_d
+    for (int64_t e = tid; e < (int64_t)rc * nd; e += nth) {
+      const int j = (int)(e % rc), t = (int)(e / rc);
+      const int pj = perm1[j];
+      if ((unsigned)pj < (unsigned)rc) Rt[pj + (int64_t)t * rc] = W[j + (int64_t)t * rc];
+    }
+  }
+  for (int t0 = warp * NC; t0 < nd; t0 += nw * NC) {
+    const int nc = min(NC, nd - t0);
+    T x[NC][QR_RPL];
+    if (TWO) {
+      // Rt_d <- P1 (Q2 V_d)
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) {
+          const int r = lane + 32 * i;
+          x[c][i] = (c < nc && r < rc) ? V[r + (int64_t)(t0 + c) * rc] : T(0);
+        }
+      apply_q_warp<T, NC>(x, P2.F + (int64_t)s * P2.F_bs, P2.tau + (int64_t)s * rc, rc, rc, lane);
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (c < nc && r < rc) {
+            const int pr = perm1[r];
+            if ((unsigned)pr < (unsigned)rc) Rt[pr + (int64_t)(t0 + c) * rc] = x[c][i];
+          }
+        }
+    }
+    // L_d <- Q1 [V_d; 0] (one QR) or Q1 L_d (two QRs, L_d staged above)
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int i = 0; i < QR_RPL; ++i) {
+        const int r = lane + 32 * i;
+        T val = T(0);
+        if (c < nc) {
+          if (TWO) val = r < mm ? L[r + (int64_t)(t0 + c) * mm] : T(0);
+          else val = r < rc ? V[r + (int64_t)(t0 + c) * rc] : T(0);
+        }
+        x[c][i] = val;
+      }
+    apply_q_warp<T, NC>(x, P.F + (int64_t)s * P.F_bs, P.tau + (int64_t)s * rc, rc, mm, lane);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int i = 0; i < QR_RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (c < nc && r < mm) L[r + (int64_t)(t0 + c) * mm] = x[c][i];
+      }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -558,8 +907,28 @@ cudaError_t qrcp(const QrParams<T>& P, int nslices, cudaStream_t st) {
 }
 
 template <typename T>
-cudaError_t qr_finish(const QrParams<T>& P, const int* ranks, int nslices, cudaStream_t st) {
+cudaError_t qr_blocked(const QrParams<T>& P, int nslices, cudaStream_t st) {
   if (nslices <= 0) return cudaSuccess;
+  if (P.rc > kQrWarpRows || P.mm != P.rc || P.rc < 1) return cudaErrorInvalidValue;
+  qr_blocked_kernel<T><<<nslices, QbThreads<T>::v, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t qr_finish(const QrParams<T>& P, const QrParams<T>* P2, const int* ranks, int nslices,
+                      cudaStream_t st) {
+  if (nslices <= 0) return cudaSuccess;
+  if (P.mm <= kQrWarpRows) {
+    constexpr int NC = sizeof(T) == 4 ? 4 : 2;
+    if (P2) {
+      if (P2->mm != P.rc || P2->rc != P.rc) return cudaErrorInvalidValue;
+      qr_finish_warp_kernel<T, NC, true><<<nslices, QF_THREADS, 0, st>>>(P, *P2, ranks);
+    } else {
+      qr_finish_warp_kernel<T, NC, false><<<nslices, QF_THREADS, 0, st>>>(P, P, ranks);
+    }
+    return cudaGetLastError();
+  }
+  if (P2) return cudaErrorInvalidValue;   // two QRs only with the register form
   cudaError_t e = cudaFuncSetAttribute(qr_finish_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)P.plan.smem_fin);
@@ -572,7 +941,11 @@ template QrPlan qr_plan<float>(int, int, int);
 template QrPlan qr_plan<double>(int, int, int);
 template cudaError_t qrcp<float>(const QrParams<float>&, int, cudaStream_t);
 template cudaError_t qrcp<double>(const QrParams<double>&, int, cudaStream_t);
-template cudaError_t qr_finish<float>(const QrParams<float>&, const int*, int, cudaStream_t);
-template cudaError_t qr_finish<double>(const QrParams<double>&, const int*, int, cudaStream_t);
+template cudaError_t qr_blocked<float>(const QrParams<float>&, int, cudaStream_t);
+template cudaError_t qr_blocked<double>(const QrParams<double>&, int, cudaStream_t);
+template cudaError_t qr_finish<float>(const QrParams<float>&, const QrParams<float>*, const int*,
+                                      int, cudaStream_t);
+template cudaError_t qr_finish<double>(const QrParams<double>&, const QrParams<double>*,
+                                       const int*, int, cudaStream_t);
 
 }  // namespace sma

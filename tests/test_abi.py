@@ -76,7 +76,7 @@ def test_rejects_bad_sizes_and_options(lib):
     assert _create([(3, 3, 2, 3, 5, bm)], decomp=S.SMA_TUCKER_SHARED_U)[0] == S.SMA_ERR_ARG
     assert _create([(3, 3, 2, 2, 5, bm)], mkind=S.SMA_M_USER)[0] == S.SMA_ERR_ARG
     assert _create([(3, 3, 2, 2, 5, bm)], prec=7)[0] == S.SMA_ERR_ARG
-    assert _create([(3, 3, 2, 2, 5, bm)], precondition=3)[0] == S.SMA_ERR_ARG
+    assert _create([(3, 3, 2, 2, 5, bm)], precondition=4)[0] == S.SMA_ERR_ARG
     assert _create([(3, 3, 2, 2, 5, bm)], precondition=-1)[0] == S.SMA_ERR_ARG
     assert _create([(3, 3, 2, 2, 5, bm)], autotune=2)[0] == S.SMA_ERR_ARG
     assert S.sma_create([], S.sma_options())[0] == S.SMA_ERR_ARG

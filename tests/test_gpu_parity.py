@@ -95,8 +95,8 @@ def test_transform_matches(prec, kind):
     assert rel(Xh, Xho) < (1e-14 if prec == S.SMA_FP64 else 2e-6)
 
 
-PRECONDS = [S.SMA_PRECOND_NONE, S.SMA_PRECOND_QRCP]
-QNAME = {S.SMA_PRECOND_NONE: "plain", S.SMA_PRECOND_QRCP: "qrcp"}
+PRECONDS = [S.SMA_PRECOND_NONE, S.SMA_PRECOND_QRCP, S.SMA_PRECOND_QRCP2]
+QNAME = {S.SMA_PRECOND_NONE: "plain", S.SMA_PRECOND_QRCP: "qrcp", S.SMA_PRECOND_QRCP2: "qrcp2"}
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
