@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_finish_kernel(const QrParams<T>
 // QB_NB columns: warp 0 factors a panel with the panel's columns in
 // registers (lane l: rows l + 32 i) and leaves the reflectors in shared
 // memory; then every warp applies them to the trailing columns, QB_NC columns
-// at a time in registers.  Two block barriers per panel instead of several
+// at a time in registers, their inner products reduced together.  Two block barriers per panel instead of several
 // per column.  Same output as qrcp_kernel: F = R on and above the diagonal
 // and the reflector tails below (ld n), tau, perm = identity, Jin = R^T.
 constexpr int QB_NB = 8;
@@ -558,6 +558,27 @@ __device__ __forceinline__ T reg_entry(const T (&x)[QR_RPL], int row) {
   for (int i = 0; i < QR_RPL; ++i)
     if (i == ir) a = x[i];
   return __shfl_sync(0xffffffffu, a, row & 31);
+}
+
+// Warp sums of 4 values at once (a reduce-scatter: lane l ends with the full
+// sum of value 2 b4 + b3 from bits b4 b3 of l; 10 shuffles in all instead of
+// 20), returned to every lane in w.
+template <typename T>
+__device__ __forceinline__ void warp_sum4(T (&w)[4], int lane) {
+  const bool h4 = lane & 16, h3 = lane & 8;
+  T u2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const T send = h4 ? w[i] : w[i + 2];
+    const T keep = h4 ? w[i + 2] : w[i];
+    u2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  T u = (h3 ? u2[1] : u2[0]) + __shfl_xor_sync(0xffffffffu, h3 ? u2[0] : u2[1], 8);
+  u += __shfl_xor_sync(0xffffffffu, u, 4);
+  u += __shfl_xor_sync(0xffffffffu, u, 2);
+  u += __shfl_xor_sync(0xffffffffu, u, 1);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) w[c] = __shfl_sync(0xffffffffu, u, 16 * (c >> 1) + 8 * (c & 1));
 }
 
 template <typename T>
@@ -699,10 +720,7 @@ __global__ void __launch_bounds__(QbThreads<T>::v) qr_blocked_kernel(const QrPar
             if (i >= i0) a = fma(v[i], x[c][i], a);
           w[c] = a;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int c = 0; c < QB_NC; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+        warp_sum4(w, lane);
 #pragma unroll
         for (int c = 0; c < QB_NC; ++c) {
           const T tw = tk * w[c];

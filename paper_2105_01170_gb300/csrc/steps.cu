@@ -299,17 +299,20 @@ __global__ void orth_kernel(const T* __restrict__ Gm, int rc, const int* __restr
   }
   T mxt = T(0);
   double mxd = 0.0;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    const int a = e % r, b = e / r;
-    if (sc && use_inv) {
-      const T ia = inv[a], ib = inv[b];
-      const T g = (ia > T(0) && ib > T(0)) ? G[a + (int64_t)b * rc] * ia * ib
-                                           : (a == b ? T(1) : T(0));
-      mxt = fmax(mxt, fabs(g - (a == b ? T(1) : T(0))));
-    } else {
-      double g = (double)G[a + (int64_t)b * rc];
-      if (sc) g = (sc[a] > 0 && sc[b] > 0) ? g / (sc[a] * sc[b]) : (a == b ? 1.0 : 0.0);
-      mxd = fmax(mxd, fabs(g - (a == b ? 1.0 : 0.0)));
+  // rows a along the lanes, columns b over the warps (coalesced, no division)
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int b = threadIdx.x >> 5; b < r; b += nwarp) {
+    for (int a = lane; a < r; a += 32) {
+      if (sc && use_inv) {
+        const T ia = inv[a], ib = inv[b];
+        const T g = (ia > T(0) && ib > T(0)) ? G[a + (int64_t)b * rc] * ia * ib
+                                             : (a == b ? T(1) : T(0));
+        mxt = fmax(mxt, fabs(g - (a == b ? T(1) : T(0))));
+      } else {
+        double g = (double)G[a + (int64_t)b * rc];
+        if (sc) g = (sc[a] > 0 && sc[b] > 0) ? g / (sc[a] * sc[b]) : (a == b ? 1.0 : 0.0);
+        mxd = fmax(mxd, fabs(g - (a == b ? 1.0 : 0.0)));
+      }
     }
   }
   double mx = fmax(mxd, (double)mxt);
@@ -632,7 +635,7 @@ cudaError_t orth_defect(const T* Gm, int rc, int p, const int* ranks, const doub
                         double* out, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
   const int use_inv = (scale && rc <= 6144) ? 1 : 0;   // reciprocals fit in 48 KB
-  orth_kernel<T><<<p, 256, use_inv ? (size_t)rc * sizeof(double) : 0, st>>>(Gm, rc, ranks, scale,
+  orth_kernel<T><<<p, 512, use_inv ? (size_t)rc * sizeof(double) : 0, st>>>(Gm, rc, ranks, scale,
                                                                              out, use_inv);
   return cudaGetLastError();
 }
