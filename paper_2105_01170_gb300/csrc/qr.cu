@@ -750,55 +750,67 @@ __global__ void __launch_bounds__(QbThreads<T>::v) qr_blocked_kernel(const QrPar
 
 // ---- rebuild with the columns held in registers (mm <= 32 QR_RPL) ---------
 // Each warp keeps NC columns in registers (lane l: rows l + 32 i) and applies
-// all rc reflectors to them, last to first, with no block barrier; the next
-// reflector's rows are loaded while the current one is applied.
+// all rc reflectors to them, last to first.  The reflectors are staged in
+// shared memory QF_CHUNK at a time by the whole CTA (one coalesced pass), so
+// each step reads its reflector at shared-memory latency.
 
 constexpr int QF_THREADS = 512;
+template <typename T> struct QfChunk { static constexpr int v = 128 / sizeof(T); };
 
-// x_c <- H_0 H_1 ... H_{rc-1} x_c for the NC register columns (length len;
-// reflector k: v = e_k + F[k+1..len, k], ld len, scalar tau[k]).
+// Warp sums of NC values (NC = 4: the reduce-scatter of warp_sum4).
 template <typename T, int NC>
-__device__ __forceinline__ void apply_q_warp(T (&x)[NC][QR_RPL], const T* __restrict__ F,
-                                             const T* __restrict__ tau, int rc, int len, int lane) {
-  if (rc <= 0) return;
-  T vn[QR_RPL];
-  auto fetch = [&](int kk) {
-    const T* f = F + (int64_t)kk * len;
-#pragma unroll
-    for (int i = 0; i < QR_RPL; ++i) {
-      const int r = lane + 32 * i;
-      vn[i] = (r > kk && r < len) ? f[r] : (r == kk ? T(1) : T(0));
-    }
-  };
-  fetch(rc - 1);
-  T tn = tau[rc - 1];
-  for (int k = rc - 1; k >= 0; --k) {
-    T v[QR_RPL];
-#pragma unroll
-    for (int i = 0; i < QR_RPL; ++i) v[i] = vn[i];
-    const T tk = tn;
-    if (k > 0) {
-      fetch(k - 1);
-      tn = tau[k - 1];
-    }
-    if (tk == T(0)) continue;
-    T w[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      T a = T(0);
-#pragma unroll
-      for (int i = 0; i < QR_RPL; ++i) a = fma(v[i], x[c][i], a);
-      w[c] = a;
-    }
+__device__ __forceinline__ void warp_sum_n(T (&w)[NC], int lane) {
+  if constexpr (NC == 4) {
+    warp_sum4(w, lane);
+  } else {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
       for (int c = 0; c < NC; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+  }
+}
+
+// x_c <- H_0 H_1 ... H_{rc-1} x_c for every warp's NC register columns
+// (reflector k: v = e_k + F[k+1..len, k], ld len, scalar tau[k]); `act`
+// says whether the warp holds columns.  Called by every thread of the CTA.
+template <typename T, int NC>
+__device__ __forceinline__ void apply_q_chunked(T (&x)[NC][QR_RPL], bool act,
+                                                const T* __restrict__ F,
+                                                const T* __restrict__ tau, int rc, int len,
+                                                T (*Fs)[kQrWarpRows], T* ts, int lane) {
+  constexpr int CH = QfChunk<T>::v;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int khi = rc - 1; khi >= 0; khi -= CH) {
+    const int klo = max(khi - CH + 1, 0), nk = khi - klo + 1;
+    __syncthreads();   // the previous chunk is consumed
+    for (int e = tid; e < nk * kQrWarpRows; e += nth) {
+      const int r = e % kQrWarpRows, kk = e / kQrWarpRows, k = klo + kk;
+      Fs[kk][r] = (r > k && r < len) ? F[r + (int64_t)k * len] : (r == k ? T(1) : T(0));
+    }
+    for (int kk = tid; kk < nk; kk += nth) ts[kk] = tau[klo + kk];
+    __syncthreads();
+    if (!act) continue;
+    for (int kk = nk - 1; kk >= 0; --kk) {
+      const T tk = ts[kk];
+      if (tk == T(0)) continue;
+      T v[QR_RPL];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const T tw = tk * w[c];
+      for (int i = 0; i < QR_RPL; ++i) v[i] = Fs[kk][lane + 32 * i];
+      T w[NC];
 #pragma unroll
-      for (int i = 0; i < QR_RPL; ++i) x[c][i] = fma(-tw, v[i], x[c][i]);
+      for (int c = 0; c < NC; ++c) {
+        T a = T(0);
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) a = fma(v[i], x[c][i], a);
+        w[c] = a;
+      }
+      warp_sum_n<T, NC>(w, lane);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const T tw = tk * w[c];
+#pragma unroll
+        for (int i = 0; i < QR_RPL; ++i) x[c][i] = fma(-tw, v[i], x[c][i]);
+      }
     }
   }
 }
@@ -810,13 +822,15 @@ __device__ __forceinline__ void apply_q_warp(T (&x)[NC][QR_RPL], const T* __rest
 //                          Rt_d = P1 (Q2 V_d),  L_d = Q1 [P2 W_d; 0].
 // P carries the first factorisation and the outputs, P2 the second.
 template <typename T, int NC, bool TWO>
-__global__ void __launch_bounds__(QF_THREADS)
+__global__ void __launch_bounds__(QF_THREADS, 1)
     qr_finish_warp_kernel(const QrParams<T> P, const QrParams<T> P2, const int* __restrict__ ranks) {
+  __shared__ T Fs[QfChunk<T>::v][kQrWarpRows];
+  __shared__ T ts[QfChunk<T>::v];
   const int s = blockIdx.x;
   const int mm = P.mm, rc = P.rc;
   const int d0 = ranks ? min(max(ranks[s], 0), rc) : 0;
   const int nd = rc - d0;
-  if (nd == 0) return;
+  if (nd == 0) return;   // (uniform over the CTA)
   const int tid = threadIdx.x, nth = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
   const int* perm1 = P.perm + (int64_t)s * rc;
@@ -836,7 +850,8 @@ __global__ void __launch_bounds__(QF_THREADS)
         L[r + (int64_t)t * mm] = T(0);
       }
     }
-    __syncthreads();
+    // (the barrier at the top of the first chunk orders these stores before
+    // the loads of L below)
   } else {
     // Rt_d <- P1 W_d
     for (int64_t e = tid; e < (int64_t)rc * nd; e += nth) {
@@ -845,11 +860,12 @@ __global__ void __launch_bounds__(QF_THREADS)
       if ((unsigned)pj < (unsigned)rc) Rt[pj + (int64_t)t * rc] = W[j + (int64_t)t * rc];
     }
   }
-  for (int t0 = warp * NC; t0 < nd; t0 += nw * NC) {
-    const int nc = min(NC, nd - t0);
-    T x[NC][QR_RPL];
-    if (TWO) {
-      // Rt_d <- P1 (Q2 V_d)
+  if (TWO) {
+    // Rt_d <- P1 (Q2 V_d)
+    for (int base = 0; base < nd; base += nw * NC) {
+      const int t0 = base + warp * NC;
+      const int nc = max(0, min(NC, nd - t0));
+      T x[NC][QR_RPL];
 #pragma unroll
       for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -857,7 +873,8 @@ __global__ void __launch_bounds__(QF_THREADS)
           const int r = lane + 32 * i;
           x[c][i] = (c < nc && r < rc) ? V[r + (int64_t)(t0 + c) * rc] : T(0);
         }
-      apply_q_warp<T, NC>(x, P2.F + (int64_t)s * P2.F_bs, P2.tau + (int64_t)s * rc, rc, rc, lane);
+      apply_q_chunked<T, NC>(x, nc > 0, P2.F + (int64_t)s * P2.F_bs, P2.tau + (int64_t)s * rc, rc,
+                             rc, Fs, ts, lane);
 #pragma unroll
       for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -869,7 +886,13 @@ __global__ void __launch_bounds__(QF_THREADS)
           }
         }
     }
-    // L_d <- Q1 [V_d; 0] (one QR) or Q1 L_d (two QRs, L_d staged above)
+  }
+  // L_d <- Q1 [V_d; 0] (one QR) or Q1 L_d (two QRs, L_d staged above)
+  for (int base = 0; base < nd; base += nw * NC) {
+    const int t0 = base + warp * NC;
+    const int nc = max(0, min(NC, nd - t0));
+    T x[NC][QR_RPL];
+    if (TWO) __syncthreads();   // the staging of L_d (first pass) or nothing
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -882,7 +905,8 @@ __global__ void __launch_bounds__(QF_THREADS)
         }
         x[c][i] = val;
       }
-    apply_q_warp<T, NC>(x, P.F + (int64_t)s * P.F_bs, P.tau + (int64_t)s * rc, rc, mm, lane);
+    apply_q_chunked<T, NC>(x, nc > 0, P.F + (int64_t)s * P.F_bs, P.tau + (int64_t)s * rc, rc, mm,
+                           Fs, ts, lane);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
