@@ -662,3 +662,73 @@ def test_two_level_planted_multilinear_rank_is_exact():
     assert h.err <= 1e-12 * np.linalg.norm(X)
     full = O.hosvd4(X, ranks=X.shape)
     assert full.err <= 1e-12 * np.linalg.norm(X)
+
+
+# ------------------------------------------------ truncation helpers, brute force
+
+def test_rank_for_tolerance_is_the_smallest_feasible_rank():
+    g = np.random.default_rng(21)
+    for trial in range(200):
+        n = int(g.integers(1, 9))
+        # integer singular values: every square and tail sum is exact
+        sig = g.integers(0, 5, size=n).astype(np.float64)
+        sq = sig ** 2
+        budget = float(g.integers(0, int(sq.sum()) + 2))
+        s = np.sort(sq)[::-1]
+        feasible = [r for r in range(n + 1) if s[r:].sum() <= budget]
+        assert O.rank_for_tolerance(g.permutation(sig), budget) == min(feasible)
+
+
+def test_representatives_are_first_in_column_major_order():
+    g = np.random.default_rng(22)
+    for trial in range(50):
+        ell, q = int(g.integers(1, 7)), int(g.integers(1, 7))
+        p = int(g.integers(1, ell * q + 1))
+        bm = np.concatenate([np.arange(p), g.integers(-1, p, size=ell * q - p)])
+        bm = g.permutation(bm).reshape(ell, q).astype(np.int32)
+        rep = O.representatives(bm, p)
+        flat = bm.T.ravel()            # column-major: index b * ell + a
+        for k in range(p):
+            first = int(np.flatnonzero(flat == k)[0])
+            assert rep[k] == (first % ell, first // ell)
+            assert bm[rep[k]] == k
+
+
+def test_truncation_margin_brackets_the_decision():
+    """Budgets inside (1 - margin, 1 + margin) times the budget keep the global
+    rule's ranks; just past either end the ranks change."""
+    g = np.random.default_rng(23)
+    checked = 0
+    for trial in range(100):
+        sig = [np.sort(g.random(int(g.integers(2, 6))))[::-1] for _ in range(3)]
+        normX2 = sum(float(np.sum(s ** 2)) for s in sig)
+        tol = float(g.uniform(0.05, 0.6))
+        ranks = O.truncate_global(sig, tol, normX2)
+        margin = O.truncation_margin(sig, ranks, tol, normX2)
+        assert margin >= 0
+        if not (1e-6 < margin < 0.5):
+            continue
+        checked += 1
+        for f in (1 - 0.9 * margin, 1 + 0.9 * margin):
+            assert np.array_equal(O.truncate_global(sig, tol * math.sqrt(f), normX2), ranks)
+        moved = [not np.array_equal(O.truncate_global(sig, tol * math.sqrt(f), normX2), ranks)
+                 for f in (1 - 1.1 * margin, 1 + 1.1 * margin)]
+        assert any(moved)
+    assert checked > 20
+
+
+def test_leading_left_singular_spans_the_top_eigenspace_of_the_gram():
+    g = np.random.default_rng(24)
+    Y = g.standard_normal((9, 30)) * np.geomspace(1, 1e-3, 9)[:, None]
+    ev, Q = np.linalg.eigh(Y @ Y.T)            # ascending
+    ev, Q = ev[::-1], Q[:, ::-1]
+    for r in (1, 3, 6):
+        U, s, rr = O.leading_left_singular(Y, r=r)
+        assert rr == r and U.shape == (9, r)
+        assert np.allclose(U.T @ U, np.eye(r), atol=1e-12)
+        assert np.linalg.norm(U @ U.T - Q[:, :r] @ Q[:, :r].T, 2) < 1e-8
+        assert np.allclose(s ** 2, ev, rtol=1e-10, atol=1e-14)
+    # budget form: the rank leaves a tail energy within the budget, one less would not
+    budget = float(np.sum(ev[4:])) * 1.0001
+    U, s, rr = O.leading_left_singular(Y, budget=budget)
+    assert rr == 4
