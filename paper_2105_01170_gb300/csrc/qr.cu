@@ -540,9 +540,10 @@ __global__ void __launch_bounds__(QR_THREADS) qr_finish_kernel(const QrParams<T>
 // QB_NB columns: warp 0 factors a panel with the panel's columns in
 // registers (lane l: rows l + 32 i) and leaves the reflectors in shared
 // memory; then every warp applies them to the trailing columns, QB_NC columns
-// at a time in registers, their inner products reduced together.  Two block barriers per panel instead of several
-// per column.  Same output as qrcp_kernel: F = R on and above the diagonal
-// and the reflector tails below (ld n), tau, perm = identity, Jin = R^T.
+// at a time in registers, their inner products reduced together.  Two block
+// barriers per panel instead of several per column.  Same output as
+// qrcp_kernel: F = R on and above the diagonal and the reflector tails below
+// (ld n), tau, perm = identity, Jin = R^T.
 constexpr int QB_NB = 8;
 constexpr int QB_NC = 4;
 template <typename T> struct QbThreads { static constexpr int v = 512; };
@@ -751,8 +752,8 @@ __global__ void __launch_bounds__(QbThreads<T>::v) qr_blocked_kernel(const QrPar
 // ---- rebuild with the columns held in registers (mm <= 32 QR_RPL) ---------
 // Each warp keeps NC columns in registers (lane l: rows l + 32 i) and applies
 // all rc reflectors to them, last to first.  The reflectors are staged in
-// shared memory QF_CHUNK at a time by the whole CTA (one coalesced pass), so
-// each step reads its reflector at shared-memory latency.
+// shared memory QfChunk (32 fp32, 16 fp64) at a time by the whole CTA (one
+// coalesced pass), so each step reads its reflector at shared-memory latency.
 
 constexpr int QF_THREADS = 512;
 template <typename T> struct QfChunk { static constexpr int v = 128 / sizeof(T); };
