@@ -216,6 +216,19 @@ typedef struct {
   double tensor_err;      /* ||X - T||_F = ||A - A_hat||_F (Lemma 1)             */
   double rel_err;         /* tensor_err / norm                                   */
   double orth_defect;     /* max |U^T U - I| over the orthonormal factors       */
+  /* Section 6.2: |tr A - tr A_hat| / |tr A|, from the slice traces of X and of
+   * the approximation on the device (tr A = sum_k tr(E_k) tr(X_k)); 0 when the
+   * block grid or the blocks are not square, for the three-level form, and
+   * for SMA_TUCKER_SPD, whose T_hat keeps the diagonal blocks exactly.      */
+  double trace_relerr;
+  /* Entries stored by the compressed form over the m n p entries of the
+   * distinct blocks (Section 6.2 quotes (r^2 T + N r) / (N^2 T) for the
+   * shared-U form): t-SVDM R (m + n + 1) with R = total_rank; block-index
+   * Tucker (p + m n) r; CP (m + n + p) r; shared U m r + r^2 p (the SPD form
+   * adds L, m (m + 1) / 2, over m n (p + 1) with its diagonal block); rows and
+   * columns m r1 + n r3 + r1 r3 p; two levels m r1 + n r2 + p1 k1 + p2 k2 +
+   * r1 r2 k1 k2; three levels sum_t p_t k_t + k1 k2 k3 over p1 p2 p3.        */
+  double storage_ratio;
 } sma_result;
 
 /* Validate the problems, derive eta_k and the weights 1/sqrt(eta_k), build M
@@ -327,12 +340,17 @@ sma_status sma_profile(sma_handle h, double* ms, int64_t* calls, int64_t* launch
  *   max_sweeps (0 = 30); stream: cudaStream_t (NULL = legacy default stream)
  * Limit: a slice that does not fit in shared memory needs
  * (max(m,n) + min(m,n)) * min(m,n) floats of scratch; a slice needing more
- * than the 8 MiB array is rejected with SMA_ERR_ARG (so is a NULL pointer or
- * a size <= 0).  Larger p is processed in stream-ordered chunks that reuse
- * the array.  SMA_ERR_CUDA if a CUDA call fails.
+ * than the 8 MiB array is rejected with SMA_ERR_ARG, as is a slice whose two
+ * stacked columns (2 (m + n) floats) do not fit in shared memory, a NULL
+ * pointer or a size <= 0; all of these are rejected on the host, before any
+ * launch.  Larger p is processed in stream-ordered chunks that reuse the
+ * array.  SMA_ERR_CUDA if a CUDA call fails.
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress and caches it; make that first call before any
- * stream capture.  Every call shares the one array and clears its status word
+ * cudaGetSymbolAddress and caches it with the device's current context; make
+ * that first call before any stream capture.  A call in a new context (after
+ * cudaDeviceReset) repeats the lookup, so that first call in the new context
+ * also belongs before any capture.  Every call shares the one array and
+ * clears its status word
  * on entry, so calls whose work overlaps on the GPU (several streams or host
  * threads) race on it and must be serialised by the caller.                */
 sma_status sma_slice_svd_noalloc(const float* X, int32_t m, int32_t n, int32_t p, float* W,

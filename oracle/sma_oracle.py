@@ -254,7 +254,12 @@ class TSVDM:
 
 
 def tsvdm(X: np.ndarray, M: np.ndarray, rel_tol: float | None = None,
-          fixed_rank: int | None = None) -> TSVDM:
+          fixed_rank: int | None = None, ranks=None) -> TSVDM:
+    """t-SVDM of X (reading R3).  The retained rank of each slice comes from
+    exactly one of: `ranks` (a given per-slice rank vector, each entry in
+    [0, min(m, n)]: the truncation of every slice at that rank), `fixed_rank`
+    (min(fixed_rank, m, n) per slice), or the global tolerance rule R4 at
+    `rel_tol`."""
     m, n, p = X.shape
     Xh = mode3(X, M)
     normX2 = float(np.sum(X * X))
@@ -264,7 +269,12 @@ def tsvdm(X: np.ndarray, M: np.ndarray, rel_tol: float | None = None,
         Us.append(u)
         Ss.append(s)
         Vs.append(vt.T)
-    if fixed_rank is not None and fixed_rank > 0:
+    if ranks is not None:
+        ranks = np.asarray(ranks, dtype=np.int64).ravel()
+        if ranks.shape != (p,) or np.any(ranks < 0) or np.any(ranks > min(m, n)):
+            raise ValueError("ranks must hold one rank in [0, min(m, n)] per slice")
+        ranks = ranks.copy()
+    elif fixed_rank is not None and fixed_rank > 0:
         ranks = np.array([min(fixed_rank, len(s)) for s in Ss], dtype=np.int64)
     else:
         ranks = truncate_global(Ss, float(rel_tol or 0.0), normX2)
@@ -315,6 +325,23 @@ def blr_dense(U: np.ndarray, F: list, W: np.ndarray, block_map: np.ndarray) -> n
     p = len(F)
     mid = struct_E(F, block_map, p)
     return np.kron(np.eye(ell), U) @ mid @ np.kron(np.eye(q), W.T)
+
+
+def apply_M_E(T: np.ndarray, block_map: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """y = M_E[T] x block by block, without forming M_E[T]: block (a, b) of
+    M_E[T] is T[:, :, k] / sqrt(eta_k) for k = block_map[a, b] (Section 3,
+    M_E = sum_k E_k (x) T_k), zero where block_map is -1.  x: (q*n, nrhs)."""
+    m, n, p = T.shape
+    ell, q = block_map.shape
+    eta = multiplicities(block_map, p)
+    y = np.zeros((ell * m, x.shape[1]))
+    for b in range(q):
+        xb = x[b * n:(b + 1) * n, :]
+        for a in range(ell):
+            k = int(block_map[a, b])
+            if k >= 0:
+                y[a * m:(a + 1) * m, :] += (T[:, :, k] / math.sqrt(eta[k])) @ xb
+    return y
 
 
 def kron_dense(terms) -> np.ndarray:

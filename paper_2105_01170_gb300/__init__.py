@@ -74,7 +74,8 @@ class sma_result(ctypes.Structure):
                 ("ranks", ctypes.c_int32 * 4), ("sweeps_max", ctypes.c_int32),
                 ("device_status", ctypes.c_int32), ("norm", ctypes.c_double),
                 ("tensor_err", ctypes.c_double), ("rel_err", ctypes.c_double),
-                ("orth_defect", ctypes.c_double)]
+                ("orth_defect", ctypes.c_double), ("trace_relerr", ctypes.c_double),
+                ("storage_ratio", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: (list(getattr(self, k)) if k == "ranks" else getattr(self, k))

@@ -125,6 +125,12 @@ struct Prob {
   double* partial = nullptr;
   int nparts = 0;
   double* stats = nullptr;                  // [0] ||X||^2, [1] discarded energy
+  // Section 6.2 trace error: tr(E_k) = d_k / sqrt(eta_k) per distinct block
+  // (d_k = diagonal positions holding k; empty when the grid or the blocks
+  // are not square), device buffer for the 2p slice traces, host M (t-SVDM)
+  std::vector<double> trw;
+  double* traces = nullptr;
+  std::vector<double> Mh;
   int* iscal = nullptr;                     // [0] total rank [1] terms [2..4] mode ranks
   int* status = nullptr;
   int* sweeps = nullptr;
@@ -654,6 +660,14 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   SMA_CK(cudaMemset(P.stats, 0, 8 * sizeof(double)));
   SMA_CK(cudaMemset(P.iscal, 0, 8 * sizeof(int)));
   SMA_CK(cudaMemset(P.status, 0, sizeof(int)));
+  if (P.ell == P.q && m == n && !P.spd) {
+    P.trw.assign(p, 0.0);
+    for (int a = 0; a < P.ell; ++a) {
+      const int k = P.map[(size_t)a + (size_t)a * P.ell];
+      if (k >= 0) P.trw[k] += isq[k];
+    }
+    SMA_TRY(mem.alloc(&P.traces, 2 * (size_t)p));
+  }
 
   if (o.decomp == SMA_TSVDM) {
     std::vector<double> M;
@@ -666,6 +680,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
       if (!o.M_user) return SMA_ERR_ARG;
       M.assign(o.M_user, o.M_user + (size_t)p * p);
     }
+    P.Mh = M;
     std::vector<T> Mt(M.begin(), M.end());
     SMA_TRY(mem.alloc(&P.Mt, (size_t)p * p));
     SMA_CK(cudaMemcpy(P.Mt, Mt.data(), Mt.size() * sizeof(T), cudaMemcpyHostToDevice));
@@ -682,6 +697,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
             (o.precondition == SMA_PRECOND_QRCP2 ||
              (o.precondition == SMA_PRECOND_AUTO && P.rc >= kQr2AutoMin));
     P.jp = P.qr ? jacobi_plan<T>(P.rc, P.rc, h->max_smem) : jacobi_plan<T>(m, n, h->max_smem);
+    if (P.jp.smem == 0) return SMA_ERR_UNSUPPORTED;   // a column too long for shared memory
     SMA_TRY(mem.alloc(&P.Xh, mnp));
     if (P.jp.block_mode)
       SMA_TRY(mem.alloc(&P.Wj, (size_t)(P.jp.mm + P.jp.rc) * P.jp.rc * p));
@@ -1292,6 +1308,10 @@ sma_status gram_solve(sma_ctx* h, Prob<T>& P, int slot, int count, int rows) {
   if (rows >= kCoopMinRows) cp = jacobi_coop_plan<double>(rows, h->max_smem);
   const bool coop = rows >= kCoopMinRows && cp.smem > 0 && h->coop_bar;
   if (coop) jp = cp;
+  if (jp.smem == 0) {   // a Gram order whose columns do not fit in shared memory
+    stage_end(h);
+    return SMA_ERR_UNSUPPORTED;
+  }
   JacobiParams<double> J;
   J.m = rows; J.n = rows;
   J.mm = jp.mm; J.rc = jp.rc; J.trans = 0; J.ldS = jp.ldS; J.bcols = jp.bcols; J.g = jp.g;
@@ -1848,6 +1868,76 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
   return SMA_OK;
 }
 
+// Entries the compressed form stores over the entries of the p distinct
+// blocks (m n p; Section 6.2 quotes this ratio for the shared-U form,
+// (r^2 T + N r) / (N^2 T) with N = m and the T distinct lags).
+template <typename T>
+double storage_ratio(const sma_ctx* h, const Prob<T>& P, const sma_result& r) {
+  const double m = P.m, n = P.n, p = P.p;
+  const sma_decomp d = h->opt.decomp;
+  double stored = 0.0, dense = m * n * p;
+  if (P.L == 3) {
+    const double p1 = P.lp[0], p2 = P.lp[1], p3 = P.lp[2];
+    stored = p1 * r.ranks[0] + p2 * r.ranks[1] + p3 * r.ranks[2] +
+             (double)r.ranks[0] * r.ranks[1] * r.ranks[2];
+    dense = p1 * p2 * p3;
+  } else if (P.ml2) {
+    stored = m * r.ranks[0] + n * r.ranks[1] + (double)P.lp[0] * r.ranks[2] +
+             (double)P.lp[1] * r.ranks[3] + (double)r.ranks[0] * r.ranks[1] * r.ranks[2] * r.ranks[3];
+  } else if (d == SMA_TSVDM) {
+    stored = (double)r.total_rank * (m + n + 1.0);           // U_i, V_i, sigma_i
+  } else if (d == SMA_TUCKER_BLOCKMODE) {
+    stored = (p + m * n) * r.ranks[0];                       // V and the core slices
+  } else if (d == SMA_CP_ALS) {
+    stored = (m + n + p) * r.ranks[0];                       // the three factors
+  } else {
+    // shared U (and the SPD form, which also keeps its Cholesky factor and
+    // the diagonal block it replaces) or U and W of the rows-and-columns form
+    const double r1 = r.ranks[0], r3 = r.ranks[1];
+    stored = m * r1 + (d == SMA_TUCKER_ROWCOL ? n * r3 : 0.0) + r1 * r3 * p;
+    if (P.spd) {
+      stored += m * (m + 1.0) / 2.0;
+      dense = m * n * (p + 1.0);
+    }
+  }
+  return dense > 0 ? stored / dense : 0.0;
+}
+
+// Section 6.2's trace error |tr A - tr A_hat| / |tr A| from the traces of
+// the slices of X and of the approximation (tr A = sum_k tr(E_k) tr(X_k)),
+// computed on the device.  0 when the matrix is not a square grid of square
+// blocks, for the three-level form, and for the SPD-preserving form (whose
+// T_hat keeps the diagonal blocks, and so the trace, exactly).
+template <typename T>
+sma_status trace_error(sma_ctx* h, Prob<T>& P, double* out) {
+  *out = 0.0;
+  if (!P.traces || P.L == 3 || P.trw.empty()) return SMA_OK;
+  const int m = P.m, n = P.n, p = P.p;
+  // the t-SVDM's approximation is T = D x3 M^T: tr T_k = sum_i M[i, k] tr D_i
+  const bool ts = h->opt.decomp == SMA_TSVDM;
+  const T* approx = ts ? P.D : P.Tt;
+  if (!approx) return SMA_OK;
+  SMA_K(slice_traces<T>(P.X, m, n, p, P.traces, h->st));
+  SMA_K(slice_traces<T>(approx, m, n, p, P.traces + p, h->st));
+  std::vector<double> tr(2 * (size_t)p);
+  SMA_CK(cudaMemcpyAsync(tr.data(), P.traces, tr.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                         h->st));
+  SMA_CK(cudaStreamSynchronize(h->st));
+  double trA = 0.0, trH = 0.0;
+  for (int k = 0; k < p; ++k) {
+    if (P.trw[k] == 0.0) continue;
+    double tk = tr[(size_t)p + k];
+    if (ts) {
+      tk = 0.0;
+      for (int i = 0; i < p; ++i) tk += P.Mh[(size_t)i + (size_t)k * p] * tr[(size_t)p + i];
+    }
+    trA += P.trw[k] * tr[k];
+    trH += P.trw[k] * tk;
+  }
+  *out = trA != 0.0 ? std::fabs(trA - trH) / std::fabs(trA) : 0.0;
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status read_result(sma_ctx* h, Prob<T>& P, sma_result* r) {
   SMA_CK(cudaStreamSynchronize(h->st));
@@ -1900,6 +1990,8 @@ sma_status read_result(sma_ctx* h, Prob<T>& P, sma_result* r) {
   }
   r->tensor_err = std::sqrt(std::fmax(err2, 0.0));
   r->rel_err = stats[0] > 0 ? r->tensor_err / r->norm : 0.0;
+  r->storage_ratio = storage_ratio(h, P, *r);
+  SMA_TRY(trace_error(h, P, &r->trace_relerr));
   return SMA_OK;
 }
 

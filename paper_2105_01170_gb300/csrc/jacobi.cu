@@ -1322,6 +1322,18 @@ JacobiPlan jacobi_plan_impl(int m, int n, int max_smem, bool allow_tile) {
   const size_t sort_bytes = (size_t)p2 * (sizeof(double) + sizeof(int)) + 16;
   const size_t col_bytes = (size_t)pl.ldS * sizeof(T);
   const size_t full = (size_t)pl.rc * col_bytes + sort_bytes;
+  // block mode needs two stacked columns and the sort buffer in shared
+  // memory at the least; a slice whose columns are longer than that has no
+  // plan (smem = 0: callers reject the shape before any launch)
+  if (2 * col_bytes + sort_bytes > (size_t)max_smem) {
+    pl.bcols = 0;
+    pl.threads = 0;
+    pl.g = 0;
+    pl.block_mode = 0;
+    pl.tile = 0;
+    pl.smem = 0;
+    return pl;
+  }
   if (full <= (size_t)max_smem) {
     pl.bcols = (pl.rc + 1) / 2 > 0 ? (pl.rc + 1) / 2 : 1;
     pl.smem = full;
@@ -1395,6 +1407,7 @@ std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem) {
   std::vector<JacobiPlan> out;
   const JacobiPlan base = jacobi_plan<T>(m, n, max_smem);
   out.push_back(base);
+  if (base.smem == 0) return out;   // no plan for this shape
   if (base.tile) {
     const JacobiPlan u = jacobi_plan_impl<T>(m, n, max_smem, false);
     if (u.block_mode == base.block_mode) out.push_back(u);
@@ -1453,6 +1466,7 @@ template <typename T>
 cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_t smem,
                        cudaStream_t st) {
   if (nslices <= 0) return cudaSuccess;
+  if (smem == 0 || threads <= 0) return cudaErrorInvalidValue;   // shape without a plan
   void (*kern)(const JacobiParams<T>) = jacobi_kernel<T, 1, 0>;
   if constexpr (sizeof(T) == 4) {
     if (P.ldS % 4 == 0 && P.mm % 4 == 0 && P.rc % 4 == 0) {

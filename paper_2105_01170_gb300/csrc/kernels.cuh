@@ -37,6 +37,10 @@ int gather_parts(int m, int n, int p);
 template <typename T>
 cudaError_t residual_norm2(const T* X, const T* Tt, int64_t count, double* partial, int nparts,
                            double* out, cudaStream_t st);
+// out[k] = trace of slice k (m x n, ld m) of an m x n x p tensor, fp64
+// (Section 6.2's trace error: tr A = sum_k tr(E_k) tr(X_k)).
+template <typename T>
+cudaError_t slice_traces(const T* src, int m, int n, int p, double* out, cudaStream_t st);
 
 // ---- step 3: Jacobi SVD ---------------------------------------------------
 // Per-slice pointers for batched launches over slices of several problems.

@@ -28,9 +28,30 @@ static __device__ __align__(256) unsigned char g_sma_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+void* g_scratch_ctx[kMaxDevices] = {nullptr};   // the context the address belongs to
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link-time
+// dependency on the driver library, so the library still loads on a host
+// without a GPU).
+using CtxGetCurrent = int (*)(void**);
+CtxGetCurrent ctx_get_current() {
+  static CtxGetCurrent fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    cudaGetLastError();
+    return reinterpret_cast<CtxGetCurrent>(f);
+  }();
+  return fn;
+}
 
 // Device address of g_sma_scratch on the current device, looked up once per
-// device (the host-side symbol is only a stand-in, never a device address).
+// device and context (the host-side symbol is only a stand-in, never a
+// device address).  The context is kept beside the address: after
+// cudaDeviceReset the device's primary context is a new one, the array is
+// mapped again at a new address, and the lookup is repeated.
 sma_status scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -38,15 +59,22 @@ sma_status scratch_address(void** out) {
     return SMA_ERR_CUDA;
   }
   if (dev < 0 || dev >= kMaxDevices) return SMA_ERR_UNSUPPORTED;
+  const CtxGetCurrent get = ctx_get_current();
+  if (!get) return SMA_ERR_CUDA;
+  void* ctx = nullptr;   // null while the runtime has not made a context current yet
+  if (get(&ctx) != 0) return SMA_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!ctx || !g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
+    // the lookup itself makes the device's primary context current
     const cudaError_t e = cudaGetSymbolAddress(&p, g_sma_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       return SMA_ERR_CUDA;
     }
+    if (get(&ctx) != 0 || !ctx) return SMA_ERR_CUDA;
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_addr[dev];
   return SMA_OK;
@@ -71,6 +99,7 @@ sma_status sma_slice_svd_noalloc(const float* X, int32_t m, int32_t n, int32_t p
     return SMA_ERR_CUDA;
   }
   const sma::JacobiPlan pl = sma::jacobi_plan<float>(m, n, max_smem);
+  if (pl.smem == 0) return SMA_ERR_ARG;   // one stacked column pair exceeds shared memory
   const int64_t per_slice = pl.block_mode ? (int64_t)(pl.mm + pl.rc) * pl.rc : 0;
   const int64_t capacity = (int64_t)((kScratchBytes - kStatusBytes) / sizeof(float));
   if (per_slice > capacity) return SMA_ERR_ARG;  // one slice's working copy exceeds 8 MiB

@@ -454,6 +454,33 @@ template cudaError_t residual_norm2<float>(const float*, const float*, int64_t, 
 template cudaError_t residual_norm2<double>(const double*, const double*, int64_t, double*, int,
                                             double*, cudaStream_t);
 
+// out[k] = trace of slice k of an m x n x p tensor (fp64 sum over the
+// min(m, n) diagonal entries), one warp per slice.
+template <typename T>
+__global__ void slice_traces_kernel(const T* __restrict__ src, int m, int n, int p,
+                                    double* __restrict__ out) {
+  const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= p) return;
+  const int d = m < n ? m : n;
+  const T* s = src + (int64_t)warp * m * n;
+  double acc = 0.0;
+  for (int j = lane; j < d; j += 32) acc += (double)s[j + (int64_t)j * m];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[warp] = acc;
+}
+
+template <typename T>
+cudaError_t slice_traces(const T* src, int m, int n, int p, double* out, cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int blocks = (int)(((int64_t)p * 32 + threads - 1) / threads);
+  slice_traces_kernel<T><<<blocks, threads, 0, st>>>(src, m, n, p, out);
+  return cudaGetLastError();
+}
+template cudaError_t slice_traces<float>(const float*, int, int, int, double*, cudaStream_t);
+template cudaError_t slice_traces<double>(const double*, int, int, int, double*, cudaStream_t);
+
 __global__ void sum_slabs_kernel(const double* __restrict__ part, int nslab, int64_t count,
                                  double* __restrict__ out) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;

@@ -1,0 +1,142 @@
+"""Block-low-rank forms of the space-time covariance at the benchmark's full
+size (16384^2, 127 distinct 256 x 256 lag blocks), at settings that compress:
+
+- the SPSD shared-U compression (Sections 5.1, 6.2) at relative tolerance
+  1e-2 (mode rank about 130 of 256);
+- the SPD-preserving form (Section 5.2) at fixed rank 64 (its whitened lag
+  blocks are not low rank: a tolerance below 0.1 keeps nearly all 256).
+
+Both precisions, against the FP64 oracle: the retained rank, the error
+report, the approximation tensor element by element, a sampled matvec, and
+the Section 6.2 trace error and storage ratio."""
+import numpy as np
+import pytest
+
+from oracle import sma_oracle as O
+from sma_inputs import generators as G
+
+from _util import gpu_tensor, rel, to_dev, tol_for
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+S = pytest.importorskip("paper_2105_01170_gb300")
+PRECS = [S.SMA_FP64, S.SMA_MIXED]
+PNAME = {S.SMA_FP64: "fp64", S.SMA_MIXED: "mixed"}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_01170_gb300 import _build
+    _build.build()
+
+
+@pytest.fixture(scope="module")
+def workload():
+    pr = G.spacetime_covariance()
+    return pr, pr.dense()
+
+
+def fill_T(h, pr, prec):
+    """sma_reconstruct fills the approximation tensor T; the dense output
+    itself is discarded."""
+    dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+    rows = pr.ell * pr.m
+    Ah = torch.empty(rows, rows, dtype=dt, device="cuda").t()
+    h.reconstruct(0, Ah)
+    torch.cuda.synchronize()
+    del Ah
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_shared_u_full_size_at_tolerance_1e2(prec, workload):
+    pr, Ad = workload
+    tol = 1e-2
+    A = Ad if prec == S.SMA_FP64 else Ad.astype(np.float32)
+    h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_SHARED_U, rel_tol=tol)
+    res = h.compress([to_dev(A)])[0]
+    assert res["device_status"] == 0
+    X = O.T_E(np.asarray(A, dtype=np.float64), pr.block_map, pr.p, pr.m, pr.n)
+    su = O.shared_u(X, rel_tol=tol)
+    assert 0 < su.rank < pr.m
+    r = int(h.ranks(0)[0])
+    assert r == su.rank, (r, su.rank)
+    assert res["ranks"][:2] == [r, r]
+    floor = tol_for(prec) * np.linalg.norm(X)
+    assert abs(res["tensor_err"] - su.err) <= 1e-6 * su.err + floor
+    fill_T(h, pr, prec)
+    T = gpu_tensor(h, S.EXPORT_T, (pr.m, pr.n, pr.p), prec)
+    To = su.tensor_approx()
+    e_T = rel(T, To)
+    print(f"shared-U full size {PNAME[prec]}: rank {r}, T rel err {e_T:.2e}")
+    assert e_T < tol_for(prec), e_T
+    del T
+    x = G.random_rhs(pr.q * pr.n, 2, 1).astype(np.float32 if prec == S.SMA_MIXED else np.float64)
+    dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+    Y = torch.empty(2, pr.ell * pr.m, dtype=dt, device="cuda").t()
+    h.apply(0, to_dev(x), Y)
+    yo = O.apply_M_E(To, pr.block_map, x.astype(np.float64))
+    assert rel(Y.cpu().numpy(), yo) < tol_for(prec)
+    # Section 6.2: the trace error of the lag-0 block's compression and the
+    # storage ratio of the shared-U form, with the p = 127 distinct lags
+    k0 = int(pr.block_map[0, 0])
+    tro = O.trace_relerr_shared_u(np.asarray(pr.blocks[k0] if prec == S.SMA_FP64 else
+                                             pr.blocks[k0].astype(np.float32), np.float64),
+                                  su.U[:, :r], pr.ell)
+    assert abs(res["trace_relerr"] - tro) <= 1e-6 * tro + 1e-7, (res["trace_relerr"], tro)
+    assert abs(res["storage_ratio"] - O.storage_ratio_blr(pr.m, pr.p, r)) <= 1e-15
+    h.close()
+
+
+def tol_x(prec, s):
+    """The bound of the SPD form's transformed tensor: the bar, or where the
+    fp32 congruence cannot reach it, 2 eps sqrt(m) c with c the cancellation
+    amplification of L^-1 T_k L^-T over the blocks."""
+    eps = 1.1e-16 if prec == S.SMA_FP64 else 6e-8
+    Li = np.abs(np.linalg.inv(s.L))
+    num = 0.0
+    for k in range(s.X.shape[2]):
+        Tw = np.abs(s.L @ s.X[:, :, k] @ s.L.T)
+        num += float(np.sum((Li @ Tw @ Li.T) ** 2))
+    c = np.sqrt(num) / np.linalg.norm(s.X)
+    return max(tol_for(prec), 2 * eps * np.sqrt(s.L.shape[0]) * c)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_spd_preserving_full_size_rank_64(prec, workload):
+    pr, Ad = workload
+    r = 64
+    dt = np.float64 if prec == S.SMA_FP64 else np.float32
+    B = np.asfortranarray(np.concatenate(list(pr.blocks), axis=1).astype(dt))
+    h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_SPD, layout=S.SMA_INPUT_BLOCKS,
+                 fixed_rank=r)
+    res = h.compress([to_dev(B)])[0]
+    assert res["device_status"] == 0
+    A = np.asarray(Ad.astype(dt), dtype=np.float64)
+    s = O.spd_preserving(A, pr.block_map, pr.p, pr.m, rank=r)
+    tx = tol_x(prec, s)
+    m = pr.m
+    assert list(h.ranks(0)) == [r, r]
+    assert rel(gpu_tensor(h, S.EXPORT_X, s.X.shape, prec), s.X) < tx
+    assert abs(res["tensor_err"] - s.su.err) <= 1e-6 * s.su.err + tx * np.linalg.norm(s.X)
+    fill_T(h, pr, prec)
+    T = gpu_tensor(h, S.EXPORT_T, s.X.shape, prec)
+    e_T = rel(T, s.su.tensor_approx())
+    print(f"SPD full size {PNAME[prec]}: T rel err {e_T:.2e} (bound {tx:.1e})")
+    assert e_T < tx, (e_T, tx)
+    del T
+    # T_hat x = (I (x) L)(x' + M_E[T] x'), x' = (I (x) L^T) x
+    nrhs = 2
+    x = G.random_rhs(pr.ell * m, nrhs, 11).astype(dt)
+    Y = torch.empty(nrhs, pr.ell * m, dtype=torch.float64 if prec == S.SMA_FP64 else torch.float32,
+                    device="cuda").t()
+    h.apply(0, to_dev(x), Y)
+    xs = x.astype(np.float64).reshape(m, pr.ell, nrhs, order="F")
+    xp = np.einsum("ji,jbs->ibs", s.L, xs).reshape(pr.ell * m, nrhs, order="F")
+    yp = xp + O.apply_M_E(s.su.tensor_approx(), s.inner_map, xp)
+    yo = np.einsum("ij,jbs->ibs", s.L, yp.reshape(m, pr.ell, nrhs, order="F"))
+    yo = yo.reshape(pr.ell * m, nrhs, order="F")
+    assert rel(Y.cpu().numpy(), yo) < tx
+    assert res["trace_relerr"] == 0.0
+    h.close()

@@ -59,7 +59,7 @@ def test_spd_with_one_remaining_block(prec):
     s = O.spd_preserving(A.astype(np.float64), pr.block_map, pr.p, m, rank=3)
     assert s.X.shape == (m, m, 1)
     Th = dense_of(h, ell * m, ell * m, prec)
-    assert rel(Th, s.dense()) < 10 * tol(prec)
+    assert rel(Th, s.dense()) < tol(prec)
     assert np.linalg.eigvalsh((Th + Th.T) / 2).min() > 0
     h.close()
 
@@ -97,7 +97,7 @@ def test_two_level_with_one_block_level_and_odd_blocks(prec):
     ho = O.hosvd4(X, ranks=(2, 2, 2, 1))
     assert tuple(res["ranks"]) == ho.ranks
     Ah = dense_of(h, 8 * 5, 8 * 3, prec)
-    assert rel(Ah, O.two_level_matrix(ho.tensor_approx(), map1, map2)) < 10 * tol(prec)
+    assert rel(Ah, O.two_level_matrix(ho.tensor_approx(), map1, map2)) < tol(prec)
     h.close()
 
 
@@ -116,3 +116,13 @@ def test_one_column_sketch(prec):
     V = gpu_tensor(h, S.EXPORT_FACTOR, (pr.p, pr.p), prec)[:, :1]
     assert np.linalg.norm(V @ V.T - t.V @ t.V.T, 2) < (1e-9 if prec == S.SMA_FP64 else 1e-5)
     h.close()
+
+
+def test_create_rejects_slice_without_jacobi_plan():
+    """A 30000 x 4 block: two of its stacked Jacobi columns do not fit in
+    shared memory, so sma_create reports SMA_ERR_UNSUPPORTED (host-side plan
+    check; no kernel runs)."""
+    pr = G.Problem("tall", np.zeros((1, 30000, 4)), G.block_diagonal_map(1))
+    with pytest.raises(S.SmaError) as e:
+        S.Handle([pr], prec=S.SMA_MIXED, rel_tol=1e-6)
+    assert e.value.status == S.SMA_ERR_UNSUPPORTED

@@ -9,7 +9,7 @@ import pytest
 from oracle import sma_oracle as O
 from sma_inputs import generators as G
 
-from _util import (TOL_MIXED, apply, gpu_tensor, input_matrix, np_dtype, oracle_tensor,
+from _util import (RANK_WINDOW_HITS, TOL_MIXED, apply, gpu_tensor, input_matrix, np_dtype, oracle_tensor,
                    reconstruct, rel, to_dev, tol_for)
 
 pytestmark = pytest.mark.gpu
@@ -91,8 +91,11 @@ def test_shared_u_128_points(prec, mode):
         e = su.sigma ** 2
         budget = tol * tol * float(np.sum(X * X)) / 2
         slack = min(budget - np.sum(e[su.rank:]), np.sum(e[su.rank - 1:]) - budget) / budget
-        if slack > 1e-6:
-            assert r == su.rank
+        if r != su.rank:
+            # only at an fp64 tie of the decision; then compare at the GPU's rank
+            assert slack <= 1e-6, (r, su.rank, slack)
+            RANK_WINDOW_HITS.append(f"shared-U 128 points: rank {r} vs oracle {su.rank}")
+            su = O.shared_u(X, rank=r)
     # both precisions form and solve the Gram in fp64 (from the same rounded
     # input), so the eigenvalues agree to fp64 accuracy
     ev = gpu_tensor(h, S.EXPORT_SIGMA, None, prec)[:pr.m]
@@ -102,9 +105,9 @@ def test_shared_u_128_points(prec, mode):
     assert projector_gap(U, su.U[:, :r]) < gap_tol
     Ah = reconstruct(h, pr, prec)
     Ao = O.M_E(su.tensor_approx(), pr.block_map)
-    assert rel(Ah, Ao) < 10 * tol_for(prec)
+    assert rel(Ah, Ao) < tol_for(prec)
     x = G.random_rhs(pr.q * pr.n, 3, 5).astype(np_dtype(prec)).astype(np.float64)
-    assert rel(apply(h, pr, x, prec), Ao @ x) < 10 * tol_for(prec)
+    assert rel(apply(h, pr, x, prec), Ao @ x) < tol_for(prec)
     floor = (1e-12 if prec == S.SMA_FP64 else TOL_MIXED) * np.linalg.norm(X)
     assert abs(res["tensor_err"] - su.err) <= 1e-6 * su.err + floor
     h.close()

@@ -10,7 +10,7 @@ import pytest
 from oracle import sma_oracle as O
 from sma_inputs import generators as G
 
-from _util import gpu_tensor, np_dtype, rel, to_dev, torch_dtype
+from _util import RANK_WINDOW_HITS, gpu_tensor, np_dtype, rel, to_dev, torch_dtype
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -105,11 +105,11 @@ def test_spd_fixed_rank_matches_oracle(prec, case, layout, host):
     assert rel(X, s.X) < tx
     assert list(h.ranks(0)) == [r, r]
     assert abs(res["norm"] - np.linalg.norm(s.X)) <= tx * np.linalg.norm(s.X)
-    assert abs(res["tensor_err"] - s.su.err) <= 10 * tx * np.linalg.norm(s.X)
+    assert abs(res["tensor_err"] - s.su.err) <= tx * np.linalg.norm(s.X)
     # T_hat, densely, and its positive definiteness
     Th = dense_that(h, pr, prec)
     To = s.dense()
-    assert rel(Th, To) < 10 * tx
+    assert rel(Th, To) < tx
     ev = np.linalg.eigvalsh((Th + Th.T) / 2)
     ev_o = np.linalg.eigvalsh(To)
     assert ev.min() > 0.5 * ev_o.min() > 0
@@ -118,10 +118,10 @@ def test_spd_fixed_rank_matches_oracle(prec, case, layout, host):
     Y = torch.empty(5, pr.ell * pr.m, dtype=torch_dtype(prec), device="cuda").t()
     h.apply(0, to_dev(x), Y)
     yo = To @ x.astype(np.float64)
-    assert rel(Y.cpu().numpy(), yo) < 10 * tx
+    assert rel(Y.cpu().numpy(), yo) < tx
     Yh = np.zeros((pr.ell * pr.m, 5), dtype=np_dtype(prec), order="F")
     h.apply(0, np.asfortranarray(x), Yh)
-    assert rel(Yh, yo) < 10 * tx
+    assert rel(Yh, yo) < tx
     h.close()
 
 
@@ -133,10 +133,20 @@ def test_spd_tolerance_rank_and_lemma_1(prec):
     s = O.spd_preserving(A, pr.block_map, pr.p, pr.m, rel_tol=tol)
     normX2 = float(np.sum(s.X ** 2))
     margin = shared_rank_margin(s.su.sigma, s.su.rank, tol, normX2)
-    if margin > 1e-3:
-        assert list(h.ranks(0)) == [s.su.rank, s.su.rank]
+    r_gpu = int(h.ranks(0)[0])
+    assert list(h.ranks(0)) == [r_gpu, r_gpu]
+    cmp = s
+    if r_gpu != s.su.rank:
+        # only where rounding of the mode-1 energies can move the decision;
+        # then compare with the oracle at the GPU's rank
+        assert prec == S.SMA_MIXED and margin <= 0.2, (r_gpu, s.su.rank, margin)
+        RANK_WINDOW_HITS.append(f"spd tol {tol:g}: rank {r_gpu} vs oracle {s.su.rank} "
+                                f"(margin {margin:.2e})")
+        cmp = O.spd_preserving(A, pr.block_map, pr.p, pr.m, rank=r_gpu)
     # the reported error is the inner tensor's, within the budget
     assert res["tensor_err"] <= tol * res["norm"] * (1 + 1e-6)
+    assert abs(res["tensor_err"] - cmp.su.err) <= tol_x(prec, s) * np.linalg.norm(s.X)
+    assert rel(dense_that(h, pr, prec), cmp.dense()) < tol_x(prec, s)
     # Lemma 1 on the inner matrix: recover A_hat = B^-1 T_hat B^-T - I with
     # the device's own L (B = I (x) L) and compare ||A - A_hat||_F with the
     # reported tensor error
@@ -147,7 +157,7 @@ def test_spd_tolerance_rank_and_lemma_1(prec):
     Ainner = O.M_E(s.X, s.inner_map)   # A = sum_k E_k (x) A_k
     err = np.linalg.norm(Ainner - inner)
     assert abs(err - res["tensor_err"]) <= 1e-3 * res["tensor_err"] + \
-        10 * tol_x(prec, s) * np.linalg.norm(Ainner)
+        tol_x(prec, s) * np.linalg.norm(Ainner)
     h.close()
 
 
@@ -191,8 +201,7 @@ def test_spd_fullsize_covariance_fp64():
     assert rel(X_gpu, s.X) < 1e-11
     normX2 = float(np.sum(s.X ** 2))
     margin = shared_rank_margin(s.su.sigma, s.su.rank, tol, normX2)
-    if margin > 1e-6:
-        assert list(h.ranks(0)) == [s.su.rank, s.su.rank]
+    assert list(h.ranks(0)) == [s.su.rank, s.su.rank], margin
     assert abs(res["tensor_err"] - s.su.err) <= 1e-6 * s.su.err + 1e-12 * np.sqrt(normX2)
     # T_hat x for 3 right-hand sides, the oracle side in factored form
     nrhs = 3

@@ -224,6 +224,57 @@ def test_tsvdm_identity_transform_diagonal_slices():
     assert np.allclose(T[:, :, 1], np.diag([4.0, 0.0, 0.0]), atol=1e-14)
 
 
+def test_tsvdm_given_rank_vector():
+    """The per-slice rank option: planted slices U diag(s) V^T under M = I
+    truncate to the closed form U_r diag(s_r) V_r^T with error
+    sqrt(sum of the dropped s^2); uniform ranks equal fixed_rank; the
+    tolerance rule's own ranks reproduce the tolerance result."""
+    g = np.random.default_rng(5)
+    m, n, p = 7, 5, 4
+    svals = [np.array([5.0, 3.0, 2.0, 0.5, 0.25]) * (i + 1) for i in range(p)]
+    X = np.zeros((m, n, p))
+    bases = []
+    for i in range(p):
+        U, _ = np.linalg.qr(g.standard_normal((m, n)))
+        V, _ = np.linalg.qr(g.standard_normal((n, n)))
+        X[:, :, i] = (U * svals[i]) @ V.T
+        bases.append((U, V))
+    r = [0, 2, 5, 1]
+    res = O.tsvdm(X, np.eye(p), ranks=r)
+    assert list(res.ranks) == r
+    T = res.tensor_approx()
+    for i in range(p):
+        U, V = bases[i]
+        want = (U[:, :r[i]] * svals[i][:r[i]]) @ V[:, :r[i]].T
+        assert np.allclose(T[:, :, i], want, atol=1e-13)
+    disc = sum(float(np.sum(svals[i][r[i]:] ** 2)) for i in range(p))
+    assert abs(res.err - math.sqrt(disc)) < 1e-13
+    # a uniform vector is fixed_rank; the tolerance rule's ranks reproduce it
+    M = O.dct2_matrix(p)
+    a = O.tsvdm(X, M, fixed_rank=3)
+    b = O.tsvdm(X, M, ranks=[3] * p)
+    assert np.array_equal(a.ranks, b.ranks) and rel(b.tensor_approx(), a.tensor_approx()) < 1e-15
+    t = O.tsvdm(X, M, rel_tol=0.05)
+    u = O.tsvdm(X, M, ranks=t.ranks)
+    assert np.array_equal(t.ranks, u.ranks) and rel(u.tensor_approx(), t.tensor_approx()) < 1e-15
+    assert u.err == t.err
+    with pytest.raises(ValueError):
+        O.tsvdm(X, M, ranks=[6, 0, 0, 0])
+
+
+def test_blockwise_M_E_matvec_equals_the_dense_map():
+    """apply_M_E (block by block, with the -1 zero blocks of a banded map)
+    against the dense M_E[T] times x, and M_E[T_E(A)] x = A x."""
+    for bm in (G.toeplitz_map(4), G.block_banded_map(5, 1), G.hankel_map(3)):
+        pr = random_problem(bm, 3, 2, seed=4)
+        A = pr.dense()
+        T = O.T_E(A, bm, pr.p, pr.m, pr.n)
+        x = np.random.default_rng(2).standard_normal((bm.shape[1] * 2, 3))
+        assert rel(O.apply_M_E(T, bm, x), A @ x) < 1e-14
+        T2 = np.random.default_rng(3).standard_normal(T.shape)
+        assert rel(O.apply_M_E(T2, bm, x), O.M_E(T2, bm) @ x) < 1e-14
+
+
 def test_tsvdm_full_rank_reproduces_A():
     pr = G.planted_kron_toeplitz(ell=5, m=4, terms=2, seed_index=0)
     A = pr.dense()

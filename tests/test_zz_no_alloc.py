@@ -87,5 +87,8 @@ def test_noalloc_rejects_oversized_slice_and_bad_args():
     ptr = buf.data_ptr()
     # a 1024 x 1024 slice needs (1024 + 1024) * 1024 floats > the 8 MiB scratch
     assert S.sma_slice_svd_noalloc(ptr, 1024, 1024, 1, ptr, ptr, d.data_ptr(), 0, 0) == S.SMA_ERR_ARG
+    # a 30000 x 4 slice fits the scratch ((30000 + 4) * 4 floats) but two of
+    # its stacked columns do not fit in shared memory: rejected on the host
+    assert S.sma_slice_svd_noalloc(ptr, 30000, 4, 1, ptr, ptr, d.data_ptr(), 0, 0) == S.SMA_ERR_ARG
     assert S.sma_slice_svd_noalloc(ptr, 0, 4, 1, ptr, ptr, d.data_ptr(), 0, 0) == S.SMA_ERR_ARG
     assert S.sma_slice_svd_noalloc(0, 4, 4, 1, ptr, ptr, d.data_ptr(), 0, 0) == S.SMA_ERR_ARG
