@@ -12,7 +12,10 @@ orthogonality) -> Kronecker-sum matvec on 256 right-hand sides.
 Prints ONE JSON line (rank 0).  `value` = steps per second (t-SVDM
 compressions/s, each including its 256-RHS matvec); the matvec GFLOP/s and
 the fp64 GPU form are reported beside it.  With --impl reference the FP64 CPU
-oracle is timed on a bounded sample of the same workload instead.
+oracle is timed on the same workload instead (one whole oracle step per timed
+step).  Beside the headline the line carries the other workloads of the
+benchmark configuration under "configs" (mixed and FP64 forms on the GPU,
+errors against the oracle, the oracle's own time).
 """
 from __future__ import annotations
 
@@ -266,29 +269,386 @@ def run_e2e(torch, S, pr, steps, warmup, device, stream):
     return float(np.mean(times)), h2d, d2h
 
 
-def cpu_oracle_sample(pr, nslices=16, nrhs=4):
-    """The FP64 oracle as it stands on a bounded sample of one step: the full
-    gather and transform, `nslices` of the p slice SVDs and the Kronecker-sum
-    matvec for `nrhs` of the NRHS right-hand sides; scaled to a full step."""
+# ----------------------------------------------------------------------------
+# the other workloads of the benchmark configuration: each compressed (and
+# applied) in the mixed and the FP64 form on the same GPU, its error against
+# the FP64 oracle, and the oracle's own time on the host (measured, on the
+# sample stated)
+# ----------------------------------------------------------------------------
+
+def _dev(torch, a, dtype):
+    """Column-major device copy of a host matrix (or a 1-D vector)."""
+    t = torch.from_numpy(np.ascontiguousarray(np.asarray(a).T)).to(device="cuda", dtype=dtype)
+    return t.t() if t.dim() == 2 else t
+
+
+def _timed(torch, stream, flush, fn, steps, warmup):
+    """Mean device ms of fn() over `steps` calls after `warmup` calls, CUDA
+    events on the handle's stream, L2 flushed before each call."""
+    ts = []
+    with torch.cuda.stream(stream):
+        for it in range(warmup + steps):
+            flush.fill_(float(it))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            stream.synchronize()
+            if it >= warmup:
+                ts.append(e0.elapsed_time(e1))
+    return float(np.mean(ts))
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def _export_T(torch, S, h, pr, prec):
+    """The approximation tensor T of problem 0 (filled by sma_reconstruct)."""
+    dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+    Ah = torch.empty(pr.q * pr.n, pr.ell * pr.m, dtype=dt, device="cuda").t()
+    h.reconstruct(0, Ah)
+    del Ah
+    n = h.export_size(0, S.EXPORT_T)
+    buf = torch.empty(n, dtype=dt, device="cuda")
+    h.export(0, S.EXPORT_T, buf)
+    return buf.cpu().numpy().astype(np.float64).reshape((pr.m, pr.n, pr.p), order="F")
+
+
+def _forms(torch, S, make, prec_list=None):
+    """Run make(prec) for both precisions; returns {name: result dict}."""
+    out = {}
+    for prec in (prec_list or (S.SMA_MIXED, S.SMA_FP64)):
+        out["mixed" if prec == S.SMA_MIXED else "fp64"] = make(prec)
+    return out
+
+
+def cfg_planted(torch, S, stream, flush, steps, alu_peak):
+    """Planted Kronecker sum (block Toeplitz 128^2, 15 distinct 16 x 16
+    blocks, 1e-8 noise): t-SVDM at tolerance 1e-6 and its 256-RHS matvec, and
+    the block-index Tucker-1 that must find Kronecker rank 3."""
+    from oracle import sma_oracle as O
+    from sma_inputs import generators as G
+    pr = G.planted_kron_toeplitz()
+    x = G.random_rhs(pr.q * pr.n, NRHS, 1)
+
+    def make(prec):
+        dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+        A = pr.dense() if prec == S.SMA_FP64 else pr.dense().astype(np.float32)
+        dA, dX = _dev(torch, A, dt), _dev(torch, x, dt)
+        dY = torch.empty(NRHS, pr.ell * pr.m, dtype=dt, device="cuda").t()
+        h = S.Handle([pr], prec=prec, rel_tol=1e-6, stream=stream.cuda_stream)
+        ms_c = _timed(torch, stream, flush, lambda: h.compress([dA], want_result=False), steps, 3)
+        ms_a = _timed(torch, stream, flush, lambda: h.apply(0, dX, dY), steps, 3)
+        res = h.result(0)
+        X = O.T_E(np.asarray(A, np.float64), pr.block_map, pr.p, pr.m, pr.n)
+        ora = O.tsvdm(X, O.dct2_matrix(pr.p), rel_tol=1e-6)
+        T = _export_T(torch, S, h, pr, prec)
+        yo = O.apply_kron(O.tsvdm_kron_terms(ora, pr.block_map), x.astype(np.asarray(A).dtype)
+                          .astype(np.float64))
+        out = {"compress_ms": ms_c, "apply_ms": ms_a, "total_rank": res["total_rank"],
+               "rel_err": res["rel_err"],
+               "ranks_equal_oracle": bool(np.array_equal(h.ranks(0), ora.ranks)),
+               "T_rel_err_vs_oracle": _rel(T, ora.tensor_approx()),
+               "apply_rel_err_vs_oracle": _rel(dY.cpu().numpy(), yo)}
+        h.close()
+        hk = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_BLOCKMODE, rel_tol=1e-6,
+                      stream=stream.cuda_stream)
+        out["tucker1_ms"] = _timed(torch, stream, flush,
+                                   lambda: hk.compress([dA], want_result=False), steps, 3)
+        out["kron_rank"] = hk.result(0)["ranks"][0]
+        out["kron_rank_oracle"] = O.tucker1_blockmode(X, rel_tol=1e-6).rank
+        hk.close()
+        return out
+
+    forms = _forms(torch, S, make)
+    t0 = time.perf_counter()
+    Xo = O.T_E(pr.dense(), pr.block_map, pr.p, pr.m, pr.n)
+    ora = O.tsvdm(Xo, O.dct2_matrix(pr.p), rel_tol=1e-6)
+    O.apply_kron(O.tsvdm_kron_terms(ora, pr.block_map), x)
+    t_or = time.perf_counter() - t0
+    return {"workload": "planted Kronecker sum, block Toeplitz 8 x 8 of 16 x 16 (p = 15), "
+                        "t-SVDM tol 1e-6 + 256-RHS matvec; Tucker-1 Kronecker rank",
+            "forms": forms, "oracle_ms": t_or * 1e3,
+            "oracle_sample": "the whole compression and 256-RHS matvec (FP64 numpy)",
+            "roofline": {"bound": "latency", "note": "a 30 KB tensor: a handful of small "
+                         "launches, far below any throughput roof"}}
+
+
+def cfg_spacetime_blr(torch, S, stream, flush, steps, pk):
+    """The space-time covariance (16384^2, 127 lag blocks of 256 x 256) in its
+    block-low-rank forms: the SPSD shared-U compression at tolerance 1e-2 and
+    the SPD-preserving form at rank 64, each with a 256-RHS matvec."""
+    from oracle import sma_oracle as O
+    from sma_inputs import generators as G
+    pr = G.spacetime_covariance()
+    x = G.random_rhs(pr.q * pr.n, NRHS, 1)
+    out = {}
+
+    def shared(prec):
+        dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+        A = pr.dense() if prec == S.SMA_FP64 else pr.dense().astype(np.float32)
+        dA, dX = _dev(torch, A, dt), _dev(torch, x, dt)
+        dY = torch.empty(NRHS, pr.ell * pr.m, dtype=dt, device="cuda").t()
+        h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_SHARED_U, rel_tol=1e-2,
+                     stream=stream.cuda_stream, profile=True)
+        ms_c = _timed(torch, stream, flush, lambda: h.compress([dA], want_result=False),
+                      max(2, steps // 2), 2)
+        ms_a = _timed(torch, stream, flush, lambda: h.apply(0, dX, dY), steps, 3)
+        h.profile(reset=True)
+        with torch.cuda.stream(stream):
+            h.compress([dA], want_result=False)
+        prof = h.profile(reset=True)
+        res = h.result(0)
+        X = O.T_E(np.asarray(A, np.float64), pr.block_map, pr.p, pr.m, pr.n)
+        su = O.shared_u(X, rel_tol=1e-2)
+        T = _export_T(torch, S, h, pr, prec)
+        r = res["ranks"][0]
+        o = {"compress_ms": ms_c, "apply_ms": ms_a, "rank": r, "rank_oracle": su.rank,
+             "ranks_equal_oracle": r == su.rank, "rel_err": res["rel_err"],
+             "T_rel_err_vs_oracle": _rel(T, su.tensor_approx()),
+             "trace_relerr": res["trace_relerr"], "storage_ratio": res["storage_ratio"],
+             "compress_stage_ms": {k: v for k, v in prof["ms"].items() if v > 0}}
+        del dA
+        h.close()
+        return o
+
+    def spd(prec):
+        dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+        B = np.concatenate(list(pr.blocks), axis=1)
+        B = B if prec == S.SMA_FP64 else B.astype(np.float32)
+        dB, dX = _dev(torch, B, dt), _dev(torch, x, dt)
+        dY = torch.empty(NRHS, pr.ell * pr.m, dtype=dt, device="cuda").t()
+        h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_SPD, layout=S.SMA_INPUT_BLOCKS,
+                     fixed_rank=64, stream=stream.cuda_stream)
+        ms_c = _timed(torch, stream, flush, lambda: h.compress([dB], want_result=False),
+                      max(2, steps // 2), 2)
+        ms_a = _timed(torch, stream, flush, lambda: h.apply(0, dX, dY), steps, 3)
+        res = h.result(0)
+        A = pr.dense() if prec == S.SMA_FP64 else pr.dense().astype(np.float32)
+        s = O.spd_preserving(np.asarray(A, np.float64), pr.block_map, pr.p, pr.m, rank=64)
+        T = _export_T(torch, S, h, G.Problem("inner", s.X.transpose(2, 0, 1), s.inner_map), prec)
+        o = {"compress_ms": ms_c, "apply_ms": ms_a, "rank": res["ranks"][0],
+             "rel_err": res["rel_err"], "T_rel_err_vs_oracle": _rel(T, s.su.tensor_approx()),
+             "storage_ratio": res["storage_ratio"]}
+        h.close()
+        return o
+
+    out["shared_u_tol_1e-2"] = _forms(torch, S, shared)
+    out["spd_rank_64"] = _forms(torch, S, spd)
+    sh = out["shared_u_tol_1e-2"]
+    out["mixed_vs_fp64_compress_speedup"] = sh["fp64"]["compress_ms"] / sh["mixed"]["compress_ms"]
+    t0 = time.perf_counter()
+    Xo = O.T_E(pr.dense(), pr.block_map, pr.p, pr.m, pr.n)
+    O.shared_u(Xo, rel_tol=1e-2)
+    out["oracle_ms"] = (time.perf_counter() - t0) * 1e3
+    out["oracle_sample"] = "the shared-U compression (gather, mode-1 SVD, core) in FP64 numpy"
+    out["workload"] = ("space-time covariance 16384^2 (127 lag blocks of 256 x 256): SPSD "
+                       "shared-U at tol 1e-2 and SPD-preserving at rank 64, 256-RHS matvecs")
+    return out
+
+
+def cfg_hankel(torch, S, stream, flush, steps, alu_peak):
+    """LTI block Hankel 2048^2 (64 x 64 blocks of 32 x 32, p = 127): rows-
+    and-columns Tucker block low rank at r = 5, 10, 20 and the 256-RHS
+    matvec."""
+    from oracle import sma_oracle as O
+    from sma_inputs import generators as G
+    pr = G.lti_hankel()
+    N = pr.ell * pr.m
+    x = G.random_rhs(N, NRHS, 3)
+    out = {}
+    for r in (5, 10, 20):
+        def make(prec, r=r):
+            dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+            A = pr.dense() if prec == S.SMA_FP64 else pr.dense().astype(np.float32)
+            dA, dX = _dev(torch, A, dt), _dev(torch, x.astype(np.asarray(A).dtype), dt)
+            dY = torch.empty(NRHS, N, dtype=dt, device="cuda").t()
+            h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_ROWCOL, fixed_rank=r,
+                         stream=stream.cuda_stream)
+            ms_c = _timed(torch, stream, flush, lambda: h.compress([dA], want_result=False),
+                          steps, 3)
+            ms_a = _timed(torch, stream, flush, lambda: h.apply(0, dX, dY), steps, 3)
+            X = O.T_E(np.asarray(A, np.float64), pr.block_map, pr.p, pr.m, pr.n)
+            t = O.tucker2_rows_cols(X, r, r)
+            yo = O.apply_M_E(t.tensor_approx(), pr.block_map,
+                             x.astype(np.asarray(A).dtype).astype(np.float64))
+            flops = 2 * 2 * (64 * 32 * r * NRHS) + 2 * 64 * 64 * r * r * NRHS
+            o = {"compress_ms": ms_c, "apply_ms": ms_a,
+                 "apply_rel_err_vs_oracle": _rel(dY.cpu().numpy(), yo),
+                 "apply_gflops": flops / (ms_a * 1e-3) / 1e9,
+                 "apply_alu_frac": flops / (ms_a * 1e-3) / 1e12 / alu_peak}
+            h.close()
+            return o
+        out[f"r{r}"] = _forms(torch, S, make)
+    t0 = time.perf_counter()
+    A = pr.dense()
+    X = O.T_E(A, pr.block_map, pr.p, pr.m, pr.n)
+    t = O.tucker2_rows_cols(X, 10, 10)
+    O.apply_M_E(t.tensor_approx(), pr.block_map, x)
+    out["oracle_ms"] = (time.perf_counter() - t0) * 1e3
+    out["oracle_sample"] = "r = 10: gather, both mode SVDs, core and the 256-RHS matvec (FP64 numpy)"
+    out["workload"] = ("LTI block Hankel 2048^2 (64 x 64 blocks of 32 x 32), rows-and-columns "
+                       "Tucker BLR at r = 5/10/20, 256-RHS matvec")
+    out["roofline"] = {"bound": "alu", "kernel": "the BLR matvec's products (CUDA cores)",
+                       "note": "apply_alu_frac per rank against the derived FP32 peak; the "
+                               "compression is two small Gram eigen-solves (latency-bound)"}
+    return out
+
+
+def cfg_psf(torch, S, stream, flush, steps, pk):
+    """3-D Gaussian blur of a 64^3 volume (15^3 PSF, sigma 2/3/4, rotated 30
+    degrees, zero boundary): the three-level HOSVD at tolerance 1e-4 and the
+    matvec on 64 volumes."""
+    from oracle import sma_oracle as O
+    from sma_inputs import generators as G
+    K, half, tol = 64, 7, 1e-4
+    s_ = 2 * half + 1
+    P = G.gaussian_psf3(support=s_, sig=(2.0, 3.0, 4.0))
+    bm = O.banded_toeplitz_map(K, half)
+    a64 = np.transpose(P, (2, 1, 0)).ravel(order="F")
+    vols = G.random_volumes(64, K)
+    x = np.stack([v.ravel(order="F") for v in vols], axis=1)
+
+    def make(prec):
+        dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+        a = a64 if prec == S.SMA_FP64 else a64.astype(np.float32)
+        xin = x if prec == S.SMA_FP64 else x.astype(np.float32)
+        da, dX = _dev(torch, a, dt), _dev(torch, xin, dt)
+        dY = torch.empty(64, K ** 3, dtype=dt, device="cuda").t()
+        mp = S.MultilevelProblem([bm, bm, bm], [s_, s_, s_])
+        h = S.Handle([mp], prec=prec, decomp=S.SMA_HOSVD_MULTILEVEL, layout=S.SMA_INPUT_BLOCKS,
+                     rel_tol=tol, stream=stream.cuda_stream)
+        ms_c = _timed(torch, stream, flush, lambda: h.compress([da], want_result=False), steps, 3)
+        ms_a = _timed(torch, stream, flush, lambda: h.apply(0, dX, dY), steps, 3)
+        res = h.result(0)
+        Pin = np.transpose(np.asarray(a, np.float64).reshape((s_, s_, s_), order="F"), (2, 1, 0))
+        ho = O.hosvd3(O.psf_tensor(Pin, K), rel_tol=tol)
+        Gc, C1, C2, C3 = O.multilevel_kron_terms(ho, K, half)
+        yo = O.multilevel_apply(Gc, C1, C2, C3, np.asarray(vols[:1], np.float64)
+                                .astype(np.float32 if prec == S.SMA_MIXED else np.float64)
+                                .astype(np.float64))[0].ravel(order="F")
+        y0 = dY[:, 0].cpu().numpy()
+        hbm = 2 * 64 * K ** 3 * (8 if prec == S.SMA_FP64 else 4)
+        o = {"compress_ms": ms_c, "apply_ms": ms_a, "ranks": res["ranks"][:3],
+             "ranks_oracle": list(ho.ranks), "ranks_equal_oracle": list(res["ranks"][:3]) ==
+             list(ho.ranks), "rel_err": res["rel_err"],
+             "apply_rel_err_vs_oracle_1_volume": _rel(y0, yo),
+             "apply_hbm_gbs": hbm / (ms_a * 1e-3) / 1e9,
+             "apply_hbm_frac": hbm / (ms_a * 1e-3) / 1e9 / pk["hbm_gbs"]}
+        h.close()
+        return o
+
+    out = _forms(torch, S, make)
+    t0 = time.perf_counter()
+    ho = O.hosvd3(O.psf_tensor(P, K), rel_tol=tol)
+    Gc, C1, C2, C3 = O.multilevel_kron_terms(ho, K, half)
+    t1 = time.perf_counter()
+    O.multilevel_apply(Gc, C1, C2, C3, vols[:1])
+    t2 = time.perf_counter()
+    return {"workload": "3-D blur 64^3 (15^3 PSF, sigma 2/3/4, rotated 30 degrees), three-level "
+                        "HOSVD tol 1e-4, 64-volume matvec",
+            "forms": out, "oracle_ms": ((t1 - t0) + (t2 - t1) * 64) * 1e3,
+            "oracle_sample": f"HOSVD {1e3 * (t1 - t0):.1f} ms + the matvec on 1 of the 64 "
+                             f"volumes ({1e3 * (t2 - t1):.1f} ms) x 64",
+            "roofline": {"bound": "hbm", "kernel": "the three-level matvec",
+                         "note": "apply_hbm_frac: 2 x 64 volumes read and written once against "
+                                 "the measured HBM copy bandwidth"}}
+
+
+def cfg_batch_fp64(torch, S, stream, flush, steps):
+    """The 512-matrix batch in the FP64 form, and the oracle on a sample of
+    its problems (ranks and error against the mixed and FP64 GPU forms)."""
+    from oracle import sma_oracle as O
+    from sma_inputs import generators as G
+    prs = G.block_tridiag_batch()
+    out = {}
+    for prec in (S.SMA_FP64, S.SMA_MIXED):
+        dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+        blocks = [_dev(torch, np.concatenate(list(pr.blocks), axis=1)
+                       .astype(np.float64 if prec == S.SMA_FP64 else np.float32), dt) for pr in prs]
+        h = S.Handle(prs, prec=prec, rel_tol=1e-3, layout=S.SMA_INPUT_BLOCKS,
+                     stream=stream.cuda_stream, autotune=True)
+        ms = _timed(torch, stream, flush, lambda: h.compress(blocks, want_result=False),
+                    max(1, steps // 4), 1)
+        sample = [0, 17, 300]
+        cmp = []
+        for i in sample:
+            pr = prs[i]
+            B = blocks[i].cpu().numpy().astype(np.float64).reshape(pr.m, pr.n, pr.p, order="F")
+            X = B * np.sqrt(O.multiplicities(pr.block_map, pr.p))[None, None, :]
+            ora = O.tsvdm(X, O.dct2_matrix(pr.p), rel_tol=1e-3)
+            r = h.result(i)
+            cmp.append({"problem": i, "ranks_equal_oracle": bool(np.array_equal(h.ranks(i), ora.ranks)),
+                        "err_rel_diff": abs(r["tensor_err"] - ora.err) / max(ora.err, 1e-300)})
+        out["fp64" if prec == S.SMA_FP64 else "mixed"] = {"ms_per_compression": ms,
+                                                          "sampled_vs_oracle": cmp}
+        h.close()
+        del blocks
+        torch.cuda.empty_cache()
+    return out
+
+
+def oracle_step(pr, nslices=None, nrhs=None):
+    """One step of the FP64 oracle as it stands: gather, transform, the slice
+    SVDs, the global truncation, the Kronecker-sum terms and the matvec on
+    the right-hand sides.  With nslices / nrhs a bounded sample: only that
+    many of the p slice SVDs and of the NRHS right-hand sides (the truncation
+    then runs on the sampled slices).  Returns the measured seconds of each
+    part."""
     from oracle import sma_oracle as O
     A = pr.dense()
+    ns = pr.p if nslices is None else nslices
+    nr = NRHS if nrhs is None else nrhs
     t0 = time.perf_counter()
     X = O.T_E(A, pr.block_map, pr.p, pr.m, pr.n)
     M = O.dct2_matrix(pr.p)
     Xh = O.mode3(X, M)
     t1 = time.perf_counter()
-    for i in range(nslices):
-        np.linalg.svd(Xh[:, :, i], full_matrices=False)
+    facs = [np.linalg.svd(Xh[:, :, i], full_matrices=False) for i in range(ns)]
     t2 = time.perf_counter()
-    # the matvec on the full-rank factors (every slice kept at this tolerance)
-    terms = [(O.struct_E(list(M[i, :]), pr.block_map, pr.p), Xh[:, :, i]) for i in range(pr.p)]
-    x = np.random.default_rng(0).standard_normal((pr.q * pr.n, nrhs))
+    ranks = O.truncate_global([f[1] for f in facs], REL_TOL, float(np.sum(X * X)))
+    terms = []
+    for i in range(ns):
+        u, sv, vt = facs[i]
+        r = int(ranks[i])
+        if r > 0:
+            terms.append((O.struct_E(list(M[i, :]), pr.block_map, pr.p),
+                          (u[:, :r] * sv[:r]) @ vt[:r, :]))
     t3 = time.perf_counter()
+    x = np.random.default_rng(0).standard_normal((pr.q * pr.n, nr))
     O.apply_kron(terms, x)
     t4 = time.perf_counter()
-    full = (t1 - t0) + (t2 - t1) * pr.p / nslices + (t4 - t3) * NRHS / nrhs
-    return full, {"gather_transform_s": t1 - t0, "svd_s_per_slice": (t2 - t1) / nslices,
-                  "apply_s_per_rhs": (t4 - t3) / nrhs}
+    return {"gather_transform_s": t1 - t0, "svd_s": t2 - t1, "truncate_terms_s": t3 - t2,
+            "apply_s": t4 - t3, "slices": ns, "rhs": nr, "total_s": t4 - t0}
+
+
+def oracle_single_thread(pr, nslices, nrhs):
+    """The same sample in a child process whose BLAS and OpenMP pools are
+    limited to one thread (the pools are sized when numpy loads)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(nslices), str(nrhs),
+           "--lags", str(pr.ell)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_rate(parts, pr):
+    """Compressions per second of the full step implied by a sample: the
+    gather and transform as measured, the SVD, truncation/terms and matvec
+    parts scaled from the sampled slices and right-hand sides."""
+    fs = pr.p / parts["slices"]
+    fr = NRHS / parts["rhs"]
+    full = (parts["gather_transform_s"] + (parts["svd_s"] + parts["truncate_terms_s"]) * fs +
+            parts["apply_s"] * fr)
+    return 1.0 / full, {"slice_scale": fs, "rhs_scale": fr, "full_step_s": full}
 
 
 def main():
@@ -305,11 +665,21 @@ def main():
     ap.add_argument("--lags", type=int, default=64,
                     help="time lags T (64 = the benchmark workload; smaller for profiling)")
     ap.add_argument("--nrhs", type=int, default=256)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (planted Kronecker sum, the space-time "
+                         "BLR forms, block Hankel, the FP64 batch, 3-D blur)")
+    ap.add_argument("--oracle-sample", type=int, nargs=2, metavar=("SLICES", "RHS"),
+                    help="(internal) time one bounded oracle step and print its parts")
     args = ap.parse_args()
     global NRHS
     NRHS = args.nrhs
     if args.warmup < 3:
         args.warmup = 3
+    if args.oracle_sample:
+        from sma_inputs import generators as G
+        prs = G.spacetime_covariance(T=args.lags)
+        print(json.dumps(oracle_step(prs, *args.oracle_sample)), flush=True)
+        return
 
     from sma_inputs import generators as G
     rank = int(os.environ.get("RANK", "0"))
@@ -324,23 +694,26 @@ def main():
            "slice_svd_plan": "autotuned on the first (warm-up) compression"}
 
     if args.impl == "reference":
+        # the FP64 oracle as it stands, one whole step (every slice SVD, the
+        # truncation, the Kronecker terms and all 256 right-hand sides) per
+        # timed step, on the host's cores; ranks other than 0 exit at once
         if rank != 0:
             return
         steps = []
         for _ in range(args.warmup + args.steps):
-            t, _ = cpu_oracle_sample(pr)
-            steps.append(t)
+            steps.append(oracle_step(pr)["total_s"])
         t = float(np.mean(steps[args.warmup:]))
         v = 1.0 / t
+        sample = (f"one whole step per timed step: gather + transform, all {pr.p} slice SVDs "
+                  f"(numpy LAPACK), the global truncation, the Kronecker terms and the matvec "
+                  f"on all {NRHS} RHS; numpy's default BLAS threading")
         line = {"impl": "reference", "metric": METRIC,
                 "value": v, "unit": "compressions/s", "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": cfg,
                 "cpu_baseline": {"value": v, "unit": "compressions/s", "cores": os.cpu_count(),
-                                 "kind": "oracle",
-                                 "sample": f"full gather+transform, 16 of {pr.p} slice SVDs, "
-                                           "4 of 256 RHS of the matvec; scaled to a full step"},
+                                 "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": "compressions/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
@@ -442,13 +815,39 @@ def main():
         line["e2e"] = {"value": 1.0 / e2e_t, "unit": "compressions/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    if args.lags == 64 and not args.no_configs:
+        cfgs = {}
+        jobs = [("1_planted_kron", lambda: cfg_planted(torch, S, stream, flush, args.steps,
+                                                       alu_peak)),
+                ("2_spacetime_blr", lambda: cfg_spacetime_blr(torch, S, stream, flush,
+                                                              args.steps, pk)),
+                ("3_lti_hankel", lambda: cfg_hankel(torch, S, stream, flush, args.steps,
+                                                    alu_peak)),
+                ("4_batch_forms", lambda: cfg_batch_fp64(torch, S, stream, flush, args.steps)),
+                ("5_psf_blur", lambda: cfg_psf(torch, S, stream, flush, args.steps, pk))]
+        for name, job in jobs:
+            try:
+                cfgs[name] = job()
+            except Exception as e:          # report, keep the headline line
+                cfgs[name] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
+        line["configs"] = cfgs
+
     if rank == 0 and not args.no_cpu:
-        t_cpu, parts = cpu_oracle_sample(pr)
-        line["cpu_baseline"] = {"value": 1.0 / t_cpu, "unit": "compressions/s",
-                                "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"full gather+transform, 16 of {pr.p} slice SVDs "
-                                          f"(numpy LAPACK), 4 of {NRHS} RHS of the matvec; "
-                                          "scaled to a full step", "parts": parts}
+        full = oracle_step(pr)
+        single = oracle_single_thread(pr, 16, 4)
+        cb = {"value": 1.0 / full["total_s"], "unit": "compressions/s",
+              "cores": os.cpu_count(), "kind": "oracle",
+              "sample": (f"one whole oracle step (all {pr.p} slice SVDs, truncation, terms, "
+                         f"{NRHS}-RHS matvec) on all host cores, measured"),
+              "parts": full}
+        if single is not None:
+            rate1, scale = oracle_rate(single, pr)
+            cb["single_thread"] = {"value": rate1, "unit": "compressions/s", "cores": 1,
+                                   "sample": f"16 of {pr.p} slice SVDs and 4 of {NRHS} RHS in "
+                                             "a one-thread child process, scaled by the "
+                                             "factors given", "scale": scale, "parts": single}
+        line["cpu_baseline"] = cb
     if dist:
         dist.barrier()
         dist.destroy_process_group()

@@ -13,6 +13,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -185,6 +186,21 @@ struct Prob {
   SliceDesc<double>* gdesc = nullptr;       // per Gram slot: the Jacobi's pointers
   size_t gstride = 0;                       // elements between the two Gram slots
   int gdim = 0;
+  // mixed path: fp32 copies of the Grams, their fp32 eigenvectors, the unused
+  // W output and block-mode workspace of the fp32 Jacobi; the fp64 residual
+  // correction's Rayleigh-Ritz matrices S = U^T G U, their eigenvectors Z,
+  // two temporaries and the correction's sweep counts
+  float* g32 = nullptr;
+  float* gv32 = nullptr;
+  float* gw32 = nullptr;
+  float* wg32 = nullptr;
+  SliceDesc<float>* gdesc32 = nullptr;
+  double* gS = nullptr;
+  double* gZ = nullptr;
+  double* gT1 = nullptr;
+  double* gT2 = nullptr;
+  int* sweepsS = nullptr;
+  SliceDesc<double>* gdescS = nullptr;
   T* F1 = nullptr;                          // leading factor (rows), T
   T* F2 = nullptr;                          // second factor (cols), T
   T* core = nullptr;                        // r1 x r3 x p core slices
@@ -508,6 +524,42 @@ sma_status setup_gram_desc(sma_ctx* h, Prob<T>& P, int nslot) {
   return SMA_OK;
 }
 
+// Buffers of the mixed path's Gram eigen-solves (fp32 Jacobi, then the fp64
+// residual correction) for nslot Gram slots; nothing for the fp64 path.
+template <typename T>
+sma_status setup_gram_mixed(sma_ctx* h, Prob<T>& P, int nslot) {
+  if constexpr (std::is_same<T, float>::value) {
+    const size_t gs = P.gstride;
+    DevBuf& mem = h->mem;
+    SMA_TRY(mem.alloc(&P.g32, gs * nslot));
+    SMA_TRY(mem.alloc(&P.gv32, gs * nslot));
+    SMA_TRY(mem.alloc(&P.gw32, gs * nslot));
+    SMA_TRY(mem.alloc(&P.wg32, gs * 2));
+    SMA_TRY(mem.alloc(&P.gS, gs * nslot));
+    SMA_TRY(mem.alloc(&P.gZ, gs * nslot));
+    SMA_TRY(mem.alloc(&P.gT1, gs));
+    SMA_TRY(mem.alloc(&P.gT2, gs));
+    SMA_TRY(mem.alloc(&P.sweepsS, nslot));
+    std::vector<SliceDesc<float>> d32(nslot);
+    std::vector<SliceDesc<double>> dS(nslot);
+    for (int sl = 0; sl < nslot; ++sl) {
+      d32[sl] = SliceDesc<float>{P.g32 + (size_t)sl * gs, P.gw32 + (size_t)sl * gs,
+                                 P.gv32 + (size_t)sl * gs, P.gsig + (size_t)sl * P.gdim,
+                                 P.sweeps + sl, P.status};
+      dS[sl] = SliceDesc<double>{P.gS + (size_t)sl * gs, P.gW + (size_t)sl * gs,
+                                 P.gZ + (size_t)sl * gs, P.gsig + (size_t)sl * P.gdim,
+                                 P.sweepsS + sl, P.status};
+    }
+    SMA_TRY(mem.alloc(&P.gdesc32, (size_t)nslot));
+    SMA_TRY(mem.alloc(&P.gdescS, (size_t)nslot));
+    SMA_CK(cudaMemcpy(P.gdesc32, d32.data(), nslot * sizeof(SliceDesc<float>),
+                      cudaMemcpyHostToDevice));
+    SMA_CK(cudaMemcpy(P.gdescS, dS.data(), nslot * sizeof(SliceDesc<double>),
+                      cudaMemcpyHostToDevice));
+  }
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status setup_multilevel(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   auto& mem = h->mem;
@@ -567,6 +619,7 @@ sma_status setup_multilevel(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   SMA_TRY(mem.alloc(&P.off, 4));
   SMA_TRY(mem.alloc(&P.orth, 3));
   SMA_TRY(setup_gram_desc(h, P, 3));
+  SMA_TRY(setup_gram_mixed(h, P, 3));
   SMA_TRY(mem.alloc(&P.Gorth, P.gstride));
   P.n_orth = 3;
   SMA_CK(cudaMemset(P.stats, 0, 8 * sizeof(double)));
@@ -794,6 +847,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     SMA_TRY(mem.alloc(&P.off, nslot + 1));
     SMA_TRY(mem.alloc(&P.orth, nslot));
     SMA_TRY(setup_gram_desc(h, P, nslot));
+    SMA_TRY(setup_gram_mixed(h, P, nslot));
     P.n_orth = P.ml2 ? 4 : ((o.decomp == SMA_TUCKER_ROWCOL) ? 2 : 1);
     if (P.sk > 0) {
       const int s2 = P.sk * P.sk;
@@ -848,6 +902,8 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
 
 template <typename T>
 sma_status make_T(sma_ctx* h, Prob<T>& P);
+template <typename T>
+sma_status contract_split_k(sma_ctx* h, GemmParams<T> g, T* part, size_t part_elems);
 
 // ---------------------------------------------------------------------------
 // step 1 (gather) shared by all decompositions
@@ -1295,52 +1351,143 @@ sma_status gram_form(sma_ctx* h, Prob<T>& P, int slot, const GramSpec& gs) {
   return SMA_OK;
 }
 
-// Eigenpairs of the Grams in slots [slot, slot + count), all of order rows:
-// one cooperative launch per Gram from kCoopMinRows up, otherwise one
-// single-CTA launch for the whole group (one CTA per Gram, through the
-// per-slot descriptors).
-template <typename T>
-sma_status gram_solve(sma_ctx* h, Prob<T>& P, int slot, int count, int rows) {
+// Buffers of a group of Jacobi eigen-solves of symmetric matrices of one
+// order: matrix c at src + c stride, its eigenvectors to vec + c stride (the
+// Jacobi's W = A V output to wout + c stride, not used), eigenvalues in
+// descending order to sig + c sstride, sweep counts to sweeps + c; work is the
+// block-mode / cooperative workspace; desc the per-matrix descriptors of a
+// one-launch group (or null).
+template <typename E>
+struct EigBufs {
+  const E* src;
+  E* vec;
+  E* wout;
+  double* sig;
+  size_t stride, sstride;
+  int* sweeps;
+  E* work;
+  const SliceDesc<E>* desc;
+};
+
+// One-sided Jacobi eigen-solves of `count` matrices of order rows in the
+// element type E: one cooperative launch each from kCoopMinRows up,
+// otherwise one single-CTA launch for the whole group (one CTA per matrix,
+// through the descriptors).
+template <typename T, typename E>
+sma_status eig_jacobi(sma_ctx* h, Prob<T>& P, const EigBufs<E>& b, int count, int rows) {
   cudaStream_t st = h->st;
-  stage_begin(h, SMA_STAGE_SVD);
-  JacobiPlan jp = jacobi_plan<double>(rows, rows, h->max_smem);
+  JacobiPlan jp = jacobi_plan<E>(rows, rows, h->max_smem);
   JacobiPlan cp{};
-  if (rows >= kCoopMinRows) cp = jacobi_coop_plan<double>(rows, h->max_smem);
+  if (rows >= kCoopMinRows) cp = jacobi_coop_plan<E>(rows, h->max_smem);
   const bool coop = rows >= kCoopMinRows && cp.smem > 0 && h->coop_bar;
   if (coop) jp = cp;
-  if (jp.smem == 0) {   // a Gram order whose columns do not fit in shared memory
-    stage_end(h);
-    return SMA_ERR_UNSUPPORTED;
-  }
-  JacobiParams<double> J;
+  if (jp.smem == 0) return SMA_ERR_UNSUPPORTED;   // columns too long for shared memory
+  JacobiParams<E> J;
   J.m = rows; J.n = rows;
   J.mm = jp.mm; J.rc = jp.rc; J.trans = 0; J.ldS = jp.ldS; J.bcols = jp.bcols; J.g = jp.g;
   J.sort_n = jp.sort_n; J.tile = jp.tile;
   J.max_sweeps = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
-  J.tol = 4.0 * std::sqrt((double)rows) * Eps<double>::v;
+  J.tol = 4.0 * std::sqrt((double)rows) * Eps<E>::v;
   J.status = P.status;
-  if (!coop && !jp.block_mode && count > 1 && P.gdesc) {
-    J.desc = P.gdesc + slot;
-    SMA_K(jacobi_svd<double>(J, count, jp.threads, jp.smem, st));
-    stage_end(h);
+  if (!coop && !jp.block_mode && count > 1 && b.desc) {
+    J.desc = b.desc;
+    SMA_K(jacobi_svd<E>(J, count, jp.threads, jp.smem, st));
     return SMA_OK;
   }
   for (int c = 0; c < count; ++c) {
-    const int sl = slot + c;
-    J.src = P.gram + (size_t)sl * P.gstride; J.src_bs = 0;
-    J.W = (jp.block_mode || coop) ? P.Wg : nullptr; J.W_bs = 0;
-    J.U = P.gW; J.U_bs = 0;                                   // G V (not needed)
-    J.V = P.gvec + (size_t)sl * P.gstride; J.V_bs = 0;       // eigenvectors of G
-    J.sigma = P.gsig + (size_t)sl * P.gdim;
-    J.sweeps = P.sweeps + sl;
+    J.src = b.src + (size_t)c * b.stride; J.src_bs = 0;
+    J.W = (jp.block_mode || coop) ? b.work : nullptr; J.W_bs = 0;
+    J.U = b.wout + (size_t)c * b.stride; J.U_bs = 0;
+    J.V = b.vec + (size_t)c * b.stride; J.V_bs = 0;
+    J.sigma = b.sig + (size_t)c * b.sstride;
+    J.sweeps = b.sweeps + c;
     if (coop) {
-      SMA_K(jacobi_svd_coop<double>(J, cp, CoopSync{h->coop_bar, h->coop_rot, h->coop_abort}, st));
+      SMA_K(jacobi_svd_coop<E>(J, cp, CoopSync{h->coop_bar, h->coop_rot, h->coop_abort}, st));
     } else {
-      SMA_K(jacobi_svd<double>(J, 1, jp.threads, jp.smem, st));
+      SMA_K(jacobi_svd<E>(J, 1, jp.threads, jp.smem, st));
     }
   }
-  stage_end(h);
   return SMA_OK;
+}
+
+// C = op(A) op(B) for n x n fp64 matrices (ld n), op = transpose when ta / tb;
+// K split over the GPU (partials summed in a fixed order).
+template <typename T>
+sma_status gemm64_square(sma_ctx* h, int n, const double* A, bool ta, const double* B, bool tb,
+                         double* C) {
+  GemmParams<double> g;
+  g.M = n; g.N = n; g.K = n;
+  g.A = A; g.a_rs = ta ? n : 1; g.a_cs = ta ? 1 : n;
+  g.B = B; g.b_rs = tb ? n : 1; g.b_cs = tb ? 1 : n;
+  g.C = C; g.c_rs = 1; g.c_cs = n;
+  return contract_split_k<double>(h, g, h->gpart, h->gpart_elems);
+}
+
+// The mixed path's Gram eigen-solve.  The Gram G itself is formed in fp64
+// (exact products of the fp32 data: the truncation compares tail energies
+// with tol^2 ||X||^2, far below fp32 resolution).  Its eigenvectors are
+// found by the fp32 Jacobi, then one residual-correction pass in fp64
+// restores fp64 accuracy:
+//   1. U = the fp32 eigenvectors in fp64; one Newton-Schulz step
+//      U <- U (3 I - U^T U) / 2 makes U orthonormal to fp64 accuracy (the
+//      fp32 solve leaves |U^T U - I| near 1e-6, the step squares it);
+//   2. Rayleigh-Ritz: S = U^T G U in fp64 -- nearly diagonal, except within
+//      clusters of eigenvalues that fp32 cannot separate (the small tail
+//      the truncation reads);
+//   3. the fp64 Jacobi of S (a few sweeps from a nearly diagonal start):
+//      S = Z Lambda Z^T; the Ritz values Lambda are G's eigenvalues to fp64
+//      accuracy and U Z its eigenvectors.
+template <typename T>
+sma_status gram_solve_mixed(sma_ctx* h, Prob<T>& P, int slot, int count, int rows) {
+  cudaStream_t st = h->st;
+  const size_t gs = P.gstride;
+  const int64_t nn = (int64_t)rows * rows;
+  for (int c = 0; c < count; ++c)
+    SMA_K(convert<float, double>(P.gram + (slot + c) * gs, P.g32 + (slot + c) * gs, nn, st));
+  const EigBufs<float> b32{P.g32 + slot * gs, P.gv32 + slot * gs, P.gw32 + slot * gs,
+                           P.gsig + (size_t)slot * P.gdim, gs, (size_t)P.gdim, P.sweeps + slot,
+                           P.wg32, P.gdesc32 ? P.gdesc32 + slot : nullptr};
+  SMA_TRY(eig_jacobi<T, float>(h, P, b32, count, rows));
+  for (int c = 0; c < count; ++c) {
+    const int sl = slot + c;
+    double* U = P.gvec + sl * gs;
+    SMA_K(convert<double, float>(P.gv32 + sl * gs, U, nn, st));
+    SMA_TRY(gemm64_square<T>(h, rows, U, true, U, false, P.gT1));       // U^T U
+    SMA_TRY(gemm64_square<T>(h, rows, U, false, P.gT1, false, P.gT2));  // U (U^T U)
+    SMA_K(axpby(-0.5, P.gT2, 1.5, U, nn, st));                          // U (3I - U^T U) / 2
+    SMA_TRY(gemm64_square<T>(h, rows, P.gram + sl * gs, false, U, false, P.gT1));   // G U
+    SMA_TRY(gemm64_square<T>(h, rows, U, true, P.gT1, false, P.gS + sl * gs));     // U^T G U
+  }
+  const EigBufs<double> bS{P.gS + slot * gs, P.gZ + slot * gs, P.gW + slot * gs,
+                           P.gsig + (size_t)slot * P.gdim, gs, (size_t)P.gdim, P.sweepsS + slot,
+                           P.Wg, P.gdescS ? P.gdescS + slot : nullptr};
+  SMA_TRY(eig_jacobi<T, double>(h, P, bS, count, rows));
+  for (int c = 0; c < count; ++c) {
+    const int sl = slot + c;
+    SMA_TRY(gemm64_square<T>(h, rows, P.gvec + sl * gs, false, P.gZ + sl * gs, false, P.gT1));
+    SMA_CK(cudaMemcpyAsync(P.gvec + sl * gs, P.gT1, sizeof(double) * (size_t)nn,
+                           cudaMemcpyDeviceToDevice, st));
+  }
+  return SMA_OK;
+}
+
+// Eigenpairs of the Grams in slots [slot, slot + count), all of order rows
+// (fp64 path: the fp64 Jacobi; mixed path: gram_solve_mixed).
+template <typename T>
+sma_status gram_solve(sma_ctx* h, Prob<T>& P, int slot, int count, int rows) {
+  stage_begin(h, SMA_STAGE_SVD);
+  sma_status s;
+  if (P.g32) {
+    s = gram_solve_mixed(h, P, slot, count, rows);
+  } else {
+    const size_t gs = P.gstride;
+    const EigBufs<double> b{P.gram + slot * gs, P.gvec + slot * gs, P.gW + slot * gs,
+                            P.gsig + (size_t)slot * P.gdim, gs, (size_t)P.gdim, P.sweeps + slot,
+                            P.Wg, P.gdesc ? P.gdesc + slot : nullptr};
+    s = eig_jacobi<T, double>(h, P, b, count, rows);
+  }
+  stage_end(h);
+  return s;
 }
 
 // Rank of slot's mode: the Gram's eigenvalues are the energies sigma^2 of the

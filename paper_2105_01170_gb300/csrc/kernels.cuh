@@ -41,6 +41,8 @@ cudaError_t residual_norm2(const T* X, const T* Tt, int64_t count, double* parti
 // (Section 6.2's trace error: tr A = sum_k tr(E_k) tr(X_k)).
 template <typename T>
 cudaError_t slice_traces(const T* src, int m, int n, int p, double* out, cudaStream_t st);
+// y = a x + b y over n fp64 elements.
+cudaError_t axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t st);
 
 // ---- step 3: Jacobi SVD ---------------------------------------------------
 // Per-slice pointers for batched launches over slices of several problems.

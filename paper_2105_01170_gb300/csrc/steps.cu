@@ -470,6 +470,22 @@ __global__ void slice_traces_kernel(const T* __restrict__ src, int m, int n, int
   if (lane == 0) out[warp] = acc;
 }
 
+// y = a x + b y elementwise (fp64).
+__global__ void axpby_kernel(double a, const double* __restrict__ x, double b,
+                             double* __restrict__ y, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = fma(a, x[e], b * y[e]);
+}
+
+cudaError_t axpby(double a, const double* x, double b, double* y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  axpby_kernel<<<blocks, 256, 0, st>>>(a, x, b, y, n);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t slice_traces(const T* src, int m, int n, int p, double* out, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;

@@ -3,8 +3,8 @@ size (16384^2, 127 distinct 256 x 256 lag blocks), at settings that compress:
 
 - the SPSD shared-U compression (Sections 5.1, 6.2) at relative tolerance
   1e-2 (mode rank about 130 of 256);
-- the SPD-preserving form (Section 5.2) at fixed rank 64 (its whitened lag
-  blocks are not low rank: a tolerance below 0.1 keeps nearly all 256).
+- the SPD-preserving form (Section 5.2) at fixed ranks 64 and 8 (its whitened
+  lag blocks are not low rank: a tolerance below 0.1 keeps nearly all 256).
 
 Both precisions, against the FP64 oracle: the retained rank, the error
 report, the approximation tensor element by element, a sampled matvec, and
@@ -103,10 +103,17 @@ def tol_x(prec, s):
     return max(tol_for(prec), 2 * eps * np.sqrt(s.L.shape[0]) * c)
 
 
-@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
-def test_spd_preserving_full_size_rank_64(prec, workload):
+@pytest.mark.parametrize("prec,r", [(S.SMA_FP64, 64), (S.SMA_FP64, 8), (S.SMA_MIXED, 8)],
+                         ids=["fp64-r64", "fp64-r8", "mixed-r8"])
+def test_spd_preserving_full_size(prec, r, workload):
+    """The whitened lag blocks have a flat mode-1 spectrum (sigma 23.4 down to
+    18.6 over the first 64): at rank 64 the relative eigengap is 7e-5, so the
+    rank-64 subspace moves by about 1e-3 under fp32 rounding of X alone and
+    only the FP64 path is compared there.  The mixed path is compared at rank
+    8 (lambda_1 / (lambda_8 - lambda_9) = 77): the bound is its transformed
+    tensor's arithmetic bound tx amplified by that first-order subspace
+    sensitivity, 1 + lambda_1 / (lambda_r - lambda_{r+1})."""
     pr, Ad = workload
-    r = 64
     dt = np.float64 if prec == S.SMA_FP64 else np.float32
     B = np.asfortranarray(np.concatenate(list(pr.blocks), axis=1).astype(dt))
     h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_SPD, layout=S.SMA_INPUT_BLOCKS,
@@ -116,6 +123,8 @@ def test_spd_preserving_full_size_rank_64(prec, workload):
     A = np.asarray(Ad.astype(dt), dtype=np.float64)
     s = O.spd_preserving(A, pr.block_map, pr.p, pr.m, rank=r)
     tx = tol_x(prec, s)
+    lam = np.sort(s.su.sigma)[::-1] ** 2
+    tT = tx if prec == S.SMA_FP64 else tx * (1.0 + lam[0] / (lam[r - 1] - lam[r]))
     m = pr.m
     assert list(h.ranks(0)) == [r, r]
     assert rel(gpu_tensor(h, S.EXPORT_X, s.X.shape, prec), s.X) < tx
@@ -123,8 +132,8 @@ def test_spd_preserving_full_size_rank_64(prec, workload):
     fill_T(h, pr, prec)
     T = gpu_tensor(h, S.EXPORT_T, s.X.shape, prec)
     e_T = rel(T, s.su.tensor_approx())
-    print(f"SPD full size {PNAME[prec]}: T rel err {e_T:.2e} (bound {tx:.1e})")
-    assert e_T < tx, (e_T, tx)
+    print(f"SPD full size {PNAME[prec]} rank {r}: T rel err {e_T:.2e} (bound {tT:.1e})")
+    assert e_T < tT, (e_T, tT)
     del T
     # T_hat x = (I (x) L)(x' + M_E[T] x'), x' = (I (x) L^T) x
     nrhs = 2
@@ -137,6 +146,6 @@ def test_spd_preserving_full_size_rank_64(prec, workload):
     yp = xp + O.apply_M_E(s.su.tensor_approx(), s.inner_map, xp)
     yo = np.einsum("ij,jbs->ibs", s.L, yp.reshape(m, pr.ell, nrhs, order="F"))
     yo = yo.reshape(pr.ell * m, nrhs, order="F")
-    assert rel(Y.cpu().numpy(), yo) < tx
+    assert rel(Y.cpu().numpy(), yo) < tT
     assert res["trace_relerr"] == 0.0
     h.close()
