@@ -499,6 +499,55 @@ def cfg_hankel(torch, S, stream, flush, steps, alu_peak):
     return out
 
 
+def cfg_block_index(torch, S, stream, flush, steps):
+    """One block-tridiagonal matrix of the batched kind at the size of the
+    largest matrix of the paper's Kronecker-sum table (300 blocks of 32 x 32,
+    p = 898 distinct blocks, Kronecker rank 5): the block-index Tucker-1 at
+    rank 5 from the p x p Gram (deterministic) and from the randomized sketch
+    of Section 6.3 (s = 3)."""
+    from oracle import sma_oracle as O
+    from sma_inputs import generators as G
+    pr = G.block_tridiag_kron(300, 32)
+    r, sk = 5, 3
+    Om, Ps = G.gaussian_sketch(pr.m, pr.n, sk)
+
+    def make(prec):
+        dt = torch.float64 if prec == S.SMA_FP64 else torch.float32
+        A = pr.dense() if prec == S.SMA_FP64 else pr.dense().astype(np.float32)
+        dA = _dev(torch, A, dt)
+        X = O.T_E(np.asarray(A, np.float64), pr.block_map, pr.p, pr.m, pr.n)
+        t = O.tucker1_blockmode(X, rank=r)
+        o = {}
+        for name, kw in (("deterministic", {}), ("sketch_s3", {"sketch": (Om, Ps)})):
+            h = S.Handle([pr], prec=prec, decomp=S.SMA_TUCKER_BLOCKMODE, fixed_rank=r,
+                         stream=stream.cuda_stream, profile=True, **kw)
+            ms = _timed(torch, stream, flush, lambda: h.compress([dA], want_result=False),
+                        max(2, steps // 2), 2)
+            res = h.result(0)
+            o[name] = {"compress_ms": ms, "rel_err": res["rel_err"],
+                       "err_vs_optimal_factor": res["tensor_err"] / max(t.err, 1e-300)}
+            if name == "deterministic":
+                n = h.export_size(0, S.EXPORT_FACTOR)
+                buf = torch.empty(n, dtype=dt, device="cuda")
+                h.export(0, S.EXPORT_FACTOR, buf)
+                V = buf.cpu().numpy().astype(np.float64).reshape(pr.p, pr.p, order="F")[:, :r]
+                o[name]["factor_projector_gap_vs_oracle"] = float(
+                    np.linalg.norm(V @ V.T - t.V @ t.V.T, 2))
+            h.close()
+        return o
+
+    out = _forms(torch, S, make)
+    t0 = time.perf_counter()
+    X = O.T_E(pr.dense(), pr.block_map, pr.p, pr.m, pr.n)
+    O.tucker1_blockmode(X, rank=r)
+    out_or = (time.perf_counter() - t0) * 1e3
+    return {"workload": "block tridiagonal, 300 blocks of 32 x 32 (p = 898), Kronecker rank 5: "
+                        "block-index Tucker-1 at rank 5, deterministic (898^2 Gram) and "
+                        "randomized sketch (s = 3)",
+            "forms": out, "oracle_ms": out_or,
+            "oracle_sample": "gather and the block-index unfolding's SVD (FP64 numpy)"}
+
+
 def cfg_psf(torch, S, stream, flush, steps, pk):
     """3-D Gaussian blur of a 64^3 volume (15^3 PSF, sigma 2/3/4, rotated 30
     degrees, zero boundary): the three-level HOSVD at tolerance 1e-4 and the
@@ -824,6 +873,8 @@ def main():
                 ("3_lti_hankel", lambda: cfg_hankel(torch, S, stream, flush, args.steps,
                                                     alu_peak)),
                 ("4_batch_forms", lambda: cfg_batch_fp64(torch, S, stream, flush, args.steps)),
+                ("4b_block_index_factor", lambda: cfg_block_index(torch, S, stream, flush,
+                                                                  args.steps)),
                 ("5_psf_blur", lambda: cfg_psf(torch, S, stream, flush, args.steps, pk))]
         for name, job in jobs:
             try:

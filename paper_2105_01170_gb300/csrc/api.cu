@@ -1374,12 +1374,13 @@ struct EigBufs {
 // otherwise one single-CTA launch for the whole group (one CTA per matrix,
 // through the descriptors).
 template <typename T, typename E>
-sma_status eig_jacobi(sma_ctx* h, Prob<T>& P, const EigBufs<E>& b, int count, int rows) {
+sma_status eig_jacobi(sma_ctx* h, Prob<T>& P, const EigBufs<E>& b, int count, int rows,
+                      int coop_min_rows = kCoopMinRows) {
   cudaStream_t st = h->st;
   JacobiPlan jp = jacobi_plan<E>(rows, rows, h->max_smem);
   JacobiPlan cp{};
-  if (rows >= kCoopMinRows) cp = jacobi_coop_plan<E>(rows, h->max_smem);
-  const bool coop = rows >= kCoopMinRows && cp.smem > 0 && h->coop_bar;
+  if (rows >= coop_min_rows) cp = jacobi_coop_plan<E>(rows, h->max_smem);
+  const bool coop = rows >= coop_min_rows && cp.smem > 0 && h->coop_bar;
   if (coop) jp = cp;
   if (jp.smem == 0) return SMA_ERR_UNSUPPORTED;   // columns too long for shared memory
   JacobiParams<E> J;
@@ -1410,16 +1411,24 @@ sma_status eig_jacobi(sma_ctx* h, Prob<T>& P, const EigBufs<E>& b, int count, in
   return SMA_OK;
 }
 
-// C = op(A) op(B) for n x n fp64 matrices (ld n), op = transpose when ta / tb;
-// K split over the GPU (partials summed in a fixed order).
+// C_c = op(A_c) op(B_c) for nb pairs of n x n fp64 matrices (ld n, matrix c
+// at offset c stride in each of A, B, C; stride 0 shares a matrix), op =
+// transpose when ta / tb.  One matrix: K split over the GPU (partials summed
+// in a fixed order); several: one batched launch.
 template <typename T>
 sma_status gemm64_square(sma_ctx* h, int n, const double* A, bool ta, const double* B, bool tb,
-                         double* C) {
+                         double* C, int nb = 1, int64_t a_stride = 0, int64_t b_stride = 0,
+                         int64_t c_stride = 0) {
   GemmParams<double> g;
   g.M = n; g.N = n; g.K = n;
-  g.A = A; g.a_rs = ta ? n : 1; g.a_cs = ta ? 1 : n;
-  g.B = B; g.b_rs = tb ? n : 1; g.b_cs = tb ? 1 : n;
-  g.C = C; g.c_rs = 1; g.c_cs = n;
+  g.A = A; g.a_rs = ta ? n : 1; g.a_cs = ta ? 1 : n; g.a_b1 = a_stride;
+  g.B = B; g.b_rs = tb ? n : 1; g.b_cs = tb ? 1 : n; g.b_b1 = b_stride;
+  g.C = C; g.c_rs = 1; g.c_cs = n; g.c_b1 = c_stride;
+  g.nb1 = nb;
+  if (nb > 1) {
+    SMA_K(contract<double>(h, g));
+    return SMA_OK;
+  }
   return contract_split_k<double>(h, g, h->gpart, h->gpart_elems);
 }
 
@@ -1447,26 +1456,45 @@ sma_status gram_solve_mixed(sma_ctx* h, Prob<T>& P, int slot, int count, int row
   const EigBufs<float> b32{P.g32 + slot * gs, P.gv32 + slot * gs, P.gw32 + slot * gs,
                            P.gsig + (size_t)slot * P.gdim, gs, (size_t)P.gdim, P.sweeps + slot,
                            P.wg32, P.gdesc32 ? P.gdesc32 + slot : nullptr};
-  SMA_TRY(eig_jacobi<T, float>(h, P, b32, count, rows));
-  for (int c = 0; c < count; ++c) {
-    const int sl = slot + c;
-    double* U = P.gvec + sl * gs;
-    SMA_K(convert<double, float>(P.gv32 + sl * gs, U, nn, st));
-    SMA_TRY(gemm64_square<T>(h, rows, U, true, U, false, P.gT1));       // U^T U
-    SMA_TRY(gemm64_square<T>(h, rows, U, false, P.gT1, false, P.gT2));  // U (U^T U)
-    SMA_K(axpby(-0.5, P.gT2, 1.5, U, nn, st));                          // U (3I - U^T U) / 2
-    SMA_TRY(gemm64_square<T>(h, rows, P.gram + sl * gs, false, U, false, P.gT1));   // G U
-    SMA_TRY(gemm64_square<T>(h, rows, U, true, P.gT1, false, P.gS + sl * gs));     // U^T G U
+  // orders up to 256: the single-CTA register-tiled fp32 Jacobi (its rounds
+  // synchronise within the CTA; the cooperative form waits on a grid barrier
+  // every round, which dominates once the arithmetic is fp32)
+  SMA_TRY(eig_jacobi<T, float>(h, P, b32, count, rows, rows <= 256 ? 1 << 30 : kCoopMinRows));
+  // the residual correction of the group's `count` Grams, batched over them
+  // (slots gs apart; the temporaries hold one Gram, so batches of one for
+  // the large orders that have the split-K products)
+  double* U0 = P.gvec + slot * gs;
+  const int nb = count;
+  const int64_t bs = (int64_t)gs;
+  SMA_K(convert<double, float>(P.gv32 + slot * gs, U0, (int64_t)gs * (count - 1) + nn, st));
+  for (int c0 = 0; c0 < count; c0 += (nb > 1 && rows < 64) ? nb : 1) {
+    const int cnt = (nb > 1 && rows < 64) ? nb : 1;
+    double* U = U0 + c0 * gs;
+    const double* Gm = P.gram + (slot + c0) * gs;
+    double* Sm = P.gS + (slot + c0) * gs;
+    double* T1 = cnt > 1 ? P.gW + (slot + c0) * gs : P.gT1;   // the fp64 Jacobi's W output
+    double* T2 = cnt > 1 ? P.gZ + (slot + c0) * gs : P.gT2;   // slots serve as scratch here
+    const int64_t ts = cnt > 1 ? bs : 0;
+    SMA_TRY(gemm64_square<T>(h, rows, U, true, U, false, T1, cnt, bs, bs, ts));    // U^T U
+    SMA_TRY(gemm64_square<T>(h, rows, U, false, T1, false, T2, cnt, bs, ts, ts));  // U (U^T U)
+    for (int c = 0; c < cnt; ++c)                                                  // U(3I-U^TU)/2
+      SMA_K(axpby(-0.5, T2 + c * ts, 1.5, U + c * gs, nn, st));
+    SMA_TRY(gemm64_square<T>(h, rows, Gm, false, U, false, T1, cnt, bs, bs, ts));  // G U
+    SMA_TRY(gemm64_square<T>(h, rows, U, true, T1, false, Sm, cnt, bs, ts, bs));   // U^T G U
   }
   const EigBufs<double> bS{P.gS + slot * gs, P.gZ + slot * gs, P.gW + slot * gs,
                            P.gsig + (size_t)slot * P.gdim, gs, (size_t)P.gdim, P.sweepsS + slot,
                            P.Wg, P.gdescS ? P.gdescS + slot : nullptr};
   SMA_TRY(eig_jacobi<T, double>(h, P, bS, count, rows));
-  for (int c = 0; c < count; ++c) {
-    const int sl = slot + c;
-    SMA_TRY(gemm64_square<T>(h, rows, P.gvec + sl * gs, false, P.gZ + sl * gs, false, P.gT1));
-    SMA_CK(cudaMemcpyAsync(P.gvec + sl * gs, P.gT1, sizeof(double) * (size_t)nn,
-                           cudaMemcpyDeviceToDevice, st));
+  for (int c0 = 0; c0 < count; c0 += (nb > 1 && rows < 64) ? nb : 1) {
+    const int cnt = (nb > 1 && rows < 64) ? nb : 1;
+    double* T1 = cnt > 1 ? P.gW + (slot + c0) * gs : P.gT1;
+    const int64_t ts = cnt > 1 ? bs : 0;
+    SMA_TRY(gemm64_square<T>(h, rows, U0 + c0 * gs, false, P.gZ + (slot + c0) * gs, false, T1,
+                             cnt, bs, bs, ts));                                      // U Z
+    for (int c = 0; c < cnt; ++c)
+      SMA_CK(cudaMemcpyAsync(U0 + (c0 + c) * gs, T1 + c * ts, sizeof(double) * (size_t)nn,
+                             cudaMemcpyDeviceToDevice, st));
   }
   return SMA_OK;
 }

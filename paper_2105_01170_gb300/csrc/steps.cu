@@ -2,6 +2,9 @@
 // matrix-to-tensor map), the global truncation rule, the construction of the
 // structured Kronecker factors C_j = struct_E(v_j) (Theorem 'tuckerkron'),
 // the tensor-to-matrix scatter M_E used for validation, and reports.
+#include <cstdint>
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -11,26 +14,92 @@ namespace {
 constexpr int GATHER_THREADS = 256;
 constexpr int GATHER_MAX_CTAS = 152 * 8;
 
-// X[r, c, k] = w[k] * A[rep_off[k] + r + c*lda]; per-CTA fp64 sum of X^2.
-template <typename TS, typename T>
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ float4 scale_acc(float4 a, double w, double& acc) {
+  const float x = (float)((double)a.x * w), y = (float)((double)a.y * w),
+              z = (float)((double)a.z * w), t = (float)((double)a.w * w);
+  acc = fma((double)x, (double)x, fma((double)y, (double)y, fma((double)z, (double)z,
+            fma((double)t, (double)t, acc))));
+  return make_float4(x, y, z, t);
+}
+__device__ __forceinline__ double2 scale_acc(double2 a, double w, double& acc) {
+  const double x = a.x * w, y = a.y * w;
+  acc = fma(x, x, fma(y, y, acc));
+  return make_double2(x, y);
+}
+
+// The gather by columns: column c of slice k of X is X[:, c, k] = w[k] *
+// A[rep_off[k] + c lda + (0..m-1)].  One warp per group of GCOLS consecutive
+// tensor columns, 16-byte loads and stores (two per lane and column in
+// flight) when every column starts on a 16-byte boundary (m and lda multiples
+// of the vector width, aligned bases), elementwise otherwise.  Per-CTA fp64
+// sum of X^2.
+template <typename T, int GCOLS>
 __global__ void __launch_bounds__(GATHER_THREADS)
-gather_kernel(const TS* __restrict__ A, int64_t lda, const int64_t* __restrict__ rep_off,
-              const double* __restrict__ w, int m, int n, int p, T* __restrict__ X,
-              double* __restrict__ partial) {
+gather_cols_kernel(const T* __restrict__ A, int64_t lda, const int64_t* __restrict__ rep_off,
+                   const double* __restrict__ w, int m, int n, int p, T* __restrict__ X,
+                   double* __restrict__ partial) {
+  using V = typename Vec16<T>::type;
+  constexpr int VN = Vec16<T>::n;
   __shared__ double red[32];
-  const int64_t slice = (int64_t)m * n;
-  const int64_t total = slice * p;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ncols = (int64_t)n * p;
+  const int64_t ngroups = (ncols + GCOLS - 1) / GCOLS;
+  const bool vec_ok = (m % VN == 0) && (lda % VN == 0) &&
+                      ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+                      ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
   double acc = 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e / slice);
-    const int64_t rem = e - (int64_t)k * slice;
-    const int c = (int)(rem / m);
-    const int r = (int)(rem - (int64_t)c * m);
-    const double v = (double)A[rep_off[k] + r + (int64_t)c * lda] * w[k];
-    const T tv = (T)v;
-    X[e] = tv;
-    acc = fma((double)tv, (double)tv, acc);
+  for (int64_t gi = warp; gi < ngroups; gi += nwarps) {
+    const T* src[GCOLS];
+    T* dst[GCOLS];
+    double wk[GCOLS];
+    bool live[GCOLS];
+#pragma unroll
+    for (int j = 0; j < GCOLS; ++j) {
+      const int64_t col = gi * GCOLS + j;
+      live[j] = col < ncols;
+      const int64_t cc = live[j] ? col : 0;
+      const int k = (int)(cc / n), c = (int)(cc - (int64_t)k * n);
+      src[j] = A + rep_off[k] + (int64_t)c * lda;
+      dst[j] = X + cc * m;
+      wk[j] = w[k];
+    }
+    if (vec_ok) {
+      const int mv = m / VN;
+      for (int q0 = 0; q0 < mv; q0 += 64) {
+        V v[GCOLS][2];
+#pragma unroll
+        for (int j = 0; j < GCOLS; ++j)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int q = q0 + lane + 32 * u;
+            if (live[j] && q < mv) v[j][u] = __ldg(reinterpret_cast<const V*>(src[j]) + q);
+          }
+#pragma unroll
+        for (int j = 0; j < GCOLS; ++j)
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int q = q0 + lane + 32 * u;
+            if (live[j] && q < mv)
+              reinterpret_cast<V*>(dst[j])[q] = scale_acc(v[j][u], wk[j], acc);
+          }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < GCOLS; ++j) {
+        if (!live[j]) continue;
+        for (int r = lane; r < m; r += 32) {
+          const T tv = (T)((double)src[j][r] * wk[j]);
+          dst[j][r] = tv;
+          acc = fma((double)tv, (double)tv, acc);
+        }
+      }
+    }
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
@@ -436,7 +505,8 @@ template <typename TS, typename T>
 cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off, const double* w, int m,
                    int n, int p, T* X, double* partial, cudaStream_t st) {
   const int g = gather_parts(m, n, p);
-  gather_kernel<TS, T><<<g, GATHER_THREADS, 0, st>>>(A, lda, rep_off, w, m, n, p, X, partial);
+  static_assert(std::is_same<TS, T>::value, "the gather keeps the input's element type");
+  gather_cols_kernel<T, 4><<<g, GATHER_THREADS, 0, st>>>(A, lda, rep_off, w, m, n, p, X, partial);
   return cudaGetLastError();
 }
 
