@@ -1421,14 +1421,16 @@ sma_status gemm64_square(sma_ctx* h, int n, const double* A, bool ta, const doub
                          int64_t c_stride = 0) {
   GemmParams<double> g;
   g.M = n; g.N = n; g.K = n;
-  g.A = A; g.a_rs = ta ? n : 1; g.a_cs = ta ? 1 : n; g.a_b1 = a_stride;
-  g.B = B; g.b_rs = tb ? n : 1; g.b_cs = tb ? 1 : n; g.b_b1 = b_stride;
-  g.C = C; g.c_rs = 1; g.c_cs = n; g.c_b1 = c_stride;
-  g.nb1 = nb;
+  g.A = A; g.a_rs = ta ? n : 1; g.a_cs = ta ? 1 : n;
+  g.B = B; g.b_rs = tb ? n : 1; g.b_cs = tb ? 1 : n;
+  g.C = C; g.c_rs = 1; g.c_cs = n;
   if (nb > 1) {
+    g.a_b1 = a_stride; g.b_b1 = b_stride; g.c_b1 = c_stride;
+    g.nb1 = nb;
     SMA_K(contract<double>(h, g));
     return SMA_OK;
   }
+  // (the split-K form uses the batch index for its K chunks: strides stay 0)
   return contract_split_k<double>(h, g, h->gpart, h->gpart_elems);
 }
 

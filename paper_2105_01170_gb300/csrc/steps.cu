@@ -31,71 +31,66 @@ __device__ __forceinline__ double2 scale_acc(double2 a, double w, double& acc) {
   return make_double2(x, y);
 }
 
-// The gather by columns: column c of slice k of X is X[:, c, k] = w[k] *
-// A[rep_off[k] + c lda + (0..m-1)].  One warp per group of GCOLS consecutive
-// tensor columns, 16-byte loads and stores (two per lane and column in
-// flight) when every column starts on a 16-byte boundary (m and lda multiples
-// of the vector width, aligned bases), elementwise otherwise.  Per-CTA fp64
-// sum of X^2.
-template <typename T, int GCOLS>
+// The gather by 16-byte vectors: column c of slice k of X is X[:, c, k] =
+// w[k] A[rep_off[k] + c lda + (0..m-1)].  The vectors of all columns are
+// numbered consecutively (column-major), and each thread loads U of them
+// (a grid stride apart) before it stores any, so U 16-byte loads per thread
+// are in flight; a warp's loads cover consecutive vectors, which are
+// consecutive addresses within a column whatever m is.  Used when every
+// column starts on a 16-byte boundary (m and lda multiples of the vector
+// width, aligned bases); otherwise elementwise with the same numbering.
+// Per-CTA fp64 sum of X^2.
+template <typename T, int U>
 __global__ void __launch_bounds__(GATHER_THREADS)
-gather_cols_kernel(const T* __restrict__ A, int64_t lda, const int64_t* __restrict__ rep_off,
-                   const double* __restrict__ w, int m, int n, int p, T* __restrict__ X,
-                   double* __restrict__ partial) {
+gather_vec_kernel(const T* __restrict__ A, int64_t lda, const int64_t* __restrict__ rep_off,
+                  const double* __restrict__ w, int m, int n, int p, T* __restrict__ X,
+                  double* __restrict__ partial) {
   using V = typename Vec16<T>::type;
   constexpr int VN = Vec16<T>::n;
   __shared__ double red[32];
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t ncols = (int64_t)n * p;
-  const int64_t ngroups = (ncols + GCOLS - 1) / GCOLS;
   const bool vec_ok = (m % VN == 0) && (lda % VN == 0) &&
                       ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
                       ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+  const int vw = vec_ok ? VN : 1;                 // elements per item
+  const int mv = m / vw;                          // items per column
+  const int64_t total = (int64_t)n * p * mv;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   double acc = 0.0;
-  for (int64_t gi = warp; gi < ngroups; gi += nwarps) {
-    const T* src[GCOLS];
-    T* dst[GCOLS];
-    double wk[GCOLS];
-    bool live[GCOLS];
+  for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < total;
+       e0 += stride * U) {
+    int64_t src_off[U];
+    double wk[U];
 #pragma unroll
-    for (int j = 0; j < GCOLS; ++j) {
-      const int64_t col = gi * GCOLS + j;
-      live[j] = col < ncols;
-      const int64_t cc = live[j] ? col : 0;
-      const int k = (int)(cc / n), c = (int)(cc - (int64_t)k * n);
-      src[j] = A + rep_off[k] + (int64_t)c * lda;
-      dst[j] = X + cc * m;
-      wk[j] = w[k];
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = e0 + u * stride;
+      const int64_t ee = e < total ? e : 0;
+      const int64_t col = ee / mv;
+      const int q = (int)(ee - col * mv);
+      const int k = (int)(col / n), c = (int)(col - (int64_t)k * n);
+      src_off[u] = rep_off[k] + (int64_t)c * lda + (int64_t)q * vw;
+      wk[u] = w[k];
     }
     if (vec_ok) {
-      const int mv = m / VN;
-      for (int q0 = 0; q0 < mv; q0 += 64) {
-        V v[GCOLS][2];
+      V v[U];
 #pragma unroll
-        for (int j = 0; j < GCOLS; ++j)
+      for (int u = 0; u < U; ++u)
+        if (e0 + u * stride < total) v[u] = __ldg(reinterpret_cast<const V*>(A + src_off[u]));
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int q = q0 + lane + 32 * u;
-            if (live[j] && q < mv) v[j][u] = __ldg(reinterpret_cast<const V*>(src[j]) + q);
-          }
-#pragma unroll
-        for (int j = 0; j < GCOLS; ++j)
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int q = q0 + lane + 32 * u;
-            if (live[j] && q < mv)
-              reinterpret_cast<V*>(dst[j])[q] = scale_acc(v[j][u], wk[j], acc);
-          }
+      for (int u = 0; u < U; ++u) {
+        const int64_t e = e0 + u * stride;
+        if (e < total) reinterpret_cast<V*>(X)[e] = scale_acc(v[u], wk[u], acc);
       }
     } else {
+      T v[U];
 #pragma unroll
-      for (int j = 0; j < GCOLS; ++j) {
-        if (!live[j]) continue;
-        for (int r = lane; r < m; r += 32) {
-          const T tv = (T)((double)src[j][r] * wk[j]);
-          dst[j][r] = tv;
+      for (int u = 0; u < U; ++u)
+        if (e0 + u * stride < total) v[u] = __ldg(A + src_off[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t e = e0 + u * stride;
+        if (e < total) {
+          const T tv = (T)((double)v[u] * wk[u]);
+          X[e] = tv;
           acc = fma((double)tv, (double)tv, acc);
         }
       }
@@ -506,7 +501,7 @@ cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off, const doubl
                    int n, int p, T* X, double* partial, cudaStream_t st) {
   const int g = gather_parts(m, n, p);
   static_assert(std::is_same<TS, T>::value, "the gather keeps the input's element type");
-  gather_cols_kernel<T, 4><<<g, GATHER_THREADS, 0, st>>>(A, lda, rep_off, w, m, n, p, X, partial);
+  gather_vec_kernel<T, 4><<<g, GATHER_THREADS, 0, st>>>(A, lda, rep_off, w, m, n, p, X, partial);
   return cudaGetLastError();
 }
 
