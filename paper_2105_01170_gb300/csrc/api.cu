@@ -1458,10 +1458,10 @@ sma_status gram_solve_mixed(sma_ctx* h, Prob<T>& P, int slot, int count, int row
   const EigBufs<float> b32{P.g32 + slot * gs, P.gv32 + slot * gs, P.gw32 + slot * gs,
                            P.gsig + (size_t)slot * P.gdim, gs, (size_t)P.gdim, P.sweeps + slot,
                            P.wg32, P.gdesc32 ? P.gdesc32 + slot : nullptr};
-  // orders up to 256: the single-CTA register-tiled fp32 Jacobi (its rounds
-  // synchronise within the CTA; the cooperative form waits on a grid barrier
-  // every round, which dominates once the arithmetic is fp32)
-  SMA_TRY(eig_jacobi<T, float>(h, P, b32, count, rows, rows <= 256 ? 1 << 30 : kCoopMinRows));
+  // the single-CTA register-tiled fp32 Jacobi (its rounds synchronise within
+  // the CTA; the cooperative form waits on a grid barrier every round, which
+  // dominates once the arithmetic is fp32)
+  SMA_TRY(eig_jacobi<T, float>(h, P, b32, count, rows, 1 << 30));
   // the residual correction of the group's `count` Grams, batched over them
   // (slots gs apart; the temporaries hold one Gram, so batches of one for
   // the large orders that have the split-K products)
@@ -1501,13 +1501,21 @@ sma_status gram_solve_mixed(sma_ctx* h, Prob<T>& P, int slot, int count, int row
   return SMA_OK;
 }
 
+// Largest Gram order for which the mixed path solves in fp32 and corrects in
+// fp64: up to it the fp32 solve is the single-CTA register-tiled Jacobi;
+// above it only the cooperative Jacobi is left, whose rounds each wait on a
+// grid barrier, and in fp32 that form is no faster than the fp64 solve (the
+// 898^2 block-index Gram: 462 ms against 408 ms measured), so larger orders
+// take the fp64 Jacobi on both paths.
+constexpr int kMixedGramMaxRows = 256;
+
 // Eigenpairs of the Grams in slots [slot, slot + count), all of order rows
 // (fp64 path: the fp64 Jacobi; mixed path: gram_solve_mixed).
 template <typename T>
 sma_status gram_solve(sma_ctx* h, Prob<T>& P, int slot, int count, int rows) {
   stage_begin(h, SMA_STAGE_SVD);
   sma_status s;
-  if (P.g32) {
+  if (P.g32 && rows <= kMixedGramMaxRows) {
     s = gram_solve_mixed(h, P, slot, count, rows);
   } else {
     const size_t gs = P.gstride;
