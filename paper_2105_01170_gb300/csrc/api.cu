@@ -232,6 +232,15 @@ struct Prob {
   int lell[3] = {0, 0, 0}, lq[3] = {0, 0, 0}, lp[3] = {0, 0, 0};
   std::vector<int32_t> lmap[3];
   int* d_lmap[3] = {nullptr, nullptr, nullptr};
+  // the levels' maps as compressed-row lists (row offsets, columns, distinct
+  // index) for the structured matvec, and its coefficient buffers
+  int* d_lptr[3] = {nullptr, nullptr, nullptr};
+  int* d_lcol[3] = {nullptr, nullptr, nullptr};
+  int* d_lkk[3] = {nullptr, nullptr, nullptr};
+  int lnnz[3] = {0, 0, 0};
+  T* mlc1 = nullptr;
+  T* mlc2 = nullptr;
+  T* mlcb = nullptr;
   double* d_lw[3] = {nullptr, nullptr, nullptr};
   double* d_lisq[3] = {nullptr, nullptr, nullptr};
   T* Uml[3] = {nullptr, nullptr, nullptr};  // factors (p_t x p_t, leading k_t used)
@@ -249,6 +258,7 @@ struct Prob {
   T* Wml = nullptr;
   size_t Wml_elems = 0;
   bool ml_valid = false;
+  bool ml_cvalid = false;                   // the structured matvec's coefficients
   // two levels with m x n blocks (Section 7): the one-level problem of the
   // product map; the factors of the four modes (m, n, p1, p2) and the core
   // and term workspaces of the Kronecker sum over (j1, j2)
@@ -590,7 +600,31 @@ sma_status setup_multilevel(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
                       cudaMemcpyHostToDevice));
     SMA_CK(cudaMemcpy(P.d_lw[t], w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
     SMA_CK(cudaMemcpy(P.d_lisq[t], isq.data(), isq.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // compressed-row list of the map (rows a, nonzero positions in column order)
+    std::vector<int> rp(P.lell[t] + 1, 0), cl, kk;
+    for (int a = 0; a < P.lell[t]; ++a) {
+      for (int b = 0; b < P.lq[t]; ++b) {
+        const int k = P.lmap[t][(size_t)a + (size_t)b * P.lell[t]];
+        if (k >= 0) {
+          cl.push_back(b);
+          kk.push_back(k);
+        }
+      }
+      rp[a + 1] = (int)cl.size();
+    }
+    P.lnnz[t] = (int)cl.size();
+    SMA_TRY(mem.alloc(&P.d_lptr[t], rp.size()));
+    SMA_TRY(mem.alloc(&P.d_lcol[t], cl.size() > 0 ? cl.size() : 1));
+    SMA_TRY(mem.alloc(&P.d_lkk[t], kk.size() > 0 ? kk.size() : 1));
+    SMA_CK(cudaMemcpy(P.d_lptr[t], rp.data(), rp.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!cl.empty()) {
+      SMA_CK(cudaMemcpy(P.d_lcol[t], cl.data(), cl.size() * sizeof(int), cudaMemcpyHostToDevice));
+      SMA_CK(cudaMemcpy(P.d_lkk[t], kk.data(), kk.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
   }
+  SMA_TRY(mem.alloc(&P.mlc1, (size_t)P.lp[0] * (P.lnnz[0] > 0 ? P.lnnz[0] : 1)));
+  SMA_TRY(mem.alloc(&P.mlc2, (size_t)P.lp[1] * (P.lnnz[1] > 0 ? P.lnnz[1] : 1)));
+  SMA_TRY(mem.alloc(&P.mlcb, (size_t)P.lp[0] * P.lp[1] * (P.lnnz[2] > 0 ? P.lnnz[2] : 1)));
   P.p = P.lp[0] * P.lp[1] * P.lp[2];
   const size_t np = (size_t)P.p;
   P.gdim = gdim;
@@ -2037,6 +2071,7 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
     SMA_TRY(compress_multilevel(h, P, A));
     P.compressed = true;
     P.ml_valid = false;
+    P.ml_cvalid = false;
     P.h_iscal[0] = -1;
     return SMA_OK;
   }
@@ -2204,6 +2239,7 @@ void mark_compressed(sma_ctx* h) {
     P.dp_valid = false;
     P.cq_valid = false;
     P.ml_valid = false;
+    P.ml_cvalid = false;
     P.h_iscal[0] = -1;
   }
 }
@@ -2401,6 +2437,23 @@ sma_status apply_multilevel(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* 
                                P.Gc + (size_t)p1 * p2 * j3, p1 * sizeof(T), k1 * sizeof(T), k2,
                                cudaMemcpyDeviceToDevice, st));
     P.ml_valid = true;
+  }
+  {  // the factors' structured form, when its plane fits in shared memory
+    MlApply<T> mp;
+    for (int t = 0; t < 3; ++t) {
+      mp.l[t] = P.lell[t]; mp.q[t] = P.lq[t]; mp.p[t] = P.lp[t]; mp.nnz[t] = P.lnnz[t];
+      mp.ptr[t] = P.d_lptr[t]; mp.col[t] = P.d_lcol[t]; mp.kk[t] = P.d_lkk[t];
+      mp.isq[t] = P.d_lisq[t]; mp.U[t] = P.Uml[t];
+    }
+    mp.r[0] = k1; mp.r[1] = k2; mp.r[2] = k3;
+    mp.G = P.Gc; mp.c1 = P.mlc1; mp.c2 = P.mlc2; mp.b = P.mlcb;
+    if (ml_apply_smem(mp) <= (size_t)h->max_smem) {
+      SMA_TRY(grow(h, &P.Wml, &P.Wml_elems, (size_t)l3 * l2 * k1 * q1 * nv));
+      h->launches += P.ml_cvalid ? 1 : 2;
+      SMA_K(ml_apply<T>(mp, !P.ml_cvalid, X, ldx, P.Wml, Y, ldy, nv, st));
+      P.ml_cvalid = true;
+      return SMA_OK;
+    }
   }
   const int64_t n21 = (int64_t)q2 * q1;
   SMA_TRY(grow(h, &P.U3x, &P.U3x_elems, (size_t)l3 * k3 * n21 * nv));

@@ -208,6 +208,35 @@ template <typename T>
 cudaError_t ml_core(const T* G, int k12, int k3, const T* U, int l3, int64_t ncol, T* V,
                     cudaStream_t st);
 
+// ---- three-level matvec in the factors' structured form (ml_apply.cu) -------
+// Level t (0 outermost): l[t] x q[t] map with p[t] distinct values, its
+// nonzero positions as a compressed-row list (ptr: l[t] + 1 offsets; col:
+// the column b; kk: the distinct index map(a, b)), 1/sqrt(eta) per distinct
+// index, the factor U_t (p[t] x p[t], leading r[t] columns used); G the core
+// (p0 x p1 x p2); c1, c2, b the coefficient buffers (r0 nnz0, r1 nnz1,
+// r0 r1 nnz2 entries).
+template <typename T>
+struct MlApply {
+  int l[3], q[3], p[3], r[3], nnz[3];
+  const int* ptr[3];
+  const int* col[3];
+  const int* kk[3];
+  const double* isq[3];
+  const T* U[3];
+  const T* G;
+  T* c1;
+  T* c2;
+  T* b;
+};
+// Shared memory of ml_xy_kernel for these sizes.
+template <typename T>
+size_t ml_apply_smem(const MlApply<T>& P);
+// Y (l0 l1 l2 x nv, ld ldy) = A_hat X (q0 q1 q2 x nv, ld ldx) through W
+// (l1 l2 r0 q0 nv elements); coef: recompute c1, c2, b first.
+template <typename T>
+cudaError_t ml_apply(const MlApply<T>& P, bool coef, const T* X, int64_t ldx, T* W, T* Y,
+                     int64_t ldy, int nv, cudaStream_t st);
+
 // copy and precision conversion helpers
 // dst[i0 + n0 (i1 + n1 i2)] = src[i0 s0 + i1 s1 + i2 s2] (fp64)
 cudaError_t permute3(const double* src, int64_t s0, int64_t s1, int64_t s2, int n0, int n1, int n2,
