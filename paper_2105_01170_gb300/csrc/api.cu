@@ -118,6 +118,7 @@ struct Prob {
   int* d_nzk = nullptr;                     // their block index k
   int nnz = 0;
   double* d_w = nullptr;                    // sqrt(eta_k)
+  float* d_wf = nullptr;                    // sqrt(eta_k) as fp32 pairs (hi, lo)
   double* d_isq = nullptr;                  // 1/sqrt(eta_k)
   int64_t* d_rep = nullptr;
   int64_t rep_lda = -1;
@@ -737,6 +738,15 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   }
   SMA_CK(cudaMemcpy(P.d_w, w.data(), p * sizeof(double), cudaMemcpyHostToDevice));
   SMA_CK(cudaMemcpy(P.d_isq, isq.data(), p * sizeof(double), cudaMemcpyHostToDevice));
+  {
+    std::vector<float> wf(2 * (size_t)p);
+    for (int k = 0; k < p; ++k) {
+      wf[2 * k] = (float)w[k];
+      wf[2 * k + 1] = (float)(w[k] - (double)wf[2 * k]);
+    }
+    SMA_TRY(mem.alloc(&P.d_wf, wf.size()));
+    SMA_CK(cudaMemcpy(P.d_wf, wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   SMA_TRY(mem.alloc(&P.X, mnp));
   P.nparts = gather_parts(m, n, p);
   SMA_TRY(mem.alloc(&P.partial, P.nparts));
@@ -991,7 +1001,7 @@ sma_status do_gather(sma_ctx* h, Prob<T>& P, const void* Ain, int64_t lda) {
     P.rep_lda = use_lda;
     P.rep_layout = layout;
   }
-  SMA_K(gather<T, T>(A, use_lda, P.d_rep, P.d_w, m, n, p, P.X, P.partial, st));
+  SMA_K(gather<T, T>(A, use_lda, P.d_rep, P.d_w, P.d_wf, m, n, p, P.X, P.partial, st));
   SMA_K(finish_norm(P.partial, P.nparts, P.stats, st));
   stage_end(h);
   return SMA_OK;

@@ -7,13 +7,15 @@
 namespace sma {
 
 // ---- step 1: struct_E gather --------------------------------------------
-// X[:, :, k] = w[k] * A_rep(k); rep_row/rep_col give the element offset of
-// the representative block (dense layout: row a*m, col b*n; blocks layout:
-// row 0, col k*n).  Source may be fp64 or fp32 (TS), output T.
+// X[:, :, k] = w[k] * A_rep(k); rep_off gives the element offset of the
+// representative block (dense layout: a*m + b*n*lda; blocks layout:
+// k*n*lda).  wf holds w[k] as the fp32 pair (RN32(w), RN32(w - RN32(w))),
+// which the fp32 form scales with (to the fp64 reference's value).  Output T
+// = the input's type.
 template <typename TS, typename T>
 cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off /*device, p*/,
-                   const double* w /*device, p*/, int m, int n, int p, T* X,
-                   double* partial /*device, >= 1024*/, cudaStream_t st);
+                   const double* w /*device, p*/, const float* wf /*device, 2p*/, int m, int n,
+                   int p, T* X, double* partial /*device, >= 1024*/, cudaStream_t st);
 // ||X||_F^2 from the per-CTA partial sums written by gather.
 cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStream_t st);
 // out[e] = sum_s part[e + s count] for e < count, s < nslab (fixed order: the

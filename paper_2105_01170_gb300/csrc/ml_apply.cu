@@ -61,8 +61,10 @@ __global__ void ml_coef_kernel(const MlApply<T> P) {
 
 // One CTA per (plane b1, volume v).  Shared memory: the plane Xp[b3 + q3 b2],
 // the level-3 pass Tp[a3 + l3 b2], the accumulator Acc[a3 + l3 a2], the
-// coefficients of the current (j1, j2) and the two levels' row lists.
-template <typename T>
+// coefficients of the current (j1, j2) and the two levels' row lists.  G
+// outputs per thread share each row's coefficient and column loads (G = 4
+// when q2 and l3 are multiples of 4, else 1).
+template <typename T, int G>
 __global__ void __launch_bounds__(ML_THREADS)
 ml_xy_kernel(const MlApply<T> P, const T* __restrict__ X, int64_t ldx, T* __restrict__ W) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -92,24 +94,49 @@ ml_xy_kernel(const MlApply<T> P, const T* __restrict__ X, int64_t ldx, T* __rest
       for (int i = tid; i < nnz3; i += nth) cb[i] = P.b[(int64_t)(j1 + P.r[0] * j2) * nnz3 + i];
       for (int i = tid; i < nnz2; i += nth) c2s[i] = P.c2[(int64_t)j2 * nnz2 + i];
       __syncthreads();
-      // level 3: Tp[a3, b2] = sum over row a3 of map 3 of B_{j1 j2}[a3, b3] x[b3, b2]
-      for (int i = tid; i < l3 * q2; i += nth) {
-        const int a3 = i % l3, b2 = i / l3;
-        const T* xr = Xp + q3 * b2;
-        T acc = T(0);
-        for (int e = ptr3[a3]; e < ptr3[a3 + 1]; ++e) acc = fma(cb[e], xr[col3[e]], acc);
-        Tp[i] = acc;
+      // level 3: Tp[a3, b2] = sum over row a3 of map 3 of B_{j1 j2}[a3, b3] x[b3, b2];
+      // a thread takes G values of b2 (q2 / G apart) on one row a3, so each
+      // coefficient and column index is read once for G products
+      {
+        const int qg = q2 / G;
+        for (int i = tid; i < l3 * qg; i += nth) {
+          const int a3 = i % l3, bg = i / l3;
+          T acc[G];
+#pragma unroll
+          for (int u = 0; u < G; ++u) acc[u] = T(0);
+          for (int e = ptr3[a3]; e < ptr3[a3 + 1]; ++e) {
+            const T cf = cb[e];
+            const T* xc = Xp + col3[e] + q3 * bg;
+#pragma unroll
+            for (int u = 0; u < G; ++u) acc[u] = fma(cf, xc[q3 * qg * u], acc[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < G; ++u) Tp[a3 + l3 * (bg + qg * u)] = acc[u];
+        }
       }
       __syncthreads();
-      // level 2: Acc[a3, a2] += sum over row a2 of map 2 of C2_j2[a2, b2] Tp[a3, b2]
-      for (int i = tid; i < l3 * l2; i += nth) {
-        const int a3 = i % l3, a2 = i / l3;
-        T acc = Acc[i];
-        for (int e = ptr2[a2]; e < ptr2[a2 + 1]; ++e) acc = fma(c2s[e], Tp[a3 + l3 * col2[e]], acc);
-        Acc[i] = acc;
+      // level 2: Acc[a3, a2] += sum over row a2 of map 2 of C2_j2[a2, b2] Tp[a3, b2];
+      // a thread takes G values of a3 (l3 / G apart) on one row a2
+      {
+        const int lg = l3 / G;
+        for (int i = tid; i < lg * l2; i += nth) {
+          const int ag = i % lg, a2 = i / lg;
+          T* ac = Acc + ag + l3 * a2;
+          T acc[G];
+#pragma unroll
+          for (int u = 0; u < G; ++u) acc[u] = ac[lg * u];
+          for (int e = ptr2[a2]; e < ptr2[a2 + 1]; ++e) {
+            const T cf = c2s[e];
+            const T* tc = Tp + ag + l3 * col2[e];
+#pragma unroll
+            for (int u = 0; u < G; ++u) acc[u] = fma(cf, tc[lg * u], acc[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < G; ++u) ac[lg * u] = acc[u];
+        }
       }
     }
-    // the same thread wrote Acc[i] in the last loop: no barrier needed here
+    __syncthreads();   // Acc is read in another thread-to-element order
     T* w = W + (int64_t)l3 * l2 * (j1 + (int64_t)P.r[0] * (b1 + (int64_t)P.q[0] * v));
     for (int i = tid; i < l3 * l2; i += nth) w[i] = Acc[i];
   }
@@ -157,10 +184,12 @@ cudaError_t ml_apply(const MlApply<T>& P, bool coef, const T* X, int64_t ldx, T*
     if (e != cudaSuccess) return e;
   }
   const size_t smem = ml_apply_smem(P);
-  cudaError_t e = cudaFuncSetAttribute(ml_xy_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  void (*kern)(const MlApply<T>, const T*, int64_t, T*) =
+      (P.q[1] % 4 == 0 && P.l[2] % 4 == 0) ? ml_xy_kernel<T, 4> : ml_xy_kernel<T, 1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  ml_xy_kernel<T><<<dim3(P.q[0], nv), ML_THREADS, smem, st>>>(P, X, ldx, W);
+  kern<<<dim3(P.q[0], nv), ML_THREADS, smem, st>>>(P, X, ldx, W);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int plane = P.l[1] * P.l[2];
   ml_z_kernel<T><<<dim3((plane + ML_THREADS - 1) / ML_THREADS, nv), ML_THREADS, 0, st>>>(P, W, Y,

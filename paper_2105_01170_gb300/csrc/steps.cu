@@ -18,18 +18,71 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
 
-__device__ __forceinline__ float4 scale_acc(float4 a, double w, double& acc) {
-  const float x = (float)((double)a.x * w), y = (float)((double)a.y * w),
-              z = (float)((double)a.z * w), t = (float)((double)a.w * w);
-  acc = fma((double)x, (double)x, fma((double)y, (double)y, fma((double)z, (double)z,
-            fma((double)t, (double)t, acc))));
-  return make_float4(x, y, z, t);
+// x = RN32(RN64(a w)) -- the product rounded to double, then to float, as the
+// fp64 reference computes it -- from fp32 arithmetic (fp64 only in rare
+// cases).  w = wh + wl + d with wh = RN32(w), wl = RN32(w - wh), |d| <=
+// 2^-48 |w|.  a wh = p + e exactly (e by FMA); f = RN32(a wl + e); then
+// r = RN32(p + f) and the residual t = (p - r) + f (p - r is exact) place
+// a w within about 2^-46 |a w| of r + t.  When |t| stays below half an ulp
+// of r by more than 2^-40 |r|, both a w and its double rounding lie strictly
+// inside r's rounding interval, so r is the reference value.  When w is
+// itself a float (wl = 0, e.g. an integer sqrt(eta)) a w = p + e exactly, its
+// double rounding is exact, and r = RN32(p + e) is the reference value ties
+// included.  Otherwise (a tie within reach, r a power of two, r tiny or not
+// finite) the fp64 product decides.
+__device__ __forceinline__ float scale_exact(float a, float wh, float wl, double w) {
+  const float p = a * wh;
+  const float e = fmaf(a, wh, -p);
+  const float f = fmaf(a, wl, e);
+  const float r = p + f;
+  const float t = (p - r) + f;
+  const float ar = fabsf(r);
+  const unsigned bits = __float_as_uint(ar);
+  const float half_ulp = __uint_as_float((bits & 0x7f800000u) - (24u << 23));
+  const bool safe = ar > 0x1p-100f && ar < 0x1p+100f && (bits & 0x007fffffu) != 0u &&
+                    fabsf(t) < half_ulp - ar * 0x1p-40f;
+  if (safe || a == 0.f || wl == 0.f) return r;
+  return (float)((double)a * w);
 }
-__device__ __forceinline__ double2 scale_acc(double2 a, double w, double& acc) {
+
+// s + (hi, lo) as a float-float sum (Knuth's two-sum for the high part; the
+// low part collects the rounding errors and the exact square remainders).
+__device__ __forceinline__ void ff_add_square(float r, float& hi, float& lo) {
+  const float sq = r * r;
+  const float esq = fmaf(r, r, -sq);
+  const float t = hi + sq;
+  const float bv = t - hi;
+  const float err = (hi - (t - bv)) + (sq - bv);
+  hi = t;
+  lo += err + esq;
+}
+
+__device__ __forceinline__ float4 scale_acc(float4 a, float wh, float wl, double w, float& hi,
+                                            float& lo) {
+  const float4 x = make_float4(scale_exact(a.x, wh, wl, w), scale_exact(a.y, wh, wl, w),
+                               scale_exact(a.z, wh, wl, w), scale_exact(a.w, wh, wl, w));
+  ff_add_square(x.x, hi, lo);
+  ff_add_square(x.y, hi, lo);
+  ff_add_square(x.z, hi, lo);
+  ff_add_square(x.w, hi, lo);
+  return x;
+}
+__device__ __forceinline__ double2 scale_acc(double2 a, float, float, double w, double& acc,
+                                             double&) {
   const double x = a.x * w, y = a.y * w;
   acc = fma(x, x, fma(y, y, acc));
   return make_double2(x, y);
 }
+
+// Division by a value fixed for the launch: shift and mask for powers of two.
+struct Div32 {
+  unsigned d, shift;
+  bool pow2;
+  __host__ __device__ Div32(unsigned d_) : d(d_), shift(0), pow2((d_ & (d_ - 1)) == 0) {
+    while ((1u << shift) < d_) ++shift;
+  }
+  __device__ __forceinline__ unsigned div(unsigned x) const { return pow2 ? x >> shift : x / d; }
+};
 
 // The gather by 16-byte vectors: column c of slice k of X is X[:, c, k] =
 // w[k] A[rep_off[k] + c lda + (0..m-1)].  The vectors of all columns are
@@ -38,64 +91,74 @@ __device__ __forceinline__ double2 scale_acc(double2 a, double w, double& acc) {
 // are in flight; a warp's loads cover consecutive vectors, which are
 // consecutive addresses within a column whatever m is.  Used when every
 // column starts on a 16-byte boundary (m and lda multiples of the vector
-// width, aligned bases); otherwise elementwise with the same numbering.
-// Per-CTA fp64 sum of X^2.
+// width, aligned bases) and the item count fits 32 bits; otherwise
+// elementwise with the same numbering.  The fp32 scaling is the fp64
+// reference's value (scale_exact) and ||X||^2 is summed per thread as a
+// float-float pair, so the loop runs on the fp32 pipe; the per-CTA partial
+// sums are fp64.
 template <typename T, int U>
 __global__ void __launch_bounds__(GATHER_THREADS)
 gather_vec_kernel(const T* __restrict__ A, int64_t lda, const int64_t* __restrict__ rep_off,
-                  const double* __restrict__ w, int m, int n, int p, T* __restrict__ X,
-                  double* __restrict__ partial) {
+                  const double* __restrict__ w, const float2* __restrict__ wf, int m, int n,
+                  int p, T* __restrict__ X, double* __restrict__ partial) {
   using V = typename Vec16<T>::type;
   constexpr int VN = Vec16<T>::n;
+  using Acc = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
   __shared__ double red[32];
+  const int64_t total_v = (int64_t)n * p * (m / VN);
   const bool vec_ok = (m % VN == 0) && (lda % VN == 0) &&
                       ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
-                      ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-  const int vw = vec_ok ? VN : 1;                 // elements per item
-  const int mv = m / vw;                          // items per column
-  const int64_t total = (int64_t)n * p * mv;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  double acc = 0.0;
-  for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e0 < total;
-       e0 += stride * U) {
-    int64_t src_off[U];
-    double wk[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t e = e0 + u * stride;
-      const int64_t ee = e < total ? e : 0;
-      const int64_t col = ee / mv;
-      const int q = (int)(ee - col * mv);
-      const int k = (int)(col / n), c = (int)(col - (int64_t)k * n);
-      src_off[u] = rep_off[k] + (int64_t)c * lda + (int64_t)q * vw;
-      wk[u] = w[k];
-    }
-    if (vec_ok) {
+                      ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && total_v < (1ll << 31);
+  Acc hi = Acc(0), lo = Acc(0);
+  if (vec_ok) {
+    const unsigned mv = (unsigned)(m / VN), total = (unsigned)total_v;
+    const Div32 dmv(mv), dn((unsigned)n);
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < total; e0 += stride * U) {
       V v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (e0 + u * stride < total) v[u] = __ldg(reinterpret_cast<const V*>(A + src_off[u]));
+      int kk[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t e = e0 + u * stride;
-        if (e < total) reinterpret_cast<V*>(X)[e] = scale_acc(v[u], wk[u], acc);
+        const unsigned e = e0 + u * stride;
+        const unsigned ee = e < total ? e : 0u;
+        const unsigned col = dmv.div(ee);
+        const unsigned q = ee - col * mv;
+        const unsigned k = dn.div(col), c = col - k * (unsigned)n;
+        kk[u] = (int)k;
+        if (e < total)
+          v[u] = __ldg(reinterpret_cast<const V*>(A + rep_off[k] + (int64_t)c * lda +
+                                                  (int64_t)q * VN));
       }
-    } else {
-      T v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (e0 + u * stride < total) v[u] = __ldg(A + src_off[u]);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int64_t e = e0 + u * stride;
+        const unsigned e = e0 + u * stride;
         if (e < total) {
-          const T tv = (T)((double)v[u] * wk[u]);
-          X[e] = tv;
-          acc = fma((double)tv, (double)tv, acc);
+          const float2 ws = wf[kk[u]];
+          reinterpret_cast<V*>(X)[e] = scale_acc(v[u], ws.x, ws.y, w[kk[u]], hi, lo);
         }
       }
     }
+  } else {
+    const int64_t total = (int64_t)n * p * m;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += stride) {
+      const int64_t col = e / m;
+      const int r = (int)(e - col * m);
+      const int k = (int)(col / n), c = (int)(col - (int64_t)k * n);
+      const T a = __ldg(A + rep_off[k] + (int64_t)c * lda + r);
+      T x;
+      if constexpr (std::is_same<T, float>::value) {
+        const float2 ws = wf[k];
+        x = scale_exact(a, ws.x, ws.y, w[k]);
+        ff_add_square(x, hi, lo);
+      } else {
+        x = a * w[k];
+        hi = fma(x, x, hi);
+      }
+      X[e] = x;
+    }
   }
+  double acc = (double)hi + (double)lo;
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
@@ -497,11 +560,13 @@ int gather_parts(int m, int n, int p) {
 }
 
 template <typename TS, typename T>
-cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off, const double* w, int m,
-                   int n, int p, T* X, double* partial, cudaStream_t st) {
+cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off, const double* w,
+                   const float* wf, int m, int n, int p, T* X, double* partial, cudaStream_t st) {
   const int g = gather_parts(m, n, p);
   static_assert(std::is_same<TS, T>::value, "the gather keeps the input's element type");
-  gather_vec_kernel<T, 4><<<g, GATHER_THREADS, 0, st>>>(A, lda, rep_off, w, m, n, p, X, partial);
+  gather_vec_kernel<T, 4><<<g, GATHER_THREADS, 0, st>>>(A, lda, rep_off, w,
+                                                         reinterpret_cast<const float2*>(wf), m, n,
+                                                         p, X, partial);
   return cudaGetLastError();
 }
 
@@ -799,9 +864,11 @@ template cudaError_t ml_scatter<double>(const MlMaps&, const double*, double*, i
                                         cudaStream_t);
 
 template cudaError_t gather<double, double>(const double*, int64_t, const int64_t*, const double*,
-                                            int, int, int, double*, double*, cudaStream_t);
+                                            const float*, int, int, int, double*, double*,
+                                            cudaStream_t);
 template cudaError_t gather<float, float>(const float*, int64_t, const int64_t*, const double*,
-                                          int, int, int, float*, double*, cudaStream_t);
+                                          const float*, int, int, int, float*, double*,
+                                          cudaStream_t);
 template cudaError_t build_struct_terms<float>(const int*, const double*, int, int, const float*,
                                                int64_t, int64_t, int, const int*, float*,
                                                cudaStream_t);
