@@ -233,7 +233,9 @@ typedef struct {
 
 /* Validate the problems, derive eta_k and the weights 1/sqrt(eta_k), build M
  * (DCT-II computed in fp64 on the host), allocate every device buffer the
- * compression needs.  No kernel runs.  nprob >= 1 problems share the options;
+ * compression needs, and build what depends on M and the maps alone (M's
+ * split operand planes on the mixed path, the t-SVDM's Kronecker factors
+ * C_i = struct_E(M[i, :])) on the device, synchronously.  nprob >= 1 problems share the options;
  * they are compressed together by one sma_compress call (batched launches).
  * Errors: SMA_ERR_ARG (sizes <= 0, nprob < 1, bad enum, M_user NULL),
  * SMA_ERR_STRUCT (map entry outside [-1, p) or a k that never occurs; for

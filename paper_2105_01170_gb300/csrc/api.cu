@@ -829,6 +829,12 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     SMA_TRY(mem.alloc(&P.D, mnp));
     SMA_TRY(mem.alloc(&P.C, (size_t)P.ell * P.q * p));
     SMA_CK(cudaMemset(P.C, 0, sizeof(T) * (size_t)P.ell * P.q * p));   // zero off the structure
+    // the structured Kronecker factors C_i = struct_E(M[i, :]) depend only on
+    // M and the map: built once here, not in every compression
+    ++h->launches;
+    SMA_CK(build_struct_terms_nz<T>(P.d_nzpos, P.d_nzk, P.nnz, P.d_isq, P.ell, P.q, P.Mt, 1, p, p,
+                                    nullptr, P.C, nullptr));
+    SMA_CK(cudaDeviceSynchronize());
   } else if (o.decomp == SMA_CP_ALS) {
     const int r = o.fixed_rank;
     if (r > p) return SMA_ERR_ARG;
@@ -1308,9 +1314,6 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P, bool truncated) {
     g.nb1 = p;
     SMA_K(contract<T>(h, g));
   }
-  // structured Kronecker factors C_i = struct_E(M[i, :])
-  SMA_K(build_struct_terms_nz<T>(P.d_nzpos, P.d_nzk, P.nnz, P.d_isq, P.ell, P.q, P.Mt, 1, p, p,
-                                  nullptr, P.C, st));
   stage_end(h);
   // orthogonality of the retained columns of the Jacobi W (the slice's left
   // singular vectors, or with the QR preconditioning its right ones)
