@@ -240,69 +240,6 @@ __device__ __forceinline__ void reflect_n(T* const (&x)[NC], const bool (&act)[N
   }
 }
 
-// p as a pointer derived from the shared-memory base (so that the compiler
-// emits shared loads and stores for it); p must point into shared memory
-template <typename T>
-__device__ __forceinline__ T* as_shared(T* p, unsigned char* base) {
-  return reinterpret_cast<T*>(base + (__cvta_generic_to_shared(p) - __cvta_generic_to_shared(base)));
-}
-
-// The trailing update of step k: x_j <- (I - tau v v^T) x_j for the columns
-// at positions k+1..rc-1, four (fp64: two, for registers) per warp at a time
-// (interleaved for latency),
-// then each column's partial norm downdated (n - y_k^2), or recomputed
-// exactly when the downdate has lost most of its digits.  SH: every column
-// is in shared memory.
-template <typename T, bool SH>
-__device__ __forceinline__ void update_columns(T* const* colp, unsigned char* base, T* nrm,
-                                               T* nrm0, const T* v, T tau, T nsc, int k, int mm,
-                                               int rc, int warp, int nw, int lane) {
-  constexpr int NC = sizeof(T) == 4 ? 4 : 2;
-  for (int j0 = k + 1 + warp; j0 < rc; j0 += NC * nw) {
-    T* xs[NC];
-    bool act[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int j = j0 + c * nw;
-      act[c] = j < rc;
-      T* p = colp[act[c] ? j : j0];
-      xs[c] = SH ? as_shared(p, base) : p;
-    }
-    T yk[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) yk[c] = T(0);
-    reflect_n<T, NC>(xs, act, v, tau, k, mm, lane, yk);
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (!act[c]) continue;
-      const int j = j0 + c * nw;
-      T nn = T(0);
-      int rec = 0;
-      if (lane == 0) {
-        const T y = yk[c] * nsc;
-        nn = nrm[j] - y * y;
-        rec = (nn > T(1e-3) * nrm0[j]) ? 0 : 1;
-      }
-      rec = __shfl_sync(0xffffffffu, rec, 0);
-      if (rec) {
-        __syncwarp();
-        T a = T(0);
-        for (int r = k + 1 + lane; r < mm; r += 32) {
-          const T z = xs[c][r] * nsc;
-          a = fma(z, z, a);
-        }
-        a = warp_sum(a);
-        if (lane == 0) {
-          nrm[j] = a;
-          nrm0[j] = a;
-        }
-      } else if (lane == 0) {
-        nrm[j] = nn;
-      }
-    }
-  }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -483,13 +420,44 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
       if (tid == 0) colp[pos] = dst;
       __syncthreads();
     }
-    // apply the reflector to the remaining columns and downdate their norms;
-    // once no overflow column is left the columns are addressed as shared
-    // memory (shared loads and stores instead of generic ones)
-    if (sh_nglob == 0)
-      update_columns<T, true>(colp, smem_raw, nrm, nrm0, v, tau, nsc, k, mm, rc, warp, nw, lane);
-    else
-      update_columns<T, false>(colp, smem_raw, nrm, nrm0, v, tau, nsc, k, mm, rc, warp, nw, lane);
+    // apply the reflector to the remaining columns, two per warp at a time;
+    // downdate their partial norms (n - y_k^2), recomputed exactly when the
+    // downdate has lost most of its digits
+    for (int j0 = k + 1 + warp; j0 < rc; j0 += 2 * nw) {
+      const int j1 = j0 + nw;
+      T* const xs[2] = {colp[j0], colp[j1 < rc ? j1 : j0]};
+      const bool act[2] = {true, j1 < rc};
+      T yk[2] = {T(0), T(0)};
+      reflect_n<T, 2>(xs, act, v, tau, k, mm, lane, yk);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (!act[c]) continue;
+        const int j = c ? j1 : j0;
+        T nn = T(0);
+        int rec = 0;
+        if (lane == 0) {
+          const T y = yk[c] * nsc;
+          nn = nrm[j] - y * y;
+          rec = (nn > T(1e-3) * nrm0[j]) ? 0 : 1;
+        }
+        rec = __shfl_sync(0xffffffffu, rec, 0);
+        if (rec) {
+          __syncwarp();
+          T a = T(0);
+          for (int r = k + 1 + lane; r < mm; r += 32) {
+            const T z = xs[c][r] * nsc;
+            a = fma(z, z, a);
+          }
+          a = warp_sum(a);
+          if (lane == 0) {
+            nrm[j] = a;
+            nrm0[j] = a;
+          }
+        } else if (lane == 0) {
+          nrm[j] = nn;
+        }
+      }
+    }
     __syncthreads();
   }
   // Jacobi input R1^T (rc x rc, lower triangular); the permutation
