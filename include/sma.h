@@ -31,7 +31,10 @@
  *     rotation angles; fp64 energy sums).
  *   - Pointers to A, X and Y may be device memory or host memory; host
  *     buffers are copied on the handle's stream (only the bytes the call
- *     needs).  Device memory owned by the handle is allocated in sma_create
+ *     needs), except a page-locked (pinned) host A of a one-level problem,
+ *     whose representative blocks the gather kernel reads in place over the
+ *     host link.  Either way the host input must stay unchanged until the
+ *     call's work on the stream has completed.  Device memory owned by the handle is allocated in sma_create
  *     and released in sma_destroy; no other call allocates, except sma_apply,
  *     which grows a per-handle workspace the first time it sees a larger nrhs.
  *   - All work is ordered on the stream given in sma_options (NULL = legacy

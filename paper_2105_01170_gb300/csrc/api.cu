@@ -53,6 +53,18 @@ cudaError_t& last_cuda_error() {
   return e;
 }
 
+// The device-side address of page-locked host memory the GPU can read in
+// place (registered or allocated pinned host memory), or null for pageable
+// memory, which has to be copied first.
+const void* mapped_host_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -314,6 +326,7 @@ struct Prob {
   T* Sy = nullptr;                          // apply workspace, inner product plus X'
   size_t Sy_elems = 0;
   bool compressed = false;
+  bool post_batched = false;                // rebuild and report in the bin's slice_post
   // host copies of results
   int h_iscal[8] = {0};
 };
@@ -326,6 +339,11 @@ struct SvdBin {
   JacobiPlan jp{};
   SliceDesc<T>* desc = nullptr;   // device
   T* W = nullptr;                 // block-mode workspace
+  // the slices (of problems without the QR preconditioning) whose truncated
+  // rebuild and orthogonality defect run as one launch after the truncation
+  PostDesc<T>* post = nullptr;    // device
+  int post_count = 0;
+  int pm = 0, pn = 0, pmm = 0, prc = 0, ptrans = 0;
 };
 
 }  // namespace
@@ -976,9 +994,14 @@ sma_status do_gather(sma_ctx* h, Prob<T>& P, const void* Ain, int64_t lda) {
                              is_device_ptr(Ain) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                              st));
   }
-  if (!is_device_ptr(Ain)) {
-    // host input: copy only the representative blocks to a staging buffer
-    // (the block list keeps the caller's numbering, T_0 included)
+  const void* mapped = is_device_ptr(Ain) ? nullptr : mapped_host_ptr(Ain);
+  if (mapped) {
+    // page-locked host input: the gather reads the representative blocks in
+    // place, over the host link, instead of staging them with copies
+    A = static_cast<const T*>(mapped);
+  } else if (!is_device_ptr(Ain)) {
+    // pageable host input: copy only the representative blocks to a staging
+    // buffer (the block list keeps the caller's numbering, T_0 included)
     if (!P.stage) SMA_TRY(h->mem.alloc(&P.stage, (size_t)m * n * (dense ? p : P.psrc)));
     if (dense) {
       for (int k = 0; k < p; ++k) {
@@ -2239,8 +2262,16 @@ sma_status enqueue_compress(sma_ctx* h, const void* const* A, const int64_t* lda
       SMA_TRY(tsvdm_svd(h, ps[0]));
     }
     const bool batched = h->nprob > 1 && h->tdesc;
-    if (batched) SMA_TRY(truncate_all<T>(h));
-    for (int i = 0; i < h->nprob; ++i) SMA_TRY(tsvdm_post(h, ps[i], batched));
+    if (batched) {
+      SMA_TRY(truncate_all<T>(h));
+      stage_begin(h, SMA_STAGE_FACTORS);
+      for (auto& b : bins<T>(h))
+        if (b.post_count > 0)
+          SMA_K(slice_post<T>(b.post, b.post_count, b.pm, b.pn, b.pmm, b.prc, b.ptrans, h->st));
+      stage_end(h);
+    }
+    for (int i = 0; i < h->nprob; ++i)
+      if (!ps[i].post_batched) SMA_TRY(tsvdm_post(h, ps[i], batched));
   }
   return SMA_OK;
 }
@@ -2961,8 +2992,37 @@ sma_status build_bins(sma_ctx* h) {
       host[bi].push_back(SliceDesc<T>{jsrc + k * jmn, P.U + k * urc, P.V + k * vrc,
                                       P.sigma + (int64_t)k * P.rc, P.sweeps + k, P.status});
   }
+  // the per-slice rebuild and report of the problems without QR, batched by
+  // bin when a slice's W and V fit in shared memory
+  std::vector<std::vector<PostDesc<T>>> post(bs.size());
+  for (auto& P : ps) {
+    if (P.qr || ps.size() < 2) continue;
+    const size_t smem = sizeof(T) * ((size_t)P.jp.mm * P.rc + (size_t)P.rc * P.rc);
+    if (smem > (size_t)h->max_smem) continue;
+    size_t bi = 0;
+    for (; bi < bs.size(); ++bi)
+      if (bs[bi].m == P.m && bs[bi].n == P.n) break;
+    if (bi == bs.size()) continue;
+    auto& b = bs[bi];
+    if (!post[bi].empty() &&
+        (b.pm != P.m || b.pn != P.n || b.pmm != P.jp.mm || b.prc != P.rc || b.ptrans != P.trans))
+      continue;
+    b.pm = P.m; b.pn = P.n; b.pmm = P.jp.mm; b.prc = P.rc; b.ptrans = P.trans;
+    const int64_t mn = (int64_t)P.m * P.n, urc = (int64_t)P.jp.mm * P.rc,
+                  vrc = (int64_t)P.rc * P.rc;
+    for (int k = 0; k < P.p; ++k)
+      post[bi].push_back(PostDesc<T>{P.Xh + k * mn, P.D + k * mn, P.U + k * urc, P.V + k * vrc,
+                                     P.sigma + (int64_t)k * P.rc, P.ranks + k, P.orth + k});
+    P.post_batched = true;
+  }
   for (size_t bi = 0; bi < bs.size(); ++bi) {
     auto& b = bs[bi];
+    if (!post[bi].empty()) {
+      b.post_count = (int)post[bi].size();
+      SMA_TRY(h->mem.alloc(&b.post, post[bi].size()));
+      SMA_CK(cudaMemcpy(b.post, post[bi].data(), post[bi].size() * sizeof(PostDesc<T>),
+                        cudaMemcpyHostToDevice));
+    }
     b.count = (int)host[bi].size();
     SMA_TRY(h->mem.alloc(&b.desc, host[bi].size()));
     SMA_CK(cudaMemcpy(b.desc, host[bi].data(), host[bi].size() * sizeof(SliceDesc<T>),

@@ -156,6 +156,24 @@ struct TruncDesc {
   int* iscal;
   double* suf;
 };
+// The t-SVDM's per-slice work after the truncation, for a batch of slices of
+// one shape from many problems (one launch): the truncated slice
+// D = Xhat - W_d V_d^T (d the columns from the slice's retained rank on;
+// trans: D = Xhat - V_d W_d^T) and the orthogonality defect max |U_r^T U_r -
+// I| of its retained left factor U = W Sigma^-1.
+template <typename T>
+struct PostDesc {
+  const T* Xh;          // m x n slice (ld m)
+  T* D;                 // m x n out
+  const T* W;           // mm x rc, ld mm (the Jacobi W = U Sigma, sorted)
+  const T* V;           // rc x rc, ld rc
+  const double* sigma;  // rc, descending
+  const int* rank;      // the slice's retained rank
+  double* orth;         // out
+};
+template <typename T>
+cudaError_t slice_post(const PostDesc<T>* d, int count, int m, int n, int mm, int rc, int trans,
+                       cudaStream_t st);
 cudaError_t truncate_ranks_batched(const TruncDesc* d, int nprob, double rel_tol, int fixed_rank,
                                    cudaStream_t st);
 cudaError_t truncate_ranks(const double* sigma, int rc, int p, const double* normX2,

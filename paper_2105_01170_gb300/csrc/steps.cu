@@ -813,6 +813,76 @@ cudaError_t orth_defect(const T* Gm, int rc, int p, const int* ranks, const doub
   return cudaGetLastError();
 }
 
+namespace {
+// One CTA per slice.  W's and V's discarded columns (and W's retained ones,
+// for the defect) are staged in shared memory when they fit; the rebuild
+// reads Xhat and writes D once, column by column.
+template <typename T>
+__global__ void __launch_bounds__(256)
+slice_post_kernel(const PostDesc<T>* __restrict__ desc, int m, int n, int mm, int rc, int trans) {
+  extern __shared__ __align__(16) unsigned char post_raw[];
+  T* Ws = reinterpret_cast<T*>(post_raw);     // mm x rc
+  T* Vs = Ws + (size_t)mm * rc;                // rc x rc
+  __shared__ double red[32];
+  const PostDesc<T> d = desc[blockIdx.x];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int r = min(max(*d.rank, 0), rc);
+  for (int e = tid; e < mm * rc; e += nth) Ws[e] = d.W[e];
+  for (int e = tid; e < rc * rc; e += nth) Vs[e] = d.V[e];
+  __syncthreads();
+  // D = Xhat - sum_{j >= r} (left_j)(right_j)^T; left = W (trans: V), right = V (W)
+  const T* Lf = trans ? Vs : Ws;
+  const T* Rf = trans ? Ws : Vs;
+  const int ldl = trans ? rc : mm, ldr = trans ? mm : rc;
+  for (int e = tid; e < m * n; e += nth) {
+    const int i = e % m, c = e / m;
+    T acc = d.Xh[e];
+    for (int j = r; j < rc; ++j) acc = fma(-Lf[i + (int64_t)ldl * j], Rf[c + (int64_t)ldr * j], acc);
+    d.D[e] = acc;
+  }
+  // max |w_a . w_b / (sigma_a sigma_b) - delta_ab| over a <= b < r
+  double mx = 0.0;
+  for (int e = tid; e < r * r; e += nth) {
+    const int a = e % r, b = e / r;
+    if (a > b) continue;
+    const double sa = d.sigma[a], sb = d.sigma[b];
+    double g;
+    if (sa > 0.0 && sb > 0.0) {
+      T dot = T(0);
+      for (int i = 0; i < mm; ++i) dot = fma(Ws[i + (int64_t)mm * a], Ws[i + (int64_t)mm * b], dot);
+      g = (double)dot / (sa * sb);
+    } else {
+      g = a == b ? 1.0 : 0.0;
+    }
+    mx = fmax(mx, fabs(g - (a == b ? 1.0 : 0.0)));
+  }
+  mx = warp_max(mx);
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid < 32) {
+    double t = tid < (nth >> 5) ? red[tid] : 0.0;
+    t = warp_max(t);
+    if (tid == 0) *d.orth = t;
+  }
+}
+}  // namespace
+
+template <typename T>
+cudaError_t slice_post(const PostDesc<T>* d, int count, int m, int n, int mm, int rc, int trans,
+                       cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = sizeof(T) * ((size_t)mm * rc + (size_t)rc * rc);
+  cudaError_t e = cudaFuncSetAttribute(slice_post_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  slice_post_kernel<T><<<count, 256, smem, st>>>(d, m, n, mm, rc, trans);
+  return cudaGetLastError();
+}
+template cudaError_t slice_post<float>(const PostDesc<float>*, int, int, int, int, int, int,
+                                       cudaStream_t);
+template cudaError_t slice_post<double>(const PostDesc<double>*, int, int, int, int, int, int,
+                                        cudaStream_t);
+
 cudaError_t permute3(const double* src, int64_t s0, int64_t s1, int64_t s2, int n0, int n1, int n2,
                      double* dst, cudaStream_t st) {
   const int64_t work = (int64_t)n0 * n1 * n2;
