@@ -370,6 +370,10 @@ struct sma_ctx {
   int* coop_abort = nullptr;
   // CUDA graph of sma_compress (options.graph)
   std::vector<const void*> warm_ptrs, graph_ptrs;
+  // the batched gather's descriptors (host copy as last uploaded, device)
+  std::vector<GatherDesc> gdesc_host;
+  GatherDesc* gdesc_dev = nullptr;
+  int gdesc_parts = 0;
   std::vector<int64_t> warm_lda, graph_lda;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_launches = 0;
@@ -976,6 +980,74 @@ sma_status contract_split_k(sma_ctx* h, GemmParams<T> g, T* part, size_t part_el
 // ---------------------------------------------------------------------------
 // step 1 (gather) shared by all decompositions
 // ---------------------------------------------------------------------------
+// Element offsets of the representative blocks in the input (dense layout,
+// or the caller's block list), uploaded when the leading dimension or the
+// layout changes.
+template <typename T>
+sma_status rep_offsets(sma_ctx* h, Prob<T>& P, int64_t use_lda, int layout, bool dense) {
+  if (P.rep_lda == use_lda && P.rep_layout == layout) return SMA_OK;
+  const int m = P.m, n = P.n, p = P.p;
+  std::vector<int64_t> off(p);
+  for (int k = 0; k < p; ++k) {
+    // a caller's block list (not a staged copy of a dense input) also holds T_0
+    const int ks = k + (P.spd && !dense && k >= P.k0 ? 1 : 0);
+    off[k] = layout == 0 ? (int64_t)P.rep_a[k] * m + (int64_t)P.rep_b[k] * n * use_lda
+                         : (int64_t)ks * n * use_lda;
+  }
+  SMA_CK(cudaMemcpyAsync(P.d_rep, off.data(), p * sizeof(int64_t), cudaMemcpyHostToDevice, h->st));
+  SMA_CK(cudaStreamSynchronize(h->st));  // off[] is a stack buffer
+  P.rep_lda = use_lda;
+  P.rep_layout = layout;
+  return SMA_OK;
+}
+
+// The gathers of every problem of the handle in one launch (several one-
+// level problems with device inputs and no SPD split); false when the
+// batched form does not apply and each problem gathers on its own.
+template <typename T>
+sma_status gather_all(sma_ctx* h, const void* const* A, const int64_t* lda, bool* done) {
+  *done = false;
+  auto& ps = probs<T>(h);
+  if (ps.size() < 2) return SMA_OK;
+  const bool dense = h->opt.layout == SMA_INPUT_DENSE;
+  for (int i = 0; i < h->nprob; ++i) {
+    const auto& P = ps[i];
+    const int64_t need_rows = dense ? (int64_t)P.ell * P.m : P.m;
+    if (P.L == 3 || P.spd || !A[i] || lda[i] < need_rows || !is_device_ptr(A[i])) return SMA_OK;
+  }
+  std::vector<GatherDesc> gd(h->nprob);
+  int parts = 0;
+  for (int i = 0; i < h->nprob; ++i) {
+    auto& P = ps[i];
+    SMA_TRY(rep_offsets(h, P, lda[i], dense ? 0 : 1, dense));
+    gd[i] = GatherDesc{A[i], lda[i], P.d_rep, P.d_w, P.d_wf, P.m, P.n, P.p, P.X, P.partial,
+                       P.stats, parts, P.nparts};
+    parts += P.nparts;
+  }
+  auto eq = [](const GatherDesc& a, const GatherDesc& b) {
+    return a.A == b.A && a.lda == b.lda && a.rep_off == b.rep_off && a.w == b.w && a.wf == b.wf &&
+           a.m == b.m && a.n == b.n && a.p == b.p && a.X == b.X && a.partial == b.partial &&
+           a.norm2 == b.norm2 && a.part0 == b.part0 && a.nparts == b.nparts;
+  };
+  bool same = gd.size() == h->gdesc_host.size();
+  for (size_t i = 0; same && i < gd.size(); ++i) same = eq(gd[i], h->gdesc_host[i]);
+  if (!same) {
+    if (h->capturing) return SMA_OK;   // new descriptors are uploaded outside a capture only
+    if (!h->gdesc_dev) SMA_TRY(h->mem.alloc(&h->gdesc_dev, (size_t)h->nprob));
+    h->gdesc_host = gd;
+    SMA_CK(cudaMemcpyAsync(h->gdesc_dev, h->gdesc_host.data(), gd.size() * sizeof(GatherDesc),
+                           cudaMemcpyHostToDevice, h->st));
+    SMA_CK(cudaStreamSynchronize(h->st));
+    h->gdesc_parts = parts;
+  }
+  stage_begin(h, SMA_STAGE_GATHER);
+  h->launches += 1;   // the norm launch (SMA_K counts the gather)
+  SMA_K(gather_batched<T>(h->gdesc_dev, h->nprob, h->gdesc_parts, h->st));
+  stage_end(h);
+  *done = true;
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status do_gather(sma_ctx* h, Prob<T>& P, const void* Ain, int64_t lda) {
   cudaStream_t st = h->st;
@@ -1017,19 +1089,7 @@ sma_status do_gather(sma_ctx* h, Prob<T>& P, const void* Ain, int64_t lda) {
     use_lda = m;
     layout = 1;
   }
-  if (P.rep_lda != use_lda || P.rep_layout != layout) {
-    std::vector<int64_t> off(p);
-    for (int k = 0; k < p; ++k) {
-      // a caller's block list (not a staged copy of a dense input) also holds T_0
-      const int ks = k + (P.spd && !dense && k >= P.k0 ? 1 : 0);
-      off[k] = layout == 0 ? (int64_t)P.rep_a[k] * m + (int64_t)P.rep_b[k] * n * use_lda
-                           : (int64_t)ks * n * use_lda;
-    }
-    SMA_CK(cudaMemcpyAsync(P.d_rep, off.data(), p * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-    SMA_CK(cudaStreamSynchronize(st));  // off[] is a stack buffer
-    P.rep_lda = use_lda;
-    P.rep_layout = layout;
-  }
+  SMA_TRY(rep_offsets(h, P, use_lda, layout, dense));
   SMA_K(gather<T, T>(A, use_lda, P.d_rep, P.d_w, P.d_wf, m, n, p, P.X, P.partial, st));
   SMA_K(finish_norm(P.partial, P.nparts, P.stats, st));
   stage_end(h);
@@ -2101,7 +2161,8 @@ sma_status compress_cp(sma_ctx* h, Prob<T>& P) {
 }
 
 template <typename T>
-sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
+sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda,
+                        bool gathered = false) {
   SMA_CK(cudaMemsetAsync(P.status, 0, sizeof(int), h->st));
   if (P.L == 3) {
     SMA_TRY(compress_multilevel(h, P, A));
@@ -2111,7 +2172,7 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda) {
     P.h_iscal[0] = -1;
     return SMA_OK;
   }
-  SMA_TRY(do_gather(h, P, A, lda));
+  if (!gathered) SMA_TRY(do_gather(h, P, A, lda));
   if (P.spd) SMA_TRY(spd_congruence(h, P));
   if (h->opt.decomp == SMA_TSVDM) SMA_TRY(tsvdm_pre(h, P));
   else if (P.ml2) SMA_TRY(compress_ml2(h, P));
@@ -2254,7 +2315,9 @@ sma_status read_result(sma_ctx* h, Prob<T>& P, sma_result* r) {
 template <typename T>
 sma_status enqueue_compress(sma_ctx* h, const void* const* A, const int64_t* lda) {
   auto& ps = probs<T>(h);
-  for (int i = 0; i < h->nprob; ++i) SMA_TRY(compress_one(h, ps[i], A[i], lda[i]));
+  bool gathered = false;
+  if (h->opt.decomp == SMA_TSVDM) SMA_TRY(gather_all<T>(h, A, lda, &gathered));
+  for (int i = 0; i < h->nprob; ++i) SMA_TRY(compress_one(h, ps[i], A[i], lda[i], gathered));
   if (h->opt.decomp == SMA_TSVDM) {
     if (h->nprob > 1) {
       SMA_TRY(tsvdm_svd_batched<T>(h));

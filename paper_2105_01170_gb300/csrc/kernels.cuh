@@ -16,6 +16,24 @@ template <typename TS, typename T>
 cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off /*device, p*/,
                    const double* w /*device, p*/, const float* wf /*device, 2p*/, int m, int n,
                    int p, T* X, double* partial /*device, >= 1024*/, cudaStream_t st);
+// The gathers of many problems (device inputs) in one launch, then each
+// problem's ||X||^2 (a second launch, one CTA per problem).  part0: the
+// first of the problem's nparts CTAs (ascending over the descriptors; the
+// launch has the sum of nparts CTAs).
+struct GatherDesc {
+  const void* A;
+  int64_t lda;
+  const int64_t* rep_off;
+  const double* w;
+  const float* wf;
+  int m, n, p;
+  void* X;
+  double* partial;
+  double* norm2;
+  int part0, nparts;
+};
+template <typename T>
+cudaError_t gather_batched(const GatherDesc* d, int nprob, int total_parts, cudaStream_t st);
 // ||X||_F^2 from the per-CTA partial sums written by gather.
 cudaError_t finish_norm(const double* partial, int nparts, double* out, cudaStream_t st);
 // out[e] = sum_s part[e + s count] for e < count, s < nslab (fixed order: the

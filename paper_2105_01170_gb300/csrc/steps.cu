@@ -97,10 +97,12 @@ struct Div32 {
 // float-float pair, so the loop runs on the fp32 pipe; the per-CTA partial
 // sums are fp64.
 template <typename T, int U>
-__global__ void __launch_bounds__(GATHER_THREADS)
-gather_vec_kernel(const T* __restrict__ A, int64_t lda, const int64_t* __restrict__ rep_off,
-                  const double* __restrict__ w, const float2* __restrict__ wf, int m, int n,
-                  int p, T* __restrict__ X, double* __restrict__ partial) {
+__device__ __forceinline__ void gather_body(const T* __restrict__ A, int64_t lda,
+                                            const int64_t* __restrict__ rep_off,
+                                            const double* __restrict__ w,
+                                            const float2* __restrict__ wf, int m, int n, int p,
+                                            T* __restrict__ X, double* __restrict__ partial,
+                                            unsigned bid, unsigned nblk) {
   using V = typename Vec16<T>::type;
   constexpr int VN = Vec16<T>::n;
   using Acc = typename std::conditional<std::is_same<T, float>::value, float, double>::type;
@@ -113,8 +115,8 @@ gather_vec_kernel(const T* __restrict__ A, int64_t lda, const int64_t* __restric
   if (vec_ok) {
     const unsigned mv = (unsigned)(m / VN), total = (unsigned)total_v;
     const Div32 dmv(mv), dn((unsigned)n);
-    const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned e0 = blockIdx.x * blockDim.x + threadIdx.x; e0 < total; e0 += stride * U) {
+    const unsigned stride = nblk * blockDim.x;
+    for (unsigned e0 = bid * blockDim.x + threadIdx.x; e0 < total; e0 += stride * U) {
       V v[U];
       int kk[U];
 #pragma unroll
@@ -140,8 +142,8 @@ gather_vec_kernel(const T* __restrict__ A, int64_t lda, const int64_t* __restric
     }
   } else {
     const int64_t total = (int64_t)n * p * m;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int64_t stride = (int64_t)nblk * blockDim.x;
+    for (int64_t e = bid * (int64_t)blockDim.x + threadIdx.x; e < total; e += stride) {
       const int64_t col = e / m;
       const int r = (int)(e - col * m);
       const int k = (int)(col / n), c = (int)(col - (int64_t)k * n);
@@ -160,7 +162,43 @@ gather_vec_kernel(const T* __restrict__ A, int64_t lda, const int64_t* __restric
   }
   double acc = (double)hi + (double)lo;
   acc = block_sum(acc, red);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  if (threadIdx.x == 0) partial[bid] = acc;
+}
+
+template <typename T, int U>
+__global__ void __launch_bounds__(GATHER_THREADS)
+gather_vec_kernel(const T* __restrict__ A, int64_t lda, const int64_t* __restrict__ rep_off,
+                  const double* __restrict__ w, const float2* __restrict__ wf, int m, int n,
+                  int p, T* __restrict__ X, double* __restrict__ partial) {
+  gather_body<T, U>(A, lda, rep_off, w, wf, m, n, p, X, partial, blockIdx.x, gridDim.x);
+}
+
+// The gathers of many problems in one launch: CTA b works for the problem
+// whose CTA range [part0, part0 + nparts) holds it (a binary search over the
+// descriptors' part0, which ascend).
+template <typename T, int U>
+__global__ void __launch_bounds__(GATHER_THREADS)
+gather_batched_kernel(const GatherDesc* __restrict__ d, int nprob) {
+  int lo = 0, hi = nprob - 1;
+  const int b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (d[mid].part0 <= b) lo = mid; else hi = mid - 1;
+  }
+  const GatherDesc g = d[lo];
+  gather_body<T, U>(static_cast<const T*>(g.A), g.lda, g.rep_off, g.w,
+                    reinterpret_cast<const float2*>(g.wf), g.m, g.n, g.p, static_cast<T*>(g.X),
+                    g.partial, (unsigned)(b - g.part0), (unsigned)g.nparts);
+}
+
+// ||X_i||^2 of each problem from its partial sums (one CTA per problem).
+__global__ void finish_norm_batched_kernel(const GatherDesc* __restrict__ d) {
+  __shared__ double red[32];
+  const GatherDesc g = d[blockIdx.x];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < g.nparts; i += blockDim.x) acc += g.partial[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) *g.norm2 = acc;
 }
 
 // per-CTA fp64 sums of (X - T)^2
@@ -571,6 +609,18 @@ cudaError_t gather(const TS* A, int64_t lda, const int64_t* rep_off, const doubl
 }
 
 template <typename T>
+cudaError_t gather_batched(const GatherDesc* d, int nprob, int total_parts, cudaStream_t st) {
+  if (nprob <= 0) return cudaSuccess;
+  gather_batched_kernel<T, 4><<<total_parts, GATHER_THREADS, 0, st>>>(d, nprob);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  finish_norm_batched_kernel<<<nprob, 256, 0, st>>>(d);
+  return cudaGetLastError();
+}
+template cudaError_t gather_batched<float>(const GatherDesc*, int, int, cudaStream_t);
+template cudaError_t gather_batched<double>(const GatherDesc*, int, int, cudaStream_t);
+
+template <typename T>
 cudaError_t residual_norm2(const T* X, const T* Tt, int64_t count, double* partial, int nparts,
                            double* out, cudaStream_t st) {
   residual_kernel<T><<<nparts, GATHER_THREADS, 0, st>>>(X, Tt, count, partial);
@@ -840,21 +890,43 @@ slice_post_kernel(const PostDesc<T>* __restrict__ desc, int m, int n, int mm, in
     for (int j = r; j < rc; ++j) acc = fma(-Lf[i + (int64_t)ldl * j], Rf[c + (int64_t)ldr * j], acc);
     d.D[e] = acc;
   }
-  // max |w_a . w_b / (sigma_a sigma_b) - delta_ab| over a <= b < r
+  // max |w_a . w_b / (sigma_a sigma_b) - delta_ab| over a <= b < r, by 4 x 4
+  // tiles of the Gram (each thread one tile pair at a time: 8 shared loads
+  // per 16 products)
   double mx = 0.0;
-  for (int e = tid; e < r * r; e += nth) {
-    const int a = e % r, b = e / r;
-    if (a > b) continue;
-    const double sa = d.sigma[a], sb = d.sigma[b];
-    double g;
-    if (sa > 0.0 && sb > 0.0) {
-      T dot = T(0);
-      for (int i = 0; i < mm; ++i) dot = fma(Ws[i + (int64_t)mm * a], Ws[i + (int64_t)mm * b], dot);
-      g = (double)dot / (sa * sb);
-    } else {
-      g = a == b ? 1.0 : 0.0;
+  const int nt = (r + 3) >> 2;
+  for (int e = tid; e < nt * nt; e += nth) {
+    const int ta = e % nt, tb = e / nt;
+    if (ta > tb) continue;
+    T g[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) g[u][v] = T(0);
+    const int a0 = 4 * ta, b0 = 4 * tb;
+    for (int i = 0; i < mm; ++i) {
+      T wa[4], wb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        wa[u] = a0 + u < r ? Ws[i + (int64_t)mm * (a0 + u)] : T(0);
+        wb[u] = b0 + u < r ? Ws[i + (int64_t)mm * (b0 + u)] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) g[u][v] = fma(wa[u], wb[v], g[u][v]);
     }
-    mx = fmax(mx, fabs(g - (a == b ? 1.0 : 0.0)));
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int a = a0 + u, b = b0 + v;
+        if (a >= r || b >= r || a > b) continue;
+        const double sa = d.sigma[a], sb = d.sigma[b];
+        const double gn = (sa > 0.0 && sb > 0.0) ? (double)g[u][v] / (sa * sb)
+                                                 : (a == b ? 1.0 : 0.0);
+        mx = fmax(mx, fabs(gn - (a == b ? 1.0 : 0.0)));
+      }
   }
   mx = warp_max(mx);
   if ((tid & 31) == 0) red[tid >> 5] = mx;
@@ -875,7 +947,10 @@ cudaError_t slice_post(const PostDesc<T>* d, int count, int m, int n, int mm, in
   cudaError_t e = cudaFuncSetAttribute(slice_post_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  slice_post_kernel<T><<<count, 256, smem, st>>>(d, m, n, mm, rc, trans);
+  // about eight slice elements per thread: small slices take small CTAs
+  int threads = 32;
+  while (threads < 256 && threads * 8 < m * n) threads <<= 1;
+  slice_post_kernel<T><<<count, threads, smem, st>>>(d, m, n, mm, rc, trans);
   return cudaGetLastError();
 }
 template cudaError_t slice_post<float>(const PostDesc<float>*, int, int, int, int, int, int,
