@@ -370,6 +370,9 @@ struct sma_ctx {
   int* coop_abort = nullptr;
   // CUDA graph of sma_compress (options.graph)
   std::vector<const void*> warm_ptrs, graph_ptrs;
+  // the problems' device status words, contiguous
+  int* status_pool = nullptr;
+  int status_used = 0;
   // the batched gather's descriptors (host copy as last uploaded, device)
   std::vector<GatherDesc> gdesc_host;
   GatherDesc* gdesc_dev = nullptr;
@@ -664,7 +667,7 @@ sma_status setup_multilevel(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   SMA_TRY(mem.alloc(&P.partial, P.nparts));
   SMA_TRY(mem.alloc(&P.stats, 8));
   SMA_TRY(mem.alloc(&P.iscal, 8));
-  SMA_TRY(mem.alloc(&P.status, 1));
+  P.status = h->status_pool + h->status_used++;   // one pool: one clear per compression
   SMA_TRY(mem.alloc(&P.gram, P.gstride * 3));
   SMA_TRY(mem.alloc(&P.gvec, P.gstride * 3));
   SMA_TRY(mem.alloc(&P.gsig, (size_t)gdim * 3));
@@ -774,7 +777,7 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
   SMA_TRY(mem.alloc(&P.partial, P.nparts));
   SMA_TRY(mem.alloc(&P.stats, 8));
   SMA_TRY(mem.alloc(&P.iscal, 8));
-  SMA_TRY(mem.alloc(&P.status, 1));
+  P.status = h->status_pool + h->status_used++;   // one pool: one clear per compression
   SMA_TRY(mem.alloc(&P.Tt, mnp));
   SMA_CK(cudaMemset(P.stats, 0, 8 * sizeof(double)));
   SMA_CK(cudaMemset(P.iscal, 0, 8 * sizeof(int)));
@@ -2163,7 +2166,6 @@ sma_status compress_cp(sma_ctx* h, Prob<T>& P) {
 template <typename T>
 sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda,
                         bool gathered = false) {
-  SMA_CK(cudaMemsetAsync(P.status, 0, sizeof(int), h->st));
   if (P.L == 3) {
     SMA_TRY(compress_multilevel(h, P, A));
     P.compressed = true;
@@ -2315,6 +2317,7 @@ sma_status read_result(sma_ctx* h, Prob<T>& P, sma_result* r) {
 template <typename T>
 sma_status enqueue_compress(sma_ctx* h, const void* const* A, const int64_t* lda) {
   auto& ps = probs<T>(h);
+  SMA_CK(cudaMemsetAsync(h->status_pool, 0, sizeof(int) * (size_t)h->nprob, h->st));
   bool gathered = false;
   if (h->opt.decomp == SMA_TSVDM) SMA_TRY(gather_all<T>(h, A, lda, &gathered));
   for (int i = 0; i < h->nprob; ++i) SMA_TRY(compress_one(h, ps[i], A[i], lda[i], gathered));
@@ -3206,6 +3209,7 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
   SMA_CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
   h->tc_ok = (opt->prec == SMA_MIXED) && tc_gemm_available(major, minor);
   SMA_CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+  SMA_TRY(h->mem.alloc(&h->status_pool, (size_t)nprob));
   if (opt->prec == SMA_FP64) {
     h->p64.resize(nprob);
     for (int i = 0; i < nprob; ++i) SMA_TRY(setup_problem(h.get(), h->p64[i], prob[i]));
