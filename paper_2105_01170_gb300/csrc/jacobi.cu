@@ -28,6 +28,7 @@
 //   zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 //   c = 1/sqrt(1+t^2), s = c t, w_a' = c w_a - s w_b, w_b' = s w_a + c w_b,
 // applied when |gamma| > tol sqrt(alpha beta); the caller sets tol (4 sqrt(mm) eps(T)).
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -609,6 +610,194 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
   return true;
 }
 
+// ---- register-tiled sweeps on part of a warp (short columns) ---------------
+// When the dot-product part has at most 4 GW rows (GW = 16, 8 or 4), a task
+// needs only GW lanes: lane gl of a group keeps float4 row gl of each of the
+// task's 8 columns, and the warp runs 32 / GW tasks side by side, one per
+// group of GW lanes.  The tasks of one warp are independent (disjoint tiles
+// of the same round), so they share every instruction: reductions are
+// shuffles within the group, every branch is taken on the warp-wide OR of
+// the groups' conditions, and a group with nothing to do in a sub-round (or
+// no task at all, live == false) applies exact identities (t = 0, c = 1).
+// The rotations, their order and their arithmetic are those of tile_group.
+
+// Sum of 4 values over a group of GW lanes (GW >= 4): lane gl ends with the
+// group sum of value 2 [gl & GW/2] + [gl & GW/4].
+template <int GW>
+__device__ __forceinline__ float reduce4_group(const float (&v)[4], int gl) {
+  const bool h4 = gl & (GW / 2), h3 = gl & (GW / 4);
+  float u2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float send = h4 ? v[i] : v[i + 2];
+    const float keep = h4 ? v[i + 2] : v[i];
+    u2[i] = keep + __shfl_xor_sync(0xffffffffu, send, GW / 2);
+  }
+  const float send = h3 ? u2[0] : u2[1];
+  const float keep = h3 ? u2[1] : u2[0];
+  float u = keep + __shfl_xor_sync(0xffffffffu, send, GW / 4);
+#pragma unroll
+  for (int o = GW / 8; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+  return u;
+}
+
+template <int GW, bool INNER>
+__device__ __forceinline__ bool tile_group_part(float* S, int ldS, int sa, int na, int sb, int nb,
+                                                bool doA, bool doB, int mq, int rq, int gl,
+                                                int grp, bool live, float tol, float floor_,
+                                                float4* csw) {
+  constexpr int NR = INNER ? 3 : 4;
+  if (!live) na = nb = 0;
+  float4 x[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const bool valid = c < 4 ? c < na : (c - 4) < nb;
+    const int slot = c < 4 ? sa + c : sb + c - 4;
+    const float4* col = reinterpret_cast<const float4*>(S + (int64_t)(valid ? slot : 0) * ldS);
+    x[c] = (valid && gl < mq) ? col[gl] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  // squared norms of the 8 columns, in every lane of the group
+  float nrm8[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float a = dot4(x[c], x[c], 0.f);
+#pragma unroll
+    for (int o = GW / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    nrm8[c] = a;
+  }
+  float d[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) d[c] = 1.f;
+  unsigned mk[NR];
+  unsigned anyg = 0, anyw = 0;
+  const int gbase = grp * GW;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    float g4[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int a, b;
+      tile_pair<INNER>(r, q, a, b);
+      g4[q] = dot4(x[a], x[b], 0.f);
+    }
+    const float gr = reduce4_group<GW>(g4, gl);
+    // lanes 0..3 of the group: the angle of pair q = gl (the others repeat them)
+    const int q = gl & 3;
+    const float gq = __shfl_sync(0xffffffffu, gr, (q >> 1) * (GW / 2) + (q & 1) * (GW / 4), GW);
+    float al = 0.f, be = 0.f, dd = 1.f;
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      int a, b;
+      tile_pair<INNER>(r, qq, a, b);
+      if (q == qq) {
+        al = nrm8[a];
+        be = nrm8[b];
+        dd = d[a] * d[b];
+      }
+    }
+    const float ga = gq * dd;
+    const bool allowed = live && (INNER ? (q < 2 ? doA : doB) : true);
+    float c = 1.f, t = 0.f;
+    const bool ok = allowed && Angle<float>::get_ct(al, be, ga, tol, floor_, c, t);
+    if (!ok) {
+      c = 1.f;
+      t = 0.f;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, ok && gl < 4);
+    const unsigned m = (bal >> gbase) & 0xfu;
+    mk[r] = m;
+    anyg |= m;
+    anyw |= bal;
+    if (bal == 0u) continue;   // warp-uniform
+    float cq[4], tq[4], gt[4], t1[4], t2[4];
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      cq[qq] = __shfl_sync(0xffffffffu, c, qq, GW);
+      tq[qq] = __shfl_sync(0xffffffffu, t, qq, GW);
+      gt[qq] = __shfl_sync(0xffffffffu, ga, qq, GW);
+    }
+#pragma unroll
+    for (int qq = 0; qq < 4; ++qq) {
+      int a, b;
+      tile_pair<INNER>(r, qq, a, b);
+      t1[qq] = __fdividef(tq[qq] * d[b], d[a]);
+      t2[qq] = __fdividef(tq[qq] * d[a], d[b]);
+      const float4 xa = x[a], xb = x[b];
+      x[a] = make_float4(fmaf(-t1[qq], xb.x, xa.x), fmaf(-t1[qq], xb.y, xa.y),
+                         fmaf(-t1[qq], xb.z, xa.z), fmaf(-t1[qq], xb.w, xa.w));
+      x[b] = make_float4(fmaf(t2[qq], xa.x, xb.x), fmaf(t2[qq], xa.y, xb.y),
+                         fmaf(t2[qq], xa.z, xb.z), fmaf(t2[qq], xa.w, xb.w));
+      d[a] *= cq[qq];
+      d[b] *= cq[qq];
+      nrm8[a] = fmaf(-tq[qq], gt[qq], nrm8[a]);
+      nrm8[b] = fmaf(tq[qq], gt[qq], nrm8[b]);
+    }
+    if (gl == 0) {
+      csw[2 * r] = make_float4(t1[0], t2[0], t1[1], t2[1]);
+      csw[2 * r + 1] = make_float4(t1[2], t2[2], t1[3], t2[3]);
+    }
+  }
+  if (anyw == 0u) return false;   // warp-uniform
+  if (anyg) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const bool valid = c < 4 ? c < na : (c - 4) < nb;
+      if (!valid) continue;
+      float4* col = reinterpret_cast<float4*>(S + (int64_t)(c < 4 ? sa + c : sb + c - 4) * ldS);
+      const float dc = d[c];
+      const float4 v = x[c];
+      if (gl < mq) col[gl] = make_float4(dc * v.x, dc * v.y, dc * v.z, dc * v.w);
+    }
+    if (gl == 0) {
+      csw[2 * NR] = make_float4(d[0], d[1], d[2], d[3]);
+      csw[2 * NR + 1] = make_float4(d[4], d[5], d[6], d[7]);
+    }
+  }
+  __syncwarp();
+  if (anyg) {
+    const float4 d03 = csw[2 * NR], d47 = csw[2 * NR + 1];
+    for (int qq = gl; qq < rq; qq += GW) {
+      float4 y[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const bool valid = c < 4 ? c < na : (c - 4) < nb;
+        const float4* col =
+            reinterpret_cast<const float4*>(S + (int64_t)(c < 4 ? sa + c : sb + c - 4) * ldS);
+        y[c] = valid ? col[mq + qq] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        if (mk[r] == 0u) continue;
+        const float4 r01 = csw[2 * r], r23 = csw[2 * r + 1];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int a, b;
+          tile_pair<INNER>(r, q, a, b);
+          const float ta = q == 0 ? r01.x : q == 1 ? r01.z : q == 2 ? r23.x : r23.z;
+          const float tb = q == 0 ? r01.y : q == 1 ? r01.w : q == 2 ? r23.y : r23.w;
+          const float4 ya = y[a], yb = y[b];
+          y[a] = make_float4(fmaf(-ta, yb.x, ya.x), fmaf(-ta, yb.y, ya.y), fmaf(-ta, yb.z, ya.z),
+                             fmaf(-ta, yb.w, ya.w));
+          y[b] = make_float4(fmaf(tb, ya.x, yb.x), fmaf(tb, ya.y, yb.y), fmaf(tb, ya.z, yb.z),
+                             fmaf(tb, ya.w, yb.w));
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const bool valid = c < 4 ? c < na : (c - 4) < nb;
+        if (!valid) continue;
+        float4* col = reinterpret_cast<float4*>(S + (int64_t)(c < 4 ? sa + c : sb + c - 4) * ldS);
+        const float dc = c == 0 ? d03.x : c == 1 ? d03.y : c == 2 ? d03.z : c == 3 ? d03.w
+                       : c == 4 ? d47.x : c == 5 ? d47.y : c == 6 ? d47.z : d47.w;
+        const float4 v = y[c];
+        col[mq + qq] = make_float4(dc * v.x, dc * v.y, dc * v.z, dc * v.w);
+      }
+    }
+  }
+  __syncwarp();   // the record is rewritten by the group's next task
+  return anyg != 0u;
+}
+
 // columns of tile t of a block of ncols columns (0 when t is past the end)
 __device__ __forceinline__ int tile_cols(int t, int ncols) {
   const int r = ncols - 4 * t;
@@ -819,8 +1008,11 @@ __device__ __forceinline__ void stage_in(T* S, int ldS, T* W, int len, int bc, i
 // NQW): the register-tiled form with at most 11 warps.
 constexpr int kMaxTileWarps = 12;
 
-template <typename T, int VEC, int TILE>
-__global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel(const JacobiParams<T> P) {
+// GW < 32 (with TILE = 1; whole slice in shared memory, mm <= 4 GW, at most
+// 4 warps): the tiled form on groups of GW lanes, 32 / GW tasks per warp.
+template <typename T, int VEC, int TILE, int GW = 32>
+__global__ void __launch_bounds__(GW < 32 ? 128 : (TILE ? 32 * kMaxTileWarps : 512))
+jacobi_kernel(const JacobiParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = blockIdx.x;
   const int tid = threadIdx.x, NTh = blockDim.x;
@@ -879,6 +1071,32 @@ __global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel
     if constexpr (TILE > 0) {
       const int wp = tid >> 5, ln = tid & 31, nwp = NTh >> 5;
       const int mq = mm >> 2, rq = rc >> 2;
+      if constexpr (GW < 32) {
+        // the whole slice in shared memory: round robin over the tiles, the
+        // tasks of a round 32 / GW to a warp
+        constexpr int TPW = 32 / GW;
+        __shared__ float4 cs_part[4 * TPW][10];   // rotation record of each group
+        const int grp = ln / GW, gl = ln % GW;
+        float4* csg = cs_part[wp * TPW + grp];
+        const TPhase ph = tphase_smem(rc);
+        const int nrounds = tphase_rounds(ph);
+        for (int t = 0; t < nrounds; ++t) {
+          const int ntasks = tphase_tasks(ph, t);
+          for (int k0 = wp * TPW; k0 < ntasks; k0 += nwp * TPW) {
+            const int k = k0 + grp;
+            TTask d{0, 0, 0, 0, false};
+            const bool live = k < ntasks && tphase_task(ph, t, k, d);
+            if (t == 0)
+              rot |= tile_group_part<GW, true>(S, ldS, d.sa, d.na, d.sb, d.nb, d.na > 0, d.nb > 0,
+                                               mq, rq, gl, grp, live, tol_t, floor_t, csg);
+            const bool cross = live && d.na > 0 && d.nb > 0;
+            if (__any_sync(0xffffffffu, cross))
+              rot |= tile_group_part<GW, false>(S, ldS, d.sa, d.na, d.sb, d.nb, false, false, mq,
+                                                rq, gl, grp, cross, tol_t, floor_t, csg);
+          }
+          __syncthreads();
+        }
+      } else {
       __shared__ float4 cs_rec[kMaxTileWarps][10];   // rotation record of each warp
       float4* csw = cs_rec[wp];
       for (int ps = 0; ps < npair_sets; ++ps) {
@@ -909,6 +1127,7 @@ __global__ void __launch_bounds__(TILE ? 32 * kMaxTileWarps : 512) jacobi_kernel
         if (!in_smem)
           copy_cols<T, VEC>(S + (int64_t)bc * ldS, ldS, W + (int64_t)(J * bc) * len, len, len,
                             ph.bJ, tid, NTh, false);
+      }
       }
     } else
     for (int ps = 0; ps < npair_sets; ++ps) {
@@ -1373,7 +1592,15 @@ JacobiPlan jacobi_plan_impl(int m, int n, int max_smem, bool allow_tile) {
       pl.smem = 2 * (size_t)pl.bcols * col_bytes + sort_bytes;
     } else {
       const int nt = (pl.rc + 3) / 4, tasks = (nt + (nt & 1)) / 2;
-      pl.threads = 32 * (tasks < 4 ? 4 : (tasks > kTileWarps ? kTileWarps : tasks));
+      if (pl.mm <= 64) {
+        // short columns (at most 16 float4 rows): groups of 16 or 8 lanes per
+        // task, so no lane idles; the round's tasks on at most 4 warps
+        const int gw = pl.mm <= 32 ? 8 : 16, tpw = 32 / gw;
+        pl.tile = gw;
+        pl.threads = 32 * std::min(4, (tasks + tpw - 1) / tpw);
+      } else {
+        pl.threads = 32 * (tasks < 4 ? 4 : (tasks > kTileWarps ? kTileWarps : tasks));
+      }
       pl.block_mode = 0;
       return pl;
     }
@@ -1438,6 +1665,13 @@ std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem) {
           v.threads = t;
           out.push_back(v);
         }
+      if (base.tile >= 8) {   // partial-warp groups: the full-warp tiled form too
+        JacobiPlan f = base;
+        const int nt = (f.rc + 3) / 4, tasks = (nt + (nt & 1)) / 2;
+        f.tile = 1;
+        f.threads = 32 * std::max(4, std::min(kMaxTileWarps, tasks));
+        out.push_back(f);
+      }
       JacobiPlan u = jacobi_plan_impl<T>(m, n, max_smem, false);
       if (!u.block_mode && u.threads >= 64) {
         const int nt = u.threads / 2;
@@ -1473,6 +1707,13 @@ cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_
       kern = jacobi_kernel<T, 4, 0>;
       if (P.tile == 1 && P.mm <= 128) kern = jacobi_kernel<T, 4, 1>;
       if (P.tile == 2 && P.mm <= 256) kern = jacobi_kernel<T, 4, 2>;
+      if (P.tile == 16 || P.tile == 8) {
+        // partial-warp groups: whole slice in shared memory, mm <= 4 GW rows,
+        // at most 4 warps (the size of the kernel's rotation record)
+        if (P.mm > 4 * P.tile || P.rc > 2 * P.bcols || threads > 128 || threads % 32)
+          return cudaErrorInvalidValue;
+        kern = P.tile == 16 ? jacobi_kernel<T, 4, 1, 16> : jacobi_kernel<T, 4, 1, 8>;
+      }
     }
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

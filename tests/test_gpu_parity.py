@@ -63,6 +63,17 @@ def problem(kind):
     if kind == "tall_300x40":              # QR reflectors longer than 256 rows
         bm = G.toeplitz_map(2)
         return G.Problem(kind, g.standard_normal((3, 300, 40)), bm)
+    # short columns: the fp32 Jacobi's partial-warp groups (16 lanes up to 64
+    # rows, 8 lanes up to 32), with full and ragged tiles and float4 rows
+    if kind == "short_64x64":
+        bm = G.block_banded_map(4, 1)
+        return G.Problem(kind, g.standard_normal((10, 64, 64)), bm)
+    if kind == "short_48x40":
+        bm = G.toeplitz_map(3)
+        return G.Problem(kind, g.standard_normal((5, 48, 40)), bm)
+    if kind == "short_32x32":
+        bm = G.toeplitz_map(3)
+        return G.Problem(kind, g.standard_normal((5, 32, 32)), bm)
     raise KeyError(kind)
 
 
@@ -102,7 +113,8 @@ QNAME = {S.SMA_PRECOND_NONE: "plain", S.SMA_PRECOND_QRCP: "qrcp", S.SMA_PRECOND_
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 @pytest.mark.parametrize("kind", ["toeplitz_ragged", "wide_trans", "tridiag_zero_blocks",
                                   "planted_cfg1", "single_block", "block_mode_fp64",
-                                  "block_mode_fp32", "tall_300x40", "p300"])
+                                  "block_mode_fp32", "tall_300x40", "p300", "short_64x64",
+                                  "short_48x40", "short_32x32"])
 @pytest.mark.parametrize("tol", [1e-2, 1e-6])
 @pytest.mark.parametrize("pre", PRECONDS, ids=QNAME.get)
 def test_tsvdm_end_to_end(prec, kind, tol, pre):
@@ -149,7 +161,7 @@ def test_tsvdm_end_to_end(prec, kind, tol, pre):
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 @pytest.mark.parametrize("kind", ["toeplitz_ragged", "wide_trans", "tridiag_zero_blocks",
-                                  "block_mode_fp32", "wide_128"])
+                                  "block_mode_fp32", "wide_128", "short_64x64", "short_32x32"])
 @pytest.mark.parametrize("pre", PRECONDS, ids=QNAME.get)
 def test_kron_sum_apply(prec, kind, pre):
     pr = problem(kind)
@@ -304,7 +316,8 @@ def test_rowcol_tucker_blr(prec):
     assert abs(res["tensor_err"] - t.err) <= 1e-6 * t.err + floor
 
 
-@pytest.mark.parametrize("kind", ["block_mode_fp32", "toeplitz_ragged", "wide_128"])
+@pytest.mark.parametrize("kind", ["block_mode_fp32", "toeplitz_ragged", "wide_128", "short_64x64",
+                                  "short_32x32"])
 def test_autotuned_plan_gives_the_same_compression(kind):
     """The autotuner only changes the Jacobi plan (tile, block width, warps):
     the retained ranks, singular values and rebuilt tensor stay those of the
