@@ -394,9 +394,23 @@ struct sma_ctx {
   double acc_ms[SMA_STAGE_COUNT] = {0};
   int64_t acc_calls[SMA_STAGE_COUNT] = {0};
   int64_t launches = 0;
+  // many-problem t-SVDM: the problems' transforms (independent products,
+  // each on its own buffers) fan out over these streams, forked from and
+  // joined back into the handle's stream by events (graph capture records
+  // the fork and join as edges)
+  static constexpr int kAux = 8;
+  cudaStream_t aux[kAux] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kAux] = {};
+  int naux = 0;
   ~sma_ctx() {
     for (cudaEvent_t e : ev_all) cudaEventDestroy(e);
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    for (int k = 0; k < naux; ++k) {
+      cudaStreamDestroy(aux[k]);
+      cudaEventDestroy(join_ev[k]);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
   }
 };
 
@@ -1134,26 +1148,52 @@ bool tc_transform<float>(sma_ctx* h, Prob<float>& P) {
          cudaSuccess;
 }
 
+// Xhat = X x3 M:  Xhat_mat (mn x p) = X_mat (mn x p) * M^T, on h->st
 template <typename T>
-sma_status tsvdm_pre(sma_ctx* h, Prob<T>& P) {
+sma_status transform_one(sma_ctx* h, Prob<T>& P) {
+  if (tc_transform(h, P)) return SMA_OK;
   const int p = P.p;
   const int64_t mn = (int64_t)P.m * P.n;
-  // Xhat = X x3 M:  Xhat_mat (mn x p) = X_mat (mn x p) * M^T
-  stage_begin(h, SMA_STAGE_TRANSFORM);
-  if (tc_transform(h, P)) {
-    stage_end(h);
-    return SMA_OK;
-  }
-  {
-    GemmParams<T> g;
-    g.M = (int)mn; g.N = p; g.K = p;
-    g.A = P.X; g.a_rs = 1; g.a_cs = mn;
-    g.B = P.Mt; g.b_rs = p; g.b_cs = 1;
-    g.C = P.Xh; g.c_rs = 1; g.c_cs = mn;
-    SMA_K(contract<T>(h, g));
-  }
-  stage_end(h);
+  GemmParams<T> g;
+  g.M = (int)mn; g.N = p; g.K = p;
+  g.A = P.X; g.a_rs = 1; g.a_cs = mn;
+  g.B = P.Mt; g.b_rs = p; g.b_cs = 1;
+  g.C = P.Xh; g.c_rs = 1; g.c_cs = mn;
+  SMA_K(contract<T>(h, g));
   return SMA_OK;
+}
+
+template <typename T>
+sma_status tsvdm_pre(sma_ctx* h, Prob<T>& P) {
+  stage_begin(h, SMA_STAGE_TRANSFORM);
+  const sma_status s = transform_one(h, P);
+  stage_end(h);
+  return s;
+}
+
+// The transforms of all problems of a many-problem handle: problem i on
+// auxiliary stream i mod naux, after everything already enqueued on the
+// handle's stream, which waits for all of them before its next work.  Each
+// problem's product reads and writes only its own buffers.
+template <typename T>
+sma_status transform_fanout(sma_ctx* h) {
+  auto& ps = probs<T>(h);
+  cudaStream_t main_st = h->st;
+  SMA_CK(cudaEventRecord(h->fork_ev, main_st));
+  for (int k = 0; k < h->naux; ++k) SMA_CK(cudaStreamWaitEvent(h->aux[k], h->fork_ev, 0));
+  sma_status s = SMA_OK;
+  for (int i = 0; i < h->nprob && s == SMA_OK; ++i) {
+    h->st = h->aux[i % h->naux];
+    s = transform_one(h, ps[i]);
+  }
+  h->st = main_st;
+  // join every branch, also after a failed enqueue (a capture must end joined)
+  for (int k = 0; k < h->naux; ++k) {
+    const cudaError_t e1 = cudaEventRecord(h->join_ev[k], h->aux[k]);
+    const cudaError_t e2 = cudaStreamWaitEvent(main_st, h->join_ev[k], 0);
+    if (s == SMA_OK && (e1 != cudaSuccess || e2 != cudaSuccess)) s = SMA_ERR_CUDA;
+  }
+  return s;
 }
 
 template <typename T>
@@ -2320,7 +2360,19 @@ sma_status enqueue_compress(sma_ctx* h, const void* const* A, const int64_t* lda
   SMA_CK(cudaMemsetAsync(h->status_pool, 0, sizeof(int) * (size_t)h->nprob, h->st));
   bool gathered = false;
   if (h->opt.decomp == SMA_TSVDM) SMA_TRY(gather_all<T>(h, A, lda, &gathered));
-  for (int i = 0; i < h->nprob; ++i) SMA_TRY(compress_one(h, ps[i], A[i], lda[i], gathered));
+  if (h->opt.decomp == SMA_TSVDM && gathered && h->naux > 0) {
+    stage_begin(h, SMA_STAGE_TRANSFORM);
+    SMA_TRY(transform_fanout<T>(h));
+    stage_end(h);
+    for (auto& P : ps) {
+      P.compressed = true;
+      P.dp_valid = false;
+      P.cq_valid = false;
+      P.h_iscal[0] = -1;
+    }
+  } else {
+    for (int i = 0; i < h->nprob; ++i) SMA_TRY(compress_one(h, ps[i], A[i], lda[i], gathered));
+  }
   if (h->opt.decomp == SMA_TSVDM) {
     if (h->nprob > 1) {
       SMA_TRY(tsvdm_svd_batched<T>(h));
@@ -3220,6 +3272,20 @@ sma_status sma_create(sma_handle* out, const sma_problem* prob, int32_t nprob,
     if (opt->decomp == SMA_TSVDM && nprob > 1) SMA_TRY(build_bins<float>(h.get()));
   }
   if (opt->decomp != SMA_TSVDM && opt->decomp != SMA_CP_ALS) SMA_TRY(setup_gram_shared(h.get()));
+  if (opt->decomp == SMA_TSVDM && nprob > 1) {
+    SMA_CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+    const int na = std::min(nprob, (int)sma_ctx::kAux);
+    for (int k = 0; k < na; ++k) {
+      SMA_CK(cudaStreamCreateWithFlags(&h->aux[k], cudaStreamNonBlocking));
+      const cudaError_t e = cudaEventCreateWithFlags(&h->join_ev[k], cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        cudaStreamDestroy(h->aux[k]);
+        h->aux[k] = nullptr;
+        SMA_CK(e);
+      }
+      h->naux = k + 1;
+    }
+  }
   *out = h.release();
   return SMA_OK;
 }
