@@ -1621,11 +1621,55 @@ sma_status gemm64_square(sma_ctx* h, int n, const double* A, bool ta, const doub
 //   3. the fp64 Jacobi of S (a few sweeps from a nearly diagonal start):
 //      S = Z Lambda Z^T; the Ritz values Lambda are G's eigenvalues to fp64
 //      accuracy and U Z its eigenvectors.
+// Orders from kPcholMinRows to kPcholMaxRows take the preconditioned form
+// (gram_pre.cu), one Gram at a time:
+//   1. G = L L^T, L = P R^T by the diagonally pivoted Cholesky in fp64 (R is
+//      the R factor of the column-pivoted QR of the unfolding's transpose);
+//   2. the fp32 Jacobi of L (as fast to converge as a QR-preconditioned
+//      slice): L V ~ U Sigma;
+//   3. V in fp64, made orthonormal to fp64 accuracy by two Newton-Schulz
+//      steps V <- V (3 I - V^T V) / 2;
+//   4. the fp64 Jacobi of L V, whose columns are already orthogonal up to the
+//      fp32 solve's accuracy, so it takes a few sweeps: L V V2 = U Sigma,
+//      and G = U Sigma^2 U^T to fp64 accuracy.
+constexpr int kPcholMinRows = 128;
+
+template <typename T>
+sma_status gram_solve_pchol(sma_ctx* h, Prob<T>& P, int slot, int rows) {
+  cudaStream_t st = h->st;
+  const size_t gs = P.gstride;
+  const int64_t nn = (int64_t)rows * rows;
+  double* L = P.gS + slot * gs;
+  SMA_K(gram_pchol(P.gram + slot * gs, rows, P.gT1, L, P.g32 + slot * gs, P.status, st));
+  const EigBufs<float> b32{P.g32 + slot * gs, P.gv32 + slot * gs, P.gw32 + slot * gs,
+                           P.gsig + (size_t)slot * P.gdim, gs, (size_t)P.gdim, P.sweeps + slot,
+                           P.wg32, nullptr};
+  SMA_TRY(eig_jacobi<T, float>(h, P, b32, 1, rows, 1 << 30));
+  double* V = P.gvec + slot * gs;
+  SMA_K(convert<double, float>(P.gv32 + slot * gs, V, nn, st));
+  for (int it = 0; it < 2; ++it) {
+    SMA_TRY(gemm64_square<T>(h, rows, V, true, V, false, P.gT1));     // V^T V
+    SMA_TRY(gemm64_square<T>(h, rows, V, false, P.gT1, false, P.gT2));  // V (V^T V)
+    SMA_K(axpby(-0.5, P.gT2, 1.5, V, nn, st));                        // V (3I - V^T V) / 2
+  }
+  SMA_TRY(gemm64_square<T>(h, rows, L, false, V, false, P.gT1));      // L V
+  const EigBufs<double> bX{P.gT1, P.gZ + slot * gs, P.gW + slot * gs,
+                           P.gsig + (size_t)slot * P.gdim, gs, (size_t)P.gdim, P.sweepsS + slot,
+                           P.Wg, nullptr};
+  SMA_TRY(eig_jacobi<T, double>(h, P, bX, 1, rows));
+  SMA_K(gram_pchol_finish(P.gW + slot * gs, P.gsig + (size_t)slot * P.gdim, rows, V, st));
+  return SMA_OK;
+}
+
 template <typename T>
 sma_status gram_solve_mixed(sma_ctx* h, Prob<T>& P, int slot, int count, int rows) {
   cudaStream_t st = h->st;
   const size_t gs = P.gstride;
   const int64_t nn = (int64_t)rows * rows;
+  if (rows >= kPcholMinRows && rows <= kPcholMaxRows) {
+    for (int c = 0; c < count; ++c) SMA_TRY(gram_solve_pchol(h, P, slot + c, rows));
+    return SMA_OK;
+  }
   for (int c = 0; c < count; ++c)
     SMA_K(convert<float, double>(P.gram + (slot + c) * gs, P.g32 + (slot + c) * gs, nn, st));
   const EigBufs<float> b32{P.g32 + slot * gs, P.gv32 + slot * gs, P.gw32 + slot * gs,

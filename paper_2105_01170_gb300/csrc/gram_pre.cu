@@ -1,0 +1,188 @@
+// Preconditioning of the mixed path's Gram eigen-solve.
+//
+// The Tucker variants (Sections 5.1, 6.2, 6.3, 7) need the eigenpairs of a
+// Gram G = Y Y^T of an unfolding Y.  One-sided Jacobi on G itself sees the
+// squared condition number of Y: in fp32 it needs many sweeps and leaves the
+// small eigenvalues unresolved.  Here G (fp64) is factored by a Cholesky
+// decomposition with diagonal pivoting,
+//   P^T G P = R^T R,   pivot of step k = the largest remaining diagonal entry,
+// which in exact arithmetic is the R factor of the column-pivoted QR of Y^T
+// (the slice SVD's preconditioner), and returned as L = P R^T, a square
+// factor G = L L^T in the original row order: L[c, k] = R[k, c'] for the
+// original index c at pivoted position c'.  The one-sided Jacobi of L (the
+// Jacobi of R^T with its rows permuted, so the same rotations) converges like
+// that of a QR-preconditioned slice; L V = U Sigma gives G = U Sigma^2 U^T.
+//
+// pchol_kernel: one CTA, the lower triangle of the trailing matrix in a
+// global fp64 workspace (n^2 doubles, L2-resident), the pivot's row of R and
+// the remaining diagonal in shared memory, one block barrier per step.  L is
+// written in fp64 and, scaled by 1 / sqrt(max_j G_jj) (entries at most 1 in
+// magnitude), in fp32.  A pivot at or below n eps max_j G_jj (the rounding
+// level of the elimination) is raised to that floor, so R stays
+// nonsingular; that changes G by about the floor, far below what the
+// eigen-solve resolves.
+#include <algorithm>
+#include <cfloat>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sma {
+namespace {
+
+constexpr int PCHOL_THREADS = 1024;
+
+__global__ void __launch_bounds__(PCHOL_THREADS)
+    pchol_kernel(const double* __restrict__ G, int n, double* __restrict__ A,
+                 double* __restrict__ L, float* __restrict__ L32, int* __restrict__ status) {
+  __shared__ double d[kPcholMaxRows];    // remaining diagonal, by original index
+  __shared__ double rk[kPcholMaxRows];   // the current row of R, by original index
+  __shared__ int ord[kPcholMaxRows];     // pivoted position -> original index
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ double s_scale, s_floor;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = (nt + 31) >> 5;
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t e = tid; e < nn; e += nt) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i >= j) A[e] = G[e];
+    L[e] = 0.0;
+    L32[e] = 0.f;
+  }
+  double mx = 0.0;
+  bool bad = false;
+  for (int j = tid; j < n; j += nt) {
+    const double v = G[j + (int64_t)n * j];
+    d[j] = v;
+    ord[j] = j;
+    bad |= !isfinite(v);
+    mx = fmax(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  bad = __syncthreads_or(bad);
+  if (lane == 0) red_v[warp] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < nw; ++w) m = fmax(m, red_v[w]);
+    s_scale = m > 0.0 ? 1.0 / sqrt(m) : 1.0;
+    s_floor = fmax((double)n * DBL_EPSILON * m, DBL_MIN);
+    if (bad) atomicOr(status, SMA_STATUS_BIT(SMA_ERR_NONFINITE));
+  }
+  __syncthreads();
+  const double scale = s_scale, flo = s_floor;
+  for (int k = 0; k < n; ++k) {
+    // pivot: the largest remaining diagonal entry, the lowest position on ties
+    double bv = -DBL_MAX;
+    int bq = n;
+    for (int q = k + tid; q < n; q += nt) {
+      const double v = d[ord[q]];
+      if (v > bv || (v == bv && q < bq)) {
+        bv = v;
+        bq = q;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+      if (ov > bv || (ov == bv && oq < bq)) {
+        bv = ov;
+        bq = oq;
+      }
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bq;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double v = red_v[0];
+      int q = red_i[0];
+      for (int w = 1; w < nw; ++w)
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < q)) {
+          v = red_v[w];
+          q = red_i[w];
+        }
+      if (q < k || q >= n) q = k;   // no comparable entry (NaN): keep the order
+      const int t = ord[k];
+      ord[k] = ord[q];
+      ord[q] = t;
+    }
+    __syncthreads();
+    const int c = ord[k];
+    const double rkk = sqrt(fmax(d[c], flo));
+    // row k of R: column k of L, by original index
+    for (int q = k + 1 + tid; q < n; q += nt) {
+      const int cq = ord[q];
+      const double a = cq >= c ? A[cq + (int64_t)n * c] : A[c + (int64_t)n * cq];
+      const double r = a / rkk;
+      rk[cq] = r;
+      L[cq + (int64_t)n * k] = r;
+      L32[cq + (int64_t)n * k] = (float)(r * scale);
+    }
+    if (tid == 0) {
+      L[c + (int64_t)n * k] = rkk;
+      L32[c + (int64_t)n * k] = (float)(rkk * scale);
+    }
+    __syncthreads();
+    // trailing update of the remaining pairs (lower triangle by original
+    // index): e -> positions (k + 1 + i, k + 1 + j), 0 <= j <= i
+    const int mrem = n - k - 1;
+    const int64_t ntri = (int64_t)mrem * (mrem + 1) / 2;
+    for (int64_t e = tid; e < ntri; e += nt) {
+      int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
+      while ((int64_t)i * (i + 1) / 2 > e) --i;
+      const int j = (int)(e - (int64_t)i * (i + 1) / 2);
+      const int c1 = ord[k + 1 + i], c2 = ord[k + 1 + j];
+      const int64_t at = c1 >= c2 ? c1 + (int64_t)n * c2 : c2 + (int64_t)n * c1;
+      A[at] = fma(-rk[c1], rk[c2], A[at]);
+    }
+    for (int q = k + 1 + tid; q < n; q += nt) {
+      const int cq = ord[q];
+      d[cq] = fma(-rk[cq], rk[cq], d[cq]);
+    }
+    __syncthreads();
+  }
+}
+
+// From the fp64 Jacobi of L V: U[:, j] = Wf[:, j] / sigma_j (e_j where sigma_j
+// is 0 or not finite, only for an all-zero G) and the eigenvalue sigma_j^2.
+__global__ void pchol_finish_kernel(const double* __restrict__ Wf, double* __restrict__ sig,
+                                    int n, double* __restrict__ U) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nn;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % n), j = (int)(e / n);
+    const double s = sig[j];
+    U[e] = (s > 0.0 && isfinite(s)) ? Wf[e] / s : (q == j ? 1.0 : 0.0);
+  }
+}
+
+__global__ void square_kernel(double* __restrict__ v, int n) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    v[j] = v[j] * v[j];
+}
+
+}  // namespace
+
+cudaError_t gram_pchol(const double* G, int n, double* work, double* L, float* L32, int* status,
+                       cudaStream_t st) {
+  if (n < 1 || n > kPcholMaxRows) return cudaErrorInvalidValue;
+  pchol_kernel<<<1, PCHOL_THREADS, 0, st>>>(G, n, work, L, L32, status);
+  return cudaGetLastError();
+}
+
+cudaError_t gram_pchol_finish(const double* Wf, double* sig, int n, double* U, cudaStream_t st) {
+  if (n < 1) return cudaErrorInvalidValue;
+  const int64_t nn = (int64_t)n * n;
+  const int blocks = (int)std::min<int64_t>((nn + 255) / 256, 1024);
+  pchol_finish_kernel<<<blocks, 256, 0, st>>>(Wf, sig, n, U);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  square_kernel<<<(n + 255) / 256, 256, 0, st>>>(sig, n);
+  return cudaGetLastError();
+}
+
+}  // namespace sma

@@ -283,6 +283,18 @@ cudaError_t permute3(const double* src, int64_t s0, int64_t s1, int64_t s2, int 
 template <typename TD, typename TS>
 cudaError_t convert(const TS* src, TD* dst, int64_t count, cudaStream_t st);
 
+// Mixed Gram eigen-solve preconditioner (gram_pre.cu): G = L L^T with L =
+// P R^T from the diagonally pivoted Cholesky P^T G P = R^T R in fp64 (G n x n
+// column-major, n <= kPcholMaxRows; work: n^2 doubles); L in fp64 and, scaled
+// by 1 / sqrt(max_j G_jj), in fp32 (both n x n column-major).
+constexpr int kPcholMaxRows = 256;
+cudaError_t gram_pchol(const double* G, int n, double* work, double* L, float* L32, int* status,
+                       cudaStream_t st);
+// After the Jacobi of L V (W_f = L V V2 = U Sigma, sig = Sigma): U = W_f
+// Sigma^-1 (e_j where sigma_j is 0 or not finite) and sig <- sig^2, the
+// eigenvalues of G.
+cudaError_t gram_pchol_finish(const double* Wf, double* sig, int n, double* U, cudaStream_t st);
+
 // ---- CP by alternating least squares (cp.cu) --------------------------------
 constexpr int kCpMaxRank = 64;
 // out[(a + ra b), j] = A[a, j] B[b, j]: the Khatri-Rao (columnwise Kronecker)

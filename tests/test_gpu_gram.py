@@ -49,9 +49,13 @@ def projector_gap(Ug, Uo):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
-def test_blockmode_99_blocks(prec):
-    pr = G.planted_kron_toeplitz(ell=50, m=6, terms=4, seed_index=5)
-    assert pr.p == 99
+@pytest.mark.parametrize("ell", [50, 80])
+def test_blockmode_99_blocks(prec, ell):
+    """p = 99 and 159 distinct blocks of 6 x 6: Grams of rank at most 36, the
+    larger one on the mixed path's pivoted-Cholesky form (orders 128 to 256),
+    whose pivots fall to the rounding floor after the 36th step."""
+    pr = G.planted_kron_toeplitz(ell=ell, m=6, terms=4, seed_index=5)
+    assert pr.p == 2 * ell - 1
     tol = 1e-6 if prec == S.SMA_FP64 else 1e-4
     h, A, res = run(pr, prec, S.SMA_TUCKER_BLOCKMODE, rel_tol=tol)
     assert res["device_status"] == 0
