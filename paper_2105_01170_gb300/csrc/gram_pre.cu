@@ -13,14 +13,16 @@
 // Jacobi of R^T with its rows permuted, so the same rotations) converges like
 // that of a QR-preconditioned slice; L V = U Sigma gives G = U Sigma^2 U^T.
 //
-// pchol_kernel: one CTA, the lower triangle of the trailing matrix in a
-// global fp64 workspace (n^2 doubles, L2-resident), the pivot's row of R and
-// the remaining diagonal in shared memory, one block barrier per step.  L is
-// written in fp64 and, scaled by 1 / sqrt(max_j G_jj) (entries at most 1 in
-// magnitude), in fp32.  A pivot at or below n eps max_j G_jj (the rounding
-// level of the elimination) is raised to that floor, so R stays
-// nonsingular; that changes G by about the floor, far below what the
-// eigen-solve resolves.
+// pchol_kernel: one CTA.  The trailing matrix is kept in pivoted order in a
+// global fp64 workspace (lower triangle, n^2 doubles, L2-resident): a pivot
+// swaps its row and column with those of position k (O(n) moves), so the
+// rank-1 update of each step runs over contiguous columns, one warp per
+// column.  The remaining diagonal and the pivot's row of R are in shared
+// memory; L is written by original index.  L is written in fp64 and, scaled
+// by 1 / sqrt(max_j G_jj) (entries at most 1 in magnitude), in fp32.  A pivot
+// at or below n eps max_j G_jj (the rounding level of the elimination) is
+// raised to that floor, so R stays nonsingular; that changes G by about the
+// floor, far below what the eigen-solve resolves.
 #include <algorithm>
 #include <cfloat>
 
@@ -35,12 +37,13 @@ constexpr int PCHOL_THREADS = 1024;
 __global__ void __launch_bounds__(PCHOL_THREADS)
     pchol_kernel(const double* __restrict__ G, int n, double* __restrict__ A,
                  double* __restrict__ L, float* __restrict__ L32, int* __restrict__ status) {
-  __shared__ double d[kPcholMaxRows];    // remaining diagonal, by original index
-  __shared__ double rk[kPcholMaxRows];   // the current row of R, by original index
-  __shared__ int ord[kPcholMaxRows];     // pivoted position -> original index
+  __shared__ double d[kPcholMaxRows];    // remaining diagonal, by position
+  __shared__ double rk[kPcholMaxRows];   // the current row of R, by position
+  __shared__ int ord[kPcholMaxRows];     // position -> original index
   __shared__ double red_v[32];
   __shared__ int red_i[32];
   __shared__ double s_scale, s_floor;
+  __shared__ int s_q;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nw = (nt + 31) >> 5;
   const int64_t nn = (int64_t)n * n;
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(PCHOL_THREADS)
     double bv = -DBL_MAX;
     int bq = n;
     for (int q = k + tid; q < n; q += nt) {
-      const double v = d[ord[q]];
+      const double v = d[q];
       if (v > bv || (v == bv && q < bq)) {
         bv = v;
         bq = q;
@@ -96,53 +99,72 @@ __global__ void __launch_bounds__(PCHOL_THREADS)
       red_i[warp] = bq;
     }
     __syncthreads();
-    if (tid == 0) {
-      double v = red_v[0];
-      int q = red_i[0];
-      for (int w = 1; w < nw; ++w)
-        if (red_v[w] > v || (red_v[w] == v && red_i[w] < q)) {
-          v = red_v[w];
-          q = red_i[w];
+    if (warp == 0) {
+      double v = lane < nw ? red_v[lane] : -DBL_MAX;
+      int q = lane < nw ? red_i[lane] : n;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, q, o);
+        if (ov > v || (ov == v && oq < q)) {
+          v = ov;
+          q = oq;
         }
-      if (q < k || q >= n) q = k;   // no comparable entry (NaN): keep the order
-      const int t = ord[k];
-      ord[k] = ord[q];
-      ord[q] = t;
+      }
+      if (lane == 0) s_q = (q < k || q >= n) ? k : q;   // no comparable entry (NaN): keep the order
     }
     __syncthreads();
-    const int c = ord[k];
-    const double rkk = sqrt(fmax(d[c], flo));
-    // row k of R: column k of L, by original index
-    for (int q = k + 1 + tid; q < n; q += nt) {
-      const int cq = ord[q];
-      const double a = cq >= c ? A[cq + (int64_t)n * c] : A[c + (int64_t)n * cq];
-      const double r = a / rkk;
-      rk[cq] = r;
-      L[cq + (int64_t)n * k] = r;
-      L32[cq + (int64_t)n * k] = (float)(r * scale);
+    const int q = s_q;
+    if (q != k) {
+      // swap positions k and q in the trailing lower triangle: (i, k) with
+      // (q, i) for k < i < q, (i, k) with (i, q) for i > q; the entry (q, k)
+      // stays and the diagonals move with d
+      for (int i = k + 1 + tid; i < n; i += nt) {
+        if (i == q) continue;
+        double* a = A + i + (int64_t)n * k;
+        double* b = i < q ? A + q + (int64_t)n * i : A + i + (int64_t)n * q;
+        const double t = *a;
+        *a = *b;
+        *b = t;
+      }
+      if (tid == 0) {
+        const double t = d[k];
+        d[k] = d[q];
+        d[q] = t;
+        const int o = ord[k];
+        ord[k] = ord[q];
+        ord[q] = o;
+      }
+      __syncthreads();
+    }
+    const double rkk = sqrt(fmax(d[k], flo));
+    // row k of R (column k of A below the diagonal): column k of L, by
+    // original index
+    for (int i = k + 1 + tid; i < n; i += nt) {
+      const double r = A[i + (int64_t)n * k] / rkk;
+      rk[i] = r;
+      const int c = ord[i];
+      L[c + (int64_t)n * k] = r;
+      L32[c + (int64_t)n * k] = (float)(r * scale);
     }
     if (tid == 0) {
-      L[c + (int64_t)n * k] = rkk;
-      L32[c + (int64_t)n * k] = (float)(rkk * scale);
+      L[ord[k] + (int64_t)n * k] = rkk;
+      L32[ord[k] + (int64_t)n * k] = (float)(rkk * scale);
     }
     __syncthreads();
-    // trailing update of the remaining pairs (lower triangle by original
-    // index): e -> positions (k + 1 + i, k + 1 + j), 0 <= j <= i
-    const int mrem = n - k - 1;
-    const int64_t ntri = (int64_t)mrem * (mrem + 1) / 2;
-    for (int64_t e = tid; e < ntri; e += nt) {
-      int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-      while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
-      while ((int64_t)i * (i + 1) / 2 > e) --i;
-      const int j = (int)(e - (int64_t)i * (i + 1) / 2);
-      const int c1 = ord[k + 1 + i], c2 = ord[k + 1 + j];
-      const int64_t at = c1 >= c2 ? c1 + (int64_t)n * c2 : c2 + (int64_t)n * c1;
-      A[at] = fma(-rk[c1], rk[c2], A[at]);
+    // rank-1 update of the trailing lower triangle, one warp per column, two
+    // 32-row chunks in flight per iteration
+    for (int j = k + 1 + warp; j < n; j += nw) {
+      const double rj = rk[j];
+      double* col = A + (int64_t)n * j;
+      int i = j + lane;
+      for (; i + 32 < n; i += 64) {
+        const double a0 = col[i], a1 = col[i + 32];
+        col[i] = fma(-rk[i], rj, a0);
+        col[i + 32] = fma(-rk[i + 32], rj, a1);
+      }
+      if (i < n) col[i] = fma(-rk[i], rj, col[i]);
     }
-    for (int q = k + 1 + tid; q < n; q += nt) {
-      const int cq = ord[q];
-      d[cq] = fma(-rk[cq], rk[cq], d[cq]);
-    }
+    for (int i = k + 1 + tid; i < n; i += nt) d[i] = fma(-rk[i], rk[i], d[i]);
     __syncthreads();
   }
 }

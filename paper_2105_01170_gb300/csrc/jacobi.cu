@@ -641,26 +641,32 @@ __device__ __forceinline__ float reduce4_group(const float (&v)[4], int gl) {
   return u;
 }
 
-template <int GW, bool INNER>
+template <int GW, int NQW, bool INNER>
 __device__ __forceinline__ bool tile_group_part(float* S, int ldS, int sa, int na, int sb, int nb,
                                                 bool doA, bool doB, int mq, int rq, int gl,
                                                 int grp, bool live, float tol, float floor_,
                                                 float4* csw) {
   constexpr int NR = INNER ? 3 : 4;
   if (!live) na = nb = 0;
-  float4 x[8];
+  float4 x[8][NQW];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const bool valid = c < 4 ? c < na : (c - 4) < nb;
     const int slot = c < 4 ? sa + c : sb + c - 4;
     const float4* col = reinterpret_cast<const float4*>(S + (int64_t)(valid ? slot : 0) * ldS);
-    x[c] = (valid && gl < mq) ? col[gl] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < NQW; ++i) {
+      const int qq = gl + GW * i;
+      x[c][i] = (valid && qq < mq) ? col[qq] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   }
   // squared norms of the 8 columns, in every lane of the group
   float nrm8[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    float a = dot4(x[c], x[c], 0.f);
+    float a = 0.f;
+#pragma unroll
+    for (int i = 0; i < NQW; ++i) a = dot4(x[c][i], x[c][i], a);
 #pragma unroll
     for (int o = GW / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     nrm8[c] = a;
@@ -678,7 +684,10 @@ __device__ __forceinline__ bool tile_group_part(float* S, int ldS, int sa, int n
     for (int q = 0; q < 4; ++q) {
       int a, b;
       tile_pair<INNER>(r, q, a, b);
-      g4[q] = dot4(x[a], x[b], 0.f);
+      float g = 0.f;
+#pragma unroll
+      for (int i = 0; i < NQW; ++i) g = dot4(x[a][i], x[b][i], g);
+      g4[q] = g;
     }
     const float gr = reduce4_group<GW>(g4, gl);
     // lanes 0..3 of the group: the angle of pair q = gl (the others repeat them)
@@ -722,11 +731,14 @@ __device__ __forceinline__ bool tile_group_part(float* S, int ldS, int sa, int n
       tile_pair<INNER>(r, qq, a, b);
       t1[qq] = __fdividef(tq[qq] * d[b], d[a]);
       t2[qq] = __fdividef(tq[qq] * d[a], d[b]);
-      const float4 xa = x[a], xb = x[b];
-      x[a] = make_float4(fmaf(-t1[qq], xb.x, xa.x), fmaf(-t1[qq], xb.y, xa.y),
-                         fmaf(-t1[qq], xb.z, xa.z), fmaf(-t1[qq], xb.w, xa.w));
-      x[b] = make_float4(fmaf(t2[qq], xa.x, xb.x), fmaf(t2[qq], xa.y, xb.y),
-                         fmaf(t2[qq], xa.z, xb.z), fmaf(t2[qq], xa.w, xb.w));
+#pragma unroll
+      for (int i = 0; i < NQW; ++i) {
+        const float4 xa = x[a][i], xb = x[b][i];
+        x[a][i] = make_float4(fmaf(-t1[qq], xb.x, xa.x), fmaf(-t1[qq], xb.y, xa.y),
+                              fmaf(-t1[qq], xb.z, xa.z), fmaf(-t1[qq], xb.w, xa.w));
+        x[b][i] = make_float4(fmaf(t2[qq], xa.x, xb.x), fmaf(t2[qq], xa.y, xb.y),
+                              fmaf(t2[qq], xa.z, xb.z), fmaf(t2[qq], xa.w, xb.w));
+      }
       d[a] *= cq[qq];
       d[b] *= cq[qq];
       nrm8[a] = fmaf(-tq[qq], gt[qq], nrm8[a]);
@@ -745,8 +757,12 @@ __device__ __forceinline__ bool tile_group_part(float* S, int ldS, int sa, int n
       if (!valid) continue;
       float4* col = reinterpret_cast<float4*>(S + (int64_t)(c < 4 ? sa + c : sb + c - 4) * ldS);
       const float dc = d[c];
-      const float4 v = x[c];
-      if (gl < mq) col[gl] = make_float4(dc * v.x, dc * v.y, dc * v.z, dc * v.w);
+#pragma unroll
+      for (int i = 0; i < NQW; ++i) {
+        const int qq = gl + GW * i;
+        const float4 v = x[c][i];
+        if (qq < mq) col[qq] = make_float4(dc * v.x, dc * v.y, dc * v.z, dc * v.w);
+      }
     }
     if (gl == 0) {
       csw[2 * NR] = make_float4(d[0], d[1], d[2], d[3]);
@@ -1008,8 +1024,8 @@ __device__ __forceinline__ void stage_in(T* S, int ldS, T* W, int len, int bc, i
 // NQW): the register-tiled form with at most 11 warps.
 constexpr int kMaxTileWarps = 12;
 
-// GW < 32 (with TILE = 1; whole slice in shared memory, mm <= 4 GW, at most
-// 4 warps): the tiled form on groups of GW lanes, 32 / GW tasks per warp.
+// GW < 32 (whole slice in shared memory, mm <= 4 GW TILE, at most 4 warps):
+// the tiled form on groups of GW lanes, 32 / GW tasks per warp.
 template <typename T, int VEC, int TILE, int GW = 32>
 __global__ void __launch_bounds__(GW < 32 ? 128 : (TILE ? 32 * kMaxTileWarps : 512))
 jacobi_kernel(const JacobiParams<T> P) {
@@ -1087,12 +1103,13 @@ jacobi_kernel(const JacobiParams<T> P) {
             TTask d{0, 0, 0, 0, false};
             const bool live = k < ntasks && tphase_task(ph, t, k, d);
             if (t == 0)
-              rot |= tile_group_part<GW, true>(S, ldS, d.sa, d.na, d.sb, d.nb, d.na > 0, d.nb > 0,
-                                               mq, rq, gl, grp, live, tol_t, floor_t, csg);
+              rot |= tile_group_part<GW, TILE, true>(S, ldS, d.sa, d.na, d.sb, d.nb, d.na > 0,
+                                                     d.nb > 0, mq, rq, gl, grp, live, tol_t,
+                                                     floor_t, csg);
             const bool cross = live && d.na > 0 && d.nb > 0;
             if (__any_sync(0xffffffffu, cross))
-              rot |= tile_group_part<GW, false>(S, ldS, d.sa, d.na, d.sb, d.nb, false, false, mq,
-                                                rq, gl, grp, cross, tol_t, floor_t, csg);
+              rot |= tile_group_part<GW, TILE, false>(S, ldS, d.sa, d.na, d.sb, d.nb, false, false,
+                                                      mq, rq, gl, grp, cross, tol_t, floor_t, csg);
           }
           __syncthreads();
         }
@@ -1593,10 +1610,11 @@ JacobiPlan jacobi_plan_impl(int m, int n, int max_smem, bool allow_tile) {
     } else {
       const int nt = (pl.rc + 3) / 4, tasks = (nt + (nt & 1)) / 2;
       if (pl.mm <= 64) {
-        // short columns (at most 16 float4 rows): groups of 16 or 8 lanes per
-        // task, so no lane idles; the round's tasks on at most 4 warps
+        // short columns (at most 16 float4 rows): groups of g = 16 or 8 lanes
+        // per task, so no lane idles; the round's tasks on at most 4 warps
         const int gw = pl.mm <= 32 ? 8 : 16, tpw = 32 / gw;
-        pl.tile = gw;
+        pl.g = gw;
+        pl.tile = 1;
         pl.threads = 32 * std::min(4, (tasks + tpw - 1) / tpw);
       } else {
         pl.threads = 32 * (tasks < 4 ? 4 : (tasks > kTileWarps ? kTileWarps : tasks));
@@ -1665,9 +1683,18 @@ std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem) {
           v.threads = t;
           out.push_back(v);
         }
-      if (base.tile >= 8) {   // partial-warp groups: the full-warp tiled form too
+      if (base.g < 32) {
+        // partial-warp groups: half as many lanes with two float4 rows each
+        // (twice the tasks per warp), and the full-warp tiled form
+        const int nt = (base.rc + 3) / 4, tasks = (nt + (nt & 1)) / 2;
+        JacobiPlan h2 = base;
+        h2.g = base.g / 2;
+        h2.tile = 2;
+        const int tpw = 32 / h2.g;
+        h2.threads = 32 * std::min(4, (tasks + tpw - 1) / tpw);
+        out.push_back(h2);
         JacobiPlan f = base;
-        const int nt = (f.rc + 3) / 4, tasks = (nt + (nt & 1)) / 2;
+        f.g = 32;
         f.tile = 1;
         f.threads = 32 * std::max(4, std::min(kMaxTileWarps, tasks));
         out.push_back(f);
@@ -1707,12 +1734,17 @@ cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_
       kern = jacobi_kernel<T, 4, 0>;
       if (P.tile == 1 && P.mm <= 128) kern = jacobi_kernel<T, 4, 1>;
       if (P.tile == 2 && P.mm <= 256) kern = jacobi_kernel<T, 4, 2>;
-      if (P.tile == 16 || P.tile == 8) {
-        // partial-warp groups: whole slice in shared memory, mm <= 4 GW rows,
-        // at most 4 warps (the size of the kernel's rotation record)
-        if (P.mm > 4 * P.tile || P.rc > 2 * P.bcols || threads > 128 || threads % 32)
+      if (P.tile > 0 && P.g < 32) {
+        // partial-warp groups of g lanes, tile float4 rows per lane: whole
+        // slice in shared memory, mm <= 4 g tile rows, at most 4 warps (the
+        // size of the kernel's rotation record)
+        if (P.mm > 4 * P.g * P.tile || P.rc > 2 * P.bcols || threads > 128 || threads % 32)
           return cudaErrorInvalidValue;
-        kern = P.tile == 16 ? jacobi_kernel<T, 4, 1, 16> : jacobi_kernel<T, 4, 1, 8>;
+        if (P.g == 16 && P.tile == 1) kern = jacobi_kernel<T, 4, 1, 16>;
+        else if (P.g == 8 && P.tile == 1) kern = jacobi_kernel<T, 4, 1, 8>;
+        else if (P.g == 8 && P.tile == 2) kern = jacobi_kernel<T, 4, 2, 8>;
+        else if (P.g == 4 && P.tile == 2) kern = jacobi_kernel<T, 4, 2, 4>;
+        else return cudaErrorInvalidValue;
       }
     }
   }

@@ -93,8 +93,8 @@ struct JacobiParams {
 };
 struct JacobiPlan {
   int trans, mm, rc, ldS, bcols, sort_n, threads, g, block_mode, vec;
-  int tile;   // 0: one pair per group of g lanes; 1, 2: register tiles (mm <= 128 tile);
-              // 16, 8: register tiles on groups of that many lanes (mm <= 4 tile)
+  int tile;   // 0: one pair per group of g lanes; 1, 2: register tiles of that many
+              // float4 rows per lane on groups of g lanes (mm <= 4 g tile)
   size_t smem;
 };
 template <typename T> JacobiPlan jacobi_plan(int m, int n, int max_smem);
