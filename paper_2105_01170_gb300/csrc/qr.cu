@@ -240,6 +240,62 @@ __device__ __forceinline__ void reflect_n(T* const (&x)[NC], const bool (&act)[N
   }
 }
 
+// reflect_n for fp32 columns with mm % 4 == 0 and mm <= 4 * 64 rows: lane l
+// holds the float4 rows q = k / 4 + l + 32 i (i < 2), so one instruction moves
+// four rows.  The rows [4 (k / 4), k) above the reflector are included with
+// v = 0 there (the caller clears them), which leaves them unchanged.
+template <int NC>
+__device__ __forceinline__ void reflect_n4(float* const (&x)[NC], const bool (&act)[NC],
+                                           const float* v, float tau, int k, int mm, int lane,
+                                           float (&yk)[NC]) {
+  const int q0 = k >> 2, mq = mm >> 2;
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+  float4 xr[NC][2];
+  float w[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    w[c] = 0.f;
+    const float4* x4 = reinterpret_cast<const float4*>(x[c]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int q = q0 + lane + 32 * i;
+      xr[c][i] = (act[c] && q < mq) ? x4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  float4 vr[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int q = q0 + lane + 32 * i;
+    vr[i] = q < mq ? v4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      w[c] = fmaf(vr[i].x, xr[c][i].x, fmaf(vr[i].y, xr[c][i].y,
+             fmaf(vr[i].z, xr[c][i].z, fmaf(vr[i].w, xr[c][i].w, w[c]))));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const float tw = tau * w[c];
+    float4* x4 = reinterpret_cast<float4*>(x[c]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int q = q0 + lane + 32 * i;
+      if (act[c] && q < mq) {
+        const float4 y = make_float4(fmaf(-tw, vr[i].x, xr[c][i].x), fmaf(-tw, vr[i].y, xr[c][i].y),
+                                     fmaf(-tw, vr[i].z, xr[c][i].z), fmaf(-tw, vr[i].w, xr[c][i].w));
+        x4[q] = y;
+        if (i == 0 && lane == 0) {
+          const int e = k & 3;
+          yk[c] = e == 0 ? y.x : e == 1 ? y.y : e == 2 ? y.z : y.w;
+        }
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -337,6 +393,9 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
   }
   __syncthreads();
 
+  // float4 rows for the reflector applications: fp32, columns of a multiple
+  // of 4 rows (16-byte aligned in the slots and in the overflow), at most 256
+  const bool vec4 = sizeof(T) == 4 && mm % 4 == 0 && mm <= 256;
   for (int k = 0; k < rc; ++k) {
     // pivot: the remaining column with the largest norm
     const int jp = block_argmax(nrm, k, rc, rv, ri);
@@ -378,6 +437,7 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
       }
       Fk[r] = out;
     }
+    if (tid < 4 && (k & ~3) + tid < k) v[(k & ~3) + tid] = T(0);   // rows above k, float4 form
     if (tid == 0) {
       v[k] = T(1);
       P.tau[(int64_t)s * rc + k] = tau;
@@ -428,7 +488,12 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(const QrParams<T> P) {
       T* const xs[2] = {colp[j0], colp[j1 < rc ? j1 : j0]};
       const bool act[2] = {true, j1 < rc};
       T yk[2] = {T(0), T(0)};
-      reflect_n<T, 2>(xs, act, v, tau, k, mm, lane, yk);
+      if constexpr (sizeof(T) == 4) {
+        if (vec4) reflect_n4<2>(xs, act, v, tau, k, mm, lane, yk);
+        else reflect_n<T, 2>(xs, act, v, tau, k, mm, lane, yk);
+      } else {
+        reflect_n<T, 2>(xs, act, v, tau, k, mm, lane, yk);
+      }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if (!act[c]) continue;
