@@ -27,6 +27,9 @@ namespace {
 // Gram eigen-solves of this order and larger run over many CTAs
 // (jacobi_svd_coop); smaller ones in one CTA.
 constexpr int kCoopMinRows = 40;
+// fp32 Gram solves (single matrices) of this order and larger run over a
+// cluster of CTAs (jacobi_svd_cluster)
+constexpr int kClusterMinRows = 128;
 // SMA_PRECOND_AUTO preconditions the slice SVD by a column-pivoted QR from
 // this min(m, n) on (below it the factorisation costs more than the sweeps
 // it saves), and by two from kQr2AutoMin on
@@ -1568,6 +1571,13 @@ sma_status eig_jacobi(sma_ctx* h, Prob<T>& P, const EigBufs<E>& b, int count, in
     SMA_K(jacobi_svd<E>(J, count, jp.threads, jp.smem, st));
     return SMA_OK;
   }
+  // one fp32 matrix of order >= kClusterMinRows: over a cluster of CTAs
+  JacobiPlan cl{};
+  if constexpr (std::is_same<E, float>::value)
+    if (!coop && rows >= kClusterMinRows && h->coop_rot) cl = jacobi_cluster_plan(rows, h->max_smem);
+  if (cl.smem > 0) {
+    J.ldS = cl.ldS; J.bcols = cl.bcols; J.g = cl.g; J.sort_n = cl.sort_n; J.tile = cl.tile;
+  }
   for (int c = 0; c < count; ++c) {
     J.src = b.src + (size_t)c * b.stride; J.src_bs = 0;
     J.W = (jp.block_mode || coop) ? b.work : nullptr; J.W_bs = 0;
@@ -1577,6 +1587,11 @@ sma_status eig_jacobi(sma_ctx* h, Prob<T>& P, const EigBufs<E>& b, int count, in
     J.sweeps = b.sweeps + c;
     if (coop) {
       SMA_K(jacobi_svd_coop<E>(J, cp, CoopSync{h->coop_bar, h->coop_rot, h->coop_abort}, st));
+    } else if (cl.smem > 0) {
+      if constexpr (std::is_same<E, float>::value) {
+        J.W = b.work;
+        SMA_K(jacobi_svd_cluster(J, cl, h->coop_rot, st));
+      }
     } else {
       SMA_K(jacobi_svd<E>(J, 1, jp.threads, jp.smem, st));
     }

@@ -1540,6 +1540,172 @@ __global__ void __launch_bounds__(512) jacobi_coop_kernel(const JacobiParams<T> 
   }
 }
 
+// ---- one fp32 matrix over a cluster of CTAs --------------------------------
+// The single-CTA block mode walks the block pairs of a sweep one after
+// another on one SM.  Here a cluster of CL CTAs shares one matrix (the fp32
+// pass of a Gram eigen-solve): the columns are split into 2 CL blocks of
+// bcols (a multiple of 4), round t of a sweep pairs the blocks by the circle
+// method and CTA c takes pair c, staging both blocks from the L2-resident
+// workspace into its shared memory and running the register-tiled phase of
+// the block mode on them (the blocks' inner pairs in round 0, where every
+// block plays, then the cross pairs); the blocks go back to the workspace
+// and the rounds are separated by the hardware cluster barrier (release /
+// acquire at cluster scope; the workspace is read with ld.global.cg so no
+// CTA sees a stale L1 line).  Every column pair is rotated exactly once per
+// sweep; a sweep that rotates nothing ends the solve (a per-sweep counter in
+// global memory, cleared by the launcher).  CTA 0 then sorts and writes the
+// outputs as jacobi_kernel does.
+constexpr int kClusterCtas = 8;
+constexpr int kClusterWarps = 4;
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+
+// ncols stacked columns of `rows` floats between shared memory (stride ldS)
+// and the workspace (stride ldg), float4, L1 bypassed on the loads
+__device__ __forceinline__ void cluster_cols(float* S, int ldS, float* G, int ldg, int rows,
+                                             int ncols, int tid, int nth, bool to_smem) {
+  const int rq = rows >> 2;
+  for (int e = tid; e < rq * ncols; e += nth) {
+    const int r = e % rq, c = e / rq;
+    float4* s4 = reinterpret_cast<float4*>(S + (int64_t)c * ldS) + r;
+    float4* g4 = reinterpret_cast<float4*>(G + (int64_t)c * ldg) + r;
+    if (to_smem) *s4 = __ldcg(g4);
+    else __stcg(g4, *s4);
+  }
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(32 * kClusterWarps)
+    jacobi_cluster_kernel(const JacobiParams<float> P, int* __restrict__ rot_count) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, NTh = blockDim.x;
+  const int cta = blockIdx.x, ncta = gridDim.x;
+  const int mm = P.mm, rc = P.rc, ldS = P.ldS, bc = P.bcols;
+  const int len = mm + rc;
+  const int nb = 2 * ncta;
+  float* S = reinterpret_cast<float*>(smem_raw);
+  float* W = P.W;
+  const int wp = tid >> 5, ln = tid & 31, nwp = NTh >> 5;
+  const int mq = mm >> 2, rq = rc >> 2;
+  __shared__ float4 cs_rec[kClusterWarps][10];
+  float4* csw = cs_rec[wp];
+  // stacked columns [A; I] into the workspace (shared by the cluster's
+  // threads) and ||A||_F^2 (every CTA sums it whole: no cross-CTA reduction)
+  __shared__ double red[32];
+  double nrm2 = 0.0;
+  {
+    const int64_t tot = (int64_t)len * rc;
+    for (int64_t e = (int64_t)cta * NTh + tid; e < tot; e += (int64_t)ncta * NTh) {
+      const int r = (int)(e % len), c = (int)(e / len);
+      __stcg(W + e, load_work(P.src, P.m, P.trans, mm, r, c));
+    }
+    for (int64_t e = tid; e < (int64_t)mm * rc; e += NTh) {
+      const int r = (int)(e % mm), c = (int)(e / mm);
+      const double v = (double)load_work(P.src, P.m, P.trans, mm, r, c);
+      nrm2 = fma(v, v, nrm2);
+    }
+    nrm2 = block_sum(nrm2, red);
+  }
+  const float tol_t = (float)P.tol;
+  const float floor_t = (float)(Eps<float>::v * Eps<float>::v * nrm2);
+  cluster_barrier();
+  int sweeps_used = 0;
+  bool converged = (rc <= 1);
+  for (int sw = 0; sw < P.max_sweeps && !converged; ++sw) {
+    bool rot = false;
+    for (int t = 0; t < nb - 1; ++t) {
+      const Pair pr = rr_pair(cta, t, nb);
+      const int bI = max(0, min(bc, rc - pr.a * bc)), bJ = max(0, min(bc, rc - pr.b * bc));
+      float* WI = W + (int64_t)pr.a * bc * len;
+      float* WJ = W + (int64_t)pr.b * bc * len;
+      cluster_cols(S, ldS, WI, len, len, bI, tid, NTh, true);
+      cluster_cols(S + (int64_t)bc * ldS, ldS, WJ, len, len, bJ, tid, NTh, true);
+      __syncthreads();
+      const TPhase ph = tphase_blocks(bI, bJ, bc, t == 0 && bI > 1, t == 0 && bJ > 1);
+      const int nrounds = (bI > 0 || bJ > 0) ? tphase_rounds(ph) : 0;
+      for (int r = 0; r < nrounds; ++r) {
+        const int ntasks = tphase_tasks(ph, r);
+        for (int k = wp; k < ntasks; k += nwp) {
+          TTask d;
+          if (!tphase_task(ph, r, k, d)) continue;
+          if (d.inner)
+            rot |= tile_group<TILE, true>(S, ldS, d.sa, d.na, d.sb, d.nb, d.na > 0, d.nb > 0, mq,
+                                          rq, ln, tol_t, floor_t, csw);
+          if (d.na > 0 && d.nb > 0)
+            rot |= tile_group<TILE, false>(S, ldS, d.sa, d.na, d.sb, d.nb, false, false, mq, rq,
+                                           ln, tol_t, floor_t, csw);
+        }
+        __syncthreads();
+      }
+      cluster_cols(S, ldS, WI, len, len, bI, tid, NTh, false);
+      cluster_cols(S + (int64_t)bc * ldS, ldS, WJ, len, len, bJ, tid, NTh, false);
+      cluster_barrier();
+    }
+    // sweep result: CTAs that rotated anything count themselves, then every
+    // CTA reads the count after one more cluster barrier
+    if (__syncthreads_or(rot) && tid == 0) atomicAdd(rot_count + sw, 1);
+    cluster_barrier();
+    sweeps_used = sw + 1;
+    converged = __ldcg(rot_count + sw) == 0;
+  }
+  if (cta != 0) return;
+  // CTA 0: column norms, descending sort, outputs (as in jacobi_kernel)
+  const int p2 = P.sort_n;
+  const size_t sig_off = ((size_t)2 * bc * ldS * sizeof(float) + 15) & ~(size_t)15;
+  double* sig = reinterpret_cast<double*>(smem_raw + sig_off);
+  int* idx = reinterpret_cast<int*>(sig + p2);
+  const int nwarps = NTh >> 5;
+  for (int c = wp; c < p2; c += nwarps) {
+    double acc = 0.0;
+    if (c < rc)
+      for (int r = ln; r < mm; r += 32) {
+        const double v = (double)__ldcg(W + r + (int64_t)c * len);
+        acc = fma(v, v, acc);
+      }
+    acc = warp_sum(acc);
+    if (ln == 0) {
+      sig[c] = (c < rc) ? sqrt(acc) : -1.0;
+      idx[c] = c;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= p2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < p2; i += NTh) {
+        const int l = i ^ j;
+        if (l > i) {
+          const double si = sig[i], sl = sig[l];
+          const int ii = idx[i], il = idx[l];
+          const bool i_first = (si > sl) || (si == sl && ii < il);
+          const bool up = ((i & k) == 0);
+          if (up ? !i_first : i_first) {
+            sig[i] = sl; sig[l] = si;
+            idx[i] = il; idx[l] = ii;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = tid; j < rc; j += NTh) {
+    P.sigma[j] = sig[j];
+    if (!isfinite(sig[j])) atomicOr(P.status, SMA_STATUS_BIT(SMA_ERR_NONFINITE));
+  }
+  for (int64_t e = tid; e < (int64_t)len * rc; e += NTh) {
+    const int r = (int)(e % len), j = (int)(e / len);
+    const float v = __ldcg(W + r + (int64_t)idx[j] * len);
+    if (r < mm) P.U[r + (int64_t)j * mm] = v;
+    else P.V[(r - mm) + (int64_t)j * rc] = v;
+  }
+  if (tid == 0) {
+    if (P.sweeps) *P.sweeps = sweeps_used;
+    if (!converged) atomicOr(P.status, SMA_STATUS_BIT(SMA_ERR_NOCONVERGE));
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -1822,6 +1988,58 @@ cudaError_t jacobi_svd_coop(const JacobiParams<T>& P, const JacobiPlan& pl, cons
   e = cudaLaunchCooperativeKernel((const void*)kern, dim3(pl.block_mode), dim3(pl.threads), args,
                                   pl.smem, st);
   if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+JacobiPlan jacobi_cluster_plan(int rows, int max_smem) {
+  JacobiPlan pl{};
+  pl.trans = 0;
+  pl.mm = pl.rc = rows;
+  pl.vec = 4;
+  pl.ldS = 2 * rows + 4;
+  const int nblk = 2 * kClusterCtas;
+  pl.bcols = (((rows + nblk - 1) / nblk) + 3) & ~3;
+  int p2 = 1;
+  while (p2 < rows) p2 <<= 1;
+  pl.sort_n = p2;
+  pl.g = 32;
+  pl.threads = 32 * kClusterWarps;
+  pl.tile = rows <= 128 ? 1 : 2;
+  pl.block_mode = kClusterCtas;   // CTAs of the cluster
+  pl.smem = (((size_t)2 * pl.bcols * pl.ldS * sizeof(float) + 15) & ~(size_t)15) +
+            (size_t)p2 * (sizeof(double) + sizeof(int)) + 16;
+  // fp32 float4 columns, a tile per 4 columns, at least one full tile per block
+  if (rows % 4 || rows > 256 || rows < 8 * kClusterCtas || pl.smem + 3072 > (size_t)max_smem)
+    pl.smem = 0;
+  return pl;
+}
+
+cudaError_t jacobi_svd_cluster(const JacobiParams<float>& P, const JacobiPlan& pl, int* rot_count,
+                               cudaStream_t st) {
+  if (pl.smem == 0 || P.mm != P.rc || P.trans != 0 || P.bcols != pl.bcols || P.ldS != pl.ldS ||
+      !P.W || !rot_count)
+    return cudaErrorInvalidValue;
+  void (*kern)(const JacobiParams<float>, int*) =
+      pl.tile == 2 ? jacobi_cluster_kernel<2> : jacobi_cluster_kernel<1>;
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(rot_count, 0, sizeof(int) * (size_t)P.max_sweeps, st)) != cudaSuccess)
+    return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterCtas);
+  cfg.blockDim = dim3(pl.threads);
+  cfg.dynamicSmemBytes = pl.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCtas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  JacobiParams<float> p = P;
+  if ((e = cudaLaunchKernelEx(&cfg, kern, p, rot_count)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

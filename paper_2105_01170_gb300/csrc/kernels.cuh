@@ -115,6 +115,15 @@ struct CoopSync {
   int* abort_flag;
 };
 template <typename T> JacobiPlan jacobi_coop_plan(int rows, int max_smem);
+// One square fp32 matrix of order rows (8 * CTAs <= rows <= 256, rows % 4 ==
+// 0) over a cluster of CTAs: 2 x CTAs blocks of bcols columns, one block pair
+// per CTA and round of a block tournament, the hardware cluster barrier
+// between rounds.  The plan's block_mode field holds the CTA count; smem == 0
+// when the shape does not qualify.  rot_count: max_sweeps ints in device
+// memory, cleared by the launcher; P.W: the (2 rows) x rows workspace.
+JacobiPlan jacobi_cluster_plan(int rows, int max_smem);
+cudaError_t jacobi_svd_cluster(const JacobiParams<float>& P, const JacobiPlan& pl, int* rot_count,
+                               cudaStream_t st);
 template <typename T>
 cudaError_t jacobi_svd_coop(const JacobiParams<T>& P, const JacobiPlan& pl, const CoopSync& cs,
                             cudaStream_t st);
