@@ -55,6 +55,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
 
   const bool a_col = (p.a_rs == 1);
   const bool b_col = (p.b_rs == 1);
+  // 16-row (column) groups of the tile that hold output (block-uniform): a
+  // tile of a small product skips the multiply-adds of its empty groups,
+  // which matters in fp64 (2 FMA per clock per SM): a 15 x 15 Gram does 1/16
+  // of the padded tile's work
+  const int gm = min(4, (M - m0 + 15) / 16), gn = min(4, (N - n0 + 15) / 16);
   int kbeg = p.dKoff ? p.dKoff[di] : 0;
   if (p.kchunk > 0) {
     kbeg = b1 * p.kchunk;
@@ -87,10 +92,18 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
       for (int i = 0; i < 4; ++i) a[i] = As[k][tx + 16 * i];
 #pragma unroll
       for (int j = 0; j < 4; ++j) b[j] = Bs[k][ty + 16 * j];
+      if (gm == 4 && gn == 4) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (i < gm && j < gn) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
     }
     __syncthreads();
   }

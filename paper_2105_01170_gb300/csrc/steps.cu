@@ -246,10 +246,101 @@ __device__ __forceinline__ int count_greater(const double* s, int rc, double v) 
   return lo;
 }
 
+// truncate_block for at most 32 slices, by warp 0 alone: the same sums in
+// the same order (a block sum over one busy warp adds only zeros after the
+// warp's own butterfly), so the same ranks bit for bit, without the block
+// barriers of the 70 bisection passes (the Gram truncations have p = 1).
+__device__ __forceinline__ void truncate_warp(const double* __restrict__ sigma, int rc, int p,
+                                              const double* normX2, double rel_tol,
+                                              int fixed_rank, int* ranks, int* off, double* err2,
+                                              int* iscal, double* suf, int energies) {
+  const int lane = threadIdx.x & 31;
+  const int i = lane;   // this lane's slice (p <= 32)
+  const bool own = i < p;
+  const double* s = sigma + (int64_t)i * rc;
+  double* E = suf + (int64_t)i * (rc + 1);
+  if (own) {
+    double acc = 0.0;
+    E[rc] = 0.0;
+    for (int j = rc - 1; j >= 0; --j) {
+      acc += energies ? fmax(s[j], 0.0) : s[j] * s[j];
+      E[j] = acc;
+    }
+  }
+  __syncwarp();
+  if (fixed_rank > 0) {
+    double disc = 0.0;
+    if (own) {
+      const int r = min(fixed_rank, rc);
+      ranks[i] = r;
+      disc = E[r];
+    }
+    disc = warp_sum(disc);
+    if (lane == 0) *err2 = disc;
+  } else {
+    const double budget = rel_tol * rel_tol * (*normX2);
+    const double mx = warp_max(own ? s[0] : 0.0);
+    unsigned long long lo = 0ull, hi = (unsigned long long)__double_as_longlong(mx);
+    for (int it = 0; it < 70 && lo < hi; ++it) {
+      const unsigned long long mid = lo + (hi - lo + 1) / 2;
+      const double v = __longlong_as_double((long long)mid);
+      double F = own ? E[count_greater(s, rc, v)] : 0.0;
+      F = warp_sum(F);   // identical in every lane
+      if (F <= budget) lo = mid; else hi = mid - 1;
+    }
+    const double vstar = __longlong_as_double((long long)lo);
+    double F = 0.0, vnext = INFINITY;
+    if (own) {
+      const int cg = count_greater(s, rc, vstar);
+      ranks[i] = cg;
+      F = E[cg];
+      if (cg > 0) vnext = s[cg - 1];
+    }
+    F = warp_sum(F);
+    vnext = -warp_max(-vnext);
+    __syncwarp();
+    if (lane == 0) {
+      double disc = F;
+      if (isfinite(vnext) && vnext > 0.0) {
+        const double e = energies ? vnext : vnext * vnext;
+        for (int q = p - 1; q >= 0; --q) {
+          const double* sq = sigma + (int64_t)q * rc;
+          int r = ranks[q];
+          while (r > 0 && sq[r - 1] == vnext && disc + e <= budget) {
+            disc += e;
+            --r;
+          }
+          ranks[q] = r;
+          if (!(disc + e <= budget)) break;
+        }
+      }
+      *err2 = disc;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    int acc = 0, nz = 0;
+    for (int q = 0; q < p; ++q) {
+      off[q] = acc;
+      acc += ranks[q];
+      nz += ranks[q] > 0;
+    }
+    off[p] = acc;
+    iscal[0] = acc;
+    iscal[1] = nz;
+  }
+}
+
 __device__ __forceinline__ void truncate_block(const double* __restrict__ sigma, int rc, int p,
                                                const double* normX2, double rel_tol,
                                                int fixed_rank, int* ranks, int* off, double* err2,
                                                int* iscal, double* suf, int energies) {
+  if (p <= 32) {   // (block-uniform) one warp does it all
+    if (threadIdx.x < 32)
+      truncate_warp(sigma, rc, p, normX2, rel_tol, fixed_rank, ranks, off, err2, iscal, suf,
+                    energies);
+    return;
+  }
   __shared__ double red[32];
   __shared__ unsigned long long s_lo, s_hi;
   const int tid = threadIdx.x;
