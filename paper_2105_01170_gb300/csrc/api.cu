@@ -296,12 +296,15 @@ struct Prob {
   T* Ys = nullptr;
   size_t Ys_elems = 0;
   // tcgen05 operands of the Kronecker-sum matvec (mixed path): Z^T and the
-  // concatenated terms D^T as three bf16 planes each, K-major
-  __nv_bfloat16* Zp = nullptr;
+  // concatenated terms D^T as two scaled fp16 planes each, K-major; tcmx:
+  // max |X|, max |C|, max row L1 of C, max |D|; tcsc: the scales from them
+  uint16_t* Zp = nullptr;
   size_t Zp_elems = 0;
   int64_t Zp_K = -1;
-  __nv_bfloat16* Dp = nullptr;
+  uint16_t* Dp = nullptr;
   size_t Dp_elems = 0;
+  unsigned* tcmx = nullptr;
+  float* tcsc = nullptr;
   // tcgen05 operands of the transform X x3 M (mixed t-SVDM)
   __nv_bfloat16* Xp = nullptr;             // X as [mn][Kp] planes
   __nv_bfloat16* Mp = nullptr;             // M as [p][Kp] planes
@@ -310,10 +313,10 @@ struct Prob {
   bool dp_valid = false;
   // tcgen05 operands of the mid-index contraction: the right-hand sides as
   // [(c + n s)][Kq] planes and the terms C_j as [(a + ell j)][Kq] planes
-  __nv_bfloat16* Xq = nullptr;
+  uint16_t* Xq = nullptr;
   size_t Xq_elems = 0;
   int64_t Xq_shape = -1;
-  __nv_bfloat16* Cq = nullptr;
+  uint16_t* Cq = nullptr;
   size_t Cq_elems = 0;
   bool cq_valid = false;
   // Section 5.2 (SMA_TUCKER_SPD): T_0 = L L^T is split off the diagonal and
@@ -2548,9 +2551,15 @@ sma_status grow(sma_ctx* h, T** buf, size_t* have, size_t need) {
 
 // Mixed-path Kronecker-sum matvec on tensor cores: Y^T = Z^T D^T with
 // Z = [X_s C_j^T] and D = [D_1 | ... | D_nt].  Both products run in tcgen05
-// kernels: the mid-index contraction (K = q) writes Z directly as the bf16
-// split planes of the long-K product's operand.  Returns false when the
-// shapes do not fit them (the caller then runs the CUDA-core form).
+// kernels on the fp16 two-piece split (x s = hi + lo with a power-of-two
+// scale s per operand that puts its largest entry below 2^15, the products
+// hi hi + hi lo + lo hi, fp32 accumulation): each piece carries 11 bits, the
+// pair 22, so a product term is exact to about 2^-21 relative, and half the
+// bf16 three-piece form's six products are needed.  The mid-index
+// contraction (K = q) writes Z directly as the scaled fp16 planes of the
+// long-K product's operand; its scale comes from the bound |Z| <= max |X|
+// max_a,j sum_b |C_j[a, b]|.  Returns false when the shapes do not fit the
+// kernels (the caller then runs the CUDA-core form).
 template <typename T>
 bool tc_apply(sma_ctx*, Prob<T>&, const T*, int64_t, T*, int64_t, int64_t, int, int) {
   return false;
@@ -2564,21 +2573,29 @@ bool tc_apply<float>(sma_ctx* h, Prob<float>& P, const float* X, int64_t ldx, fl
   const int64_t K = (int64_t)n * nt, Kp = tc_pad_k(K);
   const int64_t rowsZ = (int64_t)ell * nrhs;
   if (rowsZ > 0x7fffffff) return false;
-  const size_t zneed = (size_t)3 * rowsZ * Kp, dneed = (size_t)3 * m * Kp;
-  const __nv_bfloat16* zold = P.Zp;
+  const size_t zneed = (size_t)2 * rowsZ * Kp, dneed = (size_t)2 * m * Kp;
+  if (!P.tcmx) {
+    if (h->mem.alloc(&P.tcmx, 4) != SMA_OK || h->mem.alloc(&P.tcsc, 8) != SMA_OK) return false;
+    if (cudaMemsetAsync(P.tcmx, 0, 4 * sizeof(unsigned), st) != cudaSuccess) return false;
+  }
+  const uint16_t* zold = P.Zp;
   if (grow(h, &P.Zp, &P.Zp_elems, zneed) != SMA_OK) return false;
   if (P.Zp != zold) P.Zp_K = -1;   // a new buffer: its K padding is not zero yet
   if (grow(h, &P.Dp, &P.Dp_elems, dneed) != SMA_OK) return false;
   if (P.Zp_K != K) {  // zero the K padding once per shape
-    if (cudaMemsetAsync(P.Zp, 0, P.Zp_elems * sizeof(__nv_bfloat16), st) != cudaSuccess) return false;
+    if (cudaMemsetAsync(P.Zp, 0, P.Zp_elems * sizeof(uint16_t), st) != cudaSuccess) return false;
     P.Zp_K = K;
   }
   if (!P.dp_valid || P.Dp_K != K) {
     if (P.Dp_K != K &&
-        cudaMemsetAsync(P.Dp, 0, P.Dp_elems * sizeof(__nv_bfloat16), st) != cudaSuccess)
+        cudaMemsetAsync(P.Dp, 0, P.Dp_elems * sizeof(uint16_t), st) != cudaSuccess)
       return false;
-    ++h->launches;
-    if (tc_split_transpose(P.D, 1, m, m, (int)K, Kp, P.Dp, st) != cudaSuccess) return false;
+    h->launches += 3;
+    if (tc_absmax(P.D, m, K, m, P.tcmx + 3, st) != cudaSuccess ||
+        tc_f16_scales(P.tcmx, P.tcsc, st) != cudaSuccess ||
+        tc_split2_transpose_batched(P.D, 1, m, m, (int)K, Kp, 1, 0, 0, (int64_t)m * Kp,
+                                    P.tcsc + 2, P.Dp, st) != cudaSuccess)
+      return false;
     P.Dp_K = K;
     P.dp_valid = true;
   }
@@ -2589,31 +2606,42 @@ bool tc_apply<float>(sma_ctx* h, Prob<float>& P, const float* X, int64_t ldx, fl
   if (rowsX > 0x7fffffff || rowsC > 0x7fffffff || nrhs > 65535 || nt > 65535) return false;
   const int64_t xshape = rowsX * Kq;
   if (P.Xq_shape != xshape) {  // zero the K padding (b >= q) once per shape
-    if (grow(h, &P.Xq, &P.Xq_elems, (size_t)3 * rowsX * Kq) != SMA_OK) return false;
-    if (cudaMemsetAsync(P.Xq, 0, (size_t)3 * rowsX * Kq * sizeof(__nv_bfloat16), st) != cudaSuccess)
+    if (grow(h, &P.Xq, &P.Xq_elems, (size_t)2 * rowsX * Kq) != SMA_OK) return false;
+    if (cudaMemsetAsync(P.Xq, 0, (size_t)2 * rowsX * Kq * sizeof(uint16_t), st) != cudaSuccess)
       return false;
     P.Xq_shape = xshape;
   }
   if (!P.cq_valid) {
-    if (grow(h, &P.Cq, &P.Cq_elems, (size_t)3 * rowsC * Kq) != SMA_OK) return false;
-    if (cudaMemsetAsync(P.Cq, 0, (size_t)3 * rowsC * Kq * sizeof(__nv_bfloat16), st) != cudaSuccess)
+    if (grow(h, &P.Cq, &P.Cq_elems, (size_t)2 * rowsC * Kq) != SMA_OK) return false;
+    if (cudaMemsetAsync(P.Cq, 0, (size_t)2 * rowsC * Kq * sizeof(uint16_t), st) != cudaSuccess)
       return false;
-    ++h->launches;
-    if (tc_split_transpose_batched(P.C, 1, ell, ell, q, Kq, nt, (int64_t)ell * q, (int64_t)ell * Kq,
-                                   rowsC * Kq, P.Cq, st) != cudaSuccess)
+    h->launches += 4;
+    if (tc_absmax(P.C, (int64_t)ell * q, nt, (int64_t)ell * q, P.tcmx + 1, st) != cudaSuccess ||
+        tc_rowl1max(P.C, ell, q, nt, P.tcmx + 2, st) != cudaSuccess ||
+        tc_f16_scales(P.tcmx, P.tcsc, st) != cudaSuccess ||
+        tc_split2_transpose_batched(P.C, 1, ell, ell, q, Kq, nt, (int64_t)ell * q,
+                                    (int64_t)ell * Kq, rowsC * Kq, P.tcsc + 1, P.Cq, st) !=
+            cudaSuccess)
       return false;
     P.cq_valid = true;
   }
-  ++h->launches;
-  if (tc_split_transpose_batched(X, 1, n, n, q, Kq, nrhs, ldx, (int64_t)n * Kq, rowsX * Kq, P.Xq,
-                                 st) != cudaSuccess)
+  // the right-hand sides' scale, then every factor of this product
+  h->launches += 2;
+  if (tc_absmax(X, (int64_t)n * q, nrhs, ldx, P.tcmx, st) != cudaSuccess ||
+      tc_f16_scales(P.tcmx, P.tcsc, st) != cudaSuccess)
     return false;
   ++h->launches;
-  if (tc_mid_planes(P.Xq, (int)rowsX, P.Cq, (int)rowsC, Kq, P.Zp, Kp, rowsZ * Kp, n, ell, P.status,
-                    st) != cudaSuccess)
+  if (tc_split2_transpose_batched(X, 1, n, n, q, Kq, nrhs, ldx, (int64_t)n * Kq, rowsX * Kq,
+                                  P.tcsc, P.Xq, st) != cudaSuccess)
     return false;
   ++h->launches;
-  if (tc_gemm_planes(P.Zp, P.Dp, (int)rowsZ, m, Kp, Yd, m, P.status, st) != cudaSuccess) return false;
+  if (tc_mid_planes_f16(P.Xq, (int)rowsX, P.Cq, (int)rowsC, Kq, P.Zp, Kp, rowsZ * Kp, n, ell,
+                        P.tcsc + 4, P.status, st) != cudaSuccess)
+    return false;
+  ++h->launches;
+  if (tc_gemm_planes_f16(P.Zp, P.Dp, (int)rowsZ, m, Kp, Yd, m, P.tcsc + 5, P.status, st) !=
+      cudaSuccess)
+    return false;
   return true;
 }
 

@@ -25,8 +25,10 @@
 // frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "tc_gemm.cuh"
@@ -48,6 +50,15 @@ static_assert(THREADS == 320, "two control warps and eight epilogue warps");
 
 __constant__ int kProdA[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int kProdB[6] = {0, 1, 0, 2, 0, 1};
+// fp16 two-piece split (x = hi + lo): hi hi, hi lo, lo hi
+__constant__ int kProdA3[3] = {0, 0, 1};
+__constant__ int kProdB3[3] = {0, 1, 0};
+template <int NP> __device__ __forceinline__ int prod_a(int pr) {
+  return NP == 6 ? kProdA[pr] : kProdA3[pr];
+}
+template <int NP> __device__ __forceinline__ int prod_b(int pr) {
+  return NP == 6 ? kProdB[pr] : kProdB3[pr];
+}
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -110,10 +121,10 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   d |= (uint64_t)2 << 61;                 // 128-byte swizzle
   return d;
 }
-// kind::f16 instruction descriptor: fp32 accumulator, bf16 A and B, both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+// kind::f16 instruction descriptor: fp32 accumulator, bf16 (or, with f16,
+// fp16) A and B, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc16(int M, int N, bool f16) {
+  return (1u << 4) | (f16 ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
 __device__ __forceinline__ void mma(uint32_t dtm, uint64_t a, uint64_t b, uint32_t id,
@@ -151,8 +162,12 @@ struct TcArgs {
   int64_t ldc;
   int col_major;  // 0: C[i * ldc + j]; 1: C[i + j * ldc]
   int* err;
+  const float* scale;   // C is multiplied by *scale when set
 };
 
+// NP = 6: three bf16 planes per operand, six products; NP = 3: two fp16
+// planes per operand (scaled into fp16's range by the caller), three products.
+template <int NP>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                const TcArgs args) {
@@ -169,7 +184,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int nkb = args.Kp / BK;
-  const int total = nkb * 6;
+  const int total = nkb * NP;
   const int nch = (nkb + CHUNK - 1) / CHUNK;
 
   if (threadIdx.x == 0) {
@@ -208,11 +223,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         break;
       }
       if (*abort_flag) break;
-      const int kb = it / 6, pr = it % 6;
+      const int kb = it / NP, pr = it % NP;
       uint8_t* st = tiles + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_3d(st, &mapA, &full[s], kb * BK, m0, kProdA[pr]);
-      tma_load_3d(st + A_BYTES, &mapB, &full[s], kb * BK, n0, kProdB[pr]);
+      tma_load_3d(st, &mapA, &full[s], kb * BK, m0, prod_a<NP>(pr));
+      tma_load_3d(st + A_BYTES, &mapB, &full[s], kb * BK, n0, prod_b<NP>(pr));
       issued = it + 1;
     }
     // drain: the copies of the last stages must land before the CTA exits
@@ -220,7 +235,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       if (!mbar_wait(&full[it % STAGES], (uint32_t)(it / STAGES) & 1u)) *abort_flag = 1;
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: chunk c (CHUNK k-blocks) accumulates into buffer c & 1
-    const uint32_t id = idesc_bf16(BM, BN);
+    const uint32_t id = idesc16(BM, BN, NP == 3);
     int it = 0;
     for (int c = 0; c < nch && !*abort_flag; ++c) {
       const int b = c & 1;
@@ -230,7 +245,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       }
       fence_after();
       const uint32_t dt = tmem + (uint32_t)(b * BN);
-      const int it_end = min(total, (c + 1) * CHUNK * 6);
+      const int it_end = min(total, (c + 1) * CHUNK * NP);
       bool first = true;
       for (; it < it_end; ++it) {
         const int s = it % STAGES;
@@ -279,6 +294,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       if (lane == 0)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&acce[b])) : "memory");
     }
+    const float sc = args.scale ? *args.scale : 1.f;   // (a power of two: exact)
     if (!*abort_flag && grow < args.M && args.col_major) {
       // lanes hold consecutive rows: each store instruction is coalesced
       const int c0 = n0 + hc * 128;
@@ -286,7 +302,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       float* dst = args.C + grow + (int64_t)c0 * args.ldc;
 #pragma unroll
       for (int j = 0; j < 128; ++j)
-        if (j < nv) dst[(int64_t)j * args.ldc] = acc[j];
+        if (j < nv) dst[(int64_t)j * args.ldc] = acc[j] * sc;
     } else if (!*abort_flag && grow < args.M) {
       const int c0 = n0 + hc * 128;
       float* dst = args.C + (int64_t)grow * args.ldc + c0;
@@ -294,11 +310,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       if (nv >= 128 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
 #pragma unroll
         for (int j = 0; j < 128; j += 4)
-          *reinterpret_cast<float4*>(dst + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+          *reinterpret_cast<float4*>(dst + j) =
+              make_float4(acc[j] * sc, acc[j + 1] * sc, acc[j + 2] * sc, acc[j + 3] * sc);
       } else {
 #pragma unroll
         for (int j = 0; j < 128; ++j)
-          if (j < nv) dst[j] = acc[j];
+          if (j < nv) dst[j] = acc[j] * sc;
       }
     }
   }
@@ -332,9 +349,17 @@ struct MidArgs {
   int M, N, Kq, n, ell;
   int pairs;   // n even and Z, Kp, plane allow 32-bit stores of two rows
   int64_t Kp, plane;
-  __nv_bfloat16* Z;
+  uint16_t* Z;          // bf16 (three planes) or fp16 (two planes) elements
   int* err;
+  const float* mult;    // fp16 form: Z is scaled by *mult before the split
 };
+
+// x = hi + lo in fp16 (x already scaled into fp16's range)
+__device__ __forceinline__ void split2h(float x, uint16_t& hi, uint16_t& lo) {
+  const __half h = __float2half_rn(x);
+  hi = __half_as_ushort(h);
+  lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));
+}
 
 __device__ __forceinline__ void split3(float x, __nv_bfloat16& hi, __nv_bfloat16& mid,
                                        __nv_bfloat16& lo) {
@@ -344,6 +369,7 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& hi, __nv_bfloat16
   lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
 }
 
+template <int NP>
 __global__ void __launch_bounds__(MID_THREADS)
 tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const MidArgs args) {
@@ -358,7 +384,7 @@ tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int total = (args.Kq / BK) * 6;
+  const int total = (args.Kq / BK) * NP;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < MID_STAGES; ++s) {
@@ -392,17 +418,17 @@ tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         break;
       }
       if (*abort_flag) break;
-      const int kb = it / 6, pr = it % 6;
+      const int kb = it / NP, pr = it % NP;
       uint8_t* st = tiles + s * STAGE_BYTES;
       mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_3d(st, &mapA, &full[s], kb * BK, m0, kProdA[pr]);
-      tma_load_3d(st + A_BYTES, &mapB, &full[s], kb * BK, n0, kProdB[pr]);
+      tma_load_3d(st, &mapA, &full[s], kb * BK, m0, prod_a<NP>(pr));
+      tma_load_3d(st + A_BYTES, &mapB, &full[s], kb * BK, n0, prod_b<NP>(pr));
       issued = it + 1;
     }
     for (int it = (issued > MID_STAGES ? issued - MID_STAGES : 0); it < issued; ++it)
       if (!mbar_wait(&full[it % MID_STAGES], (uint32_t)(it / MID_STAGES) & 1u)) *abort_flag = 1;
   } else if (warp == 1 && lane == 0) {
-    const uint32_t id = idesc_bf16(BM, BN);
+    const uint32_t id = idesc16(BM, BN, NP == 3);
     for (int it = 0; it < total; ++it) {
       const int s = it % MID_STAGES;
       const uint32_t ph = (uint32_t)(it / MID_STAGES) & 1u;
@@ -423,6 +449,7 @@ tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     const int q = warp & 3;
     const int hp = (warp - 2) >> 2;   // which quarter of the columns
     const int grow = m0 + q * 32 + lane;
+    const float mult = (NP == 3 && args.mult) ? *args.mult : 1.f;
     const bool ok = mbar_wait(accf, 0u);
     fence_after();
     if (!ok) *abort_flag = 1;
@@ -456,16 +483,26 @@ tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
           }
           const int gj = g0 + 2 * kk + (odd ? 1 : 0);
           if (rows_ok && gj < args.N) {
-            __nv_bfloat16 h0, m0_, l0, h1, m1, l1;
-            split3(v0, h0, m0_, l0);
-            split3(v1, h1, m1, l1);
-            const uint32_t wh = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            const uint32_t wm = (uint32_t)__bfloat16_as_ushort(m0_) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
-            const uint32_t wl = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            __nv_bfloat16* d = args.Z + rbase + (int64_t)aj * args.Kp + (int64_t)args.n * tj;
-            asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d), "r"(wh) : "memory");
-            asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d + args.plane), "r"(wm) : "memory");
-            asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d + 2 * args.plane), "r"(wl) : "memory");
+            uint16_t* d = args.Z + rbase + (int64_t)aj * args.Kp + (int64_t)args.n * tj;
+            if (NP == 3) {
+              uint16_t h0, l0, h1, l1;
+              split2h(v0 * mult, h0, l0);
+              split2h(v1 * mult, h1, l1);
+              const uint32_t wh = (uint32_t)h0 | ((uint32_t)h1 << 16);
+              const uint32_t wl = (uint32_t)l0 | ((uint32_t)l1 << 16);
+              asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d), "r"(wh) : "memory");
+              asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d + args.plane), "r"(wl) : "memory");
+            } else {
+              __nv_bfloat16 h0, m0_, l0, h1, m1, l1;
+              split3(v0, h0, m0_, l0);
+              split3(v1, h1, m1, l1);
+              const uint32_t wh = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+              const uint32_t wm = (uint32_t)__bfloat16_as_ushort(m0_) | ((uint32_t)__bfloat16_as_ushort(m1) << 16);
+              const uint32_t wl = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+              asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d), "r"(wh) : "memory");
+              asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d + args.plane), "r"(wm) : "memory");
+              asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(d + 2 * args.plane), "r"(wl) : "memory");
+            }
           }
           a += 2;
           while (a >= args.ell) {
@@ -488,12 +525,19 @@ tc_mid_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj) {
             if (g0 + jj < args.N) {
-              __nv_bfloat16 hi, mi, lo;
-              split3(__uint_as_float(r[jj]), hi, mi, lo);
-              __nv_bfloat16* d = args.Z + rbase + (int64_t)a * args.Kp + (int64_t)args.n * t;
-              asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d), "h"(__bfloat16_as_ushort(hi)) : "memory");
-              asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d + args.plane), "h"(__bfloat16_as_ushort(mi)) : "memory");
-              asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d + 2 * args.plane), "h"(__bfloat16_as_ushort(lo)) : "memory");
+              uint16_t* d = args.Z + rbase + (int64_t)a * args.Kp + (int64_t)args.n * t;
+              if (NP == 3) {
+                uint16_t hi, lo;
+                split2h(__uint_as_float(r[jj]) * mult, hi, lo);
+                asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d), "h"(hi) : "memory");
+                asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d + args.plane), "h"(lo) : "memory");
+              } else {
+                __nv_bfloat16 hi, mi, lo;
+                split3(__uint_as_float(r[jj]), hi, mi, lo);
+                asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d), "h"(__bfloat16_as_ushort(hi)) : "memory");
+                asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d + args.plane), "h"(__bfloat16_as_ushort(mi)) : "memory");
+                asm volatile("st.global.cs.u16 [%0], %1;" ::"l"(d + 2 * args.plane), "h"(__bfloat16_as_ushort(lo)) : "memory");
+              }
             }
             if (++a == args.ell) {
               a = 0;
@@ -545,6 +589,89 @@ __global__ void split_transpose_kernel(const float* __restrict__ src, int64_t s_
   }
 }
 
+// fp32 -> two fp16 planes of x * (*scale), with transposition (as above)
+__global__ void split2_transpose_kernel(const float* __restrict__ src, int64_t s_rs, int64_t s_cs,
+                                        int R, int K, int64_t Kp, uint16_t* __restrict__ dst,
+                                        int64_t plane, int64_t src_bs, int64_t dst_bs,
+                                        const float* __restrict__ scale) {
+  __shared__ float tile[32][33];
+  const int j0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const float sc = *scale;
+  src += (int64_t)blockIdx.z * src_bs;
+  dst += (int64_t)blockIdx.z * dst_bs;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int k = k0 + i, j = j0 + threadIdx.x;
+    tile[i][threadIdx.x] = (j < R && k < K) ? src[(int64_t)j * s_rs + (int64_t)k * s_cs] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int j = j0 + i, k = k0 + threadIdx.x;
+    if (j < R && k < K) {
+      uint16_t hi, lo;
+      split2h(tile[threadIdx.x][i] * sc, hi, lo);
+      const int64_t o = (int64_t)j * Kp + k;
+      dst[o] = hi;
+      dst[o + plane] = lo;
+    }
+  }
+}
+
+// *out = max(*out, max |a[r + ld c]|) over r < rows, c < cols, on the bit
+// patterns of non-negative floats (NaN ignored)
+__global__ void absmax_kernel(const float* __restrict__ a, int64_t rows, int64_t cols, int64_t ld,
+                              unsigned* __restrict__ out) {
+  float m = 0.f;
+  const int64_t tot = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / rows, r = e - c * rows;
+    m = fmaxf(m, fabsf(a[r + c * ld]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+// *out = max over (a, j) of sum_b |C_j[a, b]|, C_j[a, b] = C[a + ell b + ell q j]
+__global__ void rowl1max_kernel(const float* __restrict__ C, int ell, int q, int nt,
+                                unsigned* __restrict__ out) {
+  float m = 0.f;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < ell * nt;
+       idx += gridDim.x * blockDim.x) {
+    const int a = idx % ell, j = idx / ell;
+    const float* c = C + a + (int64_t)ell * q * j;
+    float sum = 0.f;
+    for (int b = 0; b < q; ++b) sum += fabsf(c[(int64_t)ell * b]);
+    m = fmaxf(m, sum);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+// 2^(14 - e) for a maximum m = 1.x 2^e (1 for m = 0 or not finite): m s < 2^15
+__device__ __forceinline__ float pow2_scale(float m) {
+  if (!(m > 0.f) || !isfinite(m)) return 1.f;
+  const int e = max(-100, min(100, ilogbf(m)));
+  return ldexpf(1.f, 14 - e);
+}
+// mx: max |X|, max |C|, max row L1 of C, max |D|; sc: s_X, s_C, s_D, s_Z,
+// s_Z / (s_X s_C) (the mid product's factor), 1 / (s_Z s_D) (the output's);
+// |Z| <= max |X| max row L1 (C), so Z s_Z < 2^15 as well.  All powers of two.
+__global__ void f16_scales_kernel(const unsigned* __restrict__ mx, float* __restrict__ sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const float mX = __uint_as_float(mx[0]), mC = __uint_as_float(mx[1]);
+  const float mL = __uint_as_float(mx[2]), mD = __uint_as_float(mx[3]);
+  const float sX = pow2_scale(mX), sC = pow2_scale(mC), sD = pow2_scale(mD);
+  const float sZ = pow2_scale(mX * mL);
+  sc[0] = sX;
+  sc[1] = sC;
+  sc[2] = sD;
+  sc[3] = sZ;
+  sc[4] = sZ / (sX * sC);
+  sc[5] = 1.f / (sZ * sD);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -561,14 +688,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* map, const __nv_bfloat16* planes, int rows, int64_t Kp, int box_rows) {
+bool make_map(CUtensorMap* map, const void* planes, int rows, int64_t Kp, int box_rows,
+              int nplanes = 3, bool f16 = false) {
   auto fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 3};
+  const cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)nplanes};
   const cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Kp * 2 * rows};
   const cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(planes), dims,
+  return fn(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+            const_cast<void*>(planes), dims,
             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -609,11 +738,28 @@ cudaError_t tc_gemm_planes(const __nv_bfloat16* A, const __nv_bfloat16* B, int M
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, Kp, BM) || !make_map(&mb, B, N, Kp, BN)) return cudaErrorInvalidValue;
   const cudaError_t attr = cudaFuncSetAttribute(
-      tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      tc_gemm_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
-  TcArgs a{M, N, (int)Kp, C, ldc, col_major ? 1 : 0, err};
+  TcArgs a{M, N, (int)Kp, C, ldc, col_major ? 1 : 0, err, nullptr};
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+  tc_gemm_kernel<6><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_planes_f16(const uint16_t* A, const uint16_t* B, int M, int N, int64_t Kp,
+                               float* C, int64_t ldc, const float* scale, int* err,
+                               cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (Kp % BK != 0 || Kp <= 0 || (N + BN - 1) / BN > 65535) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, Kp, BM, 2, true) || !make_map(&mb, B, N, Kp, BN, 2, true))
+    return cudaErrorInvalidValue;
+  const cudaError_t attr = cudaFuncSetAttribute(
+      tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (attr != cudaSuccess) return attr;
+  TcArgs a{M, N, (int)Kp, C, ldc, 0, err, scale};
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  tc_gemm_kernel<3><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
   return cudaGetLastError();
 }
 
@@ -626,15 +772,74 @@ cudaError_t tc_mid_planes(const __nv_bfloat16* A, int M, const __nv_bfloat16* B,
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, M, Kq, BM) || !make_map(&mb, B, N, Kq, BN)) return cudaErrorInvalidValue;
   const cudaError_t attr = cudaFuncSetAttribute(
-      tc_mid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MID_SMEM);
+      tc_mid_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, MID_SMEM);
   if (attr != cudaSuccess) return attr;
   const int pairs = (n % 2 == 0 && M % 2 == 0 && Kp % 2 == 0 && zplane % 2 == 0 &&
                      (reinterpret_cast<uintptr_t>(Z) & 3) == 0)
                         ? 1
                         : 0;
-  MidArgs a{M, N, (int)Kq, n, ell, pairs, Kp, zplane, Z, err};
+  MidArgs a{M, N, (int)Kq, n, ell, pairs, Kp, zplane, reinterpret_cast<uint16_t*>(Z), err,
+            nullptr};
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
-  tc_mid_kernel<<<grid, MID_THREADS, MID_SMEM, st>>>(ma, mb, a);
+  tc_mid_kernel<6><<<grid, MID_THREADS, MID_SMEM, st>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_mid_planes_f16(const uint16_t* A, int M, const uint16_t* B, int N, int64_t Kq,
+                              uint16_t* Z, int64_t Kp, int64_t zplane, int n, int ell,
+                              const float* mult, int* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (Kq % BK != 0 || Kq <= 0 || n <= 0 || ell <= 0 || !mult) return cudaErrorInvalidValue;
+  if ((M + BM - 1) / BM > 0x7fffffff || (N + BN - 1) / BN > 65535) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, Kq, BM, 2, true) || !make_map(&mb, B, N, Kq, BN, 2, true))
+    return cudaErrorInvalidValue;
+  const cudaError_t attr = cudaFuncSetAttribute(
+      tc_mid_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, MID_SMEM);
+  if (attr != cudaSuccess) return attr;
+  const int pairs = (n % 2 == 0 && M % 2 == 0 && Kp % 2 == 0 && zplane % 2 == 0 &&
+                     (reinterpret_cast<uintptr_t>(Z) & 3) == 0)
+                        ? 1
+                        : 0;
+  MidArgs a{M, N, (int)Kq, n, ell, pairs, Kp, zplane, Z, err, mult};
+  dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
+  tc_mid_kernel<3><<<grid, MID_THREADS, MID_SMEM, st>>>(ma, mb, a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_split2_transpose_batched(const float* src, int64_t s_rs, int64_t s_cs, int R, int K,
+                                        int64_t Kp, int nbatch, int64_t src_bs, int64_t dst_bs,
+                                        int64_t plane, const float* scale, uint16_t* dst,
+                                        cudaStream_t st) {
+  if (R <= 0 || K <= 0 || nbatch <= 0) return cudaSuccess;
+  if (nbatch > 65535 || !scale) return cudaErrorInvalidValue;
+  dim3 grid((R + 31) / 32, (K + 31) / 32, nbatch);
+  split2_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(src, s_rs, s_cs, R, K, Kp, dst, plane,
+                                                       src_bs, dst_bs, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_absmax(const float* a, int64_t rows, int64_t cols, int64_t ld, unsigned* out,
+                      cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess || rows <= 0 || cols <= 0) return e;
+  const int64_t tot = rows * cols;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 2048);
+  absmax_kernel<<<blocks, 256, 0, st>>>(a, rows, cols, ld, out);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_rowl1max(const float* C, int ell, int q, int nt, unsigned* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess || ell <= 0 || q <= 0 || nt <= 0) return e;
+  const int64_t tot = (int64_t)ell * nt;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 1024);
+  rowl1max_kernel<<<blocks, 256, 0, st>>>(C, ell, q, nt, out);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_f16_scales(const unsigned* mx, float* sc, cudaStream_t st) {
+  f16_scales_kernel<<<1, 32, 0, st>>>(mx, sc);
   return cudaGetLastError();
 }
 
