@@ -26,9 +26,11 @@
  *     X[:, :, k] = sqrt(eta_k) A_k (the paper's m x p x n tensor with modes 2
  *     and 3 swapped).
  *   - Precision SMA_FP64 takes and returns double; SMA_MIXED takes and returns
- *     float (transform, Gram and matvec contractions as 3-piece bf16 products
- *     on tensor cores with fp32 accumulation; Jacobi SVD in fp32 with fp64
- *     rotation angles; fp64 energy sums).
+ *     float (the transform as 3-piece bf16 products and the Kronecker-sum
+ *     matvec as 2-piece fp16 products of power-of-two-scaled operands, on
+ *     tensor cores with fp32 accumulation; unfolding Grams in fp64; Jacobi
+ *     SVD in fp32 with fp64 rotation angles for nearly parallel columns;
+ *     fp64 energy sums).
  *   - Pointers to A, X and Y may be device memory or host memory; host
  *     buffers are copied on the handle's stream (only the bytes the call
  *     needs), except a page-locked (pinned) host A of a one-level problem,
