@@ -501,8 +501,11 @@ def cfg_hankel(torch, S, stream, flush, steps, alu_peak):
     out["oracle_sample"] = "r = 10: gather, both mode SVDs, core and the 256-RHS matvec (FP64 numpy)"
     out["workload"] = ("LTI block Hankel 2048^2 (64 x 64 blocks of 32 x 32), rows-and-columns "
                        "Tucker BLR at r = 5/10/20, 256-RHS matvec")
-    out["roofline"] = {"bound": "alu", "kernel": "the BLR matvec's products (CUDA cores)",
-                       "note": "apply_alu_frac per rank against the derived FP32 peak; the "
+    out["roofline"] = {"bound": "latency", "kernel": "the BLR matvec's three products",
+                       "note": "the core product on tcgen05 (fp16 two-piece split) from "
+                               "r = 5 on, the two projections on CUDA cores; 0.1 ms per "
+                               "256-RHS apply, launch- and latency-bound; apply_alu_frac is the "
+                               "fp32-equivalent rate against the derived FP32 peak; the "
                                "compression is two small Gram eigen-solves (latency-bound)"}
     return out
 

@@ -319,6 +319,20 @@ struct Prob {
   uint16_t* Cq = nullptr;
   size_t Cq_elems = 0;
   bool cq_valid = false;
+  // tcgen05 operands of the block-low-rank and SPD matvecs: the compressed
+  // factors (the A operands of their products) as scaled fp16 planes, built
+  // on first use after a compression
+  struct TcOperand {
+    const void* src = nullptr;
+    int M = 0, K = 0;
+    int64_t rs = 0, cs = 0, Kp = 0;
+    uint16_t* planes = nullptr;
+    size_t elems = 0;
+    unsigned* mx = nullptr;   // max |A|
+    float* s = nullptr;       // its power-of-two scale
+    bool valid = false;
+  };
+  std::vector<TcOperand> tca;
   // Section 5.2 (SMA_TUCKER_SPD): T_0 = L L^T is split off the diagonal and
   // every field above describes the inner problem of the A_k = L^-1 T_k L^-T
   bool spd = false;
@@ -400,6 +414,12 @@ struct sma_ctx {
   double acc_ms[SMA_STAGE_COUNT] = {0};
   int64_t acc_calls[SMA_STAGE_COUNT] = {0};
   int64_t launches = 0;
+  // the B operand of the block-low-rank matvecs' tcgen05 products (scaled
+  // fp16 planes), its maximum and the product's scales
+  uint16_t* tcb = nullptr;
+  size_t tcb_elems = 0;
+  unsigned* tcb_mx = nullptr;
+  float* tcb_sc = nullptr;
   // many-problem t-SVDM: the problems' transforms (independent products,
   // each on its own buffers) fan out over these streams, forked from and
   // joined back into the handle's stream by events (graph capture records
@@ -2284,6 +2304,7 @@ sma_status compress_one(sma_ctx* h, Prob<T>& P, const void* A, int64_t lda,
   else SMA_TRY(compress_tucker(h, P));
   P.compressed = true;
   P.dp_valid = false;
+  for (auto& o : P.tca) o.valid = false;
   P.cq_valid = false;
   P.h_iscal[0] = -1;
   return SMA_OK;
@@ -2429,6 +2450,7 @@ sma_status enqueue_compress(sma_ctx* h, const void* const* A, const int64_t* lda
     for (auto& P : ps) {
       P.compressed = true;
       P.dp_valid = false;
+      for (auto& o : P.tca) o.valid = false;
       P.cq_valid = false;
       P.h_iscal[0] = -1;
     }
@@ -2461,6 +2483,7 @@ void mark_compressed(sma_ctx* h) {
   for (auto& P : probs<T>(h)) {
     P.compressed = true;
     P.dp_valid = false;
+    for (auto& o : P.tca) o.valid = false;
     P.cq_valid = false;
     P.ml_valid = false;
     P.ml_cvalid = false;
@@ -2643,6 +2666,85 @@ bool tc_apply<float>(sma_ctx* h, Prob<float>& P, const float* X, int64_t ldx, fl
       cudaSuccess)
     return false;
   return true;
+}
+
+// The fp32 products of the block-low-rank and SPD matvecs, C = A B with A a
+// factor of the compressed form (W^T, the structured core, U, L^T, L) and B
+// the right-hand sides or an intermediate, on tcgen05 in the fp16 two-piece
+// form of the Kronecker-sum matvec when they are large: A's scaled planes are
+// built once per compression and cached (keyed by pointer, shape and
+// strides), B's each call; the output scale 1 / (s_A s_B) is applied in the
+// GEMM's epilogue.  A batch over nb2 is folded into the columns when B's and
+// C's batches continue their columns.  Other shapes, and the fp64 path, take
+// the CUDA-core product.
+template <typename T>
+sma_status contract_apply(sma_ctx* h, Prob<T>&, const GemmParams<T>& g) {
+  SMA_K(contract<T>(h, g));
+  return SMA_OK;
+}
+template <>
+sma_status contract_apply<float>(sma_ctx* h, Prob<float>& P, const GemmParams<float>& g) {
+  cudaStream_t st = h->st;
+  int64_t N = g.N;
+  bool ok = h->tc_ok && !g.dM && !g.dN && !g.dK && !g.dKoff && !g.c_off && !g.Cs &&
+            g.kchunk == 0 && g.alpha == 1.f && g.beta == 0.f && g.nb1 == 1 &&
+            (g.c_rs == 1 || g.c_cs == 1);
+  if (ok && g.nb2 > 1) {
+    ok = g.a_b2 == 0 && g.b_b2 == (int64_t)g.N * g.b_cs && g.c_b2 == (int64_t)g.N * g.c_cs;
+    N = (int64_t)g.N * g.nb2;
+  }
+  ok = ok && g.M >= 128 && N >= 128 && g.K >= 64 && N <= 0x7fffffff &&
+       (double)g.M * (double)N * (double)g.K >= 268435456.0 && (N + 255) / 256 <= 65535;
+  if (!ok) {
+    SMA_K(contract<float>(h, g));
+    return SMA_OK;
+  }
+  const int M = g.M, K = g.K;
+  const int64_t Kp = tc_pad_k(K);
+  // A: the cached factor planes
+  Prob<float>::TcOperand* op = nullptr;
+  for (auto& o : P.tca)
+    if (o.src == g.A && o.M == M && o.K == K && o.rs == g.a_rs && o.cs == g.a_cs) op = &o;
+  if (!op) {
+    P.tca.emplace_back();
+    op = &P.tca.back();
+    op->src = g.A; op->M = M; op->K = K; op->rs = g.a_rs; op->cs = g.a_cs;
+  }
+  if (!op->valid) {
+    if (!op->mx) {
+      SMA_TRY(h->mem.alloc(&op->mx, 1));
+      SMA_TRY(h->mem.alloc(&op->s, 1));
+    }
+    SMA_TRY(grow(h, &op->planes, &op->elems, (size_t)2 * M * Kp));
+    op->Kp = Kp;
+    if (Kp > K)   // the K padding of both planes
+      SMA_CK(cudaMemset2DAsync(op->planes + K, Kp * sizeof(uint16_t), 0,
+                               (Kp - K) * sizeof(uint16_t), (size_t)2 * M, st));
+    h->launches += 3;
+    SMA_CK(tc_absmax_strided(g.A, M, K, g.a_rs, g.a_cs, op->mx, st));
+    SMA_CK(tc_f16_scale1(op->mx, op->s, st));
+    SMA_CK(tc_split2_transpose_batched(g.A, g.a_rs, g.a_cs, M, K, Kp, 1, 0, 0, (int64_t)M * Kp,
+                                       op->s, op->planes, st));
+    op->valid = true;
+  }
+  // B (element (j, k) at B[k b_rs + j b_cs]) each call
+  if (!h->tcb_mx) {
+    SMA_TRY(h->mem.alloc(&h->tcb_mx, 1));
+    SMA_TRY(h->mem.alloc(&h->tcb_sc, 2));
+  }
+  SMA_TRY(grow(h, &h->tcb, &h->tcb_elems, (size_t)2 * N * Kp));
+  if (Kp > K)
+    SMA_CK(cudaMemset2DAsync(h->tcb + K, Kp * sizeof(uint16_t), 0, (Kp - K) * sizeof(uint16_t),
+                             (size_t)2 * N, st));
+  h->launches += 4;
+  SMA_CK(tc_absmax_strided(g.B, N, K, g.b_cs, g.b_rs, h->tcb_mx, st));
+  SMA_CK(tc_f16_scale_out(op->mx, h->tcb_mx, h->tcb_sc, st));
+  SMA_CK(tc_split2_transpose_batched(g.B, g.b_cs, g.b_rs, (int)N, K, Kp, 1, 0, 0, N * Kp,
+                                     h->tcb_sc, h->tcb, st));
+  const bool col = g.c_rs == 1;
+  SMA_CK(tc_gemm_planes_f16(op->planes, h->tcb, M, (int)N, Kp, g.C, col ? g.c_cs : g.c_rs,
+                            h->tcb_sc + 1, P.status, st, col));
+  return SMA_OK;
 }
 
 // Section 7.4 matvec y = sum_j G_j (C1_j1 (x) C2_j2 (x) C3_j3) x for volumes
@@ -2859,14 +2961,14 @@ sma_status apply_core(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, in
     g.B = X; g.b_rs = 1; g.b_cs = n; g.b_b2 = ldx;
     g.C = P.Z; g.c_rs = 1; g.c_cs = r3max; g.c_b2 = (int64_t)r3max * q;
     g.nb2 = nrhs;
-    SMA_K(contract<T>(h, g));
+    SMA_TRY(contract_apply<T>(h, P, g));
     // Z2 = mid Z   ((ell r1max) x nrhs)
     GemmParams<T> g2;
     g2.M = ell * r1max; g2.N = nrhs; g2.K = q * r3max;
     g2.A = P.mid; g2.a_rs = 1; g2.a_cs = (int64_t)ell * r1max;
     g2.B = P.Z; g2.b_rs = 1; g2.b_cs = (int64_t)q * r3max;
     g2.C = P.Z2; g2.c_rs = 1; g2.c_cs = (int64_t)ell * r1max;
-    SMA_K(contract<T>(h, g2));
+    SMA_TRY(contract_apply<T>(h, P, g2));
     // Y_s[:, a] = U Z2_s[:, a]
     GemmParams<T> g3;
     g3.M = m; g3.N = ell; g3.K = r1max;
@@ -2874,7 +2976,7 @@ sma_status apply_core(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, in
     g3.B = P.Z2; g3.b_rs = 1; g3.b_cs = r1max; g3.b_b2 = (int64_t)ell * r1max;
     g3.C = Yd; g3.c_rs = 1; g3.c_cs = m; g3.c_b2 = ldyd;
     g3.nb2 = nrhs;
-    SMA_K(contract<T>(h, g3));
+    SMA_TRY(contract_apply<T>(h, P, g3));
   }
   return SMA_OK;
 }
@@ -2899,7 +3001,7 @@ sma_status spd_apply(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, int
   } else {
     g.N = ell; g.b_b2 = ldx; g.c_b2 = rows; g.nb2 = nrhs;
   }
-  SMA_K(contract<T>(h, g));
+  SMA_TRY(contract_apply<T>(h, P, g));
   SMA_TRY(apply_core(h, P, P.Sx, rows, P.Sy, rows, nrhs));
   SMA_K(add_into<T>(P.Sx, rows, P.Sy, rows, rows, nrhs, st));
   // Y_s[:, a] = L Y'_s[:, a]
@@ -2913,7 +3015,7 @@ sma_status spd_apply(sma_ctx* h, Prob<T>& P, const T* X, int64_t ldx, T* Yd, int
   } else {
     g2.N = ell; g2.b_b2 = rows; g2.c_b2 = ldyd; g2.nb2 = nrhs;
   }
-  SMA_K(contract<T>(h, g2));
+  SMA_TRY(contract_apply<T>(h, P, g2));
   return SMA_OK;
 }
 

@@ -616,16 +616,33 @@ __global__ void split2_transpose_kernel(const float* __restrict__ src, int64_t s
   }
 }
 
-// *out = max(*out, max |a[r + ld c]|) over r < rows, c < cols, on the bit
-// patterns of non-negative floats (NaN ignored)
-__global__ void absmax_kernel(const float* __restrict__ a, int64_t rows, int64_t cols, int64_t ld,
-                              unsigned* __restrict__ out) {
+// The same planes from a source whose k is contiguous (s_cs = 1): rows j,
+// k along the threads, coalesced on both sides without a transposition.
+__global__ void split2_rows_kernel(const float* __restrict__ src, int64_t s_rs, int R, int K,
+                                   int64_t Kp, uint16_t* __restrict__ dst, int64_t plane,
+                                   const float* __restrict__ scale) {
+  const float sc = *scale;
+  const int64_t tot = (int64_t)R * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / K, k = e - j * K;
+    uint16_t hi, lo;
+    split2h(src[j * s_rs + k] * sc, hi, lo);
+    dst[j * Kp + k] = hi;
+    dst[j * Kp + k + plane] = lo;
+  }
+}
+
+// *out = max(*out, max |a[r rs + c cs]|) over r < rows, c < cols, on the
+// bit patterns of non-negative floats (NaN ignored)
+__global__ void absmax_kernel(const float* __restrict__ a, int64_t rows, int64_t cols, int64_t rs,
+                              int64_t cs, unsigned* __restrict__ out) {
   float m = 0.f;
   const int64_t tot = rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = e / rows, r = e - c * rows;
-    m = fmaxf(m, fabsf(a[r + c * ld]));
+    m = fmaxf(m, fabsf(a[r * rs + c * cs]));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -670,6 +687,18 @@ __global__ void f16_scales_kernel(const unsigned* __restrict__ mx, float* __rest
   sc[3] = sZ;
   sc[4] = sZ / (sX * sC);
   sc[5] = 1.f / (sZ * sD);
+}
+
+// s = the scale of one operand; out = {s_B, 1 / (s_A s_B)} of a product
+__global__ void f16_scale1_kernel(const unsigned* __restrict__ mx, float* __restrict__ s) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) s[0] = pow2_scale(__uint_as_float(mx[0]));
+}
+__global__ void f16_scale_out_kernel(const unsigned* __restrict__ mxA,
+                                     const unsigned* __restrict__ mxB, float* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const float sA = pow2_scale(__uint_as_float(mxA[0])), sB = pow2_scale(__uint_as_float(mxB[0]));
+  out[0] = sB;
+  out[1] = 1.f / (sA * sB);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -748,7 +777,7 @@ cudaError_t tc_gemm_planes(const __nv_bfloat16* A, const __nv_bfloat16* B, int M
 
 cudaError_t tc_gemm_planes_f16(const uint16_t* A, const uint16_t* B, int M, int N, int64_t Kp,
                                float* C, int64_t ldc, const float* scale, int* err,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool col_major) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   if (Kp % BK != 0 || Kp <= 0 || (N + BN - 1) / BN > 65535) return cudaErrorInvalidValue;
   CUtensorMap ma, mb;
@@ -757,7 +786,7 @@ cudaError_t tc_gemm_planes_f16(const uint16_t* A, const uint16_t* B, int M, int 
   const cudaError_t attr = cudaFuncSetAttribute(
       tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (attr != cudaSuccess) return attr;
-  TcArgs a{M, N, (int)Kp, C, ldc, 0, err, scale};
+  TcArgs a{M, N, (int)Kp, C, ldc, col_major ? 1 : 0, err, scale};
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN);
   tc_gemm_kernel<3><<<grid, THREADS, SMEM_BYTES, st>>>(ma, mb, a);
   return cudaGetLastError();
@@ -813,6 +842,12 @@ cudaError_t tc_split2_transpose_batched(const float* src, int64_t s_rs, int64_t 
                                         cudaStream_t st) {
   if (R <= 0 || K <= 0 || nbatch <= 0) return cudaSuccess;
   if (nbatch > 65535 || !scale) return cudaErrorInvalidValue;
+  if (s_cs == 1 && s_rs != 1 && nbatch == 1) {
+    const int64_t tot = (int64_t)R * K;
+    const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 8192);
+    split2_rows_kernel<<<blocks, 256, 0, st>>>(src, s_rs, R, K, Kp, dst, plane, scale);
+    return cudaGetLastError();
+  }
   dim3 grid((R + 31) / 32, (K + 31) / 32, nbatch);
   split2_transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(src, s_rs, s_cs, R, K, Kp, dst, plane,
                                                        src_bs, dst_bs, scale);
@@ -825,7 +860,32 @@ cudaError_t tc_absmax(const float* a, int64_t rows, int64_t cols, int64_t ld, un
   if (e != cudaSuccess || rows <= 0 || cols <= 0) return e;
   const int64_t tot = rows * cols;
   const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 2048);
-  absmax_kernel<<<blocks, 256, 0, st>>>(a, rows, cols, ld, out);
+  absmax_kernel<<<blocks, 256, 0, st>>>(a, rows, cols, 1, ld, out);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_absmax_strided(const float* a, int64_t rows, int64_t cols, int64_t rs, int64_t cs,
+                              unsigned* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess || rows <= 0 || cols <= 0) return e;
+  if (cs == 1 && rs != 1) {   // the unit stride along the threads
+    std::swap(rows, cols);
+    std::swap(rs, cs);
+  }
+  const int64_t tot = rows * cols;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 2048);
+  absmax_kernel<<<blocks, 256, 0, st>>>(a, rows, cols, rs, cs, out);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_f16_scale1(const unsigned* mx, float* s, cudaStream_t st) {
+  f16_scale1_kernel<<<1, 32, 0, st>>>(mx, s);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_f16_scale_out(const unsigned* mxA, const unsigned* mxB, float* out,
+                             cudaStream_t st) {
+  f16_scale_out_kernel<<<1, 32, 0, st>>>(mxA, mxB, out);
   return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ cudaError_t tc_mid_planes(const __nv_bfloat16* A, int M, const __nv_bfloat16* B,
 // patterns, two per operand.  C is multiplied by *scale (device).
 cudaError_t tc_gemm_planes_f16(const uint16_t* A, const uint16_t* B, int M, int N, int64_t Kp,
                                float* C, int64_t ldc, const float* scale, int* err,
-                               cudaStream_t st);
+                               cudaStream_t st, bool col_major = false);
 // The mid-index product in the fp16 form: Z is multiplied by *mult (device)
 // and written as two fp16 planes.
 cudaError_t tc_mid_planes_f16(const uint16_t* A, int M, const uint16_t* B, int N, int64_t Kq,
@@ -55,6 +55,13 @@ cudaError_t tc_split2_transpose_batched(const float* src, int64_t s_rs, int64_t 
 // *out = max |a[r + ld c]| (r < rows, c < cols) as the bit pattern of a float
 cudaError_t tc_absmax(const float* a, int64_t rows, int64_t cols, int64_t ld, unsigned* out,
                       cudaStream_t st);
+// *out = max |a[r rs + c cs]| (r < rows, c < cols) as the bit pattern of a float
+cudaError_t tc_absmax_strided(const float* a, int64_t rows, int64_t cols, int64_t rs, int64_t cs,
+                              unsigned* out, cudaStream_t st);
+// *s = the power-of-two scale for the maximum *mx; out = {s_B, 1 / (s_A s_B)}
+cudaError_t tc_f16_scale1(const unsigned* mx, float* s, cudaStream_t st);
+cudaError_t tc_f16_scale_out(const unsigned* mxA, const unsigned* mxB, float* out,
+                             cudaStream_t st);
 // *out = max over (a, j) of sum_b |C[a + ell b + ell q j]|
 cudaError_t tc_rowl1max(const float* C, int ell, int q, int nt, unsigned* out, cudaStream_t st);
 // sc[0..5] = s_X, s_C, s_D, s_Z, s_Z / (s_X s_C), 1 / (s_Z s_D) from mx[0..3] =
