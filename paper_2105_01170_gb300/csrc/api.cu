@@ -3304,7 +3304,7 @@ sma_status build_bins(sma_ctx* h) {
   std::vector<std::vector<PostDesc<T>>> post(bs.size());
   for (auto& P : ps) {
     if (P.qr || ps.size() < 2) continue;
-    const size_t smem = sizeof(T) * ((size_t)P.jp.mm * P.rc + (size_t)P.rc * P.rc);
+    const size_t smem = sizeof(T) * ((size_t)P.jp.mm * P.rc + (size_t)P.rc * P.rc + P.rc);
     if (smem > (size_t)h->max_smem) continue;
     size_t bi = 0;
     for (; bi < bs.size(); ++bi)

@@ -65,6 +65,9 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmParams<T> p) {
     kbeg = b1 * p.kchunk;
     K = min(K, kbeg + p.kchunk);
   }
+  // an empty K range with beta = 1 leaves C as it is (the truncated rebuild
+  // of a slice that discards nothing): nothing to read or write
+  if (kbeg >= K && p.beta == T(1) && !p.Cs) return;
   for (int k0 = kbeg; k0 < K; k0 += BK) {
 #pragma unroll
     for (int t = 0; t < (BM * BK) / NT; ++t) {

@@ -959,32 +959,69 @@ namespace {
 // for the defect) are staged in shared memory when they fit; the rebuild
 // reads Xhat and writes D once, column by column.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 slice_post_kernel(const PostDesc<T>* __restrict__ desc, int m, int n, int mm, int rc, int trans) {
   extern __shared__ __align__(16) unsigned char post_raw[];
   T* Ws = reinterpret_cast<T*>(post_raw);     // mm x rc
   T* Vs = Ws + (size_t)mm * rc;                // rc x rc
+  T* inv = Vs + (size_t)rc * rc;               // rc: 1 / sigma_a (0 where sigma_a is 0)
   __shared__ double red[32];
   const PostDesc<T> d = desc[blockIdx.x];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int r = min(max(*d.rank, 0), rc);
-  for (int e = tid; e < mm * rc; e += nth) Ws[e] = d.W[e];
-  for (int e = tid; e < rc * rc; e += nth) Vs[e] = d.V[e];
+  if (sizeof(T) == 4 && (mm * rc) % 4 == 0 && (rc * rc) % 4 == 0) {
+    // 16-byte loads (each slice's W and V start on 16-byte boundaries then)
+    const float4* w4 = reinterpret_cast<const float4*>(d.W);
+    const float4* v4 = reinterpret_cast<const float4*>(d.V);
+    float4* ws4 = reinterpret_cast<float4*>(Ws);
+    float4* vs4 = reinterpret_cast<float4*>(Vs);
+    for (int e = tid; e < (mm * rc) / 4; e += nth) ws4[e] = w4[e];
+    for (int e = tid; e < (rc * rc) / 4; e += nth) vs4[e] = v4[e];
+  } else {
+    for (int e = tid; e < mm * rc; e += nth) Ws[e] = d.W[e];
+    for (int e = tid; e < rc * rc; e += nth) Vs[e] = d.V[e];
+  }
+  const double smin = sizeof(T) == 4 ? 1e-30 : 0.0;
+  for (int a = tid; a < r; a += nth) inv[a] = d.sigma[a] > smin ? (T)(1.0 / d.sigma[a]) : T(0);
   __syncthreads();
   // D = Xhat - sum_{j >= r} (left_j)(right_j)^T; left = W (trans: V), right = V (W)
   const T* Lf = trans ? Vs : Ws;
   const T* Rf = trans ? Ws : Vs;
   const int ldl = trans ? rc : mm, ldr = trans ? mm : rc;
-  for (int e = tid; e < m * n; e += nth) {
-    const int i = e % m, c = e / m;
-    T acc = d.Xh[e];
-    for (int j = r; j < rc; ++j) acc = fma(-Lf[i + (int64_t)ldl * j], Rf[c + (int64_t)ldr * j], acc);
-    d.D[e] = acc;
+  // by 4 x 4 tiles of D (each element's multiply-adds in the same order as
+  // one element at a time; 8 shared loads per 16 products)
+  const int mt = (m + 3) >> 2, ntl = (n + 3) >> 2;
+  for (int e = tid; e < mt * ntl; e += nth) {
+    const int i0 = 4 * (e % mt), c0 = 4 * (e / mt);
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        acc[u][v] = (i0 + u < m && c0 + v < n) ? d.Xh[(i0 + u) + (int64_t)m * (c0 + v)] : T(0);
+    for (int j = r; j < rc; ++j) {
+      T lv[4], rv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        lv[u] = i0 + u < m ? Lf[i0 + u + (int64_t)ldl * j] : T(0);
+        rv[u] = c0 + u < n ? Rf[c0 + u + (int64_t)ldr * j] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(-lv[u], rv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (i0 + u < m && c0 + v < n) d.D[(i0 + u) + (int64_t)m * (c0 + v)] = acc[u][v];
   }
   // max |w_a . w_b / (sigma_a sigma_b) - delta_ab| over a <= b < r, by 4 x 4
   // tiles of the Gram (each thread one tile pair at a time: 8 shared loads
-  // per 16 products)
-  double mx = 0.0;
+  // per 16 products); the scaling by the staged reciprocals in the element
+  // type (as orth_kernel)
+  T mxt = T(0);
   const int nt = (r + 3) >> 2;
   for (int e = tid; e < nt * nt; e += nth) {
     const int ta = e % nt, tb = e / nt;
@@ -1013,13 +1050,12 @@ slice_post_kernel(const PostDesc<T>* __restrict__ desc, int m, int n, int mm, in
       for (int v = 0; v < 4; ++v) {
         const int a = a0 + u, b = b0 + v;
         if (a >= r || b >= r || a > b) continue;
-        const double sa = d.sigma[a], sb = d.sigma[b];
-        const double gn = (sa > 0.0 && sb > 0.0) ? (double)g[u][v] / (sa * sb)
-                                                 : (a == b ? 1.0 : 0.0);
-        mx = fmax(mx, fabs(gn - (a == b ? 1.0 : 0.0)));
+        const T ia = inv[a], ib = inv[b];
+        const T gn = (ia > T(0) && ib > T(0)) ? g[u][v] * ia * ib : (a == b ? T(1) : T(0));
+        mxt = fmax(mxt, fabs(gn - (a == b ? T(1) : T(0))));
       }
   }
-  mx = warp_max(mx);
+  double mx = warp_max((double)mxt);
   if ((tid & 31) == 0) red[tid >> 5] = mx;
   __syncthreads();
   if (tid < 32) {
@@ -1034,13 +1070,17 @@ template <typename T>
 cudaError_t slice_post(const PostDesc<T>* d, int count, int m, int n, int mm, int rc, int trans,
                        cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
-  const size_t smem = sizeof(T) * ((size_t)mm * rc + (size_t)rc * rc);
+  const size_t smem = sizeof(T) * ((size_t)mm * rc + (size_t)rc * rc + rc);
   cudaError_t e = cudaFuncSetAttribute(slice_post_kernel<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // about eight slice elements per thread: small slices take small CTAs
+  // the largest shared-memory carveout, so that several CTAs fit per SM
+  e = cudaFuncSetAttribute(slice_post_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           100);
+  if (e != cudaSuccess) return e;
+  // about one 4 x 4 tile of the slice per thread: small slices take small CTAs
   int threads = 32;
-  while (threads < 256 && threads * 8 < m * n) threads <<= 1;
+  while (threads < 256 && threads * 16 < m * n) threads <<= 1;
   slice_post_kernel<T><<<count, threads, smem, st>>>(d, m, n, mm, rc, trans);
   return cudaGetLastError();
 }
