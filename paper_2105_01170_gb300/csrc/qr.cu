@@ -27,6 +27,8 @@
 // recomputed exactly after every step from the updated column (it is in
 // registers anyway), so no downdating formula is involved.
 #include <algorithm>
+#include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -983,6 +985,413 @@ __global__ void __launch_bounds__(QF_THREADS, 1)
   }
 }
 
+// ---- fp32 slices of at most 256 x 256 with every column resident ----------
+// The factorisations above keep the active columns in shared-memory slots
+// (and a global overflow) and let any warp update any column, so every step
+// goes through column pointers and the generic load/store path.  Here each of
+// the QRR_WARPS warps owns a fixed set of columns for the whole
+// factorisation: its first QRR_REG slots in registers, the rest in the warp's
+// own shared-memory slots; lane l holds the float4 rows l + 32 i of each.
+// A step of the column-pivoted QR takes
+//   (1) every warp's largest remaining partial norm (kept by lane j for slot
+//       j), one block barrier, the same block-wide argmax in every warp: a
+//       max over the norms' bit patterns (non-negative floats order like
+//       their bits), ties to the lowest warp and slot;
+//   (2) the owner of the pivot column forms the Householder reflector (same
+//       scalars as qrcp_kernel), writes it to shared memory, retires the
+//       column into F (R above the diagonal, beta, the reflector tail) and
+//       moves its last active column into the freed slot, so a warp's active
+//       columns are always its first slots; one block barrier;
+//   (3) every warp applies the reflector to its active columns, four at a
+//       time (their inner products reduced together), and downdates their
+//       partial norms from the new row-k entries (exact recompute when the
+//       downdate has lost most of its digits).
+// Without pivoting (the second QR) the pivot of step k is column k, step (1)
+// and its barrier drop out, and the reflector buffer alternates between two
+// copies, so one barrier per step remains; slot j holds column
+// warp + QRR_WARPS (ns - 1 - j), so the columns retire from the last slot
+// down and the register slots stay active longest.  Outputs as qrcp_kernel:
+// F, tau, perm (position -> column), Jin = R1^T.
+constexpr int QRR_THREADS = 512;
+constexpr int QRR_WARPS = QRR_THREADS / 32;
+constexpr int QRR_SLOTS = 16;   // columns per warp: rc <= QRR_WARPS * QRR_SLOTS
+constexpr int QRR_REG = 4;      // of them in registers
+constexpr int QRR_MAX = QRR_WARPS * QRR_SLOTS;
+
+__host__ __device__ constexpr int qrr_nq(int mm) { return ((mm + 3) / 4 + 31) / 32; }
+
+size_t qr_res_smem(int mm, int rc) {
+  const size_t mq = (size_t)((mm + 3) / 4);
+  const int ns = (rc + QRR_SLOTS - 1) / QRR_SLOTS;
+  const int nsm = ns > QRR_REG ? ns - QRR_REG : 0;
+  return (2 + (size_t)nsm * QRR_WARPS) * mq * sizeof(float4);
+}
+
+__device__ __forceinline__ float f4c(const float4& a, int e) {
+  return e == 0 ? a.x : e == 1 ? a.y : e == 2 ? a.z : a.w;
+}
+
+__device__ __forceinline__ float dot4f(const float4& a, const float4& b, float acc) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+}
+
+__device__ __forceinline__ float4 axpy4(float s, const float4& v, const float4& x) {
+  return make_float4(fmaf(s, v.x, x.x), fmaf(s, v.y, x.y), fmaf(s, v.z, x.z), fmaf(s, v.w, x.w));
+}
+
+// sum over the rows r > k held by this lane of (nsc x_r)^2
+template <int NQ>
+__device__ __forceinline__ float tail_sq(const float4 (&x)[NQ], int k, int mm, int lane,
+                                         float nsc) {
+  float a = 0.f;
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) {
+    const int r0 = 4 * (lane + 32 * i);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = r0 + e;
+      if (r > k && r < mm) {
+        const float z = f4c(x[i], e) * nsc;
+        a = fmaf(z, z, a);
+      }
+    }
+  }
+  return a;
+}
+
+// The reflector of step k applied to four columns, float4 rows from I0 on
+// (rows below 128 I0 are zero in v); the lane holding row k stores the
+// updated row-k entries to yk[4].
+template <int NQ, int I0>
+__device__ __forceinline__ void qrr_apply4(float4 (&x)[4][NQ], const float4 (&vr)[NQ], float tk,
+                                           int lane, int klane, int ki, int ke, float* yk) {
+  float w[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    float a = 0.f;
+#pragma unroll
+    for (int i = I0; i < NQ; ++i) a = dot4f(vr[i], x[c][i], a);
+    w[c] = a;
+  }
+  warp_sum4(w, lane);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float tw = -tk * w[c];
+#pragma unroll
+    for (int i = I0; i < NQ; ++i) x[c][i] = axpy4(tw, vr[i], x[c][i]);
+  }
+  if (lane == klane) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float y = 0.f;
+#pragma unroll
+      for (int i = 0; i < NQ; ++i)
+        if (i == ki) y = f4c(x[c][i], ke);
+      yk[c] = y;
+    }
+  }
+}
+
+// the block-wide winner of a max over unsigned keys (0: no candidate) held
+// one per lane of each warp: ties to the lowest warp, then the lowest lane;
+// returns warp * 32 + lane (the lane part in the winning warp only).  One
+// block barrier.
+__device__ __forceinline__ int qrr_argmax(unsigned key, unsigned* ck, int warp, int lane) {
+  const unsigned m = __reduce_max_sync(0xffffffffu, key);
+  const unsigned b = __ballot_sync(0xffffffffu, key == m);
+  if (lane == 0) ck[warp] = m;
+  __syncthreads();
+  const unsigned kw = lane < QRR_WARPS ? ck[lane] : 0u;
+  const unsigned mw = __reduce_max_sync(0xffffffffu, kw);
+  const int ww = __ffs(__ballot_sync(0xffffffffu, kw == mw)) - 1;
+  // the lane within warp ww is known to warp ww (its own ballot), the only
+  // warp that needs it
+  return ww * 32 + ((warp == ww) ? (__ffs(b) - 1) : 0);
+}
+
+template <int NQ, bool PIVOT>
+__global__ void __launch_bounds__(QRR_THREADS, 1) qr_res_kernel(const QrParams<float> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned ck[QRR_WARPS];
+  __shared__ float yk_s[QRR_WARPS][QRR_SLOTS];
+  __shared__ float tau_s[2];
+  __shared__ float rv[32];
+  __shared__ float sh_nsc;
+  const int s = blockIdx.x;
+  const int mm = P.mm, rc = P.rc, mq = (mm + 3) >> 2;
+  const int ns = (rc + QRR_SLOTS - 1) / QRR_SLOTS;   // slots per warp
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float4* vS = reinterpret_cast<float4*>(smem_raw);   // [2][mq] reflectors
+  const int sstr = QRR_WARPS * mq;                    // float4s between a warp's slots
+  float4* wS = vS + 2 * mq + warp * mq;               // this warp's slot QRR_REG
+  const float* src = P.src + (int64_t)s * P.src_bs;
+  float* F = P.F + (int64_t)s * P.F_bs;
+  float* yk = yk_s[warp];
+  auto slot_ptr = [&](int j) { return wS + (j - QRR_REG) * sstr; };
+  // the column initially in slot j (>= rc: absent)
+  auto col0 = [&](int j) {
+    return PIVOT ? warp + QRR_WARPS * j : warp + QRR_WARPS * (ns - 1 - j);
+  };
+
+  // load the columns (B[r, c] = slice[r, c], or slice[c, r] when trans)
+  float4 xr[QRR_REG][NQ];
+#pragma unroll
+  for (int j = 0; j < QRR_REG; ++j)
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) xr[j][i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  float amax = 0.f;
+  unsigned act = 0;   // active slots (PIVOT: always the first na)
+#pragma unroll
+  for (int j = 0; j < QRR_SLOTS; ++j) {
+    if (j >= ns) break;
+    const int c = col0(j);
+    const bool have = c < rc;
+    if (have) act |= 1u << j;
+#pragma unroll
+    for (int i = 0; i < NQ; ++i) {
+      const int q = lane + 32 * i;
+      float e4[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 4 * q + e;
+        e4[e] = (have && r < mm) ? load_slice(src, P.m, P.trans, r, c) : 0.f;
+        amax = fmaxf(amax, fabsf(e4[e]));
+      }
+      const float4 v4 = make_float4(e4[0], e4[1], e4[2], e4[3]);
+      if (j < QRR_REG) {
+#pragma unroll
+        for (int jj = 0; jj < QRR_REG; ++jj)
+          if (jj == j) xr[jj][i] = v4;
+      } else if (q < mq) {
+        slot_ptr(j)[q] = v4;
+      }
+    }
+  }
+  amax = block_max(amax, rv);
+  if (tid == 0) {
+    const int ex = (amax > 0.f && isfinite(amax)) ? min(max(ilogb(amax), -100), 100) : -1;
+    sh_nsc = ldexpf(1.f, -ex - 1);
+  }
+  __syncthreads();
+  const float nsc = sh_nsc;
+  // lane j: the column in slot j and its scaled squared partial norm
+  int mycol = lane < QRR_SLOTS ? col0(lane) : 0;
+  float nrm = 0.f, nrm0 = 0.f;
+  if (PIVOT) {
+#pragma unroll
+    for (int j = 0; j < QRR_SLOTS; ++j) {
+      if (j >= ns) break;
+      float4 x[NQ];
+#pragma unroll
+      for (int i = 0; i < NQ; ++i) {
+        const int q = lane + 32 * i;
+        if (j < QRR_REG) {
+#pragma unroll
+          for (int jj = 0; jj < QRR_REG; ++jj)
+            if (jj == j) x[i] = xr[jj][i];
+        } else {
+          x[i] = q < mq ? slot_ptr(j)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      const float a = warp_sum(tail_sq<NQ>(x, -1, mm, lane, nsc));
+      if (lane == j) nrm = nrm0 = a;
+    }
+  }
+
+  for (int k = 0; k < rc; ++k) {
+    const int buf = k & 1;
+    float4* vk = vS + buf * mq;
+    // (1) the pivot: warp ow, slot oj
+    int ow, oj;
+    if (PIVOT) {
+      const bool mine = (act >> lane) & 1u;   // (lanes >= QRR_SLOTS: 0)
+      const unsigned key = mine ? (nrm > 0.f ? __float_as_uint(nrm) + 1u : 1u) : 0u;
+      const int wl = qrr_argmax(key, ck, warp, lane);
+      ow = wl >> 5;
+      oj = wl & 31;   // valid in warp ow only
+    } else {
+      ow = k % QRR_WARPS;
+      oj = ns - 1 - k / QRR_WARPS;
+    }
+    // (2) its owner forms the reflector and retires the column
+    const int klane = (k >> 2) & 31, ki = k >> 7, ke = k & 3;
+    if (ow == warp) {
+      float4 x[NQ];
+#pragma unroll
+      for (int i = 0; i < NQ; ++i) {
+        const int q = lane + 32 * i;
+        if (oj < QRR_REG) {
+          x[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int jj = 0; jj < QRR_REG; ++jj)
+            if (jj == oj) x[i] = xr[jj][i];
+        } else {
+          x[i] = q < mq ? slot_ptr(oj)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+      }
+      const float s2 = warp_sum(tail_sq<NQ>(x, k, mm, lane, nsc));
+      float al = 0.f;
+#pragma unroll
+      for (int i = 0; i < NQ; ++i)
+        if (i == ki) al = f4c(x[i], ke);
+      const float alpha = __shfl_sync(0xffffffffu, al, klane);
+      const float alpha_s = alpha * nsc;
+      float tk = 0.f, beta = alpha, scale = 1.f;
+      if (s2 != 0.f) {
+        const float beta_s = -copysignf(sqrtf(fmaf(alpha_s, alpha_s, s2)), alpha_s);
+        tk = (beta_s - alpha_s) / beta_s;
+        beta = beta_s / nsc;
+        scale = nsc / (alpha_s - beta_s);
+      }
+      float* Fk = F + (int64_t)k * mm;
+#pragma unroll
+      for (int i = 0; i < NQ; ++i) {
+        const int q = lane + 32 * i;
+        float vv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = 4 * q + e;
+          const float xv = f4c(x[i], e);
+          float out, ve;
+          if (r < k) {
+            out = xv;
+            ve = 0.f;
+          } else if (r == k) {
+            out = beta;
+            ve = 1.f;
+          } else {
+            out = xv * scale;
+            ve = out;
+          }
+          vv[e] = r < mm ? ve : 0.f;
+          if (r < mm) Fk[r] = out;
+        }
+        if (q < mq) vk[q] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+      }
+      const int pcol = __shfl_sync(0xffffffffu, mycol, oj);
+      if (lane == 0) {
+        tau_s[buf] = tk;
+        P.tau[(int64_t)s * rc + k] = tk;
+        P.perm[(int64_t)s * rc + k] = pcol;
+      }
+      if (PIVOT) {
+        // the last active slot e moves into the freed slot oj
+        const int e = 31 - __clz(act);
+        if (e != oj) {
+          float4 t[NQ];
+#pragma unroll
+          for (int i = 0; i < NQ; ++i) {
+            const int q = lane + 32 * i;
+            if (e < QRR_REG) {
+              t[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+              for (int jj = 0; jj < QRR_REG; ++jj)
+                if (jj == e) t[i] = xr[jj][i];
+            } else {
+              t[i] = q < mq ? slot_ptr(e)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (oj < QRR_REG) {
+#pragma unroll
+              for (int jj = 0; jj < QRR_REG; ++jj)
+                if (jj == oj) xr[jj][i] = t[i];
+            } else if (q < mq) {
+              slot_ptr(oj)[q] = t[i];
+            }
+          }
+          const float ne = __shfl_sync(0xffffffffu, nrm, e);
+          const float ne0 = __shfl_sync(0xffffffffu, nrm0, e);
+          const int ce = __shfl_sync(0xffffffffu, mycol, e);
+          if (lane == oj) {
+            nrm = ne;
+            nrm0 = ne0;
+            mycol = ce;
+          }
+        }
+        act &= ~(1u << e);
+      } else {
+        act &= ~(1u << oj);
+      }
+    }
+    __syncthreads();
+    // (3) every warp: the reflector on its active columns
+    if (act != 0u) {
+      const float tk = tau_s[buf];
+      float4 vr[NQ];
+#pragma unroll
+      for (int i = 0; i < NQ; ++i) {
+        const int q = lane + 32 * i;
+        vr[i] = q < mq ? vk[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const bool hi_only = NQ == 2 && k >= 128;
+#pragma unroll
+      for (int g = 0; g < QRR_SLOTS / 4; ++g) {
+        if (((act >> (4 * g)) & 0xfu) == 0u) continue;
+        float4 x[4][NQ];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int i = 0; i < NQ; ++i) {
+            const int j = 4 * g + c, q = lane + 32 * i;
+            if (g == 0) x[c][i] = xr[c][i];
+            else x[c][i] = (q < mq && (!hi_only || i > 0)) ? slot_ptr(j)[q]
+                                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        if (hi_only) qrr_apply4<NQ, (NQ > 1 ? 1 : 0)>(x, vr, tk, lane, klane, ki, ke, yk + 4 * g);
+        else qrr_apply4<NQ, 0>(x, vr, tk, lane, klane, ki, ke, yk + 4 * g);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int i = 0; i < NQ; ++i) {
+            const int j = 4 * g + c, q = lane + 32 * i;
+            if (g == 0) xr[c][i] = x[c][i];
+            else if (q < mq && (!hi_only || i > 0)) slot_ptr(j)[q] = x[c][i];
+          }
+      }
+    }
+    if (PIVOT) {
+      __syncwarp();
+      // partial norms without row k; exact recompute on cancellation
+      const bool mine = (act >> lane) & 1u;
+      float nn = 0.f;
+      bool rec = false;
+      if (mine) {
+        const float y = yk[lane] * nsc;
+        nn = nrm - y * y;
+        rec = !(nn > 1e-3f * nrm0);
+      }
+      const unsigned rm = __ballot_sync(0xffffffffu, rec);
+      if (mine && !rec) nrm = nn;
+      if (rm != 0u) {
+#pragma unroll
+        for (int j = 0; j < QRR_SLOTS; ++j) {
+          if (!((rm >> j) & 1u)) continue;
+          float4 x[NQ];
+#pragma unroll
+          for (int i = 0; i < NQ; ++i) {
+            const int q = lane + 32 * i;
+            if (j < QRR_REG) {
+#pragma unroll
+              for (int jj = 0; jj < QRR_REG; ++jj)
+                if (jj == j) x[i] = xr[jj][i];
+            } else {
+              x[i] = q < mq ? slot_ptr(j)[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
+          const float a = warp_sum(tail_sq<NQ>(x, k, mm, lane, nsc));
+          if (lane == j) nrm = nrm0 = a;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // Jacobi input R1^T (rc x rc, lower triangular)
+  float* J = P.Jin + (int64_t)s * P.J_bs;
+  for (int e = tid; e < rc * rc; e += QRR_THREADS) {
+    const int r = e % rc, c = e / rc;
+    J[r + (int64_t)c * rc] = (c <= r) ? F[c + (int64_t)r * mm] : 0.f;
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -1003,9 +1412,38 @@ QrPlan qr_plan(int mm, int rc, int max_smem) {
   return q;
 }
 
+namespace {
+bool qr_res_fits(int mm, int rc) {
+  if (mm < 1 || rc < 1 || mm > 4 * 32 * 2 || rc > QRR_MAX || rc > mm) return false;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  return qr_res_smem(mm, rc) + 2048 <= (size_t)optin;
+}
+
+template <int NQ, bool PIVOT>
+cudaError_t qr_res_launch(const QrParams<float>& P, int nslices, cudaStream_t st) {
+  const size_t smem = qr_res_smem(P.mm, P.rc);
+  cudaError_t e = cudaFuncSetAttribute(qr_res_kernel<NQ, PIVOT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  qr_res_kernel<NQ, PIVOT><<<nslices, QRR_THREADS, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <bool PIVOT>
+cudaError_t qr_res(const QrParams<float>& P, int nslices, cudaStream_t st) {
+  return qrr_nq(P.mm) == 1 ? qr_res_launch<1, PIVOT>(P, nslices, st)
+                           : qr_res_launch<2, PIVOT>(P, nslices, st);
+}
+}  // namespace
+
 template <typename T>
 cudaError_t qrcp(const QrParams<T>& P, int nslices, cudaStream_t st) {
   if (nslices <= 0) return cudaSuccess;
+  if constexpr (std::is_same<T, float>::value)
+    if (qr_res_fits(P.mm, P.rc)) return qr_res<true>(P, nslices, st);
   if (P.plan.novf > 0 && !P.G) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(qrcp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)P.plan.smem_qr);
@@ -1018,6 +1456,8 @@ template <typename T>
 cudaError_t qr_blocked(const QrParams<T>& P, int nslices, cudaStream_t st) {
   if (nslices <= 0) return cudaSuccess;
   if (P.rc > kQrWarpRows || P.mm != P.rc || P.rc < 1) return cudaErrorInvalidValue;
+  if constexpr (std::is_same<T, float>::value)
+    if (qr_res_fits(P.mm, P.rc)) return qr_res<false>(P, nslices, st);
   qr_blocked_kernel<T><<<nslices, QbThreads<T>::v, 0, st>>>(P);
   return cudaGetLastError();
 }
