@@ -887,7 +887,6 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     SMA_TRY(mem.alloc(&P.sweeps, p));
     SMA_TRY(mem.alloc(&P.ranks, p));
     SMA_TRY(mem.alloc(&P.off, p + 1));
-    SMA_TRY(mem.alloc(&P.Gorth, (size_t)P.rc * P.rc * p));
     SMA_TRY(mem.alloc(&P.orth, p));
     P.n_orth = p;
     P.nterms_max = p;
@@ -1472,15 +1471,8 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P, bool truncated) {
   stage_begin(h, SMA_STAGE_REPORT);
   {
     const int jmm = P.jp.mm;
-    const int64_t ubs = (int64_t)jmm * rc;
-    GemmParams<T> g;
-    g.M = rc; g.N = rc; g.K = jmm; g.dM = P.ranks; g.dN = P.ranks;
-    g.A = P.U; g.a_rs = jmm; g.a_cs = 1; g.a_b1 = ubs;
-    g.B = P.U; g.b_rs = 1; g.b_cs = jmm; g.b_b1 = ubs;
-    g.C = P.Gorth; g.c_rs = 1; g.c_cs = rc; g.c_b1 = (int64_t)rc * rc;
-    g.nb1 = p;
-    SMA_K(gemm<T>(g, st));
-    SMA_K(orth_defect<T>(P.Gorth, rc, p, P.ranks, P.sigma, P.orth, st));
+    SMA_K(orth_gram_defect<T>(P.U, jmm, (int64_t)jmm * rc, jmm, rc, p, P.ranks, P.sigma, P.orth,
+                              st));
   }
   stage_end(h);
   return SMA_OK;

@@ -231,6 +231,12 @@ cudaError_t scatter_ME(const int* map, const double* inv_sqrt_eta, int ell, int 
 template <typename T>
 cudaError_t orth_defect(const T* Gm, int rc, int p, const int* ranks, const double* scale,
                         double* out, cudaStream_t st);
+// The same defect for Gm = W_i^T W_i (W_i: the K x rc block of slice i, ld
+// ldw, slices w_bs apart) without forming the Grams; zeroes out[p] first.
+template <typename T>
+cudaError_t orth_gram_defect(const T* W, int ldw, int64_t w_bs, int K, int rc, int p,
+                             const int* ranks, const double* scale, double* out,
+                             cudaStream_t st);
 // ---- multilevel (three levels, m = n = 1) ---------------------------------
 struct MlMaps {
   const int* map[3];

@@ -583,6 +583,116 @@ __global__ void orth_kernel(const T* __restrict__ Gm, int rc, const int* __restr
   }
 }
 
+// The defect of the retained columns straight from the factor: for slice i,
+// max over a, b < r_i of |(W^T W)[a, b] / (s_a s_b) - delta_ab| with W the
+// K x rc column block of the slice (ld ldw).  One CTA per 64 x 64 tile
+// (a-tile <= b-tile) of the leading r_i x r_i block: the two column tiles
+// pass through shared memory 32 rows at a time, each thread accumulates a
+// 4 x 4 block of the tile in registers (in T: fp32 on the mixed path, as the
+// products of the unfused form), and the epilogue scales, takes the largest
+// deviation and merges it into out[i] by an integer max on the bits (the
+// deviations are non-negative doubles, which order like their bit patterns).
+// No Gram is written.  out must be zero on entry.
+constexpr int OG_TILE = 64;
+constexpr int OG_KC = 32;
+constexpr int OG_LD = OG_TILE + 4;   // row stride of a staged tile (16-byte rows)
+
+template <typename T>
+__device__ __forceinline__ void og_load4(const T* p, T (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    const double2 q0 = *reinterpret_cast<const double2*>(p);
+    const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    orth_gram_kernel(const T* __restrict__ Wall, int ldw, int64_t w_bs, int K, int rc,
+                     const int* __restrict__ ranks, const double* __restrict__ sigma,
+                     unsigned long long* __restrict__ out) {
+  __shared__ __align__(16) T As[OG_KC][OG_LD];
+  __shared__ __align__(16) T Bs[OG_KC][OG_LD];
+  __shared__ T inv_a[OG_TILE], inv_b[OG_TILE];
+  __shared__ double red[8];
+  const int i = blockIdx.y;
+  const int r = ranks ? min(max(ranks[i], 0), rc) : rc;
+  const int nt = (rc + OG_TILE - 1) / OG_TILE;
+  int t = blockIdx.x, ta = 0;
+  while (ta < nt && t >= nt - ta) {
+    t -= nt - ta;
+    ++ta;
+  }
+  const int tb = ta + t;
+  const int a0 = ta * OG_TILE, b0 = tb * OG_TILE;
+  if (ta >= nt || b0 >= r) return;   // (uniform over the CTA)
+  const T* W = Wall + (int64_t)i * w_bs;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const double smin = sizeof(T) == 4 ? 1e-30 : 0.0;
+  if (tid < 2 * OG_TILE) {
+    const int c = (tid < OG_TILE ? a0 : b0) + (tid & (OG_TILE - 1));
+    const double sv = (c < r && sigma) ? sigma[(int64_t)i * rc + c] : 1.0;
+    const T iv = (c < r) ? (sigma ? (sv > smin ? (T)(1.0 / sv) : T(0)) : T(1)) : T(0);
+    if (tid < OG_TILE) inv_a[tid] = iv;
+    else inv_b[tid - OG_TILE] = iv;
+  }
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+  for (int k0 = 0; k0 < K; k0 += OG_KC) {
+    __syncthreads();   // the previous chunk is consumed
+    // rows k0.. of the two column tiles (32 consecutive rows of a column per
+    // 32 consecutive threads)
+    for (int e = tid; e < 2 * OG_KC * OG_TILE; e += 256) {
+      const int kk = e % OG_KC, cc = (e / OG_KC) % OG_TILE, which = e / (OG_KC * OG_TILE);
+      const int c = (which ? b0 : a0) + cc, row = k0 + kk;
+      const T v = (c < r && row < K) ? W[row + (int64_t)c * ldw] : T(0);
+      if (which) Bs[kk][cc] = v;
+      else As[kk][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < OG_KC; ++kk) {
+      T a[4], b[4];
+      og_load4(&As[kk][4 * tx], a);
+      og_load4(&Bs[kk][4 * ty], b);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+  }
+  // scaled deviations (0 outside the retained block; the identity's entry
+  // where a scale is zero or below the working range)
+  double mx = 0.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int la = 4 * tx + u, lb = 4 * ty + v;
+      const int a = a0 + la, b = b0 + lb;
+      if (a < r && b < r) {
+        const T ia = inv_a[la], ib = inv_b[lb];
+        const T dl = (a == b) ? T(1) : T(0);
+        const T g = (ia > T(0) && ib > T(0)) ? acc[u][v] * ia * ib : dl;
+        mx = fmax(mx, (double)fabs(g - dl));
+      }
+    }
+  mx = warp_max(mx);
+  if ((tid & 31) == 0) red[tid >> 5] = mx;
+  __syncthreads();
+  if (tid < 32) {
+    double v = tid < 8 ? red[tid] : 0.0;
+    v = warp_max(v);
+    if (tid == 0) atomicMax(out + i, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
 // dst[i0 + n0 (i1 + n1 i2)] = src[i0 s0 + i1 s1 + i2 s2]: an unfolding laid
 // out contiguously (one GEMM then forms its Gram instead of one per slice)
 __global__ void permute3_kernel(const double* __restrict__ src, int64_t s0, int64_t s1, int64_t s2,
@@ -945,6 +1055,21 @@ cudaError_t scatter_ME(const int* map, const double* isq, int ell, int q, int m,
 }
 
 template <typename T>
+cudaError_t orth_gram_defect(const T* W, int ldw, int64_t w_bs, int K, int rc, int p,
+                             const int* ranks, const double* scale, double* out,
+                             cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * (size_t)p, st);
+  if (e != cudaSuccess) return e;
+  if (rc <= 0) return cudaSuccess;
+  const int nt = (rc + OG_TILE - 1) / OG_TILE;
+  const dim3 grid(nt * (nt + 1) / 2, p);
+  orth_gram_kernel<T><<<grid, 256, 0, st>>>(W, ldw, w_bs, K, rc, ranks, scale,
+                                            reinterpret_cast<unsigned long long*>(out));
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t orth_defect(const T* Gm, int rc, int p, const int* ranks, const double* scale,
                         double* out, cudaStream_t st) {
   if (p <= 0) return cudaSuccess;
@@ -1155,6 +1280,10 @@ template cudaError_t scatter_ME<float>(const int*, const double*, int, int, int,
                                        const float*, float*, int64_t, cudaStream_t);
 template cudaError_t scatter_ME<double>(const int*, const double*, int, int, int, int,
                                         const double*, double*, int64_t, cudaStream_t);
+template cudaError_t orth_gram_defect<float>(const float*, int, int64_t, int, int, int,
+                                            const int*, const double*, double*, cudaStream_t);
+template cudaError_t orth_gram_defect<double>(const double*, int, int64_t, int, int, int,
+                                             const int*, const double*, double*, cudaStream_t);
 template cudaError_t orth_defect<float>(const float*, int, int, const int*, const double*,
                                         double*, cudaStream_t);
 template cudaError_t orth_defect<double>(const double*, int, int, const int*, const double*,
