@@ -161,6 +161,13 @@ struct Prob {
   T* Wj = nullptr;
   T* U = nullptr;                           // Jacobi W = U Sigma (sorted), jp.mm x rc per slice
   T* V = nullptr;                           // Jacobi V, rc x rc per slice
+  // rotation log of the fp32 Jacobi (jp.rec): the kernel records its
+  // rotations instead of forming V, and after the truncation the replay
+  // forms the columns of V the rebuild reads (the discarded ones)
+  float4* vlog = nullptr;
+  int64_t vlog_bs = 0;                      // float4s per slice
+  int* vorder = nullptr;                    // pre-sort column of each sorted column
+  int* vlsw = nullptr;                      // rotating sweeps per slice
   // column-pivoted QR preconditioning (qr.cu): the Jacobi then runs on the
   // rc x rc factor R1^T, and the rebuild uses L = Q1 V (discarded columns)
   // and Rt = P W in place of the slice's own W and V
@@ -858,8 +865,23 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     P.qr2 = P.qr && P.mm <= kQrWarpRows &&
             (o.precondition == SMA_PRECOND_QRCP2 ||
              (o.precondition == SMA_PRECOND_AUTO && P.rc >= kQr2AutoMin));
-    P.jp = P.qr ? jacobi_plan<T>(P.rc, P.rc, h->max_smem) : jacobi_plan<T>(m, n, h->max_smem);
+    // one fp32 problem per handle: the rotation-log Jacobi where the shape
+    // allows it (the batched path keeps V in its kernel)
+    const bool rec = sizeof(T) == 4 && h->nprob == 1;
+    const int jm = P.qr ? P.rc : m, jn = P.qr ? P.rc : n;
+    P.jp = jacobi_plan<T>(jm, jn, h->max_smem, rec);
     if (P.jp.smem == 0) return SMA_ERR_UNSUPPORTED;   // a column too long for shared memory
+    if (P.jp.rec) {
+      // the log for the largest geometry among the autotuner's candidates
+      const int msw = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
+      size_t lf = 0;
+      for (const JacobiPlan& c : jacobi_plan_candidates<T>(jm, jn, h->max_smem, true))
+        lf = std::max(lf, jacobi_log_size(c, msw));
+      P.vlog_bs = (int64_t)lf;
+      SMA_TRY(mem.alloc(&P.vlog, lf * p));
+      SMA_TRY(mem.alloc(&P.vorder, (size_t)P.rc * p));
+      SMA_TRY(mem.alloc(&P.vlsw, (size_t)p));
+    }
     SMA_TRY(mem.alloc(&P.Xh, mnp));
     if (P.jp.block_mode)
       SMA_TRY(mem.alloc(&P.Wj, (size_t)(P.jp.mm + P.jp.rc) * P.jp.rc * p));
@@ -1294,7 +1316,8 @@ std::map<uint64_t, JacobiPlan>& tune_cache() {
 template <typename T>
 sma_status tune_plan(sma_ctx* h, JacobiParams<T> J, int count, int jm, int jn, JacobiPlan& plan,
                      const std::vector<int*>& status_words) {
-  const uint64_t key = ((uint64_t)(uint32_t)jm << 32) | ((uint64_t)(uint32_t)jn << 4) | sizeof(T);
+  const uint64_t key = ((uint64_t)(uint32_t)jm << 32) | ((uint64_t)(uint32_t)jn << 8) |
+                       ((uint64_t)(plan.rec ? 1 : 0) << 4) | sizeof(T);
   {
     std::lock_guard<std::mutex> g(tune_mutex());
     auto it = tune_cache().find(key);
@@ -1314,7 +1337,7 @@ sma_status tune_plan(sma_ctx* h, JacobiParams<T> J, int count, int jm, int jn, J
   JacobiPlan best = plan;
   float best_ms = 3.0e38f;
   cudaError_t err = cudaSuccess;
-  for (const JacobiPlan& c : jacobi_plan_candidates<T>(jm, jn, h->max_smem)) {
+  for (const JacobiPlan& c : jacobi_plan_candidates<T>(jm, jn, h->max_smem, plan.rec != 0)) {
     if (c.block_mode != plan.block_mode) continue;
     JacobiParams<T> Jc = J;
     Jc.mm = c.mm; Jc.rc = c.rc; Jc.trans = c.trans; Jc.ldS = c.ldS; Jc.bcols = c.bcols;
@@ -1347,29 +1370,36 @@ sma_status tune_plan(sma_ctx* h, JacobiParams<T> J, int count, int jm, int jn, J
   return SMA_OK;
 }
 
+// The slice-SVD parameters of a single t-SVDM problem under plan jp.
+template <typename T>
+JacobiParams<T> tsvdm_jparams(sma_ctx* h, const Prob<T>& P, const JacobiPlan& jp) {
+  const int m = P.m, n = P.n, rc = P.rc;
+  JacobiParams<T> J = jacobi_params<T>(h, jp);
+  if (P.qr) {
+    J.src = qr_jacobi_input(P); J.src_bs = (int64_t)rc * rc; J.m = rc; J.n = rc;
+  } else {
+    J.src = P.Xh; J.src_bs = (int64_t)m * n; J.m = m; J.n = n;
+  }
+  J.W = P.Wj; J.W_bs = (int64_t)(jp.mm + jp.rc) * jp.rc;
+  J.U = P.U; J.U_bs = (int64_t)jp.mm * rc;
+  J.V = P.V; J.V_bs = (int64_t)rc * rc;
+  J.sigma = P.sigma; J.sweeps = P.sweeps; J.status = P.status;
+  if (jp.rec) {
+    J.vlog = P.vlog; J.vlog_bs = P.vlog_bs; J.order = P.vorder; J.vlsweeps = P.vlsw;
+  }
+  return J;
+}
+
 template <typename T>
 sma_status tsvdm_svd(sma_ctx* h, Prob<T>& P) {
   cudaStream_t st = h->st;
   const int m = P.m, n = P.n, p = P.p, rc = P.rc;
-  const int64_t mn = (int64_t)m * n;
   if (P.qr) {
     stage_begin(h, SMA_STAGE_PRECOND);
     SMA_K(qr_precondition<T>(P, st));
     stage_end(h);
   }
-  auto params = [&](const JacobiPlan& jp) {
-    JacobiParams<T> J = jacobi_params<T>(h, jp);
-    if (P.qr) {
-      J.src = qr_jacobi_input(P); J.src_bs = (int64_t)rc * rc; J.m = rc; J.n = rc;
-    } else {
-      J.src = P.Xh; J.src_bs = mn; J.m = m; J.n = n;
-    }
-    J.W = P.Wj; J.W_bs = (int64_t)(jp.mm + jp.rc) * jp.rc;
-    J.U = P.U; J.U_bs = (int64_t)jp.mm * rc;
-    J.V = P.V; J.V_bs = (int64_t)rc * rc;
-    J.sigma = P.sigma; J.sweeps = P.sweeps; J.status = P.status;
-    return J;
-  };
+  auto params = [&](const JacobiPlan& jp) { return tsvdm_jparams<T>(h, P, jp); };
   if (h->opt.autotune && !h->capturing && !P.tuned) {
     SMA_TRY(tune_plan<T>(h, params(P.jp), p, P.qr ? rc : m, P.qr ? rc : n, P.jp, {P.status}));
     P.tuned = true;
@@ -1431,6 +1461,14 @@ sma_status tsvdm_post(sma_ctx* h, Prob<T>& P, bool truncated) {
     SMA_K(truncate_ranks(P.sigma, rc, p, P.stats, h->opt.rel_tol, h->opt.fixed_rank, P.ranks,
                          P.off, P.stats + 1, P.iscal, P.suf, st, 0));
     stage_end(h);
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (P.jp.rec) {
+      // the columns of V the rebuild reads, from the rotation log
+      stage_begin(h, SMA_STAGE_SVD);
+      SMA_K(jacobi_v_replay(tsvdm_jparams<T>(h, P, P.jp), P.jp, P.ranks, p, st));
+      stage_end(h);
+    }
   }
   if (P.qr) {
     stage_begin(h, SMA_STAGE_PRECOND);

@@ -440,7 +440,8 @@ __device__ __forceinline__ float reduce4(const float (&v)[4], int lane) {
 template <int NQW, bool INNER>
 __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, int sb, int nb,
                                            bool doA, bool doB, int mq, int rq, int lane,
-                                           float tol, float floor_, float4* csw) {
+                                           float tol, float floor_, float4* csw,
+                                           float4* glog = nullptr) {
   constexpr int NR = INNER ? 3 : 4;
   float4 x[8][NQW];
 #pragma unroll
@@ -513,7 +514,13 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
     const unsigned m = __ballot_sync(0xffffffffu, ok) & 0xfu;
     mk[r] = m;
     any |= m;
-    if (m == 0u) continue;
+    if (m == 0u) {
+      if (glog && lane == 0) {   // a sub-round of identities
+        glog[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        glog[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      continue;
+    }
     // all four pairs unconditionally (the ones not rotated are identities),
     // so their independent chains interleave
     float cq[4], tq[4], gt[4], t1[4], t2[4];
@@ -545,6 +552,26 @@ __device__ __forceinline__ bool tile_group(float* S, int ldS, int sa, int na, in
     if (lane == 0) {
       csw[2 * r] = make_float4(t1[0], t2[0], t1[1], t2[1]);
       csw[2 * r + 1] = make_float4(t1[2], t2[2], t1[3], t2[3]);
+      if (glog) {
+        glog[2 * r] = csw[2 * r];
+        glog[2 * r + 1] = csw[2 * r + 1];
+      }
+    }
+  }
+  if (glog && lane == 0) {
+    // the record: per sub-round the (t1, t2) of its four pairs (identities
+    // past NR), then the eight column scales
+#pragma unroll
+    for (int r = NR; r < 4; ++r) {
+      glog[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
+      glog[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (!any) {
+      glog[8] = make_float4(1.f, 1.f, 1.f, 1.f);
+      glog[9] = make_float4(1.f, 1.f, 1.f, 1.f);
+    } else {
+      glog[8] = make_float4(d[0], d[1], d[2], d[3]);
+      glog[9] = make_float4(d[4], d[5], d[6], d[7]);
     }
   }
   if (!any) return false;
@@ -1024,16 +1051,51 @@ __device__ __forceinline__ void stage_in(T* S, int ldS, T* W, int len, int bc, i
 // NQW): the register-tiled form with at most 11 warps.
 constexpr int kMaxTileWarps = 12;
 
+// ---- rotation log ----------------------------------------------------------
+// One record (kVlogRec float4s) per tile task and kind (inner pairs, cross
+// pairs): per sub-round the (t1, t2) of its four pairs, then the eight column
+// scales; the columns of V transform as the V pass of tile_group transforms
+// the rows of V.  Each round of each sweep and pair set owns a fixed block of
+// 2 kVlogRec kmax float4s, so that the replay finds it from the same
+// schedule (the bounds of the rounds and tasks of a phase give the
+// geometry); inside the block, the record of kind w (0 inner, 1 cross) of
+// task k is the kVlogRec float4s from (2 k + w) kVlogRec (one task's record
+// in consecutive addresses for the kernel's stores).
+constexpr int kVlogRec = 10;
+__host__ __device__ inline void vlog_dims(int rc, int bc, bool in_smem, int& nps, int& rmax,
+                                          int& kmax) {
+  if (in_smem) {   // kind 0: ntp - 1 rounds of ntp / 2 tasks
+    const int nt = (rc + 3) / 4, ntp = nt + (nt & 1);
+    nps = 1;
+    rmax = ntp;
+    kmax = ntp / 2 + 1;
+  } else {         // kind 1: at most 2 bt rounds of at most bt + 1 tasks
+    const int nb = (rc + bc - 1) / bc, bt = (bc + 3) / 4;
+    nps = nb * (nb - 1) / 2;
+    rmax = 2 * bt + 2;
+    kmax = bt + 2;
+  }
+}
+// the first float4 of the block of round t of pair set ps of sweep sw
+__host__ __device__ inline int64_t vlog_round(int sw, int ps, int t, int nps, int rmax,
+                                              int kmax) {
+  return (((int64_t)sw * nps + ps) * rmax + t) * (2 * kVlogRec * kmax);
+}
+
 // GW < 32 (whole slice in shared memory, mm <= 4 GW TILE, at most 4 warps):
 // the tiled form on groups of GW lanes, 32 / GW tasks per warp.
-template <typename T, int VEC, int TILE, int GW = 32>
+// REC: the rotation-log form (TILE > 0, GW == 32).
+template <typename T, int VEC, int TILE, int GW = 32, bool REC = false>
 __global__ void __launch_bounds__(GW < 32 ? 128 : (TILE ? 32 * kMaxTileWarps : 512))
 jacobi_kernel(const JacobiParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = blockIdx.x;
   const int tid = threadIdx.x, NTh = blockDim.x;
   const int mm = P.mm, rc = P.rc, ldS = P.ldS, g = P.g;
-  const int len = mm + rc;  // stacked column [w; v]
+  // rotation log (register tiles on whole warps only): columns w alone, the
+  // rotations recorded instead of applied to V rows
+  constexpr bool rec = REC && TILE > 0 && GW == 32;
+  const int len = rec ? mm : mm + rc;  // stacked column [w; v] (or w)
   const int lane = tid % g, gid = tid / g, ngroups = NTh / g;
   // Pair slot of this group.  Consecutive pair slots hold consecutive
   // columns, so the groups sharing a warp take slots g apart: their g-row
@@ -1116,6 +1178,13 @@ jacobi_kernel(const JacobiParams<T> P) {
       } else {
       __shared__ float4 cs_rec[kMaxTileWarps][10];   // rotation record of each warp
       float4* csw = cs_rec[wp];
+      int vl_nps = 0, vl_rmax = 0, vl_kmax = 0;
+      float4* vlog = nullptr;
+      if (rec) {
+        vlog_dims(rc, bc, in_smem, vl_nps, vl_rmax, vl_kmax);
+        vlog = P.vlog + (int64_t)s * P.vlog_bs;
+      }
+      const int rqv = rec ? 0 : rq;   // V rows of the stacked columns
       for (int ps = 0; ps < npair_sets; ++ps) {
         TPhase ph;
         if (in_smem) {
@@ -1132,12 +1201,14 @@ jacobi_kernel(const JacobiParams<T> P) {
           for (int k = wp; k < ntasks; k += nwp) {
             TTask d;
             if (!tphase_task(ph, t, k, d)) continue;
+            float4* lg = nullptr;
+            if (rec) lg = vlog + vlog_round(sw, ps, t, vl_nps, vl_rmax, vl_kmax) + 2 * kVlogRec * k;
             if (d.inner)
               rot |= tile_group<TILE, true>(S, ldS, d.sa, d.na, d.sb, d.nb, d.na > 0, d.nb > 0, mq,
-                                            rq, ln, tol_t, floor_t, csw);
+                                            rqv, ln, tol_t, floor_t, csw, lg);
             if (d.na > 0 && d.nb > 0)
-              rot |= tile_group<TILE, false>(S, ldS, d.sa, d.na, d.sb, d.nb, false, false, mq, rq,
-                                             ln, tol_t, floor_t, csw);
+              rot |= tile_group<TILE, false>(S, ldS, d.sa, d.na, d.sb, d.nb, false, false, mq, rqv,
+                                             ln, tol_t, floor_t, csw, rec ? lg + kVlogRec : nullptr);
           }
           __syncthreads();
         }
@@ -1265,6 +1336,10 @@ jacobi_kernel(const JacobiParams<T> P) {
     const T v = in_smem ? S[(int64_t)c * ldS + r] : W[r + (int64_t)c * len];
     if (r < mm) Wo[r + (int64_t)j * mm] = v;
     else Vo[(r - mm) + (int64_t)j * rc] = v;
+  }
+  if (rec) {
+    for (int j = tid; j < rc; j += NTh) P.order[(int64_t)s * rc + j] = idx[j];
+    if (tid == 0) P.vlsweeps[s] = max(converged ? sweeps_used - 1 : sweeps_used, 0);
   }
   if (tid == 0) {
     if (sweeps_out) *sweeps_out = sweeps_used;
@@ -1706,18 +1781,270 @@ __global__ void __launch_bounds__(32 * kClusterWarps)
   }
 }
 
+// ---- V from the rotation log -----------------------------------------------
+// CTA (s, g) forms the needed columns j = d0 + g + VR_SPLIT i of slice s
+// (d0 = ranks[s]) in shared memory, x[i] starting as the unit vector of the
+// pre-sort column order[j]; the columns of one slice spread over VR_SPLIT
+// CTAs, so a slice with few needed columns runs them in parallel.  V is the product of the
+// tasks' maps in execution order (each acting on the right, on the task's
+// eight columns), so its columns come from applying the maps in reverse:
+// sweeps, pair sets and rounds last to first; the tasks of a round act on
+// disjoint columns and run in parallel; a task's cross record goes before its
+// inner record.  A record maps x as the transpose of the row map of
+// tile_group's V pass: x_c *= d_c, then for the sub-rounds last to first and
+// each pair (a, b) with (t1, t2): x_a <- x_a + t2 x_b, x_b <- x_b - t1 x_a.
+// The schedule is the same in every sweep, so each task's eight columns and
+// kinds are tabled once; the coming rounds' records are copied from the log
+// into a ring in shared memory with cp.async (field-major there, so that the
+// lanes, one task each, read a field at consecutive addresses) while the
+// current round is applied.  A round's work is a short dependent chain, so a
+// slice with one needed column is replayed by one warp without block
+// barriers.
+constexpr int VR_THREADS = 256;
+constexpr int VR_SPLIT = 32;   // CTAs per slice (grid y)
+constexpr int VR_COLS = 8;     // columns per CTA (rc <= VR_SPLIT VR_COLS)
+constexpr int VR_AHEAD = 8;    // rounds prefetched ahead
+constexpr int VR_RING = VR_AHEAD + 1;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// the schedule position of one round: sweep, pair set, round
+struct VrPos {
+  int sw, ps, t;
+};
+// one round back in execution order; false past the first round
+__device__ __forceinline__ bool vr_back(VrPos& q, int nps, const unsigned char* nr) {
+  if (--q.t >= 0) return true;
+  if (--q.ps < 0) {
+    q.ps = nps - 1;
+    if (--q.sw < 0) return false;
+  }
+  q.t = nr[q.ps] - 1;
+  return true;
+}
+
+// the phase of pair set ps (the kernel's, see jacobi_kernel)
+__device__ __forceinline__ TPhase vr_phase(int ps, int rc, int bc, bool in_smem, int nb, int& I,
+                                           int& J) {
+  if (in_smem) {
+    I = 0;
+    J = 0;
+    return tphase_smem(rc);
+  }
+  bool doI, doJ;
+  tile_phase_ij(ps, nb, I, J, doI, doJ);
+  return tphase_blocks(min(bc, rc - I * bc), min(bc, rc - J * bc), bc, doI, doJ);
+}
+
+// (field f of the record at rec[f fs])
+template <bool INNER>
+__device__ __forceinline__ void vr_apply(const float4* rec, int fs, float (&x)[8]) {
+  constexpr int NR = INNER ? 3 : 4;
+  const float4 d03 = rec[8 * fs], d47 = rec[9 * fs];
+  x[0] *= d03.x; x[1] *= d03.y; x[2] *= d03.z; x[3] *= d03.w;
+  x[4] *= d47.x; x[5] *= d47.y; x[6] *= d47.z; x[7] *= d47.w;
+#pragma unroll
+  for (int r = NR - 1; r >= 0; --r) {
+    const float4 r01 = rec[(2 * r) * fs], r23 = rec[(2 * r + 1) * fs];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int a, b;
+      tile_pair<INNER>(r, q, a, b);
+      const float t1 = q == 0 ? r01.x : q == 1 ? r01.z : q == 2 ? r23.x : r23.z;
+      const float t2 = q == 0 ? r01.y : q == 1 ? r01.w : q == 2 ? r23.y : r23.w;
+      const float xa = x[a], xb = x[b];
+      x[a] = fmaf(t2, xb, xa);
+      x[b] = fmaf(-t1, xa, xb);
+    }
+  }
+}
+
+// task table entry flags
+constexpr unsigned char VR_CROSS = 1, VR_INNER = 2;
+constexpr unsigned short VR_NOCOL = 0xffff;
+
+// shared-memory bytes of the replay for rc columns, block columns bc
+__host__ __device__ inline size_t vr_smem_bytes(int rc, int bc) {
+  const bool in_smem = rc <= 2 * bc;
+  int nps, rmax, kmax;
+  vlog_dims(rc, bc, in_smem, nps, rmax, kmax);
+  const size_t ntab = (size_t)nps * rmax * kmax;
+  return (size_t)VR_RING * 2 * kVlogRec * kmax * sizeof(float4)   // ring
+         + ntab * 8 * sizeof(unsigned short)                       // task columns
+         + (size_t)VR_COLS * rc * sizeof(float)                    // x
+         + ntab + (size_t)nps * rmax + nps;                        // flags, tasks, rounds
+}
+
+__global__ void __launch_bounds__(VR_THREADS)
+    jacobi_v_replay_kernel(const JacobiParams<float> P, int bc, const int* __restrict__ ranks) {
+  extern __shared__ __align__(16) unsigned char vr_smem[];
+  const int s = blockIdx.x, g = blockIdx.y, rc = P.rc, tid = threadIdx.x;
+  const int d0 = ranks ? min(max(ranks[s], 0), rc) : 0;
+  const int nd = rc - d0;
+  // this CTA's columns j = d0 + g + VR_SPLIT i, i < nv
+  const int nv = nd > g ? min((nd - g + VR_SPLIT - 1) / VR_SPLIT, VR_COLS) : 0;
+  if (nv == 0) return;   // (uniform over the CTA)
+  const bool in_smem = rc <= 2 * bc;
+  const int nb = in_smem ? 1 : (rc + bc - 1) / bc;
+  int nps, rmax, kmax;
+  vlog_dims(rc, bc, in_smem, nps, rmax, kmax);
+  const int ntab = nps * rmax * kmax;
+  const int rec4 = 2 * kVlogRec * kmax;   // float4s of one round's records
+  float4* ring = reinterpret_cast<float4*>(vr_smem);                        // [VR_RING][rec4]
+  uint4* tcol = reinterpret_cast<uint4*>(ring + (size_t)VR_RING * rec4);     // [ntab] 8 x u16
+  float* x = reinterpret_cast<float*>(tcol + ntab);                         // [VR_COLS][rc]
+  unsigned char* tflag = reinterpret_cast<unsigned char*>(x + (size_t)VR_COLS * rc);  // [ntab]
+  unsigned char* ntk = tflag + ntab;                                        // [nps][rmax]
+  unsigned char* nr = ntk + nps * rmax;                                     // [nps]
+  // the task table (the same in every sweep), by the whole CTA
+  for (int e = tid; e < nps * rmax; e += VR_THREADS) {
+    const int ps = e / rmax, t = e % rmax;
+    int I, J;
+    const TPhase ph = vr_phase(ps, rc, bc, in_smem, nb, I, J);
+    const int nrounds = tphase_rounds(ph);
+    if (t == 0) nr[ps] = (unsigned char)nrounds;
+    const int ntasks = t < nrounds ? tphase_tasks(ph, t) : 0;
+    ntk[e] = (unsigned char)ntasks;
+    for (int k = 0; k < kmax; ++k) {
+      TTask d;
+      unsigned char fl = 0;
+      unsigned short cl[8];
+      if (k < ntasks && tphase_task(ph, t, k, d)) {
+        fl = (d.na > 0 && d.nb > 0 ? VR_CROSS : 0) | (d.inner ? VR_INNER : 0);
+        for (int c = 0; c < 8; ++c) {
+          const int slot = c < 4 ? d.sa + c : d.sb + c - 4;
+          const bool valid = c < 4 ? c < d.na : (c - 4) < d.nb;
+          const int cg = in_smem ? slot : (slot < bc ? I * bc + slot : J * bc + slot - bc);
+          cl[c] = valid ? (unsigned short)cg : VR_NOCOL;
+        }
+      } else {
+        for (int c = 0; c < 8; ++c) cl[c] = VR_NOCOL;
+      }
+      tflag[e * kmax + k] = fl;
+      tcol[e * kmax + k] = make_uint4(cl[0] | ((unsigned)cl[1] << 16), cl[2] | ((unsigned)cl[3] << 16),
+                                      cl[4] | ((unsigned)cl[5] << 16), cl[6] | ((unsigned)cl[7] << 16));
+    }
+  }
+  __syncthreads();
+  // a round's units (task, column of V) fit one warp when few columns are
+  // needed: then warp 0 alone replays and synchronises by __syncwarp
+  const bool one = nv * kmax <= 32;
+  if (one && tid >= 32) return;   // (uniform over each warp; no block barrier follows)
+  const int nth = one ? 32 : VR_THREADS;
+  auto sync = [&]() {
+    if (one) __syncwarp();
+    else __syncthreads();
+  };
+  const float4* vlog = P.vlog + (int64_t)s * P.vlog_bs;
+  const int nsw = P.vlsweeps[s];
+  const int* order = P.order + (int64_t)s * rc;
+  float* Vs = P.V + (int64_t)s * P.V_bs;
+  {
+    for (int e = tid; e < rc * nv; e += nth) x[e] = 0.f;
+    sync();
+    for (int v = tid; v < nv; v += nth) {
+      const int c = order[d0 + g + VR_SPLIT * v];
+      if ((unsigned)c < (unsigned)rc) x[v * rc + c] = 1.f;
+    }
+    // rounds in reverse execution order, from the last round of the last
+    // rotating sweep; the ring slot of the i-th round is i mod VR_RING
+    VrPos cur{nsw - 1, nps - 1, nr[nps - 1] - 1};
+    bool cur_ok = nsw > 0;
+    VrPos pre = cur;
+    bool pre_ok = cur_ok;
+    int issued = 0, done = 0;
+    auto issue = [&]() {
+      if (pre_ok) {
+        // the round's cross records (and, in a round with inner pairs, the
+        // inner ones), field-major into the ring slot
+        const float4* src = vlog + vlog_round(pre.sw, pre.ps, pre.t, nps, rmax, kmax);
+        float4* dst = ring + (size_t)(issued % VR_RING) * rec4;
+        const int nt = ntk[pre.ps * rmax + pre.t];
+        const int kinds = pre.t == 0 ? 2 : 1;
+        for (int e = tid; e < nt * kinds; e += nth) {
+          const int k = e % nt, w = kinds == 2 ? e / nt : 1;
+          const float4* rs = src + (2 * k + w) * kVlogRec;
+#pragma unroll
+          for (int f = 0; f < kVlogRec; ++f) cp_async16(dst + (w * kVlogRec + f) * kmax + k, rs + f);
+        }
+        pre_ok = vr_back(pre, nps, nr);
+      }
+      cp_async_commit();
+      ++issued;
+    };
+    for (int j = 0; j < VR_AHEAD; ++j) issue();
+    while (cur_ok) {
+      cp_async_wait<VR_AHEAD - 1>();
+      sync();   // the round's records (and the previous round's x) visible
+      const float4* rr = ring + (size_t)(done % VR_RING) * rec4;
+      const int tb = (cur.ps * rmax + cur.t) * kmax;
+      const int ntasks = ntk[cur.ps * rmax + cur.t];
+      for (int u = tid; u < ntasks * nv; u += nth) {
+        const int k = u % ntasks, v = u / ntasks;   // (lanes on tasks: distinct columns)
+        const unsigned char fl = tflag[tb + k];
+        if (!fl) continue;
+        const uint4 cw = tcol[tb + k];
+        const unsigned short col[8] = {
+            (unsigned short)(cw.x & 0xffff), (unsigned short)(cw.x >> 16),
+            (unsigned short)(cw.y & 0xffff), (unsigned short)(cw.y >> 16),
+            (unsigned short)(cw.z & 0xffff), (unsigned short)(cw.z >> 16),
+            (unsigned short)(cw.w & 0xffff), (unsigned short)(cw.w >> 16)};
+        float* xv0 = x + (size_t)v * rc;
+        float xv[8];
+        bool nz = false;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          xv[c] = col[c] != VR_NOCOL ? xv0[col[c]] : 0.f;
+          nz |= xv[c] != 0.f;
+        }
+        if (!nz) continue;   // the maps keep zero entries zero
+        if (fl & VR_CROSS) vr_apply<false>(rr + kVlogRec * kmax + k, kmax, xv);
+        if (fl & VR_INNER) vr_apply<true>(rr + k, kmax, xv);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (col[c] != VR_NOCOL) xv0[col[c]] = xv[c];
+      }
+      ++done;
+      cur_ok = vr_back(cur, nps, nr);
+      sync();   // the round is applied: its ring slot may be refilled
+      issue();
+    }
+    cp_async_wait<0>();
+    sync();
+    for (int e = tid; e < rc * nv; e += nth) {
+      const int r = e % rc, v = e / rc;
+      Vs[r + (int64_t)(d0 + g + VR_SPLIT * v) * rc] = x[e];
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
-JacobiPlan jacobi_plan_impl(int m, int n, int max_smem, bool allow_tile) {
+JacobiPlan jacobi_plan_impl(int m, int n, int max_smem, bool allow_tile, bool rec = false) {
   JacobiPlan pl;
+  const int max_smem_in = max_smem;
   // leave room for the kernel's static shared memory
   max_smem = max_smem > 3072 ? max_smem - 3072 : 0;
   pl.trans = (m < n) ? 1 : 0;
   pl.mm = pl.trans ? n : m;
   pl.rc = pl.trans ? m : n;
   pl.vec = (sizeof(T) == 4 && pl.mm % 4 == 0 && pl.rc % 4 == 0) ? 4 : 1;
-  pl.ldS = pl.mm + pl.rc + (pl.vec == 4 ? 4 : 1);
+  // the rotation-log form: register tiles on whole warps (fp32, float4 rows,
+  // 64 < mm <= 256), the stacked columns without their V rows
+  pl.rec = (rec && allow_tile && sizeof(T) == 4 && pl.vec == 4 && pl.mm > 64 && pl.mm <= 256 &&
+            pl.rc >= 32) ? 1 : 0;
+  pl.ldS = pl.mm + (pl.rec ? 0 : pl.rc) + (pl.vec == 4 ? 4 : 1);
   int p2 = 1;
   while (p2 < pl.rc) p2 <<= 1;
   pl.sort_n = p2;
@@ -1758,7 +2085,9 @@ JacobiPlan jacobi_plan_impl(int m, int n, int max_smem, bool allow_tile) {
       // blocks of a multiple of 4 columns, at most 4 per warp (one tile pair
       // per warp and cross round)
       int bmax = (int)(((size_t)max_smem - sort_bytes) / (2 * col_bytes)) & ~3;
-      if (bmax > 4 * kTileWarps) bmax = 4 * kTileWarps;
+      // (without V rows twice the columns fit: two tile pairs per warp and round)
+      const int bcap = (pl.rec ? 8 : 4) * kTileWarps;
+      if (bmax > bcap) bmax = bcap;
       if (bmax >= 4) {
         int nb = (pl.rc + bmax - 1) / bmax;
         if (nb < 3) nb = 3;
@@ -1789,6 +2118,7 @@ JacobiPlan jacobi_plan_impl(int m, int n, int max_smem, bool allow_tile) {
       return pl;
     }
   }
+  if (pl.rec) return jacobi_plan_impl<T>(m, n, max_smem_in, allow_tile, false);
   const bool in_smem = pl.rc <= 2 * pl.bcols;
   const int maxpairs = in_smem ? (pl.rc + 1) / 2 : pl.bcols;
   // threads: one group of g lanes per pair of a round, about 16 rows per lane
@@ -1805,8 +2135,15 @@ JacobiPlan jacobi_plan_impl(int m, int n, int max_smem, bool allow_tile) {
 }
 
 template <typename T>
-JacobiPlan jacobi_plan(int m, int n, int max_smem) {
-  return jacobi_plan_impl<T>(m, n, max_smem, true);
+JacobiPlan jacobi_plan(int m, int n, int max_smem, bool rec) {
+  return jacobi_plan_impl<T>(m, n, max_smem, true, rec);
+}
+
+size_t jacobi_log_size(const JacobiPlan& pl, int max_sweeps) {
+  if (!pl.rec) return 0;
+  int nps = 0, rmax = 0, kmax = 0;
+  vlog_dims(pl.rc, pl.bcols, pl.rc <= 2 * pl.bcols, nps, rmax, kmax);
+  return (size_t)(max_sweeps > 0 ? max_sweeps : 1) * nps * rmax * kmax * 2 * kVlogRec;
 }
 
 // Alternatives to the default plan for the autotuner, all with the default's
@@ -1814,12 +2151,12 @@ JacobiPlan jacobi_plan(int m, int n, int max_smem) {
 // workspace serves them: the untiled form where the default is tiled, and
 // for tiled block mode 4 columns more or fewer per block and 11 or 12 warps.
 template <typename T>
-std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem) {
+std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem, bool rec) {
   std::vector<JacobiPlan> out;
-  const JacobiPlan base = jacobi_plan<T>(m, n, max_smem);
+  const JacobiPlan base = jacobi_plan<T>(m, n, max_smem, rec);
   out.push_back(base);
   if (base.smem == 0) return out;   // no plan for this shape
-  if (base.tile) {
+  if (base.tile && !base.rec) {
     const JacobiPlan u = jacobi_plan_impl<T>(m, n, max_smem, false);
     if (u.block_mode == base.block_mode) out.push_back(u);
   }
@@ -1831,7 +2168,8 @@ std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem) {
       JacobiPlan v = base;
       v.bcols = base.bcols + d;
       v.smem = 2 * (size_t)v.bcols * col_bytes + sort_bytes;
-      if (v.bcols >= 8 && v.bcols <= 48 && v.smem <= (size_t)cap && base.rc > 2 * v.bcols &&
+      if (v.bcols >= 8 && v.bcols <= (base.rec ? 96 : 48) && v.smem <= (size_t)cap &&
+          base.rc > 2 * v.bcols &&
           (base.rc + v.bcols - 1) / v.bcols >= 3)
         out.push_back(v);
     }
@@ -1841,6 +2179,15 @@ std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem) {
   }
   // whole slice in shared memory: smaller CTAs put more slices on an SM (the
   // round robin then takes several passes of the warps per round)
+  if (!base.block_mode && base.rec) {
+    for (int t : {64, 128})
+      if (t < base.threads) {
+        JacobiPlan v = base;
+        v.threads = t;
+        out.push_back(v);
+      }
+    return out;
+  }
   if (!base.block_mode) {
     if (base.tile) {
       for (int t : {64, 128})
@@ -1898,8 +2245,10 @@ cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_
   if constexpr (sizeof(T) == 4) {
     if (P.ldS % 4 == 0 && P.mm % 4 == 0 && P.rc % 4 == 0) {
       kern = jacobi_kernel<T, 4, 0>;
-      if (P.tile == 1 && P.mm <= 128) kern = jacobi_kernel<T, 4, 1>;
-      if (P.tile == 2 && P.mm <= 256) kern = jacobi_kernel<T, 4, 2>;
+      if (P.tile == 1 && P.mm <= 128)
+        kern = P.vlog ? jacobi_kernel<T, 4, 1, 32, true> : jacobi_kernel<T, 4, 1>;
+      if (P.tile == 2 && P.mm <= 256)
+        kern = P.vlog ? jacobi_kernel<T, 4, 2, 32, true> : jacobi_kernel<T, 4, 2>;
       if (P.tile > 0 && P.g < 32) {
         // partial-warp groups of g lanes, tile float4 rows per lane: whole
         // slice in shared memory, mm <= 4 g tile rows, at most 4 warps (the
@@ -1913,6 +2262,13 @@ cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_
         else return cudaErrorInvalidValue;
       }
     }
+  }
+  if (P.vlog) {
+    // the log needs the whole-warp register-tiled form
+    bool rec_kern = false;
+    if constexpr (sizeof(T) == 4)
+      rec_kern = kern == jacobi_kernel<T, 4, 1, 32, true> || kern == jacobi_kernel<T, 4, 2, 32, true>;
+    if (!rec_kern || P.desc || !P.order || !P.vlsweeps) return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -2043,10 +2399,28 @@ cudaError_t jacobi_svd_cluster(const JacobiParams<float>& P, const JacobiPlan& p
   return cudaGetLastError();
 }
 
-template JacobiPlan jacobi_plan<float>(int, int, int);
-template JacobiPlan jacobi_plan<double>(int, int, int);
-template std::vector<JacobiPlan> jacobi_plan_candidates<float>(int, int, int);
-template std::vector<JacobiPlan> jacobi_plan_candidates<double>(int, int, int);
+cudaError_t jacobi_v_replay(const JacobiParams<float>& P, const JacobiPlan& pl, const int* ranks,
+                            int nslices, cudaStream_t st) {
+  if (nslices <= 0) return cudaSuccess;
+  if (!pl.rec || !P.vlog || !P.order || !P.vlsweeps || !P.V || P.rc != pl.rc)
+    return cudaErrorInvalidValue;
+  int nps = 0, rmax = 0, kmax = 0;
+  vlog_dims(pl.rc, pl.bcols, pl.rc <= 2 * pl.bcols, nps, rmax, kmax);
+  // (rounds, tasks and columns held in bytes and 16-bit words)
+  if (nps < 1 || rmax > 255 || kmax > 255 || pl.rc >= 0xffff) return cudaErrorInvalidValue;
+  const size_t smem = vr_smem_bytes(pl.rc, pl.bcols);
+  cudaError_t e = cudaFuncSetAttribute(jacobi_v_replay_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (pl.rc > VR_SPLIT * VR_COLS) return cudaErrorInvalidValue;
+  jacobi_v_replay_kernel<<<dim3(nslices, VR_SPLIT), VR_THREADS, smem, st>>>(P, pl.bcols, ranks);
+  return cudaGetLastError();
+}
+
+template JacobiPlan jacobi_plan<float>(int, int, int, bool);
+template JacobiPlan jacobi_plan<double>(int, int, int, bool);
+template std::vector<JacobiPlan> jacobi_plan_candidates<float>(int, int, int, bool);
+template std::vector<JacobiPlan> jacobi_plan_candidates<double>(int, int, int, bool);
 template cudaError_t jacobi_svd<float>(const JacobiParams<float>&, int, int, size_t, cudaStream_t);
 template cudaError_t jacobi_svd<double>(const JacobiParams<double>&, int, int, size_t, cudaStream_t);
 

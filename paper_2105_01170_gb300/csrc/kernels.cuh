@@ -90,16 +90,34 @@ struct JacobiParams {
   int* sweeps = nullptr;                        // out: per slice
   int* status = nullptr;                        // status bits (atomicOr)
   int tile = 0;                                 // register-tiled sweeps (JacobiPlan::tile)
+  // Rotation log (plans with JacobiPlan::rec): the kernel keeps no V rows and
+  // records every tile task's scaled rotations here instead (U and sigma as
+  // usual, V not written); jacobi_v_replay forms the columns of V needed.
+  float4* vlog = nullptr; int64_t vlog_bs = 0;  // float4s per slice (jacobi_log_size)
+  int* order = nullptr;                         // out: pre-sort column of sorted column j
+  int* vlsweeps = nullptr;                      // out: sweeps that rotated, per slice
 };
 struct JacobiPlan {
   int trans, mm, rc, ldS, bcols, sort_n, threads, g, block_mode, vec;
   int tile;   // 0: one pair per group of g lanes; 1, 2: register tiles of that many
               // float4 rows per lane on groups of g lanes (mm <= 4 g tile)
+  int rec;    // 1: the rotation-log form (fp32 register tiles on whole warps)
   size_t smem;
 };
-template <typename T> JacobiPlan jacobi_plan(int m, int n, int max_smem);
-// The default plan and the autotuner's alternatives to it (same storage mode).
-template <typename T> std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem);
+// rec: the rotation-log form where the shape allows it (else as without).
+template <typename T> JacobiPlan jacobi_plan(int m, int n, int max_smem, bool rec = false);
+// The default plan and the autotuner's alternatives to it (same storage mode
+// and the same rec).
+template <typename T>
+std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem, bool rec = false);
+// float4s of rotation log per slice for plan pl and at most max_sweeps sweeps.
+size_t jacobi_log_size(const JacobiPlan& pl, int max_sweeps);
+// After a rotation-log Jacobi run P (plan pl): V[:, j] for the columns
+// j = ranks[s]..rc-1 of every slice s (all of them where ranks is NULL),
+// the logged tasks applied in reverse order to the unit vector of the
+// pre-sort column order[j].  The other columns of V are not written.
+cudaError_t jacobi_v_replay(const JacobiParams<float>& P, const JacobiPlan& pl, const int* ranks,
+                            int nslices, cudaStream_t st);
 template <typename T>
 cudaError_t jacobi_svd(const JacobiParams<T>& P, int nslices, int threads, size_t smem,
                        cudaStream_t st);

@@ -633,9 +633,11 @@ __global__ void __launch_bounds__(256)
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const double smin = sizeof(T) == 4 ? 1e-30 : 0.0;
   if (tid < 2 * OG_TILE) {
+    // reciprocal scales in the element type (fp64 arithmetic is slow on this
+    // part; the mixed path's factors carry fp32 accuracy)
     const int c = (tid < OG_TILE ? a0 : b0) + (tid & (OG_TILE - 1));
-    const double sv = (c < r && sigma) ? sigma[(int64_t)i * rc + c] : 1.0;
-    const T iv = (c < r) ? (sigma ? (sv > smin ? (T)(1.0 / sv) : T(0)) : T(1)) : T(0);
+    const T sv = (c < r && sigma) ? (T)sigma[(int64_t)i * rc + c] : T(1);
+    const T iv = (c < r) ? (sigma ? (sv > (T)smin ? T(1) / sv : T(0)) : T(1)) : T(0);
     if (tid < OG_TILE) inv_a[tid] = iv;
     else inv_b[tid - OG_TILE] = iv;
   }
@@ -644,18 +646,32 @@ __global__ void __launch_bounds__(256)
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-  for (int k0 = 0; k0 < K; k0 += OG_KC) {
-    __syncthreads();   // the previous chunk is consumed
-    // rows k0.. of the two column tiles (32 consecutive rows of a column per
-    // 32 consecutive threads)
-    for (int e = tid; e < 2 * OG_KC * OG_TILE; e += 256) {
+  // rows k0.. of the two column tiles (32 consecutive rows of a column per
+  // 32 consecutive threads), the next chunk loaded into registers while the
+  // current one is multiplied
+  constexpr int OG_PER = 2 * OG_KC * OG_TILE / 256;
+  T pre[OG_PER];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < OG_PER; ++u) {
+      const int e = tid + 256 * u;
       const int kk = e % OG_KC, cc = (e / OG_KC) % OG_TILE, which = e / (OG_KC * OG_TILE);
       const int c = (which ? b0 : a0) + cc, row = k0 + kk;
-      const T v = (c < r && row < K) ? W[row + (int64_t)c * ldw] : T(0);
-      if (which) Bs[kk][cc] = v;
-      else As[kk][cc] = v;
+      pre[u] = (c < r && row < K) ? W[row + (int64_t)c * ldw] : T(0);
+    }
+  };
+  fetch(0);
+  for (int k0 = 0; k0 < K; k0 += OG_KC) {
+    __syncthreads();   // the previous chunk is consumed
+#pragma unroll
+    for (int u = 0; u < OG_PER; ++u) {
+      const int e = tid + 256 * u;
+      const int kk = e % OG_KC, cc = (e / OG_KC) % OG_TILE, which = e / (OG_KC * OG_TILE);
+      if (which) Bs[kk][cc] = pre[u];
+      else As[kk][cc] = pre[u];
     }
     __syncthreads();
+    if (k0 + OG_KC < K) fetch(k0 + OG_KC);
 #pragma unroll 8
     for (int kk = 0; kk < OG_KC; ++kk) {
       T a[4], b[4];
@@ -669,7 +685,7 @@ __global__ void __launch_bounds__(256)
   }
   // scaled deviations (0 outside the retained block; the identity's entry
   // where a scale is zero or below the working range)
-  double mx = 0.0;
+  T mxt = T(0);
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -680,10 +696,10 @@ __global__ void __launch_bounds__(256)
         const T ia = inv_a[la], ib = inv_b[lb];
         const T dl = (a == b) ? T(1) : T(0);
         const T g = (ia > T(0) && ib > T(0)) ? acc[u][v] * ia * ib : dl;
-        mx = fmax(mx, (double)fabs(g - dl));
+        mxt = fmax(mxt, fabs(g - dl));
       }
     }
-  mx = warp_max(mx);
+  double mx = warp_max((double)mxt);
   if ((tid & 31) == 0) red[tid >> 5] = mx;
   __syncthreads();
   if (tid < 32) {
