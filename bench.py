@@ -42,10 +42,13 @@ REL_TOL = 1e-6
 # the headline metric, as the benchmark configuration names it; value = whole
 # steps (compression + 256-RHS matvec) per second, the matvec GFLOP/s beside it
 METRIC = "t-SVDM compressions/s + Kron-sum matvec GFLOP/s, mixed vs FP64 GPU, equal err"
-# DRAM bytes (read + write) of one slice of the register-tiled Jacobi SVD at
-# 256 x 256, from an ncu capture of the 15-slice case (4,164,096 B read, 0
-# written); every slice moves the same bytes, so a launch moves p times this
-JACOBI_DRAM_BYTES_PER_SLICE = 4164096 / 15
+# DRAM bytes (read + write) per slice of the rotation-log Jacobi at 256 x 256,
+# from an ncu capture of the 15-slice case (4,098,560 B read: the slices and
+# the block workspace; 11,086,848 B written: the rotation log, part of which
+# is still in L2 at exit); every slice moves the same bytes, so a launch
+# moves p times this.  The replay reads the logs of the slices with
+# discarded columns only.
+JACOBI_DRAM_BYTES_PER_SLICE = (4098560 + 11086848) / 15
 
 
 def log(*a):
@@ -814,12 +817,16 @@ def main():
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     alu_peak = NSM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s fp32 FMA
     achieved = svd_alg / (svd_ms * 1e-3) / 1e12
-    roof = {"kernel": "jacobi_kernel<float> (per-slice SVD, one CTA per slice)",
+    roof = {"kernel": "jacobi_kernel<float> rotation-log form + jacobi_v_replay_kernel "
+                      "(the slice-SVD step: one CTA per slice, then the columns of V the "
+                      "rebuild reads)",
             "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
             "frac": achieved / alu_peak,
             "traffic": (JACOBI_DRAM_BYTES_PER_SLICE * pr.p
-                        if (pr.m, pr.n) == (256, 256) else None),
-            "traffic_note": "dram read+write bytes per launch, ncu capture of 15 slices scaled by slices",
+                        if (pr.m, pr.n) == (256, 256) and JACOBI_DRAM_BYTES_PER_SLICE else None),
+            "traffic_note": "dram read+write bytes of the Jacobi launch (the replay reads the "
+                            "logs of the slices with discarded columns), ncu capture of 15 "
+                            "slices scaled by slices",
             "peak_note": f"fp32 FMA: {NSM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz "
                          "(unit counts x max clock; no measured ALU peak)",
             "algorithmic": f"{pr.p} x GVL SVD count 4m^2n+8mn^2+9n^3 = {svd_alg:.3e} flop/launch",
