@@ -873,10 +873,10 @@ sma_status setup_problem(sma_ctx* h, Prob<T>& P, const sma_problem& pr) {
     if (P.jp.smem == 0) return SMA_ERR_UNSUPPORTED;   // a column too long for shared memory
     if (P.jp.rec) {
       // the log for the largest geometry among the autotuner's candidates
-      const int msw = h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30;
+      const int lsw = jacobi_log_sweeps(h->opt.max_sweeps > 0 ? h->opt.max_sweeps : 30);
       size_t lf = 0;
       for (const JacobiPlan& c : jacobi_plan_candidates<T>(jm, jn, h->max_smem, true))
-        lf = std::max(lf, jacobi_log_size(c, msw));
+        lf = std::max(lf, jacobi_log_size(c, lsw));
       P.vlog_bs = (int64_t)lf;
       SMA_TRY(mem.alloc(&P.vlog, lf * p));
       SMA_TRY(mem.alloc(&P.vorder, (size_t)P.rc * p));
@@ -1386,6 +1386,7 @@ JacobiParams<T> tsvdm_jparams(sma_ctx* h, const Prob<T>& P, const JacobiPlan& jp
   J.sigma = P.sigma; J.sweeps = P.sweeps; J.status = P.status;
   if (jp.rec) {
     J.vlog = P.vlog; J.vlog_bs = P.vlog_bs; J.order = P.vorder; J.vlsweeps = P.vlsw;
+    J.vlog_sweeps = jacobi_log_sweeps(J.max_sweeps);
   }
   return J;
 }

@@ -1142,7 +1142,9 @@ jacobi_kernel(const JacobiParams<T> P) {
   int sweeps_used = 0;
   bool converged = (rc <= 1);
   const int npair_sets = in_smem ? 1 : nb * (nb - 1) / 2;
-  for (int sw = 0; sw < P.max_sweeps && !converged; ++sw) {
+  // (the rotation log holds vlog_sweeps sweeps: the sweep limit in that form)
+  const int max_sw = rec ? min(P.max_sweeps, P.vlog_sweeps) : P.max_sweeps;
+  for (int sw = 0; sw < max_sw && !converged; ++sw) {
     bool rot = false;
     int I = 0, J = 1;
     int resI = -1;   // block held in slots [0, bc) (block mode)
@@ -2139,11 +2141,11 @@ JacobiPlan jacobi_plan(int m, int n, int max_smem, bool rec) {
   return jacobi_plan_impl<T>(m, n, max_smem, true, rec);
 }
 
-size_t jacobi_log_size(const JacobiPlan& pl, int max_sweeps) {
+size_t jacobi_log_size(const JacobiPlan& pl, int sweeps) {
   if (!pl.rec) return 0;
   int nps = 0, rmax = 0, kmax = 0;
   vlog_dims(pl.rc, pl.bcols, pl.rc <= 2 * pl.bcols, nps, rmax, kmax);
-  return (size_t)(max_sweeps > 0 ? max_sweeps : 1) * nps * rmax * kmax * 2 * kVlogRec;
+  return (size_t)(sweeps > 0 ? sweeps : 1) * nps * rmax * kmax * 2 * kVlogRec;
 }
 
 // Alternatives to the default plan for the autotuner, all with the default's
@@ -2168,7 +2170,11 @@ std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem, bool 
       JacobiPlan v = base;
       v.bcols = base.bcols + d;
       v.smem = 2 * (size_t)v.bcols * col_bytes + sort_bytes;
-      if (v.bcols >= 8 && v.bcols <= (base.rec ? 96 : 48) && v.smem <= (size_t)cap &&
+      // (the rotation-log form keeps the base's block count: the log is
+      // sized for the largest candidate)
+      const bool same_nb = !base.rec || (base.rc + v.bcols - 1) / v.bcols ==
+                                            (base.rc + base.bcols - 1) / base.bcols;
+      if (same_nb && v.bcols >= 8 && v.bcols <= (base.rec ? 96 : 48) && v.smem <= (size_t)cap &&
           base.rc > 2 * v.bcols &&
           (base.rc + v.bcols - 1) / v.bcols >= 3)
         out.push_back(v);

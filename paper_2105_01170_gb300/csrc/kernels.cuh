@@ -94,6 +94,7 @@ struct JacobiParams {
   // records every tile task's scaled rotations here instead (U and sigma as
   // usual, V not written); jacobi_v_replay forms the columns of V needed.
   float4* vlog = nullptr; int64_t vlog_bs = 0;  // float4s per slice (jacobi_log_size)
+  int vlog_sweeps = 0;                          // sweeps the log holds (the sweep limit then)
   int* order = nullptr;                         // out: pre-sort column of sorted column j
   int* vlsweeps = nullptr;                      // out: sweeps that rotated, per slice
 };
@@ -110,8 +111,14 @@ template <typename T> JacobiPlan jacobi_plan(int m, int n, int max_smem, bool re
 // and the same rec).
 template <typename T>
 std::vector<JacobiPlan> jacobi_plan_candidates(int m, int n, int max_smem, bool rec = false);
-// float4s of rotation log per slice for plan pl and at most max_sweeps sweeps.
-size_t jacobi_log_size(const JacobiPlan& pl, int max_sweeps);
+// Sweeps the rotation log holds for a sweep limit of max_sweeps (at most
+// kVlogMaxSweeps: the preconditioned slices converge in about 8), and the
+// float4s of log per slice for plan pl and that many sweeps.
+constexpr int kVlogMaxSweeps = 20;
+inline int jacobi_log_sweeps(int max_sweeps) {
+  return max_sweeps < 1 ? 1 : (max_sweeps < kVlogMaxSweeps ? max_sweeps : kVlogMaxSweeps);
+}
+size_t jacobi_log_size(const JacobiPlan& pl, int sweeps);
 // After a rotation-log Jacobi run P (plan pl): V[:, j] for the columns
 // j = ranks[s]..rc-1 of every slice s (all of them where ranks is NULL),
 // the logged tasks applied in reverse order to the unit vector of the
