@@ -1787,21 +1787,21 @@ __global__ void __launch_bounds__(32 * kClusterWarps)
 // CTA (s, g) forms the needed columns j = d0 + g + VR_SPLIT i of slice s
 // (d0 = ranks[s]) in shared memory, x[i] starting as the unit vector of the
 // pre-sort column order[j]; the columns of one slice spread over VR_SPLIT
-// CTAs, so a slice with few needed columns runs them in parallel.  V is the product of the
-// tasks' maps in execution order (each acting on the right, on the task's
-// eight columns), so its columns come from applying the maps in reverse:
-// sweeps, pair sets and rounds last to first; the tasks of a round act on
-// disjoint columns and run in parallel; a task's cross record goes before its
-// inner record.  A record maps x as the transpose of the row map of
-// tile_group's V pass: x_c *= d_c, then for the sub-rounds last to first and
-// each pair (a, b) with (t1, t2): x_a <- x_a + t2 x_b, x_b <- x_b - t1 x_a.
-// The schedule is the same in every sweep, so each task's eight columns and
-// kinds are tabled once; the coming rounds' records are copied from the log
-// into a ring in shared memory with cp.async (field-major there, so that the
-// lanes, one task each, read a field at consecutive addresses) while the
-// current round is applied.  A round's work is a short dependent chain, so a
-// slice with one needed column is replayed by one warp without block
-// barriers.
+// CTAs, so a slice with few needed columns runs them in parallel.  V is the
+// product of the tasks' maps in execution order (each acting on the right,
+// on the task's eight columns), so its columns come from applying the maps
+// in reverse: sweeps, pair sets and rounds last to first; the tasks of a
+// round act on disjoint columns and run in parallel; a task's cross record
+// goes before its inner record.  A record maps x as the transpose of the row
+// map of tile_group's V pass: x_c *= d_c, then for the sub-rounds last to
+// first and each pair (a, b) with (t1, t2): x_a <- x_a + t2 x_b,
+// x_b <- x_b - t1 x_a.  The schedule is the same in every sweep, so each
+// task's eight columns and kinds are tabled once; the coming rounds' records
+// are copied from the log into a ring in shared memory with cp.async
+// (field-major there, so that the lanes, one task each, read a field at
+// consecutive addresses) while the current round is applied.  A round's work
+// is a short dependent chain, so a CTA with one column is replayed by one
+// warp without block barriers.
 constexpr int VR_THREADS = 256;
 constexpr int VR_SPLIT = 32;   // CTAs per slice (grid y)
 constexpr int VR_COLS = 8;     // columns per CTA (rc <= VR_SPLIT VR_COLS)
